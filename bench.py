@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark of the DGR hot path on one B300: one optimisation iteration
+(voxelize -> project -> L1 residual -> backproject -> voxelize adjoint ->
+Adam) of 50,000 anisotropic Gaussians in a 256^3 grid against 50 cone-beam
+views of 256 x 256 pixels (source-origin 1000 mm, source-detector 1500 mm,
+1.5 mm pitch), synthetic ellipsoid phantom with N(0, 0.01^2) noise.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is DGR iterations/s with every input resident
+in HBM (CUDA events around each step on the launching stream, L2 flushed by a
+256 MiB write before every step, outside the events); `e2e` is the same
+metric through the C ABI with the measured projections copied host -> device
+from pinned memory and the loss copied back every step.  Under torchrun each
+rank runs an independent replica (the workload does not shard; no collective
+touches the data path) and rank 0 prints the aggregate.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "FVR Gvoxel-evals/s & DGR iters/s at 256³; time-to-PSNR, learned+batched vs plain"
+UNIT = "iter/s"
+WORKLOAD = 2  # 50,000 Gaussians, 256^3, cone 50 x 256^2
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS = 148
+MUFU_PER_CLK_SM = 16
+FFMA_PER_CLK_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            P = json.load(f)
+        return {"hbm_gbs": float(P["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(P.get("sm_max_mhz", 2032))}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "src": "fallback", "sm_max_mhz": 2032.0}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def setup_problem(rank, dev):
+    import torch
+    from paper_2411_04844_b300 import dgr, synth
+    wl = synth.workload(WORKLOAD)
+    rng = synth.rng_for(WORKLOAD, rank)
+    f = synth.gaussian_field(rng, wl.n_gauss, wl.grid, wl.scale)
+    f.rho = np.clip(f.rho, 0.02, 1.0).astype(np.float32)
+    phantom = synth.ellipsoid_phantom(synth.rng_for(WORKLOAD, 100 + rank), wl.grid, wl.phantom_m)
+    noise = synth.rng_for(WORKLOAD, 200 + rank).normal(0.0, wl.noise_sigma, wl.geom.shape).astype(np.float32)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    grid = dgr.Grid.of(wl.grid)
+    ang = T(wl.geom.angles)
+    geom = dgr.Geom.of(wl.geom, ang)
+    # measured projections: the phantom through the projector, plus noise
+    ws_p = dgr.Workspace(dgr.make_plan(grid, 0, 0, 0, geom))
+    meas = torch.empty(wl.geom.shape, device=dev)
+    dgr.dgr_project(grid, geom, T(phantom), meas, ws_p)
+    meas += T(noise)
+    torch.cuda.synchronize()
+    ws_p.close()
+    mu, s, q, rho = T(f.mu), T(f.s), T(f.q), T(f.rho)
+    ws0 = dgr.Workspace(dgr.make_plan(grid, f.n))
+    pairs, items = dgr.dgr_voxelize_count(grid, mu, s, q, wl.k_trunc, ws0)
+    # in-box (Gaussian, voxel) pairs: the algorithmic work of voxelize
+    an = torch.empty((f.n, 3), dtype=torch.int32, device=dev)
+    bx = torch.empty((f.n, 6), dtype=torch.int32, device=dev)
+    dgr.dgr_footprint(grid, mu, s, q, wl.k_trunc, an, bx)
+    ext = (bx[:, 3:] - bx[:, :3] + 1).clamp(min=0).to(torch.float64)
+    inbox = float(ext.prod(1).sum())
+    ws0.close()
+    plan = dgr.make_plan(grid, f.n, int(pairs * 1.5) + 1024, int(items * 1.5) + 1024, geom, step=True)
+    ws = dgr.Workspace(plan)
+    prob = dgr.make_problem(grid, geom, wl.k_trunc, 3e-4, 3e-5, wl.n_iters)
+    st = dgr.State(mu, s, q, rho)
+    dgr.dgr_params_init(prob, st)
+    return dict(wl=wl, grid=grid, geom=geom, ang=ang, meas=meas, ws=ws, prob=prob, st=st,
+                pairs=pairs, items=items, inbox=inbox, f=f)
+
+
+def run_ours(args, dist, rank, local):
+    import torch
+    from paper_2411_04844_b300 import dgr
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    P = setup_problem(rank, dev)
+    wl, ws, prob, st, meas = P["wl"], P["ws"], P["prob"], P["st"], P["meas"]
+    stream = torch.cuda.current_stream()
+    loss = torch.zeros(1, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    K, W = args.steps, args.warmup
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(dgr.DGR_STEP_EVENTS)] for _ in range(K)]
+    for row in ev:
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for _ in range(W):
+        flush.zero_()
+        dgr.dgr_step(prob, st, meas, loss, ws)
+    torch.cuda.synchronize()
+    status = dgr.dgr_status(ws)
+    if status:
+        raise RuntimeError(f"device status {status:#x} after warm-up")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    barrier(dist)
+    torch.cuda.synchronize()
+    l0 = dgr.dgr_launch_count()
+    t_wall0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        dgr.dgr_step_timed(prob, st, meas, loss, ws, ev[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = dgr.dgr_launch_count() - l0
+    barrier(dist)
+    step_ms = [ev[k][0].elapsed_time(ev[k][6]) for k in range(K)]
+    phase_ms = {name: [ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]
+                for i, name in enumerate(dgr.STEP_PHASES)}
+
+    # end to end through the C ABI: pinned host measured -> device, step, loss -> host
+    meas_host = meas.cpu().pin_memory()
+    loss_host = torch.zeros(1).pin_memory()
+    meas_dev = torch.empty_like(meas)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        e0[k].record(stream)
+        meas_dev.copy_(meas_host, non_blocking=True)
+        dgr.dgr_step(prob, st, meas_dev, loss, ws)
+        loss_host.copy_(loss, non_blocking=True)
+        e1[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    e2e_ms = [e0[k].elapsed_time(e1[k]) for k in range(K)]
+    status = dgr.dgr_status(ws)
+    if status:
+        raise RuntimeError(f"device status {status:#x} after timed steps")
+    if not math.isfinite(float(loss_host.item())):
+        raise RuntimeError("non-finite loss")
+
+    tot_s = max_over_ranks(dist, sum(step_ms) / 1000.0)
+    tot_e2e = max_over_ranks(dist, sum(e2e_ms) / 1000.0)
+    N = args.gpus
+    value = N * K / tot_s
+    e2e_value = N * K / tot_e2e
+    phases = {k: statistics.mean(v) for k, v in phase_ms.items()}
+    return dict(P=P, value=value, e2e=e2e_value, step_ms=statistics.mean(step_ms), phases=phases,
+                launches=launches, clocks=clk, t_wall=t_wall, loss=float(loss_host.item()))
+
+
+def roofline(P, phases, clk, pk):
+    """Roofline of the dominant kernel (longest phase) of one iteration."""
+    wl = P["wl"]
+    nvox = wl.grid.dims[0] * wl.grid.dims[1] * wl.grid.dims[2]
+    nrays = wl.geom.n_views * wl.geom.nu * wl.geom.nv
+    proj_bytes = 4.0 * nvox * wl.geom.n_views + 4.0 * nrays
+    mhz = clk.get("sm_mhz") or pk["sm_max_mhz"]
+    sfu_peak = SMS * MUFU_PER_CLK_SM * mhz * 1e6 / 1e9  # G ex2 / s
+    ffma_peak = SMS * FFMA_PER_CLK_SM * mhz * 1e6 / 1e9  # G FFMA / s
+    per = {}
+    for name, ms in phases.items():
+        s = ms / 1000.0
+        if name in ("project", "backproject"):
+            a = proj_bytes / s / 1e9
+            per[name] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": a / pk["hbm_gbs"], "ms": ms}
+        elif name == "voxelize":
+            a = P["inbox"] / s / 1e9
+            per[name] = {"bound": "alu", "achieved": a, "peak": sfu_peak, "unit": "Gex2/s",
+                         "frac": a / sfu_peak, "ms": ms}
+        elif name == "voxelize_backward":
+            a = 12.0 * P["inbox"] / s / 1e9
+            per[name] = {"bound": "alu", "achieved": a, "peak": ffma_peak, "unit": "GFFMA/s",
+                         "frac": a / ffma_peak, "ms": ms}
+        else:
+            per[name] = {"ms": ms}
+    dom = max(phases, key=lambda k: phases[k])
+    r = dict(per[dom])
+    r.pop("ms", None)
+    r["kernel"] = dom
+    r["peak_src"] = pk["src"] if r.get("unit") == "GB/s" else f"{SMS} SMs x unit rate x {mhz:.0f} MHz"
+    r["traffic"] = traffic_for(dom)
+    return r, per
+
+
+def traffic_for(phase):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the counters were taken; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            T = json.load(f)
+        ent = T[phase]
+        src = os.path.join(ROOT, "paper_2411_04844_b300", "csrc", ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return float(ent["dram_bytes_per_launch"]) if h == ent["source_sha256_16"] else None
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(frac_gauss, n_views_sample, seed_rank=0):
+    """Time the FP64 oracle on a bounded sample of one iteration of the
+    workload and scale to a full iteration.  Returns (iters/s, threads,
+    description, seconds spent)."""
+    import oracle as O
+    from paper_2411_04844_b300 import synth
+    wl = synth.workload(WORKLOAD)
+    f = synth.gaussian_field(synth.rng_for(WORKLOAD, seed_rank), wl.n_gauss, wl.grid, wl.scale)
+    ng = max(1, int(round(wl.n_gauss * frac_gauss)))
+    og = O.Grid(wl.grid.dims, wl.grid.h, wl.grid.org)
+    geo = wl.geom
+    idx = np.linspace(0, geo.n_views - 1, n_views_sample).round().astype(int)
+    oo = O.Geom(geo.beam, geo.angles[idx], geo.nu, geo.nv, geo.pu, geo.pv, geo.dso, geo.dsd)
+    t0 = time.perf_counter()
+    vol = O.voxelize(og, f.mu[:ng], f.s[:ng], f.q[:ng], f.rho[:ng], wl.k_trunc)
+    t1 = time.perf_counter()
+    sino = O.project(og, oo, vol)
+    t2 = time.perf_counter()
+    gv = O.backproject(og, oo, np.sign(sino) / sino.size)
+    t3 = time.perf_counter()
+    O.voxelize_backward(og, f.mu[:ng], f.s[:ng], f.q[:ng], f.rho[:ng], gv, wl.k_trunc)
+    t4 = time.perf_counter()
+    sg = wl.n_gauss / ng
+    sv = geo.n_views / n_views_sample
+    t_iter = (t1 - t0) * sg + (t2 - t1) * sv + (t3 - t2) * sv + (t4 - t3) * sg
+    desc = (f"FP64 oracle on {O.num_threads()} threads: voxelize + adjoint of {ng} of "
+            f"{wl.n_gauss} Gaussians, project + backproject of {n_views_sample} of "
+            f"{geo.n_views} views, 256^3 grid; scaled to one full iteration")
+    return 1.0 / t_iter, O.num_threads(), desc, t4 - t0
+
+
+def cpu_baseline(target_s):
+    # calibrate on a small sample, then size the sample to ~target_s
+    v, th, desc, spent = oracle_sample(0.01, 1)
+    scale = max(1.0, min(8.0, target_s / max(spent, 1e-3)))
+    fg = min(1.0, 0.01 * scale)
+    nv = int(max(1, min(50, round(scale))))
+    v, th, desc, spent = oracle_sample(fg, nv)
+    return {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": desc,
+            "seconds": round(spent, 2)}
+
+
+def run_reference(args, rank, ws_n):
+    """The reference arm: the FP64 oracle as it stands, on the host cores,
+    each step a bounded sample of one iteration."""
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    per = []
+    desc = th = None
+    for k in range(W + K):
+        v, th, desc, spent = oracle_sample(0.004, 1, seed_rank=k % 3)
+        if k >= W:
+            per.append(1.0 / v)
+    value = K / sum(per)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1000.0 * sum(per) / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                             "sample": desc + " (per step)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def config_block():
+    return {"workload": "cone256_50k: 50,000 anisotropic Gaussians (log-uniform scales 0.5-6 "
+                        "voxels, 3-sigma boxes) -> 256^3 grid, cone beam 50 views x 256^2 "
+                        "(dso 1000, dsd 1500, pitch 1.5 mm), 40-ellipsoid phantom + N(0,0.01^2)",
+            "grid": [256, 256, 256], "n_gauss": 50000, "views": 50, "detector": [256, 256],
+            "l2": "flushed before every step by a 256 MiB write (outside the timed events)",
+            "parallelism": "replicas (one independent reconstruction per GPU)"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = dist_init(world)
+    R = run_ours(args, dist, rank, local)
+    if rank != 0:
+        return
+    pk = peaks()
+    roof, per = roofline(R["P"], R["phases"], R["clocks"], pk)
+    P = R["P"]
+    wl = P["wl"]
+    fvr_ms = R["phases"]["voxelize"]
+    line = {
+        "metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": R["step_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_block(),
+        "fvr_gvoxel_evals_per_s": P["inbox"] / (fvr_ms / 1000.0) / 1e9,
+        "phases_ms": {k: round(v, 4) for k, v in R["phases"].items()},
+        "phase_roofline": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                               for kk, vv in v.items()} for k, v in per.items()},
+        "work": {"inbox_pairs": P["inbox"], "tile_pairs": P["pairs"], "items": P["items"]},
+        "roofline": roof,
+        "e2e": {"value": R["e2e"], "unit": UNIT, "h2d_bytes_per_step": int(P["meas"].numel() * 4),
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": R["launches"],
+        "clocks": R["clocks"],
+        "loss": R["loss"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * dgr.h -- C ABI of the B300 (sm_103a) hot path of Discretized Gaussian
+ * Representation (DGR, arxiv 2411.04844): Fast Volume Reconstruction (FVR),
+ * the X-ray projector, their adjoints and one optimisation step.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Array arguments are DEVICE pointers to contiguous FP32 (or int32)
+ *    memory owned by the caller; descriptor structs and the scalars they hold
+ *    live in HOST memory and are read before the call returns.
+ *  - Volumes are [nz][ny][nx] (x fastest).  Voxel (i, j, k) has its centre at
+ *    (ox + (i + 1/2) h, oy + (j + 1/2) h, oz + (k + 1/2) h).
+ *  - Sinograms are [n_views][nv][nu] (u fastest).
+ *  - Gaussian parameters: mu [n][3] world units; s [n][3] per-axis standard
+ *    deviations, world units, > 0; q [n][4] rotation quaternion (w, x, y, z),
+ *    need not be normalised (it is normalised inside); rho [n] intensity
+ *    (the paper's I).  Sigma = R(q) diag(s^2) R(q)^T.
+ *  - Every call is asynchronous on `stream`, never synchronises (except the
+ *    explicitly synchronous dgr_voxelize_count and dgr_status) and never
+ *    allocates: device scratch comes from a dgr_ws made by dgr_ws_create.
+ *  - Return value: DGR_OK, or a host-detected error (DGR_ERR_ARG,
+ *    DGR_ERR_WS_TOO_SMALL, DGR_ERR_CUDA) in which case nothing was launched
+ *    (DGR_ERR_CUDA: a launch failed; the stream may hold earlier launches).
+ *    Errors found on the device (non-finite inputs, work-list overflow) are
+ *    OR-ed into the workspace's device status word, read with dgr_status.
+ *  - Thread safety: calls sharing one dgr_ws must be ordered on one stream.
+ */
+#ifndef DGR_H
+#define DGR_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* host-detected return codes */
+#define DGR_OK 0
+#define DGR_ERR_ARG 1
+#define DGR_ERR_WS_TOO_SMALL 2
+#define DGR_ERR_CUDA 3
+/* device status bits (dgr_status) */
+#define DGR_STATUS_NONFINITE 0x10   /* a Gaussian had a non-finite parameter; it was skipped */
+#define DGR_STATUS_PAIR_OVERFLOW 0x20 /* (tile, Gaussian) work list exceeded the plan; volume incomplete */
+#define DGR_STATUS_ITEM_OVERFLOW 0x40 /* backward work items exceeded the plan; gradients incomplete */
+
+/* Voxel grid: nx, ny, nz <= 32767 voxels of size h, min corner (ox, oy, oz). */
+typedef struct {
+    int nx, ny, nz;
+    float h;
+    float ox, oy, oz;
+} dgr_grid;
+
+#define DGR_PARALLEL 0
+#define DGR_CONE 1
+
+/* Scan geometry (paper Sec. 4.3: "general geometry projection transformation";
+ * conventions fixed by this library):  views rotate about z by angles[k]
+ * (radians, DEVICE array [n_views]); r = (cos a, sin a, 0), e_u = (-sin a,
+ * cos a, 0), e_v = (0, 0, 1); detector pixel (iu, iv) sits at
+ * u = (iu - (nu-1)/2) pu, v = (iv - (nv-1)/2) pv.
+ *   parallel: the ray through u e_u + v e_v along r.
+ *   cone:     source at -dso r, flat detector centred at (dsd - dso) r; the
+ *             ray from the source through the pixel centre.
+ * Line integrals are in (value x world length). */
+typedef struct {
+    int beam;          /* DGR_PARALLEL or DGR_CONE */
+    int n_views, nu, nv;
+    float pu, pv;      /* detector pitch, world units */
+    float dso, dsd;    /* cone only: source-origin, source-detector distance */
+    const float *angles; /* device [n_views] */
+} dgr_geom;
+
+/* Opaque device workspace: one cudaMalloc made by dgr_ws_create, carved by
+ * every call according to the plan it was created with. */
+typedef struct dgr_ws dgr_ws;
+
+/* What a workspace must hold.  max_pairs bounds the (voxel tile, Gaussian)
+ * work list of the voxelizer; max_items bounds the backward work items
+ * (z-chunks of Gaussian boxes).  Use dgr_voxelize_count for exact values.
+ * grid_vox/rays > 0 reserve the step's volume and sinogram buffers. */
+typedef struct {
+    int max_n;               /* largest Gaussian count */
+    int max_tiles;           /* largest number of voxel tiles (dgr_tile_count) */
+    long long max_pairs;
+    long long max_items;
+    long long max_vox;       /* dgr_step only: voxels of the volume (0 otherwise) */
+    long long max_rays;      /* dgr_step only: rays of the sinogram (0 otherwise) */
+    int max_views, max_nu, max_nv; /* projector tables */
+} dgr_ws_plan;
+
+/* Bytes a workspace with this plan needs. */
+int dgr_ws_bytes(const dgr_ws_plan *plan, size_t *bytes);
+/* The only allocating calls: cudaMalloc / cudaFree of the workspace arena. */
+int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan);
+int dgr_ws_destroy(dgr_ws *ws);
+/* Voxel tiles (8 x 16 x 8 voxels) covering a grid. */
+int dgr_tile_count(const dgr_grid *grid, int *tiles);
+
+/* Reads and clears the device status word (synchronises `stream`). */
+int dgr_status(dgr_ws *ws, cudaStream_t stream, int *status);
+const char *dgr_strerror(int code);
+/* 1 (default): the voxelizer sorts each tile's Gaussian list, so results are
+ * bit-reproducible run to run; 0: skip the sort (order follows atomics). */
+int dgr_set_deterministic(int on);
+
+/* Footprint integers (paper Sec. 4.1 "Gaussian Effect Confinement",
+ * "Discretize and Align" Eq. 6; valid mask of Algorithm 1):
+ * anchor a = floor(u), u = (mu - o)/h - 1/2 (voxel centres at integers);
+ *   k_trunc > 0: per axis R = ceil(k_trunc * sigma_a), sigma_a = sqrt(Sigma_aa)/h,
+ *                box [a - R, a + R + 1];
+ *   k_trunc < 0: the paper's fixed odd box K = -k_trunc, [a - (K-1)/2, a + (K-1)/2];
+ * clipped to the grid (axis empty when lo > hi).  Computed with a fixed FP32
+ * operation sequence (every operation rounded on its own).
+ * anchor [n][3], box [n][6] = (lo x, y, z, hi x, y, z), device int32. */
+int dgr_footprint(const dgr_grid *grid, int n, const float *mu, const float *s, const float *q,
+                  float k_trunc, int *anchor, int *box, cudaStream_t stream);
+
+/* Exact work-list sizes for these Gaussians (synchronises `stream`). */
+int dgr_voxelize_count(const dgr_grid *grid, int n, const float *mu, const float *s,
+                       const float *q, float k_trunc, long long *pairs, long long *items,
+                       dgr_ws *ws, cudaStream_t stream);
+
+/* FVR forward (paper Eq. 4 with confinement, Eq. 6-7 alignment, Algorithm 1):
+ * vol[v] = sum_g rho_g exp(-1/2 (v - u_g)^T A_g (v - u_g)) over the voxels of
+ * each Gaussian's box, A_g = h^2 Sigma_g^-1.  Overwrites vol [nz][ny][nx]. */
+int dgr_voxelize(const dgr_grid *grid, int n, const float *mu, const float *s, const float *q,
+                 const float *rho, float k_trunc, float *vol, dgr_ws *ws, cudaStream_t stream);
+
+/* Adjoint of dgr_voxelize: given grad_vol = dL/dV, writes dL/dmu [n][3],
+ * dL/ds [n][3], dL/dq [n][4], dL/drho [n] (overwrites).  Box and anchor are
+ * held fixed (piecewise-constant), the gradient to mu flowing through
+ * u - a (paper Sec. 4.1, end of "Discretize and Align"). */
+int dgr_voxelize_backward(const dgr_grid *grid, int n, const float *mu, const float *s,
+                          const float *q, const float *rho, float k_trunc, const float *grad_vol,
+                          float *g_mu, float *g_s, float *g_q, float *g_rho, dgr_ws *ws,
+                          cudaStream_t stream);
+
+/* Projector T (paper Sec. 4.3, Eq. 12, P_hat = T(V)): each detector pixel is
+ * the exact line integral of the piecewise-constant voxel image along its ray
+ * (Siddon's radiological path).  Overwrites sino [n_views][nv][nu]. */
+int dgr_project(const dgr_grid *grid, const dgr_geom *geom, const float *vol, float *sino,
+                dgr_ws *ws, cudaStream_t stream);
+
+/* Exact transpose of dgr_project: vol[v] = sum_rays L(ray, v) sino[ray], with
+ * L the same chord lengths.  Gathers per voxel (no atomics).  Overwrites vol. */
+int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sino, float *vol,
+                    dgr_ws *ws, cudaStream_t stream);
+
+/* L1 data term of the paper's objective (Sec. 4.3, Eq. 13, first term):
+ * loss = mean |pred - meas| (device scalar, fixed-order reduction) and
+ * resid = sign(pred - meas) / m (sign(0) = 0).  resid may alias pred. */
+int dgr_l1_residual(const float *pred, const float *meas, long long m, float *resid,
+                    float *loss, dgr_ws *ws, cudaStream_t stream);
+
+/* One optimisation iteration (paper Sec. 4.3 "Global Optimization"; Adam with
+ * lr decaying lr0 -> lr1, Sec. 5.1 "Implementation Details"). */
+typedef struct {
+    dgr_grid grid;
+    dgr_geom geom;
+    float k_trunc;
+    float lr0, lr1;    /* lr(t) = lr0 (lr1/lr0)^((t-1)/(n_iters-1)), t = 1..n_iters */
+    int n_iters;
+    float beta1, beta2, eps;
+} dgr_problem;
+
+/* Optimiser state.  theta/m/v are [11 n] laid out [mu 3n | s 3n | q 4n | rho n]
+ * with theta = ((mu - c)/half, log s, q, softplus^-1(rho)), c and half the
+ * grid centre and half-extent.  mu/s/q/rho are rewritten from theta by every
+ * step; step is a device int counting completed steps. */
+typedef struct {
+    int n;
+    float *mu, *s, *q, *rho;
+    float *theta, *m, *v;
+    int *step;
+} dgr_params;
+
+/* theta from (mu, s, q, rho); m = v = 0; step = 0. */
+int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t stream);
+
+/* voxelize -> project -> L1 residual -> backproject -> voxelize adjoint ->
+ * chain rule to theta -> Adam.  measured: device [n_views][nv][nu];
+ * loss_out: device scalar (the L1 loss before the update).  The workspace
+ * plan must carry max_vox and max_rays of this problem. */
+int dgr_step(const dgr_problem *prob, const dgr_params *p, const float *measured,
+             float *loss_out, dgr_ws *ws, cudaStream_t stream);
+
+/* dgr_step with CUDA events recorded on `stream` at its phase boundaries:
+ * events[0] before voxelize, [1] after voxelize, [2] after project, [3] after
+ * the L1 residual, [4] after backproject, [5] after the voxelize adjoint,
+ * [6] after Adam.  events: host array of n_events (>= 7) cudaEvent_t. */
+#define DGR_STEP_EVENTS 7
+int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *measured,
+                   float *loss_out, dgr_ws *ws, cudaStream_t stream, cudaEvent_t *events,
+                   int n_events);
+
+/* Total number of kernels this library has launched in this process (a host
+ * counter; lets callers count launches inside a timed region). */
+long long dgr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGR_H */

@@ -84,9 +84,12 @@ void oracle_footprint(const int dims[3], float h, const float org[3], int n,
     for (int g = 0; g < n; ++g) {
         float R[9];
         rot_from_quat_f32(q + 4 * g, R);
+        int far = 0;
         for (int a = 0; a < 3; ++a) {
             float u = (mu[3 * g + a] - org[a]) / h;
             u = u - 0.5f;
+            /* |u| >= 2^24 voxels: treated as outside the grid */
+            if (!(fabsf(u) < 16777216.0f)) { far = 1; u = 0.0f; }
             int an = (int)floorf(u);
             int rad;
             if (k_trunc > 0.0f) {
@@ -97,7 +100,9 @@ void oracle_footprint(const int dims[3], float h, const float org[3], int n,
                 var = var + t1 * t1;
                 var = var + t2 * t2;
                 float sig = sqrtf(var) / h;
-                rad = (int)ceilf(k_trunc * sig);
+                float kr = k_trunc * sig;
+                /* a radius beyond the grid only needs to cover the grid */
+                rad = kr < 65536.0f ? (int)ceilf(kr) : 65536;
             } else {
                 rad = 0; /* fixed box handled below */
             }
@@ -117,6 +122,8 @@ void oracle_footprint(const int dims[3], float h, const float org[3], int n,
             box[6 * g + a] = lo;
             box[6 * g + 3 + a] = hi;
         }
+        if (far)
+            for (int a = 0; a < 3; ++a) { box[6 * g + a] = 1; box[6 * g + 3 + a] = 0; }
     }
 }
 

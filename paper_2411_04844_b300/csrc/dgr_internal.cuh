@@ -1,0 +1,115 @@
+// Internal definitions of libdgr (sm_103a).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "dgr.h"
+
+namespace dgr {
+
+// Voxel tile of the forward voxelizer: 8 (x) x 16 (y) x 8 (z).  A CTA of four
+// warps owns one tile; a warp owns an 8 x 4 patch in (x, y) and every lane
+// keeps the 8 z-voxels of its (x, y) column in registers.
+constexpr int TX = 8, TY = 16, TZ = 8;
+constexpr int VOX_THREADS = 128;
+constexpr int VOX_CHUNK = 64;  // prep records staged in shared memory at a time
+
+// Backward work item: a z-chunk of one Gaussian's box holding at most about
+// ITEM_VOX voxels, processed by one warp.
+constexpr int ITEM_VOX = 2048;
+constexpr int NMOM = 10;  // moments per item: S0, S1[3], S2[6]
+
+// log2(e): the exponent exp(-x/2) is evaluated as ex2(-x/2 * log2(e)).
+constexpr float LOG2E = 1.4426950408889634f;
+
+// Per-Gaussian record written by the prep kernel (64 bytes, 4 x float4).
+struct __align__(16) Prep {
+    float dx, dy, dz, rho;      // delta = u - a (voxel units), intensity
+    float a00, a11, a22, a01;   // -1/2 log2(e) * A, off-diagonals doubled
+    float a02, a12;
+    int ax, ay;                 // anchor a = floor(u)
+    int az;
+    int bx, by, bz;             // box per axis: lo | hi << 16 (lo > hi: empty)
+};
+static_assert(sizeof(Prep) == 64, "Prep must be 64 bytes");
+
+__host__ __device__ inline int box_lo(int p) { return (int)(short)(p & 0xffff); }
+__host__ __device__ inline int box_hi(int p) { return (int)(short)((unsigned)p >> 16); }
+__host__ __device__ inline int box_pack(int lo, int hi) {
+    return (int)(((unsigned)lo & 0xffffu) | (((unsigned)hi & 0xffffu) << 16));
+}
+
+// Per (view, iu) ray data of the projector: the ray is X(t) = X0 + t D with
+// X0 the point of the (x, y) line closest to the grid axis.  xi = (X - o)/h
+// is the continuous voxel coordinate; e = D / h.
+struct __align__(16) RayXY {
+    float xi0x, xi0y, ex, ey;
+    float inv_ex, inv_ey, tc, dxy2;  // 1/e (0 when e == 0), t-shift for z, |D_xy|^2
+};
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// host-side count of kernel launches issued by the library
+extern std::atomic<long long> g_launches;
+inline void counted(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+}  // namespace dgr
+
+// Workspace: one device arena and the plan that fixed its layout.
+struct dgr_ws {
+    char *base;
+    size_t bytes;
+    dgr_ws_plan plan;
+    // byte offsets into base
+    size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
+        partials, grads, vol, sino, loss_part, rayxy;
+    size_t scan_tmp_elems;
+};
+
+namespace dgr {
+template <class T>
+inline T *ws_ptr(dgr_ws *ws, size_t off) { return reinterpret_cast<T *>(ws->base + off); }
+
+// scan.cu
+// Exclusive scan of len uint32 counts into out[0..len] (out[len] = total).
+// If the total exceeds cap, `flag` is OR-ed into *status and out[len] keeps
+// the (saturated) total.
+cudaError_t scan_u32(const uint32_t *in, uint32_t *out, int len, unsigned long long cap,
+                     int *status, int flag, unsigned long long *tmp, cudaStream_t st);
+size_t scan_tmp_elems(int len);
+
+// voxelize.cu
+int tile_dims(const dgr_grid &g, int &ntx, int &nty, int &ntz);
+cudaError_t launch_prep(const dgr_grid &g, int n, const float *mu, const float *s, const float *q,
+                        const float *rho, float k, Prep *prep, uint32_t *itemcnt, int *status,
+                        cudaStream_t st);
+cudaError_t launch_voxelize(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws, float *vol,
+                            int deterministic, cudaStream_t st);
+cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const float *s,
+                             const float *q, float k, int *anchor, int *box, cudaStream_t st);
+cudaError_t launch_count_pairs(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws,
+                               unsigned long long cap, cudaStream_t st);
+
+// voxelize_bwd.cu
+cudaError_t launch_voxelize_backward(const dgr_grid &g, int n, const float *mu, const float *s,
+                                     const float *q, const float *rho, const Prep *prep,
+                                     const float *grad_vol, float *g_mu, float *g_s, float *g_q,
+                                     float *g_rho, dgr_ws *ws, cudaStream_t st);
+
+// project.cu
+cudaError_t launch_ray_tables(const dgr_grid &g, const dgr_geom &geo, RayXY *tab, cudaStream_t st);
+cudaError_t launch_project(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
+                           const float *vol, float *sino, cudaStream_t st);
+cudaError_t launch_backproject(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
+                               const float *sino, float *vol, cudaStream_t st);
+
+// step.cu
+cudaError_t launch_l1(const float *pred, const float *meas, long long m, float *resid, float *loss,
+                      float *part, cudaStream_t st);
+cudaError_t launch_params_init(const dgr_problem &P, const dgr_params &p, cudaStream_t st);
+cudaError_t launch_adam(const dgr_problem &P, const dgr_params &p, const float *grads,
+                        cudaStream_t st);
+constexpr int L1_BLOCKS = 592;  // 4 x 148 SMs; fixed so the loss reduction order is fixed
+}  // namespace dgr

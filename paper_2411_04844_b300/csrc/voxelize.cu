@@ -1,0 +1,438 @@
+// Fast Volume Reconstruction forward on sm_103a.
+//
+//   a1  k_prep          per Gaussian: footprint integers (fixed FP32 op
+//                       sequence), anchor, delta = u - a, scaled precision A'
+//   a2  k_tile_count /  binning: per-tile Gaussian counts, exclusive scan,
+//       k_tile_fill /   fill of the (tile, Gaussian) work list, sort of each
+//       k_tile_sort     tile's list by Gaussian index (deterministic order)
+//   a3  k_voxelize      one CTA per 8x16x8 tile: prep records staged in shared
+//                       memory, voxels in registers, one ex2 per in-box pair
+//
+// The paper (Sec. 4.2, Algorithm 1) materialises a [n, 17, 17, 17]
+// contribution tensor and scatter_adds it with global atomics; here nothing
+// per pair is stored and every voxel is written once by the CTA owning it.
+#include <math.h>
+
+#include "dgr_internal.cuh"
+
+namespace dgr {
+namespace {
+
+// ---------------------------------------------------------------------------
+// footprint integers: the fixed FP32 sequence (every operation rounded on
+// its own; no contraction) shared with the CPU oracle by specification only
+// ---------------------------------------------------------------------------
+struct Foot {
+    float R[9];  // rotation of the normalised quaternion (FP32)
+    int an[3], lo[3], hi[3];
+};
+
+__device__ __forceinline__ void rot_f32_exact(float w, float x, float y, float z, float *R) {
+    float n2 = __fmul_rn(w, w);
+    n2 = __fadd_rn(n2, __fmul_rn(x, x));
+    n2 = __fadd_rn(n2, __fmul_rn(y, y));
+    n2 = __fadd_rn(n2, __fmul_rn(z, z));
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
+    w = __fmul_rn(w, inv); x = __fmul_rn(x, inv); y = __fmul_rn(y, inv); z = __fmul_rn(z, inv);
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+    const float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+    R[0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+    R[1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    R[2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    R[3] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    R[4] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+    R[5] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    R[6] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    R[7] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    R[8] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+}
+
+__device__ __forceinline__ void footprint_f32(const dgr_grid &g, const float *mu, const float *s,
+                                              const float4 q, float k, Foot &F) {
+    rot_f32_exact(q.x, q.y, q.z, q.w, F.R);
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    const float org[3] = {g.ox, g.oy, g.oz};
+    bool far = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = __fdiv_rn(__fsub_rn(mu[a], org[a]), g.h);
+        u = __fsub_rn(u, 0.5f);
+        // |u| >= 2^24 voxels: the Gaussian is treated as outside the grid
+        if (!(fabsf(u) < 16777216.0f)) { far = true; u = 0.0f; }
+        const int an = (int)floorf(u);
+        int lo, hi;
+        if (k > 0.0f) {
+            const float t0 = __fmul_rn(F.R[3 * a + 0], s[0]);
+            const float t1 = __fmul_rn(F.R[3 * a + 1], s[1]);
+            const float t2 = __fmul_rn(F.R[3 * a + 2], s[2]);
+            float var = __fmul_rn(t0, t0);
+            var = __fadd_rn(var, __fmul_rn(t1, t1));
+            var = __fadd_rn(var, __fmul_rn(t2, t2));
+            const float sig = __fdiv_rn(__fsqrt_rn(var), g.h);
+            const float kr = __fmul_rn(k, sig);
+            // a radius beyond the grid only needs to cover the grid
+            const int rad = kr < 65536.0f ? (int)ceilf(kr) : 65536;
+            lo = an - rad;
+            hi = an + rad + 1;
+        } else {
+            const int K = (int)(-k);
+            const int half = (K - 1) / 2;
+            lo = an - half;
+            hi = an + half;
+        }
+        lo = max(lo, 0);
+        hi = min(hi, dims[a] - 1);
+        F.an[a] = an;
+        F.lo[a] = lo;
+        F.hi[a] = hi;
+    }
+    if (far) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { F.lo[a] = 1; F.hi[a] = 0; }
+    }
+}
+
+__device__ __forceinline__ bool finite3(const float *p) {
+    return isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]);
+}
+
+__global__ void k_footprint(dgr_grid g, int n, const float *__restrict__ mu,
+                            const float *__restrict__ s, const float4 *__restrict__ q, float k,
+                            int *__restrict__ anchor, int *__restrict__ box) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float m[3] = {mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]};
+    float sc[3] = {s[3 * i], s[3 * i + 1], s[3 * i + 2]};
+    Foot F;
+    footprint_f32(g, m, sc, q[i], k, F);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        anchor[3 * i + a] = F.an[a];
+        box[6 * i + a] = F.lo[a];
+        box[6 * i + 3 + a] = F.hi[a];
+    }
+}
+
+// a1: per-Gaussian prep.
+__global__ void k_prep(dgr_grid g, int n, const float *__restrict__ mu, const float *__restrict__ s,
+                       const float4 *__restrict__ q, const float *__restrict__ rho, float k,
+                       Prep *__restrict__ prep, uint32_t *__restrict__ itemcnt, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float m[3] = {mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]};
+    float sc[3] = {s[3 * i], s[3 * i + 1], s[3 * i + 2]};
+    const float4 qq = q[i];
+    const float r = rho[i];
+    Prep P;
+    bool ok = finite3(m) && finite3(sc) && isfinite(qq.x) && isfinite(qq.y) && isfinite(qq.z) &&
+              isfinite(qq.w) && isfinite(r) && sc[0] > 0.f && sc[1] > 0.f && sc[2] > 0.f &&
+              (qq.x != 0.f || qq.y != 0.f || qq.z != 0.f || qq.w != 0.f);
+    if (!ok) {
+        atomicOr(status, DGR_STATUS_NONFINITE);
+        P = Prep{};
+        P.bx = P.by = P.bz = box_pack(1, 0);  // empty
+        prep[i] = P;
+        itemcnt[i] = 0;
+        return;
+    }
+    Foot F;
+    footprint_f32(g, m, sc, qq, k, F);
+    // delta = u - a, with u in FP64 so the fractional offset is exact to FP32
+    const double h = (double)g.h;
+    const double org[3] = {(double)g.ox, (double)g.oy, (double)g.oz};
+    float del[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double u = ((double)m[a] - org[a]) / h - 0.5;
+        del[a] = (float)(u - (double)F.an[a]);
+    }
+    // A = h^2 R diag(1/s^2) R^T (voxel units), scaled by -1/2 log2(e)
+    const float* R = F.R;
+    const float h2 = g.h * g.h;
+    const float is0 = h2 / (sc[0] * sc[0]), is1 = h2 / (sc[1] * sc[1]), is2 = h2 / (sc[2] * sc[2]);
+    float A[6];
+    A[0] = R[0] * R[0] * is0 + R[1] * R[1] * is1 + R[2] * R[2] * is2;  // 00
+    A[1] = R[3] * R[3] * is0 + R[4] * R[4] * is1 + R[5] * R[5] * is2;  // 11
+    A[2] = R[6] * R[6] * is0 + R[7] * R[7] * is1 + R[8] * R[8] * is2;  // 22
+    A[3] = R[0] * R[3] * is0 + R[1] * R[4] * is1 + R[2] * R[5] * is2;  // 01
+    A[4] = R[0] * R[6] * is0 + R[1] * R[7] * is1 + R[2] * R[8] * is2;  // 02
+    A[5] = R[3] * R[6] * is0 + R[4] * R[7] * is1 + R[5] * R[8] * is2;  // 12
+    const float c = -0.5f * LOG2E;
+    P.dx = del[0]; P.dy = del[1]; P.dz = del[2]; P.rho = r;
+    P.a00 = c * A[0]; P.a11 = c * A[1]; P.a22 = c * A[2];
+    P.a01 = 2.f * c * A[3]; P.a02 = 2.f * c * A[4]; P.a12 = 2.f * c * A[5];
+    P.ax = F.an[0]; P.ay = F.an[1]; P.az = F.an[2];
+    // an axis that misses the grid empties the whole box (packed as lo 1, hi 0)
+    const bool empty = F.lo[0] > F.hi[0] || F.lo[1] > F.hi[1] || F.lo[2] > F.hi[2];
+    P.bx = empty ? box_pack(1, 0) : box_pack(F.lo[0], F.hi[0]);
+    P.by = empty ? box_pack(1, 0) : box_pack(F.lo[1], F.hi[1]);
+    P.bz = empty ? box_pack(1, 0) : box_pack(F.lo[2], F.hi[2]);
+    prep[i] = P;
+    // backward work items: z-chunks of at most ~ITEM_VOX voxels
+    const int ex = F.hi[0] - F.lo[0] + 1, ey = F.hi[1] - F.lo[1] + 1, ez = F.hi[2] - F.lo[2] + 1;
+    uint32_t items = 0;
+    if (!empty && ex > 0 && ey > 0 && ez > 0) {
+        const int zc = max(1, ITEM_VOX / (ex * ey));
+        items = (uint32_t)((ez + zc - 1) / zc);
+    }
+    itemcnt[i] = items;
+}
+
+// Tile range of a Gaussian; false if its box misses the grid.
+__device__ __forceinline__ bool tile_range(const Prep &P, int &t0x, int &t0y, int &t0z, int &ntx,
+                                           int &nty, int &ntz) {
+    const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
+              lz = box_lo(P.bz), hz = box_hi(P.bz);
+    if (lx > hx || ly > hy || lz > hz) return false;
+    t0x = lx / TX; t0y = ly / TY; t0z = lz / TZ;
+    ntx = hx / TX - t0x + 1; nty = hy / TY - t0y + 1; ntz = hz / TZ - t0z + 1;
+    return true;
+}
+
+// a2: count Gaussians per tile (one warp per Gaussian, lanes over its tiles).
+__global__ void k_tile_count(int n, const Prep *__restrict__ prep, int NTX, int NTY,
+                             uint32_t *__restrict__ tile_cnt) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const Prep P = prep[i];
+        int t0x, t0y, t0z, ntx, nty, ntz;
+        if (!tile_range(P, t0x, t0y, t0z, ntx, nty, ntz)) continue;
+        const int tot = ntx * nty * ntz;
+        for (int j = lane; j < tot; j += 32) {
+            const int jx = j % ntx, jy = (j / ntx) % nty, jz = j / (ntx * nty);
+            const int t = ((t0z + jz) * NTY + (t0y + jy)) * NTX + (t0x + jx);
+            atomicAdd(&tile_cnt[t], 1u);
+        }
+    }
+}
+
+// a2: write each Gaussian index into the lists of the tiles it overlaps.
+__global__ void k_tile_fill(int n, const Prep *__restrict__ prep, int NTX, int NTY,
+                            const uint32_t *__restrict__ tile_off, uint32_t *__restrict__ tile_fill,
+                            uint32_t *__restrict__ list, unsigned long long cap) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const Prep P = prep[i];
+        int t0x, t0y, t0z, ntx, nty, ntz;
+        if (!tile_range(P, t0x, t0y, t0z, ntx, nty, ntz)) continue;
+        const int tot = ntx * nty * ntz;
+        for (int j = lane; j < tot; j += 32) {
+            const int jx = j % ntx, jy = (j / ntx) % nty, jz = j / (ntx * nty);
+            const int t = ((t0z + jz) * NTY + (t0y + jy)) * NTX + (t0x + jx);
+            const unsigned long long pos =
+                (unsigned long long)tile_off[t] + atomicAdd(&tile_fill[t], 1u);
+            if (pos < cap) list[pos] = (uint32_t)i;
+        }
+    }
+}
+
+// a2: sort each tile's list ascending (bitonic; in shared memory up to
+// SORT_SMEM entries, else in place in global memory).
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_SMEM = 4096;
+
+__device__ void bitonic_smem(uint32_t *a, int m2) {
+    for (int k = 2; k <= m2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t x = a[i], y = a[l];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) { a[i] = y; a[l] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void k_tile_sort(int ntiles, const uint32_t *__restrict__ tile_off,
+                            uint32_t *__restrict__ list, unsigned long long cap) {
+    __shared__ uint32_t sm[SORT_SMEM];
+    const int t = blockIdx.x;
+    unsigned long long b = tile_off[t], e = tile_off[t + 1];
+    if (e > cap) e = cap;
+    if (b >= e) return;
+    const int m = (int)(e - b);
+    if (m < 2) return;
+    int m2 = 1;
+    while (m2 < m) m2 <<= 1;
+    uint32_t *seg = list + b;
+    if (m2 <= SORT_SMEM) {
+        for (int i = threadIdx.x; i < m2; i += blockDim.x) sm[i] = i < m ? seg[i] : 0xffffffffu;
+        __syncthreads();
+        bitonic_smem(sm, m2);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) seg[i] = sm[i];
+        return;
+    }
+    // large list: bitonic network over the padded length with out-of-range
+    // entries treated as +infinity, operating in place in global memory
+    for (int k = 2; k <= m2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t x = i < m ? seg[i] : 0xffffffffu;
+                    const uint32_t y = l < m ? seg[l] : 0xffffffffu;
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        if (i < m) seg[i] = y;
+                        if (l < m) seg[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// a3: one CTA per tile.  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
+// (lx, ly) = (lane & 7, lane >> 3), and z in [tz0, tz0 + 8) in registers.
+__global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
+    dgr_grid g, int NTX, int NTY, const Prep *__restrict__ prep,
+    const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
+    unsigned long long cap, float *__restrict__ vol) {
+    __shared__ float4 sp[VOX_CHUNK * 4];
+    const int t = blockIdx.x;
+    const int tx = t % NTX, ty = (t / NTX) % NTY, tz = t / (NTX * NTY);
+    const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = x0 + (lane & 7);
+    const int wy0 = y0 + 4 * w;
+    const int y = wy0 + (lane >> 3);
+    float acc[TZ];
+#pragma unroll
+    for (int k = 0; k < TZ; ++k) acc[k] = 0.f;
+
+    unsigned long long b = tile_off[t], e = tile_off[t + 1];
+    if (e > cap) e = cap;
+    for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
+        const int nc = (int)min((unsigned long long)VOX_CHUNK, e - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nc * 4; i += VOX_THREADS) {
+            const uint32_t gi = list[c0 + (i >> 2)];
+            sp[i] = reinterpret_cast<const float4 *>(prep + gi)[i & 3];
+        }
+        __syncthreads();
+        for (int j = 0; j < nc; ++j) {
+            const float4 p3 = sp[4 * j + 3];
+            const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z),
+                      bz = __float_as_int(p3.w);
+            const int lx = box_lo(bx), hx = box_hi(bx), ly = box_lo(by), hy = box_hi(by);
+            const int zlo = max(box_lo(bz) - z0, 0), zhi = min(box_hi(bz) - z0, TZ - 1);
+            // warp-uniform skip: the warp's 8 x 4 patch or the z range misses the box
+            if (hx < x0 || lx > x0 + 7 || hy < wy0 || ly > wy0 + 3 || zlo > zhi) continue;
+            const float4 p0 = sp[4 * j], p1 = sp[4 * j + 1], p2 = sp[4 * j + 2];
+            const int ax = __float_as_int(p2.z), ay = __float_as_int(p2.w),
+                      az = __float_as_int(p3.x);
+            const float dx = (float)(x - ax) - p0.x;
+            const float dy = (float)(y - ay) - p0.y;
+            const bool in = x >= lx && x <= hx && y >= ly && y <= hy;
+            // quadratic form in dz: a22 dz^2 + Lz dz + C  (already scaled)
+            float C = fmaf(p1.x * dx, dx, fmaf(p1.y * dy, dy, p1.w * dx * dy));
+            C = in ? C : -INFINITY;
+            const float Lz = fmaf(p2.x, dx, p2.y * dy);
+            const float dz0 = (float)(z0 - az) - p0.z;
+            const float a22 = p1.z, r = p0.w;
+#pragma unroll
+            for (int k = 0; k < TZ; ++k) {
+                if (k >= zlo && k <= zhi) {
+                    const float dz = dz0 + (float)k;
+                    const float qf = fmaf(dz, fmaf(a22, dz, Lz), C);
+                    acc[k] = fmaf(r, ex2_approx(qf), acc[k]);
+                }
+            }
+        }
+    }
+    if (x < g.nx && y < g.ny) {
+        float *col = vol + (size_t)y * g.nx + x;
+        const size_t zs = (size_t)g.nx * g.ny;
+#pragma unroll
+        for (int k = 0; k < TZ; ++k)
+            if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+    }
+}
+
+}  // namespace
+
+int tile_dims(const dgr_grid &g, int &ntx, int &nty, int &ntz) {
+    ntx = (g.nx + TX - 1) / TX;
+    nty = (g.ny + TY - 1) / TY;
+    ntz = (g.nz + TZ - 1) / TZ;
+    return ntx * nty * ntz;
+}
+
+cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const float *s,
+                             const float *q, float k, int *anchor, int *box, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_footprint<<<(n + 127) / 128, 128, 0, st>>>(g, n, mu, s, reinterpret_cast<const float4 *>(q),
+                                                 k, anchor, box);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const dgr_grid &g, int n, const float *mu, const float *s, const float *q,
+                        const float *rho, float k, Prep *prep, uint32_t *itemcnt, int *status,
+                        cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_prep<<<(n + 127) / 128, 128, 0, st>>>(g, n, mu, s, reinterpret_cast<const float4 *>(q), rho,
+                                            k, prep, itemcnt, status);
+    counted(1);
+    return cudaGetLastError();
+}
+
+static int warp_grid(int n) {
+    int blocks = (n + 7) / 8;  // 8 warps per 256-thread block
+    return blocks < 1 ? 1 : (blocks > 148 * 16 ? 148 * 16 : blocks);
+}
+
+cudaError_t launch_count_pairs(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws,
+                               unsigned long long cap, cudaStream_t st) {
+    int NTX, NTY, NTZ;
+    const int ntiles = tile_dims(g, NTX, NTY, NTZ);
+    uint32_t *tile_cnt = ws_ptr<uint32_t>(ws, ws->tile_cnt);
+    uint32_t *tile_off = ws_ptr<uint32_t>(ws, ws->tile_off);
+    int *status = ws_ptr<int>(ws, ws->status);
+    cudaError_t err = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * ntiles, st);
+    if (err != cudaSuccess) return err;
+    if (n > 0) {
+        k_tile_count<<<warp_grid(n), 256, 0, st>>>(n, prep, NTX, NTY, tile_cnt);
+        counted(1);
+    }
+    return scan_u32(tile_cnt, tile_off, ntiles, cap, status, DGR_STATUS_PAIR_OVERFLOW, ws_ptr<unsigned long long>(ws, ws->scan_tmp), st);
+}
+
+cudaError_t launch_voxelize(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws, float *vol,
+                            int deterministic, cudaStream_t st) {
+    int NTX, NTY, NTZ;
+    const int ntiles = tile_dims(g, NTX, NTY, NTZ);
+    uint32_t *tile_off = ws_ptr<uint32_t>(ws, ws->tile_off);
+    uint32_t *tile_fill = ws_ptr<uint32_t>(ws, ws->tile_fill);
+    uint32_t *list = ws_ptr<uint32_t>(ws, ws->list);
+    const unsigned long long cap = (unsigned long long)ws->plan.max_pairs;
+    cudaError_t err = launch_count_pairs(g, n, prep, ws, cap, st);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(tile_fill, 0, sizeof(uint32_t) * ntiles, st);
+    if (err != cudaSuccess) return err;
+    if (n > 0) {
+        k_tile_fill<<<warp_grid(n), 256, 0, st>>>(n, prep, NTX, NTY, tile_off, tile_fill, list, cap);
+        counted(1);
+    }
+    if (deterministic) {
+        k_tile_sort<<<ntiles, SORT_THREADS, 0, st>>>(ntiles, tile_off, list, cap);
+        counted(1);
+    }
+    k_voxelize<<<ntiles, VOX_THREADS, 0, st>>>(g, NTX, NTY, prep, tile_off, list, cap, vol);
+    counted(1);
+    return cudaGetLastError();
+}
+
+}  // namespace dgr

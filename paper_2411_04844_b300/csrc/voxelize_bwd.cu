@@ -1,0 +1,212 @@
+// Adjoint of Fast Volume Reconstruction (a7) on sm_103a.
+//
+// Gaussian-driven gather: the volume gradient G_V is read at each pair, so no
+// per-voxel scatter and no atomics are needed.  Each Gaussian's box is cut into
+// z-chunks of at most ~ITEM_VOX voxels (work items, so one huge Gaussian is
+// spread over many warps).  A warp walks its item: lanes over the (x, y) patch,
+// an inner loop over z with the quadratic form updated in closed form, and
+// accumulates the 10 moments
+//     M0 = sum G e,  M1 = sum G e d,  M2 = sum G e d d^T      (d = v - u)
+// that determine the whole gradient.  Per-item moments are reduced across the
+// warp with shuffles and summed per Gaussian in item order (deterministic).
+// The per-Gaussian epilogue chains
+//     dL/drho = M0,  dL/du = rho A M1,  dL/dA = -1/2 rho M2
+// through u = (mu - o)/h - 1/2 and A = h^2 R(q/|q|) diag(s^-2) R^T.
+#include <math.h>
+
+#include "dgr_internal.cuh"
+
+namespace dgr {
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__global__ void __launch_bounds__(256) k_bwd_items(
+    dgr_grid g, int n, const Prep *__restrict__ prep, const uint32_t *__restrict__ item_off,
+    unsigned long long cap, const float *__restrict__ gv, float *__restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long total = item_off[n];
+    if (total > cap) total = cap;
+    for (long long it = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+         it < (long long)total; it += warps) {
+        // Gaussian owning item `it`: last gi with item_off[gi] <= it
+        int lo = 0, hi = n;  // item_off[lo] <= it < item_off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if ((unsigned long long)item_off[mid] <= (unsigned long long)it) lo = mid; else hi = mid;
+        }
+        const int gi = lo;
+        const int c = (int)(it - item_off[gi]);
+        const Prep P = prep[gi];
+        const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
+                  lz = box_lo(P.bz), hz = box_hi(P.bz);
+        const int ex = hx - lx + 1, ey = hy - ly + 1;
+        const int zc = max(1, ITEM_VOX / (ex * ey));
+        const int zb = lz + c * zc, ze = min(zb + zc - 1, hz);
+        float m[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) m[k] = 0.f;
+        const int exy = ex * ey;
+        const float dz0 = (float)(zb - P.az) - P.dz;
+        for (int j = lane; j < exy; j += 32) {
+            const int yy = ly + j / ex, xx = lx + j % ex;
+            const float dx = (float)(xx - P.ax) - P.dx;
+            const float dy = (float)(yy - P.ay) - P.dy;
+            const float C = fmaf(P.a00 * dx, dx, fmaf(P.a11 * dy, dy, P.a01 * dx * dy));
+            const float Lz = fmaf(P.a02, dx, P.a12 * dy);
+            const float *col = gv + ((size_t)zb * g.ny + yy) * g.nx + xx;
+            const size_t zs = (size_t)g.nx * g.ny;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int z = zb; z <= ze; ++z) {
+                const float dz = dz0 + (float)(z - zb);
+                const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
+                const float ge = __ldg(col) * e;
+                col += zs;
+                s0 += ge;
+                const float t = ge * dz;
+                s1 += t;
+                s2 = fmaf(t, dz, s2);
+            }
+            m[0] += s0;
+            m[1] = fmaf(dx, s0, m[1]);
+            m[2] = fmaf(dy, s0, m[2]);
+            m[3] += s1;
+            m[4] = fmaf(dx * dx, s0, m[4]);  // xx
+            m[5] = fmaf(dy * dy, s0, m[5]);  // yy
+            m[6] += s2;                      // zz
+            m[7] = fmaf(dx * dy, s0, m[7]);  // xy
+            m[8] = fmaf(dx, s1, m[8]);       // xz
+            m[9] = fmaf(dy, s1, m[9]);       // yz
+        }
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+        }
+        if (lane == 0) {
+            float *dst = part + (size_t)it * NMOM;
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) dst[k] = m[k];
+        }
+    }
+}
+
+__global__ void k_bwd_final(dgr_grid g, int n, const float *__restrict__ mu,
+                            const float *__restrict__ s, const float4 *__restrict__ q,
+                            const float *__restrict__ rho, const uint32_t *__restrict__ item_off,
+                            unsigned long long cap, const float *__restrict__ part,
+                            float *__restrict__ g_mu, float *__restrict__ g_s,
+                            float *__restrict__ g_q, float *__restrict__ g_rho) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long b = item_off[i], e = item_off[i + 1];
+    if (e > cap) e = cap;
+    float M[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) M[k] = 0.f;
+    for (unsigned long long it = b; it < e; ++it) {
+        const float *src = part + it * NMOM;
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) M[k] += src[k];
+    }
+    if (b >= e) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { g_mu[3 * i + a] = 0.f; g_s[3 * i + a] = 0.f; }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) g_q[4 * i + a] = 0.f;
+        g_rho[i] = 0.f;
+        return;
+    }
+    // rotation of the normalised quaternion
+    const float4 qq = q[i];
+    const float qnorm = sqrtf(qq.x * qq.x + qq.y * qq.y + qq.z * qq.z + qq.w * qq.w);
+    const float iq = 1.0f / qnorm;
+    const float w = qq.x * iq, x = qq.y * iq, y = qq.z * iq, z = qq.w * iq;
+    float R[9];
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+    const float h = g.h, h2 = h * h;
+    const float sx = s[3 * i], sy = s[3 * i + 1], sz = s[3 * i + 2];
+    const float D[3] = {1.f / (sx * sx), 1.f / (sy * sy), 1.f / (sz * sz)};
+    // A = h^2 R D R^T
+    float A[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2)
+            A[3 * a + b2] = h2 * (R[3 * a] * R[3 * b2] * D[0] + R[3 * a + 1] * R[3 * b2 + 1] * D[1] +
+                                  R[3 * a + 2] * R[3 * b2 + 2] * D[2]);
+    const float r = rho[i];
+    g_rho[i] = M[0];
+    const float M1[3] = {M[1], M[2], M[3]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        g_mu[3 * i + a] = r * (A[3 * a] * M1[0] + A[3 * a + 1] * M1[1] + A[3 * a + 2] * M1[2]) / h;
+    // dL/dA = -1/2 rho M2 (symmetric)
+    const float c = -0.5f * r;
+    const float GA[9] = {c * M[4], c * M[7], c * M[8],
+                         c * M[7], c * M[5], c * M[9],
+                         c * M[8], c * M[9], c * M[6]};
+    // GR = GA R  (3x3)
+    float GR[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            GR[3 * a + k] = GA[3 * a] * R[k] + GA[3 * a + 1] * R[3 + k] + GA[3 * a + 2] * R[6 + k];
+    // dL/ds_k = h^2 (R^T GA R)_kk (-2 / s_k^3)
+    const float sv[3] = {sx, sy, sz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float rgr = R[k] * GR[k] + R[3 + k] * GR[3 + k] + R[6 + k] * GR[6 + k];
+        g_s[3 * i + k] = h2 * rgr * (-2.f / (sv[k] * sv[k] * sv[k]));
+    }
+    // dL/dR = 2 h^2 GA R D
+    float gR[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gR[3 * a + k] = 2.f * h2 * GR[3 * a + k] * D[k];
+    const float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    const float gx = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] +
+                            z * gR[6] + w * gR[7] - 2.f * x * gR[8]);
+    const float gy = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] -
+                            w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
+    const float gz = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] +
+                            y * gR[5] + x * gR[6] + y * gR[7]);
+    const float dot = w * gw + x * gx + y * gy + z * gz;
+    g_q[4 * i + 0] = (gw - w * dot) * iq;
+    g_q[4 * i + 1] = (gx - x * dot) * iq;
+    g_q[4 * i + 2] = (gy - y * dot) * iq;
+    g_q[4 * i + 3] = (gz - z * dot) * iq;
+}
+
+}  // namespace
+
+cudaError_t launch_voxelize_backward(const dgr_grid &g, int n, const float *mu, const float *s,
+                                     const float *q, const float *rho, const Prep *prep,
+                                     const float *grad_vol, float *g_mu, float *g_s, float *g_q,
+                                     float *g_rho, dgr_ws *ws, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint32_t *itemcnt = ws_ptr<uint32_t>(ws, ws->itemcnt);
+    uint32_t *item_off = ws_ptr<uint32_t>(ws, ws->item_off);
+    float *part = ws_ptr<float>(ws, ws->partials);
+    int *status = ws_ptr<int>(ws, ws->status);
+    const unsigned long long cap = (unsigned long long)ws->plan.max_items;
+    cudaError_t err = scan_u32(itemcnt, item_off, n, cap, status, DGR_STATUS_ITEM_OVERFLOW,
+                               ws_ptr<unsigned long long>(ws, ws->scan_tmp), st);
+    if (err != cudaSuccess) return err;
+    k_bwd_items<<<148 * 8, 256, 0, st>>>(g, n, prep, item_off, cap, grad_vol, part);
+    k_bwd_final<<<(n + 127) / 128, 128, 0, st>>>(g, n, mu, s, reinterpret_cast<const float4 *>(q),
+                                                 rho, item_off, cap, part, g_mu, g_s, g_q, g_rho);
+    counted(2);
+    return cudaGetLastError();
+}
+
+}  // namespace dgr

@@ -1,0 +1,354 @@
+"""Thin Python binding of libdgr (include/dgr.h): argument marshalling only.
+
+Every function named ``dgr_*`` maps one-to-one onto the C entry point of the
+same name; tensors are passed as device pointers, the stream is torch's
+current stream unless given.  No computation happens here and there is no
+fallback: if the library is missing or fails to load, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+DGR_OK = 0
+DGR_ERR_ARG = 1
+DGR_ERR_WS_TOO_SMALL = 2
+DGR_ERR_CUDA = 3
+DGR_STATUS_NONFINITE = 0x10
+DGR_STATUS_PAIR_OVERFLOW = 0x20
+DGR_STATUS_ITEM_OVERFLOW = 0x40
+DGR_PARALLEL = 0
+DGR_CONE = 1
+
+# voxel tile of the forward voxelizer (x, y, z)
+TILE = (8, 16, 8)
+
+EXPORTS = [
+    "dgr_ws_bytes", "dgr_ws_create", "dgr_ws_destroy", "dgr_tile_count", "dgr_status",
+    "dgr_strerror", "dgr_set_deterministic", "dgr_footprint", "dgr_voxelize_count",
+    "dgr_voxelize", "dgr_voxelize_backward", "dgr_project", "dgr_backproject",
+    "dgr_l1_residual", "dgr_params_init", "dgr_step", "dgr_step_timed", "dgr_launch_count",
+]
+DGR_STEP_EVENTS = 7
+STEP_PHASES = ("voxelize", "project", "l1", "backproject", "voxelize_backward", "adam")
+
+
+class DgrError(RuntimeError):
+    pass
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_float), ("ox", ctypes.c_float), ("oy", ctypes.c_float),
+                ("oz", ctypes.c_float)]
+
+    @staticmethod
+    def of(spec) -> "Grid":
+        """From any object with dims (nx, ny, nz), h and org."""
+        nx, ny, nz = spec.dims
+        return Grid(nx, ny, nz, spec.h, *spec.org)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int), ("n_views", ctypes.c_int), ("nu", ctypes.c_int),
+                ("nv", ctypes.c_int), ("pu", ctypes.c_float), ("pv", ctypes.c_float),
+                ("dso", ctypes.c_float), ("dsd", ctypes.c_float), ("angles", ctypes.c_void_p)]
+
+    @staticmethod
+    def of(spec, angles_dev: torch.Tensor) -> "Geom":
+        """From a geometry description and its angles already on the device
+        (the tensor must outlive every call made with this descriptor)."""
+        _check(angles_dev, "angles")
+        return Geom(spec.beam, spec.n_views, spec.nu, spec.nv, spec.pu, spec.pv, spec.dso,
+                    spec.dsd, angles_dev.data_ptr())
+
+    @property
+    def shape(self):
+        return (self.n_views, self.nv, self.nu)
+
+
+class WsPlan(ctypes.Structure):
+    _fields_ = [("max_n", ctypes.c_int), ("max_tiles", ctypes.c_int),
+                ("max_pairs", ctypes.c_longlong), ("max_items", ctypes.c_longlong),
+                ("max_vox", ctypes.c_longlong), ("max_rays", ctypes.c_longlong),
+                ("max_views", ctypes.c_int), ("max_nu", ctypes.c_int), ("max_nv", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("geom", Geom), ("k_trunc", ctypes.c_float),
+                ("lr0", ctypes.c_float), ("lr1", ctypes.c_float), ("n_iters", ctypes.c_int),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("mu", ctypes.c_void_p), ("s", ctypes.c_void_p),
+                ("q", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+                ("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("step", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdgr.so (building it if its sources are newer).  Raises if the
+    library cannot be built or loaded -- there is no CPU fallback."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise DgrError(f"libdgr not found at {path}")
+        L = ctypes.CDLL(path)
+        P, i, f, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong
+        sig = {
+            "dgr_ws_bytes": [ctypes.POINTER(WsPlan), ctypes.POINTER(ctypes.c_size_t)],
+            "dgr_ws_create": [ctypes.POINTER(P), ctypes.POINTER(WsPlan)],
+            "dgr_ws_destroy": [P],
+            "dgr_tile_count": [ctypes.POINTER(Grid), ctypes.POINTER(i)],
+            "dgr_status": [P, P, ctypes.POINTER(i)],
+            "dgr_set_deterministic": [i],
+            "dgr_footprint": [ctypes.POINTER(Grid), i, P, P, P, f, P, P, P],
+            "dgr_voxelize_count": [ctypes.POINTER(Grid), i, P, P, P, f, ctypes.POINTER(ll),
+                                   ctypes.POINTER(ll), P, P],
+            "dgr_voxelize": [ctypes.POINTER(Grid), i, P, P, P, P, f, P, P, P],
+            "dgr_voxelize_backward": [ctypes.POINTER(Grid), i, P, P, P, P, f, P, P, P, P, P, P, P],
+            "dgr_project": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P, P],
+            "dgr_backproject": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P, P],
+            "dgr_l1_residual": [P, P, ll, P, P, P, P],
+            "dgr_params_init": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P],
+            "dgr_step": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P],
+            "dgr_step_timed": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P,
+                               ctypes.POINTER(P), i],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.dgr_launch_count.argtypes = []
+        L.dgr_launch_count.restype = ctypes.c_longlong
+        L.dgr_strerror.argtypes = [i]
+        L.dgr_strerror.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def _rc(code: int, what: str):
+    if code != DGR_OK:
+        msg = lib().dgr_strerror(code).decode()
+        raise DgrError(f"{what}: {msg} ({code})")
+
+
+def _check(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a tensor")
+    if not t.is_cuda:
+        raise DgrError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise DgrError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise DgrError(f"{name} must be contiguous")
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+# ---------------------------------------------------------------------------
+# workspace
+# ---------------------------------------------------------------------------
+class Workspace:
+    """Owns one dgr_ws (a single cudaMalloc made by dgr_ws_create)."""
+
+    def __init__(self, plan: WsPlan):
+        self.plan = plan
+        h = ctypes.c_void_p()
+        _rc(lib().dgr_ws_create(ctypes.byref(h), ctypes.byref(plan)), "dgr_ws_create")
+        self.handle = h
+
+    @property
+    def ptr(self):
+        return self.handle
+
+    def close(self):
+        if self.handle:
+            lib().dgr_ws_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dgr_ws_bytes(plan: WsPlan) -> int:
+    b = ctypes.c_size_t()
+    _rc(lib().dgr_ws_bytes(ctypes.byref(plan), ctypes.byref(b)), "dgr_ws_bytes")
+    return int(b.value)
+
+
+def dgr_tile_count(grid: Grid) -> int:
+    t = ctypes.c_int()
+    _rc(lib().dgr_tile_count(ctypes.byref(grid), ctypes.byref(t)), "dgr_tile_count")
+    return int(t.value)
+
+
+def make_plan(grid: Grid = None, n: int = 0, max_pairs: int = 0, max_items: int = 0,
+              geom=None, step: bool = False) -> WsPlan:
+    p = WsPlan()
+    p.max_n = int(n)
+    p.max_tiles = dgr_tile_count(grid) if grid is not None else 0
+    p.max_pairs = int(max_pairs)
+    p.max_items = int(max_items)
+    if geom is not None:
+        p.max_views, p.max_nu, p.max_nv = int(geom.n_views), int(geom.nu), int(geom.nv)
+    if step:
+        p.max_vox = grid.nx * grid.ny * grid.nz
+        p.max_rays = geom.n_views * geom.nu * geom.nv
+    return p
+
+
+def dgr_status(ws: Workspace, stream=None) -> int:
+    v = ctypes.c_int()
+    _rc(lib().dgr_status(ws.ptr, _stream(stream), ctypes.byref(v)), "dgr_status")
+    return int(v.value)
+
+
+def dgr_set_deterministic(on: bool):
+    _rc(lib().dgr_set_deterministic(1 if on else 0), "dgr_set_deterministic")
+
+
+# ---------------------------------------------------------------------------
+# voxelizer
+# ---------------------------------------------------------------------------
+def dgr_footprint(grid: Grid, mu, s, q, k_trunc, anchor, box, stream=None):
+    for t, nm in ((mu, "mu"), (s, "s"), (q, "q")):
+        _check(t, nm)
+    _check(anchor, "anchor", torch.int32)
+    _check(box, "box", torch.int32)
+    n = mu.shape[0]
+    _rc(lib().dgr_footprint(ctypes.byref(grid), n, _ptr(mu), _ptr(s), _ptr(q), float(k_trunc),
+                            _ptr(anchor), _ptr(box), _stream(stream)), "dgr_footprint")
+
+
+def dgr_voxelize_count(grid: Grid, mu, s, q, k_trunc, ws: Workspace, stream=None):
+    for t, nm in ((mu, "mu"), (s, "s"), (q, "q")):
+        _check(t, nm)
+    pairs, items = ctypes.c_longlong(), ctypes.c_longlong()
+    _rc(lib().dgr_voxelize_count(ctypes.byref(grid), mu.shape[0], _ptr(mu), _ptr(s), _ptr(q),
+                                 float(k_trunc), ctypes.byref(pairs), ctypes.byref(items),
+                                 ws.ptr, _stream(stream)), "dgr_voxelize_count")
+    return int(pairs.value), int(items.value)
+
+
+def dgr_voxelize(grid: Grid, mu, s, q, rho, k_trunc, vol, ws: Workspace, stream=None):
+    for t, nm in ((mu, "mu"), (s, "s"), (q, "q"), (rho, "rho"), (vol, "vol")):
+        _check(t, nm)
+    _rc(lib().dgr_voxelize(ctypes.byref(grid), mu.shape[0], _ptr(mu), _ptr(s), _ptr(q),
+                           _ptr(rho), float(k_trunc), _ptr(vol), ws.ptr, _stream(stream)),
+        "dgr_voxelize")
+
+
+def dgr_voxelize_backward(grid: Grid, mu, s, q, rho, k_trunc, grad_vol, g_mu, g_s, g_q, g_rho,
+                          ws: Workspace, stream=None):
+    for t, nm in ((mu, "mu"), (s, "s"), (q, "q"), (rho, "rho"), (grad_vol, "grad_vol"),
+                  (g_mu, "g_mu"), (g_s, "g_s"), (g_q, "g_q"), (g_rho, "g_rho")):
+        _check(t, nm)
+    _rc(lib().dgr_voxelize_backward(ctypes.byref(grid), mu.shape[0], _ptr(mu), _ptr(s), _ptr(q),
+                                    _ptr(rho), float(k_trunc), _ptr(grad_vol), _ptr(g_mu),
+                                    _ptr(g_s), _ptr(g_q), _ptr(g_rho), ws.ptr, _stream(stream)),
+        "dgr_voxelize_backward")
+
+
+# ---------------------------------------------------------------------------
+# projector
+# ---------------------------------------------------------------------------
+def dgr_project(grid: Grid, geom: Geom, vol, sino, ws: Workspace, stream=None):
+    _check(vol, "vol"); _check(sino, "sino")
+    _rc(lib().dgr_project(ctypes.byref(grid), ctypes.byref(geom), _ptr(vol), _ptr(sino), ws.ptr,
+                          _stream(stream)), "dgr_project")
+
+
+def dgr_backproject(grid: Grid, geom: Geom, sino, vol, ws: Workspace, stream=None):
+    _check(vol, "vol"); _check(sino, "sino")
+    _rc(lib().dgr_backproject(ctypes.byref(grid), ctypes.byref(geom), _ptr(sino), _ptr(vol),
+                              ws.ptr, _stream(stream)), "dgr_backproject")
+
+
+def dgr_l1_residual(pred, meas, resid, loss, ws: Workspace, stream=None):
+    for t, nm in ((pred, "pred"), (meas, "meas"), (resid, "resid"), (loss, "loss")):
+        _check(t, nm)
+    _rc(lib().dgr_l1_residual(_ptr(pred), _ptr(meas), pred.numel(), _ptr(resid), _ptr(loss),
+                              ws.ptr, _stream(stream)), "dgr_l1_residual")
+
+
+# ---------------------------------------------------------------------------
+# optimisation step
+# ---------------------------------------------------------------------------
+def make_problem(grid: Grid, geom: Geom, k_trunc=3.0, lr0=3e-4, lr1=3e-5, n_iters=2000,
+                 beta1=0.9, beta2=0.999, eps=1e-8) -> Problem:
+    return Problem(grid, geom, k_trunc, lr0, lr1, n_iters, beta1, beta2, eps)
+
+
+class State:
+    """Device tensors of the optimiser state (dgr_params)."""
+
+    def __init__(self, mu, s, q, rho):
+        n = mu.shape[0]
+        dev = mu.device
+        self.n = n
+        self.mu, self.s, self.q, self.rho = (t.contiguous().clone() for t in (mu, s, q, rho))
+        self.theta = torch.zeros(11 * n, device=dev)
+        self.m = torch.zeros(11 * n, device=dev)
+        self.v = torch.zeros(11 * n, device=dev)
+        self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def params(self) -> Params:
+        return Params(self.n, _ptr(self.mu), _ptr(self.s), _ptr(self.q), _ptr(self.rho),
+                      _ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.step))
+
+
+def dgr_params_init(prob: Problem, st: State, stream=None):
+    p = st.params()
+    _rc(lib().dgr_params_init(ctypes.byref(prob), ctypes.byref(p), _stream(stream)),
+        "dgr_params_init")
+
+
+def dgr_step(prob: Problem, st: State, measured, loss_out, ws: Workspace, stream=None):
+    _check(measured, "measured"); _check(loss_out, "loss_out")
+    p = st.params()
+    _rc(lib().dgr_step(ctypes.byref(prob), ctypes.byref(p), _ptr(measured), _ptr(loss_out),
+                       ws.ptr, _stream(stream)), "dgr_step")
+
+
+def dgr_step_timed(prob: Problem, st: State, measured, loss_out, ws: Workspace, events,
+                   stream=None):
+    """dgr_step recording torch.cuda.Events (already created, i.e. recorded
+    once) at the 7 phase boundaries."""
+    _check(measured, "measured"); _check(loss_out, "loss_out")
+    if len(events) < DGR_STEP_EVENTS:
+        raise DgrError("dgr_step_timed needs 7 events")
+    arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+    p = st.params()
+    _rc(lib().dgr_step_timed(ctypes.byref(prob), ctypes.byref(p), _ptr(measured), _ptr(loss_out),
+                             ws.ptr, _stream(stream), arr, len(events)), "dgr_step_timed")
+
+
+def dgr_launch_count() -> int:
+    return int(lib().dgr_launch_count())

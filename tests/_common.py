@@ -1,0 +1,53 @@
+"""Shared test helpers: matching oracle / device descriptions of one problem."""
+import math
+
+import numpy as np
+
+import oracle as O
+from paper_2411_04844_b300 import synth
+
+
+def oracle_grid(spec: synth.GridSpec) -> O.Grid:
+    return O.Grid(spec.dims, spec.h, spec.org)
+
+
+def oracle_geom(spec: synth.GeomSpec) -> O.Geom:
+    return O.Geom(spec.beam, spec.angles, spec.nu, spec.nv, spec.pu, spec.pv, spec.dso, spec.dsd)
+
+
+def guard_field(field: synth.Field, grid: synth.GridSpec, k=3.0, band=1e-3, rng=None):
+    """Resample Gaussians whose voxel-unit centre u_a or k sigma_a lies within
+    `band` of an integer (FP64 check), so no footprint decision sits on an
+    FP32 rounding edge.  Returns a new field with the same size."""
+    rng = rng or np.random.default_rng(12345)
+    f = synth.Field(field.mu.copy(), field.s.copy(), field.q.copy(), field.rho.copy())
+    for _ in range(100):
+        bad = _near_integer(f, grid, k, band)
+        if not bad.any():
+            return f
+        idx = np.nonzero(bad)[0]
+        lo = np.array(grid.org); hi = lo + np.array(grid.extent)
+        f.mu[idx] = rng.uniform(lo, hi, (len(idx), 3)).astype(np.float32)
+        f.s[idx] = (f.s[idx] * rng.uniform(0.97, 1.03, (len(idx), 3))).astype(np.float32)
+    raise RuntimeError("guard band not reached")
+
+
+def _near_integer(f, grid, k, band):
+    q = f.q.astype(np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+    var = np.einsum("nak,nk->na", R ** 2, f.s.astype(np.float64) ** 2)
+    ks = k * np.sqrt(var) / grid.h
+    u = (f.mu.astype(np.float64) - np.array(grid.org)) / grid.h - 0.5
+    near = lambda a: np.abs(a - np.round(a)) < band
+    return (near(u) | near(ks)).any(1)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))

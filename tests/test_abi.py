@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point declared in include/dgr.h.  No compute calls (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dgr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(dgr_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("dgr_voxelize", "dgr_voxelize_backward", "dgr_project", "dgr_backproject",
+              "dgr_step", "dgr_ws_create", "dgr_ws_destroy", "dgr_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2411_04844_b300 import dgr
+    L = dgr.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(dgr.EXPORTS) <= set(declared_functions())
+
+
+def test_host_side_validation_without_gpu():
+    """Argument checks run on the host and never touch the device."""
+    from paper_2411_04844_b300 import dgr
+    L = dgr.lib()
+    g = dgr.Grid(0, 4, 4, 1.0, 0.0, 0.0, 0.0)
+    t = ctypes.c_int()
+    assert L.dgr_tile_count(ctypes.byref(g), ctypes.byref(t)) == dgr.DGR_ERR_ARG
+    g = dgr.Grid(64, 64, 64, 1.0, -32.0, -32.0, -32.0)
+    assert L.dgr_tile_count(ctypes.byref(g), ctypes.byref(t)) == dgr.DGR_OK
+    assert t.value == 8 * 4 * 8
+    plan = dgr.WsPlan()
+    plan.max_n = 10; plan.max_tiles = 4; plan.max_pairs = 100
+    b = ctypes.c_size_t()
+    assert L.dgr_ws_bytes(ctypes.byref(plan), ctypes.byref(b)) == dgr.DGR_OK and b.value > 0
+    plan.max_pairs = -1
+    assert L.dgr_ws_bytes(ctypes.byref(plan), ctypes.byref(b)) == dgr.DGR_ERR_ARG
+    # k_trunc must be > 0 or a negative odd integer; a null workspace is refused
+    assert L.dgr_voxelize(ctypes.byref(g), 0, None, None, None, None, ctypes.c_float(-4.0),
+                          ctypes.c_void_p(1), None, None) == dgr.DGR_ERR_ARG
+    assert L.dgr_voxelize(ctypes.byref(g), 0, None, None, None, None, ctypes.c_float(3.0),
+                          ctypes.c_void_p(1), None, None) == dgr.DGR_ERR_ARG
+    assert L.dgr_strerror(dgr.DGR_ERR_WS_TOO_SMALL).decode().startswith("workspace")
+
+
+def test_library_is_sm103a_only():
+    from paper_2411_04844_b300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
