@@ -46,6 +46,8 @@ def lib():
         L.oracle_footprint.restype = None
         L.oracle_voxelize_core.argtypes = [P, d, P, i, P, P, P, P, P, i, P]
         L.oracle_voxelize_core.restype = None
+        L.oracle_voxelize_points.argtypes = [P, d, P, i, P, P, P, P, P, i, P, P]
+        L.oracle_voxelize_points.restype = None
         L.oracle_voxelize_backward_core.argtypes = [P, d, P, i, P, P, P, P, P, P, P, P, P, P]
         L.oracle_voxelize_backward_core.restype = None
         proj = [P, d, P, i, i, i, i, d, d, d, d, P, P, P]
@@ -151,6 +153,21 @@ def voxelize(grid: Grid, mu, s, q, rho, k_trunc: float = 3.0, brute: bool = Fals
                          np.asarray(s, np.float32).astype(np.float64),
                          np.asarray(q, np.float32).astype(np.float64),
                          np.asarray(rho, np.float32).astype(np.float64), box, brute)
+
+
+def voxelize_points(grid: Grid, mu, s, q, rho, pts, k_trunc: float = 3.0):
+    """V at voxels pts [m, 3] = (x, y, z) (brute force over all Gaussians)."""
+    _, box = footprint(grid, mu, s, q, k_trunc)
+    f = lambda a, c: np.ascontiguousarray(np.asarray(a, np.float32).astype(np.float64).reshape(-1, c))
+    mu64, s64, q64 = f(mu, 3), f(s, 3), f(q, 4)
+    rho64 = np.ascontiguousarray(np.asarray(rho, np.float32).astype(np.float64))
+    pts = _c(pts, np.int32).reshape(-1, 3)
+    out = np.zeros(pts.shape[0])
+    dims = np.array(grid.dims, np.int32)
+    org = np.array(grid.org, np.float64)
+    lib().oracle_voxelize_points(_p(dims), grid.h, _p(org), mu64.shape[0], _p(mu64), _p(s64),
+                                 _p(q64), _p(rho64), _p(box), pts.shape[0], _p(pts), _p(out))
+    return out
 
 
 def voxelize_backward_core(grid: Grid, mu, s, q, rho, box, grad_vol):

@@ -235,6 +235,35 @@ void oracle_voxelize_core(const int dims[3], double h, const double org[3], int 
     free(G);
 }
 
+/* V at a list of voxels pts[npts][3] = (x, y, z): the brute-force definition
+ * (every Gaussian's box tested) restricted to those voxels, for spot checks of
+ * volumes too large to evaluate whole. */
+void oracle_voxelize_points(const int dims[3], double h, const double org[3], int n,
+                            const double *mu, const double *s, const double *q,
+                            const double *rho, const int *box, int npts, const int *pts,
+                            double *out)
+{
+    (void)dims;
+    gauss64 *G = (gauss64 *)malloc(sizeof(gauss64) * (size_t)(n > 0 ? n : 1));
+    for (int g = 0; g < n; ++g)
+        make_gauss(h, org, mu + 3 * g, s + 3 * g, q + 4 * g, rho[g], box + 6 * g, &G[g]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < npts; ++p) {
+        const int x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+        double acc = 0;
+        for (int g = 0; g < n; ++g) {
+            const gauss64 *P = &G[g];
+            if (x < P->lo[0] || x > P->hi[0] || y < P->lo[1] || y > P->hi[1] || z < P->lo[2] ||
+                z > P->hi[2])
+                continue;
+            double d[3] = {x - P->u[0], y - P->u[1], z - P->u[2]};
+            acc += P->rho * exp(-0.5 * quad_form(P->A, d));
+        }
+        out[p] = acc;
+    }
+    free(G);
+}
+
 /* Analytic gradient of L = <grad_vol, V> with the integers (box, anchor) held
  * fixed.  Per Gaussian, with e = exp(-1/2 d^T A d), d = v - u:
  *   dL/drho = sum G e

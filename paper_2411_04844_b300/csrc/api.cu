@@ -76,7 +76,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA; }
 
 struct Layout {
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy, total;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, total;
     size_t scan_elems;
 };
 
@@ -107,8 +107,9 @@ Layout layout_of(const dgr_ws_plan &p) {
     L.scan_tmp = take(8 * L.scan_elems);
     L.list = take(4 * (size_t)p.max_pairs);
     L.partials = take(4 * (size_t)NMOM * (size_t)p.max_items);
-    L.rayxy = take(sizeof(RayXY) * (size_t)p.max_views * p.max_nu + 8 * (size_t)p.max_views +
-                   4 * (size_t)p.max_nv);
+    L.rayxy = take(ray_table_bytes(p.max_views, p.max_nu, p.max_nv));
+    // residual x |D| for the backprojector (standalone calls; the step reuses its sinogram)
+    L.sino_scaled = take(4 * (size_t)p.max_views * p.max_nu * p.max_nv);
     L.loss_part = take(4 * (size_t)(L1_BLOCKS + 1));
     L.grads = take(4 * 11 * (size_t)p.max_n);
     L.vol = take(4 * (size_t)p.max_vox);
@@ -144,6 +145,7 @@ int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan) {
     w->tile_cnt = L.tile_cnt; w->tile_off = L.tile_off; w->tile_fill = L.tile_fill;
     w->scan_tmp = L.scan_tmp; w->list = L.list; w->partials = L.partials; w->grads = L.grads;
     w->vol = L.vol; w->sino = L.sino; w->loss_part = L.loss_part; w->rayxy = L.rayxy;
+    w->sino_scaled = L.sino_scaled;
     w->scan_tmp_elems = L.scan_elems;
     if (cudaMemset(w->base + L.status, 0, 256) != cudaSuccess) {
         cudaFree(w->base);
@@ -288,7 +290,8 @@ int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sin
     if (rc) return rc;
     RayXY *tab = ws_ptr<RayXY>(ws, ws->rayxy);
     cudaError_t e = launch_ray_tables(*grid, *geom, tab, stream);
-    if (e == cudaSuccess) e = launch_backproject(*grid, *geom, tab, sino, vol, stream);
+    if (e == cudaSuccess)
+        e = launch_backproject(*grid, *geom, tab, sino, ws_ptr<float>(ws, ws->sino_scaled), vol, stream);
     return cuda_rc(e);
 }
 
@@ -349,7 +352,8 @@ static int step_impl(const dgr_problem *prob, const dgr_params *p, const float *
     if (e == cudaSuccess)
         e = launch_l1(sino, measured, nrays, sino, loss_out, ws_ptr<float>(ws, ws->loss_part), stream);
     if (e == cudaSuccess) e = mark(3);
-    if (e == cudaSuccess) e = launch_backproject(g, geo, tab, sino, vol, stream);
+    if (e == cudaSuccess)
+        e = launch_backproject(g, geo, tab, sino, ws_ptr<float>(ws, ws->sino_scaled), vol, stream);
     if (e == cudaSuccess) e = mark(4);
     if (e == cudaSuccess)
         e = launch_voxelize_backward(g, n, p->mu, p->s, p->q, p->rho, prep, vol, grads,

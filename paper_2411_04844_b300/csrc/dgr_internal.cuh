@@ -16,10 +16,42 @@ constexpr int TX = 8, TY = 16, TZ = 8;
 constexpr int VOX_THREADS = 128;
 constexpr int VOX_CHUNK = 64;  // prep records staged in shared memory at a time
 
-// Backward work item: a z-chunk of one Gaussian's box holding at most about
-// ITEM_VOX voxels, processed by one warp.
+// Backward work item: a piece of one Gaussian's box holding at most about
+// ITEM_VOX voxels (see item_count), processed by one warp.
 constexpr int ITEM_VOX = 2048;
 constexpr int NMOM = 10;  // moments per item: S0, S1[3], S2[6]
+
+// Work items of the backward pass cover a box of ex * ey * ez voxels:
+//   ex * ey <= ITEM_VOX: z-slabs of zc = ITEM_VOX / (ex * ey) layers;
+//   otherwise: per z layer, y-slabs of yc = max(1, ITEM_VOX / ex) rows.
+__host__ __device__ inline uint32_t item_count(int ex, int ey, int ez) {
+    if (ex <= 0 || ey <= 0 || ez <= 0) return 0u;
+    const long long exy = (long long)ex * ey;
+    if (exy <= ITEM_VOX) {
+        const int zc = (int)(ITEM_VOX / exy);
+        return (uint32_t)((ez + zc - 1) / zc);
+    }
+    const int yc = ex < ITEM_VOX ? ITEM_VOX / ex : 1;
+    return (uint32_t)ez * (uint32_t)((ey + yc - 1) / yc);
+}
+// item c of a box with lower corner (ly, lz) and upper (hy, hz): y and z ranges
+__host__ __device__ inline void item_range(int c, int ex, int ey, int ly, int hy, int lz, int hz,
+                                           int &yb, int &ye, int &zb, int &ze) {
+    const long long exy = (long long)ex * ey;
+    if (exy <= ITEM_VOX) {
+        const int zc = (int)(ITEM_VOX / exy);
+        zb = lz + c * zc;
+        ze = min(zb + zc - 1, hz);
+        yb = ly;
+        ye = hy;
+    } else {
+        const int yc = ex < ITEM_VOX ? ITEM_VOX / ex : 1;
+        const int nyc = (ey + yc - 1) / yc;
+        zb = ze = lz + c / nyc;
+        yb = ly + (c % nyc) * yc;
+        ye = min(yb + yc - 1, hy);
+    }
+}
 
 // log2(e): the exponent exp(-x/2) is evaluated as ex2(-x/2 * log2(e)).
 constexpr float LOG2E = 1.4426950408889634f;
@@ -64,7 +96,7 @@ struct dgr_ws {
     dgr_ws_plan plan;
     // byte offsets into base
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled;
     size_t scan_tmp_elems;
 };
 
@@ -102,8 +134,10 @@ cudaError_t launch_voxelize_backward(const dgr_grid &g, int n, const float *mu, 
 cudaError_t launch_ray_tables(const dgr_grid &g, const dgr_geom &geo, RayXY *tab, cudaStream_t st);
 cudaError_t launch_project(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
                            const float *vol, float *sino, cudaStream_t st);
+// sino_scaled: scratch of n_rays floats (residual x |D|, [view][u][v]); must not alias sino
 cudaError_t launch_backproject(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
-                               const float *sino, float *vol, cudaStream_t st);
+                               const float *sino, float *sino_scaled, float *vol, cudaStream_t st);
+size_t ray_table_bytes(int n_views, int nu, int nv);
 
 // step.cu
 cudaError_t launch_l1(const float *pred, const float *meas, long long m, float *resid, float *loss,

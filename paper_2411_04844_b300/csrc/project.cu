@@ -11,12 +11,16 @@
 // adjoint, for a voxel, intersects the three slab intervals built from the SAME
 // plane crossings, so each chord length is the same FP32 value in both.
 //
-//   k_ray_tables  per (view, iu): X0, D (FP64 arithmetic, stored FP32)
+//   k_ray_tables  per (view, iu): X0, D (FP64 arithmetic, stored FP32);
+//                 per detector row: z slope, its reciprocal, FP64 layer snap
 //   k_project     one thread per ray, incremental plane walk; u-adjacent
 //                 rays in a warp read neighbouring voxels
+//   k_scale_dn    residual x |D| per ray (chord lengths are t-intervals x |D|)
 //   k_backproject one thread per (x, y) column and a chunk of z: for each view
-//                 it finds the few rays whose pixel footprint can meet the
-//                 voxel and gathers length x residual -- no atomics
+//                 the candidate detector columns come from the column's four
+//                 corners, the candidate rows per voxel in closed form from the
+//                 column's slab interval; each candidate costs one slab test
+//                 and one load -- no divisions, no atomics
 #include <math.h>
 
 #include "dgr_internal.cuh"
@@ -24,8 +28,13 @@
 namespace dgr {
 namespace {
 
-constexpr int BP_ZC = 16;        // voxels per backprojector thread along z
 constexpr float CAND_EPS = 1e-3f;  // pixel margin of the candidate-ray search
+
+// Per detector row: zv = v / h (FP32), its reciprocal (0 when zv == 0), the
+// FP64-snapped z layer used when the ray runs parallel to the z planes, and v.
+struct __align__(16) RowZ {
+    float zv, izv, zsnap, v;
+};
 
 // For an axis the ray runs parallel to, only floor(xi) matters (which voxel
 // layer holds the ray).  That decision is taken in FP64 and stored as the
@@ -34,14 +43,20 @@ constexpr float CAND_EPS = 1e-3f;  // pixel margin of the candidate-ray search
 __device__ __forceinline__ float snap_layer(double xi) { return (float)(floor(xi) + 0.5); }
 
 __global__ void k_ray_tables(dgr_grid g, dgr_geom geo, RayXY *__restrict__ tab,
-                             float2 *__restrict__ view_cs, float *__restrict__ zsnap) {
+                             float2 *__restrict__ view_cs, RowZ *__restrict__ rows) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < geo.nv) {
-        // z layer of the rays of detector row idx when they run parallel to
-        // the z planes (parallel beam, or the cone's v = 0 row)
-        const double v = ((double)idx - 0.5 * (double)(geo.nv - 1)) * (double)geo.pv;
-        const double X0z = geo.beam == DGR_CONE ? 0.0 : v;
-        zsnap[idx] = snap_layer((X0z - (double)g.oz) / (double)g.h);
+        const float v = ((float)idx - 0.5f * (float)(geo.nv - 1)) * geo.pv;
+        RowZ R;
+        R.v = v;
+        R.zv = geo.beam == DGR_CONE ? v / g.h : 0.f;
+        R.izv = R.zv != 0.f ? 1.0f / R.zv : 0.f;
+        // z layer of the rays of this row when they run parallel to the z
+        // planes (parallel beam, or the cone's v = 0 row)
+        const double v64 = ((double)idx - 0.5 * (double)(geo.nv - 1)) * (double)geo.pv;
+        const double X0z = geo.beam == DGR_CONE ? 0.0 : v64;
+        R.zsnap = snap_layer((X0z - (double)g.oz) / (double)g.h);
+        rows[idx] = R;
     }
     if (idx >= geo.n_views * geo.nu) return;
     const int k = idx / geo.nu, iu = idx % geo.nu;
@@ -75,35 +90,37 @@ __global__ void k_ray_tables(dgr_grid g, dgr_geom geo, RayXY *__restrict__ tab,
 }
 
 struct RayZ {
-    float xi0z, ez, inv_ez, dn;
+    float xi0z, ez, inv_ez;
 };
 
-// z part of ray (iu, iv); identical FP32 sequence in both kernels.
-__device__ __forceinline__ RayZ ray_z(const RayXY &r, const dgr_grid &g, const dgr_geom &geo,
-                                      const float *__restrict__ zsnap, int iv) {
+// z part of ray (iu, iv); the identical FP32 sequence in every kernel.
+// zoff = -oz / h.
+__device__ __forceinline__ RayZ ray_z(const RayXY &r, const RowZ &row, float zoff) {
     RayZ z;
-    const float v = ((float)iv - 0.5f * (float)(geo.nv - 1)) * geo.pv;
-    if (geo.beam == DGR_CONE && v != 0.f) {
-        z.ez = v / g.h;
-        z.dn = sqrtf(r.dxy2 + v * v);
-        z.xi0z = (r.tc * v - g.oz) / g.h;
-        z.inv_ez = 1.0f / z.ez;
+    if (row.zv != 0.f) {
+        z.ez = row.zv;
+        z.inv_ez = row.izv;
+        z.xi0z = fmaf(r.tc, row.zv, zoff);
     } else {
         z.ez = 0.f;
-        z.dn = sqrtf(geo.beam == DGR_CONE ? r.dxy2 + v * v : r.dxy2);
-        z.xi0z = zsnap[iv];
         z.inv_ez = 0.f;
+        z.xi0z = row.zsnap;
     }
     return z;
+}
+
+// |D| of ray (iu, iv): the world length of a unit t-interval
+__device__ __forceinline__ float ray_norm(const RayXY &r, const RowZ &row, int beam) {
+    return sqrtf(beam == DGR_CONE ? fmaf(row.v, row.v, r.dxy2) : r.dxy2);
 }
 
 __device__ __forceinline__ float plane_t(int p, float xi0, float inv) {
     return ((float)p - xi0) * inv;
 }
 
-__global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo,
+__global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo, float zoff,
                                                  const RayXY *__restrict__ tab,
-                                                 const float *__restrict__ zsnap,
+                                                 const RowZ *__restrict__ rows,
                                                  const float *__restrict__ vol,
                                                  float *__restrict__ sino) {
     const long long nrays = (long long)geo.n_views * geo.nv * geo.nu;
@@ -113,7 +130,8 @@ __global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo,
     const int iv = (int)((r / geo.nu) % geo.nv);
     const int k = (int)(r / ((long long)geo.nu * geo.nv));
     const RayXY R = tab[k * geo.nu + iu];
-    const RayZ Z = ray_z(R, g, geo, zsnap, iv);
+    const RowZ row = rows[iv];
+    const RayZ Z = ray_z(R, row, zoff);
     const float xi0[3] = {R.xi0x, R.xi0y, Z.xi0z};
     const float ev[3] = {R.ex, R.ey, Z.ez};
     const float inv[3] = {R.inv_ex, R.inv_ey, Z.inv_ez};
@@ -165,29 +183,73 @@ __global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo,
     long long idx = idx3[2] * sz + idx3[1] * sy + idx3[0];
     int ix = idx3[0], iy = idx3[1], iz = idx3[2];
     float t = tmin, acc = 0.f;
-    const int maxit = g.nx + g.ny + g.nz + 3;
-    for (int it = 0; it < maxit; ++it) {
-        const float tnext = fminf(tn[0], fminf(tn[1], tn[2]));
-        acc = fmaf(tnext - t, __ldg(vol + idx), acc);
-        t = tnext;
-        if (tnext == tn[0]) {
-            ix += sgn[0];
-            if (ix < 0 || ix >= g.nx) break;
-            idx += sgn[0] * sx;
-            tn[0] = plane_t(sgn[0] > 0 ? ix + 1 : ix, xi0[0], inv[0]);
-        } else if (tnext == tn[1]) {
-            iy += sgn[1];
-            if (iy < 0 || iy >= g.ny) break;
-            idx += sgn[1] * sy;
-            tn[1] = plane_t(sgn[1] > 0 ? iy + 1 : iy, xi0[1], inv[1]);
-        } else {
-            iz += sgn[2];
-            if (iz < 0 || iz >= g.nz) break;
-            idx += sgn[2] * sz;
-            tn[2] = plane_t(sgn[2] > 0 ? iz + 1 : iz, xi0[2], inv[2]);
+    // walk the plane crossings WALK segments at a time: the segment lengths and
+    // voxel indices first (ALU only), then their loads together, so several
+    // gathers are in flight per thread; the sum order is the walk order
+    constexpr int WALK = 4;
+    const int maxgroups = (g.nx + g.ny + g.nz + 3) / WALK + 1;
+    bool done = false;
+    for (int grp = 0; grp < maxgroups && !done; ++grp) {
+        float len[WALK];
+        long long at[WALK];
+#pragma unroll
+        for (int j = 0; j < WALK; ++j) {
+            at[j] = idx;
+            len[j] = 0.f;
+            if (done) continue;
+            const float tnext = fminf(tn[0], fminf(tn[1], tn[2]));
+            len[j] = tnext - t;
+            t = tnext;
+            if (tnext == tn[0]) {
+                ix += sgn[0];
+                if (ix < 0 || ix >= g.nx) { done = true; continue; }
+                idx += sgn[0] * sx;
+                tn[0] = plane_t(sgn[0] > 0 ? ix + 1 : ix, xi0[0], inv[0]);
+            } else if (tnext == tn[1]) {
+                iy += sgn[1];
+                if (iy < 0 || iy >= g.ny) { done = true; continue; }
+                idx += sgn[1] * sy;
+                tn[1] = plane_t(sgn[1] > 0 ? iy + 1 : iy, xi0[1], inv[1]);
+            } else {
+                iz += sgn[2];
+                if (iz < 0 || iz >= g.nz) { done = true; continue; }
+                idx += sgn[2] * sz;
+                tn[2] = plane_t(sgn[2] > 0 ? iz + 1 : iz, xi0[2], inv[2]);
+            }
         }
+        float v[WALK];
+#pragma unroll
+        for (int j = 0; j < WALK; ++j) v[j] = __ldg(vol + at[j]);
+#pragma unroll
+        for (int j = 0; j < WALK; ++j) acc = fmaf(len[j], v[j], acc);
     }
-    sino[r] = acc * Z.dn;
+    sino[r] = acc * ray_norm(R, row, geo.beam);
+}
+
+// residual x |D| per ray, written view-major with v fastest ([view][u][v]) so
+// that the backprojector's lanes (consecutive z -> consecutive detector rows)
+// read it coalesced; the chord lengths are t-intervals x |D|
+constexpr int TR = 32;
+__global__ void k_scale_dn_t(dgr_geom geo, const RayXY *__restrict__ tab,
+                             const RowZ *__restrict__ rows, const float *__restrict__ in,
+                             float *__restrict__ out) {
+    __shared__ float tile[TR][TR + 1];
+    const int k = blockIdx.z;
+    const int u0 = blockIdx.x * TR, v0 = blockIdx.y * TR;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    const float *src = in + (size_t)k * geo.nv * geo.nu;
+    for (int j = ty; j < TR; j += 8) {
+        const int iv = v0 + j, iu = u0 + tx;
+        if (iv < geo.nv && iu < geo.nu)
+            tile[j][tx] = src[(size_t)iv * geo.nu + iu] *
+                          ray_norm(tab[k * geo.nu + iu], rows[iv], geo.beam);
+    }
+    __syncthreads();
+    float *dst = out + (size_t)k * geo.nu * geo.nv;
+    for (int j = ty; j < TR; j += 8) {
+        const int iu = u0 + j, iv = v0 + tx;
+        if (iv < geo.nv && iu < geo.nu) dst[(size_t)iu * geo.nv + iv] = tile[tx][j];
+    }
 }
 
 // slab interval of voxel index i along one axis; false if empty
@@ -203,91 +265,143 @@ __device__ __forceinline__ bool slab(int i, float xi0, float e, float inv, float
     return floorf(xi0) == (float)i;
 }
 
-__global__ void __launch_bounds__(128) k_backproject(dgr_grid g, dgr_geom geo,
-                                                     const RayXY *__restrict__ tab,
-                                                     const float2 *__restrict__ view_cs,
-                                                     const float *__restrict__ zsnap,
-                                                     const float *__restrict__ sino,
-                                                     float *__restrict__ vol) {
-    const int ix = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int iy = blockIdx.y * 4 + (threadIdx.x >> 5);
-    const int z0 = blockIdx.z * BP_ZC;
-    if (ix >= g.nx || iy >= g.ny) return;
-    float acc[BP_ZC];
+// Backprojector: a CTA of BP_W warps owns BP_W consecutive x-columns at one y
+// and a z-pass of 32 * BP_ZJ voxels; a warp owns one column, its lanes
+// consecutive z (lane + 32 j).  For each view the candidate detector columns
+// follow from the column's 4 corners (warp-uniform), the slab interval of each
+// candidate ray column is warp-uniform, and each lane finds its candidate rows
+// in closed form and gathers length x scaled residual (rows contiguous across
+// lanes).  The CTA's results leave through shared memory as full sectors.
+constexpr int BP_W = 8;
+constexpr int BP_ZJ = 8;
+constexpr int BP_ZP = 32 * BP_ZJ;
+
+template <bool CONE>
+__global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(dgr_grid g, dgr_geom geo, float zoff,
+                                                          const RayXY *__restrict__ tab,
+                                                          const float2 *__restrict__ view_cs,
+                                                          const RowZ *__restrict__ rows,
+                                                          const float *__restrict__ sino_t,
+                                                          float *__restrict__ vol) {
+    __shared__ float out_tile[BP_ZP][BP_W];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ix = blockIdx.x * BP_W + w;
+    const int iy = blockIdx.y;
+    const int zp = blockIdx.z * BP_ZP;
+    float acc[BP_ZJ];
 #pragma unroll
-    for (int k = 0; k < BP_ZC; ++k) acc[k] = 0.f;
-    const float h = g.h;
-    const float xl = g.ox + ix * h, xh = xl + h, yl = g.oy + iy * h, yh = yl + h;
-    const float cu = 0.5f * (float)(geo.nu - 1), cv = 0.5f * (float)(geo.nv - 1);
-    const bool cone = geo.beam == DGR_CONE;
-    for (int k = 0; k < geo.n_views; ++k) {
-        const float2 cs = view_cs[k];
-        // pixel-u range of the column's 4 (x, y) corners, magnification range
-        float umin = INFINITY, umax = -INFINITY, mmin = INFINITY, mmax = -INFINITY;
+    for (int j = 0; j < BP_ZJ; ++j) acc[j] = 0.f;
+    if (ix < g.nx) {
+        const float h = g.h;
+        const float xl = g.ox + ix * h, xh = xl + h, yl = g.oy + iy * h, yh = yl + h;
+        const float cu = 0.5f * (float)(geo.nu - 1), cv = 0.5f * (float)(geo.nv - 1);
+        const float inv_pu = 1.0f / geo.pu;
+        const float rows_per_zv = g.h / geo.pv;  // detector rows per unit of zv
+        const float row_of_oz = g.oz / geo.pv + cv;
+        for (int k = 0; k < geo.n_views; ++k) {
+            const float2 cs = __ldg(view_cs + k);
+            float umin = INFINITY, umax = -INFINITY;
 #pragma unroll
-        for (int cnr = 0; cnr < 4; ++cnr) {
-            const float X = (cnr & 1) ? xh : xl, Y = (cnr & 2) ? yh : yl;
-            const float pu_ = -X * cs.y + Y * cs.x;
-            const float pr = X * cs.x + Y * cs.y;
-            const float M = cone ? geo.dsd / (geo.dso + pr) : 1.f;
-            const float uu = M * pu_ / geo.pu + cu;
-            umin = fminf(umin, uu); umax = fmaxf(umax, uu);
-            mmin = fminf(mmin, M); mmax = fmaxf(mmax, M);
-        }
-        const int iu0 = max(0, (int)ceilf(umin - CAND_EPS));
-        const int iu1 = min(geo.nu - 1, (int)floorf(umax + CAND_EPS));
-        for (int iu = iu0; iu <= iu1; ++iu) {
-            const RayXY R = tab[k * geo.nu + iu];
-            float xlo, xhi, ylo, yhi;
-            if (!slab(ix, R.xi0x, R.ex, R.inv_ex, xlo, xhi)) continue;
-            if (!slab(iy, R.xi0y, R.ey, R.inv_ey, ylo, yhi)) continue;
-            const float tlo = fmaxf(xlo, ylo), thi = fminf(xhi, yhi);
-            if (!(thi > tlo)) continue;
-            const float *srow = sino + (size_t)k * geo.nv * geo.nu + iu;
-#pragma unroll
-            for (int zz = 0; zz < BP_ZC; ++zz) {
-                const int iz = z0 + zz;
-                if (iz >= g.nz) break;
-                const float zl = g.oz + iz * h, zh = zl + h;
-                float v0, v1;
-                if (cone) {
-                    v0 = fminf(zl * mmin, zl * mmax);
-                    v1 = fmaxf(zh * mmin, zh * mmax);
+            for (int cnr = 0; cnr < 4; ++cnr) {
+                const float X = (cnr & 1) ? xh : xl, Y = (cnr & 2) ? yh : yl;
+                const float pu_ = fmaf(-X, cs.y, Y * cs.x);
+                float uu;
+                if (CONE) {
+                    const float pr = fmaf(X, cs.x, Y * cs.y);
+                    uu = __fdividef(geo.dsd * pu_, geo.dso + pr) * inv_pu + cu;
                 } else {
-                    v0 = zl; v1 = zh;
+                    uu = pu_ * inv_pu + cu;
                 }
-                const int iv0 = max(0, (int)ceilf(v0 / geo.pv + cv - CAND_EPS));
-                const int iv1 = min(geo.nv - 1, (int)floorf(v1 / geo.pv + cv + CAND_EPS));
-                float a = acc[zz];
-                for (int iv = iv0; iv <= iv1; ++iv) {
-                    const RayZ Z = ray_z(R, g, geo, zsnap, iv);
-                    float zlo, zhi;
-                    if (!slab(iz, Z.xi0z, Z.ez, Z.inv_ez, zlo, zhi)) continue;
-                    const float len = fminf(thi, zhi) - fmaxf(tlo, zlo);
-                    if (len > 0.f) a = fmaf(len * Z.dn, __ldg(srow + (size_t)iv * geo.nu), a);
+                umin = fminf(umin, uu);
+                umax = fmaxf(umax, uu);
+            }
+            const int iu0 = max(0, (int)ceilf(umin - CAND_EPS));
+            const int iu1 = min(geo.nu - 1, (int)floorf(umax + CAND_EPS));
+            for (int iu = iu0; iu <= iu1; ++iu) {
+                const RayXY R = tab[k * geo.nu + iu];
+                float xlo, xhi, ylo, yhi;
+                if (!slab(ix, R.xi0x, R.ex, R.inv_ex, xlo, xhi)) continue;
+                if (!slab(iy, R.xi0y, R.ey, R.inv_ey, ylo, yhi)) continue;
+                const float tlo = fmaxf(xlo, ylo), thi = fminf(xhi, yhi);
+                if (!(thi > tlo)) continue;
+                const float *scol = sino_t + ((size_t)k * geo.nu + iu) * geo.nv;
+                if (CONE) {
+                    // ray row zv meets layer iz over t in [tlo, thi] only if
+                    // z = zv (tc + t) + zoff, with tc + t in [wa, wb] (> 0: between
+                    // source and detector), reaches [iz, iz + 1]:
+                    //   zv in [min(zr/wa, zr/wb), max((zr+1)/wa, (zr+1)/wb)], zr = iz - zoff
+                    const float ia = __fdividef(rows_per_zv, R.tc + tlo);
+                    const float ib = __fdividef(rows_per_zv, R.tc + thi);
+#pragma unroll
+                    for (int j = 0; j < BP_ZJ; ++j) {
+                        const int iz = zp + lane + 32 * j;
+                        if (iz >= g.nz) break;
+                        const float zr = (float)iz - zoff;
+                        const float f0 = fminf(fmaf(zr, ia, cv), fmaf(zr, ib, cv));
+                        const float f1 = fmaxf(fmaf(zr + 1.0f, ia, cv), fmaf(zr + 1.0f, ib, cv));
+                        const int iv0 = max(0, (int)ceilf(f0 - CAND_EPS));
+                        const int iv1 = min(geo.nv - 1, (int)floorf(f1 + CAND_EPS));
+                        float a = acc[j];
+                        for (int iv = iv0; iv <= iv1; ++iv) {
+                            const RowZ row = rows[iv];
+                            const RayZ Z = ray_z(R, row, zoff);
+                            float zlo, zhi;
+                            if (!slab(iz, Z.xi0z, Z.ez, Z.inv_ez, zlo, zhi)) continue;
+                            const float len = fminf(thi, zhi) - fmaxf(tlo, zlo);
+                            if (len > 0.f) a = fmaf(len, __ldg(scol + iv), a);
+                        }
+                        acc[j] = a;
+                    }
+                } else {
+                    const float len = thi - tlo;
+#pragma unroll
+                    for (int j = 0; j < BP_ZJ; ++j) {
+                        const int iz = zp + lane + 32 * j;
+                        if (iz >= g.nz) break;
+                        const float f = fmaf((float)iz, rows_per_zv, row_of_oz);
+                        const int iv0 = max(0, (int)ceilf(f - CAND_EPS));
+                        const int iv1 = min(geo.nv - 1, (int)floorf(f + rows_per_zv + CAND_EPS));
+                        float a = acc[j];
+                        for (int iv = iv0; iv <= iv1; ++iv) {
+                            if (floorf(rows[iv].zsnap) == (float)iz) a = fmaf(len, __ldg(scol + iv), a);
+                        }
+                        acc[j] = a;
+                    }
                 }
-                acc[zz] = a;
             }
         }
     }
-    float *col = vol + (size_t)iy * g.nx + ix;
-    const size_t zs = (size_t)g.nx * g.ny;
 #pragma unroll
-    for (int zz = 0; zz < BP_ZC; ++zz)
-        if (z0 + zz < g.nz) col[(size_t)(z0 + zz) * zs] = acc[zz];
+    for (int j = 0; j < BP_ZJ; ++j) out_tile[lane + 32 * j][w] = acc[j];
+    __syncthreads();
+    // write back: 8 consecutive x of one z per 8 threads (one 32-byte sector)
+    const size_t zs = (size_t)g.nx * g.ny;
+    for (int i = threadIdx.x; i < BP_ZP * BP_W; i += 32 * BP_W) {
+        const int zz = i / BP_W, xx = i % BP_W;
+        const int x = blockIdx.x * BP_W + xx, z = zp + zz;
+        if (x < g.nx && z < g.nz) vol[(size_t)z * zs + (size_t)iy * g.nx + x] = out_tile[zz][xx];
+    }
 }
 
-}  // namespace
-
-// table layout: RayXY [n_views * nu] | float2 cos/sin [n_views] | float zsnap [nv]
+// table layout: RayXY [n_views * nu] | float2 cos/sin [n_views] (padded to 16 B) | RowZ [nv]
 struct Tables {
     const float2 *view_cs;
-    const float *zsnap;
+    const RowZ *rows;
 };
 static Tables tables_of(const dgr_geom &geo, const RayXY *tab) {
     const int n = geo.n_views * geo.nu;
     const float2 *cs = reinterpret_cast<const float2 *>(tab + n);
-    return Tables{cs, reinterpret_cast<const float *>(cs + geo.n_views)};
+    const size_t cs_bytes = align_up(sizeof(float2) * (size_t)geo.n_views, 16);
+    return Tables{cs, reinterpret_cast<const RowZ *>(reinterpret_cast<const char *>(cs) + cs_bytes)};
+}
+
+static float zoff_of(const dgr_grid &g) { return -g.oz / g.h; }
+
+}  // namespace
+
+size_t ray_table_bytes(int n_views, int nu, int nv) {
+    return sizeof(RayXY) * (size_t)n_views * nu + align_up(sizeof(float2) * (size_t)n_views, 16) +
+           sizeof(RowZ) * (size_t)nv;
 }
 
 cudaError_t launch_ray_tables(const dgr_grid &g, const dgr_geom &geo, RayXY *tab, cudaStream_t st) {
@@ -295,7 +409,7 @@ cudaError_t launch_ray_tables(const dgr_grid &g, const dgr_geom &geo, RayXY *tab
     const Tables T = tables_of(geo, tab);
     const int m = n > geo.nv ? n : geo.nv;
     k_ray_tables<<<(m + 127) / 128, 128, 0, st>>>(g, geo, tab, const_cast<float2 *>(T.view_cs),
-                                                  const_cast<float *>(T.zsnap));
+                                                  const_cast<RowZ *>(T.rows));
     counted(1);
     return cudaGetLastError();
 }
@@ -304,17 +418,25 @@ cudaError_t launch_project(const dgr_grid &g, const dgr_geom &geo, const RayXY *
                            const float *vol, float *sino, cudaStream_t st) {
     const long long nrays = (long long)geo.n_views * geo.nv * geo.nu;
     const long long blocks = (nrays + 127) / 128;
-    k_project<<<(unsigned)blocks, 128, 0, st>>>(g, geo, tab, tables_of(geo, tab).zsnap, vol, sino);
+    k_project<<<(unsigned)blocks, 128, 0, st>>>(g, geo, zoff_of(g), tab, tables_of(geo, tab).rows,
+                                                vol, sino);
     counted(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
-                               const float *sino, float *vol, cudaStream_t st) {
+                               const float *sino, float *sino_scaled, float *vol, cudaStream_t st) {
     const Tables T = tables_of(geo, tab);
-    dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, (g.nz + BP_ZC - 1) / BP_ZC);
-    k_backproject<<<grid, 128, 0, st>>>(g, geo, tab, T.view_cs, T.zsnap, sino, vol);
-    counted(1);
+    dim3 tgrid((geo.nu + TR - 1) / TR, (geo.nv + TR - 1) / TR, geo.n_views);
+    k_scale_dn_t<<<tgrid, 256, 0, st>>>(geo, tab, T.rows, sino, sino_scaled);
+    dim3 grid((g.nx + BP_W - 1) / BP_W, g.ny, (g.nz + BP_ZP - 1) / BP_ZP);
+    if (geo.beam == DGR_CONE)
+        k_backproject<true><<<grid, 32 * BP_W, 0, st>>>(g, geo, zoff_of(g), tab, T.view_cs, T.rows,
+                                                        sino_scaled, vol);
+    else
+        k_backproject<false><<<grid, 32 * BP_W, 0, st>>>(g, geo, zoff_of(g), tab, T.view_cs, T.rows,
+                                                         sino_scaled, vol);
+    counted(2);
     return cudaGetLastError();
 }
 

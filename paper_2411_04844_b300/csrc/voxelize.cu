@@ -169,14 +169,9 @@ __global__ void k_prep(dgr_grid g, int n, const float *__restrict__ mu, const fl
     P.by = empty ? box_pack(1, 0) : box_pack(F.lo[1], F.hi[1]);
     P.bz = empty ? box_pack(1, 0) : box_pack(F.lo[2], F.hi[2]);
     prep[i] = P;
-    // backward work items: z-chunks of at most ~ITEM_VOX voxels
+    // backward work items of at most ~ITEM_VOX voxels (item_count)
     const int ex = F.hi[0] - F.lo[0] + 1, ey = F.hi[1] - F.lo[1] + 1, ez = F.hi[2] - F.lo[2] + 1;
-    uint32_t items = 0;
-    if (!empty && ex > 0 && ey > 0 && ez > 0) {
-        const int zc = max(1, ITEM_VOX / (ex * ey));
-        items = (uint32_t)((ez + zc - 1) / zc);
-    }
-    itemcnt[i] = items;
+    itemcnt[i] = empty ? 0u : item_count(ex, ey, ez);
 }
 
 // Tile range of a Gaussian; false if its box misses the grid.

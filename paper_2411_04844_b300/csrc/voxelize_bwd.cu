@@ -46,15 +46,15 @@ __global__ void __launch_bounds__(256) k_bwd_items(
         const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
                   lz = box_lo(P.bz), hz = box_hi(P.bz);
         const int ex = hx - lx + 1, ey = hy - ly + 1;
-        const int zc = max(1, ITEM_VOX / (ex * ey));
-        const int zb = lz + c * zc, ze = min(zb + zc - 1, hz);
+        int yb, ye, zb, ze;
+        item_range(c, ex, ey, ly, hy, lz, hz, yb, ye, zb, ze);
         float m[NMOM];
 #pragma unroll
         for (int k = 0; k < NMOM; ++k) m[k] = 0.f;
-        const int exy = ex * ey;
+        const int exy = ex * (ye - yb + 1);
         const float dz0 = (float)(zb - P.az) - P.dz;
         for (int j = lane; j < exy; j += 32) {
-            const int yy = ly + j / ex, xx = lx + j % ex;
+            const int yy = yb + j / ex, xx = lx + j % ex;
             const float dx = (float)(xx - P.ax) - P.dx;
             const float dy = (float)(yy - P.ay) - P.dy;
             const float C = fmaf(P.a00 * dx, dx, fmaf(P.a11 * dy, dy, P.a01 * dx * dy));
@@ -106,14 +106,18 @@ __global__ void k_bwd_final(dgr_grid g, int n, const float *__restrict__ mu,
     if (i >= n) return;
     unsigned long long b = item_off[i], e = item_off[i + 1];
     if (e > cap) e = cap;
-    float M[NMOM];
+    // item partials summed in FP64 (a large box has tens of thousands of items)
+    double Md[NMOM];
 #pragma unroll
-    for (int k = 0; k < NMOM; ++k) M[k] = 0.f;
+    for (int k = 0; k < NMOM; ++k) Md[k] = 0.0;
     for (unsigned long long it = b; it < e; ++it) {
         const float *src = part + it * NMOM;
 #pragma unroll
-        for (int k = 0; k < NMOM; ++k) M[k] += src[k];
+        for (int k = 0; k < NMOM; ++k) Md[k] += (double)src[k];
     }
+    float M[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) M[k] = (float)Md[k];
     if (b >= e) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) { g_mu[3 * i + a] = 0.f; g_s[3 * i + a] = 0.f; }

@@ -1,0 +1,82 @@
+"""Run one entry point of the C ABI a few times on a synthetic workload, with
+every input already in HBM -- a fixed, small command for profilers.
+
+    python -m paper_2411_04844_b300.profile_cases OP [--workload 2] [--reps 3] [--views N]
+
+OP: voxelize | voxelize_backward | project | backproject | step.
+Workload numbers are those of synth.workload (2: 50,000 Gaussians, 256^3,
+cone 50 views x 256^2).  --views keeps only the first N views (smaller
+captures).  Prints the mean CUDA-event time per call.
+"""
+import argparse
+import sys
+
+import numpy as np
+import torch
+
+from . import dgr, synth
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("op", choices=["voxelize", "voxelize_backward", "project", "backproject", "step"])
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--views", type=int, default=0)
+    a = ap.parse_args(argv)
+    wl = synth.workload(a.workload)
+    geo_spec = wl.geom
+    if a.views:
+        geo_spec = synth.GeomSpec(geo_spec.beam, geo_spec.angles[:a.views], geo_spec.nu,
+                                  geo_spec.nv, geo_spec.pu, geo_spec.pv, geo_spec.dso, geo_spec.dsd)
+    dev = "cuda"
+    T = lambda x: torch.as_tensor(np.ascontiguousarray(x), device=dev)
+    grid = dgr.Grid.of(wl.grid)
+    ang = T(geo_spec.angles)
+    geom = dgr.Geom.of(geo_spec, ang)
+    f = synth.gaussian_field(synth.rng_for(a.workload, 0), wl.n_gauss, wl.grid, wl.scale)
+    f.rho = np.clip(f.rho, 0.02, 1.0).astype(np.float32)
+    mu, s, q, rho = T(f.mu), T(f.s), T(f.q), T(f.rho)
+    ws0 = dgr.Workspace(dgr.make_plan(grid, f.n))
+    pairs, items = dgr.dgr_voxelize_count(grid, mu, s, q, wl.k_trunc, ws0)
+    ws0.close()
+    ws = dgr.Workspace(dgr.make_plan(grid, f.n, int(pairs * 1.5) + 1024, int(items * 1.5) + 1024,
+                                     geom, step=True))
+    rng = np.random.default_rng(0)
+    vol = T(rng.uniform(0, 1, wl.grid.shape).astype(np.float32))
+    sino = T(rng.standard_normal(geo_spec.shape).astype(np.float32))
+    outs = [torch.empty(sh, device=dev) for sh in ((f.n, 3), (f.n, 3), (f.n, 4), (f.n,))]
+    prob = dgr.make_problem(grid, geom, wl.k_trunc, 3e-4, 3e-5, max(wl.n_iters, 2))
+    st = dgr.State(mu, s, q, rho)
+    dgr.dgr_params_init(prob, st)
+    loss = torch.zeros(1, device=dev)
+    out_vol = torch.empty(wl.grid.shape, device=dev)
+    out_sino = torch.empty(geo_spec.shape, device=dev)
+
+    def once():
+        if a.op == "voxelize":
+            dgr.dgr_voxelize(grid, mu, s, q, rho, wl.k_trunc, out_vol, ws)
+        elif a.op == "voxelize_backward":
+            dgr.dgr_voxelize_backward(grid, mu, s, q, rho, wl.k_trunc, vol, *outs, ws)
+        elif a.op == "project":
+            dgr.dgr_project(grid, geom, vol, out_sino, ws)
+        elif a.op == "backproject":
+            dgr.dgr_backproject(grid, geom, sino, out_vol, ws)
+        else:
+            dgr.dgr_step(prob, st, sino, loss, ws)
+
+    once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    status = dgr.dgr_status(ws)
+    print(f"{a.op}: {e0.elapsed_time(e1) / a.reps:.4f} ms per call (status {status})")
+    return 0 if status == 0 else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -182,6 +182,16 @@ def test_brute_force_equals_footprint_loop():
     assert np.max(np.abs(a - b)) < 1e-13
 
 
+def test_point_evaluation_equals_full_volume():
+    g = grid_of((21, 18, 15))
+    rng = synth.rng_for(1, 98)
+    f = synth.gaussian_field(rng, 80, synth.GridSpec((21, 18, 15), 1.0, g.org), ("loguniform", 0.5, 3.0))
+    vol = O.voxelize(g, f.mu, f.s, f.q, f.rho, 3.0, brute=True)
+    pts = np.stack([rng.integers(0, 21, 50), rng.integers(0, 18, 50), rng.integers(0, 15, 50)], 1)
+    v = O.voxelize_points(g, f.mu, f.s, f.q, f.rho, pts, 3.0)
+    assert np.max(np.abs(v - vol[pts[:, 2], pts[:, 1], pts[:, 0]])) < 1e-14
+
+
 # ---------------------------------------------------------------------------
 # footprint integers
 # ---------------------------------------------------------------------------
