@@ -195,6 +195,34 @@ int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *me
                    float *loss_out, dgr_ws *ws, cudaStream_t stream, cudaEvent_t *events,
                    int n_events);
 
+/* Projector for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a library-level variant of dgr_project.
+ *
+ * Some callers may not call cudaMalloc at all: code hosted inside an
+ * application that hands out all device memory from its own pool and forbids
+ * driver allocations in plug-ins; loops with a latency budget in which an
+ * allocation (which may synchronise the device) is not allowed; code that runs
+ * after a one-time initialisation phase during which all memory was reserved.
+ * For them this entry point computes exactly what dgr_project computes (same
+ * kernels, same results) without any dgr_ws: its scratch (the ray tables,
+ * 32 bytes per (view, detector column) + 16 bytes per detector row + 8 bytes
+ * per view, rounded) lives in one fixed device array of
+ * DGR_NOALLOC_SCRATCH_BYTES that every GPU using the library holds until the
+ * process exits.  The caller still passes vol and sino (device pointers).
+ *  - Geometries whose ray tables exceed the array (e.g. more than ~130,000
+ *    views x detector columns) return DGR_ERR_WS_TOO_SMALL; nothing runs.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *    first call before any stream capture on the device.
+ *  - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - All calls on a device share the one array (it keeps the last call's
+ *    tables, every call rewrites them in full): calls that overlap on the GPU
+ *    (e.g. on two streams at once) race and give wrong results.  Order them.
+ * Arguments, layouts and errors otherwise as dgr_project. */
+#define DGR_NOALLOC_SCRATCH_BYTES (4 << 20)
+int dgr_project_noalloc(const dgr_grid *grid, const dgr_geom *geom, const float *vol,
+                        float *sino, cudaStream_t stream);
+
 /* Total number of kernels this library has launched in this process (a host
  * counter; lets callers count launches inside a timed region). */
 long long dgr_launch_count(void);

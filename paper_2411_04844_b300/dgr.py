@@ -34,7 +34,10 @@ EXPORTS = [
     "dgr_strerror", "dgr_set_deterministic", "dgr_footprint", "dgr_voxelize_count",
     "dgr_voxelize", "dgr_voxelize_backward", "dgr_project", "dgr_backproject",
     "dgr_l1_residual", "dgr_params_init", "dgr_step", "dgr_step_timed", "dgr_launch_count",
+    "dgr_project_noalloc",
 ]
+# size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
+NOALLOC_SCRATCH_BYTES = 4 << 20
 DGR_STEP_EVENTS = 7
 STEP_PHASES = ("voxelize", "project", "l1", "backproject", "voxelize_backward", "adam")
 
@@ -129,6 +132,7 @@ def lib():
             "dgr_step": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P],
             "dgr_step_timed": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P,
                                ctypes.POINTER(P), i],
+            "dgr_project_noalloc": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -289,6 +293,15 @@ def dgr_backproject(grid: Grid, geom: Geom, sino, vol, ws: Workspace, stream=Non
     _check(vol, "vol"); _check(sino, "sino")
     _rc(lib().dgr_backproject(ctypes.byref(grid), ctypes.byref(geom), _ptr(sino), _ptr(vol),
                               ws.ptr, _stream(stream)), "dgr_backproject")
+
+
+def dgr_project_noalloc(grid: Grid, geom: Geom, vol, sino, stream=None):
+    """dgr_project without a workspace: scratch in a fixed device array (for
+    callers that cannot allocate).  Raises DgrError if the geometry's ray
+    tables do not fit NOALLOC_SCRATCH_BYTES."""
+    _check(vol, "vol"); _check(sino, "sino")
+    _rc(lib().dgr_project_noalloc(ctypes.byref(grid), ctypes.byref(geom), _ptr(vol), _ptr(sino),
+                                  _stream(stream)), "dgr_project_noalloc")
 
 
 def dgr_l1_residual(pred, meas, resid, loss, ws: Workspace, stream=None):
