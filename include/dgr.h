@@ -95,7 +95,7 @@ int dgr_ws_bytes(const dgr_ws_plan *plan, size_t *bytes);
 /* The only allocating calls: cudaMalloc / cudaFree of the workspace arena. */
 int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan);
 int dgr_ws_destroy(dgr_ws *ws);
-/* Voxel tiles (8 x 16 x 8 voxels) covering a grid. */
+/* Voxel tiles (8 x 16 x 32 voxels) covering a grid. */
 int dgr_tile_count(const dgr_grid *grid, int *tiles);
 
 /* Reads and clears the device status word (synchronises `stream`). */

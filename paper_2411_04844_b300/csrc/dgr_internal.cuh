@@ -9,10 +9,12 @@
 
 namespace dgr {
 
-// Voxel tile of the forward voxelizer: 8 (x) x 16 (y) x 8 (z).  A CTA of four
+// Voxel tile of the forward voxelizer: 8 (x) x 16 (y) x 32 (z).  A CTA of four
 // warps owns one tile; a warp owns an 8 x 4 patch in (x, y) and every lane
-// keeps the 8 z-voxels of its (x, y) column in registers.
-constexpr int TX = 8, TY = 16, TZ = 8;
+// keeps the 32 z-voxels of its (x, y) column in registers, so the per-Gaussian
+// set-up of a lane is shared by up to 32 exponentials.
+constexpr int TX = 8, TY = 16, TZ = 32;
+constexpr int TZG = 8;  // z handled in groups of 8 (a group outside the box is skipped)
 constexpr int VOX_THREADS = 128;
 constexpr int VOX_CHUNK = 64;  // prep records staged in shared memory at a time
 

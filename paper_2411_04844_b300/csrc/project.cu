@@ -179,13 +179,20 @@ __global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo, float
             tn[a] = INFINITY;
         }
     }
-    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
-    long long idx = idx3[2] * sz + idx3[1] * sy + idx3[0];
+    // per-axis state as scalars (selected, never indexed, so it stays in registers)
+    const long long sx = sgn[0], sy = (long long)sgn[1] * g.nx,
+                    sz = (long long)sgn[2] * g.nx * g.ny;  // signed index steps
+    long long idx = (long long)idx3[2] * g.nx * g.ny + (long long)idx3[1] * g.nx + idx3[0];
     int ix = idx3[0], iy = idx3[1], iz = idx3[2];
+    float tx = tn[0], ty = tn[1], tz = tn[2];
+    const float x0 = xi0[0], y0 = xi0[1], z0 = xi0[2];
+    const float ivx = inv[0], ivy = inv[1], ivz = inv[2];
+    const int ux = sgn[0] > 0, uy = sgn[1] > 0, uz = sgn[2] > 0;
     float t = tmin, acc = 0.f;
-    // walk the plane crossings WALK segments at a time: the segment lengths and
-    // voxel indices first (ALU only), then their loads together, so several
-    // gathers are in flight per thread; the sum order is the walk order
+    // branch-free walk: every lane takes one crossing per iteration whatever
+    // its axis (selects, no divergent branches); segment lengths and voxel
+    // indices of WALK crossings first, their loads together, then the sums
+    // in walk order
     constexpr int WALK = 4;
     const int maxgroups = (g.nx + g.ny + g.nz + 3) / WALK + 1;
     bool done = false;
@@ -195,27 +202,28 @@ __global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo, float
 #pragma unroll
         for (int j = 0; j < WALK; ++j) {
             at[j] = idx;
-            len[j] = 0.f;
-            if (done) continue;
-            const float tnext = fminf(tn[0], fminf(tn[1], tn[2]));
-            len[j] = tnext - t;
-            t = tnext;
-            if (tnext == tn[0]) {
-                ix += sgn[0];
-                if (ix < 0 || ix >= g.nx) { done = true; continue; }
-                idx += sgn[0] * sx;
-                tn[0] = plane_t(sgn[0] > 0 ? ix + 1 : ix, xi0[0], inv[0]);
-            } else if (tnext == tn[1]) {
-                iy += sgn[1];
-                if (iy < 0 || iy >= g.ny) { done = true; continue; }
-                idx += sgn[1] * sy;
-                tn[1] = plane_t(sgn[1] > 0 ? iy + 1 : iy, xi0[1], inv[1]);
-            } else {
-                iz += sgn[2];
-                if (iz < 0 || iz >= g.nz) { done = true; continue; }
-                idx += sgn[2] * sz;
-                tn[2] = plane_t(sgn[2] > 0 ? iz + 1 : iz, xi0[2], inv[2]);
-            }
+            const float tnext = fminf(tx, fminf(ty, tz));
+            len[j] = done ? 0.f : tnext - t;
+            t = done ? t : tnext;
+            const bool cx = tnext == tx;
+            const bool cy = !cx && tnext == ty;
+            const bool cz = !cx && !cy;
+            const int nxi = ix + sgn[0], nyi = iy + sgn[1], nzi = iz + sgn[2];
+            const bool out = cx ? (nxi < 0 || nxi >= g.nx)
+                                : (cy ? (nyi < 0 || nyi >= g.ny) : (nzi < 0 || nzi >= g.nz));
+            const bool step = !done && !out;
+            done = done || out;
+            const bool sxs = step && cx, sys = step && cy, szs = step && cz;
+            ix = sxs ? nxi : ix;
+            iy = sys ? nyi : iy;
+            iz = szs ? nzi : iz;
+            idx += sxs ? sx : (sys ? sy : (szs ? sz : 0));
+            // next crossing on the stepped axis
+            const int pl = cx ? nxi + ux : (cy ? nyi + uy : nzi + uz);
+            const float tnew = plane_t(pl, cx ? x0 : (cy ? y0 : z0), cx ? ivx : (cy ? ivy : ivz));
+            tx = sxs ? tnew : tx;
+            ty = sys ? tnew : ty;
+            tz = szs ? tnew : tz;
         }
         float v[WALK];
 #pragma unroll

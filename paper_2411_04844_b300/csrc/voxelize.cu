@@ -5,7 +5,7 @@
 //   a2  k_tile_count /  binning: per-tile Gaussian counts, exclusive scan,
 //       k_tile_fill /   fill of the (tile, Gaussian) work list, sort of each
 //       k_tile_sort     tile's list by Gaussian index (deterministic order)
-//   a3  k_voxelize      one CTA per 8x16x8 tile: prep records staged in shared
+//   a3  k_voxelize      one CTA per 8x16x32 tile: prep records staged in shared
 //                       memory, voxels in registers, one ex2 per in-box pair
 //
 // The paper (Sec. 4.2, Algorithm 1) materialises a [n, 17, 17, 17]
@@ -290,7 +290,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // a3: one CTA per tile.  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
-// (lx, ly) = (lane & 7, lane >> 3), and z in [tz0, tz0 + 8) in registers.
+// (lx, ly) = (lane & 7, lane >> 3), and z in [tz0, tz0 + TZ) in registers.
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     dgr_grid g, int NTX, int NTY, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
@@ -338,11 +338,16 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
             const float dz0 = (float)(z0 - az) - p0.z;
             const float a22 = p1.z, r = p0.w;
 #pragma unroll
-            for (int k = 0; k < TZ; ++k) {
-                if (k >= zlo && k <= zhi) {
-                    const float dz = dz0 + (float)k;
-                    const float qf = fmaf(dz, fmaf(a22, dz, Lz), C);
-                    acc[k] = fmaf(r, ex2_approx(qf), acc[k]);
+            for (int g8 = 0; g8 < TZ / TZG; ++g8) {
+                if (zhi < g8 * TZG || zlo >= (g8 + 1) * TZG) continue;  // warp-uniform
+#pragma unroll
+                for (int kk = 0; kk < TZG; ++kk) {
+                    const int k = g8 * TZG + kk;
+                    if (k >= zlo && k <= zhi) {
+                        const float dz = dz0 + (float)k;
+                        const float qf = fmaf(dz, fmaf(a22, dz, Lz), C);
+                        acc[k] = fmaf(r, ex2_approx(qf), acc[k]);
+                    }
                 }
             }
         }

@@ -34,11 +34,17 @@ __global__ void __launch_bounds__(256) k_bwd_items(
     if (total > cap) total = cap;
     for (long long it = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
          it < (long long)total; it += warps) {
-        // Gaussian owning item `it`: last gi with item_off[gi] <= it
+        // Gaussian owning item `it`: the last gi with item_off[gi] <= it, by a
+        // 32-ary search (each round every lane probes one pivot)
         int lo = 0, hi = n;  // item_off[lo] <= it < item_off[hi]
         while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if ((unsigned long long)item_off[mid] <= (unsigned long long)it) lo = mid; else hi = mid;
+            const int step = (hi - lo + 31) >> 5;
+            const int probe = lo + lane * step;
+            const bool le = probe < hi && (unsigned long long)item_off[probe] <= (unsigned long long)it;
+            const unsigned m = __ballot_sync(0xffffffffu, le);  // lane 0 always set
+            const int k = 31 - __clz(m);
+            lo += k * step;
+            hi = min(hi, lo + step);
         }
         const int gi = lo;
         const int c = (int)(it - item_off[gi]);
@@ -53,8 +59,13 @@ __global__ void __launch_bounds__(256) k_bwd_items(
         for (int k = 0; k < NMOM; ++k) m[k] = 0.f;
         const int exy = ex * (ye - yb + 1);
         const float dz0 = (float)(zb - P.az) - P.dz;
+        const float inv_ex = 1.0f / (float)ex;
         for (int j = lane; j < exy; j += 32) {
-            const int yy = yb + j / ex, xx = lx + j % ex;
+            // j = row * ex + col, by a float reciprocal and one correction
+            int row = (int)((float)j * inv_ex);
+            row -= row * ex > j;
+            row += (row + 1) * ex <= j;
+            const int yy = yb + row, xx = lx + (j - row * ex);
             const float dx = (float)(xx - P.ax) - P.dx;
             const float dy = (float)(yy - P.ay) - P.dy;
             const float C = fmaf(P.a00 * dx, dx, fmaf(P.a11 * dy, dy, P.a01 * dx * dy));
@@ -62,7 +73,25 @@ __global__ void __launch_bounds__(256) k_bwd_items(
             const float *col = gv + ((size_t)zb * g.ny + yy) * g.nx + xx;
             const size_t zs = (size_t)g.nx * g.ny;
             float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int z = zb; z <= ze; ++z) {
+            int z = zb;
+            // four layers at a time: loads first, then the arithmetic
+            for (; z + 3 <= ze; z += 4) {
+                float gz[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) gz[u] = __ldg(col + u * zs);
+                col += 4 * zs;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float dz = dz0 + (float)(z + u - zb);
+                    const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
+                    const float ge = gz[u] * e;
+                    s0 += ge;
+                    const float t = ge * dz;
+                    s1 += t;
+                    s2 = fmaf(t, dz, s2);
+                }
+            }
+            for (; z <= ze; ++z) {
                 const float dz = dz0 + (float)(z - zb);
                 const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
                 const float ge = __ldg(col) * e;

@@ -27,7 +27,7 @@ DGR_PARALLEL = 0
 DGR_CONE = 1
 
 # voxel tile of the forward voxelizer (x, y, z)
-TILE = (8, 16, 8)
+TILE = (8, 16, 32)
 
 EXPORTS = [
     "dgr_ws_bytes", "dgr_ws_create", "dgr_ws_destroy", "dgr_tile_count", "dgr_status",

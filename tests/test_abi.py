@@ -40,7 +40,7 @@ def test_host_side_validation_without_gpu():
     assert L.dgr_tile_count(ctypes.byref(g), ctypes.byref(t)) == dgr.DGR_ERR_ARG
     g = dgr.Grid(64, 64, 64, 1.0, -32.0, -32.0, -32.0)
     assert L.dgr_tile_count(ctypes.byref(g), ctypes.byref(t)) == dgr.DGR_OK
-    assert t.value == 8 * 4 * 8
+    assert t.value == 8 * 4 * 2
     plan = dgr.WsPlan()
     plan.max_n = 10; plan.max_tiles = 4; plan.max_pairs = 100
     b = ctypes.c_size_t()
