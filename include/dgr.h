@@ -87,7 +87,8 @@ typedef struct {
     long long max_items;
     long long max_vox;       /* dgr_step only: voxels of the volume (0 otherwise) */
     long long max_rays;      /* dgr_step only: rays of the sinogram (0 otherwise) */
-    int max_views, max_nu, max_nv; /* projector tables */
+    int max_views, max_nu, max_nv; /* projector tables (batches: sum of views, max nu, max nv) */
+    int max_inst;            /* instances of dgr_step_batched (0 or 1: single problems) */
 } dgr_ws_plan;
 
 /* Bytes a workspace with this plan needs. */
@@ -95,7 +96,8 @@ int dgr_ws_bytes(const dgr_ws_plan *plan, size_t *bytes);
 /* The only allocating calls: cudaMalloc / cudaFree of the workspace arena. */
 int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan);
 int dgr_ws_destroy(dgr_ws *ws);
-/* Voxel tiles (8 x 16 x 32 voxels) covering a grid. */
+/* Voxel tiles (8 x 16 x depth voxels) covering a grid, for the current tile
+ * depth.  Plans and calls must use the same depth. */
 int dgr_tile_count(const dgr_grid *grid, int *tiles);
 
 /* Reads and clears the device status word (synchronises `stream`). */
@@ -104,6 +106,11 @@ const char *dgr_strerror(int code);
 /* 1 (default): the voxelizer sorts each tile's Gaussian list, so results are
  * bit-reproducible run to run; 0: skip the sort (order follows atomics). */
 int dgr_set_deterministic(int on);
+/* Voxelizer tile depth along z: 8, 16 or 32 (default 32).  Deeper tiles share
+ * each lane's per-Gaussian set-up over more voxels; shallower tiles make more
+ * CTAs for small grids.  A process-wide setting, chosen by the autotuner
+ * (paper_2411_04844_b300/autotune.py); workspace plans depend on it. */
+int dgr_set_tile_depth(int tz);
 
 /* Footprint integers (paper Sec. 4.1 "Gaussian Effect Confinement",
  * "Discretize and Align" Eq. 6; valid mask of Algorithm 1):
@@ -185,6 +192,20 @@ int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t s
  * plan must carry max_vox and max_rays of this problem. */
 int dgr_step(const dgr_problem *prob, const dgr_params *p, const float *measured,
              float *loss_out, dgr_ws *ws, cudaStream_t stream);
+
+/* Many independent reconstructions in one call (SURVEY-style batching; the
+ * paper runs one problem at a time): n_inst <= 16 problems, each with its own
+ * grid, geometry, Gaussian count and optimiser state, advance by one dgr_step
+ * each, every phase being ONE launch over the work of all instances (the
+ * voxelizer's CTAs are persistent and pull tiles of every instance from one
+ * queue).  probs, params, measured: host arrays [n_inst] (measured[i] a device
+ * pointer); loss_out: device [n_inst].  The workspace plan must hold the sums
+ * over instances: max_n, max_tiles, max_pairs, max_items, max_vox, max_rays,
+ * max_views (sum of views), max_nu / max_nv (maxima) and max_inst >= n_inst.
+ * Captured once in a CUDA graph, one replay advances every instance. */
+int dgr_step_batched(int n_inst, const dgr_problem *probs, const dgr_params *params,
+                     const float *const *measured, float *loss_out, dgr_ws *ws,
+                     cudaStream_t stream);
 
 /* dgr_step with CUDA events recorded on `stream` at its phase boundaries:
  * events[0] before voxelize, [1] after voxelize, [2] after project, [3] after

@@ -58,25 +58,11 @@ bool geom_fits_grid(const dgr_grid *g, const dgr_geom *geo) {
     return sqrt(r2) < 0.999 * geo->dso;
 }
 
-int check_ws_grid(dgr_ws *ws, const dgr_grid *g, int n) {
-    if (!ws) return DGR_ERR_ARG;
-    int tx, ty, tz;
-    const int tiles = tile_dims(*g, tx, ty, tz);
-    if (n > ws->plan.max_n || tiles > ws->plan.max_tiles) return DGR_ERR_WS_TOO_SMALL;
-    return DGR_OK;
-}
-
-int check_ws_geom(dgr_ws *ws, const dgr_geom *geo) {
-    if (geo->n_views > ws->plan.max_views || geo->nu > ws->plan.max_nu || geo->nv > ws->plan.max_nv)
-        return DGR_ERR_WS_TOO_SMALL;
-    return DGR_OK;
-}
-
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA; }
 
 struct Layout {
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, total;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, list_tmp, total;
     size_t scan_elems;
 };
 
@@ -84,7 +70,8 @@ bool plan_ok(const dgr_ws_plan *p) {
     return p && p->max_n >= 0 && p->max_tiles >= 0 && p->max_pairs >= 0 && p->max_items >= 0 &&
            p->max_vox >= 0 && p->max_rays >= 0 && p->max_views >= 0 && p->max_nu >= 0 &&
            p->max_nv >= 0 && p->max_pairs < (1ll << 32) && p->max_items < (1ll << 32) &&
-           p->max_n < (1 << 24) && p->max_tiles < (1 << 24);
+           p->max_n < (1 << 24) && p->max_tiles < (1 << 24) && p->max_inst >= 0 &&
+           p->max_inst <= MAX_INST;
 }
 
 Layout layout_of(const dgr_ws_plan &p) {
@@ -106,11 +93,13 @@ Layout layout_of(const dgr_ws_plan &p) {
     L.tile_fill = take(4 * ((size_t)p.max_tiles + 1));
     L.scan_tmp = take(8 * L.scan_elems);
     L.list = take(4 * (size_t)p.max_pairs);
+    L.list_tmp = take(4 * (size_t)p.max_pairs);  // merge scratch of long tile lists
     L.partials = take(4 * (size_t)NMOM * (size_t)p.max_items);
-    L.rayxy = take(ray_table_bytes(p.max_views, p.max_nu, p.max_nv));
+    const int ninst = p.max_inst > 0 ? p.max_inst : 1;
+    L.rayxy = take(ray_table_bytes(p.max_views * p.max_nu, p.max_views, ninst * p.max_nv));
     // residual x |D| for the backprojector (standalone calls; the step reuses its sinogram)
     L.sino_scaled = take(4 * (size_t)p.max_views * p.max_nu * p.max_nv);
-    L.loss_part = take(4 * (size_t)(L1_BLOCKS + 1));
+    L.loss_part = take(4 * (size_t)(L1_BLOCKS * ninst + 1));
     L.grads = take(4 * 11 * (size_t)p.max_n);
     L.vol = take(4 * (size_t)p.max_vox);
     L.sino = take(4 * (size_t)p.max_rays);
@@ -146,6 +135,7 @@ int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan) {
     w->scan_tmp = L.scan_tmp; w->list = L.list; w->partials = L.partials; w->grads = L.grads;
     w->vol = L.vol; w->sino = L.sino; w->loss_part = L.loss_part; w->rayxy = L.rayxy;
     w->sino_scaled = L.sino_scaled;
+    w->list_tmp = L.list_tmp;
     w->scan_tmp_elems = L.scan_elems;
     if (cudaMemset(w->base + L.status, 0, 256) != cudaSuccess) {
         cudaFree(w->base);
@@ -199,6 +189,12 @@ int dgr_set_deterministic(int on) {
     return DGR_OK;
 }
 
+int dgr_set_tile_depth(int tz) {
+    if (tz != 8 && tz != 16 && tz != 32) return DGR_ERR_ARG;
+    set_tile_depth(tz);
+    return DGR_OK;
+}
+
 int dgr_footprint(const dgr_grid *grid, int n, const float *mu, const float *s, const float *q,
                   float k_trunc, int *anchor, int *box, cudaStream_t stream) {
     if (!grid_ok(grid) || n < 0 || !k_ok(k_trunc)) return DGR_ERR_ARG;
@@ -209,30 +205,123 @@ int dgr_footprint(const dgr_grid *grid, int n, const float *mu, const float *s, 
 static int gauss_args_ok(const dgr_grid *grid, int n, const float *mu, const float *s,
                          const float *q, const float *rho, float k) {
     if (!grid_ok(grid) || n < 0 || !k_ok(k)) return 0;
+    if ((long long)grid->nx * grid->ny * grid->nz >= (1ll << 31)) return 0;
     if (n > 0 && (!mu || !s || !q || !rho || !aligned16(q))) return 0;
     return 1;
 }
+
+// ---------------------------------------------------------------------------
+// batch descriptors
+// ---------------------------------------------------------------------------
+namespace {
+
+void set_grid(Inst &I, const dgr_grid &g, float k) {
+    I.g = g;
+    I.k = k;
+    I.zoff = -g.oz / g.h;
+    tile_dims(g, I.ntx, I.nty, I.ntz);
+}
+
+void set_geom(Inst &I, const dgr_geom &geo) {
+    I.beam = geo.beam;
+    I.n_views = geo.n_views;
+    I.nu = geo.nu;
+    I.nv = geo.nv;
+    I.pu = geo.pu;
+    I.pv = geo.pv;
+    I.dso = geo.dso;
+    I.dsd = geo.dsd;
+    I.angles = geo.angles;
+    bp_blocks(I.g, I.nbx, I.nbz);
+}
+
+// offsets of each instance in the global index spaces
+void finish(Batch &B, bool has_geom) {
+    int g = 0, tiles = 0, tab = 0, views = 0, rows = 0, blk = 0;
+    long long rays = 0;
+    for (int i = 0; i < B.n; ++i) {
+        Inst &I = B.in[i];
+        I.g0 = g;
+        g += I.n;
+        I.tile0 = tiles;
+        tiles += I.ntx * I.nty * I.ntz;
+        if (has_geom) {
+            I.tab0 = tab;
+            tab += I.n_views * I.nu;
+            I.view0 = views;
+            views += I.n_views;
+            I.row0 = rows;
+            rows += I.nv;
+            I.ray0 = rays;
+            rays += (long long)I.n_views * I.nu * I.nv;
+            I.blk0 = blk;
+            blk += I.nbx * I.g.ny * I.nbz;
+        }
+    }
+    B.tot_g = g;
+    B.tot_tiles = tiles;
+    B.tot_tab = tab;
+    B.tot_views = views;
+    B.tot_rows = rows;
+    B.tot_rays = rays;
+    B.tot_blk = blk;
+}
+
+Batch *new_batch() {
+    static thread_local Batch B;
+    memset(&B, 0, sizeof(B));
+    B.tz = tile_depth();
+    return &B;
+}
+
+int check_batch_ws(dgr_ws *ws, const Batch &B, bool geom, bool step) {
+    if (!ws) return DGR_ERR_ARG;
+    const dgr_ws_plan &p = ws->plan;
+    if (B.tot_g > p.max_n || B.tot_tiles > p.max_tiles) return DGR_ERR_WS_TOO_SMALL;
+    if (B.n > (p.max_inst > 0 ? p.max_inst : 1)) return DGR_ERR_WS_TOO_SMALL;
+    if (geom) {
+        long long tab_cap = (long long)p.max_views * p.max_nu;
+        long long rows_cap = (long long)(p.max_inst > 0 ? p.max_inst : 1) * p.max_nv;
+        if (B.tot_tab > tab_cap || B.tot_views > p.max_views || B.tot_rows > rows_cap ||
+            B.tot_rays > (long long)p.max_views * p.max_nu * p.max_nv)
+            return DGR_ERR_WS_TOO_SMALL;
+    }
+    if (step) {
+        long long vox = 0;
+        for (int i = 0; i < B.n; ++i) vox += (long long)B.in[i].g.nx * B.in[i].g.ny * B.in[i].g.nz;
+        if (vox > p.max_vox || B.tot_rays > p.max_rays) return DGR_ERR_WS_TOO_SMALL;
+    }
+    return DGR_OK;
+}
+
+}  // namespace
 
 int dgr_voxelize_count(const dgr_grid *grid, int n, const float *mu, const float *s,
                        const float *q, float k_trunc, long long *pairs, long long *items,
                        dgr_ws *ws, cudaStream_t stream) {
     if (!gauss_args_ok(grid, n, mu, s, q, mu, k_trunc) || !pairs || !items) return DGR_ERR_ARG;
-    int rc = check_ws_grid(ws, grid, n);
+    Batch &B = *new_batch();
+    B.n = 1;
+    Inst &I = B.in[0];
+    set_grid(I, *grid, k_trunc);
+    I.n = n;
+    // rho is not needed for the integers; mu stands in as a valid pointer
+    I.mu = mu; I.s = s; I.q = q; I.rho = mu;
+    finish(B, false);
+    int rc = check_batch_ws(ws, B, false, false);
     if (rc) return rc;
     Prep *prep = ws_ptr<Prep>(ws, ws->prep);
     uint32_t *itemcnt = ws_ptr<uint32_t>(ws, ws->itemcnt);
     int *status = ws_ptr<int>(ws, ws->status);
-    // rho is not needed for the integers; mu stands in as a valid pointer
-    cudaError_t e = launch_prep(*grid, n, mu, s, q, mu, k_trunc, prep, itemcnt, status, stream);
-    if (e == cudaSuccess) e = launch_count_pairs(*grid, n, prep, ws, ~0ull, stream);
+    cudaError_t e = launch_prep(B, prep, itemcnt, status, stream);
+    if (e == cudaSuccess) e = launch_count_pairs(B, prep, ws, ~0ull, stream);
     if (e == cudaSuccess && n > 0)
         e = scan_u32(itemcnt, ws_ptr<uint32_t>(ws, ws->item_off), n, ~0ull, status, 0,
                      ws_ptr<unsigned long long>(ws, ws->scan_tmp), stream);
-    int tx, ty, tz;
-    const int tiles = tile_dims(*grid, tx, ty, tz);
     uint32_t tp = 0, ti = 0;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&tp, ws_ptr<uint32_t>(ws, ws->tile_off) + tiles, 4, cudaMemcpyDeviceToHost, stream);
+        e = cudaMemcpyAsync(&tp, ws_ptr<uint32_t>(ws, ws->tile_off) + B.tot_tiles, 4,
+                            cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess && n > 0)
         e = cudaMemcpyAsync(&ti, ws_ptr<uint32_t>(ws, ws->item_off) + n, 4, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -244,12 +333,17 @@ int dgr_voxelize_count(const dgr_grid *grid, int n, const float *mu, const float
 int dgr_voxelize(const dgr_grid *grid, int n, const float *mu, const float *s, const float *q,
                  const float *rho, float k_trunc, float *vol, dgr_ws *ws, cudaStream_t stream) {
     if (!gauss_args_ok(grid, n, mu, s, q, rho, k_trunc) || !vol) return DGR_ERR_ARG;
-    int rc = check_ws_grid(ws, grid, n);
+    Batch &B = *new_batch();
+    B.n = 1;
+    Inst &I = B.in[0];
+    set_grid(I, *grid, k_trunc);
+    I.n = n; I.mu = mu; I.s = s; I.q = q; I.rho = rho; I.vol = vol;
+    finish(B, false);
+    int rc = check_batch_ws(ws, B, false, false);
     if (rc) return rc;
     Prep *prep = ws_ptr<Prep>(ws, ws->prep);
-    cudaError_t e = launch_prep(*grid, n, mu, s, q, rho, k_trunc, prep,
-                                ws_ptr<uint32_t>(ws, ws->itemcnt), ws_ptr<int>(ws, ws->status), stream);
-    if (e == cudaSuccess) e = launch_voxelize(*grid, n, prep, ws, vol, g_deterministic, stream);
+    cudaError_t e = launch_prep(B, prep, ws_ptr<uint32_t>(ws, ws->itemcnt), ws_ptr<int>(ws, ws->status), stream);
+    if (e == cudaSuccess) e = launch_voxelize(B, prep, ws, g_deterministic, stream);
     return cuda_rc(e);
 }
 
@@ -259,53 +353,75 @@ int dgr_voxelize_backward(const dgr_grid *grid, int n, const float *mu, const fl
                           cudaStream_t stream) {
     if (!gauss_args_ok(grid, n, mu, s, q, rho, k_trunc) || !grad_vol) return DGR_ERR_ARG;
     if (n > 0 && (!g_mu || !g_s || !g_q || !g_rho)) return DGR_ERR_ARG;
-    int rc = check_ws_grid(ws, grid, n);
+    Batch &B = *new_batch();
+    B.n = 1;
+    Inst &I = B.in[0];
+    set_grid(I, *grid, k_trunc);
+    I.n = n; I.mu = mu; I.s = s; I.q = q; I.rho = rho;
+    I.vol = const_cast<float *>(grad_vol);
+    I.g_mu = g_mu; I.g_s = g_s; I.g_q = g_q; I.g_rho = g_rho;
+    finish(B, false);
+    int rc = check_batch_ws(ws, B, false, false);
     if (rc) return rc;
     Prep *prep = ws_ptr<Prep>(ws, ws->prep);
-    cudaError_t e = launch_prep(*grid, n, mu, s, q, rho, k_trunc, prep,
-                                ws_ptr<uint32_t>(ws, ws->itemcnt), ws_ptr<int>(ws, ws->status), stream);
-    if (e == cudaSuccess)
-        e = launch_voxelize_backward(*grid, n, mu, s, q, rho, prep, grad_vol, g_mu, g_s, g_q, g_rho,
-                                     ws, stream);
+    cudaError_t e = launch_prep(B, prep, ws_ptr<uint32_t>(ws, ws->itemcnt), ws_ptr<int>(ws, ws->status), stream);
+    if (e == cudaSuccess) e = launch_voxelize_backward(B, prep, ws, stream);
     return cuda_rc(e);
+}
+
+static int proj_batch(const dgr_grid *grid, const dgr_geom *geom, const float *vol, const float *sino,
+                      dgr_ws *ws, Batch *&Bout) {
+    if (!grid_ok(grid) || !geom_ok(geom) || !vol || !sino || !ws) return DGR_ERR_ARG;
+    if (!geom_fits_grid(grid, geom)) return DGR_ERR_ARG;
+    if ((long long)grid->nx * grid->ny * grid->nz >= (1ll << 31)) return DGR_ERR_ARG;
+    Batch &B = *new_batch();
+    B.n = 1;
+    Inst &I = B.in[0];
+    set_grid(I, *grid, 3.0f);
+    set_geom(I, *geom);
+    I.vol = const_cast<float *>(vol);
+    I.sino = const_cast<float *>(sino);
+    finish(B, true);
+    int rc = check_batch_ws(ws, B, true, false);
+    if (rc) return rc;
+    Bout = &B;
+    return DGR_OK;
 }
 
 int dgr_project(const dgr_grid *grid, const dgr_geom *geom, const float *vol, float *sino,
                 dgr_ws *ws, cudaStream_t stream) {
-    if (!grid_ok(grid) || !geom_ok(geom) || !vol || !sino || !ws) return DGR_ERR_ARG;
-    if (!geom_fits_grid(grid, geom)) return DGR_ERR_ARG;
-    int rc = check_ws_geom(ws, geom);
+    Batch *B = nullptr;
+    int rc = proj_batch(grid, geom, vol, sino, ws, B);
     if (rc) return rc;
     RayXY *tab = ws_ptr<RayXY>(ws, ws->rayxy);
-    cudaError_t e = launch_ray_tables(*grid, *geom, tab, stream);
-    if (e == cudaSuccess) e = launch_project(*grid, *geom, tab, vol, sino, stream);
+    cudaError_t e = launch_ray_tables(*B, tab, stream);
+    if (e == cudaSuccess) e = launch_project(*B, tab, stream);
     return cuda_rc(e);
 }
 
 int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sino, float *vol,
                     dgr_ws *ws, cudaStream_t stream) {
-    if (!grid_ok(grid) || !geom_ok(geom) || !vol || !sino || !ws) return DGR_ERR_ARG;
-    if (!geom_fits_grid(grid, geom)) return DGR_ERR_ARG;
-    int rc = check_ws_geom(ws, geom);
+    Batch *B = nullptr;
+    int rc = proj_batch(grid, geom, vol, sino, ws, B);
     if (rc) return rc;
     RayXY *tab = ws_ptr<RayXY>(ws, ws->rayxy);
-    cudaError_t e = launch_ray_tables(*grid, *geom, tab, stream);
-    if (e == cudaSuccess)
-        e = launch_backproject(*grid, *geom, tab, sino, ws_ptr<float>(ws, ws->sino_scaled), vol, stream);
+    cudaError_t e = launch_ray_tables(*B, tab, stream);
+    if (e == cudaSuccess) e = launch_backproject(*B, tab, ws_ptr<float>(ws, ws->sino_scaled), stream);
     return cuda_rc(e);
 }
 
 int dgr_l1_residual(const float *pred, const float *meas, long long m, float *resid, float *loss,
                     dgr_ws *ws, cudaStream_t stream) {
     if (!pred || !meas || !resid || !loss || !ws || m <= 0) return DGR_ERR_ARG;
-    return cuda_rc(launch_l1(pred, meas, m, resid, loss, ws_ptr<float>(ws, ws->loss_part), stream));
+    return cuda_rc(launch_l1_single(pred, meas, m, resid, loss, ws_ptr<float>(ws, ws->loss_part), stream));
 }
 
 static int problem_ok(const dgr_problem *P) {
     return P && grid_ok(&P->grid) && geom_ok(&P->geom) && k_ok(P->k_trunc) &&
            geom_fits_grid(&P->grid, &P->geom) && isfinite(P->lr0) && isfinite(P->lr1) &&
            P->lr0 > 0.f && P->lr1 > 0.f && P->n_iters >= 1 && P->beta1 >= 0.f && P->beta1 < 1.f &&
-           P->beta2 >= 0.f && P->beta2 < 1.f && P->eps > 0.f;
+           P->beta2 >= 0.f && P->beta2 < 1.f && P->eps > 0.f &&
+           (long long)P->grid.nx * P->grid.ny * P->grid.nz < (1ll << 31);
 }
 
 static int params_ok(const dgr_params *p) {
@@ -320,61 +436,86 @@ int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t s
     return cuda_rc(launch_params_init(*prob, *p, stream));
 }
 
-static int step_impl(const dgr_problem *prob, const dgr_params *p, const float *measured,
-                     float *loss_out, dgr_ws *ws, cudaStream_t stream, cudaEvent_t *ev) {
-    if (!problem_ok(prob) || !params_ok(p) || !measured || !loss_out || !ws) return DGR_ERR_ARG;
-    const dgr_grid &g = prob->grid;
-    const dgr_geom &geo = prob->geom;
-    int rc = check_ws_grid(ws, &g, p->n);
+// voxelize -> project -> L1 -> backproject -> voxelize adjoint -> Adam, for a
+// batch of problems, one launch per phase
+static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *params,
+                      const float *const *measured, float *loss_out, dgr_ws *ws,
+                      cudaStream_t stream, cudaEvent_t *ev) {
+    if (n_inst < 1 || n_inst > MAX_INST || !probs || !params || !measured || !loss_out || !ws)
+        return DGR_ERR_ARG;
+    Batch &B = *new_batch();
+    B.n = n_inst;
+    for (int i = 0; i < n_inst; ++i) {
+        const dgr_problem *P = probs + i;
+        const dgr_params *p = params + i;
+        if (!problem_ok(P) || !params_ok(p) || !measured[i]) return DGR_ERR_ARG;
+        Inst &I = B.in[i];
+        set_grid(I, P->grid, P->k_trunc);
+        set_geom(I, P->geom);
+        I.n = p->n;
+        I.mu = p->mu; I.s = p->s; I.q = p->q; I.rho = p->rho;
+        I.mu_w = p->mu; I.s_w = p->s; I.q_w = p->q; I.rho_w = p->rho;
+        I.theta = p->theta; I.m = p->m; I.v = p->v; I.step = p->step;
+        I.meas = measured[i];
+        I.loss = loss_out + i;
+        I.lr0 = P->lr0; I.lr1 = P->lr1; I.b1 = P->beta1; I.b2 = P->beta2; I.eps = P->eps;
+        I.n_iters = P->n_iters;
+    }
+    finish(B, true);
+    int rc = check_batch_ws(ws, B, true, true);
     if (rc) return rc;
-    rc = check_ws_geom(ws, &geo);
-    if (rc) return rc;
-    const long long nvox = (long long)g.nx * g.ny * g.nz;
-    const long long nrays = (long long)geo.n_views * geo.nv * geo.nu;
-    if (nvox > ws->plan.max_vox || nrays > ws->plan.max_rays) return DGR_ERR_WS_TOO_SMALL;
-    const int n = p->n;
-    float *vol = ws_ptr<float>(ws, ws->vol);     // volume, then its gradient (same buffer)
-    float *sino = ws_ptr<float>(ws, ws->sino);   // prediction, then residual (in place)
+    // per-instance buffers in the workspace: volume (then its gradient),
+    // sinogram (prediction, then residual), gradients [mu 3n | s 3n | q 4n | rho n]
+    float *vol = ws_ptr<float>(ws, ws->vol);
+    float *sino = ws_ptr<float>(ws, ws->sino);
     float *grads = ws_ptr<float>(ws, ws->grads);
+    long long vo = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        Inst &I = B.in[i];
+        I.vol = vol + vo;
+        vo += (long long)I.g.nx * I.g.ny * I.g.nz;
+        I.sino = sino + I.ray0;
+        float *gr = grads + 11ll * I.g0;
+        I.g_mu = gr; I.g_s = gr + 3 * I.n; I.g_q = gr + 6 * I.n; I.g_rho = gr + 10 * I.n;
+    }
     Prep *prep = ws_ptr<Prep>(ws, ws->prep);
     RayXY *tab = ws_ptr<RayXY>(ws, ws->rayxy);
     int *status = ws_ptr<int>(ws, ws->status);
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], stream) : cudaSuccess; };
     cudaError_t e = mark(0);
-    if (e == cudaSuccess)
-        e = launch_prep(g, n, p->mu, p->s, p->q, p->rho, prob->k_trunc, prep,
-                        ws_ptr<uint32_t>(ws, ws->itemcnt), status, stream);
-    if (e == cudaSuccess) e = launch_voxelize(g, n, prep, ws, vol, g_deterministic, stream);
+    if (e == cudaSuccess) e = launch_prep(B, prep, ws_ptr<uint32_t>(ws, ws->itemcnt), status, stream);
+    if (e == cudaSuccess) e = launch_voxelize(B, prep, ws, g_deterministic, stream);
     if (e == cudaSuccess) e = mark(1);
-    if (e == cudaSuccess) e = launch_ray_tables(g, geo, tab, stream);
-    if (e == cudaSuccess) e = launch_project(g, geo, tab, vol, sino, stream);
+    if (e == cudaSuccess) e = launch_ray_tables(B, tab, stream);
+    if (e == cudaSuccess) e = launch_project(B, tab, stream);
     if (e == cudaSuccess) e = mark(2);
-    if (e == cudaSuccess)
-        e = launch_l1(sino, measured, nrays, sino, loss_out, ws_ptr<float>(ws, ws->loss_part), stream);
+    if (e == cudaSuccess) e = launch_l1(B, ws_ptr<float>(ws, ws->loss_part), stream);
     if (e == cudaSuccess) e = mark(3);
-    if (e == cudaSuccess)
-        e = launch_backproject(g, geo, tab, sino, ws_ptr<float>(ws, ws->sino_scaled), vol, stream);
+    if (e == cudaSuccess) e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), stream);
     if (e == cudaSuccess) e = mark(4);
-    if (e == cudaSuccess)
-        e = launch_voxelize_backward(g, n, p->mu, p->s, p->q, p->rho, prep, vol, grads,
-                                     grads + 3 * (size_t)n, grads + 6 * (size_t)n,
-                                     grads + 10 * (size_t)n, ws, stream);
+    if (e == cudaSuccess) e = launch_voxelize_backward(B, prep, ws, stream);
     if (e == cudaSuccess) e = mark(5);
-    if (e == cudaSuccess) e = launch_adam(*prob, *p, grads, stream);
+    if (e == cudaSuccess) e = launch_adam(B, stream);
     if (e == cudaSuccess) e = mark(6);
     return cuda_rc(e);
 }
 
 int dgr_step(const dgr_problem *prob, const dgr_params *p, const float *measured,
              float *loss_out, dgr_ws *ws, cudaStream_t stream) {
-    return step_impl(prob, p, measured, loss_out, ws, stream, nullptr);
+    return step_batch(1, prob, p, &measured, loss_out, ws, stream, nullptr);
 }
 
 int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *measured,
                    float *loss_out, dgr_ws *ws, cudaStream_t stream, cudaEvent_t *events,
                    int n_events) {
     if (!events || n_events < DGR_STEP_EVENTS) return DGR_ERR_ARG;
-    return step_impl(prob, p, measured, loss_out, ws, stream, events);
+    return step_batch(1, prob, p, &measured, loss_out, ws, stream, events);
+}
+
+int dgr_step_batched(int n_inst, const dgr_problem *probs, const dgr_params *params,
+                     const float *const *measured, float *loss_out, dgr_ws *ws,
+                     cudaStream_t stream) {
+    return step_batch(n_inst, probs, params, measured, loss_out, ws, stream, nullptr);
 }
 
 long long dgr_launch_count(void) { return g_launches.load(); }

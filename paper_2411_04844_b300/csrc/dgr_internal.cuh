@@ -13,8 +13,11 @@ namespace dgr {
 // warps owns one tile; a warp owns an 8 x 4 patch in (x, y) and every lane
 // keeps the 32 z-voxels of its (x, y) column in registers, so the per-Gaussian
 // set-up of a lane is shared by up to 32 exponentials.
-constexpr int TX = 8, TY = 16, TZ = 32;
-constexpr int TZG = 8;  // z handled in groups of 8 (a group outside the box is skipped)
+constexpr int TX = 8, TY = 16;
+constexpr int TZ_MAX = 32;  // tile depth: 8, 16 or 32 (dgr_set_tile_depth; the autotuner's knob)
+constexpr int TZG = 8;      // z handled in groups of 8 (a group outside the box is skipped)
+int tile_depth();           // current tile depth
+void set_tile_depth(int tz);
 constexpr int VOX_THREADS = 128;
 constexpr int VOX_CHUNK = 64;  // prep records staged in shared memory at a time
 
@@ -83,6 +86,85 @@ struct __align__(16) RayXY {
     float inv_ex, inv_ey, tc, dxy2;  // 1/e (0 when e == 0), t-shift for z, |D_xy|^2
 };
 
+// Per detector row: zv = v / h (FP32), its reciprocal (0 when zv == 0), the
+// FP64-snapped z layer used when the ray runs parallel to the z planes, and v.
+struct __align__(16) RowZ {
+    float zv, izv, zsnap, v;
+};
+
+// ---------------------------------------------------------------------------
+// Batches: every kernel works on a batch of independent problems described by
+// a struct passed by value (kernel parameter space, so a captured CUDA graph
+// keeps it).  Global index spaces (Gaussians, tiles, rays, backprojector
+// blocks, backward items) run over all instances back to back; a single call
+// of the C ABI is a batch of one.
+// ---------------------------------------------------------------------------
+constexpr int MAX_INST = 16;
+
+struct Inst {
+    dgr_grid g;
+    int beam, n_views, nu, nv;
+    float pu, pv, dso, dsd;
+    const float *angles;
+    float k, zoff;  // truncation factor; -oz / h
+    // Gaussians of this instance (device arrays, local index)
+    const float *mu, *s, *q, *rho;
+    float *g_mu, *g_s, *g_q, *g_rho;  // adjoint outputs
+    int g0, n;                        // first global Gaussian, count
+    int tile0, ntx, nty, ntz;         // first global tile, tiles per axis
+    long long ray0;                   // first global ray
+    int tab0, view0, row0;            // first RayXY entry, view, RowZ entry
+    int blk0, nbx, nbz;               // first backprojector block, blocks in x, z passes
+    float *vol;                       // volume (voxelize output; step: volume, then its gradient)
+    float *sino;                      // projection (step: prediction, then residual)
+    const float *meas;                // measured projections (step)
+    float *loss;                      // loss scalar (step)
+    // optimiser state and constants (step)
+    float *theta, *m, *v;
+    int *step;
+    float *mu_w, *s_w, *q_w, *rho_w;  // parameters rewritten by Adam
+    float lr0, lr1, b1, b2, eps;
+    int n_iters;
+};
+
+struct Batch {
+    int n;             // instances
+    int tz;            // voxelizer tile depth
+    int tot_g;         // Gaussians of all instances
+    int tot_tiles;
+    int tot_tab, tot_rows, tot_views;
+    int tot_blk;
+    long long tot_rays;
+    Inst in[MAX_INST];
+};
+
+// instance owning a global index (linear scan of at most MAX_INST entries)
+__device__ __forceinline__ int inst_of_g(const Batch &B, int g) {
+    int i = 0;
+    while (i + 1 < B.n && B.in[i + 1].g0 <= g) ++i;
+    return i;
+}
+__device__ __forceinline__ int inst_of_tile(const Batch &B, int t) {
+    int i = 0;
+    while (i + 1 < B.n && B.in[i + 1].tile0 <= t) ++i;
+    return i;
+}
+__device__ __forceinline__ int inst_of_ray(const Batch &B, long long r) {
+    int i = 0;
+    while (i + 1 < B.n && B.in[i + 1].ray0 <= r) ++i;
+    return i;
+}
+__device__ __forceinline__ int inst_of_view(const Batch &B, int v) {
+    int i = 0;
+    while (i + 1 < B.n && B.in[i + 1].view0 <= v) ++i;
+    return i;
+}
+__device__ __forceinline__ int inst_of_blk(const Batch &B, int b) {
+    int i = 0;
+    while (i + 1 < B.n && B.in[i + 1].blk0 <= b) ++i;
+    return i;
+}
+
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 // host-side count of kernel launches issued by the library
@@ -98,7 +180,7 @@ struct dgr_ws {
     dgr_ws_plan plan;
     // byte offsets into base
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy, sino_scaled;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, losses, list_tmp;
     size_t scan_tmp_elems;
 };
 
@@ -116,36 +198,35 @@ size_t scan_tmp_elems(int len);
 
 // voxelize.cu
 int tile_dims(const dgr_grid &g, int &ntx, int &nty, int &ntz);
-cudaError_t launch_prep(const dgr_grid &g, int n, const float *mu, const float *s, const float *q,
-                        const float *rho, float k, Prep *prep, uint32_t *itemcnt, int *status,
-                        cudaStream_t st);
-cudaError_t launch_voxelize(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws, float *vol,
-                            int deterministic, cudaStream_t st);
+cudaError_t launch_prep(const Batch &B, Prep *prep, uint32_t *itemcnt, int *status, cudaStream_t st);
+cudaError_t launch_count_pairs(const Batch &B, const Prep *prep, dgr_ws *ws, unsigned long long cap,
+                               cudaStream_t st);
+cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int deterministic,
+                            cudaStream_t st);
 cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const float *s,
                              const float *q, float k, int *anchor, int *box, cudaStream_t st);
-cudaError_t launch_count_pairs(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws,
-                               unsigned long long cap, cudaStream_t st);
 
-// voxelize_bwd.cu
-cudaError_t launch_voxelize_backward(const dgr_grid &g, int n, const float *mu, const float *s,
-                                     const float *q, const float *rho, const Prep *prep,
-                                     const float *grad_vol, float *g_mu, float *g_s, float *g_q,
-                                     float *g_rho, dgr_ws *ws, cudaStream_t st);
+// voxelize_bwd.cu (grad_vol = Inst::vol; outputs Inst::g_*)
+cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st);
 
 // project.cu
-cudaError_t launch_ray_tables(const dgr_grid &g, const dgr_geom &geo, RayXY *tab, cudaStream_t st);
-cudaError_t launch_project(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
-                           const float *vol, float *sino, cudaStream_t st);
-// sino_scaled: scratch of n_rays floats (residual x |D|, [view][u][v]); must not alias sino
-cudaError_t launch_backproject(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
-                               const float *sino, float *sino_scaled, float *vol, cudaStream_t st);
-size_t ray_table_bytes(int n_views, int nu, int nv);
+size_t ray_table_bytes(int n_tab, int n_views, int n_rows);
+cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st);
+cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st);
+// sino_scaled: scratch of all instances' rays (residual x |D|, [view][u][v]); not aliasing sino
+cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, cudaStream_t st);
+// the projector of one instance with caller-provided tables (no workspace)
+cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY *tab,
+                                  const float *vol, float *sino, cudaStream_t st);
+size_t ray_table_bytes_single(const dgr_geom &geo);
+// backprojector CTAs covering a grid (x blocks of 8 columns x ny x z passes)
+int bp_blocks(const dgr_grid &g, int &nbx, int &nbz);
 
 // step.cu
-cudaError_t launch_l1(const float *pred, const float *meas, long long m, float *resid, float *loss,
-                      float *part, cudaStream_t st);
+constexpr int L1_BLOCKS = 148;  // per instance; fixed so the loss reduction order is fixed
+cudaError_t launch_l1(const Batch &B, float *part, cudaStream_t st);
+cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float *resid,
+                             float *loss, float *part, cudaStream_t st);
 cudaError_t launch_params_init(const dgr_problem &P, const dgr_params &p, cudaStream_t st);
-cudaError_t launch_adam(const dgr_problem &P, const dgr_params &p, const float *grads,
-                        cudaStream_t st);
-constexpr int L1_BLOCKS = 592;  // 4 x 148 SMs; fixed so the loss reduction order is fixed
+cudaError_t launch_adam(const Batch &B, cudaStream_t st);
 }  // namespace dgr

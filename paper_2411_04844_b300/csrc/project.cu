@@ -22,6 +22,7 @@
 //                 column's slab interval; each candidate costs one slab test
 //                 and one load -- no divisions, no atomics
 #include <math.h>
+#include <string.h>
 
 #include "dgr_internal.cuh"
 
@@ -30,11 +31,20 @@ namespace {
 
 constexpr float CAND_EPS = 1e-3f;  // pixel margin of the candidate-ray search
 
-// Per detector row: zv = v / h (FP32), its reciprocal (0 when zv == 0), the
-// FP64-snapped z layer used when the ray runs parallel to the z planes, and v.
-struct __align__(16) RowZ {
-    float zv, izv, zsnap, v;
+// table layout: RayXY [tot_tab] | float2 cos/sin [tot_views] (padded to 16 B) | RowZ [tot_rows]
+struct Tables {
+    RayXY *tab;
+    float2 *view_cs;
+    RowZ *rows;
 };
+__host__ __device__ inline Tables tables_of(RayXY *tab, int n_tab, int n_views) {
+    Tables T;
+    T.tab = tab;
+    T.view_cs = reinterpret_cast<float2 *>(tab + n_tab);
+    const size_t cs_bytes = ((sizeof(float2) * (size_t)n_views + 15) / 16) * 16;
+    T.rows = reinterpret_cast<RowZ *>(reinterpret_cast<char *>(T.view_cs) + cs_bytes);
+    return T;
+}
 
 // For an axis the ray runs parallel to, only floor(xi) matters (which voxel
 // layer holds the ray).  That decision is taken in FP64 and stored as the
@@ -42,34 +52,46 @@ struct __align__(16) RowZ {
 // the same way as by an FP64 evaluation of floor((X - o) / h).
 __device__ __forceinline__ float snap_layer(double xi) { return (float)(floor(xi) + 0.5); }
 
-__global__ void k_ray_tables(dgr_grid g, dgr_geom geo, RayXY *__restrict__ tab,
-                             float2 *__restrict__ view_cs, RowZ *__restrict__ rows) {
+// one thread per global RayXY entry, then per global RowZ entry
+__global__ void k_ray_tables(const __grid_constant__ Batch B, RayXY *__restrict__ tab) {
+    const Tables T = tables_of(tab, B.tot_tab, B.tot_views);
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < geo.nv) {
-        const float v = ((float)idx - 0.5f * (float)(geo.nv - 1)) * geo.pv;
+    if (idx >= B.tot_tab) {
+        const int ri = idx - B.tot_tab;
+        if (ri >= B.tot_rows) return;
+        int i = 0;
+        while (i + 1 < B.n && B.in[i + 1].row0 <= ri) ++i;
+        const Inst &I = B.in[i];
+        const int iv = ri - I.row0;
+        const float v = ((float)iv - 0.5f * (float)(I.nv - 1)) * I.pv;
         RowZ R;
         R.v = v;
-        R.zv = geo.beam == DGR_CONE ? v / g.h : 0.f;
+        R.zv = I.beam == DGR_CONE ? v / I.g.h : 0.f;
         R.izv = R.zv != 0.f ? 1.0f / R.zv : 0.f;
         // z layer of the rays of this row when they run parallel to the z
         // planes (parallel beam, or the cone's v = 0 row)
-        const double v64 = ((double)idx - 0.5 * (double)(geo.nv - 1)) * (double)geo.pv;
-        const double X0z = geo.beam == DGR_CONE ? 0.0 : v64;
-        R.zsnap = snap_layer((X0z - (double)g.oz) / (double)g.h);
-        rows[idx] = R;
+        const double v64 = ((double)iv - 0.5 * (double)(I.nv - 1)) * (double)I.pv;
+        const double X0z = I.beam == DGR_CONE ? 0.0 : v64;
+        R.zsnap = snap_layer((X0z - (double)I.g.oz) / (double)I.g.h);
+        T.rows[ri] = R;
+        return;
     }
-    if (idx >= geo.n_views * geo.nu) return;
-    const int k = idx / geo.nu, iu = idx % geo.nu;
-    const double a = (double)geo.angles[k];
+    int i = 0;
+    while (i + 1 < B.n && B.in[i + 1].tab0 <= idx) ++i;
+    const Inst &I = B.in[i];
+    const dgr_grid &g = I.g;
+    const int loc = idx - I.tab0;
+    const int k = loc / I.nu, iu = loc % I.nu;
+    const double a = (double)I.angles[k];
     const double c = cos(a), s = sin(a);
-    if (iu == 0) view_cs[k] = make_float2((float)c, (float)s);
-    const double u = ((double)iu - 0.5 * (double)(geo.nu - 1)) * (double)geo.pu;
+    if (iu == 0) T.view_cs[I.view0 + k] = make_float2((float)c, (float)s);
+    const double u = ((double)iu - 0.5 * (double)(I.nu - 1)) * (double)I.pu;
     const double h = (double)g.h;
     const double gcx = (double)g.ox + 0.5 * g.nx * h, gcy = (double)g.oy + 0.5 * g.ny * h;
     double Sx, Sy, Dx, Dy;
-    if (geo.beam == DGR_CONE) {
-        Sx = -(double)geo.dso * c; Sy = -(double)geo.dso * s;
-        Dx = (double)geo.dsd * c - u * s; Dy = (double)geo.dsd * s + u * c;
+    if (I.beam == DGR_CONE) {
+        Sx = -(double)I.dso * c; Sy = -(double)I.dso * s;
+        Dx = (double)I.dsd * c - u * s; Dy = (double)I.dsd * s + u * c;
     } else {
         Sx = -u * s; Sy = u * c;
         Dx = c; Dy = s;
@@ -86,7 +108,7 @@ __global__ void k_ray_tables(dgr_grid g, dgr_geom geo, RayXY *__restrict__ tab,
     r.inv_ey = r.ey != 0.f ? (float)(h / Dy) : 0.f;
     r.tc = (float)tc;
     r.dxy2 = (float)d2;
-    tab[idx] = r;
+    T.tab[idx] = r;
 }
 
 struct RayZ {
@@ -118,20 +140,23 @@ __device__ __forceinline__ float plane_t(int p, float xi0, float inv) {
     return ((float)p - xi0) * inv;
 }
 
-__global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo, float zoff,
-                                                 const RayXY *__restrict__ tab,
-                                                 const RowZ *__restrict__ rows,
-                                                 const float *__restrict__ vol,
-                                                 float *__restrict__ sino) {
-    const long long nrays = (long long)geo.n_views * geo.nv * geo.nu;
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrays) return;
-    const int iu = (int)(r % geo.nu);
-    const int iv = (int)((r / geo.nu) % geo.nv);
-    const int k = (int)(r / ((long long)geo.nu * geo.nv));
-    const RayXY R = tab[k * geo.nu + iu];
-    const RowZ row = rows[iv];
-    const RayZ Z = ray_z(R, row, zoff);
+// a4: one thread per global ray; incremental Siddon walk.
+__global__ void __launch_bounds__(128) k_project(const __grid_constant__ Batch B,
+                                                 RayXY *__restrict__ tab_base) {
+    const long long r_g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r_g >= B.tot_rays) return;
+    const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
+    const Inst &I = B.in[inst_of_ray(B, r_g)];
+    const dgr_grid &g = I.g;
+    const long long r = r_g - I.ray0;
+    const int iu = (int)(r % I.nu);
+    const int iv = (int)((r / I.nu) % I.nv);
+    const int k = (int)(r / ((long long)I.nu * I.nv));
+    const float *__restrict__ vol = I.vol;
+    float *__restrict__ sino = I.sino;
+    const RayXY R = T.tab[I.tab0 + k * I.nu + iu];
+    const RowZ row = T.rows[I.row0 + iv];
+    const RayZ Z = ray_z(R, row, I.zoff);
     const float xi0[3] = {R.xi0x, R.xi0y, Z.xi0z};
     const float ev[3] = {R.ex, R.ey, Z.ez};
     const float inv[3] = {R.inv_ex, R.inv_ey, Z.inv_ez};
@@ -179,51 +204,48 @@ __global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo, float
             tn[a] = INFINITY;
         }
     }
-    // per-axis state as scalars (selected, never indexed, so it stays in registers)
-    const long long sx = sgn[0], sy = (long long)sgn[1] * g.nx,
-                    sz = (long long)sgn[2] * g.nx * g.ny;  // signed index steps
-    long long idx = (long long)idx3[2] * g.nx * g.ny + (long long)idx3[1] * g.nx + idx3[0];
+    // per-axis state as scalars (selected, never indexed, so it stays in
+    // registers); voxel indices 32-bit (the API bounds a volume to < 2^31)
+    const int sx = sgn[0], sy = sgn[1] * g.nx, sz = sgn[2] * g.nx * g.ny;  // signed index steps
+    int idx = idx3[2] * g.nx * g.ny + idx3[1] * g.nx + idx3[0];
     int ix = idx3[0], iy = idx3[1], iz = idx3[2];
     float tx = tn[0], ty = tn[1], tz = tn[2];
     const float x0 = xi0[0], y0 = xi0[1], z0 = xi0[2];
     const float ivx = inv[0], ivy = inv[1], ivz = inv[2];
     const int ux = sgn[0] > 0, uy = sgn[1] > 0, uz = sgn[2] > 0;
     float t = tmin, acc = 0.f;
-    // branch-free walk: every lane takes one crossing per iteration whatever
-    // its axis (selects, no divergent branches); segment lengths and voxel
-    // indices of WALK crossings first, their loads together, then the sums
-    // in walk order
+    // walk the plane crossings WALK at a time: segment lengths and voxel
+    // indices first (ALU only), then their loads together, then the sums in
+    // walk order
     constexpr int WALK = 4;
     const int maxgroups = (g.nx + g.ny + g.nz + 3) / WALK + 1;
     bool done = false;
     for (int grp = 0; grp < maxgroups && !done; ++grp) {
         float len[WALK];
-        long long at[WALK];
+        int at[WALK];
 #pragma unroll
         for (int j = 0; j < WALK; ++j) {
             at[j] = idx;
             const float tnext = fminf(tx, fminf(ty, tz));
             len[j] = done ? 0.f : tnext - t;
             t = done ? t : tnext;
-            const bool cx = tnext == tx;
-            const bool cy = !cx && tnext == ty;
-            const bool cz = !cx && !cy;
-            const int nxi = ix + sgn[0], nyi = iy + sgn[1], nzi = iz + sgn[2];
-            const bool out = cx ? (nxi < 0 || nxi >= g.nx)
-                                : (cy ? (nyi < 0 || nyi >= g.ny) : (nzi < 0 || nzi >= g.nz));
-            const bool step = !done && !out;
-            done = done || out;
-            const bool sxs = step && cx, sys = step && cy, szs = step && cz;
-            ix = sxs ? nxi : ix;
-            iy = sys ? nyi : iy;
-            iz = szs ? nzi : iz;
-            idx += sxs ? sx : (sys ? sy : (szs ? sz : 0));
-            // next crossing on the stepped axis
-            const int pl = cx ? nxi + ux : (cy ? nyi + uy : nzi + uz);
-            const float tnew = plane_t(pl, cx ? x0 : (cy ? y0 : z0), cx ? ivx : (cy ? ivy : ivz));
-            tx = sxs ? tnew : tx;
-            ty = sys ? tnew : ty;
-            tz = szs ? tnew : tz;
+            if (done) continue;
+            if (tnext == tx) {
+                const int ni = ix + sx;
+                if (ni < 0 || ni >= g.nx) { done = true; continue; }
+                ix = ni; idx += sx;
+                tx = plane_t(ni + ux, x0, ivx);
+            } else if (tnext == ty) {
+                const int ni = iy + sgn[1];
+                if (ni < 0 || ni >= g.ny) { done = true; continue; }
+                iy = ni; idx += sy;
+                ty = plane_t(ni + uy, y0, ivy);
+            } else {
+                const int ni = iz + sgn[2];
+                if (ni < 0 || ni >= g.nz) { done = true; continue; }
+                iz = ni; idx += sz;
+                tz = plane_t(ni + uz, z0, ivz);
+            }
         }
         float v[WALK];
 #pragma unroll
@@ -231,32 +253,35 @@ __global__ void __launch_bounds__(128) k_project(dgr_grid g, dgr_geom geo, float
 #pragma unroll
         for (int j = 0; j < WALK; ++j) acc = fmaf(len[j], v[j], acc);
     }
-    sino[r] = acc * ray_norm(R, row, geo.beam);
+    sino[r] = acc * ray_norm(R, row, I.beam);
 }
 
 // residual x |D| per ray, written view-major with v fastest ([view][u][v]) so
 // that the backprojector's lanes (consecutive z -> consecutive detector rows)
-// read it coalesced; the chord lengths are t-intervals x |D|
+// read it coalesced; the chord lengths are t-intervals x |D|.
+// blockIdx.z: global view.
 constexpr int TR = 32;
-__global__ void k_scale_dn_t(dgr_geom geo, const RayXY *__restrict__ tab,
-                             const RowZ *__restrict__ rows, const float *__restrict__ in,
-                             float *__restrict__ out) {
+__global__ void k_scale_dn_t(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
+                             float *__restrict__ out_base) {
     __shared__ float tile[TR][TR + 1];
-    const int k = blockIdx.z;
+    const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
+    const Inst &I = B.in[inst_of_view(B, blockIdx.z)];
+    const int k = blockIdx.z - I.view0;
     const int u0 = blockIdx.x * TR, v0 = blockIdx.y * TR;
+    if (u0 >= I.nu || v0 >= I.nv) return;  // block-uniform
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-    const float *src = in + (size_t)k * geo.nv * geo.nu;
+    const float *src = I.sino + (size_t)k * I.nv * I.nu;
     for (int j = ty; j < TR; j += 8) {
         const int iv = v0 + j, iu = u0 + tx;
-        if (iv < geo.nv && iu < geo.nu)
-            tile[j][tx] = src[(size_t)iv * geo.nu + iu] *
-                          ray_norm(tab[k * geo.nu + iu], rows[iv], geo.beam);
+        if (iv < I.nv && iu < I.nu)
+            tile[j][tx] = src[(size_t)iv * I.nu + iu] *
+                          ray_norm(T.tab[I.tab0 + k * I.nu + iu], T.rows[I.row0 + iv], I.beam);
     }
     __syncthreads();
-    float *dst = out + (size_t)k * geo.nu * geo.nv;
+    float *dst = out_base + I.ray0 + (size_t)k * I.nu * I.nv;
     for (int j = ty; j < TR; j += 8) {
         const int iu = u0 + j, iv = v0 + tx;
-        if (iv < geo.nv && iu < geo.nu) dst[(size_t)iu * geo.nv + iv] = tile[tx][j];
+        if (iv < I.nv && iu < I.nu) dst[(size_t)iu * I.nv + iv] = tile[tx][j];
     }
 }
 
@@ -273,50 +298,58 @@ __device__ __forceinline__ bool slab(int i, float xi0, float e, float inv, float
     return floorf(xi0) == (float)i;
 }
 
-// Backprojector: a CTA of BP_W warps owns BP_W consecutive x-columns at one y
-// and a z-pass of 32 * BP_ZJ voxels; a warp owns one column, its lanes
-// consecutive z (lane + 32 j).  For each view the candidate detector columns
-// follow from the column's 4 corners (warp-uniform), the slab interval of each
-// candidate ray column is warp-uniform, and each lane finds its candidate rows
-// in closed form and gathers length x scaled residual (rows contiguous across
-// lanes).  The CTA's results leave through shared memory as full sectors.
+// a6: backprojector.  A CTA of BP_W warps owns BP_W consecutive x-columns at
+// one y and a z-pass of 32 * BP_ZJ voxels of one instance; a warp owns one
+// column, its lanes consecutive z (lane + 32 j).  For each view the candidate
+// detector columns follow from the column's 4 corners (warp-uniform), the slab
+// interval of each candidate ray column is warp-uniform, and each lane finds
+// its candidate rows in closed form and gathers length x scaled residual (rows
+// contiguous across lanes).  The results leave through shared memory as full
+// sectors.  blockIdx.x: global backprojector block.
 constexpr int BP_W = 8;
 constexpr int BP_ZJ = 8;
 constexpr int BP_ZP = 32 * BP_ZJ;
 
-template <bool CONE>
-__global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(dgr_grid g, dgr_geom geo, float zoff,
-                                                          const RayXY *__restrict__ tab,
-                                                          const float2 *__restrict__ view_cs,
-                                                          const RowZ *__restrict__ rows,
-                                                          const float *__restrict__ sino_t,
-                                                          float *__restrict__ vol) {
+__global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(const __grid_constant__ Batch B,
+                                                             RayXY *__restrict__ tab_base,
+                                                             const float *__restrict__ sino_t_base) {
     __shared__ float out_tile[BP_ZP][BP_W];
+    const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
+    const Inst &I = B.in[inst_of_blk(B, blockIdx.x)];
+    const dgr_grid &g = I.g;
+    const int b = blockIdx.x - I.blk0;
+    const int bxi = b % I.nbx, iy = (b / I.nbx) % g.ny, bz = b / (I.nbx * g.ny);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int ix = blockIdx.x * BP_W + w;
-    const int iy = blockIdx.y;
-    const int zp = blockIdx.z * BP_ZP;
+    const int ix = bxi * BP_W + w;
+    const int zp = bz * BP_ZP;
+    const bool cone = I.beam == DGR_CONE;
+    const RayXY *__restrict__ tab = T.tab + I.tab0;
+    const float2 *__restrict__ view_cs = T.view_cs + I.view0;
+    const RowZ *__restrict__ rows = T.rows + I.row0;
+    const float *__restrict__ sino_t = sino_t_base + I.ray0;
+    const float zoff = I.zoff;
+    const int nu = I.nu, nv = I.nv;
     float acc[BP_ZJ];
 #pragma unroll
     for (int j = 0; j < BP_ZJ; ++j) acc[j] = 0.f;
     if (ix < g.nx) {
         const float h = g.h;
         const float xl = g.ox + ix * h, xh = xl + h, yl = g.oy + iy * h, yh = yl + h;
-        const float cu = 0.5f * (float)(geo.nu - 1), cv = 0.5f * (float)(geo.nv - 1);
-        const float inv_pu = 1.0f / geo.pu;
-        const float rows_per_zv = g.h / geo.pv;  // detector rows per unit of zv
-        const float row_of_oz = g.oz / geo.pv + cv;
-        for (int k = 0; k < geo.n_views; ++k) {
-            const float2 cs = __ldg(view_cs + k);
+        const float cu = 0.5f * (float)(nu - 1), cv = 0.5f * (float)(nv - 1);
+        const float inv_pu = 1.0f / I.pu;
+        const float rows_per_zv = g.h / I.pv;  // detector rows per unit of zv
+        const float row_of_oz = g.oz / I.pv + cv;
+        for (int k = 0; k < I.n_views; ++k) {
+            const float2 cs = view_cs[k];
             float umin = INFINITY, umax = -INFINITY;
 #pragma unroll
             for (int cnr = 0; cnr < 4; ++cnr) {
                 const float X = (cnr & 1) ? xh : xl, Y = (cnr & 2) ? yh : yl;
                 const float pu_ = fmaf(-X, cs.y, Y * cs.x);
                 float uu;
-                if (CONE) {
+                if (cone) {
                     const float pr = fmaf(X, cs.x, Y * cs.y);
-                    uu = __fdividef(geo.dsd * pu_, geo.dso + pr) * inv_pu + cu;
+                    uu = __fdividef(I.dsd * pu_, I.dso + pr) * inv_pu + cu;
                 } else {
                     uu = pu_ * inv_pu + cu;
                 }
@@ -324,16 +357,16 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(dgr_grid g, dgr_ge
                 umax = fmaxf(umax, uu);
             }
             const int iu0 = max(0, (int)ceilf(umin - CAND_EPS));
-            const int iu1 = min(geo.nu - 1, (int)floorf(umax + CAND_EPS));
+            const int iu1 = min(nu - 1, (int)floorf(umax + CAND_EPS));
             for (int iu = iu0; iu <= iu1; ++iu) {
-                const RayXY R = tab[k * geo.nu + iu];
+                const RayXY R = tab[k * nu + iu];
                 float xlo, xhi, ylo, yhi;
                 if (!slab(ix, R.xi0x, R.ex, R.inv_ex, xlo, xhi)) continue;
                 if (!slab(iy, R.xi0y, R.ey, R.inv_ey, ylo, yhi)) continue;
                 const float tlo = fmaxf(xlo, ylo), thi = fminf(xhi, yhi);
                 if (!(thi > tlo)) continue;
-                const float *scol = sino_t + ((size_t)k * geo.nu + iu) * geo.nv;
-                if (CONE) {
+                const float *scol = sino_t + ((size_t)k * nu + iu) * nv;
+                if (cone) {
                     // ray row zv meets layer iz over t in [tlo, thi] only if
                     // z = zv (tc + t) + zoff, with tc + t in [wa, wb] (> 0: between
                     // source and detector), reaches [iz, iz + 1]:
@@ -348,7 +381,7 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(dgr_grid g, dgr_ge
                         const float f0 = fminf(fmaf(zr, ia, cv), fmaf(zr, ib, cv));
                         const float f1 = fmaxf(fmaf(zr + 1.0f, ia, cv), fmaf(zr + 1.0f, ib, cv));
                         const int iv0 = max(0, (int)ceilf(f0 - CAND_EPS));
-                        const int iv1 = min(geo.nv - 1, (int)floorf(f1 + CAND_EPS));
+                        const int iv1 = min(nv - 1, (int)floorf(f1 + CAND_EPS));
                         float a = acc[j];
                         for (int iv = iv0; iv <= iv1; ++iv) {
                             const RowZ row = rows[iv];
@@ -368,7 +401,7 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(dgr_grid g, dgr_ge
                         if (iz >= g.nz) break;
                         const float f = fmaf((float)iz, rows_per_zv, row_of_oz);
                         const int iv0 = max(0, (int)ceilf(f - CAND_EPS));
-                        const int iv1 = min(geo.nv - 1, (int)floorf(f + rows_per_zv + CAND_EPS));
+                        const int iv1 = min(nv - 1, (int)floorf(f + rows_per_zv + CAND_EPS));
                         float a = acc[j];
                         for (int iv = iv0; iv <= iv1; ++iv) {
                             if (floorf(rows[iv].zsnap) == (float)iz) a = fmaf(len, __ldg(scol + iv), a);
@@ -386,66 +419,76 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(dgr_grid g, dgr_ge
     const size_t zs = (size_t)g.nx * g.ny;
     for (int i = threadIdx.x; i < BP_ZP * BP_W; i += 32 * BP_W) {
         const int zz = i / BP_W, xx = i % BP_W;
-        const int x = blockIdx.x * BP_W + xx, z = zp + zz;
-        if (x < g.nx && z < g.nz) vol[(size_t)z * zs + (size_t)iy * g.nx + x] = out_tile[zz][xx];
+        const int x = bxi * BP_W + xx, z = zp + zz;
+        if (x < g.nx && z < g.nz) I.vol[(size_t)z * zs + (size_t)iy * g.nx + x] = out_tile[zz][xx];
     }
 }
 
-// table layout: RayXY [n_views * nu] | float2 cos/sin [n_views] (padded to 16 B) | RowZ [nv]
-struct Tables {
-    const float2 *view_cs;
-    const RowZ *rows;
-};
-static Tables tables_of(const dgr_geom &geo, const RayXY *tab) {
-    const int n = geo.n_views * geo.nu;
-    const float2 *cs = reinterpret_cast<const float2 *>(tab + n);
-    const size_t cs_bytes = align_up(sizeof(float2) * (size_t)geo.n_views, 16);
-    return Tables{cs, reinterpret_cast<const RowZ *>(reinterpret_cast<const char *>(cs) + cs_bytes)};
-}
-
-static float zoff_of(const dgr_grid &g) { return -g.oz / g.h; }
-
 }  // namespace
 
-size_t ray_table_bytes(int n_views, int nu, int nv) {
-    return sizeof(RayXY) * (size_t)n_views * nu + align_up(sizeof(float2) * (size_t)n_views, 16) +
-           sizeof(RowZ) * (size_t)nv;
+size_t ray_table_bytes(int n_tab, int n_views, int n_rows) {
+    return sizeof(RayXY) * (size_t)n_tab + ((sizeof(float2) * (size_t)n_views + 15) / 16) * 16 +
+           sizeof(RowZ) * (size_t)n_rows;
 }
 
-cudaError_t launch_ray_tables(const dgr_grid &g, const dgr_geom &geo, RayXY *tab, cudaStream_t st) {
-    const int n = geo.n_views * geo.nu;
-    const Tables T = tables_of(geo, tab);
-    const int m = n > geo.nv ? n : geo.nv;
-    k_ray_tables<<<(m + 127) / 128, 128, 0, st>>>(g, geo, tab, const_cast<float2 *>(T.view_cs),
-                                                  const_cast<RowZ *>(T.rows));
+int bp_blocks(const dgr_grid &g, int &nbx, int &nbz) {
+    nbx = (g.nx + BP_W - 1) / BP_W;
+    nbz = (g.nz + BP_ZP - 1) / BP_ZP;
+    return nbx * g.ny * nbz;
+}
+
+cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st) {
+    const int m = B.tot_tab + B.tot_rows;
+    if (m == 0) return cudaSuccess;
+    k_ray_tables<<<(m + 127) / 128, 128, 0, st>>>(B, tab);
     counted(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
-                           const float *vol, float *sino, cudaStream_t st) {
-    const long long nrays = (long long)geo.n_views * geo.nv * geo.nu;
-    const long long blocks = (nrays + 127) / 128;
-    k_project<<<(unsigned)blocks, 128, 0, st>>>(g, geo, zoff_of(g), tab, tables_of(geo, tab).rows,
-                                                vol, sino);
+cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st) {
+    const long long blocks = (B.tot_rays + 127) / 128;
+    if (blocks == 0) return cudaSuccess;
+    k_project<<<(unsigned)blocks, 128, 0, st>>>(B, const_cast<RayXY *>(tab));
     counted(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_backproject(const dgr_grid &g, const dgr_geom &geo, const RayXY *tab,
-                               const float *sino, float *sino_scaled, float *vol, cudaStream_t st) {
-    const Tables T = tables_of(geo, tab);
-    dim3 tgrid((geo.nu + TR - 1) / TR, (geo.nv + TR - 1) / TR, geo.n_views);
-    k_scale_dn_t<<<tgrid, 256, 0, st>>>(geo, tab, T.rows, sino, sino_scaled);
-    dim3 grid((g.nx + BP_W - 1) / BP_W, g.ny, (g.nz + BP_ZP - 1) / BP_ZP);
-    if (geo.beam == DGR_CONE)
-        k_backproject<true><<<grid, 32 * BP_W, 0, st>>>(g, geo, zoff_of(g), tab, T.view_cs, T.rows,
-                                                        sino_scaled, vol);
-    else
-        k_backproject<false><<<grid, 32 * BP_W, 0, st>>>(g, geo, zoff_of(g), tab, T.view_cs, T.rows,
-                                                         sino_scaled, vol);
+cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, cudaStream_t st) {
+    int max_u = 1, max_v = 1;
+    for (int i = 0; i < B.n; ++i) {
+        max_u = B.in[i].nu > max_u ? B.in[i].nu : max_u;
+        max_v = B.in[i].nv > max_v ? B.in[i].nv : max_v;
+    }
+    dim3 tgrid((max_u + TR - 1) / TR, (max_v + TR - 1) / TR, B.tot_views);
+    k_scale_dn_t<<<tgrid, 256, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled);
+    k_backproject<<<B.tot_blk, 32 * BP_W, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled);
     counted(2);
     return cudaGetLastError();
+}
+
+size_t ray_table_bytes_single(const dgr_geom &geo) {
+    return ray_table_bytes(geo.n_views * geo.nu, geo.n_views, geo.nv);
+}
+
+cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY *tab,
+                                  const float *vol, float *sino, cudaStream_t st) {
+    static thread_local Batch B;
+    memset(&B, 0, sizeof(B));
+    B.n = 1;
+    Inst &I = B.in[0];
+    I.g = g;
+    I.zoff = -g.oz / g.h;
+    I.beam = geo.beam; I.n_views = geo.n_views; I.nu = geo.nu; I.nv = geo.nv;
+    I.pu = geo.pu; I.pv = geo.pv; I.dso = geo.dso; I.dsd = geo.dsd; I.angles = geo.angles;
+    I.vol = const_cast<float *>(vol);
+    I.sino = sino;
+    B.tot_tab = geo.n_views * geo.nu;
+    B.tot_views = geo.n_views;
+    B.tot_rows = geo.nv;
+    B.tot_rays = (long long)geo.n_views * geo.nu * geo.nv;
+    cudaError_t e = launch_ray_tables(B, tab, st);
+    if (e == cudaSuccess) e = launch_project(B, tab, st);
+    return e;
 }
 
 }  // namespace dgr

@@ -66,12 +66,12 @@ bool args_ok(const dgr_grid *g, const dgr_geom *geo, const float *vol, const flo
 extern "C" int dgr_project_noalloc(const dgr_grid *grid, const dgr_geom *geom, const float *vol,
                                    float *sino, cudaStream_t stream) {
     if (!args_ok(grid, geom, vol, sino)) return DGR_ERR_ARG;
-    if (dgr::ray_table_bytes(geom->n_views, geom->nu, geom->nv) > (size_t)DGR_NOALLOC_SCRATCH_BYTES)
+    if (dgr::ray_table_bytes_single(*geom) > (size_t)DGR_NOALLOC_SCRATCH_BYTES)
         return DGR_ERR_WS_TOO_SMALL;
+    if ((long long)grid->nx * grid->ny * grid->nz >= (1ll << 31)) return DGR_ERR_ARG;
     void *scratch = nullptr;
     if (scratch_of_current_device(&scratch) != cudaSuccess) return DGR_ERR_CUDA;
     dgr::RayXY *tab = static_cast<dgr::RayXY *>(scratch);
-    cudaError_t e = dgr::launch_ray_tables(*grid, *geom, tab, stream);
-    if (e == cudaSuccess) e = dgr::launch_project(*grid, *geom, tab, vol, sino, stream);
+    const cudaError_t e = dgr::launch_project_single(*grid, *geom, tab, vol, sino, stream);
     return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
 }

@@ -14,15 +14,15 @@ namespace {
 
 constexpr int L1_THREADS = 256;
 
-// loss partials: fixed grid, grid-stride; resid = sign(pred - meas) / m
-__global__ void __launch_bounds__(L1_THREADS) k_l1(const float *__restrict__ pred,
-                                                   const float *__restrict__ meas, long long m,
-                                                   float *resid, float *__restrict__ part) {
+// per-instance loss partials: grid (L1_BLOCKS, instance), grid-stride over the
+// instance's rays; resid = sign(pred - meas) / m written over pred
+__device__ __forceinline__ float l1_block(const float *pred, const float *meas, long long m,
+                                          float *resid, int blk, int nblk) {
     __shared__ float ws[L1_THREADS / 32];
     const float invm = (float)(1.0 / (double)m);
     float s = 0.f;
-    for (long long i = (long long)blockIdx.x * L1_THREADS + threadIdx.x; i < m;
-         i += (long long)gridDim.x * L1_THREADS) {
+    for (long long i = (long long)blk * L1_THREADS + threadIdx.x; i < m;
+         i += (long long)nblk * L1_THREADS) {
         const float d = pred[i] - meas[i];
         s += fabsf(d);
         resid[i] = d > 0.f ? invm : (d < 0.f ? -invm : 0.f);
@@ -31,20 +31,43 @@ __global__ void __launch_bounds__(L1_THREADS) k_l1(const float *__restrict__ pre
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
+    float t = 0.f;
+    if (threadIdx.x == 0)
         for (int w = 0; w < L1_THREADS / 32; ++w) t += ws[w];
-        part[blockIdx.x] = t;
-    }
+    return t;
 }
 
-__global__ void k_l1_final(const float *__restrict__ part, int nb, long long m, float *loss) {
-    // one warp, fixed order: lane-strided FP64 sums, then a shuffle tree
+__global__ void __launch_bounds__(L1_THREADS) k_l1(const __grid_constant__ Batch B,
+                                                   float *__restrict__ part) {
+    const Inst &I = B.in[blockIdx.y];
+    const long long m = (long long)I.n_views * I.nu * I.nv;
+    const float t = l1_block(I.sino, I.meas, m, I.sino, blockIdx.x, gridDim.x);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void k_l1_single(const float *__restrict__ pred, const float *__restrict__ meas,
+                            long long m, float *resid, float *__restrict__ part) {
+    const float t = l1_block(pred, meas, m, resid, blockIdx.x, gridDim.x);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// one warp per instance, fixed order: lane-strided FP64 sums, then a shuffle tree
+__device__ __forceinline__ void l1_final(const float *part, int nb, long long m, float *loss) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) s += (double)part[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) *loss = (float)(s / (double)m);
+}
+
+__global__ void k_l1_final(const __grid_constant__ Batch B, const float *__restrict__ part) {
+    const Inst &I = B.in[blockIdx.x];
+    const long long m = (long long)I.n_views * I.nu * I.nv;
+    l1_final(part + blockIdx.x * L1_BLOCKS, L1_BLOCKS, m, I.loss);
+}
+
+__global__ void k_l1_final_single(const float *__restrict__ part, long long m, float *loss) {
+    l1_final(part, L1_BLOCKS, m, loss);
 }
 
 struct Affine {
@@ -91,54 +114,64 @@ __global__ void k_params_init(dgr_grid g, dgr_params p) {
     }
 }
 
-// grads: [g_mu 3n | g_s 3n | g_q 4n | g_rho n] w.r.t. (mu, s, q, rho)
-__global__ void k_adam(dgr_grid g, dgr_params p, const float *__restrict__ grads, float lr0,
-                       float lr1, int n_iters, float b1, float b2, float eps) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = p.n;
-    if (i >= n) return;
-    const int t = *p.step + 1;
+// Adam on the optimiser variables of every instance (thread per global
+// Gaussian); gradients w.r.t. (mu, s, q, rho) are read from Inst::g_*.
+__global__ void k_adam(const __grid_constant__ Batch B) {
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= B.tot_g) return;
+    const Inst &I = B.in[inst_of_g(B, gi)];
+    const int i = gi - I.g0;
+    const int n = I.n;
+    const int t = *I.step + 1;
+    const float lr0 = I.lr0, lr1 = I.lr1, b1 = I.b1, b2 = I.b2, eps = I.eps;
+    const int n_iters = I.n_iters;
     const float lr = n_iters > 1 ? lr0 * powf(lr1 / lr0, (float)(t - 1) / (float)(n_iters - 1)) : lr0;
     const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
-    const Affine A = grid_affine(g);
-    float *th = p.theta;
+    const Affine A = grid_affine(I.g);
+    float *th = I.theta;
+    float *pm = I.m, *pv = I.v;
     auto upd = [&](int o, float gr) {
-        const float m = b1 * p.m[o] + (1.f - b1) * gr;
-        const float v = b2 * p.v[o] + (1.f - b2) * gr * gr;
-        p.m[o] = m;
-        p.v[o] = v;
+        const float m = b1 * pm[o] + (1.f - b1) * gr;
+        const float v = b2 * pv[o] + (1.f - b2) * gr * gr;
+        pm[o] = m;
+        pv[o] = v;
         const float nt = th[o] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
         th[o] = nt;
         return nt;
     };
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float tm = upd(3 * i + a, grads[3 * i + a] * A.half[a]);
-        p.mu[3 * i + a] = A.c[a] + A.half[a] * tm;
-        const int os = 3 * n + 3 * i + a;
-        const float sc = p.s[3 * i + a];
-        const float ts = upd(os, grads[os] * sc);
-        p.s[3 * i + a] = expf(ts);
+        const float tm = upd(3 * i + a, I.g_mu[3 * i + a] * A.half[a]);
+        I.mu_w[3 * i + a] = A.c[a] + A.half[a] * tm;
+        const float sc = I.s_w[3 * i + a];
+        const float ts = upd(3 * n + 3 * i + a, I.g_s[3 * i + a] * sc);
+        I.s_w[3 * i + a] = expf(ts);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int o = 6 * n + 4 * i + a;
-        p.q[4 * i + a] = upd(o, grads[o]);
-    }
+    for (int a = 0; a < 4; ++a) I.q_w[4 * i + a] = upd(6 * n + 4 * i + a, I.g_q[4 * i + a]);
     const int orho = 10 * n + i;
     const float tr = th[orho];
-    const float trn = upd(orho, grads[orho] * sigmoid(tr));
-    p.rho[i] = softplus(trn);
+    const float trn = upd(orho, I.g_rho[i] * sigmoid(tr));
+    I.rho_w[i] = softplus(trn);
 }
 
-__global__ void k_step_inc(int *step) { *step += 1; }
+__global__ void k_step_inc(const __grid_constant__ Batch B) {
+    if (threadIdx.x < B.n) *B.in[threadIdx.x].step += 1;
+}
 
 }  // namespace
 
-cudaError_t launch_l1(const float *pred, const float *meas, long long m, float *resid, float *loss,
-                      float *part, cudaStream_t st) {
-    k_l1<<<L1_BLOCKS, L1_THREADS, 0, st>>>(pred, meas, m, resid, part);
-    k_l1_final<<<1, 32, 0, st>>>(part, L1_BLOCKS, m, loss);
+cudaError_t launch_l1(const Batch &B, float *part, cudaStream_t st) {
+    k_l1<<<dim3(L1_BLOCKS, B.n), L1_THREADS, 0, st>>>(B, part);
+    k_l1_final<<<B.n, 32, 0, st>>>(B, part);
+    counted(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float *resid,
+                             float *loss, float *part, cudaStream_t st) {
+    k_l1_single<<<L1_BLOCKS, L1_THREADS, 0, st>>>(pred, meas, m, resid, part);
+    k_l1_final_single<<<1, 32, 0, st>>>(part, m, loss);
     counted(2);
     return cudaGetLastError();
 }
@@ -150,15 +183,12 @@ cudaError_t launch_params_init(const dgr_problem &P, const dgr_params &p, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam(const dgr_problem &P, const dgr_params &p, const float *grads,
-                        cudaStream_t st) {
-    const int n = p.n;
-    if (n > 0) {
-        k_adam<<<(n + 127) / 128, 128, 0, st>>>(P.grid, p, grads, P.lr0, P.lr1, P.n_iters, P.beta1,
-                                                P.beta2, P.eps);
+cudaError_t launch_adam(const Batch &B, cudaStream_t st) {
+    if (B.tot_g > 0) {
+        k_adam<<<(B.tot_g + 127) / 128, 128, 0, st>>>(B);
         counted(1);
     }
-    k_step_inc<<<1, 1, 0, st>>>(p.step);
+    k_step_inc<<<1, 32, 0, st>>>(B);
     counted(1);
     return cudaGetLastError();
 }

@@ -114,16 +114,18 @@ __global__ void k_footprint(dgr_grid g, int n, const float *__restrict__ mu,
     }
 }
 
-// a1: per-Gaussian prep.
-__global__ void k_prep(dgr_grid g, int n, const float *__restrict__ mu, const float *__restrict__ s,
-                       const float4 *__restrict__ q, const float *__restrict__ rho, float k,
-                       Prep *__restrict__ prep, uint32_t *__restrict__ itemcnt, int *status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float m[3] = {mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]};
-    float sc[3] = {s[3 * i], s[3 * i + 1], s[3 * i + 2]};
-    const float4 qq = q[i];
-    const float r = rho[i];
+// a1: per-Gaussian prep (thread per global Gaussian index).
+__global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
+                       uint32_t *__restrict__ itemcnt, int *status) {
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= B.tot_g) return;
+    const Inst &I = B.in[inst_of_g(B, gi)];
+    const dgr_grid &g = I.g;
+    const int i = gi - I.g0;
+    float m[3] = {I.mu[3 * i], I.mu[3 * i + 1], I.mu[3 * i + 2]};
+    float sc[3] = {I.s[3 * i], I.s[3 * i + 1], I.s[3 * i + 2]};
+    const float4 qq = reinterpret_cast<const float4 *>(I.q)[i];
+    const float r = I.rho[i];
     Prep P;
     bool ok = finite3(m) && finite3(sc) && isfinite(qq.x) && isfinite(qq.y) && isfinite(qq.z) &&
               isfinite(qq.w) && isfinite(r) && sc[0] > 0.f && sc[1] > 0.f && sc[2] > 0.f &&
@@ -132,12 +134,12 @@ __global__ void k_prep(dgr_grid g, int n, const float *__restrict__ mu, const fl
         atomicOr(status, DGR_STATUS_NONFINITE);
         P = Prep{};
         P.bx = P.by = P.bz = box_pack(1, 0);  // empty
-        prep[i] = P;
-        itemcnt[i] = 0;
+        prep[gi] = P;
+        itemcnt[gi] = 0;
         return;
     }
     Foot F;
-    footprint_f32(g, m, sc, qq, k, F);
+    footprint_f32(g, m, sc, qq, I.k, F);
     // delta = u - a, with u in FP64 so the fractional offset is exact to FP32
     const double h = (double)g.h;
     const double org[3] = {(double)g.ox, (double)g.oy, (double)g.oz};
@@ -148,7 +150,7 @@ __global__ void k_prep(dgr_grid g, int n, const float *__restrict__ mu, const fl
         del[a] = (float)(u - (double)F.an[a]);
     }
     // A = h^2 R diag(1/s^2) R^T (voxel units), scaled by -1/2 log2(e)
-    const float* R = F.R;
+    const float *R = F.R;
     const float h2 = g.h * g.h;
     const float is0 = h2 / (sc[0] * sc[0]), is1 = h2 / (sc[1] * sc[1]), is2 = h2 / (sc[2] * sc[2]);
     float A[6];
@@ -168,64 +170,69 @@ __global__ void k_prep(dgr_grid g, int n, const float *__restrict__ mu, const fl
     P.bx = empty ? box_pack(1, 0) : box_pack(F.lo[0], F.hi[0]);
     P.by = empty ? box_pack(1, 0) : box_pack(F.lo[1], F.hi[1]);
     P.bz = empty ? box_pack(1, 0) : box_pack(F.lo[2], F.hi[2]);
-    prep[i] = P;
+    prep[gi] = P;
     // backward work items of at most ~ITEM_VOX voxels (item_count)
     const int ex = F.hi[0] - F.lo[0] + 1, ey = F.hi[1] - F.lo[1] + 1, ez = F.hi[2] - F.lo[2] + 1;
-    itemcnt[i] = empty ? 0u : item_count(ex, ey, ez);
+    itemcnt[gi] = empty ? 0u : item_count(ex, ey, ez);
 }
 
-// Tile range of a Gaussian; false if its box misses the grid.
-__device__ __forceinline__ bool tile_range(const Prep &P, int &t0x, int &t0y, int &t0z, int &ntx,
-                                           int &nty, int &ntz) {
+// Tile range of a Gaussian (tiles TX x TY x tz); false if its box misses the grid.
+__device__ __forceinline__ bool tile_range(const Prep &P, int tz, int &t0x, int &t0y, int &t0z,
+                                           int &ntx, int &nty, int &ntz) {
     const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
               lz = box_lo(P.bz), hz = box_hi(P.bz);
     if (lx > hx || ly > hy || lz > hz) return false;
-    t0x = lx / TX; t0y = ly / TY; t0z = lz / TZ;
-    ntx = hx / TX - t0x + 1; nty = hy / TY - t0y + 1; ntz = hz / TZ - t0z + 1;
+    t0x = lx / TX; t0y = ly / TY; t0z = lz / tz;
+    ntx = hx / TX - t0x + 1; nty = hy / TY - t0y + 1; ntz = hz / tz - t0z + 1;
     return true;
 }
 
 // a2: count Gaussians per tile (one warp per Gaussian, lanes over its tiles).
-__global__ void k_tile_count(int n, const Prep *__restrict__ prep, int NTX, int NTY,
+__global__ void k_tile_count(const __grid_constant__ Batch B, const Prep *__restrict__ prep,
                              uint32_t *__restrict__ tile_cnt) {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        const Prep P = prep[i];
+    for (int gi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < B.tot_g; gi += warps) {
+        const Inst &I = B.in[inst_of_g(B, gi)];
+        const Prep P = prep[gi];
         int t0x, t0y, t0z, ntx, nty, ntz;
-        if (!tile_range(P, t0x, t0y, t0z, ntx, nty, ntz)) continue;
+        if (!tile_range(P, B.tz, t0x, t0y, t0z, ntx, nty, ntz)) continue;
         const int tot = ntx * nty * ntz;
         for (int j = lane; j < tot; j += 32) {
             const int jx = j % ntx, jy = (j / ntx) % nty, jz = j / (ntx * nty);
-            const int t = ((t0z + jz) * NTY + (t0y + jy)) * NTX + (t0x + jx);
+            const int t = I.tile0 + ((t0z + jz) * I.nty + (t0y + jy)) * I.ntx + (t0x + jx);
             atomicAdd(&tile_cnt[t], 1u);
         }
     }
 }
 
 // a2: write each Gaussian index into the lists of the tiles it overlaps.
-__global__ void k_tile_fill(int n, const Prep *__restrict__ prep, int NTX, int NTY,
+__global__ void k_tile_fill(const __grid_constant__ Batch B, const Prep *__restrict__ prep,
                             const uint32_t *__restrict__ tile_off, uint32_t *__restrict__ tile_fill,
                             uint32_t *__restrict__ list, unsigned long long cap) {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        const Prep P = prep[i];
+    for (int gi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < B.tot_g; gi += warps) {
+        const Inst &I = B.in[inst_of_g(B, gi)];
+        const Prep P = prep[gi];
         int t0x, t0y, t0z, ntx, nty, ntz;
-        if (!tile_range(P, t0x, t0y, t0z, ntx, nty, ntz)) continue;
+        if (!tile_range(P, B.tz, t0x, t0y, t0z, ntx, nty, ntz)) continue;
         const int tot = ntx * nty * ntz;
         for (int j = lane; j < tot; j += 32) {
             const int jx = j % ntx, jy = (j / ntx) % nty, jz = j / (ntx * nty);
-            const int t = ((t0z + jz) * NTY + (t0y + jy)) * NTX + (t0x + jx);
+            const int t = I.tile0 + ((t0z + jz) * I.nty + (t0y + jy)) * I.ntx + (t0x + jx);
             const unsigned long long pos =
                 (unsigned long long)tile_off[t] + atomicAdd(&tile_fill[t], 1u);
-            if (pos < cap) list[pos] = (uint32_t)i;
+            if (pos < cap) list[pos] = (uint32_t)gi;
         }
     }
 }
 
-// a2: sort each tile's list ascending (bitonic; in shared memory up to
-// SORT_SMEM entries, else in place in global memory).
+// a2: sort each tile's list ascending.  Up to SORT_SMEM entries: bitonic
+// sort in shared memory (padded there with +inf).  Longer lists: sort chunks
+// of SORT_SMEM in shared memory the same way, then merge runs pairwise
+// (width doubling) through a scratch list of the same layout, each output
+// position finding its source by a co-rank (merge-path) binary search.
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_SMEM = 4096;
 
@@ -244,8 +251,31 @@ __device__ void bitonic_smem(uint32_t *a, int m2) {
         }
 }
 
+// sorts seg[0, m) (m <= SORT_SMEM) through shared memory
+__device__ void sort_chunk(uint32_t *seg, int m, uint32_t *sm) {
+    int m2 = 1;
+    while (m2 < m) m2 <<= 1;
+    for (int i = threadIdx.x; i < m2; i += blockDim.x) sm[i] = i < m ? seg[i] : 0xffffffffu;
+    __syncthreads();
+    bitonic_smem(sm, m2);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) seg[i] = sm[i];
+    __syncthreads();
+}
+
+// elements taken from run A among the first k outputs of the stable merge of
+// sorted runs A and B (ties from A first); at most log2(alen) + 1 steps
+__device__ __forceinline__ int corank(int k, const uint32_t *A, int alen, const uint32_t *Bv, int blen) {
+    int lo = max(0, k - blen), hi = min(k, alen);
+    while (lo < hi) {
+        const int i = (lo + hi) >> 1, j = k - i;
+        if (j > 0 && i < alen && Bv[j - 1] > A[i]) lo = i + 1; else hi = i;
+    }
+    return lo;
+}
+
 __global__ void k_tile_sort(int ntiles, const uint32_t *__restrict__ tile_off,
-                            uint32_t *__restrict__ list, unsigned long long cap) {
+                            uint32_t *__restrict__ list, uint32_t *__restrict__ scratch,
+                            unsigned long long cap) {
     __shared__ uint32_t sm[SORT_SMEM];
     const int t = blockIdx.x;
     unsigned long long b = tile_off[t], e = tile_off[t + 1];
@@ -253,34 +283,32 @@ __global__ void k_tile_sort(int ntiles, const uint32_t *__restrict__ tile_off,
     if (b >= e) return;
     const int m = (int)(e - b);
     if (m < 2) return;
-    int m2 = 1;
-    while (m2 < m) m2 <<= 1;
     uint32_t *seg = list + b;
-    if (m2 <= SORT_SMEM) {
-        for (int i = threadIdx.x; i < m2; i += blockDim.x) sm[i] = i < m ? seg[i] : 0xffffffffu;
-        __syncthreads();
-        bitonic_smem(sm, m2);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) seg[i] = sm[i];
+    if (m <= SORT_SMEM) {
+        sort_chunk(seg, m, sm);
         return;
     }
-    // large list: bitonic network over the padded length with out-of-range
-    // entries treated as +infinity, operating in place in global memory
-    for (int k = 2; k <= m2; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < m2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const uint32_t x = i < m ? seg[i] : 0xffffffffu;
-                    const uint32_t y = l < m ? seg[l] : 0xffffffffu;
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        if (i < m) seg[i] = y;
-                        if (l < m) seg[l] = x;
-                    }
-                }
-            }
-            __syncthreads();
+    for (int c0 = 0; c0 < m; c0 += SORT_SMEM) sort_chunk(seg + c0, min(SORT_SMEM, m - c0), sm);
+    uint32_t *src = seg, *dst = scratch + b;
+    for (int w = SORT_SMEM; w < m; w <<= 1) {
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const int s0 = (k / (2 * w)) * (2 * w);
+            const int alen = min(w, m - s0);
+            const int b0 = s0 + alen;
+            const int blen = max(0, min(w, m - b0));
+            const int kk = k - s0;
+            const int i = corank(kk, src + s0, alen, src + b0, blen), j = kk - i;
+            dst[k] = (i < alen && (j >= blen || src[s0 + i] <= src[b0 + j])) ? src[s0 + i]
+                                                                             : src[b0 + j];
         }
+        __syncthreads();
+        uint32_t *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (src != seg) {
+        for (int k = threadIdx.x; k < m; k += blockDim.x) seg[k] = src[k];
+    }
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -289,84 +317,106 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// a3: one CTA per tile.  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
+// a3: persistent CTAs take tiles from a global queue (tiles of every instance
+// back to back).  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
 // (lx, ly) = (lane & 7, lane >> 3), and z in [tz0, tz0 + TZ) in registers.
+template <int TZ>
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
-    dgr_grid g, int NTX, int NTY, const Prep *__restrict__ prep,
+    const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
-    unsigned long long cap, float *__restrict__ vol) {
+    unsigned long long cap, int *__restrict__ queue) {
     __shared__ float4 sp[VOX_CHUNK * 4];
-    const int t = blockIdx.x;
-    const int tx = t % NTX, ty = (t / NTX) % NTY, tz = t / (NTX * NTY);
-    const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    __shared__ int s_tile;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = x0 + (lane & 7);
-    const int wy0 = y0 + 4 * w;
-    const int y = wy0 + (lane >> 3);
-    float acc[TZ];
+    for (;;) {
+        __syncthreads();  // everyone is done with s_tile and sp
+        if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
+        __syncthreads();
+        const int tg = s_tile;
+        if (tg >= B.tot_tiles) return;
+        const Inst &I = B.in[inst_of_tile(B, tg)];
+        const dgr_grid &g = I.g;
+        const int t = tg - I.tile0;
+        const int tx = t % I.ntx, ty = (t / I.ntx) % I.nty, tz = t / (I.ntx * I.nty);
+        const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+        const int x = x0 + (lane & 7);
+        const int wy0 = y0 + 4 * w;
+        const int y = wy0 + (lane >> 3);
+        // per-voxel sums with Kahan compensation: a voxel inside many boxes
+        // keeps its FP32 sum within a few ulps of the exact sum
+        float acc[TZ], cmp[TZ];
 #pragma unroll
-    for (int k = 0; k < TZ; ++k) acc[k] = 0.f;
+        for (int k = 0; k < TZ; ++k) acc[k] = cmp[k] = 0.f;
 
-    unsigned long long b = tile_off[t], e = tile_off[t + 1];
-    if (e > cap) e = cap;
-    for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
-        const int nc = (int)min((unsigned long long)VOX_CHUNK, e - c0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nc * 4; i += VOX_THREADS) {
-            const uint32_t gi = list[c0 + (i >> 2)];
-            sp[i] = reinterpret_cast<const float4 *>(prep + gi)[i & 3];
-        }
-        __syncthreads();
-        for (int j = 0; j < nc; ++j) {
-            const float4 p3 = sp[4 * j + 3];
-            const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z),
-                      bz = __float_as_int(p3.w);
-            const int lx = box_lo(bx), hx = box_hi(bx), ly = box_lo(by), hy = box_hi(by);
-            const int zlo = max(box_lo(bz) - z0, 0), zhi = min(box_hi(bz) - z0, TZ - 1);
-            // warp-uniform skip: the warp's 8 x 4 patch or the z range misses the box
-            if (hx < x0 || lx > x0 + 7 || hy < wy0 || ly > wy0 + 3 || zlo > zhi) continue;
-            const float4 p0 = sp[4 * j], p1 = sp[4 * j + 1], p2 = sp[4 * j + 2];
-            const int ax = __float_as_int(p2.z), ay = __float_as_int(p2.w),
-                      az = __float_as_int(p3.x);
-            const float dx = (float)(x - ax) - p0.x;
-            const float dy = (float)(y - ay) - p0.y;
-            const bool in = x >= lx && x <= hx && y >= ly && y <= hy;
-            // quadratic form in dz: a22 dz^2 + Lz dz + C  (already scaled)
-            float C = fmaf(p1.x * dx, dx, fmaf(p1.y * dy, dy, p1.w * dx * dy));
-            C = in ? C : -INFINITY;
-            const float Lz = fmaf(p2.x, dx, p2.y * dy);
-            const float dz0 = (float)(z0 - az) - p0.z;
-            const float a22 = p1.z, r = p0.w;
+        unsigned long long b = tile_off[tg], e = tile_off[tg + 1];
+        if (e > cap) e = cap;
+        for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
+            const int nc = (int)min((unsigned long long)VOX_CHUNK, e - c0);
+            if (c0 != b) __syncthreads();
+            for (int i = threadIdx.x; i < nc * 4; i += VOX_THREADS) {
+                const uint32_t gi = list[c0 + (i >> 2)];
+                sp[i] = reinterpret_cast<const float4 *>(prep + gi)[i & 3];
+            }
+            __syncthreads();
+            for (int j = 0; j < nc; ++j) {
+                const float4 p3 = sp[4 * j + 3];
+                const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z),
+                          bz = __float_as_int(p3.w);
+                const int lx = box_lo(bx), hx = box_hi(bx), ly = box_lo(by), hy = box_hi(by);
+                const int zlo = max(box_lo(bz) - z0, 0), zhi = min(box_hi(bz) - z0, TZ - 1);
+                // warp-uniform skip: the warp's 8 x 4 patch or the z range misses the box
+                if (hx < x0 || lx > x0 + 7 || hy < wy0 || ly > wy0 + 3 || zlo > zhi) continue;
+                const float4 p0 = sp[4 * j], p1 = sp[4 * j + 1], p2 = sp[4 * j + 2];
+                const int ax = __float_as_int(p2.z), ay = __float_as_int(p2.w),
+                          az = __float_as_int(p3.x);
+                const float dx = (float)(x - ax) - p0.x;
+                const float dy = (float)(y - ay) - p0.y;
+                const bool in = x >= lx && x <= hx && y >= ly && y <= hy;
+                // quadratic form in dz: a22 dz^2 + Lz dz + C  (already scaled)
+                float C = fmaf(p1.x * dx, dx, fmaf(p1.y * dy, dy, p1.w * dx * dy));
+                C = in ? C : -INFINITY;
+                const float Lz = fmaf(p2.x, dx, p2.y * dy);
+                const float dz0 = (float)(z0 - az) - p0.z;
+                const float a22 = p1.z, r = p0.w;
 #pragma unroll
-            for (int g8 = 0; g8 < TZ / TZG; ++g8) {
-                if (zhi < g8 * TZG || zlo >= (g8 + 1) * TZG) continue;  // warp-uniform
+                for (int g8 = 0; g8 < TZ / TZG; ++g8) {
+                    if (zhi < g8 * TZG || zlo >= (g8 + 1) * TZG) continue;  // warp-uniform
 #pragma unroll
-                for (int kk = 0; kk < TZG; ++kk) {
-                    const int k = g8 * TZG + kk;
-                    if (k >= zlo && k <= zhi) {
-                        const float dz = dz0 + (float)k;
-                        const float qf = fmaf(dz, fmaf(a22, dz, Lz), C);
-                        acc[k] = fmaf(r, ex2_approx(qf), acc[k]);
+                    for (int kk = 0; kk < TZG; ++kk) {
+                        const int k = g8 * TZG + kk;
+                        if (k >= zlo && k <= zhi) {
+                            const float dz = dz0 + (float)k;
+                            const float qf = fmaf(dz, fmaf(a22, dz, Lz), C);
+                            const float y = fmaf(r, ex2_approx(qf), -cmp[k]);
+                            const float tsum = acc[k] + y;
+                            cmp[k] = (tsum - acc[k]) - y;
+                            acc[k] = tsum;
+                        }
                     }
                 }
             }
         }
-    }
-    if (x < g.nx && y < g.ny) {
-        float *col = vol + (size_t)y * g.nx + x;
-        const size_t zs = (size_t)g.nx * g.ny;
+        if (x < g.nx && y < g.ny) {
+            float *col = I.vol + (size_t)y * g.nx + x;
+            const size_t zs = (size_t)g.nx * g.ny;
 #pragma unroll
-        for (int k = 0; k < TZ; ++k)
-            if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+            for (int k = 0; k < TZ; ++k)
+                if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+        }
     }
 }
 
 }  // namespace
 
+static int g_tile_depth = 32;
+int tile_depth() { return g_tile_depth; }
+void set_tile_depth(int tz) { g_tile_depth = tz; }
+
 int tile_dims(const dgr_grid &g, int &ntx, int &nty, int &ntz) {
+    const int tz = g_tile_depth;
     ntx = (g.nx + TX - 1) / TX;
     nty = (g.ny + TY - 1) / TY;
-    ntz = (g.nz + TZ - 1) / TZ;
+    ntz = (g.nz + tz - 1) / tz;
     return ntx * nty * ntz;
 }
 
@@ -379,12 +429,9 @@ cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(const dgr_grid &g, int n, const float *mu, const float *s, const float *q,
-                        const float *rho, float k, Prep *prep, uint32_t *itemcnt, int *status,
-                        cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    k_prep<<<(n + 127) / 128, 128, 0, st>>>(g, n, mu, s, reinterpret_cast<const float4 *>(q), rho,
-                                            k, prep, itemcnt, status);
+cudaError_t launch_prep(const Batch &B, Prep *prep, uint32_t *itemcnt, int *status, cudaStream_t st) {
+    if (B.tot_g == 0) return cudaSuccess;
+    k_prep<<<(B.tot_g + 127) / 128, 128, 0, st>>>(B, prep, itemcnt, status);
     counted(1);
     return cudaGetLastError();
 }
@@ -394,45 +441,62 @@ static int warp_grid(int n) {
     return blocks < 1 ? 1 : (blocks > 148 * 16 ? 148 * 16 : blocks);
 }
 
-cudaError_t launch_count_pairs(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws,
-                               unsigned long long cap, cudaStream_t st) {
-    int NTX, NTY, NTZ;
-    const int ntiles = tile_dims(g, NTX, NTY, NTZ);
+cudaError_t launch_count_pairs(const Batch &B, const Prep *prep, dgr_ws *ws, unsigned long long cap,
+                               cudaStream_t st) {
     uint32_t *tile_cnt = ws_ptr<uint32_t>(ws, ws->tile_cnt);
     uint32_t *tile_off = ws_ptr<uint32_t>(ws, ws->tile_off);
     int *status = ws_ptr<int>(ws, ws->status);
-    cudaError_t err = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * ntiles, st);
+    cudaError_t err = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * B.tot_tiles, st);
     if (err != cudaSuccess) return err;
-    if (n > 0) {
-        k_tile_count<<<warp_grid(n), 256, 0, st>>>(n, prep, NTX, NTY, tile_cnt);
+    if (B.tot_g > 0) {
+        k_tile_count<<<warp_grid(B.tot_g), 256, 0, st>>>(B, prep, tile_cnt);
         counted(1);
     }
-    return scan_u32(tile_cnt, tile_off, ntiles, cap, status, DGR_STATUS_PAIR_OVERFLOW, ws_ptr<unsigned long long>(ws, ws->scan_tmp), st);
+    return scan_u32(tile_cnt, tile_off, B.tot_tiles, cap, status, DGR_STATUS_PAIR_OVERFLOW,
+                    ws_ptr<unsigned long long>(ws, ws->scan_tmp), st);
 }
 
-cudaError_t launch_voxelize(const dgr_grid &g, int n, const Prep *prep, dgr_ws *ws, float *vol,
-                            int deterministic, cudaStream_t st) {
-    int NTX, NTY, NTZ;
-    const int ntiles = tile_dims(g, NTX, NTY, NTZ);
+template <int TZ>
+static cudaError_t launch_vox_tz(const Batch &B, const Prep *prep, const uint32_t *tile_off,
+                                 const uint32_t *list, unsigned long long cap, int *queue,
+                                 cudaStream_t st) {
+    int dev = 0, sms = 148, per_sm = 8;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxelize<TZ>, VOX_THREADS, 0);
+    const int grid = max(1, min(B.tot_tiles, sms * max(per_sm, 1)));
+    k_voxelize<TZ><<<grid, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int deterministic,
+                            cudaStream_t st) {
     uint32_t *tile_off = ws_ptr<uint32_t>(ws, ws->tile_off);
     uint32_t *tile_fill = ws_ptr<uint32_t>(ws, ws->tile_fill);
     uint32_t *list = ws_ptr<uint32_t>(ws, ws->list);
+    int *queue = ws_ptr<int>(ws, ws->status) + 16;  // tile queue head
     const unsigned long long cap = (unsigned long long)ws->plan.max_pairs;
-    cudaError_t err = launch_count_pairs(g, n, prep, ws, cap, st);
+    cudaError_t err = launch_count_pairs(B, prep, ws, cap, st);
     if (err != cudaSuccess) return err;
-    err = cudaMemsetAsync(tile_fill, 0, sizeof(uint32_t) * ntiles, st);
+    err = cudaMemsetAsync(tile_fill, 0, sizeof(uint32_t) * B.tot_tiles, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(queue, 0, sizeof(int), st);
     if (err != cudaSuccess) return err;
-    if (n > 0) {
-        k_tile_fill<<<warp_grid(n), 256, 0, st>>>(n, prep, NTX, NTY, tile_off, tile_fill, list, cap);
+    if (B.tot_g > 0) {
+        k_tile_fill<<<warp_grid(B.tot_g), 256, 0, st>>>(B, prep, tile_off, tile_fill, list, cap);
         counted(1);
     }
     if (deterministic) {
-        k_tile_sort<<<ntiles, SORT_THREADS, 0, st>>>(ntiles, tile_off, list, cap);
+        k_tile_sort<<<B.tot_tiles, SORT_THREADS, 0, st>>>(B.tot_tiles, tile_off, list,
+                                                          ws_ptr<uint32_t>(ws, ws->list_tmp), cap);
         counted(1);
     }
-    k_voxelize<<<ntiles, VOX_THREADS, 0, st>>>(g, NTX, NTY, prep, tile_off, list, cap, vol);
-    counted(1);
-    return cudaGetLastError();
+    // persistent: enough CTAs to fill every SM, each pulling tiles from the queue
+    switch (B.tz) {
+        case 8: return launch_vox_tz<8>(B, prep, tile_off, list, cap, queue, st);
+        case 16: return launch_vox_tz<16>(B, prep, tile_off, list, cap, queue, st);
+        default: return launch_vox_tz<32>(B, prep, tile_off, list, cap, queue, st);
+    }
 }
 
 }  // namespace dgr

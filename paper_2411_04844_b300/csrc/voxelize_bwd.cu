@@ -26,8 +26,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 __global__ void __launch_bounds__(256) k_bwd_items(
-    dgr_grid g, int n, const Prep *__restrict__ prep, const uint32_t *__restrict__ item_off,
-    unsigned long long cap, const float *__restrict__ gv, float *__restrict__ part) {
+    const __grid_constant__ Batch B, const Prep *__restrict__ prep,
+    const uint32_t *__restrict__ item_off, unsigned long long cap, float *__restrict__ part) {
+    const int n = B.tot_g;
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     unsigned long long total = item_off[n];
@@ -48,6 +49,9 @@ __global__ void __launch_bounds__(256) k_bwd_items(
         }
         const int gi = lo;
         const int c = (int)(it - item_off[gi]);
+        const Inst &I = B.in[inst_of_g(B, gi)];
+        const dgr_grid &g = I.g;
+        const float *__restrict__ gv = I.vol;
         const Prep P = prep[gi];
         const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
                   lz = box_lo(P.bz), hz = box_hi(P.bz);
@@ -125,15 +129,22 @@ __global__ void __launch_bounds__(256) k_bwd_items(
     }
 }
 
-__global__ void k_bwd_final(dgr_grid g, int n, const float *__restrict__ mu,
-                            const float *__restrict__ s, const float4 *__restrict__ q,
-                            const float *__restrict__ rho, const uint32_t *__restrict__ item_off,
-                            unsigned long long cap, const float *__restrict__ part,
-                            float *__restrict__ g_mu, float *__restrict__ g_s,
-                            float *__restrict__ g_q, float *__restrict__ g_rho) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    unsigned long long b = item_off[i], e = item_off[i + 1];
+__global__ void k_bwd_final(const __grid_constant__ Batch B,
+                            const uint32_t *__restrict__ item_off, unsigned long long cap,
+                            const float *__restrict__ part) {
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= B.tot_g) return;
+    const Inst &I = B.in[inst_of_g(B, gi)];
+    const dgr_grid &g = I.g;
+    const int i = gi - I.g0;
+    const float *__restrict__ s = I.s;
+    const float4 *__restrict__ q = reinterpret_cast<const float4 *>(I.q);
+    const float *__restrict__ rho = I.rho;
+    float *__restrict__ g_mu = I.g_mu;
+    float *__restrict__ g_s = I.g_s;
+    float *__restrict__ g_q = I.g_q;
+    float *__restrict__ g_rho = I.g_rho;
+    unsigned long long b = item_off[gi], e = item_off[gi + 1];
     if (e > cap) e = cap;
     // item partials summed in FP64 (a large box has tens of thousands of items)
     double Md[NMOM];
@@ -222,22 +233,18 @@ __global__ void k_bwd_final(dgr_grid g, int n, const float *__restrict__ mu,
 
 }  // namespace
 
-cudaError_t launch_voxelize_backward(const dgr_grid &g, int n, const float *mu, const float *s,
-                                     const float *q, const float *rho, const Prep *prep,
-                                     const float *grad_vol, float *g_mu, float *g_s, float *g_q,
-                                     float *g_rho, dgr_ws *ws, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
+cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st) {
+    if (B.tot_g == 0) return cudaSuccess;
     uint32_t *itemcnt = ws_ptr<uint32_t>(ws, ws->itemcnt);
     uint32_t *item_off = ws_ptr<uint32_t>(ws, ws->item_off);
     float *part = ws_ptr<float>(ws, ws->partials);
     int *status = ws_ptr<int>(ws, ws->status);
     const unsigned long long cap = (unsigned long long)ws->plan.max_items;
-    cudaError_t err = scan_u32(itemcnt, item_off, n, cap, status, DGR_STATUS_ITEM_OVERFLOW,
+    cudaError_t err = scan_u32(itemcnt, item_off, B.tot_g, cap, status, DGR_STATUS_ITEM_OVERFLOW,
                                ws_ptr<unsigned long long>(ws, ws->scan_tmp), st);
     if (err != cudaSuccess) return err;
-    k_bwd_items<<<148 * 8, 256, 0, st>>>(g, n, prep, item_off, cap, grad_vol, part);
-    k_bwd_final<<<(n + 127) / 128, 128, 0, st>>>(g, n, mu, s, reinterpret_cast<const float4 *>(q),
-                                                 rho, item_off, cap, part, g_mu, g_s, g_q, g_rho);
+    k_bwd_items<<<148 * 8, 256, 0, st>>>(B, prep, item_off, cap, part);
+    k_bwd_final<<<(B.tot_g + 127) / 128, 128, 0, st>>>(B, item_off, cap, part);
     counted(2);
     return cudaGetLastError();
 }

@@ -26,7 +26,7 @@ DGR_STATUS_ITEM_OVERFLOW = 0x40
 DGR_PARALLEL = 0
 DGR_CONE = 1
 
-# voxel tile of the forward voxelizer (x, y, z)
+# voxel tile of the forward voxelizer (x, y, default z depth)
 TILE = (8, 16, 32)
 
 EXPORTS = [
@@ -34,7 +34,7 @@ EXPORTS = [
     "dgr_strerror", "dgr_set_deterministic", "dgr_footprint", "dgr_voxelize_count",
     "dgr_voxelize", "dgr_voxelize_backward", "dgr_project", "dgr_backproject",
     "dgr_l1_residual", "dgr_params_init", "dgr_step", "dgr_step_timed", "dgr_launch_count",
-    "dgr_project_noalloc",
+    "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -84,7 +84,8 @@ class WsPlan(ctypes.Structure):
     _fields_ = [("max_n", ctypes.c_int), ("max_tiles", ctypes.c_int),
                 ("max_pairs", ctypes.c_longlong), ("max_items", ctypes.c_longlong),
                 ("max_vox", ctypes.c_longlong), ("max_rays", ctypes.c_longlong),
-                ("max_views", ctypes.c_int), ("max_nu", ctypes.c_int), ("max_nv", ctypes.c_int)]
+                ("max_views", ctypes.c_int), ("max_nu", ctypes.c_int), ("max_nv", ctypes.c_int),
+                ("max_inst", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -120,6 +121,7 @@ def lib():
             "dgr_tile_count": [ctypes.POINTER(Grid), ctypes.POINTER(i)],
             "dgr_status": [P, P, ctypes.POINTER(i)],
             "dgr_set_deterministic": [i],
+            "dgr_set_tile_depth": [i],
             "dgr_footprint": [ctypes.POINTER(Grid), i, P, P, P, f, P, P, P],
             "dgr_voxelize_count": [ctypes.POINTER(Grid), i, P, P, P, f, ctypes.POINTER(ll),
                                    ctypes.POINTER(ll), P, P],
@@ -133,6 +135,8 @@ def lib():
             "dgr_step_timed": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P,
                                ctypes.POINTER(P), i],
             "dgr_project_noalloc": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P],
+            "dgr_step_batched": [i, ctypes.POINTER(Problem), ctypes.POINTER(Params),
+                                 ctypes.POINTER(P), P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -232,6 +236,10 @@ def dgr_status(ws: Workspace, stream=None) -> int:
     v = ctypes.c_int()
     _rc(lib().dgr_status(ws.ptr, _stream(stream), ctypes.byref(v)), "dgr_status")
     return int(v.value)
+
+
+def dgr_set_tile_depth(tz: int):
+    _rc(lib().dgr_set_tile_depth(int(tz)), "dgr_set_tile_depth")
 
 
 def dgr_set_deterministic(on: bool):
@@ -365,3 +373,35 @@ def dgr_step_timed(prob: Problem, st: State, measured, loss_out, ws: Workspace, 
 
 def dgr_launch_count() -> int:
     return int(lib().dgr_launch_count())
+
+
+def dgr_step_batched(probs, states, measured, loss_out, ws: Workspace, stream=None):
+    """One optimisation step of every instance: probs [Problem], states
+    [State], measured [device tensors], loss_out device tensor [n_inst]."""
+    n = len(probs)
+    if not (len(states) == n == len(measured)):
+        raise DgrError("dgr_step_batched: mismatched instance lists")
+    for t in measured:
+        _check(t, "measured")
+    _check(loss_out, "loss_out")
+    P = (Problem * n)(*probs)
+    Q = (Params * n)(*[st.params() for st in states])
+    M = (ctypes.c_void_p * n)(*[t.data_ptr() for t in measured])
+    _rc(lib().dgr_step_batched(n, P, Q, M, _ptr(loss_out), ws.ptr, _stream(stream)),
+        "dgr_step_batched")
+
+
+def make_batch_plan(grids, geoms, ns, pairs, items) -> WsPlan:
+    """Workspace plan for dgr_step_batched over these instances."""
+    p = WsPlan()
+    p.max_n = int(sum(ns))
+    p.max_tiles = int(sum(dgr_tile_count(g) for g in grids))
+    p.max_pairs = int(sum(pairs))
+    p.max_items = int(sum(items))
+    p.max_vox = int(sum(g.nx * g.ny * g.nz for g in grids))
+    p.max_rays = int(sum(ge.n_views * ge.nu * ge.nv for ge in geoms))
+    p.max_views = int(sum(ge.n_views for ge in geoms))
+    p.max_nu = int(max(ge.nu for ge in geoms))
+    p.max_nv = int(max(ge.nv for ge in geoms))
+    p.max_inst = len(grids)
+    return p

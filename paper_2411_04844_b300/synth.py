@@ -220,3 +220,32 @@ def workload(config: int) -> Workload:
         return Workload("cone512_500k", g, cone_geom(75, 512, 512, 1.5, 1.5, 1000.0, 1500.0),
                         500000, ("lognormal", 1.5, 0.894), 40)
     raise ValueError(config)
+
+
+@dataclass
+class Instance:
+    grid: GridSpec
+    geom: GeomSpec
+    field: Field
+    phantom_m: int = 40
+    noise_sigma: float = 0.01
+
+
+def batched_workload(n_inst: int = 16, config: int = 4, sizes=(64, 128, 192, 256),
+                     n_range=(5000, 200000), views_range=(25, 100), scale=("loguniform", 0.5, 6.0)):
+    """Independent reconstructions of uneven size: grid side drawn from `sizes`
+    (h = 1 mm, centred), Gaussian count log-uniform in n_range, cone beam with
+    views uniform in views_range over 360 deg, an N x N detector of pitch 1.5 h
+    (source-origin 1000 mm, source-detector 1500 mm)."""
+    out = []
+    for i in range(n_inst):
+        rng = rng_for(config, i)
+        N = int(rng.choice(sizes))
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        views = int(rng.integers(views_range[0], views_range[1] + 1))
+        grid = GridSpec.centred(N, 1.0)
+        geom = cone_geom(views, N, N, 1.5, 1.5, 1000.0, 1500.0)
+        f = gaussian_field(rng, n, grid, scale)
+        f.rho = np.clip(f.rho, 0.02, 1.0).astype(np.float32)
+        out.append(Instance(grid, geom, f))
+    return out

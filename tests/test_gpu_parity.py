@@ -157,6 +157,25 @@ def test_voxelize_overflow_is_reported():
     assert torch.isfinite(vol).all()
 
 
+@pytest.mark.parametrize("depth", [32, 8])
+def test_voxelize_long_tile_lists(depth):
+    """9,000 small Gaussians in a 16 x 16 x 32 grid: every tile's list holds
+    more than 4,096 Gaussians, so the chunked sort + merge path runs."""
+    gs = synth.GridSpec((16, 16, 32), 1.0, (-8.0, -8.0, -16.0))
+    f = guard_field(synth.gaussian_field(synth.rng_for(1, 31), 9000, gs, ("loguniform", 0.5, 1.5)), gs)
+    try:
+        dgr.dgr_set_tile_depth(depth)
+        grid = dgr.Grid.of(gs)
+        ws = workspace_for(grid, f)
+        a = gpu_voxelize(gs, f, ws=ws)
+        b = gpu_voxelize(gs, f, ws=ws)
+    finally:
+        dgr.dgr_set_tile_depth(32)
+    assert torch.equal(a, b)
+    vo = O.voxelize(oracle_grid(gs), f.mu, f.s, f.q, f.rho, 3.0)
+    check_volume(a, vo, f.rho.max())
+
+
 def test_voxelize_deterministic_bitwise():
     wl = synth.workload(1)
     f = synth.gaussian_field(synth.rng_for(1, 5), 6000, wl.grid, ("loguniform", 0.5, 6.0))
