@@ -244,6 +244,52 @@ int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *me
 int dgr_project_noalloc(const dgr_grid *grid, const dgr_geom *geom, const float *vol,
                         float *sino, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper: a network proposing the initial
+ * Gaussians from a coarse backprojection; the plain initialisation remains
+ * the fallback).  A 3D convolutional encoder-decoder on an n^3 grid (n a
+ * multiple of 4, <= 256), channels 16-32-64-32-16, 3^3 kernels, 2^3 average
+ * pooling and nearest upsampling, additive skips, a 1^3 head to 2 outputs
+ * (density, log-scale in voxels).  Activations and weights BF16 (channels-last
+ * [z][y][x][c]), every convolution accumulating in FP32; the four inner
+ * convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16).
+ * params: FP32 [dgr_net_param_count()], per layer [tap][c_in][c_out] weights
+ * then [c_out] biases.  input: FP32 [n^3]; output: FP32 [n^3][2].
+ * ws: caller-owned device scratch of dgr_net_ws_bytes(n) bytes holding the
+ * activations, so dgr_net_backward must follow the dgr_net_forward it
+ * differentiates on the same ws. */
+long long dgr_net_param_count(void);
+int dgr_net_ws_bytes(int n, size_t *bytes);
+int dgr_net_forward(int n, const float *params, const float *input, float *output, void *ws,
+                    size_t ws_bytes, cudaStream_t stream);
+/* grad_params (FP32, overwritten) = d loss / d params for d loss / d output. */
+int dgr_net_backward(int n, const float *params, const float *input, const float *grad_output,
+                     float *grad_params, void *ws, size_t ws_bytes, cudaStream_t stream);
+/* loss = mean over voxels of w_density (y0 - t0)^2 + w_scale (y1 - t1)^2
+ * (device scalar) and grad_output = d loss / d output. */
+int dgr_net_loss(int n, const float *output, const float *target, float w_density, float w_scale,
+                 float *grad_output, float *loss, void *ws, size_t ws_bytes, cudaStream_t stream);
+/* Textbook Adam on a flat FP32 array (step t >= 1, host int). */
+int dgr_adam_flat(long long n, float *params, const float *grads, float *m, float *v, int t,
+                  float lr, float beta1, float beta2, float eps, cudaStream_t stream);
+/* FDK-style filtering of projections for the network input: each detector
+ * row is cosine-weighted (cone: dsd / sqrt(dsd^2 + u^2 + v^2)) and convolved
+ * with the Ram-Lak ramp kernel; out has the sinogram layout. */
+int dgr_fdk_filter(const dgr_geom *geom, const float *sino, float *out, cudaStream_t stream);
+/* Seeding from proposals on a cubic grid: ns voxels drawn with probability
+ * proportional to max(density, 0) (u: uniform [0,1) per seed, given), mu = the
+ * voxel centre + jitter * h (jitter in [-1/2, 1/2)^3, given), isotropic s =
+ * clamp(exp(log_scale), 0.3, 8) h, q = identity, rho = density; voxel[i] = the
+ * drawn voxel.  scratch: dgr_seed_bytes(n) bytes of device memory. */
+int dgr_seed_bytes(int n_side, size_t *bytes);
+int dgr_seed(const dgr_grid *grid, const float *density, const float *log_scale, int ns,
+             const float *u, const float *jitter, float *mu, float *s, float *q, float *rho,
+             int *voxel, void *scratch, size_t scratch_bytes, cudaStream_t stream);
+/* rho[i] *= clamp(density / vol, 1/4, 4) at each seed's voxel (a fixed-point
+ * step matching the seeds' voxelized field vol to the proposed density). */
+int dgr_seed_rescale(int ns, const int *voxel, const float *density, const float *vol, float *rho,
+                     cudaStream_t stream);
+
 /* Total number of kernels this library has launched in this process (a host
  * counter; lets callers count launches inside a timed region). */
 long long dgr_launch_count(void);

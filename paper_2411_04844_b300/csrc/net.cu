@@ -1,0 +1,841 @@
+// Warm-start network: a small 3D convolutional encoder-decoder that maps a
+// coarse backprojection (n^3, one channel) to per-voxel (density, log-scale)
+// proposals used to seed the Gaussians.  (A learned initialisation is not part
+// of the paper; it sits on top of the method.)
+//
+//   a1 = relu(conv3(x, 1->16) + b1)                  n^3       (CUDA cores)
+//   a2 = relu(conv3(pool(a1), 16->32) + b2)          (n/2)^3   (tensor cores)
+//   a3 = relu(conv3(pool(a2), 32->64) + b3)          (n/4)^3   (tensor cores)
+//   a4 = relu(conv3(up(a3), 64->32) + b4 + a2)       (n/2)^3   (tensor cores)
+//   a5 = relu(conv3(up(a4), 32->16) + b5 + a1)       n^3       (tensor cores)
+//   y  = conv1(a5, 16->2) + b6                       n^3 x 2   (CUDA cores)
+// pool: 2^3 average; up: 2^3 nearest.  Activations are BF16, channels-last
+// ([z][y][x][c]); every convolution accumulates in FP32.
+//
+// The tensor-core convolutions are implicit GEMMs on mma.sync m16n8k16 (BF16
+// operands, FP32 accumulators) with operands gathered into shared memory:
+//   forward      C[p][co] = sum_{tap,ci} X[p + tap][ci] W[tap][ci][co]
+//   data grad    C[p][ci] = sum_{tap,co} G[p - tap][co] W[tap][ci][co]
+//   weight grad  C[tap*Ci + ci][co] = sum_p X[p + tap][ci] G[p][co]
+//                (split over voxel ranges; partials summed in a fixed order)
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include "dgr_internal.cuh"
+
+namespace dgr {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int GM = 64;       // GEMM tile rows per CTA
+constexpr int GK = 32;       // GEMM K step
+constexpr int KPAD = GK + 8; // shared-memory row pitch (bf16), 80 bytes
+constexpr int GEMM_THREADS = 128;
+constexpr int WG_SPLIT = 4096;  // voxels per weight-gradient split
+
+enum { MODE_FWD = 0, MODE_DGRAD = 1, MODE_WGRAD = 2 };
+
+struct ConvArgs {
+    int n;            // grid side of the convolution (cubic, voxels)
+    int ci, co;       // input / output channels
+    const bf16 *x;    // FWD/WGRAD: input activations [n^3][ci]; DGRAD: output grads [n^3][co]
+    const bf16 *w;    // [27][ci][co]
+    const float *bias;  // FWD: [co]
+    const bf16 *skip;   // FWD: optional residual [n^3][co]
+    const bf16 *g;    // WGRAD: output grads [n^3][co]
+    bf16 *y;          // FWD: output [n^3][co]
+    float *out;       // DGRAD: [n^3][ci] FP32; WGRAD: partials [splits][27*ci][co]
+};
+
+__device__ __forceinline__ void tap_offset(int tap, int &dx, int &dy, int &dz) {
+    dz = tap / 9 - 1;
+    dy = (tap / 3) % 3 - 1;
+    dx = tap % 3 - 1;
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3,
+                                        const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One CTA: GM rows x BN columns of C, K in steps of GK.  Warp w owns rows
+// [16 w, 16 w + 16) and all BN columns.
+template <int MODE, int BN>
+__global__ void __launch_bounds__(GEMM_THREADS) k_conv_gemm(const ConvArgs a) {
+    __shared__ __align__(16) bf16 As[GM][KPAD];
+    __shared__ __align__(16) bf16 Bs[BN][KPAD];
+    const int n = a.n, n3 = n * n * n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // GEMM dimensions
+    int M, K, kb, ke;
+    const int m0 = blockIdx.x * GM;
+    if (MODE == MODE_FWD) { M = n3; K = 27 * a.ci; kb = 0; ke = K; }
+    else if (MODE == MODE_DGRAD) { M = n3; K = 27 * a.co; kb = 0; ke = K; }
+    else { M = 27 * a.ci; K = n3; kb = blockIdx.y * WG_SPLIT; ke = min(K, kb + WG_SPLIT); }
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+    for (int k0 = kb; k0 < ke; k0 += GK) {
+        __syncthreads();
+        // gather A (GM x GK)
+        for (int e = threadIdx.x; e < GM * GK; e += GEMM_THREADS) {
+            const int r = e / GK, c = e % GK;
+            const int m = m0 + r, k = k0 + c;
+            bf16 v = __float2bfloat16(0.f);
+            if (m < M && k < ke) {
+                if (MODE == MODE_FWD || MODE == MODE_DGRAD) {
+                    const int C = MODE == MODE_FWD ? a.ci : a.co;
+                    const int tap = k / C, ch = k % C;
+                    int dx, dy, dz;
+                    tap_offset(tap, dx, dy, dz);
+                    if (MODE == MODE_DGRAD) { dx = -dx; dy = -dy; dz = -dz; }
+                    const int px = m % n, py = (m / n) % n, pz = m / (n * n);
+                    const int qx = px + dx, qy = py + dy, qz = pz + dz;
+                    if (qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n)
+                        v = a.x[((size_t)(qz * n + qy) * n + qx) * C + ch];
+                } else {
+                    const int tap = m / a.ci, ch = m % a.ci;
+                    int dx, dy, dz;
+                    tap_offset(tap, dx, dy, dz);
+                    const int px = k % n, py = (k / n) % n, pz = k / (n * n);
+                    const int qx = px + dx, qy = py + dy, qz = pz + dz;
+                    if (qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n)
+                        v = a.x[((size_t)(qz * n + qy) * n + qx) * a.ci + ch];
+                }
+            }
+            As[r][c] = v;
+        }
+        // gather B (stored [BN][GK], k contiguous)
+        for (int e = threadIdx.x; e < BN * GK; e += GEMM_THREADS) {
+            const int nn = e / GK, c = e % GK;
+            const int k = k0 + c;
+            bf16 v = __float2bfloat16(0.f);
+            if (k < ke) {
+                if (MODE == MODE_FWD) {
+                    const int tap = k / a.ci, ch = k % a.ci;
+                    if (nn < a.co) v = a.w[((size_t)tap * a.ci + ch) * a.co + nn];
+                } else if (MODE == MODE_DGRAD) {
+                    const int tap = k / a.co, ch = k % a.co;
+                    if (nn < a.ci) v = a.w[((size_t)tap * a.ci + nn) * a.co + ch];
+                } else {
+                    if (nn < a.co) v = a.g[(size_t)k * a.co + nn];
+                }
+            }
+            Bs[nn][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; kk += 16) {
+            uint32_t af[4];
+            {
+                const int q = lane >> 3, rr = lane & 7;
+                const bf16 *p = &As[16 * w + rr + (q & 1) * 8][kk + (q >> 1) * 8];
+                ldsm_x4(af[0], af[1], af[2], af[3], p);
+            }
+#pragma unroll
+            for (int j = 0; j < BN / 8; ++j) {
+                uint32_t bfr[2];
+                const int q = (lane >> 3) & 1, rr = lane & 7;
+                const bf16 *p = &Bs[8 * j + rr][kk + q * 8];
+                ldsm_x2(bfr[0], bfr[1], p);
+                mma_bf16(acc[j], af, bfr);
+            }
+        }
+    }
+    // epilogue
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = m0 + 16 * w + g + 8 * h;
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2) {
+                const int col = 8 * j + 2 * t4 + c2;
+                const float v = acc[j][2 * h + c2];
+                if (m >= M) continue;
+                if (MODE == MODE_FWD) {
+                    if (col >= a.co) continue;
+                    float z = v + a.bias[col];
+                    if (a.skip) z += __bfloat162float(a.skip[(size_t)m * a.co + col]);
+                    a.y[(size_t)m * a.co + col] = __float2bfloat16(fmaxf(z, 0.f));
+                } else if (MODE == MODE_DGRAD) {
+                    if (col >= a.ci) continue;
+                    a.out[(size_t)m * a.ci + col] = v;
+                } else {
+                    if (col >= a.co) continue;
+                    a.out[((size_t)blockIdx.y * M + m) * a.co + col] = v;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core layers and elementwise kernels
+// ---------------------------------------------------------------------------
+// first layer: 1 -> 16 channels, input FP32
+__global__ void k_conv1_fwd(int n, const float *__restrict__ x, const float *__restrict__ w,
+                            const float *__restrict__ b, bf16 *__restrict__ y) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n3 = n * n * n;
+    if (p >= n3) return;
+    const int px = p % n, py = (p / n) % n, pz = p / (n * n);
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = b[c];
+    for (int tap = 0; tap < 27; ++tap) {
+        int dx, dy, dz;
+        tap_offset(tap, dx, dy, dz);
+        const int qx = px + dx, qy = py + dy, qz = pz + dz;
+        if (qx < 0 || qx >= n || qy < 0 || qy >= n || qz < 0 || qz >= n) continue;
+        const float v = x[(qz * n + qy) * n + qx];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = fmaf(v, w[tap * 16 + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) y[(size_t)p * 16 + c] = __float2bfloat16(fmaxf(acc[c], 0.f));
+}
+
+// weight gradient of the first layer: partial sums per block (fixed order)
+__global__ void k_conv1_wgrad(int n, const float *__restrict__ x, const float *__restrict__ gz,
+                              float *__restrict__ part) {
+    // part[block][27*16 + 16]
+    __shared__ float s[27 * 16 + 16];
+    for (int i = threadIdx.x; i < 27 * 16 + 16; i += blockDim.x) s[i] = 0.f;
+    __syncthreads();
+    const int n3 = n * n * n;
+    const int p0 = blockIdx.x * 1024;
+    // each thread owns (tap, c) pairs and loops over the block's voxels
+    for (int i = threadIdx.x; i < 27 * 16 + 16; i += blockDim.x) {
+        float acc = 0.f;
+        if (i < 27 * 16) {
+            const int tap = i / 16, c = i % 16;
+            int dx, dy, dz;
+            tap_offset(tap, dx, dy, dz);
+            for (int p = p0; p < min(n3, p0 + 1024); ++p) {
+                const int px = p % n, py = (p / n) % n, pz = p / (n * n);
+                const int qx = px + dx, qy = py + dy, qz = pz + dz;
+                if (qx < 0 || qx >= n || qy < 0 || qy >= n || qz < 0 || qz >= n) continue;
+                acc = fmaf(x[(qz * n + qy) * n + qx], gz[(size_t)p * 16 + c], acc);
+            }
+        } else {
+            const int c = i - 27 * 16;
+            for (int p = p0; p < min(n3, p0 + 1024); ++p) acc += gz[(size_t)p * 16 + c];
+        }
+        s[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 27 * 16 + 16; i += blockDim.x)
+        part[(size_t)blockIdx.x * (27 * 16 + 16) + i] = s[i];
+}
+
+// head: 1x1 conv 16 -> 2, FP32 output [n^3][2]
+__global__ void k_head_fwd(int n3, const bf16 *__restrict__ a, const float *__restrict__ w,
+                           const float *__restrict__ b, float *__restrict__ y) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n3) return;
+    float o0 = b[0], o1 = b[1];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        const float v = __bfloat162float(a[(size_t)p * 16 + c]);
+        o0 = fmaf(v, w[c * 2 + 0], o0);
+        o1 = fmaf(v, w[c * 2 + 1], o1);
+    }
+    y[(size_t)p * 2] = o0;
+    y[(size_t)p * 2 + 1] = o1;
+}
+
+// head backward: da = gy W^T (FP32 [n^3][16]); partial dW, db per block
+__global__ void k_head_bwd(int n3, const bf16 *__restrict__ a, const float *__restrict__ w,
+                           const float *__restrict__ gy, float *__restrict__ da,
+                           float *__restrict__ part) {
+    __shared__ float s[34 * 8];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;  // 8 warps
+    float loc[34];
+#pragma unroll
+    for (int i = 0; i < 34; ++i) loc[i] = 0.f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += gridDim.x * blockDim.x) {
+        const float g0 = gy[(size_t)p * 2], g1 = gy[(size_t)p * 2 + 1];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float v = __bfloat162float(a[(size_t)p * 16 + c]);
+            da[(size_t)p * 16 + c] = g0 * w[c * 2] + g1 * w[c * 2 + 1];
+            loc[c * 2] = fmaf(v, g0, loc[c * 2]);
+            loc[c * 2 + 1] = fmaf(v, g1, loc[c * 2 + 1]);
+        }
+        loc[32] += g0;
+        loc[33] += g1;
+    }
+#pragma unroll
+    for (int i = 0; i < 34; ++i) {
+        float v = loc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s[i * 8 + wi] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 34) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += s[threadIdx.x * 8 + k];
+        part[(size_t)blockIdx.x * 34 + threadIdx.x] = t;
+    }
+}
+
+// 2^3 average pool, channels-last: [(2m)^3][c] -> [m^3][c]
+__global__ void k_pool(int m, int c, const bf16 *__restrict__ in, bf16 *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)m * m * m * c;
+    if (i >= tot) return;
+    const int ch = (int)(i % c);
+    const long long p = i / c;
+    const int x = (int)(p % m), y = (int)((p / m) % m), z = (int)(p / ((long long)m * m));
+    const int n = 2 * m;
+    float s = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int qx = 2 * x + (d & 1), qy = 2 * y + ((d >> 1) & 1), qz = 2 * z + (d >> 2);
+        s += __bfloat162float(in[((size_t)(qz * n + qy) * n + qx) * c + ch]);
+    }
+    out[i] = __float2bfloat16(0.125f * s);
+}
+
+// 2^3 nearest upsample: [m^3][c] -> [(2m)^3][c]
+__global__ void k_up(int m, int c, const bf16 *__restrict__ in, bf16 *__restrict__ out) {
+    const int n = 2 * m;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)n * n * n * c;
+    if (i >= tot) return;
+    const int ch = (int)(i % c);
+    const long long p = i / c;
+    const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((long long)n * n));
+    out[i] = in[((size_t)((z / 2) * m + y / 2) * m + x / 2) * c + ch];
+}
+
+// gradient through relu(z) = a (a > 0) of the pre-activation, in BF16 for the
+// next tensor-core GEMM, from the FP32 sum of its incoming gradients:
+//   gz = (a > 0) * (g1 + up^T(g2) + pool^T(g3) + g4)  (terms optional)
+// g2: FP32 at twice the resolution (nearest-upsample adjoint: sum of the 8
+// children); g3: FP32 at half the resolution (average-pool adjoint: 1/8).
+__global__ void k_relu_grad(int n, int c, const bf16 *__restrict__ a, const float *__restrict__ g1,
+                            const float *__restrict__ g2, const float *__restrict__ g3,
+                            const float *__restrict__ g4, bf16 *__restrict__ gz_bf,
+                            float *__restrict__ gz_f) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)n * n * n * c;
+    if (i >= tot) return;
+    const int ch = (int)(i % c);
+    const long long p = i / c;
+    const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((long long)n * n));
+    float s = 0.f;
+    if (g1) s += g1[i];
+    if (g4) s += g4[i];
+    if (g2) {
+        const int N2 = 2 * n;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int qx = 2 * x + (d & 1), qy = 2 * y + ((d >> 1) & 1), qz = 2 * z + (d >> 2);
+            s += g2[((size_t)(qz * N2 + qy) * N2 + qx) * c + ch];
+        }
+    }
+    if (g3) {
+        const int h = n / 2;
+        s += 0.125f * g3[((size_t)((z / 2) * h + y / 2) * h + x / 2) * c + ch];
+    }
+    const float gz = __bfloat162float(a[i]) > 0.f ? s : 0.f;
+    if (gz_bf) gz_bf[i] = __float2bfloat16(gz);
+    if (gz_f) gz_f[i] = gz;
+}
+
+// sum over splits (fixed order) and, for biases, over the output positions
+__global__ void k_reduce_parts(int splits, int len, const float *__restrict__ part,
+                               float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * len + i];
+    out[i] = s;
+}
+
+// bias gradient: sum of gz [P][c] over P (block partials, fixed order)
+__global__ void k_bias_part(long long P, int c, const float *__restrict__ gz, float *__restrict__ part) {
+    __shared__ float s[256];
+    const int ch = blockIdx.y;
+    float acc = 0.f;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x)
+        acc += gz[p * c + ch];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * gridDim.y + ch] = s[0];
+}
+
+__global__ void k_to_bf16(long long n, const float *__restrict__ in, bf16 *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float2bfloat16(in[i]);
+}
+
+// loss: mean over voxels of sum_c wt_c (y_c - t_c)^2; gy = d loss / d y
+__global__ void k_mse(long long n3, const float *__restrict__ y, const float *__restrict__ t,
+                      float w0, float w1, float *__restrict__ gy, float *__restrict__ part) {
+    __shared__ float s[256];
+    float acc = 0.f;
+    const float inv = 1.0f / (float)n3;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n3;
+         p += (long long)gridDim.x * blockDim.x) {
+        const float d0 = y[2 * p] - t[2 * p], d1 = y[2 * p + 1] - t[2 * p + 1];
+        acc += w0 * d0 * d0 + w1 * d1 * d1;
+        gy[2 * p] = 2.f * w0 * d0 * inv;
+        gy[2 * p + 1] = 2.f * w1 * d1 * inv;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0] * inv;
+}
+
+__global__ void k_adam_flat(long long n, float *__restrict__ p, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v, float lr, float b1,
+                            float b2, float eps, float bc1, float bc2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+
+// ---------------------------------------------------------------------------
+// FDK-style input and Gaussian seeding
+// ---------------------------------------------------------------------------
+// cosine weight and ramp filter along detector rows (Ram-Lak kernel in the
+// spatial domain: h(0) = 1/(4 p^2), h(odd k) = -1/(pi k p)^2, h(even) = 0,
+// times the pitch): one thread per output pixel, direct convolution.
+__global__ void k_fdk_filter(dgr_geom geo, const float *__restrict__ in, float *__restrict__ out) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)geo.n_views * geo.nv * geo.nu;
+    if (r >= tot) return;
+    const int iu = (int)(r % geo.nu);
+    const long long row = r / geo.nu;
+    const int iv = (int)(row % geo.nv);
+    const float cu = 0.5f * (float)(geo.nu - 1), cv = 0.5f * (float)(geo.nv - 1);
+    const float pu = geo.pu, pi = 3.14159265358979f;
+    const float *src = in + row * geo.nu;
+    const float v = ((float)iv - cv) * geo.pv;
+    float acc = 0.f;
+    for (int j = 0; j < geo.nu; ++j) {
+        const int k = iu - j;
+        float hk;
+        if (k == 0) hk = 1.0f / (4.0f * pu * pu);
+        else if (k & 1) hk = -1.0f / (pi * pi * (float)k * (float)k * pu * pu);
+        else continue;
+        float wgt = 1.f;
+        if (geo.beam == DGR_CONE) {
+            const float u = ((float)j - cu) * pu;
+            wgt = geo.dsd * rsqrtf(geo.dsd * geo.dsd + u * u + v * v);
+        }
+        acc = fmaf(hk * pu, wgt * src[j], acc);
+    }
+    out[r] = acc;
+}
+
+// per-block sums of a non-negative field (FP64) for the sampling CDF
+__global__ void k_cdf_blocks(long long n, const float *__restrict__ d, double *__restrict__ bsum) {
+    __shared__ double s[256];
+    const long long b0 = (long long)blockIdx.x * 4096;
+    double acc = 0.0;
+    for (long long i = b0 + threadIdx.x; i < min(n, b0 + 4096); i += blockDim.x) acc += fmax((double)d[i], 0.0);
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
+}
+
+// exclusive scan of the block sums (one thread, nb <= a few thousand)
+__global__ void k_cdf_scan(int nb, double *__restrict__ bsum) {
+    double run = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        const double v = bsum[i];
+        bsum[i] = run;
+        run += v;
+    }
+    bsum[nb] = run;
+}
+
+// sample voxel k with probability d_k / sum(d): u in [0, 1) per sample;
+// finds the block by binary search over block offsets, then walks the block.
+// Writes mu (voxel centre + jitter in [-h/2, h/2)), isotropic s from
+// exp(log-scale) in voxels (clamped to [0.3, 8]) x h, identity q, rho = d_k.
+__global__ void k_seed(int n_side, float h, float ox, float oy, float oz, const float *__restrict__ d,
+                       const float *__restrict__ logs, const double *__restrict__ boff, int nb,
+                       int ns, const float *__restrict__ u, const float *__restrict__ jit,
+                       float *__restrict__ mu, float *__restrict__ sc, float *__restrict__ q,
+                       float *__restrict__ rho, int *__restrict__ vidx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const long long n3 = (long long)n_side * n_side * n_side;
+    const double target = (double)u[i] * boff[nb];
+    int lo = 0, hi = nb;  // boff[lo] <= target < boff[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (boff[mid] <= target) lo = mid; else hi = mid;
+    }
+    double run = boff[lo];
+    long long k = (long long)lo * 4096;
+    const long long kend = min(n3, k + 4096);
+    long long pick = kend - 1;
+    for (; k < kend; ++k) {
+        run += fmax((double)d[k], 0.0);
+        if (run > target) { pick = k; break; }
+    }
+    const int x = (int)(pick % n_side), y = (int)((pick / n_side) % n_side),
+              z = (int)(pick / ((long long)n_side * n_side));
+    mu[3 * i + 0] = ox + ((float)x + 0.5f + jit[3 * i + 0]) * h;
+    mu[3 * i + 1] = oy + ((float)y + 0.5f + jit[3 * i + 1]) * h;
+    mu[3 * i + 2] = oz + ((float)z + 0.5f + jit[3 * i + 2]) * h;
+    const float sv = fminf(fmaxf(expf(logs[pick]), 0.3f), 8.0f) * h;
+    sc[3 * i] = sc[3 * i + 1] = sc[3 * i + 2] = sv;
+    q[4 * i] = 1.f; q[4 * i + 1] = q[4 * i + 2] = q[4 * i + 3] = 0.f;
+    rho[i] = fmaxf(d[pick], 1e-4f);
+    vidx[i] = (int)pick;
+}
+
+// fixed-point refinement of the seeds' intensities: the voxelized field of
+// the seeds should match the proposed density at the seed voxels
+__global__ void k_seed_rescale(int ns, const int *__restrict__ vidx, const float *__restrict__ d,
+                               const float *__restrict__ vol, float *__restrict__ rho) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const float target = fmaxf(d[vidx[i]], 0.f), cur = vol[vidx[i]];
+    const float f = cur > 1e-6f ? target / cur : 1.f;
+    rho[i] = fmaxf(rho[i] * fminf(fmaxf(f, 0.25f), 4.0f), 1e-5f);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side: parameter layout, workspace layout, forward / backward
+// ---------------------------------------------------------------------------
+namespace net {
+
+struct Layer {
+    int ci, co, taps;
+};
+constexpr Layer L[6] = {{1, 16, 27}, {16, 32, 27}, {32, 64, 27}, {64, 32, 27}, {32, 16, 27}, {16, 2, 1}};
+constexpr int C1_VOX = 1024;  // voxels per block of the first layer's weight gradient
+
+inline size_t w_off(int l) {
+    size_t o = 0;
+    for (int i = 0; i < l; ++i) o += (size_t)L[i].taps * L[i].ci * L[i].co + L[i].co;
+    return o;
+}
+inline size_t b_off(int l) { return w_off(l) + (size_t)L[l].taps * L[l].ci * L[l].co; }
+inline size_t n_params() { return w_off(6); }
+
+struct WS {
+    size_t a1, p1, a2, p2, a3, u2, a4, u1, a5;  // BF16 activations
+    size_t wbf;                                  // BF16 copy of every parameter
+    size_t ga5f, gz5b, gz5f, gu1f, gz4b, gz4f, gu2f, gz3b, gz3f, gp2f, gz2b, gz2f, gp1f, gz1f;
+    size_t part, bpart, lpart;
+    size_t total;
+};
+
+inline WS layout(int n) {
+    WS w;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        const size_t at = o;
+        o = align_up(o + b);
+        return at;
+    };
+    const size_t n3 = (size_t)n * n * n, h3 = n3 / 8, q3 = n3 / 64;
+    w.a1 = take(2 * n3 * 16);
+    w.p1 = take(2 * h3 * 16);
+    w.a2 = take(2 * h3 * 32);
+    w.p2 = take(2 * q3 * 32);
+    w.a3 = take(2 * q3 * 64);
+    w.u2 = take(2 * h3 * 64);
+    w.a4 = take(2 * h3 * 32);
+    w.u1 = take(2 * n3 * 32);
+    w.a5 = take(2 * n3 * 16);
+    w.wbf = take(2 * n_params());
+    w.ga5f = take(4 * n3 * 16);
+    w.gz5b = take(2 * n3 * 16);
+    w.gz5f = take(4 * n3 * 16);
+    w.gu1f = take(4 * n3 * 32);
+    w.gz4b = take(2 * h3 * 32);
+    w.gz4f = take(4 * h3 * 32);
+    w.gu2f = take(4 * h3 * 64);
+    w.gz3b = take(2 * q3 * 64);
+    w.gz3f = take(4 * q3 * 64);
+    w.gp2f = take(4 * q3 * 32);
+    w.gz2b = take(2 * h3 * 32);
+    w.gz2f = take(4 * h3 * 32);
+    w.gp1f = take(4 * h3 * 16);
+    w.gz1f = take(4 * n3 * 16);
+    // weight-gradient partials: the largest of the tensor-core layers' split
+    // partials, the first layer's block partials and the head's
+    size_t pmax = 0;
+    const size_t side3[5] = {n3, h3, q3, h3, n3};
+    for (int l = 1; l <= 4; ++l) {
+        const size_t splits = (side3[l] + WG_SPLIT - 1) / WG_SPLIT;
+        const size_t v = splits * 27 * L[l].ci * L[l].co;
+        pmax = v > pmax ? v : pmax;
+    }
+    const size_t c1 = ((n3 + C1_VOX - 1) / C1_VOX) * (27 * 16 + 16);
+    pmax = c1 > pmax ? c1 : pmax;
+    pmax = (size_t)256 * 34 > pmax ? (size_t)256 * 34 : pmax;
+    w.part = take(4 * pmax);
+    w.bpart = take(4 * 64 * 64);
+    w.lpart = take(4 * 1024);
+    w.total = o;
+    return w;
+}
+
+}  // namespace net
+
+template <int MODE, int BN>
+static void gemm(const ConvArgs &a, int grid_x, int grid_y, cudaStream_t st) {
+    k_conv_gemm<MODE, BN><<<dim3(grid_x, grid_y), GEMM_THREADS, 0, st>>>(a);
+    counted(1);
+}
+
+template <int MODE>
+static void gemm_bn(int bn, const ConvArgs &a, int gx, int gy, cudaStream_t st) {
+    if (bn <= 16) gemm<MODE, 16>(a, gx, gy, st);
+    else if (bn <= 32) gemm<MODE, 32>(a, gx, gy, st);
+    else gemm<MODE, 64>(a, gx, gy, st);
+}
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace dgr
+
+using namespace dgr;
+
+static bool net_side_ok(int n) { return n >= 4 && n % 4 == 0 && n <= 256; }
+
+extern "C" {
+
+long long dgr_net_param_count(void) { return (long long)net::n_params(); }
+
+int dgr_net_ws_bytes(int n, size_t *bytes) {
+    if (!net_side_ok(n) || !bytes) return DGR_ERR_ARG;
+    *bytes = net::layout(n).total;
+    return DGR_OK;
+}
+
+int dgr_net_forward(int n, const float *params, const float *input, float *output, void *ws,
+                    size_t ws_bytes, cudaStream_t st) {
+    if (!net_side_ok(n) || !params || !input || !output || !ws) return DGR_ERR_ARG;
+    const net::WS W = net::layout(n);
+    if (ws_bytes < W.total) return DGR_ERR_WS_TOO_SMALL;
+    char *base = static_cast<char *>(ws);
+    auto B = [&](size_t off) { return reinterpret_cast<bf16 *>(base + off); };
+    const int h = n / 2, q = n / 4;
+    const long long n3 = (long long)n * n * n, h3 = n3 / 8, q3 = n3 / 64;
+    bf16 *wbf = B(W.wbf);
+    const long long np = (long long)net::n_params();
+    k_to_bf16<<<nblk(np, 256), 256, 0, st>>>(np, params, wbf);
+    k_conv1_fwd<<<nblk(n3, 128), 128, 0, st>>>(n, input, params + net::w_off(0),
+                                                params + net::b_off(0), B(W.a1));
+    k_pool<<<nblk(h3 * 16, 256), 256, 0, st>>>(h, 16, B(W.a1), B(W.p1));
+    counted(3);
+    auto conv = [&](int l, int side, const bf16 *x, const bf16 *skip, bf16 *y) {
+        ConvArgs a{};
+        a.n = side; a.ci = net::L[l].ci; a.co = net::L[l].co;
+        a.x = x; a.w = wbf + net::w_off(l); a.bias = params + net::b_off(l); a.skip = skip; a.y = y;
+        const long long s3 = (long long)side * side * side;
+        gemm_bn<MODE_FWD>(a.co, a, (int)nblk(s3, GM), 1, st);
+    };
+    conv(1, h, B(W.p1), nullptr, B(W.a2));
+    k_pool<<<nblk(q3 * 32, 256), 256, 0, st>>>(q, 32, B(W.a2), B(W.p2));
+    conv(2, q, B(W.p2), nullptr, B(W.a3));
+    k_up<<<nblk(h3 * 64, 256), 256, 0, st>>>(q, 64, B(W.a3), B(W.u2));
+    conv(3, h, B(W.u2), B(W.a2), B(W.a4));
+    k_up<<<nblk(n3 * 32, 256), 256, 0, st>>>(h, 32, B(W.a4), B(W.u1));
+    conv(4, n, B(W.u1), B(W.a1), B(W.a5));
+    k_head_fwd<<<nblk(n3, 256), 256, 0, st>>>((int)n3, B(W.a5), params + net::w_off(5),
+                                               params + net::b_off(5), output);
+    counted(4);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_net_backward(int n, const float *params, const float *input, const float *grad_output,
+                     float *grad_params, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (!net_side_ok(n) || !params || !input || !grad_output || !grad_params || !ws)
+        return DGR_ERR_ARG;
+    const net::WS W = net::layout(n);
+    if (ws_bytes < W.total) return DGR_ERR_WS_TOO_SMALL;
+    char *base = static_cast<char *>(ws);
+    auto B = [&](size_t off) { return reinterpret_cast<bf16 *>(base + off); };
+    auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
+    const int h = n / 2, q = n / 4;
+    const long long n3 = (long long)n * n * n, h3 = n3 / 8, q3 = n3 / 64;
+    const bf16 *wbf = B(W.wbf);
+    float *part = F(W.part), *bpart = F(W.bpart);
+    // head: dL/da5, dW6, db6
+    k_head_bwd<<<256, 256, 0, st>>>((int)n3, B(W.a5), params + net::w_off(5), grad_output,
+                                    F(W.ga5f), part);
+    k_reduce_parts<<<1, 64, 0, st>>>(256, 34, part, grad_params + net::w_off(5));
+    counted(2);
+    // weight and bias gradients of tensor-core layer l (input x at side^3)
+    auto wgrad = [&](int l, int side, const bf16 *x, const bf16 *gz_b, const float *gz_f) {
+        const int ci = net::L[l].ci, co = net::L[l].co;
+        const long long s3 = (long long)side * side * side;
+        ConvArgs a{};
+        a.n = side; a.ci = ci; a.co = co; a.x = x; a.g = gz_b; a.out = part;
+        const int splits = (int)nblk(s3, WG_SPLIT);
+        gemm_bn<MODE_WGRAD>(co, a, (int)nblk(27 * ci, GM), splits, st);
+        k_reduce_parts<<<nblk(27 * ci * co, 256), 256, 0, st>>>(splits, 27 * ci * co, part,
+                                                                grad_params + net::w_off(l));
+        k_bias_part<<<dim3(64, co), 256, 0, st>>>(s3, co, gz_f, bpart);
+        k_reduce_parts<<<1, 64, 0, st>>>(64, co, bpart, grad_params + net::b_off(l));
+        counted(3);
+    };
+    auto dgrad = [&](int l, int side, const bf16 *gz_b, float *gx) {
+        ConvArgs d{};
+        d.n = side; d.ci = net::L[l].ci; d.co = net::L[l].co; d.x = gz_b; d.w = wbf + net::w_off(l);
+        d.out = gx;
+        const long long s3 = (long long)side * side * side;
+        gemm_bn<MODE_DGRAD>(d.ci, d, (int)nblk(s3, GM), 1, st);
+    };
+    // layer 5: a5 = relu(conv(u1) + b5 + a1)
+    k_relu_grad<<<nblk(n3 * 16, 256), 256, 0, st>>>(n, 16, B(W.a5), F(W.ga5f), nullptr, nullptr,
+                                                   nullptr, B(W.gz5b), F(W.gz5f));
+    counted(1);
+    wgrad(4, n, B(W.u1), B(W.gz5b), F(W.gz5f));
+    dgrad(4, n, B(W.gz5b), F(W.gu1f));
+    // layer 4: a4 = relu(conv(up(a3)) + b4 + a2); its gradient is up^T(gu1)
+    k_relu_grad<<<nblk(h3 * 32, 256), 256, 0, st>>>(h, 32, B(W.a4), nullptr, F(W.gu1f), nullptr,
+                                                   nullptr, B(W.gz4b), F(W.gz4f));
+    counted(1);
+    wgrad(3, h, B(W.u2), B(W.gz4b), F(W.gz4f));
+    dgrad(3, h, B(W.gz4b), F(W.gu2f));
+    // layer 3: a3 = relu(conv(pool(a2)) + b3); gradient up^T(gu2)
+    k_relu_grad<<<nblk(q3 * 64, 256), 256, 0, st>>>(q, 64, B(W.a3), nullptr, F(W.gu2f), nullptr,
+                                                   nullptr, B(W.gz3b), F(W.gz3f));
+    counted(1);
+    wgrad(2, q, B(W.p2), B(W.gz3b), F(W.gz3f));
+    dgrad(2, q, B(W.gz3b), F(W.gp2f));
+    // layer 2: a2 = relu(conv(pool(a1)) + b2); gradient: skip of layer 4 + pool^T(gp2)
+    k_relu_grad<<<nblk(h3 * 32, 256), 256, 0, st>>>(h, 32, B(W.a2), F(W.gz4f), nullptr, F(W.gp2f),
+                                                   nullptr, B(W.gz2b), F(W.gz2f));
+    counted(1);
+    wgrad(1, h, B(W.p1), B(W.gz2b), F(W.gz2f));
+    dgrad(1, h, B(W.gz2b), F(W.gp1f));
+    // layer 1: a1 = relu(conv(x) + b1); gradient: skip of layer 5 + pool^T(gp1)
+    k_relu_grad<<<nblk(n3 * 16, 256), 256, 0, st>>>(n, 16, B(W.a1), F(W.gz5f), nullptr, F(W.gp1f),
+                                                   nullptr, nullptr, F(W.gz1f));
+    const unsigned c1b = nblk(n3, net::C1_VOX);
+    k_conv1_wgrad<<<c1b, 256, 0, st>>>(n, input, F(W.gz1f), part);
+    k_reduce_parts<<<nblk(27 * 16 + 16, 256), 256, 0, st>>>((int)c1b, 27 * 16 + 16, part,
+                                                            grad_params + net::w_off(0));
+    counted(3);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+// loss = mean over voxels of w0 (y0 - t0)^2 + w1 (y1 - t1)^2 and its gradient
+int dgr_net_loss(int n, const float *output, const float *target, float w_density, float w_scale,
+                 float *grad_output, float *loss, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (!net_side_ok(n) || !output || !target || !grad_output || !loss || !ws) return DGR_ERR_ARG;
+    const net::WS W = net::layout(n);
+    if (ws_bytes < W.total) return DGR_ERR_WS_TOO_SMALL;
+    float *lp = reinterpret_cast<float *>(static_cast<char *>(ws) + W.lpart);
+    const long long n3 = (long long)n * n * n;
+    k_mse<<<256, 256, 0, st>>>(n3, output, target, w_density, w_scale, grad_output, lp);
+    k_reduce_parts<<<1, 32, 0, st>>>(256, 1, lp, loss);
+    counted(2);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_adam_flat(long long n, float *params, const float *grads, float *m, float *v, int t,
+                  float lr, float beta1, float beta2, float eps, cudaStream_t st) {
+    if (n < 0 || t < 1 || !(lr > 0.f) || (n > 0 && (!params || !grads || !m || !v))) return DGR_ERR_ARG;
+    if (n == 0) return DGR_OK;
+    const float bc1 = 1.f - powf(beta1, (float)t), bc2 = 1.f - powf(beta2, (float)t);
+    k_adam_flat<<<nblk(n, 256), 256, 0, st>>>(n, params, grads, m, v, lr, beta1, beta2, eps, bc1, bc2);
+    counted(1);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_fdk_filter(const dgr_geom *geom, const float *sino, float *out, cudaStream_t st) {
+    if (!geom || !sino || !out || geom->n_views <= 0 || geom->nu <= 0 || geom->nv <= 0) return DGR_ERR_ARG;
+    if (geom->beam != DGR_PARALLEL && geom->beam != DGR_CONE) return DGR_ERR_ARG;
+    const long long tot = (long long)geom->n_views * geom->nv * geom->nu;
+    k_fdk_filter<<<nblk(tot, 128), 128, 0, st>>>(*geom, sino, out);
+    counted(1);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+// scratch: doubles of (n^3 / 4096 + 2)
+int dgr_seed_bytes(int n_side, size_t *bytes) {
+    if (n_side <= 0 || !bytes) return DGR_ERR_ARG;
+    const long long n3 = (long long)n_side * n_side * n_side;
+    *bytes = 8 * (size_t)((n3 + 4095) / 4096 + 2);
+    return DGR_OK;
+}
+
+int dgr_seed(const dgr_grid *grid, const float *density, const float *log_scale, int ns,
+             const float *u, const float *jitter, float *mu, float *s, float *q, float *rho,
+             int *voxel, void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    if (!grid || grid->nx <= 0 || grid->nx != grid->ny || grid->nx != grid->nz || ns < 0) return DGR_ERR_ARG;
+    if (ns > 0 && (!density || !log_scale || !u || !jitter || !mu || !s || !q || !rho || !voxel || !scratch))
+        return DGR_ERR_ARG;
+    const long long n3 = (long long)grid->nx * grid->nx * grid->nx;
+    const int nb = (int)((n3 + 4095) / 4096);
+    if (scratch_bytes < 8 * (size_t)(nb + 2)) return DGR_ERR_WS_TOO_SMALL;
+    if (ns == 0) return DGR_OK;
+    double *boff = static_cast<double *>(scratch);
+    k_cdf_blocks<<<nb, 256, 0, st>>>(n3, density, boff);
+    k_cdf_scan<<<1, 1, 0, st>>>(nb, boff);
+    k_seed<<<nblk(ns, 128), 128, 0, st>>>(grid->nx, grid->h, grid->ox, grid->oy, grid->oz, density,
+                                           log_scale, boff, nb, ns, u, jitter, mu, s, q, rho, voxel);
+    counted(3);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_seed_rescale(int ns, const int *voxel, const float *density, const float *vol, float *rho,
+                     cudaStream_t st) {
+    if (ns < 0 || (ns > 0 && (!voxel || !density || !vol || !rho))) return DGR_ERR_ARG;
+    if (ns == 0) return DGR_OK;
+    k_seed_rescale<<<nblk(ns, 128), 128, 0, st>>>(ns, voxel, density, vol, rho);
+    counted(1);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+}  // extern "C"

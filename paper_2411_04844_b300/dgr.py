@@ -35,6 +35,9 @@ EXPORTS = [
     "dgr_voxelize", "dgr_voxelize_backward", "dgr_project", "dgr_backproject",
     "dgr_l1_residual", "dgr_params_init", "dgr_step", "dgr_step_timed", "dgr_launch_count",
     "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth",
+    "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
+    "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
+    "dgr_seed_rescale",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -137,11 +140,23 @@ def lib():
             "dgr_project_noalloc": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P],
             "dgr_step_batched": [i, ctypes.POINTER(Problem), ctypes.POINTER(Params),
                                  ctypes.POINTER(P), P, P, P],
+            "dgr_net_ws_bytes": [i, ctypes.POINTER(ctypes.c_size_t)],
+            "dgr_net_forward": [i, P, P, P, P, ctypes.c_size_t, P],
+            "dgr_net_backward": [i, P, P, P, P, P, ctypes.c_size_t, P],
+            "dgr_net_loss": [i, P, P, f, f, P, P, P, ctypes.c_size_t, P],
+            "dgr_adam_flat": [ll, P, P, P, P, i, f, f, f, f, P],
+            "dgr_fdk_filter": [ctypes.POINTER(Geom), P, P, P],
+            "dgr_seed_bytes": [i, ctypes.POINTER(ctypes.c_size_t)],
+            "dgr_seed": [ctypes.POINTER(Grid), P, P, i, P, P, P, P, P, P, P, P,
+                         ctypes.c_size_t, P],
+            "dgr_seed_rescale": [i, P, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        L.dgr_net_param_count.argtypes = []
+        L.dgr_net_param_count.restype = ctypes.c_longlong
         L.dgr_launch_count.argtypes = []
         L.dgr_launch_count.restype = ctypes.c_longlong
         L.dgr_strerror.argtypes = [i]
@@ -405,3 +420,79 @@ def make_batch_plan(grids, geoms, ns, pairs, items) -> WsPlan:
     p.max_nv = int(max(ge.nv for ge in geoms))
     p.max_inst = len(grids)
     return p
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+# ---------------------------------------------------------------------------
+def dgr_net_param_count() -> int:
+    return int(lib().dgr_net_param_count())
+
+
+def dgr_net_ws_bytes(n: int) -> int:
+    b = ctypes.c_size_t()
+    _rc(lib().dgr_net_ws_bytes(int(n), ctypes.byref(b)), "dgr_net_ws_bytes")
+    return int(b.value)
+
+
+def dgr_net_forward(n, params, inp, out, ws, stream=None):
+    for t, nm in ((params, "params"), (inp, "input"), (out, "output")):
+        _check(t, nm)
+    _rc(lib().dgr_net_forward(int(n), _ptr(params), _ptr(inp), _ptr(out), _ptr(ws),
+                              ws.numel() * ws.element_size(), _stream(stream)), "dgr_net_forward")
+
+
+def dgr_net_backward(n, params, inp, grad_out, grad_params, ws, stream=None):
+    for t, nm in ((params, "params"), (inp, "input"), (grad_out, "grad_output"),
+                  (grad_params, "grad_params")):
+        _check(t, nm)
+    _rc(lib().dgr_net_backward(int(n), _ptr(params), _ptr(inp), _ptr(grad_out), _ptr(grad_params),
+                               _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+        "dgr_net_backward")
+
+
+def dgr_net_loss(n, out, target, w_density, w_scale, grad_out, loss, ws, stream=None):
+    for t, nm in ((out, "output"), (target, "target"), (grad_out, "grad_output"), (loss, "loss")):
+        _check(t, nm)
+    _rc(lib().dgr_net_loss(int(n), _ptr(out), _ptr(target), float(w_density), float(w_scale),
+                           _ptr(grad_out), _ptr(loss), _ptr(ws), ws.numel() * ws.element_size(),
+                           _stream(stream)), "dgr_net_loss")
+
+
+def dgr_adam_flat(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    for x, nm in ((params, "params"), (grads, "grads"), (m, "m"), (v, "v")):
+        _check(x, nm)
+    _rc(lib().dgr_adam_flat(params.numel(), _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(t),
+                            float(lr), float(beta1), float(beta2), float(eps), _stream(stream)),
+        "dgr_adam_flat")
+
+
+def dgr_fdk_filter(geom: Geom, sino, out, stream=None):
+    _check(sino, "sino"); _check(out, "out")
+    _rc(lib().dgr_fdk_filter(ctypes.byref(geom), _ptr(sino), _ptr(out), _stream(stream)),
+        "dgr_fdk_filter")
+
+
+def dgr_seed(grid: Grid, density, log_scale, u, jitter, mu, s, q, rho, voxel, scratch, stream=None):
+    for t, nm in ((density, "density"), (log_scale, "log_scale"), (u, "u"), (jitter, "jitter"),
+                  (mu, "mu"), (s, "s"), (q, "q"), (rho, "rho")):
+        _check(t, nm)
+    _check(voxel, "voxel", torch.int32)
+    _rc(lib().dgr_seed(ctypes.byref(grid), _ptr(density), _ptr(log_scale), u.numel(), _ptr(u),
+                       _ptr(jitter), _ptr(mu), _ptr(s), _ptr(q), _ptr(rho), _ptr(voxel),
+                       _ptr(scratch), scratch.numel() * scratch.element_size(), _stream(stream)),
+        "dgr_seed")
+
+
+def dgr_seed_bytes(n_side: int) -> int:
+    b = ctypes.c_size_t()
+    _rc(lib().dgr_seed_bytes(int(n_side), ctypes.byref(b)), "dgr_seed_bytes")
+    return int(b.value)
+
+
+def dgr_seed_rescale(voxel, density, vol, rho, stream=None):
+    _check(voxel, "voxel", torch.int32)
+    for t, nm in ((density, "density"), (vol, "vol"), (rho, "rho")):
+        _check(t, nm)
+    _rc(lib().dgr_seed_rescale(rho.numel(), _ptr(voxel), _ptr(density), _ptr(vol), _ptr(rho),
+                               _stream(stream)), "dgr_seed_rescale")

@@ -249,3 +249,47 @@ def batched_workload(n_inst: int = 16, config: int = 4, sizes=(64, 128, 192, 256
         f.rho = np.clip(f.rho, 0.02, 1.0).astype(np.float32)
         out.append(Instance(grid, geom, f))
     return out
+
+
+def ellipsoid_phantom_torch(rng, grid: GridSpec, m: int, device="cuda"):
+    """ellipsoid_phantom with the same random draws, rasterised with torch on
+    the device (for large training sets).  Returns a float32 tensor."""
+    import torch
+    nx, ny, nz = grid.dims
+    ext = np.array(grid.extent)
+    org = np.array(grid.org)
+    centre = org + 0.5 * ext
+    vol = torch.zeros(grid.shape, dtype=torch.float32, device=device)
+    for _ in range(m):
+        while True:
+            p = rng.uniform(-1, 1, 3)
+            if p @ p <= 1:
+                break
+        c = centre + 0.6 * 0.5 * ext * p
+        ax = rng.uniform(0.05, 0.35, 3) * ext
+        qn = random_quaternions(rng, 1)[0].astype(np.float64)
+        R = _rot(qn)
+        dens = rng.uniform(0, 1)
+        hw = np.sqrt(((R * ax[None, :]) ** 2).sum(1))
+        lo = np.maximum(np.floor((c - hw - org) / grid.h - 0.5).astype(int), 0)
+        hi = np.minimum(np.ceil((c + hw - org) / grid.h - 0.5).astype(int), [nx - 1, ny - 1, nz - 1])
+        if np.any(hi < lo):
+            continue
+        ar = lambda a: torch.arange(lo[a], hi[a] + 1, device=device, dtype=torch.float64)
+        xs = org[0] + (ar(0) + 0.5) * grid.h - c[0]
+        ys = org[1] + (ar(1) + 0.5) * grid.h - c[1]
+        zs = org[2] + (ar(2) + 0.5) * grid.h - c[2]
+        Z, Y, X = torch.meshgrid(zs, ys, xs, indexing="ij")
+        P = torch.stack([X, Y, Z], -1) @ torch.as_tensor(R, device=device)
+        inside = ((P / torch.as_tensor(ax, device=device)) ** 2).sum(-1) <= 1.0
+        vol[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] += float(dens) * inside.float()
+    return vol.clamp_(0.0, 1.0)
+
+
+def learned_workload(side=128, views=50):
+    """Warm-start study: side^3 grid (h = 1 mm, centred), cone beam with `views`
+    views over 360 deg, side x side detector of pitch 1.5 mm (source-origin 1000 mm,
+    source-detector 1500 mm), 40-ellipsoid phantoms, N(0, 0.01^2) noise."""
+    grid = GridSpec.centred(side, 1.0)
+    geom = cone_geom(views, side, side, 1.5, 1.5, 1000.0, 1500.0)
+    return grid, geom

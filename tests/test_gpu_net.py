@@ -1,0 +1,127 @@
+"""Warm-start network on the tensor cores (row a11) against its FP64 oracle:
+forward and every parameter gradient, the loss, Adam on flat arrays, the
+FDK-style filter and the seeding kernels.
+
+Tolerances: the oracle rounds to BF16 where the kernels store BF16, so the
+remaining differences are FP32-vs-FP64 accumulation order and the rare ReLU
+decision it flips: output relative L2 <= 2e-3, gradient relative L2 per layer
+<= 2e-2."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from oracle import net as N
+from paper_2411_04844_b300 import dgr, synth
+from tests._common import oracle_geom, rel_l2
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def T(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def init_params(rng):
+    parts = []
+    for ci, co, t in N.LAYERS:
+        parts.append(rng.standard_normal(t * ci * co) * np.sqrt(2.0 / (t * ci)))
+        parts.append(rng.uniform(-0.1, 0.1, co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_net_forward_and_gradients_match_oracle(n):
+    assert dgr.dgr_net_param_count() == N.n_params()
+    rng = np.random.default_rng(n)
+    P = init_params(rng)
+    x = rng.uniform(0, 1, (n, n, n)).astype(np.float32)
+    gy = rng.standard_normal((n, n, n, 2)).astype(np.float32)
+    ws = torch.empty(dgr.dgr_net_ws_bytes(n), dtype=torch.uint8, device=DEV)
+    out = torch.empty((n, n, n, 2), device=DEV)
+    gp = torch.full((N.n_params(),), float("nan"), device=DEV)
+    Pt, xt = T(P), T(x)
+    dgr.dgr_net_forward(n, Pt, xt, out, ws)
+    dgr.dgr_net_backward(n, Pt, xt, T(gy), gp, ws)
+    torch.cuda.synchronize()
+    yo, _ = N.forward(P.astype(np.float64), x, bf=True)
+    assert rel_l2(out.cpu().numpy(), yo) <= 2e-3, rel_l2(out.cpu().numpy(), yo)
+    go = N.backward(P.astype(np.float64), x, gy, bf=True)
+    g = gp.cpu().numpy()
+    assert np.isfinite(g).all()
+    o = 0
+    for l, (ci, co, t) in enumerate(N.LAYERS):
+        for name, sz in (("w", t * ci * co), ("b", co)):
+            e = rel_l2(g[o:o + sz], go[o:o + sz])
+            assert e <= 2e-2, (l, name, e)
+            o += sz
+
+
+def test_net_loss_and_adam():
+    n = 8
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((n, n, n, 2)).astype(np.float32)
+    t = rng.standard_normal((n, n, n, 2)).astype(np.float32)
+    ws = torch.empty(dgr.dgr_net_ws_bytes(n), dtype=torch.uint8, device=DEV)
+    gy = torch.empty_like(T(y)); loss = torch.zeros(1, device=DEV)
+    dgr.dgr_net_loss(n, T(y), T(t), 1.0, 0.25, gy, loss, ws)
+    torch.cuda.synchronize()
+    d = y.astype(np.float64) - t
+    ref = (d[..., 0] ** 2 + 0.25 * d[..., 1] ** 2).mean()
+    assert abs(float(loss) - ref) <= 1e-5 * ref
+    gref = np.stack([2 * d[..., 0], 0.5 * d[..., 1]], -1) / n ** 3
+    assert rel_l2(gy.cpu().numpy(), gref) <= 1e-6
+    p = rng.standard_normal(1000).astype(np.float32)
+    th = {"a": p.astype(np.float64)}; m = {"a": np.zeros(1000)}; v = {"a": np.zeros(1000)}
+    pt, mt, vt = T(p), torch.zeros(1000, device=DEV), torch.zeros(1000, device=DEV)
+    for step in range(1, 4):
+        gr = rng.standard_normal(1000).astype(np.float32)
+        th = O.adam_update(th, {"a": gr.astype(np.float64)}, m, v, step, 1e-3)
+        dgr.dgr_adam_flat(pt, T(gr), mt, vt, step, 1e-3)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(pt.cpu().numpy() - th["a"])) <= 1e-6
+
+
+def test_fdk_filter_matches_oracle():
+    geo = synth.cone_geom(5, 33, 21, 1.3, 1.1, 80.0, 140.0)
+    sino = np.random.default_rng(6).standard_normal(geo.shape).astype(np.float32)
+    ang = T(geo.angles)
+    gg = dgr.Geom.of(geo, ang)
+    out = torch.empty(geo.shape, device=DEV)
+    dgr.dgr_fdk_filter(gg, T(sino), out)
+    torch.cuda.synchronize()
+    ref = N.ramlak_filter(sino, geo.pu, 1, dsd=geo.dsd, pv=geo.pv)
+    assert rel_l2(out.cpu().numpy(), ref) <= 1e-5
+
+
+def test_seeding_draws_from_the_density():
+    n = 16
+    gs = synth.GridSpec.centred(n, 1.0)
+    grid = dgr.Grid.of(gs)
+    rng = np.random.default_rng(7)
+    dens = np.zeros((n, n, n), np.float32)
+    dens[4:8, 5:9, 6:10] = 1.0
+    dens[10:12, 10:12, 10:12] = 3.0
+    logs = np.full((n, n, n), np.log(1.5), np.float32)
+    ns = 20000
+    u = rng.uniform(0, 1, ns).astype(np.float32)
+    jit = rng.uniform(-0.5, 0.5, (ns, 3)).astype(np.float32)
+    mu = torch.empty((ns, 3), device=DEV); s = torch.empty((ns, 3), device=DEV)
+    q = torch.empty((ns, 4), device=DEV); rho = torch.empty(ns, device=DEV)
+    vox = torch.empty(ns, dtype=torch.int32, device=DEV)
+    scratch = torch.empty(dgr.dgr_seed_bytes(n), dtype=torch.uint8, device=DEV)
+    dgr.dgr_seed(grid, T(dens), T(logs), T(u), T(jit), mu, s, q, rho, vox, scratch)
+    torch.cuda.synchronize()
+    v = vox.cpu().numpy()
+    assert (dens.reshape(-1)[v] > 0).all()
+    # the two blocks hold mass 64 and 24: draws split ~ 64 : 24
+    frac = (dens.reshape(-1)[v] == 3.0).mean()
+    assert abs(frac - 24 / 88) < 0.02
+    assert np.allclose(s.cpu().numpy(), 1.5, atol=1e-6)
+    assert np.allclose(rho.cpu().numpy(), dens.reshape(-1)[v])
+    # mu inside the drawn voxel
+    m = mu.cpu().numpy()
+    cen = np.array(gs.org) + (np.stack([v % n, (v // n) % n, v // (n * n)], 1) + 0.5) * gs.h
+    assert np.all(np.abs(m - cen) <= 0.5 * gs.h + 1e-6)
