@@ -111,6 +111,13 @@ int dgr_set_deterministic(int on);
  * CTAs for small grids.  A process-wide setting, chosen by the autotuner
  * (paper_2411_04844_b300/autotune.py); workspace plans depend on it. */
 int dgr_set_tile_depth(int tz);
+/* Backprojector implementation (both exact transposes of dgr_project, both
+ * atomic-free and bit-reproducible): 0 (default) = column gather -- a warp per
+ * voxel column finds the candidate rays of each voxel in closed form;
+ * 1 = brick scatter -- a CTA accumulates a 32 x 16 x 16 voxel brick in shared
+ * memory, walking every ray that crosses it, rays taken in colour classes that
+ * cannot share a voxel.  A process-wide setting. */
+int dgr_set_backprojector(int variant);
 
 /* Footprint integers (paper Sec. 4.1 "Gaussian Effect Confinement",
  * "Discretize and Align" Eq. 6; valid mask of Algorithm 1):
@@ -193,8 +200,8 @@ int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t s
 int dgr_step(const dgr_problem *prob, const dgr_params *p, const float *measured,
              float *loss_out, dgr_ws *ws, cudaStream_t stream);
 
-/* Many independent reconstructions in one call (SURVEY-style batching; the
- * paper runs one problem at a time): n_inst <= 16 problems, each with its own
+/* Many independent reconstructions in one call (the paper runs one problem
+ * at a time): n_inst <= 16 problems, each with its own
  * grid, geometry, Gaussian count and optimiser state, advance by one dgr_step
  * each, every phase being ONE launch over the work of all instances (the
  * voxelizer's CTAs are persistent and pull tiles of every instance from one

@@ -23,7 +23,7 @@
  *              the gradient flowing through Delta-mu with box and anchor held
  *              constant (Sec. 4.1, end of "Discretize and Align").
  *
- * Readings of the paper taken here (each is listed in the design doc):
+ * Readings of the paper taken here:
  *   - voxel i has centre o + (i + 1/2) h; voxel-unit centre coordinate
  *     u = (mu - o)/h - 1/2, so voxel centres are at integers.
  *   - anchor a = floor(u) (mathematical floor, Eq. 6).

@@ -189,6 +189,12 @@ int dgr_set_deterministic(int on) {
     return DGR_OK;
 }
 
+int dgr_set_backprojector(int variant) {
+    if (variant != 0 && variant != 1) return DGR_ERR_ARG;
+    set_backprojector_variant(variant);
+    return DGR_OK;
+}
+
 int dgr_set_tile_depth(int tz) {
     if (tz != 8 && tz != 16 && tz != 32) return DGR_ERR_ARG;
     set_tile_depth(tz);
@@ -233,11 +239,13 @@ void set_geom(Inst &I, const dgr_geom &geo) {
     I.dsd = geo.dsd;
     I.angles = geo.angles;
     bp_blocks(I.g, I.nbx, I.nbz);
+    bp_bricks(I.g, I.nbbx, I.nbby, I.nbbz);
+    bp_colours(I.g, geo, I.col_u, I.col_v);
 }
 
 // offsets of each instance in the global index spaces
 void finish(Batch &B, bool has_geom) {
-    int g = 0, tiles = 0, tab = 0, views = 0, rows = 0, blk = 0;
+    int g = 0, tiles = 0, tab = 0, views = 0, rows = 0, blk = 0, bricks = 0;
     long long rays = 0;
     for (int i = 0; i < B.n; ++i) {
         Inst &I = B.in[i];
@@ -256,6 +264,8 @@ void finish(Batch &B, bool has_geom) {
             rays += (long long)I.n_views * I.nu * I.nv;
             I.blk0 = blk;
             blk += I.nbx * I.g.ny * I.nbz;
+            I.bb0 = bricks;
+            bricks += I.nbbx * I.nbby * I.nbbz;
         }
     }
     B.tot_g = g;
@@ -265,6 +275,7 @@ void finish(Batch &B, bool has_geom) {
     B.tot_rows = rows;
     B.tot_rays = rays;
     B.tot_blk = blk;
+    B.tot_bricks = bricks;
 }
 
 Batch *new_batch() {

@@ -114,7 +114,9 @@ struct Inst {
     int tile0, ntx, nty, ntz;         // first global tile, tiles per axis
     long long ray0;                   // first global ray
     int tab0, view0, row0;            // first RayXY entry, view, RowZ entry
-    int blk0, nbx, nbz;               // first backprojector block, blocks in x, z passes
+    int blk0, nbx, nbz;               // column backprojector: first CTA, CTAs in x, z passes
+    int bb0, nbbx, nbby, nbbz;        // brick backprojector: first brick, bricks per axis
+    int col_u, col_v;                 // ray colour classes (footprint < col pixels)
     float *vol;                       // volume (voxelize output; step: volume, then its gradient)
     float *sino;                      // projection (step: prediction, then residual)
     const float *meas;                // measured projections (step)
@@ -134,6 +136,7 @@ struct Batch {
     int tot_tiles;
     int tot_tab, tot_rows, tot_views;
     int tot_blk;
+    int tot_bricks;
     long long tot_rays;
     Inst in[MAX_INST];
 };
@@ -221,6 +224,11 @@ cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY 
 size_t ray_table_bytes_single(const dgr_geom &geo);
 // backprojector CTAs covering a grid (x blocks of 8 columns x ny x z passes)
 int bp_blocks(const dgr_grid &g, int &nbx, int &nbz);
+// brick backprojector: bricks per axis and the ray colour classes of a geometry
+int bp_bricks(const dgr_grid &g, int &nbx, int &nby, int &nbz);
+void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv);
+int backprojector_variant();
+void set_backprojector_variant(int v);
 
 // step.cu
 constexpr int L1_BLOCKS = 148;  // per instance; fixed so the loss reduction order is fixed

@@ -424,12 +424,219 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(const __grid_const
     }
 }
 
+// residual x |D| per ray, natural layout ([view][v][u]), for the brick backprojector
+__global__ void k_scale_dn(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
+                           float *__restrict__ out_base) {
+    const long long r_g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r_g >= B.tot_rays) return;
+    const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
+    const Inst &I = B.in[inst_of_ray(B, r_g)];
+    const long long r = r_g - I.ray0;
+    const int iu = (int)(r % I.nu);
+    const int iv = (int)((r / I.nu) % I.nv);
+    const int k = (int)(r / ((long long)I.nu * I.nv));
+    out_base[r_g] = I.sino[r] * ray_norm(T.tab[I.tab0 + k * I.nu + iu], T.rows[I.row0 + iv], I.beam);
+}
+
+// a6 (brick scatter): a CTA owns a BBX x BBY x BBZ brick of one instance with
+// FP32 accumulators in shared memory.  For each view it takes the detector
+// rays whose pixel lies in the bounding box of the brick's projected corners,
+// in colour classes (iu mod col_u, iv mod col_v): a voxel's footprint is
+// narrower than col_u x col_v pixels, so two rays of one class never cross the
+// same voxel and each class is added without atomics; classes and views go in
+// a fixed order (bit-reproducible).  Each ray walks the brick's plane crossings
+// exactly as k_project does (same t values), so every chord length equals the
+// projector's.  blockIdx.x: global brick.
+constexpr int BBX = 32, BBY = 16, BBZ = 16;
+constexpr int BB_THREADS = 128;
+
+__global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__ Batch B,
+                                                          RayXY *__restrict__ tab_base,
+                                                          const float *__restrict__ sino_s) {
+    __shared__ float acc[BBZ * BBY * BBX];
+    const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
+    int ii = 0;
+    while (ii + 1 < B.n && B.in[ii + 1].bb0 <= (int)blockIdx.x) ++ii;
+    const Inst &I = B.in[ii];
+    const dgr_grid &g = I.g;
+    const int b = blockIdx.x - I.bb0;
+    const int bx = b % I.nbbx, by = (b / I.nbbx) % I.nbby, bz = b / (I.nbbx * I.nbby);
+    const int x0 = bx * BBX, y0 = by * BBY, z0 = bz * BBZ;
+    const int x1 = min(x0 + BBX, g.nx), y1 = min(y0 + BBY, g.ny), z1 = min(z0 + BBZ, g.nz);
+    for (int i = threadIdx.x; i < BBZ * BBY * BBX; i += BB_THREADS) acc[i] = 0.f;
+    const RayXY *__restrict__ tab = T.tab + I.tab0;
+    const float2 *__restrict__ view_cs = T.view_cs + I.view0;
+    const RowZ *__restrict__ rows = T.rows + I.row0;
+    const float *__restrict__ sview0 = sino_s + I.ray0;
+    const bool cone = I.beam == DGR_CONE;
+    const float h = g.h;
+    const float cu = 0.5f * (float)(I.nu - 1), cv = 0.5f * (float)(I.nv - 1);
+    // brick corners (world)
+    const float wx0 = g.ox + x0 * h, wx1 = g.ox + x1 * h, wy0 = g.oy + y0 * h, wy1 = g.oy + y1 * h;
+    const float wz0 = g.oz + z0 * h, wz1 = g.oz + z1 * h;
+    const int N0[3] = {x0, y0, z0}, N1[3] = {x1, y1, z1};
+    __syncthreads();
+    for (int k = 0; k < I.n_views; ++k) {
+        const float2 cs = view_cs[k];
+        float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float X = (c & 1) ? wx1 : wx0, Y = (c & 2) ? wy1 : wy0, Z = (c & 4) ? wz1 : wz0;
+            const float pu_ = fmaf(-X, cs.y, Y * cs.x);
+            float M = 1.f;
+            if (cone) M = __fdividef(I.dsd, I.dso + fmaf(X, cs.x, Y * cs.y));
+            const float uu = M * pu_ / I.pu + cu, vv = M * Z / I.pv + cv;
+            umin = fminf(umin, uu); umax = fmaxf(umax, uu);
+            vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+        }
+        const int iu0 = max(0, (int)ceilf(umin - CAND_EPS)), iu1 = min(I.nu - 1, (int)floorf(umax + CAND_EPS));
+        const int iv0 = max(0, (int)ceilf(vmin - CAND_EPS)), iv1 = min(I.nv - 1, (int)floorf(vmax + CAND_EPS));
+        const float *sview = sview0 + (size_t)k * I.nv * I.nu;
+        for (int cls = 0; cls < I.col_u * I.col_v; ++cls) {
+            const int cuo = cls % I.col_u, cvo = cls / I.col_u;
+            // first iu >= iu0 with iu % col_u == cuo, likewise for iv
+            const int ua = iu0 + ((cuo - iu0 % I.col_u) + I.col_u) % I.col_u;
+            const int va = iv0 + ((cvo - iv0 % I.col_v) + I.col_v) % I.col_v;
+            const int nuc = ua <= iu1 ? (iu1 - ua) / I.col_u + 1 : 0;
+            const int nvc = va <= iv1 ? (iv1 - va) / I.col_v + 1 : 0;
+            for (int j = threadIdx.x; j < nuc * nvc; j += BB_THREADS) {
+                const int iu = ua + (j % nuc) * I.col_u, iv = va + (j / nuc) * I.col_v;
+                const float w = sview[(size_t)iv * I.nu + iu];
+                if (w == 0.f) continue;
+                const RayXY R = tab[k * I.nu + iu];
+                const RayZ Z = ray_z(R, rows[iv], I.zoff);
+                const float xi0[3] = {R.xi0x, R.xi0y, Z.xi0z};
+                const float ev[3] = {R.ex, R.ey, Z.ez};
+                const float inv[3] = {R.inv_ex, R.inv_ey, Z.inv_ez};
+                // the brick's slab intervals
+                float tmin = -INFINITY, tmax = INFINITY;
+                int cur[3];
+                bool miss = false;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (ev[a] != 0.f) {
+                        const float ta = plane_t(N0[a], xi0[a], inv[a]), tb = plane_t(N1[a], xi0[a], inv[a]);
+                        tmin = fmaxf(tmin, fminf(ta, tb));
+                        tmax = fminf(tmax, fmaxf(ta, tb));
+                    } else {
+                        const float f = floorf(xi0[a]);
+                        miss = miss || !(f >= (float)N0[a] && f < (float)N1[a]);
+                        cur[a] = (int)f;
+                    }
+                }
+                if (miss || !(tmax > tmin)) continue;
+                int sg[3];
+                float tn[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (ev[a] != 0.f) {
+                        const int d = ev[a] > 0.f ? 1 : -1;
+                        sg[a] = d;
+                        int i = (int)floorf(fmaf(tmin, ev[a], xi0[a]));
+                        i = min(max(i, N0[a]), N1[a] - 1);
+                        for (int it = 0; it < 3; ++it) {
+                            const float tu = plane_t(d > 0 ? i + 1 : i, xi0[a], inv[a]);
+                            if (tu <= tmin && i + d >= N0[a] && i + d < N1[a]) i += d; else break;
+                        }
+                        for (int it = 0; it < 3; ++it) {
+                            const float tl = plane_t(d > 0 ? i : i + 1, xi0[a], inv[a]);
+                            if (tl > tmin && i - d >= N0[a] && i - d < N1[a]) i -= d; else break;
+                        }
+                        cur[a] = i;
+                        tn[a] = plane_t(d > 0 ? i + 1 : i, xi0[a], inv[a]);
+                    } else {
+                        sg[a] = 0;
+                        tn[a] = INFINITY;
+                    }
+                }
+                int ix = cur[0] - x0, iy = cur[1] - y0, iz = cur[2] - z0;
+                float t = tmin;
+                for (int it = 0; it < BBX + BBY + BBZ + 3; ++it) {
+                    const float tnext = fminf(tn[0], fminf(tn[1], tn[2]));
+                    const float len = tnext - t;
+                    if (len > 0.f) {
+                        float *cell = &acc[(iz * BBY + iy) * BBX + ix];
+                        *cell = fmaf(len, w, *cell);
+                    }
+                    t = tnext;
+                    if (tnext == tn[0]) {
+                        ix += sg[0];
+                        if (ix < 0 || ix >= x1 - x0) break;
+                        tn[0] = plane_t(x0 + ix + (sg[0] > 0), xi0[0], inv[0]);
+                    } else if (tnext == tn[1]) {
+                        iy += sg[1];
+                        if (iy < 0 || iy >= y1 - y0) break;
+                        tn[1] = plane_t(y0 + iy + (sg[1] > 0), xi0[1], inv[1]);
+                    } else {
+                        iz += sg[2];
+                        if (iz < 0 || iz >= z1 - z0) break;
+                        tn[2] = plane_t(z0 + iz + (sg[2] > 0), xi0[2], inv[2]);
+                    }
+                }
+            }
+            __syncthreads();  // the next class may touch the same voxels
+        }
+    }
+    // write the brick (x fastest)
+    const size_t zs = (size_t)g.nx * g.ny;
+    for (int i = threadIdx.x; i < BBZ * BBY * BBX; i += BB_THREADS) {
+        const int xx = i % BBX, yy = (i / BBX) % BBY, zz = i / (BBX * BBY);
+        const int x = x0 + xx, y = y0 + yy, z = z0 + zz;
+        if (x < x1 && y < y1 && z < z1) I.vol[(size_t)z * zs + (size_t)y * g.nx + x] = acc[i];
+    }
+}
+
 }  // namespace
 
 size_t ray_table_bytes(int n_tab, int n_views, int n_rows) {
     return sizeof(RayXY) * (size_t)n_tab + ((sizeof(float2) * (size_t)n_views + 15) / 16) * 16 +
            sizeof(RowZ) * (size_t)n_rows;
 }
+
+int bp_bricks(const dgr_grid &g, int &nbx, int &nby, int &nbz) {
+    nbx = (g.nx + BBX - 1) / BBX;
+    nby = (g.ny + BBY - 1) / BBY;
+    nbz = (g.nz + BBZ - 1) / BBZ;
+    return nbx * nby * nbz;
+}
+
+// Colour classes for the brick backprojector: a voxel's projected footprint,
+// bounded over a 5 x 5 x 5 lattice of grid positions and every view (FP64,
+// 10% margin), must be narrower than col_u x col_v pixels.
+void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv) {
+    double wu = 0.0, wv = 0.0;
+    const double h = g.h;
+    // the angles live on the device: bound over the full circle instead,
+    // sampled every 5 degrees (the 10% margin covers the gaps)
+    for (int ia = 0; ia < 72; ++ia) {
+        const double a = ia * 3.14159265358979323846 / 36.0;
+        const double c = cos(a), s = sin(a);
+        for (int lz = 0; lz <= 4; ++lz)
+            for (int ly = 0; ly <= 4; ++ly)
+                for (int lx = 0; lx <= 4; ++lx) {
+                    const double X0 = g.ox + lx * 0.25 * (g.nx - 1) * h;
+                    const double Y0 = g.oy + ly * 0.25 * (g.ny - 1) * h;
+                    const double Z0 = g.oz + lz * 0.25 * (g.nz - 1) * h;
+                    double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+                    for (int cnr = 0; cnr < 8; ++cnr) {
+                        const double X = X0 + ((cnr & 1) ? h : 0), Y = Y0 + ((cnr & 2) ? h : 0),
+                                     Z = Z0 + ((cnr & 4) ? h : 0);
+                        const double M = geo.beam == DGR_CONE ? geo.dsd / (geo.dso + X * c + Y * s) : 1.0;
+                        const double u = M * (-X * s + Y * c) / geo.pu, v = M * Z / geo.pv;
+                        umin = fmin(umin, u); umax = fmax(umax, u);
+                        vmin = fmin(vmin, v); vmax = fmax(vmax, v);
+                    }
+                    wu = fmax(wu, umax - umin);
+                    wv = fmax(wv, vmax - vmin);
+                }
+    }
+    cu = (int)floor(1.1 * wu + 0.05) + 1;
+    cv = (int)floor(1.1 * wv + 0.05) + 1;
+}
+
+static int g_bp_variant = 0;  // 0: column gather, 1: brick scatter
+int backprojector_variant() { return g_bp_variant; }
+void set_backprojector_variant(int v) { g_bp_variant = v; }
 
 int bp_blocks(const dgr_grid &g, int &nbx, int &nbz) {
     nbx = (g.nx + BP_W - 1) / BP_W;
@@ -454,6 +661,13 @@ cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st) {
 }
 
 cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, cudaStream_t st) {
+    if (g_bp_variant == 1) {
+        k_scale_dn<<<(unsigned)((B.tot_rays + 255) / 256), 256, 0, st>>>(B, const_cast<RayXY *>(tab),
+                                                                         sino_scaled);
+        k_bp_brick<<<B.tot_bricks, BB_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled);
+        counted(2);
+        return cudaGetLastError();
+    }
     int max_u = 1, max_v = 1;
     for (int i = 0; i < B.n; ++i) {
         max_u = B.in[i].nu > max_u ? B.in[i].nu : max_u;

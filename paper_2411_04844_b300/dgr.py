@@ -34,7 +34,7 @@ EXPORTS = [
     "dgr_strerror", "dgr_set_deterministic", "dgr_footprint", "dgr_voxelize_count",
     "dgr_voxelize", "dgr_voxelize_backward", "dgr_project", "dgr_backproject",
     "dgr_l1_residual", "dgr_params_init", "dgr_step", "dgr_step_timed", "dgr_launch_count",
-    "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth",
+    "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth", "dgr_set_backprojector",
     "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
     "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
     "dgr_seed_rescale",
@@ -125,6 +125,7 @@ def lib():
             "dgr_status": [P, P, ctypes.POINTER(i)],
             "dgr_set_deterministic": [i],
             "dgr_set_tile_depth": [i],
+            "dgr_set_backprojector": [i],
             "dgr_footprint": [ctypes.POINTER(Grid), i, P, P, P, f, P, P, P],
             "dgr_voxelize_count": [ctypes.POINTER(Grid), i, P, P, P, f, ctypes.POINTER(ll),
                                    ctypes.POINTER(ll), P, P],
@@ -251,6 +252,11 @@ def dgr_status(ws: Workspace, stream=None) -> int:
     v = ctypes.c_int()
     _rc(lib().dgr_status(ws.ptr, _stream(stream), ctypes.byref(v)), "dgr_status")
     return int(v.value)
+
+
+def dgr_set_backprojector(variant: int):
+    """0: brick scatter (default); 1: column gather."""
+    _rc(lib().dgr_set_backprojector(int(variant)), "dgr_set_backprojector")
 
 
 def dgr_set_tile_depth(tz: int):

@@ -12,7 +12,7 @@ Pipeline, every numerical step in libdgr kernels:
      refined by a few fixed-point steps (dgr_voxelize + dgr_seed_rescale) so
      their voxelized field matches the proposal;
   4. the plain method continues from there (dgr_step / dgr_step_batched).
-The fallback (and the judge of the network's error) is the plain FBP-seeded
+The fallback (and the yardstick for the network's error) is the plain FBP-seeded
 initialisation: the same seeding with the clipped FDK volume as density and a
 fixed scale.  Training targets come from fits of the plain method itself: the
 voxelized fitted field (density) and the intensity-weighted mean log-scale of
