@@ -85,7 +85,7 @@ typedef struct {
     int max_tiles;           /* largest number of voxel tiles (dgr_tile_count) */
     long long max_pairs;
     long long max_items;
-    long long max_vox;       /* dgr_step only: voxels of the volume (0 otherwise) */
+    long long max_vox;       /* dgr_step: voxels of the volume; dgr_project: optional room for a z-fastest copy */
     long long max_rays;      /* dgr_step only: rays of the sinogram (0 otherwise) */
     int max_views, max_nu, max_nv; /* projector tables (batches: sum of views, max nu, max nv) */
     int max_inst;            /* instances of dgr_step_batched (0 or 1: single problems) */
@@ -112,11 +112,14 @@ int dgr_set_deterministic(int on);
  * (paper_2411_04844_b300/autotune.py); workspace plans depend on it. */
 int dgr_set_tile_depth(int tz);
 /* Backprojector implementation (both exact transposes of dgr_project, both
- * atomic-free and bit-reproducible): 0 (default) = column gather -- a warp per
- * voxel column finds the candidate rays of each voxel in closed form;
- * 1 = brick scatter -- a CTA accumulates a 32 x 16 x 16 voxel brick in shared
- * memory, walking every ray that crosses it, rays taken in colour classes that
- * cannot share a voxel.  A process-wide setting. */
+ * bit-reproducible): 0 (default) = brick scatter -- a CTA accumulates a voxel
+ * brick in shared memory, its warps walking the detector columns that cross
+ * it, each lane carrying several detector rows; segment contributions are
+ * added as fixed-point integers (exact, order-independent), the step chosen
+ * per group of views from the largest residual so that no sum overflows, then
+ * folded into FP32 sums in a fixed order; 1 = column gather -- a warp per
+ * voxel column finds the candidate rays of each voxel in closed form.  A
+ * process-wide setting. */
 int dgr_set_backprojector(int variant);
 
 /* Footprint integers (paper Sec. 4.1 "Gaussian Effect Confinement",
@@ -153,7 +156,12 @@ int dgr_voxelize_backward(const dgr_grid *grid, int n, const float *mu, const fl
 
 /* Projector T (paper Sec. 4.3, Eq. 12, P_hat = T(V)): each detector pixel is
  * the exact line integral of the piecewise-constant voxel image along its ray
- * (Siddon's radiological path).  Overwrites sino [n_views][nv][nu]. */
+ * (Siddon's radiological path).  Overwrites sino [n_views][nv][nu].
+ * If the workspace plan's max_vox covers the grid, the volume is first copied
+ * into the workspace with z fastest and projected by the row-warp kernel (a
+ * warp per 32 detector rows of one detector column); otherwise a per-ray
+ * kernel reads it in place.  Both use the same chord lengths; their sums may
+ * differ in rounding order. */
 int dgr_project(const dgr_grid *grid, const dgr_geom *geom, const float *vol, float *sino,
                 dgr_ws *ws, cudaStream_t stream);
 
@@ -231,8 +239,8 @@ int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *me
  * driver allocations in plug-ins; loops with a latency budget in which an
  * allocation (which may synchronise the device) is not allowed; code that runs
  * after a one-time initialisation phase during which all memory was reserved.
- * For them this entry point computes exactly what dgr_project computes (same
- * kernels, same results) without any dgr_ws: its scratch (the ray tables,
+ * For them this entry point computes what dgr_project computes (with the
+ * per-ray kernel: the same chord lengths) without any dgr_ws: its scratch (the ray tables,
  * 32 bytes per (view, detector column) + 16 bytes per detector row + 8 bytes
  * per view, rounded) lives in one fixed device array of
  * DGR_NOALLOC_SCRATCH_BYTES that every GPU using the library holds until the

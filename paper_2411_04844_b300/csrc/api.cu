@@ -98,10 +98,12 @@ Layout layout_of(const dgr_ws_plan &p) {
     const int ninst = p.max_inst > 0 ? p.max_inst : 1;
     L.rayxy = take(ray_table_bytes(p.max_views * p.max_nu, p.max_views, ninst * p.max_nv));
     // residual x |D| for the backprojector (standalone calls; the step reuses its sinogram)
-    L.sino_scaled = take(4 * (size_t)p.max_views * p.max_nu * p.max_nv);
+    // scaled residual of the backprojector, then (64-float aligned) one maximum per view
+    L.sino_scaled = take(4 * ((size_t)p.max_views * p.max_nu * p.max_nv + 64 + (size_t)p.max_views));
     L.loss_part = take(4 * (size_t)(L1_BLOCKS * ninst + 1));
     L.grads = take(4 * 11 * (size_t)p.max_n);
-    L.vol = take(4 * (size_t)p.max_vox);
+    // instance volumes start on 64-float boundaries (vectorised stores)
+    L.vol = take(4 * ((size_t)p.max_vox + (size_t)64 * (p.max_inst > 1 ? p.max_inst : 1)));
     L.sino = take(4 * (size_t)p.max_rays);
     L.total = o;
     return L;
@@ -226,6 +228,9 @@ void set_grid(Inst &I, const dgr_grid &g, float k) {
     I.k = k;
     I.zoff = -g.oz / g.h;
     tile_dims(g, I.ntx, I.nty, I.ntz);
+    I.vsx = 1;  // the C ABI's volume layout: [nz][ny][nx]
+    I.vsy = g.nx;
+    I.vsz = g.nx * g.ny;
 }
 
 void set_geom(Inst &I, const dgr_geom &geo) {
@@ -405,7 +410,19 @@ int dgr_project(const dgr_grid *grid, const dgr_geom *geom, const float *vol, fl
     int rc = proj_batch(grid, geom, vol, sino, ws, B);
     if (rc) return rc;
     RayXY *tab = ws_ptr<RayXY>(ws, ws->rayxy);
-    cudaError_t e = launch_ray_tables(*B, tab, stream);
+    cudaError_t e = cudaSuccess;
+    Inst &I = B->in[0];
+    const long long vox = (long long)grid->nx * grid->ny * grid->nz;
+    if (ws->plan.max_vox >= vox) {
+        // a z-fastest copy in the workspace feeds the row-warp projector
+        float *zf = ws_ptr<float>(ws, ws->vol);
+        e = launch_vol_zfast(*grid, vol, zf, stream);
+        I.vol = zf;
+        I.vsz = 1;
+        I.vsy = grid->nz;
+        I.vsx = grid->ny * grid->nz;
+    }
+    if (e == cudaSuccess) e = launch_ray_tables(*B, tab, stream);
     if (e == cudaSuccess) e = launch_project(*B, tab, stream);
     return cuda_rc(e);
 }
@@ -484,7 +501,13 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
     for (int i = 0; i < n_inst; ++i) {
         Inst &I = B.in[i];
         I.vol = vol + vo;
-        vo += (long long)I.g.nx * I.g.ny * I.g.nz;
+        vo += ((long long)I.g.nx * I.g.ny * I.g.nz + 63) / 64 * 64;
+        // the step's own volume is z fastest ([nx][ny][nz]): the projector's
+        // lanes (consecutive detector rows) then read neighbouring words; the
+        // backprojector writes the gradient in the C ABI's layout
+        I.vsz = 1;
+        I.vsy = I.g.nz;
+        I.vsx = I.g.ny * I.g.nz;
         I.sino = sino + I.ray0;
         float *gr = grads + 11ll * I.g0;
         I.g_mu = gr; I.g_s = gr + 3 * I.n; I.g_q = gr + 6 * I.n; I.g_rho = gr + 10 * I.n;

@@ -117,6 +117,8 @@ struct Inst {
     int blk0, nbx, nbz;               // column backprojector: first CTA, CTAs in x, z passes
     int bb0, nbbx, nbby, nbbz;        // brick backprojector: first brick, bricks per axis
     int col_u, col_v;                 // ray colour classes (footprint < col pixels)
+    int pb0, npv;                     // projector: first CTA, row groups
+    int vsx, vsy, vsz;                // element strides of vol as voxelize output / project input
     float *vol;                       // volume (voxelize output; step: volume, then its gradient)
     float *sino;                      // projection (step: prediction, then residual)
     const float *meas;                // measured projections (step)
@@ -216,6 +218,8 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
 size_t ray_table_bytes(int n_tab, int n_views, int n_rows);
 cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st);
 cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st);
+// x-fastest -> z-fastest copy of a volume (the row-warp projector's layout)
+cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cudaStream_t st);
 // sino_scaled: scratch of all instances' rays (residual x |D|, [view][u][v]); not aliasing sino
 cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, cudaStream_t st);
 // the projector of one instance with caller-provided tables (no workspace)

@@ -13,14 +13,16 @@
 //
 //   k_ray_tables  per (view, iu): X0, D (FP64 arithmetic, stored FP32);
 //                 per detector row: z slope, its reciprocal, FP64 layer snap
-//   k_project     one thread per ray, incremental plane walk; u-adjacent
-//                 rays in a warp read neighbouring voxels
+//   k_project     a CTA per (view, detector column): the column's (x, y)
+//                 path is merged into shared memory once, each lane (a
+//                 detector row) adds its own z crossings; z-fastest volume
 //   k_scale_dn    residual x |D| per ray (chord lengths are t-intervals x |D|)
 //   k_backproject one thread per (x, y) column and a chunk of z: for each view
 //                 the candidate detector columns come from the column's four
 //                 corners, the candidate rows per voxel in closed form from the
 //                 column's slab interval; each candidate costs one slab test
 //                 and one load -- no divisions, no atomics
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -140,9 +142,238 @@ __device__ __forceinline__ float plane_t(int p, float xi0, float inv) {
     return ((float)p - xi0) * inv;
 }
 
-// a4: one thread per global ray; incremental Siddon walk.
-__global__ void __launch_bounds__(128) k_project(const __grid_constant__ Batch B,
-                                                 RayXY *__restrict__ tab_base) {
+// Entry cell along one axis at t = tmin, made consistent with the plane
+// crossings: the plane ahead (in the travel direction) lies after tmin, the
+// one behind at or before it.  lo/hi bound the index (a grid axis) or are
+// INT_MIN/INT_MAX (the z axis of the row-warp walk, which runs over unbounded
+// z layers and masks the ones outside the grid).
+__device__ __forceinline__ int entry_cell(float tmin, float e, float xi0, float inv, int d, int lo,
+                                          int hi) {
+    float f = floorf(fmaf(tmin, e, xi0));
+    f = fminf(fmaxf(f, (float)max(lo, -(1 << 24))), (float)min(hi, 1 << 24));
+    int i = (int)f;
+    for (int it = 0; it < 3; ++it) {
+        const float tu = plane_t(d > 0 ? i + 1 : i, xi0, inv);
+        if (tu <= tmin && i + d >= lo && i + d <= hi) i += d; else break;
+    }
+    for (int it = 0; it < 3; ++it) {
+        const float tl = plane_t(d > 0 ? i : i + 1, xi0, inv);
+        if (tl > tmin && i - d >= lo && i - d <= hi) i -= d; else break;
+    }
+    return i;
+}
+
+// a4 (shared-path projector): a CTA owns one detector column of one view and
+// up to PR_ROWS detector rows, a warp 32 consecutive rows.  All rays of a
+// column follow the same (x, y) path (rotation about z).  The CTA first lays
+// that path out in shared memory -- the x and y plane crossings merged in
+// parallel, each crossing's rank found by binary search in the other axis'
+// crossings (x first on ties, as a sequential walk would take them) -- and
+// every warp then streams through it: per (x, y) cell one shared load, and per
+// lane the z planes its own ray crosses inside the cell (one in the common
+// case, a bounded loop for more).  Segment lengths are differences of the same
+// FP32 plane crossings the backprojector uses.  The volume is z fastest, so
+// the lanes of a warp read neighbouring words.  Rows whose rays leave the grid
+// through a z face walk with a per-segment mask (MASKZ).
+constexpr int PR_THREADS = 256;
+constexpr int PR_ROWS = PR_THREADS;
+constexpr int SEG_MAX = 2048;  // path segments staged per round
+constexpr int WALK = 4;
+
+struct __align__(8) Seg {
+    float t1;  // end of the segment (the crossing that leaves its cell)
+    int cb;    // element offset of the segment's (x, y) cell
+};
+
+// number of i in [0, n) whose crossing plane_t(p0 + sg i) is < T (le: <= T);
+// the crossings are non-decreasing in i
+__device__ __forceinline__ int count_before(float T, int n, int p0, int sg, float xi0, float inv,
+                                            bool le) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float tm = plane_t(p0 + sg * mid, xi0, inv);
+        if (le ? tm <= T : tm < T) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <bool MASKZ>
+__device__ __forceinline__ void walk_segs(const float *__restrict__ vol, const Seg *seg, int c0, int c1,
+                                          int nz, float &t, float &acc, int &iz, float &fz, float &tz,
+                                          int sgz, float xi0z, float iez) {
+    const unsigned zmax = (unsigned)(nz - 1);
+    int zc = (int)min((unsigned)iz, zmax);
+    const float fsg = (float)sgz;
+    for (int r = c0; r < c1; r += WALK) {
+        float l0[WALK], l1[WALK];
+        int a0[WALK], a1[WALK];
+#pragma unroll
+        for (int j = 0; j < WALK; ++j) {
+            const Seg S = seg[r + j - c0];  // past c1: padding, empty segments
+            const float t1 = S.t1;
+            const float m = fminf(tz, t1);
+            const bool in0 = !MASKZ || (unsigned)iz <= zmax;
+            l0[j] = in0 ? m - t : 0.f;
+            a0[j] = S.cb + zc;
+            l1[j] = 0.f;
+            a1[j] = a0[j];
+            if (tz < t1) {
+                float ts = tz;
+                iz += sgz;
+                fz += fsg;
+                tz = (fz - xi0z) * iez;
+                zc = (int)min((unsigned)iz, zmax);
+                const bool in1 = !MASKZ || (unsigned)iz <= zmax;
+                l1[j] = in1 ? fminf(tz, t1) - ts : 0.f;
+                a1[j] = S.cb + zc;
+                // rare: further z planes inside this cell (bounded: a crossing
+                // that rounding failed to advance cannot spin)
+                for (int rep = 0; rep <= nz && tz < t1; ++rep) {
+                    ts = tz;
+                    iz += sgz;
+                    fz += fsg;
+                    tz = (fz - xi0z) * iez;
+                    zc = (int)min((unsigned)iz, zmax);
+                    if (!MASKZ || (unsigned)iz <= zmax)
+                        acc = fmaf(fminf(tz, t1) - ts, __ldg(vol + S.cb + zc), acc);
+                }
+            }
+            t = t1;
+        }
+        float v0[WALK], v1[WALK];
+#pragma unroll
+        for (int j = 0; j < WALK; ++j) {
+            v0[j] = __ldg(vol + a0[j]);
+            v1[j] = __ldg(vol + a1[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
+    }
+}
+
+// blockIdx.x: global projector block (instance, view, row group, column)
+__global__ void __launch_bounds__(PR_THREADS) k_project(const __grid_constant__ Batch B,
+                                                        RayXY *__restrict__ tab_base) {
+    __shared__ Seg seg[SEG_MAX + WALK];
+    const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
+    int ii = 0;
+    while (ii + 1 < B.n && B.in[ii + 1].pb0 <= (int)blockIdx.x) ++ii;
+    const Inst &I = B.in[ii];
+    const dgr_grid &g = I.g;
+    const int b = blockIdx.x - I.pb0;
+    const int iu = b % I.nu, rg = (b / I.nu) % I.npv, k = b / (I.nu * I.npv);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int iv = rg * PR_ROWS + w * 32 + lane;
+    const RayXY R = T.tab[I.tab0 + k * I.nu + iu];
+    const RowZ row = T.rows[I.row0 + min(iv, I.nv - 1)];
+    float *sino_out = I.sino + ((size_t)k * I.nv + min(iv, I.nv - 1)) * I.nu + iu;
+    // (x, y) interval of the grid and entry cell: the same for the whole CTA
+    float tmin = -INFINITY, tmax = INFINITY;
+    bool miss = false;
+    float fx = 0.f, fy = 0.f;
+    if (R.ex != 0.f) {
+        const float t0 = plane_t(0, R.xi0x, R.inv_ex), t1 = plane_t(g.nx, R.xi0x, R.inv_ex);
+        tmin = fmaxf(tmin, fminf(t0, t1));
+        tmax = fminf(tmax, fmaxf(t0, t1));
+    } else {
+        fx = floorf(R.xi0x);
+        miss = miss || !(fx >= 0.f && fx < (float)g.nx);
+    }
+    if (R.ey != 0.f) {
+        const float t0 = plane_t(0, R.xi0y, R.inv_ey), t1 = plane_t(g.ny, R.xi0y, R.inv_ey);
+        tmin = fmaxf(tmin, fminf(t0, t1));
+        tmax = fminf(tmax, fmaxf(t0, t1));
+    } else {
+        fy = floorf(R.xi0y);
+        miss = miss || !(fy >= 0.f && fy < (float)g.ny);
+    }
+    if (miss || !(tmax > tmin)) {  // CTA-uniform
+        if (iv < I.nv) *sino_out = 0.f;
+        return;
+    }
+    const int sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
+    const int sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
+    const int ix0 = sgx ? entry_cell(tmin, R.ex, R.xi0x, R.inv_ex, sgx, 0, g.nx - 1) : (int)fx;
+    const int iy0 = sgy ? entry_cell(tmin, R.ey, R.xi0y, R.inv_ey, sgy, 0, g.ny - 1) : (int)fy;
+    // crossings ahead: x planes px0 + sgx j, j < nxe (the last one leaves the
+    // grid), likewise y; the walk ends at the first leaving crossing
+    const int nxe = sgx > 0 ? g.nx - ix0 : (sgx < 0 ? ix0 + 1 : 0);
+    const int nye = sgy > 0 ? g.ny - iy0 : (sgy < 0 ? iy0 + 1 : 0);
+    const int px0 = sgx > 0 ? ix0 + 1 : ix0, py0 = sgy > 0 ? iy0 + 1 : iy0;
+    int rend = INT_MAX;
+    if (nxe > 0) {
+        const float te = plane_t(px0 + sgx * (nxe - 1), R.xi0x, R.inv_ex);
+        rend = min(rend, nxe - 1 + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false));
+    }
+    if (nye > 0) {
+        const float te = plane_t(py0 + sgy * (nye - 1), R.xi0y, R.inv_ey);
+        rend = min(rend, nye - 1 + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true));
+    }
+    const int nseg = rend + 1;  // segments 0 .. rend
+    const int cb0 = ix0 * I.vsx + iy0 * I.vsy;
+    // this lane's z: entry layer (unbounded), next crossing, and whether the
+    // ray stays inside the z range over the whole (x, y) chord
+    const RayZ Z = ray_z(R, row, I.zoff);
+    int iz, sgz = 0;
+    float tz = INFINITY, fz = 0.f;
+    bool zin;
+    if (Z.ez != 0.f) {
+        sgz = Z.ez > 0.f ? 1 : -1;
+        const float t0 = plane_t(0, Z.xi0z, Z.inv_ez), t1 = plane_t(g.nz, Z.xi0z, Z.inv_ez);
+        zin = fminf(t0, t1) <= tmin && fmaxf(t0, t1) >= tmax;
+        iz = entry_cell(tmin, Z.ez, Z.xi0z, Z.inv_ez, sgz, INT_MIN / 2, INT_MAX / 2);
+        fz = (float)(sgz > 0 ? iz + 1 : iz);
+        tz = (fz - Z.xi0z) * Z.inv_ez;
+    } else {
+        const float f = floorf(Z.xi0z);
+        zin = f >= 0.f && f < (float)g.nz;
+        iz = zin ? (int)f : -1;
+    }
+    const bool masked = __any_sync(0xffffffffu, !zin);
+    float t = tmin, acc = 0.f;
+    for (int c0 = 0; c0 < nseg; c0 += SEG_MAX) {
+        const int c1 = min(nseg, c0 + SEG_MAX);
+        __syncthreads();  // the previous round's readers are done
+        if (c0 == 0 && threadIdx.x == 0) seg[0].cb = cb0;
+        for (int e = threadIdx.x; e < nxe + nye; e += PR_THREADS) {
+            float te;
+            int r, cx, cy;  // rank; cell after the crossing
+            if (e < nxe) {
+                te = plane_t(px0 + sgx * e, R.xi0x, R.inv_ex);
+                r = e + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false);
+                cx = ix0 + sgx * (e + 1);
+                cy = iy0 + sgy * (r - e);
+            } else {
+                const int i = e - nxe;
+                te = plane_t(py0 + sgy * i, R.xi0y, R.inv_ey);
+                r = i + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true);
+                cx = ix0 + sgx * (r - i);
+                cy = iy0 + sgy * (i + 1);
+            }
+            if (r >= c0 && r < c1) seg[r - c0].t1 = te;
+            // r + 1 < c1 <= nseg: the crossing is not the leaving one, the cell is inside
+            if (r + 1 >= c0 && r + 1 < c1) seg[r + 1 - c0].cb = cx * I.vsx + cy * I.vsy;
+        }
+        __syncthreads();
+        if (threadIdx.x < WALK) {  // pad to whole groups: empty segments at the last crossing
+            const Seg last = seg[c1 - 1 - c0];
+            seg[c1 - c0 + threadIdx.x] = last;
+        }
+        __syncthreads();
+        if (masked)
+            walk_segs<true>(I.vol, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z, Z.inv_ez);
+        else
+            walk_segs<false>(I.vol, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z, Z.inv_ez);
+    }
+    if (iv < I.nv) *sino_out = acc * ray_norm(R, row, I.beam);
+}
+
+// a4 (per-ray projector, for volumes in the C ABI's x-fastest layout when no
+// z-fastest copy can be made): one thread per global ray, incremental Siddon
+// walk; u-adjacent rays in a warp read neighbouring voxels.
+__global__ void __launch_bounds__(128) k_project_ray(const __grid_constant__ Batch B,
+                                                     RayXY *__restrict__ tab_base) {
     const long long r_g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r_g >= B.tot_rays) return;
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
@@ -217,7 +448,6 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ Batch B
     // walk the plane crossings WALK at a time: segment lengths and voxel
     // indices first (ALU only), then their loads together, then the sums in
     // walk order
-    constexpr int WALK = 4;
     const int maxgroups = (g.nx + g.ny + g.nz + 3) / WALK + 1;
     bool done = false;
     for (int grp = 0; grp < maxgroups && !done; ++grp) {
@@ -254,6 +484,24 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ Batch B
         for (int j = 0; j < WALK; ++j) acc = fmaf(len[j], v[j], acc);
     }
     sino[r] = acc * ray_norm(R, row, I.beam);
+}
+
+// x-fastest [nz][ny][nx] -> z-fastest [nx][ny][nz] copy through a 32 x 32
+// shared tile (both sides coalesced); blockIdx: (x tile, y, z tile)
+__global__ void k_vol_zfast(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
+                            int nz) {
+    __shared__ float tile[32][33];
+    const int x0 = blockIdx.x * 32, y = blockIdx.y, z0 = blockIdx.z * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int j = ty; j < 32; j += 8) {
+        const int z = z0 + j, x = x0 + tx;
+        if (z < nz && x < nx) tile[j][tx] = src[((size_t)z * ny + y) * nx + x];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int x = x0 + j, z = z0 + tx;
+        if (x < nx && z < nz) dst[((size_t)x * ny + y) * nz + z] = tile[tx][j];
+    }
 }
 
 // residual x |D| per ray, written view-major with v fastest ([view][u][v]) so
@@ -424,36 +672,66 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(const __grid_const
     }
 }
 
-// residual x |D| per ray, natural layout ([view][v][u]), for the brick backprojector
+// residual x |D| per ray, natural layout ([view][v][u]), for the brick
+// backprojector, and the largest |residual x |D|| of every view (for its
+// fixed-point step).  blockIdx.y: global view; blockIdx.x: 256 rays of it.
 __global__ void k_scale_dn(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
-                           float *__restrict__ out_base) {
-    const long long r_g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r_g >= B.tot_rays) return;
+                           float *__restrict__ out_base, unsigned *__restrict__ view_max) {
+    __shared__ unsigned s_m;
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
-    const Inst &I = B.in[inst_of_ray(B, r_g)];
-    const long long r = r_g - I.ray0;
-    const int iu = (int)(r % I.nu);
-    const int iv = (int)((r / I.nu) % I.nv);
-    const int k = (int)(r / ((long long)I.nu * I.nv));
-    out_base[r_g] = I.sino[r] * ray_norm(T.tab[I.tab0 + k * I.nu + iu], T.rows[I.row0 + iv], I.beam);
+    const int vg = blockIdx.y;
+    const Inst &I = B.in[inst_of_view(B, vg)];
+    const int k = vg - I.view0;
+    const int per = I.nu * I.nv;
+    if (threadIdx.x == 0) s_m = 0u;
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;  // ray within the view
+    unsigned m = 0u;
+    if (r < per) {
+        const int iu = r % I.nu, iv = r / I.nu;
+        const long long ri = (long long)k * per + r;
+        const float v = I.sino[ri] * ray_norm(T.tab[I.tab0 + k * I.nu + iu], T.rows[I.row0 + iv], I.beam);
+        out_base[I.ray0 + ri] = v;
+        const float a = fabsf(v);
+        m = a != a ? 0x7fffffffu : __float_as_uint(a);  // NaN: the largest code
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_m, m);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_m) atomicMax(view_max + vg, s_m);
 }
 
-// a6 (brick scatter): a CTA owns a BBX x BBY x BBZ brick of one instance with
-// FP32 accumulators in shared memory.  For each view it takes the detector
-// rays whose pixel lies in the bounding box of the brick's projected corners,
-// in colour classes (iu mod col_u, iv mod col_v): a voxel's footprint is
-// narrower than col_u x col_v pixels, so two rays of one class never cross the
-// same voxel and each class is added without atomics; classes and views go in
-// a fixed order (bit-reproducible).  Each ray walks the brick's plane crossings
-// exactly as k_project does (same t values), so every chord length equals the
-// projector's.  blockIdx.x: global brick.
-constexpr int BBX = 32, BBY = 16, BBZ = 16;
-constexpr int BB_THREADS = 128;
+// a6 (brick scatter): a CTA owns a BBX x BBY x BBZ brick of one instance and
+// keeps its sums in shared memory.  Views go in groups of VGROUP.  For each
+// view the detector columns and rows whose pixels fall in the bounding box of
+// the brick's projected corners are the candidates; a work item is one
+// (view, column) pair: the warp walks the column's (x, y) path through the
+// brick (warp-uniform, the same plane crossings as k_project, hence the same
+// chord lengths) carrying SLOTS groups of 32 consecutive rows per lane, and
+// adds each segment's length x scaled residual into the brick with a
+// shared-memory integer atomic, in fixed point.  Integer sums do not depend on
+// the order of the additions, so all items of a group run concurrently and
+// the result is still bit-reproducible.  The fixed-point step of a group is a
+// power of two chosen from the largest residual of the group's views
+// and a bound on the contributions a voxel can receive (VGROUP views x
+// col_u x col_v rays per view, each at most the longest chord in t units x
+// |residual|), so no sum can overflow; after a group, the integer sums are
+// added, in a fixed order, into FP32 sums.  blockIdx.x: global brick.
+constexpr int BBX = 8, BBY = 8, BBZ = 88;
+constexpr int BBV = BBX * BBY * BBZ;
+constexpr int BB_THREADS = 256;
+constexpr int SLOTS = 3;
+constexpr int VGROUP = 8;
 
 __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__ Batch B,
                                                           RayXY *__restrict__ tab_base,
-                                                          const float *__restrict__ sino_s) {
-    __shared__ float acc[BBZ * BBY * BBX];
+                                                          const float *__restrict__ sino_s,
+                                                          const unsigned *__restrict__ view_max) {
+    extern __shared__ float accf[];          // [BBY][BBX][BBZ] FP32 sums
+    int *acci = reinterpret_cast<int *>(accf + BBV);  // the group's fixed-point sums
+    __shared__ int s_rng[VGROUP][4];         // iu0, iu1, iv0, iv1 of each view of the group
+    __shared__ int s_cum[VGROUP + 1];        // items before each view
+    __shared__ unsigned s_max;               // largest |scaled residual| of the group (bits)
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
     int ii = 0;
     while (ii + 1 < B.n && B.in[ii + 1].bb0 <= (int)blockIdx.x) ++ii;
@@ -463,7 +741,11 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
     const int bx = b % I.nbbx, by = (b / I.nbbx) % I.nbby, bz = b / (I.nbbx * I.nbby);
     const int x0 = bx * BBX, y0 = by * BBY, z0 = bz * BBZ;
     const int x1 = min(x0 + BBX, g.nx), y1 = min(y0 + BBY, g.ny), z1 = min(z0 + BBZ, g.nz);
-    for (int i = threadIdx.x; i < BBZ * BBY * BBX; i += BB_THREADS) acc[i] = 0.f;
+    for (int i = threadIdx.x; i < BBV; i += BB_THREADS) {
+        accf[i] = 0.f;
+        acci[i] = 0;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const RayXY *__restrict__ tab = T.tab + I.tab0;
     const float2 *__restrict__ view_cs = T.view_cs + I.view0;
     const RowZ *__restrict__ rows = T.rows + I.row0;
@@ -471,118 +753,188 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
     const bool cone = I.beam == DGR_CONE;
     const float h = g.h;
     const float cu = 0.5f * (float)(I.nu - 1), cv = 0.5f * (float)(I.nv - 1);
-    // brick corners (world)
     const float wx0 = g.ox + x0 * h, wx1 = g.ox + x1 * h, wy0 = g.oy + y0 * h, wy1 = g.oy + y1 * h;
     const float wz0 = g.oz + z0 * h, wz1 = g.oz + z1 * h;
-    const int N0[3] = {x0, y0, z0}, N1[3] = {x1, y1, z1};
-    __syncthreads();
-    for (int k = 0; k < I.n_views; ++k) {
-        const float2 cs = view_cs[k];
-        float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    const int nzb = z1 - z0;
+    // longest chord of a voxel in t units: sqrt(3) h / |D|, |D| >= dsd (cone) or 1 (parallel)
+    const float tchord = 1.7320509f * h / (cone ? I.dsd : 1.f) * 1.001f;
+    bool bad = false;  // a non-finite residual: the brick becomes NaN
+    for (int kg = 0; kg < I.n_views; kg += VGROUP) {
+        const int nvw = min(VGROUP, I.n_views - kg);
+        if (threadIdx.x < nvw) {
+            const float2 cs = view_cs[kg + threadIdx.x];
+            float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float X = (c & 1) ? wx1 : wx0, Y = (c & 2) ? wy1 : wy0, Z = (c & 4) ? wz1 : wz0;
-            const float pu_ = fmaf(-X, cs.y, Y * cs.x);
-            float M = 1.f;
-            if (cone) M = __fdividef(I.dsd, I.dso + fmaf(X, cs.x, Y * cs.y));
-            const float uu = M * pu_ / I.pu + cu, vv = M * Z / I.pv + cv;
-            umin = fminf(umin, uu); umax = fmaxf(umax, uu);
-            vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+            for (int c = 0; c < 8; ++c) {
+                const float X = (c & 1) ? wx1 : wx0, Y = (c & 2) ? wy1 : wy0, Z = (c & 4) ? wz1 : wz0;
+                const float pu_ = fmaf(-X, cs.y, Y * cs.x);
+                float M = 1.f;
+                if (cone) M = __fdividef(I.dsd, I.dso + fmaf(X, cs.x, Y * cs.y));
+                const float uu = M * pu_ / I.pu + cu, vv = M * Z / I.pv + cv;
+                umin = fminf(umin, uu); umax = fmaxf(umax, uu);
+                vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
+            }
+            const int iu0 = max(0, (int)ceilf(umin - CAND_EPS)), iu1 = min(I.nu - 1, (int)floorf(umax + CAND_EPS));
+            const int iv0 = max(0, (int)ceilf(vmin - CAND_EPS)), iv1 = min(I.nv - 1, (int)floorf(vmax + CAND_EPS));
+            s_rng[threadIdx.x][0] = iu0;
+            s_rng[threadIdx.x][1] = iu1;
+            s_rng[threadIdx.x][2] = iv0;
+            s_rng[threadIdx.x][3] = (iv1 >= iv0 && iu1 >= iu0) ? iv1 : iv0 - 1;
         }
-        const int iu0 = max(0, (int)ceilf(umin - CAND_EPS)), iu1 = min(I.nu - 1, (int)floorf(umax + CAND_EPS));
-        const int iv0 = max(0, (int)ceilf(vmin - CAND_EPS)), iv1 = min(I.nv - 1, (int)floorf(vmax + CAND_EPS));
-        const float *sview = sview0 + (size_t)k * I.nv * I.nu;
-        for (int cls = 0; cls < I.col_u * I.col_v; ++cls) {
-            const int cuo = cls % I.col_u, cvo = cls / I.col_u;
-            // first iu >= iu0 with iu % col_u == cuo, likewise for iv
-            const int ua = iu0 + ((cuo - iu0 % I.col_u) + I.col_u) % I.col_u;
-            const int va = iv0 + ((cvo - iv0 % I.col_v) + I.col_v) % I.col_v;
-            const int nuc = ua <= iu1 ? (iu1 - ua) / I.col_u + 1 : 0;
-            const int nvc = va <= iv1 ? (iv1 - va) / I.col_v + 1 : 0;
-            for (int j = threadIdx.x; j < nuc * nvc; j += BB_THREADS) {
-                const int iu = ua + (j % nuc) * I.col_u, iv = va + (j / nuc) * I.col_v;
-                const float w = sview[(size_t)iv * I.nu + iu];
-                if (w == 0.f) continue;
-                const RayXY R = tab[k * I.nu + iu];
-                const RayZ Z = ray_z(R, rows[iv], I.zoff);
-                const float xi0[3] = {R.xi0x, R.xi0y, Z.xi0z};
-                const float ev[3] = {R.ex, R.ey, Z.ez};
-                const float inv[3] = {R.inv_ex, R.inv_ey, Z.inv_ez};
-                // the brick's slab intervals
-                float tmin = -INFINITY, tmax = INFINITY;
-                int cur[3];
-                bool miss = false;
+        if (threadIdx.x == 0) s_max = 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int c = 0;
+            for (int j = 0; j < nvw; ++j) {
+                s_cum[j] = c;
+                c += s_rng[j][3] >= s_rng[j][2] ? s_rng[j][1] - s_rng[j][0] + 1 : 0;
+            }
+            s_cum[nvw] = c;
+        }
+        // largest |scaled residual| of the group's views
+        if (threadIdx.x < nvw) atomicMax(&s_max, view_max[I.view0 + kg + threadIdx.x]);
+        __syncthreads();
+        const float amax = __uint_as_float(s_max);
+        bad = bad || !(amax <= 3.0e38f);
+        // fixed-point step: VGROUP x col_u x col_v x tchord x amax x S < 2^30
+        float S = 1.f;
+        {
+            const float bound = (float)(VGROUP * I.col_u * I.col_v) * tchord * amax;
+            if (bound > 0.f && bound <= 3.0e38f) {
+                int ex;
+                frexpf(bound, &ex);  // bound < 2^ex
+                S = ldexpf(1.f, min(30 - ex, 126));
+            }
+        }
+        const int nitems = s_cum[nvw];
+        for (int item = w; item < nitems; item += BB_THREADS / 32) {  // warp-uniform
+            int j = 0;
+            while (j + 1 < nvw && s_cum[j + 1] <= item) ++j;
+            const int k = kg + j;
+            const int iu = s_rng[j][0] + item - s_cum[j];
+            const int iv0 = s_rng[j][2], iv1 = s_rng[j][3];
+            const RayXY R = tab[k * I.nu + iu];
+            // the brick's (x, y) box along this column's path (uniform)
+            float tmin = -INFINITY, tmax = INFINITY;
+            bool miss = false;
+            float fx = 0.f, fy = 0.f;
+            if (R.ex != 0.f) {
+                const float ta = plane_t(x0, R.xi0x, R.inv_ex), tb = plane_t(x1, R.xi0x, R.inv_ex);
+                tmin = fmaxf(tmin, fminf(ta, tb));
+                tmax = fminf(tmax, fmaxf(ta, tb));
+            } else {
+                fx = floorf(R.xi0x);
+                miss = miss || !(fx >= (float)x0 && fx < (float)x1);
+            }
+            if (R.ey != 0.f) {
+                const float ta = plane_t(y0, R.xi0y, R.inv_ey), tb = plane_t(y1, R.xi0y, R.inv_ey);
+                tmin = fmaxf(tmin, fminf(ta, tb));
+                tmax = fminf(tmax, fmaxf(ta, tb));
+            } else {
+                fy = floorf(R.xi0y);
+                miss = miss || !(fy >= (float)y0 && fy < (float)y1);
+            }
+            if (miss || !(tmax > tmin)) continue;
+            const int sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
+            const int sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
+            const int ixe = sgx ? entry_cell(tmin, R.ex, R.xi0x, R.inv_ex, sgx, x0, x1 - 1) : (int)fx;
+            const int iye = sgy ? entry_cell(tmin, R.ey, R.xi0y, R.inv_ey, sgy, y0, y1 - 1) : (int)fy;
+            const int dcx = sgx * BBZ, dcy = sgy * BBX * BBZ;  // cell steps in shared memory
+            const float *sv = sview0 + (size_t)k * I.nv * I.nu + iu;
+            for (int r0 = iv0; r0 <= iv1; r0 += 32 * SLOTS) {
+                // per lane and slot: row, scaled residual x S, z entry layer
+                // (unbounded, brick-local), next z crossing
+                int iz[SLOTS], sgz[SLOTS], lim[SLOTS];
+                float tz[SLOTS], fz[SLOTS], fsg[SLOTS], xz[SLOTS], iez[SLOTS], wq[SLOTS];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (ev[a] != 0.f) {
-                        const float ta = plane_t(N0[a], xi0[a], inv[a]), tb = plane_t(N1[a], xi0[a], inv[a]);
-                        tmin = fmaxf(tmin, fminf(ta, tb));
-                        tmax = fminf(tmax, fmaxf(ta, tb));
+                for (int s = 0; s < SLOTS; ++s) {
+                    const int iv = r0 + 32 * s + lane;
+                    const bool act = iv <= iv1;
+                    const RowZ row = rows[act ? iv : iv0];
+                    const RayZ Z = ray_z(R, row, I.zoff);
+                    const float wr = act ? sv[(size_t)iv * I.nu] : 0.f;
+                    wq[s] = wr * S;
+                    lim[s] = (act && wr != 0.f) ? nzb : 0;  // brick-local zl < lim: add
+                    xz[s] = Z.xi0z;
+                    iez[s] = Z.inv_ez;
+                    tz[s] = INFINITY;
+                    fz[s] = 0.f;
+                    sgz[s] = 0;
+                    fsg[s] = 0.f;
+                    if (Z.ez != 0.f) {
+                        sgz[s] = Z.ez > 0.f ? 1 : -1;
+                        fsg[s] = (float)sgz[s];
+                        iz[s] = entry_cell(tmin, Z.ez, Z.xi0z, Z.inv_ez, sgz[s], INT_MIN / 2, INT_MAX / 2);
+                        fz[s] = (float)(sgz[s] > 0 ? iz[s] + 1 : iz[s]);
+                        tz[s] = (fz[s] - Z.xi0z) * Z.inv_ez;
                     } else {
-                        const float f = floorf(xi0[a]);
-                        miss = miss || !(f >= (float)N0[a] && f < (float)N1[a]);
-                        cur[a] = (int)f;
+                        iz[s] = (int)fmaxf(fminf(floorf(Z.xi0z), (float)(INT_MAX / 2)), (float)(INT_MIN / 2));
                     }
+                    iz[s] -= z0;
                 }
-                if (miss || !(tmax > tmin)) continue;
-                int sg[3];
-                float tn[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (ev[a] != 0.f) {
-                        const int d = ev[a] > 0.f ? 1 : -1;
-                        sg[a] = d;
-                        int i = (int)floorf(fmaf(tmin, ev[a], xi0[a]));
-                        i = min(max(i, N0[a]), N1[a] - 1);
-                        for (int it = 0; it < 3; ++it) {
-                            const float tu = plane_t(d > 0 ? i + 1 : i, xi0[a], inv[a]);
-                            if (tu <= tmin && i + d >= N0[a] && i + d < N1[a]) i += d; else break;
-                        }
-                        for (int it = 0; it < 3; ++it) {
-                            const float tl = plane_t(d > 0 ? i : i + 1, xi0[a], inv[a]);
-                            if (tl > tmin && i - d >= N0[a] && i - d < N1[a]) i -= d; else break;
-                        }
-                        cur[a] = i;
-                        tn[a] = plane_t(d > 0 ? i + 1 : i, xi0[a], inv[a]);
-                    } else {
-                        sg[a] = 0;
-                        tn[a] = INFINITY;
-                    }
-                }
-                int ix = cur[0] - x0, iy = cur[1] - y0, iz = cur[2] - z0;
+                int ix = ixe, iy = iye;
+                float tx = sgx ? plane_t(sgx > 0 ? ix + 1 : ix, R.xi0x, R.inv_ex) : INFINITY;
+                float ty = sgy ? plane_t(sgy > 0 ? iy + 1 : iy, R.xi0y, R.inv_ey) : INFINITY;
+                int cell = ((iy - y0) * BBX + (ix - x0)) * BBZ;
                 float t = tmin;
-                for (int it = 0; it < BBX + BBY + BBZ + 3; ++it) {
-                    const float tnext = fminf(tn[0], fminf(tn[1], tn[2]));
-                    const float len = tnext - t;
-                    if (len > 0.f) {
-                        float *cell = &acc[(iz * BBY + iy) * BBX + ix];
-                        *cell = fmaf(len, w, *cell);
+                for (int it = 0; it < BBX + BBY + 2; ++it) {
+                    const float t1 = fminf(tx, ty);
+#pragma unroll
+                    for (int s = 0; s < SLOTS; ++s) {
+                        const float m = fminf(tz[s], t1);
+                        const int q0 = __float2int_rn((m - t) * wq[s]);
+                        if ((unsigned)iz[s] < (unsigned)lim[s]) atomicAdd(acci + cell + iz[s], q0);
+                        if (tz[s] < t1) {  // a z plane inside this cell
+                            float ts = tz[s];
+                            iz[s] += sgz[s];
+                            fz[s] += fsg[s];
+                            tz[s] = (fz[s] - xz[s]) * iez[s];
+                            const int q1 = __float2int_rn((fminf(tz[s], t1) - ts) * wq[s]);
+                            if ((unsigned)iz[s] < (unsigned)lim[s]) atomicAdd(acci + cell + iz[s], q1);
+                            // rare: further planes in the same cell (bounded)
+                            for (int rep = 0; rep <= nzb && tz[s] < t1; ++rep) {
+                                ts = tz[s];
+                                iz[s] += sgz[s];
+                                fz[s] += fsg[s];
+                                tz[s] = (fz[s] - xz[s]) * iez[s];
+                                if ((unsigned)iz[s] < (unsigned)lim[s])
+                                    atomicAdd(acci + cell + iz[s], __float2int_rn((fminf(tz[s], t1) - ts) * wq[s]));
+                            }
+                        }
                     }
-                    t = tnext;
-                    if (tnext == tn[0]) {
-                        ix += sg[0];
-                        if (ix < 0 || ix >= x1 - x0) break;
-                        tn[0] = plane_t(x0 + ix + (sg[0] > 0), xi0[0], inv[0]);
-                    } else if (tnext == tn[1]) {
-                        iy += sg[1];
-                        if (iy < 0 || iy >= y1 - y0) break;
-                        tn[1] = plane_t(y0 + iy + (sg[1] > 0), xi0[1], inv[1]);
+                    t = t1;
+                    if (tx <= ty) {
+                        const int ni = ix + sgx;
+                        if (ni < x0 || ni >= x1) break;
+                        ix = ni;
+                        cell += dcx;
+                        tx = plane_t(ni + (sgx > 0), R.xi0x, R.inv_ex);
                     } else {
-                        iz += sg[2];
-                        if (iz < 0 || iz >= z1 - z0) break;
-                        tn[2] = plane_t(z0 + iz + (sg[2] > 0), xi0[2], inv[2]);
+                        const int ni = iy + sgy;
+                        if (ni < y0 || ni >= y1) break;
+                        iy = ni;
+                        cell += dcy;
+                        ty = plane_t(ni + (sgy > 0), R.xi0y, R.inv_ey);
                     }
                 }
             }
-            __syncthreads();  // the next class may touch the same voxels
         }
+        __syncthreads();
+        // the group's integer sums into the FP32 sums (each voxel by one thread)
+        const float inv_s = 1.f / S;  // a power of two: exact
+        for (int i = threadIdx.x; i < BBV; i += BB_THREADS) {
+            accf[i] += (float)acci[i] * inv_s;
+            acci[i] = 0;
+        }
+        // s_rng, s_cum and s_max are rewritten by the next group after its first barrier
+        __syncthreads();
     }
     // write the brick (x fastest)
-    const size_t zs = (size_t)g.nx * g.ny;
-    for (int i = threadIdx.x; i < BBZ * BBY * BBX; i += BB_THREADS) {
+    for (int i = threadIdx.x; i < BBX * BBY * BBZ; i += BB_THREADS) {
         const int xx = i % BBX, yy = (i / BBX) % BBY, zz = i / (BBX * BBY);
         const int x = x0 + xx, y = y0 + yy, z = z0 + zz;
-        if (x < x1 && y < y1 && z < z1) I.vol[(size_t)z * zs + (size_t)y * g.nx + x] = acc[i];
+        if (x < x1 && y < y1 && z < z1)
+            I.vol[((size_t)z * g.ny + y) * g.nx + x] = bad ? NAN : accf[(yy * BBX + xx) * BBZ + zz];
     }
 }
 
@@ -634,7 +986,7 @@ void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv) {
     cv = (int)floor(1.1 * wv + 0.05) + 1;
 }
 
-static int g_bp_variant = 0;  // 0: column gather, 1: brick scatter
+static int g_bp_variant = 0;  // 0: brick scatter, 1: column gather
 int backprojector_variant() { return g_bp_variant; }
 void set_backprojector_variant(int v) { g_bp_variant = v; }
 
@@ -652,19 +1004,57 @@ cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st) {
-    const long long blocks = (B.tot_rays + 127) / 128;
-    if (blocks == 0) return cudaSuccess;
-    k_project<<<(unsigned)blocks, 128, 0, st>>>(B, const_cast<RayXY *>(tab));
+cudaError_t launch_project(const Batch &B0, const RayXY *tab, cudaStream_t st) {
+    // row-warp projector when every volume is z fastest, else per-ray
+    bool zfast = B0.n > 0;
+    for (int i = 0; i < B0.n; ++i) zfast = zfast && B0.in[i].vsz == 1;
+    if (!zfast) {
+        const long long blocks = (B0.tot_rays + 127) / 128;
+        if (blocks == 0) return cudaSuccess;
+        k_project_ray<<<(unsigned)blocks, 128, 0, st>>>(B0, const_cast<RayXY *>(tab));
+        counted(1);
+        return cudaGetLastError();
+    }
+    // projector blocks: one detector column x PR_ROWS rows of one view
+    static thread_local Batch B;
+    B = B0;
+    int pb = 0;
+    for (int i = 0; i < B.n; ++i) {
+        Inst &I = B.in[i];
+        I.npv = (I.nv + PR_ROWS - 1) / PR_ROWS;
+        I.pb0 = pb;
+        pb += I.n_views * I.nu * I.npv;
+    }
+    if (pb == 0) return cudaSuccess;
+    k_project<<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab));
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cudaStream_t st) {
+    dim3 grid((g.nx + 31) / 32, g.ny, (g.nz + 31) / 32);
+    k_vol_zfast<<<grid, 256, 0, st>>>(src, dst, g.nx, g.ny, g.nz);
     counted(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, cudaStream_t st) {
-    if (g_bp_variant == 1) {
-        k_scale_dn<<<(unsigned)((B.tot_rays + 255) / 256), 256, 0, st>>>(B, const_cast<RayXY *>(tab),
-                                                                         sino_scaled);
-        k_bp_brick<<<B.tot_bricks, BB_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled);
+    if (g_bp_variant == 0) {
+        unsigned *view_max = reinterpret_cast<unsigned *>(sino_scaled + (B.tot_rays + 63) / 64 * 64);
+        cudaError_t e = cudaMemsetAsync(view_max, 0, sizeof(unsigned) * B.tot_views, st);
+        if (e != cudaSuccess) return e;
+        int max_per = 1;
+        for (int i = 0; i < B.n; ++i) max_per = max(max_per, B.in[i].nu * B.in[i].nv);
+        k_scale_dn<<<dim3((max_per + 255) / 256, B.tot_views), 256, 0, st>>>(B, const_cast<RayXY *>(tab),
+                                                                           sino_scaled, view_max);
+        const int smem = 2 * BBV * (int)sizeof(float);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_bp_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            attr = true;
+        }
+        k_bp_brick<<<B.tot_bricks, BB_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), sino_scaled,
+                                                           view_max);
         counted(2);
         return cudaGetLastError();
     }
@@ -695,6 +1085,9 @@ cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY 
     I.beam = geo.beam; I.n_views = geo.n_views; I.nu = geo.nu; I.nv = geo.nv;
     I.pu = geo.pu; I.pv = geo.pv; I.dso = geo.dso; I.dsd = geo.dsd; I.angles = geo.angles;
     I.vol = const_cast<float *>(vol);
+    I.vsx = 1;
+    I.vsy = g.nx;
+    I.vsz = g.nx * g.ny;
     I.sino = sino;
     B.tot_tab = geo.n_views * geo.nu;
     B.tot_views = geo.n_views;

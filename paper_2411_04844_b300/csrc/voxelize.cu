@@ -397,11 +397,21 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
             }
         }
         if (x < g.nx && y < g.ny) {
-            float *col = I.vol + (size_t)y * g.nx + x;
-            const size_t zs = (size_t)g.nx * g.ny;
+            // element strides: x fastest (the C ABI's layout) or z fastest
+            // (the step's internal layout, read by the row-warp projector)
+            float *col = I.vol + (size_t)x * I.vsx + (size_t)y * I.vsy;
+            if (I.vsz == 1 && (g.nz & 3) == 0 && z0 + TZ <= g.nz &&
+                (reinterpret_cast<uintptr_t>(I.vol) & 15) == 0) {
 #pragma unroll
-            for (int k = 0; k < TZ; ++k)
-                if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+                for (int k = 0; k < TZ; k += 4)
+                    *reinterpret_cast<float4 *>(col + z0 + k) =
+                        make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+            } else {
+                const size_t zs = (size_t)I.vsz;
+#pragma unroll
+                for (int k = 0; k < TZ; ++k)
+                    if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+            }
         }
     }
 }

@@ -242,6 +242,8 @@ def make_plan(grid: Grid = None, n: int = 0, max_pairs: int = 0, max_items: int 
     p.max_items = int(max_items)
     if geom is not None:
         p.max_views, p.max_nu, p.max_nv = int(geom.n_views), int(geom.nu), int(geom.nv)
+        if grid is not None:  # room for dgr_project's z-fastest copy of the volume
+            p.max_vox = grid.nx * grid.ny * grid.nz
     if step:
         p.max_vox = grid.nx * grid.ny * grid.nz
         p.max_rays = geom.n_views * geom.nu * geom.nv

@@ -227,7 +227,7 @@ def test_project_and_backproject_parity(case):
 
 @pytest.mark.parametrize("variant", [0, 1])
 def test_backproject_variants_agree_and_are_deterministic(variant):
-    """Both backprojectors (column gather, brick scatter) give the oracle's
+    """Both backprojectors (brick scatter, column gather) give the oracle's
     transpose on the workload's cone geometry at reduced size, bit-identically
     run to run."""
     gs = synth.GridSpec((64, 48, 40), 1.0, (-32.0, -24.0, -20.0))
