@@ -111,15 +111,18 @@ int dgr_set_deterministic(int on);
  * CTAs for small grids.  A process-wide setting, chosen by the autotuner
  * (paper_2411_04844_b300/autotune.py); workspace plans depend on it. */
 int dgr_set_tile_depth(int tz);
-/* Backprojector implementation (both exact transposes of dgr_project, both
- * bit-reproducible): 0 (default) = brick scatter -- a CTA accumulates a voxel
- * brick in shared memory, its warps walking the detector columns that cross
- * it, each lane carrying several detector rows; segment contributions are
- * added as fixed-point integers (exact, order-independent), the step chosen
- * per group of views from the largest residual so that no sum overflows, then
- * folded into FP32 sums in a fixed order; 1 = column gather -- a warp per
- * voxel column finds the candidate rays of each voxel in closed form.  A
- * process-wide setting. */
+/* Backprojector implementation (all exact transposes of dgr_project, all
+ * bit-reproducible): 0 (default) = ray scatter -- a CTA per detector column
+ * walks the column's path like the projector and adds into integer sums in
+ * the workspace (needs a plan whose max_vox covers the volumes, else the
+ * brick scatter runs); 1 = column gather -- a warp per voxel column finds the
+ * candidate rays of each voxel in closed form; 2 = brick scatter -- a CTA
+ * accumulates a voxel brick in shared memory, its warps walking the detector
+ * columns that cross it, each lane carrying several detector rows.  The two
+ * scatters add the same fixed-point integers (exact, order-independent; the
+ * step is chosen per group of 64 views from the largest residual so that no
+ * sum can overflow) and fold them into FP32 sums in a fixed order: they
+ * return the same bits.  A process-wide setting. */
 int dgr_set_backprojector(int variant);
 
 /* Footprint integers (paper Sec. 4.1 "Gaussian Effect Confinement",

@@ -62,7 +62,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA; }
 
 struct Layout {
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, list_tmp, total;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, list_tmp, acc, total;
     size_t scan_elems;
 };
 
@@ -105,6 +105,8 @@ Layout layout_of(const dgr_ws_plan &p) {
     // instance volumes start on 64-float boundaries (vectorised stores)
     L.vol = take(4 * ((size_t)p.max_vox + (size_t)64 * (p.max_inst > 1 ? p.max_inst : 1)));
     L.sino = take(4 * (size_t)p.max_rays);
+    // integer sums of the ray-driven backprojector (z fastest), kept zero between calls
+    L.acc = take(p.max_vox > 0 ? 4 * ((size_t)p.max_vox + (size_t)64 * (p.max_inst > 1 ? p.max_inst : 1)) : 0);
     L.total = o;
     return L;
 }
@@ -138,8 +140,10 @@ int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan) {
     w->vol = L.vol; w->sino = L.sino; w->loss_part = L.loss_part; w->rayxy = L.rayxy;
     w->sino_scaled = L.sino_scaled;
     w->list_tmp = L.list_tmp;
+    w->acc = L.acc;
     w->scan_tmp_elems = L.scan_elems;
-    if (cudaMemset(w->base + L.status, 0, 256) != cudaSuccess) {
+    if (cudaMemset(w->base + L.status, 0, 256) != cudaSuccess ||
+        cudaMemset(w->base + L.acc, 0, L.total - L.acc) != cudaSuccess) {
         cudaFree(w->base);
         delete w;
         return DGR_ERR_CUDA;
@@ -192,7 +196,7 @@ int dgr_set_deterministic(int on) {
 }
 
 int dgr_set_backprojector(int variant) {
-    if (variant != 0 && variant != 1) return DGR_ERR_ARG;
+    if (variant < 0 || variant > 2) return DGR_ERR_ARG;
     set_backprojector_variant(variant);
     return DGR_OK;
 }
@@ -434,7 +438,7 @@ int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sin
     if (rc) return rc;
     RayXY *tab = ws_ptr<RayXY>(ws, ws->rayxy);
     cudaError_t e = launch_ray_tables(*B, tab, stream);
-    if (e == cudaSuccess) e = launch_backproject(*B, tab, ws_ptr<float>(ws, ws->sino_scaled), stream);
+    if (e == cudaSuccess) e = launch_backproject(*B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, stream);
     return cuda_rc(e);
 }
 
@@ -525,7 +529,7 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
     if (e == cudaSuccess) e = mark(2);
     if (e == cudaSuccess) e = launch_l1(B, ws_ptr<float>(ws, ws->loss_part), stream);
     if (e == cudaSuccess) e = mark(3);
-    if (e == cudaSuccess) e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), stream);
+    if (e == cudaSuccess) e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, stream);
     if (e == cudaSuccess) e = mark(4);
     if (e == cudaSuccess) e = launch_voxelize_backward(B, prep, ws, stream);
     if (e == cudaSuccess) e = mark(5);

@@ -117,7 +117,10 @@ struct Inst {
     int blk0, nbx, nbz;               // column backprojector: first CTA, CTAs in x, z passes
     int bb0, nbbx, nbby, nbbz;        // brick backprojector: first brick, bricks per axis
     int col_u, col_v;                 // ray colour classes (footprint < col pixels)
-    int pb0, npv;                     // projector: first CTA, row groups
+    int pb0, npv;                     // projector / ray scatter: first CTA, row groups
+    int kv0, nkv;                     // views of this launch (ray scatter: one view group)
+    int fb0;                          // ray scatter fold: first tile
+    int *acc;                         // ray scatter: integer sums (z fastest)
     int vsx, vsy, vsz;                // element strides of vol as voxelize output / project input
     float *vol;                       // volume (voxelize output; step: volume, then its gradient)
     float *sino;                      // projection (step: prediction, then residual)
@@ -185,7 +188,7 @@ struct dgr_ws {
     dgr_ws_plan plan;
     // byte offsets into base
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, losses, list_tmp;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, losses, list_tmp, acc;
     size_t scan_tmp_elems;
 };
 
@@ -221,7 +224,9 @@ cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st);
 // x-fastest -> z-fastest copy of a volume (the row-warp projector's layout)
 cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cudaStream_t st);
 // sino_scaled: scratch of all instances' rays (residual x |D|, [view][u][v]); not aliasing sino
-cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, cudaStream_t st);
+// acc: the workspace's integer sums (ray scatter), room for acc_vox voxels
+cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, int *acc,
+                               long long acc_vox, cudaStream_t st);
 // the projector of one instance with caller-provided tables (no workspace)
 cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY *tab,
                                   const float *vol, float *sino, cudaStream_t st);

@@ -198,10 +198,32 @@ __device__ __forceinline__ int count_before(float T, int n, int p0, int sg, floa
     return lo;
 }
 
-template <bool MASKZ>
-__device__ __forceinline__ void walk_segs(const float *__restrict__ vol, const Seg *seg, int c0, int c1,
-                                          int nz, float &t, float &acc, int &iz, float &fz, float &tz,
-                                          int sgz, float xi0z, float iez) {
+// fixed-point step of one group of views of an instance: the largest power
+// of two S with VGROUP x col_u x col_v x (longest chord in t units) x
+// max |scaled residual| x S < 2^30, so that a voxel's integer sum over the
+// group cannot overflow (a voxel meets at most col_u x col_v rays per view).
+// Returns 0 if a residual of the group is not finite.
+constexpr int VGROUP = 64;
+__device__ __forceinline__ float group_step(const Inst &I, const unsigned *view_max, int kv0, int nkv) {
+    unsigned m = 0u;
+    for (int j = 0; j < nkv; ++j) m = max(m, view_max[I.view0 + kv0 + j]);
+    const float amax = __uint_as_float(m);
+    if (!(amax <= 3.0e38f)) return 0.f;
+    // longest chord of a voxel in t units: sqrt(3) h / |D|, |D| >= dsd (cone) or 1 (parallel)
+    const float tchord = 1.7320509f * I.g.h / (I.beam == DGR_CONE ? I.dsd : 1.f) * 1.001f;
+    const float bound = (float)(VGROUP * I.col_u * I.col_v) * tchord * amax;
+    if (!(bound > 0.f)) return 1.f;
+    int ex;
+    frexpf(bound, &ex);  // bound < 2^ex
+    return ldexpf(1.f, min(30 - ex, 126));
+}
+
+// MODE 0 (project): acc += length x volume value.  MODE 1 (backproject
+// scatter): the integer sums at the same voxels += round(length x wq).
+template <int MODE, bool MASKZ>
+__device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__restrict__ acci, float wq,
+                                          const Seg *seg, int c0, int c1, int nz, float &t, float &acc,
+                                          int &iz, float &fz, float &tz, int sgz, float xi0z, float iez) {
     const unsigned zmax = (unsigned)(nz - 1);
     int zc = (int)min((unsigned)iz, zmax);
     const float fsg = (float)sgz;
@@ -235,26 +257,46 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, const S
                     fz += fsg;
                     tz = (fz - xi0z) * iez;
                     zc = (int)min((unsigned)iz, zmax);
-                    if (!MASKZ || (unsigned)iz <= zmax)
-                        acc = fmaf(fminf(tz, t1) - ts, __ldg(vol + S.cb + zc), acc);
+                    if (!MASKZ || (unsigned)iz <= zmax) {
+                        const float len = fminf(tz, t1) - ts;
+                        if (MODE == 0) acc = fmaf(len, __ldg(vol + S.cb + zc), acc);
+                        else if (len != 0.f) atomicAdd(acci + S.cb + zc, __float2int_rn(len * wq));
+                    }
                 }
             }
             t = t1;
         }
-        float v0[WALK], v1[WALK];
+        if (MODE == 0) {
+            float v0[WALK], v1[WALK];
 #pragma unroll
-        for (int j = 0; j < WALK; ++j) {
-            v0[j] = __ldg(vol + a0[j]);
-            v1[j] = __ldg(vol + a1[j]);
+            for (int j = 0; j < WALK; ++j) {
+                v0[j] = __ldg(vol + a0[j]);
+                v1[j] = __ldg(vol + a1[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
+        } else {
+#pragma unroll
+            for (int j = 0; j < WALK; ++j) {
+                if (l0[j] != 0.f) atomicAdd(acci + a0[j], __float2int_rn(l0[j] * wq));
+                if (l1[j] != 0.f) atomicAdd(acci + a1[j], __float2int_rn(l1[j] * wq));
+            }
         }
-#pragma unroll
-        for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
     }
 }
 
-// blockIdx.x: global projector block (instance, view, row group, column)
-__global__ void __launch_bounds__(PR_THREADS) k_project(const __grid_constant__ Batch B,
-                                                        RayXY *__restrict__ tab_base) {
+// MODE 0: a4, the projector.  MODE 1: a6, the ray-driven backprojector for
+// the views [kv0, kv0 + nkv) of every instance: each lane's row adds
+// length x scaled residual, in the fixed point of its view group, into
+// integer sums laid out like the projector's volume (z fastest); k_bp_fold
+// then moves them into the FP32 gradient.  Integer sums do not depend on the
+// order of the additions, so the result is bit-reproducible.
+// blockIdx.x: global block (instance, view of the launch, row group, column).
+template <int MODE>
+__global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Batch B,
+                                                     RayXY *__restrict__ tab_base,
+                                                     const float *__restrict__ sino_s,
+                                                     const unsigned *__restrict__ view_max) {
     __shared__ Seg seg[SEG_MAX + WALK];
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
     int ii = 0;
@@ -262,12 +304,12 @@ __global__ void __launch_bounds__(PR_THREADS) k_project(const __grid_constant__ 
     const Inst &I = B.in[ii];
     const dgr_grid &g = I.g;
     const int b = blockIdx.x - I.pb0;
-    const int iu = b % I.nu, rg = (b / I.nu) % I.npv, k = b / (I.nu * I.npv);
+    const int iu = b % I.nu, rg = (b / I.nu) % I.npv, k = I.kv0 + b / (I.nu * I.npv);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int iv = rg * PR_ROWS + w * 32 + lane;
     const RayXY R = T.tab[I.tab0 + k * I.nu + iu];
     const RowZ row = T.rows[I.row0 + min(iv, I.nv - 1)];
-    float *sino_out = I.sino + ((size_t)k * I.nv + min(iv, I.nv - 1)) * I.nu + iu;
+    const size_t ray = ((size_t)k * I.nv + min(iv, I.nv - 1)) * I.nu + iu;
     // (x, y) interval of the grid and entry cell: the same for the whole CTA
     float tmin = -INFINITY, tmax = INFINITY;
     bool miss = false;
@@ -289,8 +331,14 @@ __global__ void __launch_bounds__(PR_THREADS) k_project(const __grid_constant__ 
         miss = miss || !(fy >= 0.f && fy < (float)g.ny);
     }
     if (miss || !(tmax > tmin)) {  // CTA-uniform
-        if (iv < I.nv) *sino_out = 0.f;
+        if (MODE == 0 && iv < I.nv) I.sino[ray] = 0.f;
         return;
+    }
+    float wq = 0.f;  // MODE 1: this row's scaled residual in fixed point
+    if (MODE == 1) {
+        const float S = group_step(I, view_max, I.kv0, I.nkv);
+        wq = iv < I.nv ? sino_s[I.ray0 + ray] * S : 0.f;
+        if (__syncthreads_and(wq == 0.f)) return;  // nothing to add (or a bad group)
     }
     const int sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
     const int sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
@@ -362,11 +410,51 @@ __global__ void __launch_bounds__(PR_THREADS) k_project(const __grid_constant__ 
         }
         __syncthreads();
         if (masked)
-            walk_segs<true>(I.vol, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z, Z.inv_ez);
+            walk_segs<MODE, true>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z,
+                                  Z.inv_ez);
         else
-            walk_segs<false>(I.vol, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z, Z.inv_ez);
+            walk_segs<MODE, false>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z,
+                                   Z.inv_ez);
     }
-    if (iv < I.nv) *sino_out = acc * ray_norm(R, row, I.beam);
+    if (MODE == 0 && iv < I.nv) I.sino[ray] = acc * ray_norm(R, row, I.beam);
+}
+
+// a6, last step of the ray-driven backprojector: after a group of views, the
+// integer sums (z fastest) are scaled by the group's fixed-point step and
+// added to the FP32 gradient ([nz][ny][nx]; the first group writes it), then
+// cleared.  A 32 x 32 (x, z) tile at one y goes through shared memory so both
+// sides are coalesced.  blockIdx.x: global tile of the instances in the group.
+__global__ void k_bp_fold(const __grid_constant__ Batch B, const unsigned *__restrict__ view_max) {
+    __shared__ float tile[32][33];
+    int ii = 0;
+    while (ii + 1 < B.n && B.in[ii + 1].fb0 <= (int)blockIdx.x) ++ii;
+    const Inst &I = B.in[ii];
+    if (I.nkv <= 0) return;
+    const dgr_grid &g = I.g;
+    const int ntx = (g.nx + 31) / 32, ntz = (g.nz + 31) / 32;
+    const int b = blockIdx.x - I.fb0;
+    const int bx = b % ntx, y = (b / ntx) % g.ny, bzt = b / (ntx * g.ny);
+    if (bzt >= ntz) return;
+    const float S = group_step(I, view_max, I.kv0, I.nkv);
+    const float inv_s = S > 0.f ? 1.f / S : 0.f;  // a power of two: exact
+    const int x0 = bx * 32, z0 = bzt * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int j = ty; j < 32; j += 8) {  // read along z
+        const int x = x0 + j, z = z0 + tx;
+        if (x < g.nx && z < g.nz) {
+            int *p = I.acc + ((size_t)x * g.ny + y) * g.nz + z;
+            tile[j][tx] = S > 0.f ? (float)*p * inv_s : NAN;
+            *p = 0;
+        }
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {  // write along x
+        const int z = z0 + j, x = x0 + tx;
+        if (x < g.nx && z < g.nz) {
+            float *q = I.vol + ((size_t)z * g.ny + y) * g.nx + x;
+            *q = I.kv0 == 0 ? tile[tx][j] : *q + tile[tx][j];
+        }
+    }
 }
 
 // a4 (per-ray projector, for volumes in the C ABI's x-fastest layout when no
@@ -721,7 +809,6 @@ constexpr int BBX = 8, BBY = 8, BBZ = 88;
 constexpr int BBV = BBX * BBY * BBZ;
 constexpr int BB_THREADS = 256;
 constexpr int SLOTS = 3;
-constexpr int VGROUP = 8;
 
 __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__ Batch B,
                                                           RayXY *__restrict__ tab_base,
@@ -731,7 +818,6 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
     int *acci = reinterpret_cast<int *>(accf + BBV);  // the group's fixed-point sums
     __shared__ int s_rng[VGROUP][4];         // iu0, iu1, iv0, iv1 of each view of the group
     __shared__ int s_cum[VGROUP + 1];        // items before each view
-    __shared__ unsigned s_max;               // largest |scaled residual| of the group (bits)
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
     int ii = 0;
     while (ii + 1 < B.n && B.in[ii + 1].bb0 <= (int)blockIdx.x) ++ii;
@@ -756,8 +842,6 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
     const float wx0 = g.ox + x0 * h, wx1 = g.ox + x1 * h, wy0 = g.oy + y0 * h, wy1 = g.oy + y1 * h;
     const float wz0 = g.oz + z0 * h, wz1 = g.oz + z1 * h;
     const int nzb = z1 - z0;
-    // longest chord of a voxel in t units: sqrt(3) h / |D|, |D| >= dsd (cone) or 1 (parallel)
-    const float tchord = 1.7320509f * h / (cone ? I.dsd : 1.f) * 1.001f;
     bool bad = false;  // a non-finite residual: the brick becomes NaN
     for (int kg = 0; kg < I.n_views; kg += VGROUP) {
         const int nvw = min(VGROUP, I.n_views - kg);
@@ -781,7 +865,6 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
             s_rng[threadIdx.x][2] = iv0;
             s_rng[threadIdx.x][3] = (iv1 >= iv0 && iu1 >= iu0) ? iv1 : iv0 - 1;
         }
-        if (threadIdx.x == 0) s_max = 0u;
         __syncthreads();
         if (threadIdx.x == 0) {
             int c = 0;
@@ -791,21 +874,10 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
             }
             s_cum[nvw] = c;
         }
-        // largest |scaled residual| of the group's views
-        if (threadIdx.x < nvw) atomicMax(&s_max, view_max[I.view0 + kg + threadIdx.x]);
         __syncthreads();
-        const float amax = __uint_as_float(s_max);
-        bad = bad || !(amax <= 3.0e38f);
-        // fixed-point step: VGROUP x col_u x col_v x tchord x amax x S < 2^30
-        float S = 1.f;
-        {
-            const float bound = (float)(VGROUP * I.col_u * I.col_v) * tchord * amax;
-            if (bound > 0.f && bound <= 3.0e38f) {
-                int ex;
-                frexpf(bound, &ex);  // bound < 2^ex
-                S = ldexpf(1.f, min(30 - ex, 126));
-            }
-        }
+        // the group's fixed-point step (0: a non-finite residual)
+        const float S = group_step(I, view_max, kg, nvw);
+        bad = bad || S == 0.f;
         const int nitems = s_cum[nvw];
         for (int item = w; item < nitems; item += BB_THREADS / 32) {  // warp-uniform
             int j = 0;
@@ -921,12 +993,12 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
         }
         __syncthreads();
         // the group's integer sums into the FP32 sums (each voxel by one thread)
-        const float inv_s = 1.f / S;  // a power of two: exact
+        const float inv_s = S > 0.f ? 1.f / S : 0.f;  // a power of two: exact
         for (int i = threadIdx.x; i < BBV; i += BB_THREADS) {
             accf[i] += (float)acci[i] * inv_s;
             acci[i] = 0;
         }
-        // s_rng, s_cum and s_max are rewritten by the next group after its first barrier
+        // s_rng and s_cum are rewritten by the next group after its first barrier
         __syncthreads();
     }
     // write the brick (x fastest)
@@ -986,7 +1058,7 @@ void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv) {
     cv = (int)floor(1.1 * wv + 0.05) + 1;
 }
 
-static int g_bp_variant = 0;  // 0: brick scatter, 1: column gather
+static int g_bp_variant = 0;  // 0: ray scatter, 1: column gather, 2: brick scatter
 int backprojector_variant() { return g_bp_variant; }
 void set_backprojector_variant(int v) { g_bp_variant = v; }
 
@@ -1023,10 +1095,12 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, cudaStream_t st) {
         Inst &I = B.in[i];
         I.npv = (I.nv + PR_ROWS - 1) / PR_ROWS;
         I.pb0 = pb;
+        I.kv0 = 0;
+        I.nkv = I.n_views;
         pb += I.n_views * I.nu * I.npv;
     }
     if (pb == 0) return cudaSuccess;
-    k_project<<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab));
+    k_path<0><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     counted(1);
     return cudaGetLastError();
 }
@@ -1038,8 +1112,53 @@ cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, cudaStream_t st) {
-    if (g_bp_variant == 0) {
+// ray-driven backprojector: per group of VGROUP views, the scatter and the fold
+static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const float *sino_scaled,
+                                     const unsigned *view_max, int *acc, cudaStream_t st) {
+    static thread_local Batch B;
+    B = B0;
+    int ngroups = 0;
+    long long ao = 0;
+    for (int i = 0; i < B.n; ++i) {
+        Inst &I = B.in[i];
+        ngroups = max(ngroups, (I.n_views + VGROUP - 1) / VGROUP);
+        I.npv = (I.nv + PR_ROWS - 1) / PR_ROWS;
+        I.acc = acc + ao;  // z fastest, instances on 64-int boundaries
+        ao += ((long long)I.g.nx * I.g.ny * I.g.nz + 63) / 64 * 64;
+        I.vsz = 1;
+        I.vsy = I.g.nz;
+        I.vsx = I.g.ny * I.g.nz;
+    }
+    for (int gi = 0; gi < ngroups; ++gi) {
+        int pb = 0, fb = 0;
+        for (int i = 0; i < B.n; ++i) {
+            Inst &I = B.in[i];
+            I.kv0 = gi * VGROUP;
+            I.nkv = max(0, min(VGROUP, I.n_views - I.kv0));
+            I.pb0 = pb;
+            pb += I.nkv * I.nu * I.npv;
+            I.fb0 = fb;
+            if (I.nkv > 0) fb += ((I.g.nx + 31) / 32) * I.g.ny * ((I.g.nz + 31) / 32);
+        }
+        if (pb > 0) {
+            k_path<1><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
+            counted(1);
+        }
+        if (fb > 0) {
+            k_bp_fold<<<fb, 256, 0, st>>>(B, view_max);
+            counted(1);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, int *acc,
+                               long long acc_vox, cudaStream_t st) {
+    long long vox = 0;
+    for (int i = 0; i < B.n; ++i) vox += (long long)B.in[i].g.nx * B.in[i].g.ny * B.in[i].g.nz;
+    // the ray scatter (0) needs the workspace's integer sums; without them, the brick scatter (2)
+    const int variant = (g_bp_variant == 0 && acc_vox < vox) ? 2 : g_bp_variant;
+    if (variant == 0 || variant == 2) {
         unsigned *view_max = reinterpret_cast<unsigned *>(sino_scaled + (B.tot_rays + 63) / 64 * 64);
         cudaError_t e = cudaMemsetAsync(view_max, 0, sizeof(unsigned) * B.tot_views, st);
         if (e != cudaSuccess) return e;
@@ -1047,6 +1166,8 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
         for (int i = 0; i < B.n; ++i) max_per = max(max_per, B.in[i].nu * B.in[i].nv);
         k_scale_dn<<<dim3((max_per + 255) / 256, B.tot_views), 256, 0, st>>>(B, const_cast<RayXY *>(tab),
                                                                            sino_scaled, view_max);
+        counted(1);
+        if (variant == 0) return launch_bp_scatter(B, tab, sino_scaled, view_max, acc, st);
         const int smem = 2 * BBV * (int)sizeof(float);
         static bool attr = false;
         if (!attr) {
@@ -1055,7 +1176,7 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
         }
         k_bp_brick<<<B.tot_bricks, BB_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), sino_scaled,
                                                            view_max);
-        counted(2);
+        counted(1);
         return cudaGetLastError();
     }
     int max_u = 1, max_v = 1;

@@ -257,7 +257,7 @@ def dgr_status(ws: Workspace, stream=None) -> int:
 
 
 def dgr_set_backprojector(variant: int):
-    """0: brick scatter (default); 1: column gather."""
+    """0: ray scatter (default); 1: column gather; 2: brick scatter."""
     _rc(lib().dgr_set_backprojector(int(variant)), "dgr_set_backprojector")
 
 

@@ -2,7 +2,7 @@
 every input already in HBM -- a fixed, small command for profilers.
 
     python -m paper_2411_04844_b300.profile_cases OP [--workload 2] [--reps 3] [--views N]
-        [--backprojector 0|1]
+        [--backprojector 0|1|2]
 
 OP: voxelize | voxelize_backward | project | backproject | step.
 Workload numbers are those of synth.workload (2: 50,000 Gaussians, 256^3,
@@ -24,7 +24,7 @@ def main(argv=None):
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--views", type=int, default=0)
-    ap.add_argument("--backprojector", type=int, default=0, help="0: brick scatter, 1: column gather")
+    ap.add_argument("--backprojector", type=int, default=0, help="0: ray scatter, 1: column gather, 2: brick scatter")
     a = ap.parse_args(argv)
     dgr.dgr_set_backprojector(a.backprojector)
     wl = synth.workload(a.workload)

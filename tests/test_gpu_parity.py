@@ -225,9 +225,9 @@ def test_project_and_backproject_parity(case):
     assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs))
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_backproject_variants_agree_and_are_deterministic(variant):
-    """Both backprojectors (brick scatter, column gather) give the oracle's
+    """Every backprojector (ray scatter, column gather, brick scatter) gives the oracle's
     transpose on the workload's cone geometry at reduced size, bit-identically
     run to run."""
     gs = synth.GridSpec((64, 48, 40), 1.0, (-32.0, -24.0, -20.0))
@@ -248,6 +248,39 @@ def test_backproject_variants_agree_and_are_deterministic(variant):
     assert torch.equal(a, b)
     bo = O.backproject(oracle_grid(gs), oracle_geom(geo), y)
     assert rel_l2(H(a), bo) <= 1e-5
+
+
+def test_ray_and_brick_scatter_agree_bitwise():
+    """The two fixed-point scatters add the same integer contributions (same
+    chord lengths, same step per group of views) and fold them in the same
+    order, so they return the same bits; a workspace without room for the
+    integer sums falls back to the brick scatter."""
+    gs = synth.GridSpec((40, 56, 36), 1.0, (-20.0, -28.0, -18.0))
+    geo = synth.cone_geom(19, 80, 50, 1.4, 1.3, 400.0, 650.0)
+    y = np.random.default_rng(17).standard_normal(geo.shape).astype(np.float32)
+    grid = dgr.Grid.of(gs)
+    ang = T(geo.angles)
+    gg = dgr.Geom.of(geo, ang)
+    ws = dgr.Workspace(dgr.make_plan(grid, 0, 0, 0, gg))
+    out = []
+    try:
+        for variant in (0, 2):
+            dgr.dgr_set_backprojector(variant)
+            v = torch.empty(gs.shape, device=DEV)
+            dgr.dgr_backproject(grid, gg, T(y), v, ws)
+            out.append(v)
+        dgr.dgr_set_backprojector(0)
+        plan = dgr.make_plan(grid, 0, 0, 0, gg)
+        plan.max_vox = 0  # no room for the integer sums
+        ws2 = dgr.Workspace(plan)
+        v = torch.empty(gs.shape, device=DEV)
+        dgr.dgr_backproject(grid, gg, T(y), v, ws2)
+        out.append(v)
+        torch.cuda.synchronize()
+    finally:
+        dgr.dgr_set_backprojector(0)
+    assert torch.equal(out[0], out[1])
+    assert torch.equal(out[0], out[2])
 
 
 # ---------------------------------------------------------------------------
