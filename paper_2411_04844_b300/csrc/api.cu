@@ -250,6 +250,7 @@ void set_geom(Inst &I, const dgr_geom &geo) {
     bp_blocks(I.g, I.nbx, I.nbz);
     bp_bricks(I.g, I.nbbx, I.nbby, I.nbbz);
     bp_colours(I.g, geo, I.col_u, I.col_v);
+    I.multiz = multi_z(geo);
 }
 
 // offsets of each instance in the global index spaces

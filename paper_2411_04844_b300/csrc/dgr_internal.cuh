@@ -117,6 +117,7 @@ struct Inst {
     int blk0, nbx, nbz;               // column backprojector: first CTA, CTAs in x, z passes
     int bb0, nbbx, nbby, nbbz;        // brick backprojector: first brick, bricks per axis
     int col_u, col_v;                 // ray colour classes (footprint < col pixels)
+    int multiz;                       // a ray may cross two z planes inside one (x, y) cell
     int pb0, npv;                     // projector / ray scatter: first CTA, row groups
     int kv0, nkv;                     // views of this launch (ray scatter: one view group)
     int fb0;                          // ray scatter fold: first tile
@@ -235,6 +236,7 @@ size_t ray_table_bytes_single(const dgr_geom &geo);
 int bp_blocks(const dgr_grid &g, int &nbx, int &nbz);
 // brick backprojector: bricks per axis and the ray colour classes of a geometry
 int bp_bricks(const dgr_grid &g, int &nbx, int &nby, int &nbz);
+int multi_z(const dgr_geom &geo);
 void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv);
 int backprojector_variant();
 void set_backprojector_variant(int v);

@@ -218,6 +218,56 @@ __device__ __forceinline__ float group_step(const Inst &I, const unsigned *view_
     return ldexpf(1.f, min(30 - ex, 126));
 }
 
+// Fast walk for geometries where no ray crosses two z planes inside one
+// (x, y) cell (sqrt(2) max|e_z| / min|e_xy| < 1 with margin; checked on the
+// host): the crossing is a predicated update and the second segment's length
+// is min(tz, t1) - min(tz_before, t1), zero when nothing was crossed.
+template <int MODE, bool MASKZ>
+__device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *__restrict__ acci, float wq,
+                                           const Seg *seg, int c0, int c1, int nz, float &t, float &acc,
+                                           int &iz, float &fz, float &tz, int sgz, float xi0z, float iez) {
+    const unsigned zmax = (unsigned)(nz - 1);
+    int zc = (int)min((unsigned)iz, zmax);
+    const float fsg = (float)sgz;
+    for (int r = c0; r < c1; r += WALK) {
+        float l0[WALK], l1[WALK];
+        int a0[WALK], a1[WALK];
+#pragma unroll
+        for (int j = 0; j < WALK; ++j) {
+            const Seg S = seg[r + j - c0];  // past c1: padding, empty segments
+            const float t1 = S.t1;
+            const float m = fminf(tz, t1);
+            l0[j] = (!MASKZ || (unsigned)iz <= zmax) ? m - t : 0.f;
+            a0[j] = S.cb + zc;
+            if (tz < t1) {
+                iz += sgz;
+                fz += fsg;
+                tz = (fz - xi0z) * iez;
+                zc = (int)min((unsigned)iz, zmax);
+            }
+            l1[j] = (!MASKZ || (unsigned)iz <= zmax) ? fminf(tz, t1) - m : 0.f;
+            a1[j] = S.cb + zc;
+            t = t1;
+        }
+        if (MODE == 0) {
+            float v0[WALK], v1[WALK];
+#pragma unroll
+            for (int j = 0; j < WALK; ++j) {
+                v0[j] = __ldg(vol + a0[j]);
+                v1[j] = __ldg(vol + a1[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
+        } else {
+#pragma unroll
+            for (int j = 0; j < WALK; ++j) {
+                if (l0[j] != 0.f) atomicAdd(acci + a0[j], __float2int_rn(l0[j] * wq));
+                if (l1[j] != 0.f) atomicAdd(acci + a1[j], __float2int_rn(l1[j] * wq));
+            }
+        }
+    }
+}
+
 // MODE 0 (project): acc += length x volume value.  MODE 1 (backproject
 // scatter): the integer sums at the same voxels += round(length x wq).
 template <int MODE, bool MASKZ>
@@ -409,12 +459,21 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
             seg[c1 - c0 + threadIdx.x] = last;
         }
         __syncthreads();
-        if (masked)
-            walk_segs<MODE, true>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z,
-                                  Z.inv_ez);
-        else
-            walk_segs<MODE, false>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, Z.xi0z,
-                                   Z.inv_ez);
+        if (I.multiz) {
+            if (masked)
+                walk_segs<MODE, true>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
+                                      Z.xi0z, Z.inv_ez);
+            else
+                walk_segs<MODE, false>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
+                                       Z.xi0z, Z.inv_ez);
+        } else {
+            if (masked)
+                walk_segs1<MODE, true>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
+                                       Z.xi0z, Z.inv_ez);
+            else
+                walk_segs1<MODE, false>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
+                                        Z.xi0z, Z.inv_ez);
+        }
     }
     if (MODE == 0 && iv < I.nv) I.sino[ray] = acc * ray_norm(R, row, I.beam);
 }
@@ -1058,6 +1117,15 @@ void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv) {
     cv = (int)floor(1.1 * wv + 0.05) + 1;
 }
 
+// Whether a ray may cross two z planes inside one (x, y) cell: the z change
+// over a cell is at most sqrt(2) |e_z| / |e_xy|, and |e_z| / |e_xy| <=
+// v_max / dsd for the cone (|D_xy| >= dsd), 0 for parallel beams.
+int multi_z(const dgr_geom &geo) {
+    if (geo.beam != DGR_CONE) return 0;
+    const double vmax = 0.5 * (geo.nv - 1) * (double)geo.pv;
+    return 1.4142135623730951 * vmax / (double)geo.dsd > 0.9 ? 1 : 0;
+}
+
 static int g_bp_variant = 0;  // 0: ray scatter, 1: column gather, 2: brick scatter
 int backprojector_variant() { return g_bp_variant; }
 void set_backprojector_variant(int v) { g_bp_variant = v; }
@@ -1209,6 +1277,7 @@ cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY 
     I.vsx = 1;
     I.vsy = g.nx;
     I.vsz = g.nx * g.ny;
+    I.multiz = 1;
     I.sino = sino;
     B.tot_tab = geo.n_views * geo.nu;
     B.tot_views = geo.n_views;

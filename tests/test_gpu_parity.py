@@ -196,8 +196,11 @@ def _projector_cases():
     odd = synth.GridSpec((33, 29, 21), 0.8, (-12.0, -13.0, -9.0))
     odd_geom = synth.parallel_geom(17, 45, 27, 0.9, 0.7)
     odd_cone = synth.cone_geom(13, 41, 31, 1.1, 1.3, 60.0, 95.0, arc=1.3)
+    # a wide cone: rays cross several z planes inside one (x, y) cell
+    steep_g = synth.GridSpec((24, 24, 24), 1.0, (-12.0, -12.0, -12.0))
+    steep = synth.cone_geom(8, 40, 64, 1.5, 1.5, 30.0, 45.0)
     return [("parallel64", par.grid, par.geom), ("cone", cone_g, cone),
-            ("parallel_odd", odd, odd_geom), ("cone_odd", odd, odd_cone)]
+            ("parallel_odd", odd, odd_geom), ("cone_odd", odd, odd_cone), ("cone_steep", steep_g, steep)]
 
 
 @pytest.mark.parametrize("case", _projector_cases(), ids=lambda c: c[0])
