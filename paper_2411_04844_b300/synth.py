@@ -89,6 +89,18 @@ def cone_geom(n_views, nu, nv, pu, pv, dso, dsd, arc=2 * math.pi):
     return GeomSpec(CONE, ang, nu, nv, pu, pv, dso, dsd)
 
 
+def fan_geom(n_views, nu, pu, dso, dsd, arc=2 * math.pi):
+    """2D fan beam: a cone beam with one detector row through z = 0, for a
+    volume one voxel thick centred on that plane.  A limited-angle scan is
+    the same with arc < pi (the paper's 90 degree case: arc = pi / 2)."""
+    return cone_geom(n_views, nu, 1, pu, 1.0, dso, dsd, arc)
+
+
+def slice_grid(n, h=1.0):
+    """n x n x 1 voxels centred on the origin (z = 0 in the middle of the slice)."""
+    return GridSpec((n, n, 1), h, (-0.5 * n * h, -0.5 * n * h, -0.5 * h))
+
+
 # ---------------------------------------------------------------------------
 # Gaussian fields
 # ---------------------------------------------------------------------------

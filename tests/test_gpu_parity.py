@@ -199,8 +199,15 @@ def _projector_cases():
     # a wide cone: rays cross several z planes inside one (x, y) cell
     steep_g = synth.GridSpec((24, 24, 24), 1.0, (-12.0, -12.0, -12.0))
     steep = synth.cone_geom(8, 40, 64, 1.5, 1.5, 30.0, 45.0)
+    # 2D fan beam on a slice; 90-degree limited-angle scans (fan and 3D parallel)
+    fan_g = synth.slice_grid(64, 1.0)
+    fan = synth.fan_geom(36, 96, 1.4, 160.0, 260.0)
+    fan90 = synth.fan_geom(24, 96, 1.4, 160.0, 260.0, arc=np.pi / 2)
+    par90 = synth.parallel_geom(20, 56, 44, 1.0, 1.0, arc=np.pi / 2)
     return [("parallel64", par.grid, par.geom), ("cone", cone_g, cone),
-            ("parallel_odd", odd, odd_geom), ("cone_odd", odd, odd_cone), ("cone_steep", steep_g, steep)]
+            ("parallel_odd", odd, odd_geom), ("cone_odd", odd, odd_cone), ("cone_steep", steep_g, steep),
+            ("fan2d", fan_g, fan), ("fan2d_limited90", fan_g, fan90),
+            ("parallel_limited90", cone_g, par90)]
 
 
 @pytest.mark.parametrize("case", _projector_cases(), ids=lambda c: c[0])
@@ -371,8 +378,23 @@ def _step_problem():
     return gs, geo, f, meas
 
 
-def test_step_parity_with_oracle():
-    gs, geo, f, meas = _step_problem()
+def _fan_step_problem(arc):
+    """2D fan beam over a one-voxel-thick slice (full scan or 90 degrees)."""
+    gs = synth.slice_grid(48, 1.0)
+    geo = synth.fan_geom(40, 72, 1.5, 150.0, 240.0, arc)
+    f = guard_field(synth.gaussian_field(synth.rng_for(1, 11), 250, gs, ("loguniform", 0.5, 3.0)), gs)
+    f.rho = np.clip(f.rho, 0.05, 1.0).astype(np.float32)
+    phantom = synth.ellipsoid_phantom(synth.rng_for(1, 12), gs, 6)
+    meas = O.project(oracle_grid(gs), oracle_geom(geo), phantom).astype(np.float32)
+    return gs, geo, f, meas
+
+
+@pytest.mark.parametrize("which", ["parallel3d", "fan", "fan_limited90"])
+def test_step_parity_with_oracle(which):
+    if which == "parallel3d":
+        gs, geo, f, meas = _step_problem()
+    else:
+        gs, geo, f, meas = _fan_step_problem(2 * np.pi if which == "fan" else np.pi / 2)
     grid = dgr.Grid.of(gs)
     ang = T(geo.angles)
     gg = dgr.Geom.of(geo, ang)

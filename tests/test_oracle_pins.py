@@ -315,6 +315,39 @@ def test_adjoint_identity(which):
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0) * 10
 
 
+@pytest.mark.parametrize("arc", [2 * math.pi, math.pi / 2])
+def test_fan_beam_slice_chord_lengths(arc):
+    """2D fan beam (one detector row through z = 0) over a one-voxel-thick
+    slice of ones: every pixel is the 2D chord of its ray through the square,
+    computed here from the source/detector positions written out by hand
+    (full scan and the 90-degree limited-angle scan)."""
+    F = lambda x: float(np.float32(x))  # the geometry is handed over in FP32
+    n, h = 10, F(1.2)
+    gs = synth.slice_grid(n, h)
+    geo = synth.fan_geom(7, 23, F(1.1), 25.0, 41.0, arc)
+    g = grid_of((n, n, 1), h=h, org=gs.org)
+    sino = O.project(g, O.Geom(geo.beam, geo.angles, geo.nu, geo.nv, geo.pu, geo.pv, geo.dso, geo.dsd),
+                     np.ones(g.shape))
+    lo = np.array(g.org[:2]); hi = lo + n * g.h  # the FP32 grid as handed over
+    for k, th in enumerate(geo.angles.astype(np.float64)):
+        c, sn = math.cos(th), math.sin(th)
+        src = np.array([-geo.dso * c, -geo.dso * sn])
+        for iu in range(geo.nu):
+            u = (iu - 0.5 * (geo.nu - 1)) * geo.pu
+            det = src + geo.dsd * np.array([c, sn]) + u * np.array([-sn, c])
+            d = det - src
+            t0, t1 = -np.inf, np.inf
+            for a in range(2):
+                if d[a] == 0.0:
+                    if not (lo[a] <= src[a] < hi[a]):
+                        t0, t1 = 1.0, 0.0
+                    continue
+                ta, tb = (lo[a] - src[a]) / d[a], (hi[a] - src[a]) / d[a]
+                t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+            chord = max(0.0, t1 - t0) * float(np.linalg.norm(d))
+            assert abs(sino[k, 0, iu] - chord) < 1e-10, (k, iu, sino[k, 0, iu], chord)
+
+
 def test_axis_aligned_parallel_rays_are_column_sums():
     """theta = 0: rays run along +x at (y, z) = (u, v); each pixel is h times the
     sum of the voxel row it lies in."""
