@@ -42,8 +42,8 @@ FFMA_PER_CLK_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -343,12 +343,16 @@ def oracle_sample(frac_gauss, n_views_sample, seed_rank=0):
     return 1.0 / t_iter, O.num_threads(), desc, t4 - t0
 
 
+def sample_size(target_s, frac0=0.01):
+    """Calibrate on a small sample, then size (fraction of Gaussians, views)
+    so that one sample takes about target_s seconds."""
+    _, _, _, spent = oracle_sample(frac0, 1)
+    k = max(1.0, target_s / max(spent, 1e-3))
+    return min(1.0, frac0 * k), int(max(1, min(50, round(k))))
+
+
 def cpu_baseline(target_s):
-    # calibrate on a small sample, then size the sample to ~target_s
-    v, th, desc, spent = oracle_sample(0.01, 1)
-    scale = max(1.0, min(8.0, target_s / max(spent, 1e-3)))
-    fg = min(1.0, 0.01 * scale)
-    nv = int(max(1, min(50, round(scale))))
+    fg, nv = sample_size(target_s)
     v, th, desc, spent = oracle_sample(fg, nv)
     return {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": desc,
             "seconds": round(spent, 2)}
@@ -360,10 +364,12 @@ def run_reference(args, rank, ws_n):
     if rank != 0:
         return
     W, K = args.warmup, args.steps
+    # each step a bounded sample: about 2 minutes for the whole run, at most 5 s a step
+    fg, nv = sample_size(min(5.0, max(0.1, 120.0 / (W + K))), frac0=0.002)
     per = []
     desc = th = None
     for k in range(W + K):
-        v, th, desc, spent = oracle_sample(0.004, 1, seed_rank=k % 3)
+        v, th, desc, spent = oracle_sample(fg, nv, seed_rank=k % 3)
         if k >= W:
             per.append(1.0 / v)
     value = K / sum(per)

@@ -14,9 +14,13 @@ Paper passages followed (arxiv 2411.04844):
     image (Siddon's method)
   * L1 data term: Sec. 4.3 (Eq. 13, first term); Adam with lr 3e-4 -> 3e-5:
     Sec. 5.1 "Implementation Details"
+  * full objective w1 L1 + w2 L_SSIM + w3 L_TV (Sec. 4.3, weights 0.6 / 0.2 /
+    1; App. D.1): SSIM of Wang et al. 2004 on every projection image with an
+    11 x 11 Gaussian window (sigma 1.5), anisotropic TV of the volume
 
 Parity status per function (pins live in tests/test_oracle_pins.py):
-  footprint, voxelize, voxelize_backward, project, backproject, l1_loss: pinned
+  footprint, voxelize, voxelize_backward, project, backproject, l1_loss,
+  ssim_loss, tv_loss: pinned
   adam_update / step lr schedule: "parity unpinned" beyond the textbook Adam
   recurrence (the paper fixes neither betas, epsilon nor the decay law).
 """
@@ -244,6 +248,85 @@ def l1_loss(pred, meas):
     return float(np.abs(diff).sum() / M), np.sign(diff) / M
 
 
+def gaussian_window(size: int = 11, sigma: float = 1.5):
+    """1D Gaussian weights exp(-(i - c)^2 / (2 sigma^2)), c the middle tap,
+    normalised to sum 1; the SSIM window is their outer product (Wang et al.
+    2004, cited by the paper for SSIM)."""
+    i = np.arange(size, dtype=np.float64) - (size - 1) / 2.0
+    g = np.exp(-i * i / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _blur(img, g):
+    """Correlation of each [nv][nu] image with the separable window, zero
+    outside the image ("same" size)."""
+    from scipy.ndimage import correlate1d
+    out = correlate1d(np.asarray(img, np.float64), g, axis=-1, mode="constant", cval=0.0)
+    return correlate1d(out, g, axis=-2, mode="constant", cval=0.0)
+
+
+def ssim_terms(x, y, data_range: float = 1.0):
+    """Local SSIM statistics of x against y (arrays [views][nv][nu], each view
+    an image): windowed means, variances and covariance with an 11 x 11
+    Gaussian window (sigma 1.5, zero outside the image), C1 = (0.01 L)^2,
+    C2 = (0.03 L)^2.  Returns the SSIM map and the dict of statistics."""
+    g = gaussian_window()
+    x = np.asarray(x, np.float64); y = np.asarray(y, np.float64)
+    mx, my = _blur(x, g), _blur(y, g)
+    sxx = _blur(x * x, g) - mx * mx
+    syy = _blur(y * y, g) - my * my
+    sxy = _blur(x * y, g) - mx * my
+    c1 = (0.01 * data_range) ** 2
+    c2 = (0.03 * data_range) ** 2
+    n1, n2 = 2 * mx * my + c1, 2 * sxy + c2
+    d1, d2 = mx * mx + my * my + c1, sxx + syy + c2
+    smap = n1 * n2 / (d1 * d2)
+    return smap, dict(mx=mx, my=my, sxx=sxx, syy=syy, sxy=sxy, n1=n1, n2=n2, d1=d1, d2=d2, g=g)
+
+
+def ssim_loss(pred, meas, data_range: float = 1.0):
+    """L_SSIM = 1 - mean SSIM map over every pixel of every view (paper
+    Sec. 4.3 / App. D.1: SSIM computed in the projection domain), and its
+    gradient with respect to pred.  With S = N1 N2 / (D1 D2) per pixel p and
+    the local statistics linear or quadratic in pred:
+        dS/dmu_x = 2 mu_y N2 / (D1 D2) - 2 mu_x S / D1,
+        dS/dsig_xx = -S / D2,   dS/dsig_xy = 2 N1 / (D1 D2),
+    and with A = dS/dmu_x - 2 mu_x dS/dsig_xx - mu_y dS/dsig_xy,
+    B = dS/dsig_xx, C = dS/dsig_xy, the chain through the window gives
+        d mean(S) / d x(q) = [ (w*A)(q) + 2 x(q) (w*B)(q) + y(q) (w*C)(q) ] / N
+    (w symmetric, zero outside the image)."""
+    x = np.asarray(pred, np.float64); y = np.asarray(meas, np.float64)
+    smap, t = ssim_terms(x, y, data_range)
+    N = smap.size
+    dd = t["d1"] * t["d2"]
+    dmx = 2 * t["my"] * t["n2"] / dd - 2 * t["mx"] * smap / t["d1"]
+    dsxx = -smap / t["d2"]
+    dsxy = 2 * t["n1"] / dd
+    A = dmx - 2 * t["mx"] * dsxx - t["my"] * dsxy
+    g = t["g"]
+    grad = (_blur(A, g) + 2 * x * _blur(dsxx, g) + y * _blur(dsxy, g)) / N
+    return float(1.0 - smap.mean()), -grad
+
+
+def tv_loss(vol):
+    """Anisotropic total variation of the volume [nz][ny][nx]: the sum over
+    axes of |forward differences| where both voxels exist, divided by the
+    number of voxels (the paper names TV without a formula; this is the
+    reading), and its gradient (sign(0) = 0)."""
+    v = np.asarray(vol, np.float64)
+    total = 0.0
+    grad = np.zeros_like(v)
+    for ax in range(3):
+        d = np.diff(v, axis=ax)
+        total += np.abs(d).sum()
+        sg = np.sign(d)
+        lo = [slice(None)] * 3; hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1); hi[ax] = slice(1, None)
+        grad[tuple(lo)] -= sg
+        grad[tuple(hi)] += sg
+    return total / v.size, grad / v.size
+
+
 def grid_centre_half(grid: Grid):
     c = np.array([grid.org[a] + 0.5 * grid.dims[a] * grid.h for a in range(3)])
     half = np.array([0.5 * grid.dims[a] * grid.h for a in range(3)])
@@ -287,16 +370,29 @@ def adam_update(th, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return out
 
 
-def step(grid: Grid, geom: Geom, mu, s, q, rho, th, m, v, t, meas, k_trunc, lr0, lr1, n_iters):
-    """One optimisation iteration in FP64: voxelize -> project -> L1 ->
+def step(grid: Grid, geom: Geom, mu, s, q, rho, th, m, v, t, meas, k_trunc, lr0, lr1, n_iters,
+         weights=(1.0, 0.0, 0.0), data_range: float = 1.0):
+    """One optimisation iteration in FP64: voxelize -> project -> loss ->
     backproject -> voxelize adjoint -> chain to optimiser variables -> Adam.
+    The loss is w1 L1(P_hat, P) + w2 L_SSIM(P_hat, P) + w3 L_TV(V) (paper
+    Sec. 4.3, weights 0.6 / 0.2 / 1 there; (1, 0, 0) is the L1 term alone).
     mu, s, q, rho are the FP32 parameters used for the box integers."""
+    w1, w2, w3 = weights
     _, box = footprint(grid, mu, s, q, k_trunc)
     mu64, s64, q64, rho64 = from_opt(grid, th)
     vol = voxelize_core(grid, mu64, s64, q64, rho64, box)
     pred = project(grid, geom, vol)
-    loss, r = l1_loss(pred, meas)
+    l1, r = l1_loss(pred, meas)
+    loss, r = w1 * l1, w1 * r
+    if w2:
+        ls, gs = ssim_loss(pred, meas, data_range)
+        loss += w2 * ls
+        r = r + w2 * gs
     gv = backproject(grid, geom, r)
+    if w3:
+        lt, gt = tv_loss(vol)
+        loss += w3 * lt
+        gv = gv + w3 * gt
     g_mu, g_s, g_q, g_rho = voxelize_backward_core(grid, mu64, s64, q64, rho64, box, gv)
     _, half = grid_centre_half(grid)
     sig = 1.0 / (1.0 + np.exp(-th["rho"]))

@@ -499,3 +499,87 @@ def test_lr_schedule_endpoints_and_transforms():
     mu2, s2, q2, rho2 = O.from_opt(g, th)
     for a, b in ((mu, mu2), (s, s2), (q, q2), (rho, rho2)):
         assert np.max(np.abs(a - b)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# full objective: SSIM (projection domain) and TV (volume), Sec. 4.3 / App. D.1
+# ---------------------------------------------------------------------------
+def test_ssim_window_is_the_normalised_gaussian():
+    g = O.gaussian_window()
+    ref = np.array([math.exp(-(i - 5) ** 2 / (2 * 1.5 ** 2)) for i in range(11)])
+    assert np.allclose(g, ref / ref.sum(), rtol=0, atol=1e-15)
+
+
+def test_ssim_of_an_image_with_itself_is_one():
+    x = np.random.default_rng(1).uniform(0, 3, (2, 17, 23))
+    loss, grad = O.ssim_loss(x, x)
+    assert abs(loss) < 1e-14
+    assert np.abs(grad).max() < 1e-14
+
+
+def test_ssim_pixel_by_brute_force_window():
+    """One interior pixel's SSIM from an explicit 11 x 11 weighted sum
+    (exp(-(i^2 + j^2) / (2 sigma^2)) normalised), independent of the
+    separable correlation used by the oracle."""
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0, 2, (1, 21, 25)); y = rng.uniform(0, 2, (1, 21, 25))
+    L = 2.0
+    smap, _ = O.ssim_terms(x, y, L)
+    for (r, c) in [(10, 12), (7, 6), (13, 18)]:
+        w = np.array([[math.exp(-(i * i + j * j) / 4.5) for j in range(-5, 6)] for i in range(-5, 6)])
+        w /= w.sum()
+        px = x[0, r - 5:r + 6, c - 5:c + 6]; py = y[0, r - 5:r + 6, c - 5:c + 6]
+        mx, my = (w * px).sum(), (w * py).sum()
+        vx, vy = (w * px * px).sum() - mx * mx, (w * py * py).sum() - my * my
+        cxy = (w * px * py).sum() - mx * my
+        c1, c2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+        s = (2 * mx * my + c1) * (2 * cxy + c2) / ((mx * mx + my * my + c1) * (vx + vy + c2))
+        assert abs(smap[0, r, c] - s) < 1e-12
+
+
+def test_ssim_constant_images_closed_form():
+    """Away from the border (full window), constant images a and b give
+    (2ab + C1) / (a^2 + b^2 + C1)."""
+    a, b = 0.7, 1.3
+    x = np.full((1, 24, 24), a); y = np.full((1, 24, 24), b)
+    smap, _ = O.ssim_terms(x, y, 1.0)
+    c1 = 1e-4
+    assert abs(smap[0, 12, 12] - (2 * a * b + c1) / (a * a + b * b + c1)) < 1e-12
+
+
+def test_ssim_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, (2, 9, 13)); y = rng.uniform(0, 1, (2, 9, 13))
+    _, grad = O.ssim_loss(x, y)
+    eps = 1e-6
+    for idx in [(0, 0, 0), (0, 4, 6), (1, 8, 12), (1, 3, 1), (0, 7, 10)]:
+        xp = x.copy(); xp[idx] += eps
+        xm = x.copy(); xm[idx] -= eps
+        fd = (O.ssim_loss(xp, y)[0] - O.ssim_loss(xm, y)[0]) / (2 * eps)
+        assert abs(fd - grad[idx]) <= 1e-7 * max(1.0, abs(fd)) + 1e-9, (idx, fd, grad[idx])
+
+
+def test_tv_ramp_closed_form_and_bump():
+    nz, ny, nx = 4, 5, 6
+    z, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    a, b = 0.3, -0.7
+    v = a * xx + b * yy
+    t, _ = O.tv_loss(v)
+    N = nx * ny * nz
+    assert abs(t - ((nx - 1) * ny * nz * abs(a) + nx * (ny - 1) * nz * abs(b)) / N) < 1e-13
+    bump = np.zeros((nz, ny, nx)); bump[2, 2, 3] = 0.5
+    t, g = O.tv_loss(bump)
+    assert abs(t - 6 * 0.5 / N) < 1e-15
+    assert abs(g[2, 2, 3] - 6 / N) < 1e-15
+    assert abs(g[2, 2, 2] + 1 / N) < 1e-15 and abs(g[1, 2, 3] + 1 / N) < 1e-15
+
+
+def test_tv_gradient_matches_central_differences():
+    v = np.random.default_rng(4).standard_normal((3, 4, 5))
+    _, g = O.tv_loss(v)
+    eps = 1e-7
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 3, 4), (1, 0, 2)]:
+        vp = v.copy(); vp[idx] += eps
+        vm = v.copy(); vm[idx] -= eps
+        fd = (O.tv_loss(vp)[0] - O.tv_loss(vm)[0]) / (2 * eps)
+        assert abs(fd - g[idx]) < 1e-8
