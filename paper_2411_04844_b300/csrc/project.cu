@@ -261,8 +261,11 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
         } else {
 #pragma unroll
             for (int j = 0; j < WALK; ++j) {
-                if (l0[j] != 0.f) atomicAdd(acci + a0[j], __float2int_rn(l0[j] * wq));
-                if (l1[j] != 0.f) atomicAdd(acci + a1[j], __float2int_rn(l1[j] * wq));
+                // without a crossing the second segment is empty and names the same voxel
+                const int q0 = __float2int_rn(l0[j] * wq), q1 = __float2int_rn(l1[j] * wq);
+                const bool same = a1[j] == a0[j];
+                atomicAdd(acci + a0[j], same ? q0 + q1 : q0);
+                if (!same) atomicAdd(acci + a1[j], q1);
             }
         }
     }
