@@ -179,6 +179,19 @@ int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sin
 int dgr_l1_residual(const float *pred, const float *meas, long long m, float *resid,
                     float *loss, dgr_ws *ws, cudaStream_t stream);
 
+/* SSIM term of the objective (paper Sec. 4.3, App. D.1) on its own:
+ * loss_out (device scalar) = 1 - SSIM(pred, meas), the mean of the SSIM map
+ * over every pixel of every view (statistics as in dgr_problem), and
+ * grad = d loss / d pred.  pred, meas, grad: device [n_views][nv][nu] of geom.
+ * The workspace plan must hold max_rays >= the projection size. */
+int dgr_ssim_loss(const dgr_geom *geom, const float *pred, const float *meas, float data_range,
+                  float *grad, float *loss_out, dgr_ws *ws, cudaStream_t stream);
+/* TV term on its own: loss_out = sum over axes of |forward differences| of
+ * vol divided by the voxel count; grad = d loss / d vol.  vol, grad: device
+ * [nz][ny][nx].  The workspace plan must hold max_vox >= the voxel count. */
+int dgr_tv_loss(const dgr_grid *grid, const float *vol, float *grad, float *loss_out, dgr_ws *ws,
+                cudaStream_t stream);
+
 /* One optimisation iteration (paper Sec. 4.3 "Global Optimization"; Adam with
  * lr decaying lr0 -> lr1, Sec. 5.1 "Implementation Details"). */
 typedef struct {
@@ -188,6 +201,13 @@ typedef struct {
     float lr0, lr1;    /* lr(t) = lr0 (lr1/lr0)^((t-1)/(n_iters-1)), t = 1..n_iters */
     int n_iters;
     float beta1, beta2, eps;
+    /* objective (paper Sec. 4.3, App. D.1; 0.6 / 0.2 / 1 there):
+     *   loss = w_l1 mean|P_hat - P| + w_ssim (1 - SSIM(P_hat, P)) + w_tv TV(V),
+     * SSIM over every projection image (11 x 11 Gaussian window, sigma 1.5,
+     * zero outside the image, C1 = (0.01 L)^2, C2 = (0.03 L)^2 with
+     * L = ssim_range, 1 if 0), TV = sum over axes of |forward differences| /
+     * voxels.  All three weights 0: the L1 term alone with weight 1. */
+    float w_l1, w_ssim, w_tv, ssim_range;
 } dgr_problem;
 
 /* Optimiser state.  theta/m/v are [11 n] laid out [mu 3n | s 3n | q 4n | rho n]
@@ -204,7 +224,7 @@ typedef struct {
 /* theta from (mu, s, q, rho); m = v = 0; step = 0. */
 int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t stream);
 
-/* voxelize -> project -> L1 residual -> backproject -> voxelize adjoint ->
+/* voxelize -> project -> loss and residual -> backproject (+ TV gradient) -> voxelize adjoint ->
  * chain rule to theta -> Adam.  measured: device [n_views][nv][nu];
  * loss_out: device scalar (the L1 loss before the update).  The workspace
  * plan must carry max_vox and max_rays of this problem. */

@@ -62,7 +62,8 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA; }
 
 struct Layout {
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, list_tmp, acc, total;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, list_tmp, gvol, ssim_maps, ssim_g,
+        ssim_part, tv_part, acc, total;
     size_t scan_elems;
 };
 
@@ -105,8 +106,17 @@ Layout layout_of(const dgr_ws_plan &p) {
     // instance volumes start on 64-float boundaries (vectorised stores)
     L.vol = take(4 * ((size_t)p.max_vox + (size_t)64 * (p.max_inst > 1 ? p.max_inst : 1)));
     L.sino = take(4 * (size_t)p.max_rays);
+    // step: the volume gradient (x fastest; the volume itself stays z fastest
+    // for the TV term), SSIM maps A, B, C and gradient, SSIM and TV partial sums
+    const size_t vpad = (size_t)64 * (p.max_inst > 1 ? p.max_inst : 1);
+    const bool step = p.max_rays > 0 && p.max_vox > 0;
+    L.gvol = take(step ? 4 * ((size_t)p.max_vox + vpad) : 0);
+    L.ssim_maps = take(4 * 3 * (size_t)p.max_rays);
+    L.ssim_g = take(4 * (size_t)p.max_rays);
+    L.ssim_part = take(4 * ssim_tiles_cap(p.max_views, p.max_nu, p.max_nv, ninst));
+    L.tv_part = take(4 * tv_tiles_cap(p.max_vox, ninst));
     // integer sums of the ray-driven backprojector (z fastest), kept zero between calls
-    L.acc = take(p.max_vox > 0 ? 4 * ((size_t)p.max_vox + (size_t)64 * (p.max_inst > 1 ? p.max_inst : 1)) : 0);
+    L.acc = take(p.max_vox > 0 ? 4 * ((size_t)p.max_vox + vpad) : 0);
     L.total = o;
     return L;
 }
@@ -141,6 +151,8 @@ int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan) {
     w->sino_scaled = L.sino_scaled;
     w->list_tmp = L.list_tmp;
     w->acc = L.acc;
+    w->gvol = L.gvol; w->ssim_maps = L.ssim_maps; w->ssim_g = L.ssim_g; w->ssim_part = L.ssim_part;
+    w->tv_part = L.tv_part;
     w->scan_tmp_elems = L.scan_elems;
     if (cudaMemset(w->base + L.status, 0, 256) != cudaSuccess ||
         cudaMemset(w->base + L.acc, 0, L.total - L.acc) != cudaSuccess) {
@@ -379,7 +391,7 @@ int dgr_voxelize_backward(const dgr_grid *grid, int n, const float *mu, const fl
     Inst &I = B.in[0];
     set_grid(I, *grid, k_trunc);
     I.n = n; I.mu = mu; I.s = s; I.q = q; I.rho = rho;
-    I.vol = const_cast<float *>(grad_vol);
+    I.gvol = const_cast<float *>(grad_vol);
     I.g_mu = g_mu; I.g_s = g_s; I.g_q = g_q; I.g_rho = g_rho;
     finish(B, false);
     int rc = check_batch_ws(ws, B, false, false);
@@ -401,6 +413,7 @@ static int proj_batch(const dgr_grid *grid, const dgr_geom *geom, const float *v
     set_grid(I, *grid, 3.0f);
     set_geom(I, *geom);
     I.vol = const_cast<float *>(vol);
+    I.gvol = const_cast<float *>(vol);  // dgr_backproject writes here
     I.sino = const_cast<float *>(sino);
     finish(B, true);
     int rc = check_batch_ws(ws, B, true, false);
@@ -449,8 +462,24 @@ int dgr_l1_residual(const float *pred, const float *meas, long long m, float *re
     return cuda_rc(launch_l1_single(pred, meas, m, resid, loss, ws_ptr<float>(ws, ws->loss_part), stream));
 }
 
+static bool weights_ok(const dgr_problem *P) {
+    auto ok = [](float w) { return isfinite(w) && w >= 0.f; };
+    return ok(P->w_l1) && ok(P->w_ssim) && ok(P->w_tv) && ok(P->ssim_range);
+}
+
+// objective weights and SSIM constants of an instance (all weights 0: L1 alone)
+static void set_objective(Inst &I, const dgr_problem &P) {
+    const bool none = P.w_l1 == 0.f && P.w_ssim == 0.f && P.w_tv == 0.f;
+    I.w_l1 = none ? 1.f : P.w_l1;
+    I.w_ssim = none ? 0.f : P.w_ssim;
+    I.w_tv = none ? 0.f : P.w_tv;
+    const float L = P.ssim_range > 0.f ? P.ssim_range : 1.f;
+    I.ssim_c1 = (0.01f * L) * (0.01f * L);
+    I.ssim_c2 = (0.03f * L) * (0.03f * L);
+}
+
 static int problem_ok(const dgr_problem *P) {
-    return P && grid_ok(&P->grid) && geom_ok(&P->geom) && k_ok(P->k_trunc) &&
+    return P && grid_ok(&P->grid) && geom_ok(&P->geom) && k_ok(P->k_trunc) && weights_ok(P) &&
            geom_fits_grid(&P->grid, &P->geom) && isfinite(P->lr0) && isfinite(P->lr1) &&
            P->lr0 > 0.f && P->lr1 > 0.f && P->n_iters >= 1 && P->beta1 >= 0.f && P->beta1 < 1.f &&
            P->beta2 >= 0.f && P->beta2 < 1.f && P->eps > 0.f &&
@@ -493,19 +522,35 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
         I.loss = loss_out + i;
         I.lr0 = P->lr0; I.lr1 = P->lr1; I.b1 = P->beta1; I.b2 = P->beta2; I.eps = P->eps;
         I.n_iters = P->n_iters;
+        set_objective(I, *P);
     }
     finish(B, true);
+    loss_tiles(B);
     int rc = check_batch_ws(ws, B, true, true);
     if (rc) return rc;
+    {
+        const dgr_ws_plan &p = ws->plan;
+        const int ninst = p.max_inst > 0 ? p.max_inst : 1;
+        if ((size_t)B.tot_st > ssim_tiles_cap(p.max_views, p.max_nu, p.max_nv, ninst) ||
+            (size_t)B.tot_tv > tv_tiles_cap(p.max_vox, ninst))
+            return DGR_ERR_WS_TOO_SMALL;
+    }
+    bool any_ssim = false, any_tv = false;
+    for (int i = 0; i < n_inst; ++i) {
+        any_ssim = any_ssim || B.in[i].w_ssim != 0.f;
+        any_tv = any_tv || B.in[i].w_tv != 0.f;
+    }
     // per-instance buffers in the workspace: volume (then its gradient),
     // sinogram (prediction, then residual), gradients [mu 3n | s 3n | q 4n | rho n]
     float *vol = ws_ptr<float>(ws, ws->vol);
+    float *gvol = ws_ptr<float>(ws, ws->gvol);
     float *sino = ws_ptr<float>(ws, ws->sino);
     float *grads = ws_ptr<float>(ws, ws->grads);
     long long vo = 0;
     for (int i = 0; i < n_inst; ++i) {
         Inst &I = B.in[i];
         I.vol = vol + vo;
+        I.gvol = gvol + vo;
         vo += ((long long)I.g.nx * I.g.ny * I.g.nz + 63) / 64 * 64;
         // the step's own volume is z fastest ([nx][ny][nz]): the projector's
         // lanes (consecutive detector rows) then read neighbouring words; the
@@ -528,9 +573,16 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
     if (e == cudaSuccess) e = launch_ray_tables(B, tab, stream);
     if (e == cudaSuccess) e = launch_project(B, tab, stream);
     if (e == cudaSuccess) e = mark(2);
-    if (e == cudaSuccess) e = launch_l1(B, ws_ptr<float>(ws, ws->loss_part), stream);
+    float *ssim_g = ws_ptr<float>(ws, ws->ssim_g);
+    if (e == cudaSuccess && any_ssim)
+        e = launch_ssim(B, ws_ptr<float>(ws, ws->ssim_maps), ws_ptr<float>(ws, ws->ssim_part), ssim_g, stream);
+    if (e == cudaSuccess) e = launch_l1(B, ws_ptr<float>(ws, ws->loss_part), any_ssim ? ssim_g : nullptr, stream);
     if (e == cudaSuccess) e = mark(3);
     if (e == cudaSuccess) e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, stream);
+    if (e == cudaSuccess && any_tv) e = launch_tv(B, ws_ptr<float>(ws, ws->tv_part), 1, stream);
+    if (e == cudaSuccess)
+        e = launch_loss_final(B, ws_ptr<float>(ws, ws->loss_part), L1_BLOCKS, ws_ptr<float>(ws, ws->ssim_part),
+                              ws_ptr<float>(ws, ws->tv_part), stream);
     if (e == cudaSuccess) e = mark(4);
     if (e == cudaSuccess) e = launch_voxelize_backward(B, prep, ws, stream);
     if (e == cudaSuccess) e = mark(5);
@@ -555,6 +607,55 @@ int dgr_step_batched(int n_inst, const dgr_problem *probs, const dgr_params *par
                      const float *const *measured, float *loss_out, dgr_ws *ws,
                      cudaStream_t stream) {
     return step_batch(n_inst, probs, params, measured, loss_out, ws, stream, nullptr);
+}
+
+int dgr_ssim_loss(const dgr_geom *geom, const float *pred, const float *meas, float data_range,
+                  float *grad, float *loss_out, dgr_ws *ws, cudaStream_t stream) {
+    if (!geom_ok(geom) || !pred || !meas || !grad || !loss_out || !ws || !isfinite(data_range) ||
+        data_range < 0.f)
+        return DGR_ERR_ARG;
+    Batch &B = *new_batch();
+    B.n = 1;
+    Inst &I = B.in[0];
+    I.n_views = geom->n_views; I.nu = geom->nu; I.nv = geom->nv;
+    I.sino = const_cast<float *>(pred);
+    I.meas = meas;
+    I.loss = loss_out;
+    dgr_problem P;
+    memset(&P, 0, sizeof(P));
+    P.w_ssim = 1.f;
+    P.ssim_range = data_range;
+    set_objective(I, P);
+    B.tot_rays = (long long)I.n_views * I.nu * I.nv;
+    loss_tiles(B);
+    const dgr_ws_plan &p = ws->plan;
+    if (B.tot_rays > p.max_rays || (size_t)B.tot_st > ssim_tiles_cap(p.max_views, p.max_nu, p.max_nv, 1))
+        return DGR_ERR_WS_TOO_SMALL;
+    cudaError_t e = launch_ssim(B, ws_ptr<float>(ws, ws->ssim_maps), ws_ptr<float>(ws, ws->ssim_part), grad, stream);
+    if (e == cudaSuccess) e = launch_loss_final(B, nullptr, 0, ws_ptr<float>(ws, ws->ssim_part), nullptr, stream);
+    return cuda_rc(e);
+}
+
+int dgr_tv_loss(const dgr_grid *grid, const float *vol, float *grad, float *loss_out, dgr_ws *ws,
+                cudaStream_t stream) {
+    if (!grid_ok(grid) || !vol || !grad || !loss_out || !ws) return DGR_ERR_ARG;
+    if ((long long)grid->nx * grid->ny * grid->nz >= (1ll << 31)) return DGR_ERR_ARG;
+    Batch &B = *new_batch();
+    B.n = 1;
+    Inst &I = B.in[0];
+    set_grid(I, *grid, 3.0f);
+    I.vol = const_cast<float *>(vol);
+    I.gvol = grad;
+    I.loss = loss_out;
+    dgr_problem P;
+    memset(&P, 0, sizeof(P));
+    P.w_tv = 1.f;
+    set_objective(I, P);
+    loss_tiles(B);
+    if ((size_t)B.tot_tv > tv_tiles_cap(ws->plan.max_vox, 1)) return DGR_ERR_WS_TOO_SMALL;
+    cudaError_t e = launch_tv(B, ws_ptr<float>(ws, ws->tv_part), 0, stream);
+    if (e == cudaSuccess) e = launch_loss_final(B, nullptr, 0, nullptr, ws_ptr<float>(ws, ws->tv_part), stream);
+    return cuda_rc(e);
 }
 
 long long dgr_launch_count(void) { return g_launches.load(); }

@@ -123,7 +123,11 @@ struct Inst {
     int fb0;                          // ray scatter fold: first tile
     int *acc;                         // ray scatter: integer sums (z fastest)
     int vsx, vsy, vsz;                // element strides of vol as voxelize output / project input
-    float *vol;                       // volume (voxelize output; step: volume, then its gradient)
+    float *vol;                       // volume (voxelize output, project input)
+    float *gvol;                      // volume gradient, x fastest (backproject output, FVR adjoint input)
+    float w_l1, w_ssim, w_tv;         // objective weights
+    float ssim_c1, ssim_c2;           // SSIM constants
+    int st0, nst, tv0, ntv;           // SSIM tiles, TV tiles: first and count
     float *sino;                      // projection (step: prediction, then residual)
     const float *meas;                // measured projections (step)
     float *loss;                      // loss scalar (step)
@@ -143,6 +147,8 @@ struct Batch {
     int tot_tab, tot_rows, tot_views;
     int tot_blk;
     int tot_bricks;
+    int tot_st, tot_tv;  // SSIM and TV tiles
+    float ssim_w[11];    // SSIM window taps
     long long tot_rays;
     Inst in[MAX_INST];
 };
@@ -189,7 +195,8 @@ struct dgr_ws {
     dgr_ws_plan plan;
     // byte offsets into base
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
-        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, losses, list_tmp, acc;
+        partials, grads, vol, sino, loss_part, rayxy, sino_scaled, losses, list_tmp, acc, gvol, ssim_maps,
+        ssim_g, ssim_part, tv_part;
     size_t scan_tmp_elems;
 };
 
@@ -225,6 +232,15 @@ cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st);
 // x-fastest -> z-fastest copy of a volume (the row-warp projector's layout)
 cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cudaStream_t st);
 // sino_scaled: scratch of all instances' rays (residual x |D|, [view][u][v]); not aliasing sino
+// loss.cu: SSIM and TV terms of the objective
+void ssim_window(float *w);
+void loss_tiles(Batch &B);
+size_t ssim_tiles_cap(long long max_views, int max_nu, int max_nv, int ninst);
+size_t tv_tiles_cap(long long max_vox, int ninst);
+cudaError_t launch_ssim(const Batch &B, float *maps, float *spart, float *gout, cudaStream_t st);
+cudaError_t launch_tv(const Batch &B, float *tpart, int accumulate, cudaStream_t st);
+cudaError_t launch_loss_final(const Batch &B, const float *l1part, int l1_blocks, const float *spart,
+                              const float *tpart, cudaStream_t st);
 // acc: the workspace's integer sums (ray scatter), room for acc_vox voxels
 cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, int *acc,
                                long long acc_vox, cudaStream_t st);
@@ -243,7 +259,7 @@ void set_backprojector_variant(int v);
 
 // step.cu
 constexpr int L1_BLOCKS = 148;  // per instance; fixed so the loss reduction order is fixed
-cudaError_t launch_l1(const Batch &B, float *part, cudaStream_t st);
+cudaError_t launch_l1(const Batch &B, float *part, const float *gadd, cudaStream_t st);
 cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float *resid,
                              float *loss, float *part, cudaStream_t st);
 cudaError_t launch_params_init(const dgr_problem &P, const dgr_params &p, cudaStream_t st);

@@ -513,7 +513,7 @@ __global__ void k_bp_fold(const __grid_constant__ Batch B, const unsigned *__res
     for (int j = ty; j < 32; j += 8) {  // write along x
         const int z = z0 + j, x = x0 + tx;
         if (x < g.nx && z < g.nz) {
-            float *q = I.vol + ((size_t)z * g.ny + y) * g.nx + x;
+            float *q = I.gvol + ((size_t)z * g.ny + y) * g.nx + x;
             *q = I.kv0 == 0 ? tile[tx][j] : *q + tile[tx][j];
         }
     }
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(const __grid_const
     for (int i = threadIdx.x; i < BP_ZP * BP_W; i += 32 * BP_W) {
         const int zz = i / BP_W, xx = i % BP_W;
         const int x = bxi * BP_W + xx, z = zp + zz;
-        if (x < g.nx && z < g.nz) I.vol[(size_t)z * zs + (size_t)iy * g.nx + x] = out_tile[zz][xx];
+        if (x < g.nx && z < g.nz) I.gvol[(size_t)z * zs + (size_t)iy * g.nx + x] = out_tile[zz][xx];
     }
 }
 
@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
         const int xx = i % BBX, yy = (i / BBX) % BBY, zz = i / (BBX * BBY);
         const int x = x0 + xx, y = y0 + yy, z = z0 + zz;
         if (x < x1 && y < y1 && z < z1)
-            I.vol[((size_t)z * g.ny + y) * g.nx + x] = bad ? NAN : accf[(yy * BBX + xx) * BBZ + zz];
+            I.gvol[((size_t)z * g.ny + y) * g.nx + x] = bad ? NAN : accf[(yy * BBX + xx) * BBZ + zz];
     }
 }
 

@@ -1,6 +1,7 @@
 // L1 data term (a5), optimiser-variable transforms and fused Adam (a8).
 //
-// Objective: the L1 term of the paper's loss (Sec. 4.3, Eq. 13); Adam with the
+// Objective: the L1 term of the paper's loss (Sec. 4.3, Eq. 13; the SSIM and TV
+// terms are in loss.cu, the weighted total in k_loss_final); Adam with the
 // learning rate decaying 3e-4 -> 3e-5 over the run (Sec. 5.1).  The decay law,
 // the Adam constants and the parameterisation are not stated in the paper; the
 // choices (exponential decay; betas 0.9/0.999, eps 1e-8; mu in [-1,1]^3 box
@@ -15,17 +16,21 @@ namespace {
 constexpr int L1_THREADS = 256;
 
 // per-instance loss partials: grid (L1_BLOCKS, instance), grid-stride over the
-// instance's rays; resid = sign(pred - meas) / m written over pred
+// instance's rays; resid = w sign(pred - meas) / m (+ gadd, the other terms'
+// gradient with respect to pred) written over pred
 __device__ __forceinline__ float l1_block(const float *pred, const float *meas, long long m,
-                                          float *resid, int blk, int nblk) {
+                                          float *resid, int blk, int nblk, float w,
+                                          const float *gadd) {
     __shared__ float ws[L1_THREADS / 32];
-    const float invm = (float)(1.0 / (double)m);
+    const float wm = (float)((double)w / (double)m);
     float s = 0.f;
     for (long long i = (long long)blk * L1_THREADS + threadIdx.x; i < m;
          i += (long long)nblk * L1_THREADS) {
         const float d = pred[i] - meas[i];
         s += fabsf(d);
-        resid[i] = d > 0.f ? invm : (d < 0.f ? -invm : 0.f);
+        float r = d > 0.f ? wm : (d < 0.f ? -wm : 0.f);
+        if (gadd) r += gadd[i];
+        resid[i] = r;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -38,16 +43,18 @@ __device__ __forceinline__ float l1_block(const float *pred, const float *meas, 
 }
 
 __global__ void __launch_bounds__(L1_THREADS) k_l1(const __grid_constant__ Batch B,
-                                                   float *__restrict__ part) {
+                                                   float *__restrict__ part,
+                                                   const float *__restrict__ gadd) {
     const Inst &I = B.in[blockIdx.y];
     const long long m = (long long)I.n_views * I.nu * I.nv;
-    const float t = l1_block(I.sino, I.meas, m, I.sino, blockIdx.x, gridDim.x);
+    const float t = l1_block(I.sino, I.meas, m, I.sino, blockIdx.x, gridDim.x, I.w_l1,
+                             (gadd && I.w_ssim != 0.f) ? gadd + I.ray0 : nullptr);
     if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 __global__ void k_l1_single(const float *__restrict__ pred, const float *__restrict__ meas,
                             long long m, float *resid, float *__restrict__ part) {
-    const float t = l1_block(pred, meas, m, resid, blockIdx.x, gridDim.x);
+    const float t = l1_block(pred, meas, m, resid, blockIdx.x, gridDim.x, 1.f, nullptr);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -58,12 +65,6 @@ __device__ __forceinline__ void l1_final(const float *part, int nb, long long m,
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) *loss = (float)(s / (double)m);
-}
-
-__global__ void k_l1_final(const __grid_constant__ Batch B, const float *__restrict__ part) {
-    const Inst &I = B.in[blockIdx.x];
-    const long long m = (long long)I.n_views * I.nu * I.nv;
-    l1_final(part + blockIdx.x * L1_BLOCKS, L1_BLOCKS, m, I.loss);
 }
 
 __global__ void k_l1_final_single(const float *__restrict__ part, long long m, float *loss) {
@@ -161,10 +162,9 @@ __global__ void k_step_inc(const __grid_constant__ Batch B) {
 
 }  // namespace
 
-cudaError_t launch_l1(const Batch &B, float *part, cudaStream_t st) {
-    k_l1<<<dim3(L1_BLOCKS, B.n), L1_THREADS, 0, st>>>(B, part);
-    k_l1_final<<<B.n, 32, 0, st>>>(B, part);
-    counted(2);
+cudaError_t launch_l1(const Batch &B, float *part, const float *gadd, cudaStream_t st) {
+    k_l1<<<dim3(L1_BLOCKS, B.n), L1_THREADS, 0, st>>>(B, part, gadd);
+    counted(1);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_bwd_items(
         const int c = (int)(it - item_off[gi]);
         const Inst &I = B.in[inst_of_g(B, gi)];
         const dgr_grid &g = I.g;
-        const float *__restrict__ gv = I.vol;
+        const float *__restrict__ gv = I.gvol;
         const Prep P = prep[gi];
         const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
                   lz = box_lo(P.bz), hz = box_hi(P.bz);

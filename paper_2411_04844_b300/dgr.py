@@ -37,7 +37,7 @@ EXPORTS = [
     "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth", "dgr_set_backprojector",
     "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
     "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
-    "dgr_seed_rescale",
+    "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -94,7 +94,9 @@ class WsPlan(ctypes.Structure):
 class Problem(ctypes.Structure):
     _fields_ = [("grid", Grid), ("geom", Geom), ("k_trunc", ctypes.c_float),
                 ("lr0", ctypes.c_float), ("lr1", ctypes.c_float), ("n_iters", ctypes.c_int),
-                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("w_l1", ctypes.c_float), ("w_ssim", ctypes.c_float), ("w_tv", ctypes.c_float),
+                ("ssim_range", ctypes.c_float)]
 
 
 class Params(ctypes.Structure):
@@ -134,6 +136,8 @@ def lib():
             "dgr_project": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P, P],
             "dgr_backproject": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P, P],
             "dgr_l1_residual": [P, P, ll, P, P, P, P],
+            "dgr_ssim_loss": [ctypes.POINTER(Geom), P, P, f, P, P, P, P],
+            "dgr_tv_loss": [ctypes.POINTER(Grid), P, P, P, P, P],
             "dgr_params_init": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P],
             "dgr_step": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P],
             "dgr_step_timed": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P,
@@ -342,12 +346,35 @@ def dgr_l1_residual(pred, meas, resid, loss, ws: Workspace, stream=None):
                               ws.ptr, _stream(stream)), "dgr_l1_residual")
 
 
+def dgr_ssim_loss(geom: Geom, pred, meas, grad, loss, ws: Workspace, data_range=1.0, stream=None):
+    """loss = 1 - SSIM(pred, meas) over every projection image, grad = dloss/dpred."""
+    for t, nm in ((pred, "pred"), (meas, "meas"), (grad, "grad"), (loss, "loss")):
+        _check(t, nm)
+    _rc(lib().dgr_ssim_loss(ctypes.byref(geom), _ptr(pred), _ptr(meas), float(data_range), _ptr(grad),
+                            _ptr(loss), ws.ptr, _stream(stream)), "dgr_ssim_loss")
+
+
+def dgr_tv_loss(grid: Grid, vol, grad, loss, ws: Workspace, stream=None):
+    """loss = anisotropic TV of vol / voxels, grad = dloss/dvol."""
+    for t, nm in ((vol, "vol"), (grad, "grad"), (loss, "loss")):
+        _check(t, nm)
+    _rc(lib().dgr_tv_loss(ctypes.byref(grid), _ptr(vol), _ptr(grad), _ptr(loss), ws.ptr,
+                          _stream(stream)), "dgr_tv_loss")
+
+
 # ---------------------------------------------------------------------------
 # optimisation step
 # ---------------------------------------------------------------------------
+PAPER_WEIGHTS = (0.6, 0.2, 1.0)  # L1, SSIM, TV (paper Sec. 4.3)
+
+
 def make_problem(grid: Grid, geom: Geom, k_trunc=3.0, lr0=3e-4, lr1=3e-5, n_iters=2000,
-                 beta1=0.9, beta2=0.999, eps=1e-8) -> Problem:
-    return Problem(grid, geom, k_trunc, lr0, lr1, n_iters, beta1, beta2, eps)
+                 beta1=0.9, beta2=0.999, eps=1e-8, weights=(1.0, 0.0, 0.0),
+                 ssim_range=1.0) -> Problem:
+    """weights: (w_l1, w_ssim, w_tv) of the objective; PAPER_WEIGHTS for the
+    paper's full loss.  ssim_range: the data range L of the SSIM constants."""
+    return Problem(grid, geom, k_trunc, lr0, lr1, n_iters, beta1, beta2, eps,
+                   float(weights[0]), float(weights[1]), float(weights[2]), float(ssim_range))
 
 
 class State:
