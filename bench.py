@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--objective", choices=["l1", "paper"], default="l1",
+                    help="l1: the L1 data term (the hot path); paper: 0.6 L1 + 0.2 SSIM + 1 TV")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -143,7 +145,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def setup_problem(rank, dev):
+def setup_problem(rank, dev, objective="l1"):
     import torch
     from paper_2411_04844_b300 import dgr, synth
     wl = synth.workload(WORKLOAD)
@@ -175,7 +177,8 @@ def setup_problem(rank, dev):
     ws0.close()
     plan = dgr.make_plan(grid, f.n, int(pairs * 1.5) + 1024, int(items * 1.5) + 1024, geom, step=True)
     ws = dgr.Workspace(plan)
-    prob = dgr.make_problem(grid, geom, wl.k_trunc, 3e-4, 3e-5, wl.n_iters)
+    weights = dgr.PAPER_WEIGHTS if objective == "paper" else (1.0, 0.0, 0.0)
+    prob = dgr.make_problem(grid, geom, wl.k_trunc, 3e-4, 3e-5, wl.n_iters, weights=weights)
     st = dgr.State(mu, s, q, rho)
     dgr.dgr_params_init(prob, st)
     return dict(wl=wl, grid=grid, geom=geom, ang=ang, meas=meas, ws=ws, prob=prob, st=st,
@@ -187,7 +190,7 @@ def run_ours(args, dist, rank, local):
     from paper_2411_04844_b300 import dgr
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
-    P = setup_problem(rank, dev)
+    P = setup_problem(rank, dev, args.objective)
     wl, ws, prob, st, meas = P["wl"], P["ws"], P["prob"], P["st"], P["meas"]
     stream = torch.cuda.current_stream()
     loss = torch.zeros(1, device=dev)
@@ -423,6 +426,7 @@ def main():
         "gpu_launches": R["launches"],
         "clocks": R["clocks"],
         "loss": R["loss"],
+        "objective": args.objective,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
