@@ -219,6 +219,8 @@ typedef struct {
     float *mu, *s, *q, *rho;
     float *theta, *m, *v;
     int *step;
+    float *grad_accum;  /* optional device [n] (NULL: none): every step adds |dL/dmu| (world
+                         * units) of each Gaussian -- the statistic of dgr_densify */
 } dgr_params;
 
 /* theta from (mu, s, q, rho); m = v = 0; step = 0. */
@@ -230,6 +232,32 @@ int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t s
  * plan must carry max_vox and max_rays of this problem. */
 int dgr_step(const dgr_problem *prob, const dgr_params *p, const float *measured,
              float *loss_out, dgr_ws *ws, cudaStream_t stream);
+
+/* Adaptive density control (paper App. F, Algorithm 2).  With avg = grad_accum
+ * / iters and sigma = the largest axis scale of a Gaussian:
+ *   clone  avg >= tau, sigma <= theta_frac x body diagonal of the grid: the
+ *          n_clone of largest avg (ties: lower index), n_clone <= n_max - n;
+ *          the original and its copy each get half the intensity;
+ *   split  avg >= tau, sigma > theta: the n_split of largest avg, n_split <=
+ *          n_max - n - n_clone; each is replaced by two children
+ *          mu + R(q) diag(s) z (z: normals[i][c], standard normal 3-vectors
+ *          supplied by the caller, device [n][2][3]), scales s / 2^(1/3), the
+ *          same rotation and intensity;
+ *   prune  the other originals with avg <= tau or sigma > 3 size h.
+ * out receives surviving originals (index order; theta, m, v kept), clones
+ * and children (theta from their parameters, zero moments, zero grad_accum);
+ * its arrays must hold n_max Gaussians and must not alias in's; *out->step =
+ * *in->step.  in->grad_accum is required.  *n_out (host) receives the new
+ * count: the call synchronises the stream.  The decisions are taken on the
+ * FP32 values.  The plan needs max_n >= in->n. */
+typedef struct {
+    float tau;         /* minimum mean gradient (2e-4 in the paper) */
+    float theta_frac;  /* small/large threshold as a fraction of the body diagonal (0.005) */
+    float size;        /* box size in voxels (17): wider than 3 size h is pruned */
+    int n_max;         /* cap on the number of Gaussians (500,000) */
+} dgr_densify_cfg;
+int dgr_densify(const dgr_grid *grid, const dgr_densify_cfg *cfg, int iters, const dgr_params *in,
+                const float *normals, dgr_params *out, int *n_out, dgr_ws *ws, cudaStream_t stream);
 
 /* Many independent reconstructions in one call (the paper runs one problem
  * at a time): n_inst <= 16 problems, each with its own

@@ -10,6 +10,8 @@ Readings taken where the algorithm is silent or ambiguous:
     theta = 0.005 x the grid's body diagonal; the pruning bound is 3 x size x h
     (size = box size in voxels, 17 by default);
   * top_k picks the largest avg_grad first, equal values by lower index;
+  * the decisions (thresholds, order) are taken on FP32 values, as the
+    kernel takes them;
   * clones and split children are new: pruning applies to the Gaussians that
     existed before this densification (a clone has zero gradient by
     construction and would otherwise be removed at once); a split original is
@@ -54,10 +56,16 @@ def densify(grid, mu, s, q, rho, grad_accum, iters, normals, tau=2e-4, n_max=500
     q = np.asarray(q, np.float64); rho = np.asarray(rho, np.float64)
     n = mu.shape[0]
     h = grid.h
-    diag = float(np.sqrt(sum((d * h) ** 2 for d in grid.dims)))
-    theta = theta_frac * diag
-    avg = np.asarray(grad_accum, np.float64) / iters
-    sig = s.max(axis=1)
+    # the decisions are integer outcomes of FP32 comparisons: taken in FP32,
+    # as the kernel takes them (avg = acc / iters rounded to FP32, thresholds
+    # rounded to FP32)
+    f32 = np.float32
+    diag = float(np.sqrt(sum((float(d) * d) for d in grid.dims))) * h
+    theta = f32(float(f32(theta_frac)) * diag)
+    tau = f32(tau)
+    avg = (np.asarray(grad_accum, f32) / f32(iters)).astype(f32)
+    sig = np.asarray(s, f32).max(axis=1)
+    prune_sig = f32(f32(3.0) * f32(size) * f32(h))
     # clone: under-reconstructed, small
     cand = (avg >= tau) & (sig <= theta)
     n_clone = min(max(n_max - n, 0), int(cand.sum()))
@@ -69,7 +77,7 @@ def densify(grid, mu, s, q, rho, grad_accum, iters, normals, tau=2e-4, n_max=500
     n_split = min(max(n_max - n1, 0), int(cand.sum()))
     split = top_k(avg, cand, n_split)
     # prune among the originals that stay
-    prune = ((avg <= tau) | (sig > 3 * size * h)) & ~split
+    prune = ((avg <= tau) | (sig > prune_sig)) & ~split
     keep = ~split & ~prune
     out_mu = [mu[keep]]; out_s = [s[keep]]; out_q = [q[keep]]; out_rho = [rho_c[keep]]
     kind = [np.zeros(int(keep.sum()), int)]; src = [np.flatnonzero(keep)]

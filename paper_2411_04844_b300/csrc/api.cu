@@ -63,7 +63,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA; }
 struct Layout {
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
         partials, grads, vol, sino, loss_part, rayxy, sino_scaled, list_tmp, gvol, ssim_maps, ssim_g,
-        ssim_part, tv_part, acc, total;
+        ssim_part, tv_part, dens, acc, total;
     size_t scan_elems;
 };
 
@@ -115,6 +115,8 @@ Layout layout_of(const dgr_ws_plan &p) {
     L.ssim_g = take(4 * (size_t)p.max_rays);
     L.ssim_part = take(4 * ssim_tiles_cap(p.max_views, p.max_nu, p.max_nv, ninst));
     L.tv_part = take(4 * tv_tiles_cap(p.max_vox, ninst));
+    // densification: keys, flags, three offset scans of max_n + 1, counts
+    L.dens = take(4 * (5 * ((size_t)p.max_n + 1) + 8));
     // integer sums of the ray-driven backprojector (z fastest), kept zero between calls
     L.acc = take(p.max_vox > 0 ? 4 * ((size_t)p.max_vox + vpad) : 0);
     L.total = o;
@@ -152,7 +154,7 @@ int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan) {
     w->list_tmp = L.list_tmp;
     w->acc = L.acc;
     w->gvol = L.gvol; w->ssim_maps = L.ssim_maps; w->ssim_g = L.ssim_g; w->ssim_part = L.ssim_part;
-    w->tv_part = L.tv_part;
+    w->tv_part = L.tv_part; w->dens = L.dens;
     w->scan_tmp_elems = L.scan_elems;
     if (cudaMemset(w->base + L.status, 0, 256) != cudaSuccess ||
         cudaMemset(w->base + L.acc, 0, L.total - L.acc) != cudaSuccess) {
@@ -517,7 +519,7 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
         I.n = p->n;
         I.mu = p->mu; I.s = p->s; I.q = p->q; I.rho = p->rho;
         I.mu_w = p->mu; I.s_w = p->s; I.q_w = p->q; I.rho_w = p->rho;
-        I.theta = p->theta; I.m = p->m; I.v = p->v; I.step = p->step;
+        I.theta = p->theta; I.m = p->m; I.v = p->v; I.step = p->step; I.gacc = p->grad_accum;
         I.meas = measured[i];
         I.loss = loss_out + i;
         I.lr0 = P->lr0; I.lr1 = P->lr1; I.b1 = P->beta1; I.b2 = P->beta2; I.eps = P->eps;
@@ -656,6 +658,27 @@ int dgr_tv_loss(const dgr_grid *grid, const float *vol, float *grad, float *loss
     cudaError_t e = launch_tv(B, ws_ptr<float>(ws, ws->tv_part), 0, stream);
     if (e == cudaSuccess) e = launch_loss_final(B, nullptr, 0, nullptr, ws_ptr<float>(ws, ws->tv_part), stream);
     return cuda_rc(e);
+}
+
+int dgr_densify(const dgr_grid *grid, const dgr_densify_cfg *cfg, int iters, const dgr_params *in,
+                const float *normals, dgr_params *out, int *n_out, dgr_ws *ws, cudaStream_t stream) {
+    if (!grid_ok(grid) || !cfg || !in || !out || !n_out || !ws || iters < 1) return DGR_ERR_ARG;
+    if (!(cfg->tau >= 0.f) || !(cfg->theta_frac >= 0.f) || !(cfg->size > 0.f) || cfg->n_max < 1 ||
+        cfg->n_max >= (1 << 24))
+        return DGR_ERR_ARG;
+    if (!params_ok(in) || !in->grad_accum || (in->n > 0 && !normals)) return DGR_ERR_ARG;
+    if (!out->mu || !out->s || !out->q || !out->rho || !out->theta || !out->m || !out->v || !out->step ||
+        !aligned16(out->q))
+        return DGR_ERR_ARG;
+    if (in->n > ws->plan.max_n) return DGR_ERR_WS_TOO_SMALL;
+    int *counts = reinterpret_cast<int *>(ws_ptr<unsigned>(ws, ws->dens) + 5 * ((size_t)ws->plan.max_n + 1));
+    cudaError_t e = launch_densify(*grid, *cfg, iters, *in, normals, *out, ws, counts, stream);
+    int h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return DGR_ERR_CUDA;
+    *n_out = h[2];
+    return DGR_OK;
 }
 
 long long dgr_launch_count(void) { return g_launches.load(); }

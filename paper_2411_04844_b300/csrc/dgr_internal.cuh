@@ -135,6 +135,7 @@ struct Inst {
     float *theta, *m, *v;
     int *step;
     float *mu_w, *s_w, *q_w, *rho_w;  // parameters rewritten by Adam
+    float *gacc;                      // optional |dL/dmu| accumulator (densification)
     float lr0, lr1, b1, b2, eps;
     int n_iters;
 };
@@ -196,7 +197,7 @@ struct dgr_ws {
     // byte offsets into base
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
         partials, grads, vol, sino, loss_part, rayxy, sino_scaled, losses, list_tmp, acc, gvol, ssim_maps,
-        ssim_g, ssim_part, tv_part;
+        ssim_g, ssim_part, tv_part, dens;
     size_t scan_tmp_elems;
 };
 
@@ -232,6 +233,10 @@ cudaError_t launch_project(const Batch &B, const RayXY *tab, cudaStream_t st);
 // x-fastest -> z-fastest copy of a volume (the row-warp projector's layout)
 cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cudaStream_t st);
 // sino_scaled: scratch of all instances' rays (residual x |D|, [view][u][v]); not aliasing sino
+// densify.cu: adaptive density control; counts_dev: device int[3] (n_clone, n_split, n_out)
+cudaError_t launch_densify(const dgr_grid &g, const dgr_densify_cfg &cfg, int iters, const dgr_params &in,
+                           const float *normals, const dgr_params &out, dgr_ws *ws, int *counts_dev,
+                           cudaStream_t st);
 // loss.cu: SSIM and TV terms of the objective
 void ssim_window(float *w);
 void loss_tiles(Batch &B);

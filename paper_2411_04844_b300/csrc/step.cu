@@ -140,6 +140,10 @@ __global__ void k_adam(const __grid_constant__ Batch B) {
         th[o] = nt;
         return nt;
     };
+    if (I.gacc) {  // densification statistic: |dL/dmu| in world units
+        const float gx = I.g_mu[3 * i], gy = I.g_mu[3 * i + 1], gz = I.g_mu[3 * i + 2];
+        I.gacc[i] += sqrtf(gx * gx + gy * gy + gz * gz);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float tm = upd(3 * i + a, I.g_mu[3 * i + a] * A.half[a]);

@@ -37,7 +37,7 @@ EXPORTS = [
     "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth", "dgr_set_backprojector",
     "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
     "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
-    "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss",
+    "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss", "dgr_densify",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -102,7 +102,18 @@ class Problem(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("mu", ctypes.c_void_p), ("s", ctypes.c_void_p),
                 ("q", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("theta", ctypes.c_void_p),
-                ("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("step", ctypes.c_void_p)]
+                ("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("step", ctypes.c_void_p),
+                ("grad_accum", ctypes.c_void_p)]
+
+
+class DensifyCfg(ctypes.Structure):
+    """Algorithm 2 constants (paper defaults)."""
+    _fields_ = [("tau", ctypes.c_float), ("theta_frac", ctypes.c_float), ("size", ctypes.c_float),
+                ("n_max", ctypes.c_int)]
+
+    @classmethod
+    def paper(cls, n_max=500_000):
+        return cls(2e-4, 0.005, 17.0, int(n_max))
 
 
 def lib_path() -> str:
@@ -138,6 +149,8 @@ def lib():
             "dgr_l1_residual": [P, P, ll, P, P, P, P],
             "dgr_ssim_loss": [ctypes.POINTER(Geom), P, P, f, P, P, P, P],
             "dgr_tv_loss": [ctypes.POINTER(Grid), P, P, P, P, P],
+            "dgr_densify": [ctypes.POINTER(Grid), ctypes.POINTER(DensifyCfg), i, ctypes.POINTER(Params),
+                            P, ctypes.POINTER(Params), ctypes.POINTER(i), P, P],
             "dgr_params_init": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P],
             "dgr_step": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P],
             "dgr_step_timed": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P,
@@ -378,21 +391,54 @@ def make_problem(grid: Grid, geom: Geom, k_trunc=3.0, lr0=3e-4, lr1=3e-5, n_iter
 
 
 class State:
-    """Device tensors of the optimiser state (dgr_params)."""
+    """Device tensors of the optimiser state (dgr_params).  With accumulate=True
+    every step adds |dL/dmu| per Gaussian to grad_accum (densification).
+    capacity >= n reserves room for densification (arrays hold capacity
+    Gaussians, the first n in use)."""
 
-    def __init__(self, mu, s, q, rho):
+    def __init__(self, mu, s, q, rho, accumulate=False, capacity=None):
         n = mu.shape[0]
+        cap = max(n, capacity or n)
         dev = mu.device
         self.n = n
-        self.mu, self.s, self.q, self.rho = (t.contiguous().clone() for t in (mu, s, q, rho))
-        self.theta = torch.zeros(11 * n, device=dev)
-        self.m = torch.zeros(11 * n, device=dev)
-        self.v = torch.zeros(11 * n, device=dev)
+        self.cap = cap
+
+        def buf(t, w):
+            b = torch.zeros((cap, w) if w > 1 else (cap,), device=dev)
+            b[:n] = t
+            return b
+        self.mu, self.s, self.q = buf(mu, 3), buf(s, 3), buf(q, 4)
+        self.rho = buf(rho, 1)
+        self.theta = torch.zeros(11 * cap, device=dev)
+        self.m = torch.zeros(11 * cap, device=dev)
+        self.v = torch.zeros(11 * cap, device=dev)
         self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.grad_accum = torch.zeros(cap, device=dev) if accumulate else None
 
     def params(self) -> Params:
         return Params(self.n, _ptr(self.mu), _ptr(self.s), _ptr(self.q), _ptr(self.rho),
-                      _ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.step))
+                      _ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.step),
+                      _ptr(self.grad_accum) if self.grad_accum is not None else None)
+
+    def view(self):
+        """(mu, s, q, rho) of the n Gaussians in use."""
+        return self.mu[:self.n], self.s[:self.n], self.q[:self.n], self.rho[:self.n]
+
+
+def dgr_densify(grid: Grid, cfg: DensifyCfg, iters: int, src: State, normals, dst: State,
+                ws: Workspace, stream=None) -> int:
+    """Algorithm 2 from src into dst (dst.cap >= cfg.n_max); returns the new n
+    (dst.n is updated).  normals: device [src.n, 2, 3] standard normals."""
+    if dst.cap < cfg.n_max:
+        raise DgrError("dgr_densify: destination capacity below n_max")
+    _check(normals, "normals")
+    pin, pout = src.params(), dst.params()
+    n_out = ctypes.c_int(0)
+    _rc(lib().dgr_densify(ctypes.byref(grid), ctypes.byref(cfg), int(iters), ctypes.byref(pin),
+                          _ptr(normals), ctypes.byref(pout), ctypes.byref(n_out), ws.ptr, _stream(stream)),
+        "dgr_densify")
+    dst.n = int(n_out.value)
+    return dst.n
 
 
 def dgr_params_init(prob: Problem, st: State, stream=None):
