@@ -111,6 +111,13 @@ int dgr_set_deterministic(int on);
  * CTAs for small grids.  A process-wide setting, chosen by the autotuner
  * (paper_2411_04844_b300/autotune.py); workspace plans depend on it. */
 int dgr_set_tile_depth(int tz);
+/* 1 (default): when every Gaussian of a voxelize call has a diagonal A
+ * (isotropic scales -- the paper's representation -- or an identity rotation),
+ * the voxelizer uses its separable form, exp(-d^T A d / 2) = EXY(x, y) EZ(z):
+ * per tile an outer-product sum, two small exponential tables per Gaussian
+ * and one FMA per (Gaussian, voxel) pair (tile depth 32 only); 0: always the
+ * general kernel.  A process-wide setting. */
+int dgr_set_separable(int on);
 /* Backprojector implementation (all exact transposes of dgr_project, all
  * bit-reproducible): 0 (default) = ray scatter -- a CTA per detector column
  * walks the column's path like the projector and adds into integer sums in

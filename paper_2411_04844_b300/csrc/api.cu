@@ -215,6 +215,11 @@ int dgr_set_backprojector(int variant) {
     return DGR_OK;
 }
 
+int dgr_set_separable(int on) {
+    set_separable(on);
+    return DGR_OK;
+}
+
 int dgr_set_tile_depth(int tz) {
     if (tz != 8 && tz != 16 && tz != 32) return DGR_ERR_ARG;
     set_tile_depth(tz);

@@ -26,36 +26,33 @@ constexpr int VOX_CHUNK = 64;  // prep records staged in shared memory at a time
 constexpr int ITEM_VOX = 2048;
 constexpr int NMOM = 10;  // moments per item: S0, S1[3], S2[6]
 
-// Work items of the backward pass cover a box of ex * ey * ez voxels:
-//   ex * ey <= ITEM_VOX: z-slabs of zc = ITEM_VOX / (ex * ey) layers;
-//   otherwise: per z layer, y-slabs of yc = max(1, ITEM_VOX / ex) rows.
+// Work items of the backward pass cover a box of ex * ey * ez voxels: a
+// warp's lanes take the (x, y) columns of the item and walk its z range, so
+// the z range is kept long (the per-column set-up is paid once per column):
+//   zc = min(ez, max(1, ITEM_VOX / ex)) layers, yc = min(ey, max(1, ITEM_VOX /
+//   (ex zc))) rows; items are the ceil(ey / yc) x ceil(ez / zc) blocks.
+__host__ __device__ inline void item_shape(int ex, int ey, int ez, int &yc, int &zc) {
+    zc = ez < ITEM_VOX / ex ? ez : (ITEM_VOX / ex > 1 ? ITEM_VOX / ex : 1);
+    const long long xz = (long long)ex * zc;
+    yc = xz < ITEM_VOX ? (int)(ITEM_VOX / xz) : 1;
+    if (yc > ey) yc = ey;
+}
 __host__ __device__ inline uint32_t item_count(int ex, int ey, int ez) {
     if (ex <= 0 || ey <= 0 || ez <= 0) return 0u;
-    const long long exy = (long long)ex * ey;
-    if (exy <= ITEM_VOX) {
-        const int zc = (int)(ITEM_VOX / exy);
-        return (uint32_t)((ez + zc - 1) / zc);
-    }
-    const int yc = ex < ITEM_VOX ? ITEM_VOX / ex : 1;
-    return (uint32_t)ez * (uint32_t)((ey + yc - 1) / yc);
+    int yc, zc;
+    item_shape(ex, ey, ez, yc, zc);
+    return (uint32_t)((ey + yc - 1) / yc) * (uint32_t)((ez + zc - 1) / zc);
 }
 // item c of a box with lower corner (ly, lz) and upper (hy, hz): y and z ranges
 __host__ __device__ inline void item_range(int c, int ex, int ey, int ly, int hy, int lz, int hz,
                                            int &yb, int &ye, int &zb, int &ze) {
-    const long long exy = (long long)ex * ey;
-    if (exy <= ITEM_VOX) {
-        const int zc = (int)(ITEM_VOX / exy);
-        zb = lz + c * zc;
-        ze = min(zb + zc - 1, hz);
-        yb = ly;
-        ye = hy;
-    } else {
-        const int yc = ex < ITEM_VOX ? ITEM_VOX / ex : 1;
-        const int nyc = (ey + yc - 1) / yc;
-        zb = ze = lz + c / nyc;
-        yb = ly + (c % nyc) * yc;
-        ye = min(yb + yc - 1, hy);
-    }
+    int yc, zc;
+    item_shape(ex, ey, hz - lz + 1, yc, zc);
+    const int nyc = (ey + yc - 1) / yc;
+    yb = ly + (c % nyc) * yc;
+    ye = min(yb + yc - 1, hy);
+    zb = lz + (c / nyc) * zc;
+    ze = min(zb + zc - 1, hz);
 }
 
 // log2(e): the exponent exp(-x/2) is evaluated as ex2(-x/2 * log2(e)).
@@ -100,6 +97,9 @@ struct __align__(16) RowZ {
 // of the C ABI is a batch of one.
 // ---------------------------------------------------------------------------
 constexpr int MAX_INST = 16;
+// status block (256 bytes of the workspace): [0] device status flags,
+// [16] voxelizer tile queue head, [17] set when a Gaussian is not separable
+constexpr int SEP_FLAG = 17;
 
 struct Inst {
     dgr_grid g;
@@ -258,6 +258,7 @@ int bp_blocks(const dgr_grid &g, int &nbx, int &nbz);
 // brick backprojector: bricks per axis and the ray colour classes of a geometry
 int bp_bricks(const dgr_grid &g, int &nbx, int &nby, int &nbz);
 int multi_z(const dgr_geom &geo);
+void set_separable(int on);
 void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv);
 int backprojector_variant();
 void set_backprojector_variant(int v);

@@ -154,12 +154,20 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
     const float h2 = g.h * g.h;
     const float is0 = h2 / (sc[0] * sc[0]), is1 = h2 / (sc[1] * sc[1]), is2 = h2 / (sc[2] * sc[2]);
     float A[6];
-    A[0] = R[0] * R[0] * is0 + R[1] * R[1] * is1 + R[2] * R[2] * is2;  // 00
-    A[1] = R[3] * R[3] * is0 + R[4] * R[4] * is1 + R[5] * R[5] * is2;  // 11
-    A[2] = R[6] * R[6] * is0 + R[7] * R[7] * is1 + R[8] * R[8] * is2;  // 22
-    A[3] = R[0] * R[3] * is0 + R[1] * R[4] * is1 + R[2] * R[5] * is2;  // 01
-    A[4] = R[0] * R[6] * is0 + R[1] * R[7] * is1 + R[2] * R[8] * is2;  // 02
-    A[5] = R[3] * R[6] * is0 + R[4] * R[7] * is1 + R[5] * R[8] * is2;  // 12
+    if (sc[0] == sc[1] && sc[1] == sc[2]) {
+        // isotropic (the paper's representation): A = h^2 / s^2 I for any rotation
+        A[0] = A[1] = A[2] = is0;
+        A[3] = A[4] = A[5] = 0.f;
+    } else {
+        A[0] = R[0] * R[0] * is0 + R[1] * R[1] * is1 + R[2] * R[2] * is2;  // 00
+        A[1] = R[3] * R[3] * is0 + R[4] * R[4] * is1 + R[5] * R[5] * is2;  // 11
+        A[2] = R[6] * R[6] * is0 + R[7] * R[7] * is1 + R[8] * R[8] * is2;  // 22
+        A[3] = R[0] * R[3] * is0 + R[1] * R[4] * is1 + R[2] * R[5] * is2;  // 01
+        A[4] = R[0] * R[6] * is0 + R[1] * R[7] * is1 + R[2] * R[8] * is2;  // 02
+        A[5] = R[3] * R[6] * is0 + R[4] * R[7] * is1 + R[5] * R[8] * is2;  // 12
+    }
+    // a Gaussian with off-diagonal terms rules out the separable voxelizer
+    if (A[3] != 0.f || A[4] != 0.f || A[5] != 0.f) status[SEP_FLAG] = 1;
     const float c = -0.5f * LOG2E;
     P.dx = del[0]; P.dy = del[1]; P.dz = del[2]; P.rho = r;
     P.a00 = c * A[0]; P.a11 = c * A[1]; P.a22 = c * A[2];
@@ -324,9 +332,10 @@ template <int TZ>
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
-    unsigned long long cap, int *__restrict__ queue) {
+    unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off) {
     __shared__ float4 sp[VOX_CHUNK * 4];
     __shared__ int s_tile;
+    if (sep_off && *sep_off == 0) return;  // every Gaussian separable: k_voxelize_sep runs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (;;) {
         __syncthreads();  // everyone is done with s_tile and sp
@@ -416,9 +425,124 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     }
 }
 
+// FVR for separable Gaussians (the paper's isotropic representation, or
+// axis-aligned ones): with A diagonal, rho exp2(a00 dx^2 + a11 dy^2 + a22 dz^2)
+// = EXY(x, y) EZ(z).  Same tiles, work lists, warps and skips as k_voxelize
+// (a warp owns an 8 x 4 (x, y) patch, each lane a z column of the tile), but
+// per chunk of Gaussians the z factors EZ (zero outside each box) are built
+// once in shared memory, each lane evaluates one exponential per (Gaussian,
+// column), and every (Gaussian, voxel) pair costs one FMA on a value read as
+// part of a 16-byte shared load.  Chunk sums join the running sums with Kahan
+// compensation.  Runs only when every Gaussian of the call is separable
+// (k_prep's flag), tile depth 32.
+constexpr int SEP_TZ = 32;
+
+__global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
+    const __grid_constant__ Batch B, const Prep *__restrict__ prep,
+    const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
+    unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off) {
+    __shared__ float4 sp[VOX_CHUNK * 4];
+    __shared__ __align__(16) float ez[VOX_CHUNK][SEP_TZ];
+    __shared__ int s_tile;
+    if (*sep_off != 0) return;  // a non-separable Gaussian: the general kernel runs
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
+        __syncthreads();
+        const int tg = s_tile;
+        if (tg >= B.tot_tiles) return;
+        const Inst &I = B.in[inst_of_tile(B, tg)];
+        const dgr_grid &g = I.g;
+        const int tl = tg - I.tile0;
+        const int tx = tl % I.ntx, ty = (tl / I.ntx) % I.nty, tz = tl / (I.ntx * I.nty);
+        const int x0 = tx * TX, y0 = ty * TY, z0 = tz * SEP_TZ;
+        const int x = x0 + (lane & 7);
+        const int wy0 = y0 + 4 * w;
+        const int y = wy0 + (lane >> 3);
+        float acc[SEP_TZ], cmp[SEP_TZ];
+#pragma unroll
+        for (int k = 0; k < SEP_TZ; ++k) acc[k] = cmp[k] = 0.f;
+        unsigned long long b = tile_off[tg], e = tile_off[tg + 1];
+        if (e > cap) e = cap;
+        for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
+            const int nc = (int)min((unsigned long long)VOX_CHUNK, e - c0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < nc * 4; i += VOX_THREADS) {
+                const uint32_t gi = list[c0 + (i >> 2)];
+                sp[i] = reinterpret_cast<const float4 *>(prep + gi)[i & 3];
+            }
+            __syncthreads();
+            // z factors of the chunk, zero outside each box
+            for (int f = threadIdx.x; f < nc * SEP_TZ; f += VOX_THREADS) {
+                const int j = f / SEP_TZ, k = f % SEP_TZ, z = z0 + k;
+                const float4 p0 = sp[4 * j], p1 = sp[4 * j + 1], p3 = sp[4 * j + 3];
+                const int bz = __float_as_int(p3.w), az = __float_as_int(p3.x);
+                const float dz = (float)(z - az) - p0.z;
+                ez[j][k] = (z >= box_lo(bz) && z <= box_hi(bz)) ? ex2_approx(p1.z * dz * dz) : 0.f;
+            }
+            __syncthreads();
+            float cs[SEP_TZ];
+#pragma unroll
+            for (int k = 0; k < SEP_TZ; ++k) cs[k] = 0.f;
+            for (int j = 0; j < nc; ++j) {
+                const float4 p3 = sp[4 * j + 3];
+                const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z), bz = __float_as_int(p3.w);
+                const int lx = box_lo(bx), hx = box_hi(bx), ly = box_lo(by), hy = box_hi(by);
+                const int zlo = max(box_lo(bz) - z0, 0), zhi = min(box_hi(bz) - z0, SEP_TZ - 1);
+                // warp-uniform skip: the warp's 8 x 4 patch or the z range misses the box
+                if (hx < x0 || lx > x0 + 7 || hy < wy0 || ly > wy0 + 3 || zlo > zhi) continue;
+                const float4 p0 = sp[4 * j], p1 = sp[4 * j + 1], p2 = sp[4 * j + 2];
+                const int ax = __float_as_int(p2.z), ay = __float_as_int(p2.w);
+                const float dx = (float)(x - ax) - p0.x;
+                const float dy = (float)(y - ay) - p0.y;
+                const bool in = x >= lx && x <= hx && y >= ly && y <= hy;
+                const float a = in ? p0.w * ex2_approx(fmaf(p1.x * dx, dx, p1.y * dy * dy)) : 0.f;
+                const float4 *e4 = reinterpret_cast<const float4 *>(ez[j]);
+#pragma unroll
+                for (int g8 = 0; g8 < SEP_TZ / 8; ++g8) {
+                    if (zhi < g8 * 8 || zlo >= (g8 + 1) * 8) continue;  // warp-uniform
+                    const float4 u = e4[2 * g8], v = e4[2 * g8 + 1];
+                    cs[8 * g8 + 0] = fmaf(a, u.x, cs[8 * g8 + 0]);
+                    cs[8 * g8 + 1] = fmaf(a, u.y, cs[8 * g8 + 1]);
+                    cs[8 * g8 + 2] = fmaf(a, u.z, cs[8 * g8 + 2]);
+                    cs[8 * g8 + 3] = fmaf(a, u.w, cs[8 * g8 + 3]);
+                    cs[8 * g8 + 4] = fmaf(a, v.x, cs[8 * g8 + 4]);
+                    cs[8 * g8 + 5] = fmaf(a, v.y, cs[8 * g8 + 5]);
+                    cs[8 * g8 + 6] = fmaf(a, v.z, cs[8 * g8 + 6]);
+                    cs[8 * g8 + 7] = fmaf(a, v.w, cs[8 * g8 + 7]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SEP_TZ; ++k) {  // Kahan: chunk sum into the running sum
+                const float yv = cs[k] - cmp[k];
+                const float tsum = acc[k] + yv;
+                cmp[k] = (tsum - acc[k]) - yv;
+                acc[k] = tsum;
+            }
+        }
+        if (x < g.nx && y < g.ny) {
+            float *col = I.vol + (size_t)x * I.vsx + (size_t)y * I.vsy;
+            if (I.vsz == 1 && (g.nz & 3) == 0 && z0 + SEP_TZ <= g.nz &&
+                (reinterpret_cast<uintptr_t>(I.vol) & 15) == 0) {
+#pragma unroll
+                for (int k = 0; k < SEP_TZ; k += 4)
+                    *reinterpret_cast<float4 *>(col + z0 + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+            } else {
+                const size_t zs = (size_t)I.vsz;
+#pragma unroll
+                for (int k = 0; k < SEP_TZ; ++k)
+                    if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+            }
+        }
+    }
+}
+
 }  // namespace
 
 static int g_tile_depth = 32;
+static int g_separable = 1;
+void set_separable(int on) { g_separable = on ? 1 : 0; }
 int tile_depth() { return g_tile_depth; }
 void set_tile_depth(int tz) { g_tile_depth = tz; }
 
@@ -440,7 +564,8 @@ cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const fl
 }
 
 cudaError_t launch_prep(const Batch &B, Prep *prep, uint32_t *itemcnt, int *status, cudaStream_t st) {
-    if (B.tot_g == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(status + SEP_FLAG, 0, sizeof(int), st);
+    if (e != cudaSuccess || B.tot_g == 0) return e;
     k_prep<<<(B.tot_g + 127) / 128, 128, 0, st>>>(B, prep, itemcnt, status);
     counted(1);
     return cudaGetLastError();
@@ -469,14 +594,23 @@ cudaError_t launch_count_pairs(const Batch &B, const Prep *prep, dgr_ws *ws, uns
 template <int TZ>
 static cudaError_t launch_vox_tz(const Batch &B, const Prep *prep, const uint32_t *tile_off,
                                  const uint32_t *list, unsigned long long cap, int *queue,
-                                 cudaStream_t st) {
+                                 const int *sep_flag, cudaStream_t st) {
     int dev = 0, sms = 148, per_sm = 8;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxelize<TZ>, VOX_THREADS, 0);
     const int grid = max(1, min(B.tot_tiles, sms * max(per_sm, 1)));
-    k_voxelize<TZ><<<grid, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue);
+    // depth 32: the separable kernel as well; exactly one of the two does the work
+    const bool sep = TZ == SEP_TZ && g_separable;
+    k_voxelize<TZ><<<grid, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep ? sep_flag : nullptr);
     counted(1);
+    if (sep) {
+        int per_sm2 = 4;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_voxelize_sep, VOX_THREADS, 0);
+        const int grid2 = max(1, min(B.tot_tiles, sms * max(per_sm2, 1)));
+        k_voxelize_sep<<<grid2, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep_flag);
+        counted(1);
+    }
     return cudaGetLastError();
 }
 
@@ -502,10 +636,11 @@ cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int de
         counted(1);
     }
     // persistent: enough CTAs to fill every SM, each pulling tiles from the queue
+    const int *sep_flag = ws_ptr<int>(ws, ws->status) + SEP_FLAG;
     switch (B.tz) {
-        case 8: return launch_vox_tz<8>(B, prep, tile_off, list, cap, queue, st);
-        case 16: return launch_vox_tz<16>(B, prep, tile_off, list, cap, queue, st);
-        default: return launch_vox_tz<32>(B, prep, tile_off, list, cap, queue, st);
+        case 8: return launch_vox_tz<8>(B, prep, tile_off, list, cap, queue, sep_flag, st);
+        case 16: return launch_vox_tz<16>(B, prep, tile_off, list, cap, queue, sep_flag, st);
+        default: return launch_vox_tz<32>(B, prep, tile_off, list, cap, queue, sep_flag, st);
     }
 }
 

@@ -2,7 +2,7 @@
 every input already in HBM -- a fixed, small command for profilers.
 
     python -m paper_2411_04844_b300.profile_cases OP [--workload 2] [--reps 3] [--views N]
-        [--backprojector 0|1|2]
+        [--backprojector 0|1|2] [--isotropic] [--no-separable]
 
 OP: voxelize | voxelize_backward | project | backproject | step.
 Workload numbers are those of synth.workload (2: 50,000 Gaussians, 256^3,
@@ -25,8 +25,11 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--views", type=int, default=0)
     ap.add_argument("--backprojector", type=int, default=0, help="0: ray scatter, 1: column gather, 2: brick scatter")
+    ap.add_argument("--isotropic", action="store_true", help="one scale per Gaussian (separable FVR)")
+    ap.add_argument("--no-separable", action="store_true", help="general voxelizer even when separable")
     a = ap.parse_args(argv)
     dgr.dgr_set_backprojector(a.backprojector)
+    dgr.dgr_set_separable(not a.no_separable)
     wl = synth.workload(a.workload)
     geo_spec = wl.geom
     if a.views:
@@ -37,7 +40,7 @@ def main(argv=None):
     grid = dgr.Grid.of(wl.grid)
     ang = T(geo_spec.angles)
     geom = dgr.Geom.of(geo_spec, ang)
-    f = synth.gaussian_field(synth.rng_for(a.workload, 0), wl.n_gauss, wl.grid, wl.scale)
+    f = synth.gaussian_field(synth.rng_for(a.workload, 0), wl.n_gauss, wl.grid, wl.scale, isotropic=a.isotropic)
     f.rho = np.clip(f.rho, 0.02, 1.0).astype(np.float32)
     mu, s, q, rho = T(f.mu), T(f.s), T(f.q), T(f.rho)
     ws0 = dgr.Workspace(dgr.make_plan(grid, f.n))

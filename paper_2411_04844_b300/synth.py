@@ -128,10 +128,11 @@ class Field:
 
 
 def gaussian_field(rng, n, grid: GridSpec, scale=("loguniform", 0.5, 3.0), rho=(0.0, 1.0),
-                   unnormalised_q=False):
+                   unnormalised_q=False, isotropic=False):
     """n Gaussians: centres uniform in the volume, uniform random rotations,
     rho ~ U[rho], per-axis scales (in voxels, times h) from
-    ("loguniform", lo, hi) or ("lognormal", median, sigma_log)."""
+    ("loguniform", lo, hi) or ("lognormal", median, sigma_log); isotropic:
+    one scale per Gaussian for all three axes (the paper's representation)."""
     lo = np.array(grid.org)
     hi = lo + np.array(grid.extent)
     mu = rng.uniform(lo, hi, (n, 3))
@@ -143,6 +144,8 @@ def gaussian_field(rng, n, grid: GridSpec, scale=("loguniform", 0.5, 3.0), rho=(
         s = np.full((n, 3), float(scale[1]))
     else:
         raise ValueError(scale)
+    if isotropic:
+        s = np.repeat(s[:, :1], 3, axis=1)
     s = s * grid.h
     q = random_quaternions(rng, n)
     if unnormalised_q:

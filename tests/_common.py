@@ -28,7 +28,8 @@ def guard_field(field: synth.Field, grid: synth.GridSpec, k=3.0, band=1e-3, rng=
         idx = np.nonzero(bad)[0]
         lo = np.array(grid.org); hi = lo + np.array(grid.extent)
         f.mu[idx] = rng.uniform(lo, hi, (len(idx), 3)).astype(np.float32)
-        f.s[idx] = (f.s[idx] * rng.uniform(0.97, 1.03, (len(idx), 3))).astype(np.float32)
+        # one factor per Gaussian: isotropic Gaussians stay isotropic
+        f.s[idx] = (f.s[idx] * rng.uniform(0.97, 1.03, (len(idx), 1))).astype(np.float32)
     raise RuntimeError("guard band not reached")
 
 
