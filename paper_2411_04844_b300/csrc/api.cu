@@ -215,6 +215,11 @@ int dgr_set_backprojector(int variant) {
     return DGR_OK;
 }
 
+int dgr_set_staged_walk(int on) {
+    set_staged_walk(on);
+    return DGR_OK;
+}
+
 int dgr_set_separable(int on) {
     set_separable(on);
     return DGR_OK;
@@ -448,7 +453,7 @@ int dgr_project(const dgr_grid *grid, const dgr_geom *geom, const float *vol, fl
         I.vsx = grid->ny * grid->nz;
     }
     if (e == cudaSuccess) e = launch_ray_tables(*B, tab, stream);
-    if (e == cudaSuccess) e = launch_project(*B, tab, stream);
+    if (e == cudaSuccess) e = launch_project(*B, tab, ws_ptr<int>(ws, ws->status), stream);
     return cuda_rc(e);
 }
 
@@ -459,7 +464,7 @@ int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sin
     if (rc) return rc;
     RayXY *tab = ws_ptr<RayXY>(ws, ws->rayxy);
     cudaError_t e = launch_ray_tables(*B, tab, stream);
-    if (e == cudaSuccess) e = launch_backproject(*B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, stream);
+    if (e == cudaSuccess) e = launch_backproject(*B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, ws_ptr<int>(ws, ws->status), stream);
     return cuda_rc(e);
 }
 
@@ -578,14 +583,14 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
     if (e == cudaSuccess) e = launch_voxelize(B, prep, ws, g_deterministic, stream);
     if (e == cudaSuccess) e = mark(1);
     if (e == cudaSuccess) e = launch_ray_tables(B, tab, stream);
-    if (e == cudaSuccess) e = launch_project(B, tab, stream);
+    if (e == cudaSuccess) e = launch_project(B, tab, ws_ptr<int>(ws, ws->status), stream);
     if (e == cudaSuccess) e = mark(2);
     float *ssim_g = ws_ptr<float>(ws, ws->ssim_g);
     if (e == cudaSuccess && any_ssim)
         e = launch_ssim(B, ws_ptr<float>(ws, ws->ssim_maps), ws_ptr<float>(ws, ws->ssim_part), ssim_g, stream);
     if (e == cudaSuccess) e = launch_l1(B, ws_ptr<float>(ws, ws->loss_part), any_ssim ? ssim_g : nullptr, stream);
     if (e == cudaSuccess) e = mark(3);
-    if (e == cudaSuccess) e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, stream);
+    if (e == cudaSuccess) e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, ws_ptr<int>(ws, ws->status), stream);
     if (e == cudaSuccess && any_tv) e = launch_tv(B, ws_ptr<float>(ws, ws->tv_part), 1, stream);
     if (e == cudaSuccess)
         e = launch_loss_final(B, ws_ptr<float>(ws, ws->loss_part), L1_BLOCKS, ws_ptr<float>(ws, ws->ssim_part),

@@ -218,43 +218,110 @@ __device__ __forceinline__ float group_step(const Inst &I, const unsigned *view_
     return ldexpf(1.f, min(30 - ex, 126));
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (the Tensor Memory Accelerator's 1D form) through
+// shared memory: a CTA's detector column walks a path of (x, y) cells; with
+// the volume z fastest, the part of a cell's z column its rows can reach is
+// one contiguous run, so per chunk of cells one thread issues a bulk copy per
+// cell (global -> shared, completion counted in bytes on an mbarrier) for the
+// projector, or a bulk reduce-add per cell (shared -> global integer sums)
+// for the backprojector, and the lanes work on shared memory.  Two stages: the
+// next chunk's copies fly while the current one is walked.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g_add(int *dst, const int *src, unsigned bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// a bounded wait: gives up (and flags the status word) instead of spinning forever
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *status) {
+    for (int it = 0; it < (1 << 20); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(status, DGR_STATUS_TIMEOUT);
+    return false;
+}
+
+// where the walk reads (MODE 0) or adds (MODE 1): the global volume / integer
+// sums at cell offset + z (unstaged), or a shared-memory window of each cell's
+// column: [slot][z - zlo] for the segments s0 .. s0 + nslot - 1 (staged)
+struct Stage {
+    int s0, nslot, zspan, zlo, zhi;
+};
+
 // Fast walk for geometries where no ray crosses two z planes inside one
 // (x, y) cell (sqrt(2) max|e_z| / min|e_xy| < 1 with margin; checked on the
 // host): the crossing is a predicated update and the second segment's length
 // is min(tz, t1) - min(tz_before, t1), zero when nothing was crossed.
-template <int MODE, bool MASKZ>
+template <int MODE, bool MASKZ, bool STAGED>
 __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *__restrict__ acci, float wq,
-                                           const Seg *seg, int c0, int c1, int nz, float &t, float &acc,
-                                           int &iz, float &fz, float &tz, int sgz, float xi0z, float iez) {
+                                           const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
+                                           float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
+                                           float xi0z, float iez) {
     const unsigned zmax = (unsigned)(nz - 1);
-    int zc = (int)min((unsigned)iz, zmax);
+    const int zl = STAGED ? G.zlo : 0, zh = STAGED ? G.zhi : nz - 1;
+    int zc = min(max(iz, zl), zh);
     const float fsg = (float)sgz;
-    for (int r = c0; r < c1; r += WALK) {
+    for (int r = r0; r < r1; r += WALK) {
         float l0[WALK], l1[WALK];
         int a0[WALK], a1[WALK];
 #pragma unroll
         for (int j = 0; j < WALK; ++j) {
-            const Seg S = seg[r + j - c0];  // past c1: padding, empty segments
+            const Seg S = seg[r + j - c0];  // past the round's end: padding, empty segments
+            const int base = STAGED ? min(r + j - G.s0, G.nslot - 1) * G.zspan - G.zlo : S.cb;
             const float t1 = S.t1;
             const float m = fminf(tz, t1);
             l0[j] = (!MASKZ || (unsigned)iz <= zmax) ? m - t : 0.f;
-            a0[j] = S.cb + zc;
+            a0[j] = base + zc;
             if (tz < t1) {
                 iz += sgz;
                 fz += fsg;
                 tz = (fz - xi0z) * iez;
-                zc = (int)min((unsigned)iz, zmax);
+                zc = min(max(iz, zl), zh);
             }
             l1[j] = (!MASKZ || (unsigned)iz <= zmax) ? fminf(tz, t1) - m : 0.f;
-            a1[j] = S.cb + zc;
+            a1[j] = base + zc;
             t = t1;
         }
         if (MODE == 0) {
             float v0[WALK], v1[WALK];
 #pragma unroll
             for (int j = 0; j < WALK; ++j) {
-                v0[j] = __ldg(vol + a0[j]);
-                v1[j] = __ldg(vol + a1[j]);
+                v0[j] = STAGED ? vol[a0[j]] : __ldg(vol + a0[j]);
+                v1[j] = STAGED ? vol[a1[j]] : __ldg(vol + a1[j]);
             }
 #pragma unroll
             for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
@@ -273,24 +340,27 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
 
 // MODE 0 (project): acc += length x volume value.  MODE 1 (backproject
 // scatter): the integer sums at the same voxels += round(length x wq).
-template <int MODE, bool MASKZ>
+template <int MODE, bool MASKZ, bool STAGED>
 __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__restrict__ acci, float wq,
-                                          const Seg *seg, int c0, int c1, int nz, float &t, float &acc,
-                                          int &iz, float &fz, float &tz, int sgz, float xi0z, float iez) {
+                                          const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
+                                          float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
+                                          float xi0z, float iez) {
     const unsigned zmax = (unsigned)(nz - 1);
-    int zc = (int)min((unsigned)iz, zmax);
+    const int zl = STAGED ? G.zlo : 0, zh = STAGED ? G.zhi : nz - 1;
+    int zc = min(max(iz, zl), zh);
     const float fsg = (float)sgz;
-    for (int r = c0; r < c1; r += WALK) {
+    for (int r = r0; r < r1; r += WALK) {
         float l0[WALK], l1[WALK];
         int a0[WALK], a1[WALK];
 #pragma unroll
         for (int j = 0; j < WALK; ++j) {
-            const Seg S = seg[r + j - c0];  // past c1: padding, empty segments
+            const Seg S = seg[r + j - c0];  // past the round's end: padding, empty segments
+            const int base = STAGED ? min(r + j - G.s0, G.nslot - 1) * G.zspan - G.zlo : S.cb;
             const float t1 = S.t1;
             const float m = fminf(tz, t1);
             const bool in0 = !MASKZ || (unsigned)iz <= zmax;
             l0[j] = in0 ? m - t : 0.f;
-            a0[j] = S.cb + zc;
+            a0[j] = base + zc;
             l1[j] = 0.f;
             a1[j] = a0[j];
             if (tz < t1) {
@@ -298,10 +368,10 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
                 iz += sgz;
                 fz += fsg;
                 tz = (fz - xi0z) * iez;
-                zc = (int)min((unsigned)iz, zmax);
+                zc = min(max(iz, zl), zh);
                 const bool in1 = !MASKZ || (unsigned)iz <= zmax;
                 l1[j] = in1 ? fminf(tz, t1) - ts : 0.f;
-                a1[j] = S.cb + zc;
+                a1[j] = base + zc;
                 // rare: further z planes inside this cell (bounded: a crossing
                 // that rounding failed to advance cannot spin)
                 for (int rep = 0; rep <= nz && tz < t1; ++rep) {
@@ -309,11 +379,11 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
                     iz += sgz;
                     fz += fsg;
                     tz = (fz - xi0z) * iez;
-                    zc = (int)min((unsigned)iz, zmax);
+                    zc = min(max(iz, zl), zh);
                     if (!MASKZ || (unsigned)iz <= zmax) {
                         const float len = fminf(tz, t1) - ts;
-                        if (MODE == 0) acc = fmaf(len, __ldg(vol + S.cb + zc), acc);
-                        else if (len != 0.f) atomicAdd(acci + S.cb + zc, __float2int_rn(len * wq));
+                        if (MODE == 0) acc = fmaf(len, STAGED ? vol[base + zc] : __ldg(vol + base + zc), acc);
+                        else if (len != 0.f) atomicAdd(acci + base + zc, __float2int_rn(len * wq));
                     }
                 }
             }
@@ -323,8 +393,8 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
             float v0[WALK], v1[WALK];
 #pragma unroll
             for (int j = 0; j < WALK; ++j) {
-                v0[j] = __ldg(vol + a0[j]);
-                v1[j] = __ldg(vol + a1[j]);
+                v0[j] = STAGED ? vol[a0[j]] : __ldg(vol + a0[j]);
+                v1[j] = STAGED ? vol[a1[j]] : __ldg(vol + a1[j]);
             }
 #pragma unroll
             for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
@@ -338,6 +408,25 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
     }
 }
 
+// one walk over segments [r0, r1) of the current round (starting at c0)
+template <int MODE, bool STAGED>
+__device__ __forceinline__ void walk_any(bool multiz, bool masked, const float *vol, int *acci, float wq,
+                                         const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
+                                         float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
+                                         float xi0z, float iez) {
+    if (multiz) {
+        if (masked)
+            walk_segs<MODE, true, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+        else
+            walk_segs<MODE, false, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+    } else {
+        if (masked)
+            walk_segs1<MODE, true, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+        else
+            walk_segs1<MODE, false, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+    }
+}
+
 // MODE 0: a4, the projector.  MODE 1: a6, the ray-driven backprojector for
 // the views [kv0, kv0 + nkv) of every instance: each lane's row adds
 // length x scaled residual, in the fixed point of its view group, into
@@ -345,12 +434,17 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
 // then moves them into the FP32 gradient.  Integer sums do not depend on the
 // order of the additions, so the result is bit-reproducible.
 // blockIdx.x: global block (instance, view of the launch, row group, column).
-template <int MODE>
+template <int MODE, bool TMA>
 __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Batch B,
                                                      RayXY *__restrict__ tab_base,
                                                      const float *__restrict__ sino_s,
                                                      const unsigned *__restrict__ view_max) {
     __shared__ Seg seg[SEG_MAX + WALK];
+    // TMA: two stages of B.tma_ch cell columns of up to B.tma_zcap words each
+    extern __shared__ __align__(128) float cols[];
+    __shared__ unsigned long long bar[2];
+    __shared__ float s_zr[2][PR_THREADS / 32];
+    __shared__ int s_abort;  // a bounded wait gave up: leave the staged walk
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
     int ii = 0;
     while (ii + 1 < B.n && B.in[ii + 1].pb0 <= (int)blockIdx.x) ++ii;
@@ -433,6 +527,47 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
     }
     const bool masked = __any_sync(0xffffffffu, !zin);
     float t = tmin, acc = 0.f;
+    // TMA: the z window every row of this CTA can reach along the whole path
+    Stage G = {0, 1, 4, 0, 3};
+    bool staged = false;
+    if (TMA) {
+        const float za = fmaf(tmin, Z.ez, Z.xi0z), zb = fmaf(tmax, Z.ez, Z.xi0z);
+        float lo = fminf(za, zb), hi = fmaxf(za, zb);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            s_zr[0][w] = lo;
+            s_zr[1][w] = hi;
+        }
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_barrier_init();
+            s_abort = 0;
+        }
+        fence_async_smem();
+        __syncthreads();
+        for (int j = 0; j < PR_THREADS / 32; ++j) {
+            lo = fminf(lo, s_zr[0][j]);
+            hi = fmaxf(hi, s_zr[1][j]);
+        }
+        // one voxel of margin each side, z0 rounded down to 4 words (16-byte copies)
+        const int zlo = (int)fmaxf(fminf(floorf(lo) - 1.f, (float)g.nz), 0.f) & ~3;
+        const int zhi = (int)fminf(fmaxf(floorf(hi) + 1.f, 0.f), (float)(g.nz - 1));
+        const int span = (zhi - zlo + 4) & ~3;
+        staged = span > 0 && span <= B.tma_zcap;  // CTA-uniform
+        G.zlo = zlo;
+        G.zspan = max(span, 4);
+        G.zhi = zlo + G.zspan - 1;
+        if (MODE == 1 && staged) {
+            for (int i = threadIdx.x; i < 2 * B.tma_ch * B.tma_zcap; i += PR_THREADS) cols[i] = 0.f;
+            __syncthreads();
+        }
+    }
+    int use = 0;  // sub-chunks processed (stage = use & 1, phase = (use >> 1) & 1)
     for (int c0 = 0; c0 < nseg; c0 += SEG_MAX) {
         const int c1 = min(nseg, c0 + SEG_MAX);
         __syncthreads();  // the previous round's readers are done
@@ -462,22 +597,64 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
             seg[c1 - c0 + threadIdx.x] = last;
         }
         __syncthreads();
-        if (I.multiz) {
-            if (masked)
-                walk_segs<MODE, true>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
-                                      Z.xi0z, Z.inv_ez);
-            else
-                walk_segs<MODE, false>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
-                                       Z.xi0z, Z.inv_ez);
-        } else {
-            if (masked)
-                walk_segs1<MODE, true>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
-                                       Z.xi0z, Z.inv_ez);
-            else
-                walk_segs1<MODE, false>(I.vol, I.acc, wq, seg, c0, c1, g.nz, t, acc, iz, fz, tz, sgz,
-                                        Z.xi0z, Z.inv_ez);
+        if (!TMA || !staged) {
+            walk_any<MODE, false>(I.multiz, masked, I.vol, I.acc, wq, seg, c0, c0, c1, g.nz, G, t, acc, iz,
+                                  fz, tz, sgz, Z.xi0z, Z.inv_ez);
+            continue;
         }
+        // staged: sub-chunks of tma_ch cells, their z windows in shared memory
+        const int CH = B.tma_ch, ZC = B.tma_zcap;
+        const int nsub = (c1 - c0 + CH - 1) / CH;
+        const unsigned bytes = (unsigned)G.zspan * 4u;
+        auto issue = [&](int sc, int stg) {  // thread 0: bulk copies of sub-chunk sc into stage stg
+            const int s0 = c0 + sc * CH, n = min(CH, c1 - s0);
+            mbar_expect_tx(&bar[stg], bytes * (unsigned)n);
+            for (int j = 0; j < n; ++j)
+                bulk_g2s(cols + (size_t)(stg * CH + j) * ZC, I.vol + seg[s0 + j - c0].cb + G.zlo, bytes, &bar[stg]);
+        };
+        if (MODE == 0 && threadIdx.x == 0) issue(0, use & 1);
+        for (int sc = 0; sc < nsub; ++sc, ++use) {
+            const int stg = use & 1;
+            Stage Gs = G;
+            Gs.s0 = c0 + sc * CH;
+            Gs.nslot = min(CH, c1 - Gs.s0);
+            const int r1 = Gs.s0 + Gs.nslot;
+            float *col = cols + (size_t)stg * CH * ZC;
+            if (MODE == 0) {
+                if (threadIdx.x == 0 && sc + 1 < nsub) issue(sc + 1, stg ^ 1);
+                if (!mbar_wait(&bar[stg], (use >> 1) & 1, B.status)) s_abort = 1;
+                Gs.zspan = ZC;  // slots are ZC words apart
+                Gs.zlo = G.zlo;
+                walk_any<MODE, true>(I.multiz, masked, col, nullptr, wq, seg, c0, Gs.s0, r1, g.nz, Gs, t, acc,
+                                     iz, fz, tz, sgz, Z.xi0z, Z.inv_ez);
+                __syncthreads();  // this stage may be refilled
+                if (s_abort) {
+                    // let the copies already in flight land before leaving (bounded)
+                    if (threadIdx.x == 0 && sc + 1 < nsub) mbar_wait(&bar[stg ^ 1], ((use + 1) >> 1) & 1, B.status);
+                    break;
+                }
+            } else {
+                Gs.zspan = ZC;
+                walk_any<MODE, true>(I.multiz, masked, nullptr, reinterpret_cast<int *>(col), wq, seg, c0,
+                                     Gs.s0, r1, g.nz, Gs, t, acc, iz, fz, tz, sgz, Z.xi0z, Z.inv_ez);
+                fence_async_smem();  // each thread's shared atomics, before the bulk reads
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int j = 0; j < Gs.nslot; ++j)
+                        bulk_s2g_add(I.acc + seg[Gs.s0 + j - c0].cb + G.zlo,
+                                     reinterpret_cast<const int *>(col) + (size_t)j * ZC, bytes);
+                    bulk_commit();
+                    bulk_wait_read1();  // the other stage's adds have read their source
+                }
+                __syncthreads();
+                float *other = cols + (size_t)(stg ^ 1) * CH * ZC;
+                for (int i = threadIdx.x; i < CH * ZC; i += PR_THREADS) other[i] = 0.f;
+                __syncthreads();
+            }
+        }
+        if (TMA && s_abort) break;
     }
+    if (TMA && MODE == 1 && staged && threadIdx.x == 0) bulk_wait_all();
     if (MODE == 0 && iv < I.nv) I.sino[ray] = acc * ray_norm(R, row, I.beam);
 }
 
@@ -1147,7 +1324,41 @@ cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const Batch &B0, const RayXY *tab, cudaStream_t st) {
+static int g_staged = 0;  // measured slower than the direct walk (see the header)
+void set_staged_walk(int on) { g_staged = on ? 1 : 0; }
+
+// The staged (bulk-copy) path walk: every volume z fastest with nz a multiple
+// of 4 (16-byte copies), columns of at most 4096 words.  Sets the batch's
+// stage geometry; returns the dynamic shared memory (0: unstaged walk).
+static int staging(Batch &B, int *status) {
+    if (!g_staged || !status) return 0;
+    int zc = 4;
+    for (int i = 0; i < B.n; ++i) {
+        const dgr_grid &g = B.in[i].g;
+        if (B.in[i].vsz != 1 || (g.nz & 3) != 0) return 0;
+        zc = max(zc, g.nz);
+    }
+    if (zc > 4096) return 0;
+    const int ch = max(4, min(32, 32768 / (2 * zc * 4)));
+    B.tma_ch = ch;
+    B.tma_zcap = zc;
+    B.status = status;
+    const int smem = 2 * ch * zc * (int)sizeof(float);  // at most 2 x 4 x 4096 words
+    static int attr = 0;  // 0: not tried, 1: set, -1: refused (stay unstaged above 48 KB)
+    if (attr == 0) {
+        const int most = 2 * 4 * 4096 * (int)sizeof(float);
+        const bool ok = cudaFuncSetAttribute(k_path<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
+                            cudaSuccess &&
+                        cudaFuncSetAttribute(k_path<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
+                            cudaSuccess;
+        if (!ok) cudaGetLastError();  // clear it: the launch below stays within the default
+        attr = ok ? 1 : -1;
+    }
+    if (attr < 0 && smem > 48 * 1024) return 0;
+    return smem;
+}
+
+cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaStream_t st) {
     // row-warp projector when every volume is z fastest, else per-ray
     bool zfast = B0.n > 0;
     for (int i = 0; i < B0.n; ++i) zfast = zfast && B0.in[i].vsz == 1;
@@ -1171,7 +1382,11 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, cudaStream_t st) {
         pb += I.n_views * I.nu * I.npv;
     }
     if (pb == 0) return cudaSuccess;
-    k_path<0><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
+    const int smem = staging(B, status);
+    if (smem > 0)
+        k_path<0, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
+    else
+        k_path<0, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     counted(1);
     return cudaGetLastError();
 }
@@ -1185,7 +1400,7 @@ cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cu
 
 // ray-driven backprojector: per group of VGROUP views, the scatter and the fold
 static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const float *sino_scaled,
-                                     const unsigned *view_max, int *acc, cudaStream_t st) {
+                                     const unsigned *view_max, int *acc, int *status, cudaStream_t st) {
     static thread_local Batch B;
     B = B0;
     int ngroups = 0;
@@ -1212,7 +1427,11 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
             if (I.nkv > 0) fb += ((I.g.nx + 31) / 32) * I.g.ny * ((I.g.nz + 31) / 32);
         }
         if (pb > 0) {
-            k_path<1><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
+            const int smem = staging(B, status);
+            if (smem > 0)
+                k_path<1, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
+            else
+                k_path<1, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
             counted(1);
         }
         if (fb > 0) {
@@ -1224,7 +1443,7 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
 }
 
 cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, int *acc,
-                               long long acc_vox, cudaStream_t st) {
+                               long long acc_vox, int *status, cudaStream_t st) {
     long long vox = 0;
     for (int i = 0; i < B.n; ++i) vox += (long long)B.in[i].g.nx * B.in[i].g.ny * B.in[i].g.nz;
     // the ray scatter (0) needs the workspace's integer sums; without them, the brick scatter (2)
@@ -1238,7 +1457,7 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
         k_scale_dn<<<dim3((max_per + 255) / 256, B.tot_views), 256, 0, st>>>(B, const_cast<RayXY *>(tab),
                                                                            sino_scaled, view_max);
         counted(1);
-        if (variant == 0) return launch_bp_scatter(B, tab, sino_scaled, view_max, acc, st);
+        if (variant == 0) return launch_bp_scatter(B, tab, sino_scaled, view_max, acc, status, st);
         const int smem = 2 * BBV * (int)sizeof(float);
         static bool attr = false;
         if (!attr) {
@@ -1287,7 +1506,7 @@ cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY 
     B.tot_rows = geo.nv;
     B.tot_rays = (long long)geo.n_views * geo.nu * geo.nv;
     cudaError_t e = launch_ray_tables(B, tab, st);
-    if (e == cudaSuccess) e = launch_project(B, tab, st);
+    if (e == cudaSuccess) e = launch_project(B, tab, nullptr, st);
     return e;
 }
 

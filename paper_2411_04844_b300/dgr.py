@@ -37,7 +37,7 @@ EXPORTS = [
     "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth", "dgr_set_backprojector",
     "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
     "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
-    "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss", "dgr_densify", "dgr_set_separable",
+    "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss", "dgr_densify", "dgr_set_separable", "dgr_set_staged_walk",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -139,6 +139,7 @@ def lib():
             "dgr_set_deterministic": [i],
             "dgr_set_tile_depth": [i],
             "dgr_set_separable": [i],
+            "dgr_set_staged_walk": [i],
             "dgr_set_backprojector": [i],
             "dgr_footprint": [ctypes.POINTER(Grid), i, P, P, P, f, P, P, P],
             "dgr_voxelize_count": [ctypes.POINTER(Grid), i, P, P, P, f, ctypes.POINTER(ll),
@@ -282,6 +283,11 @@ def dgr_set_backprojector(variant: int):
 def dgr_set_separable(on: bool):
     """Separable voxelizer for all-diagonal-A calls (default on)."""
     _rc(lib().dgr_set_separable(1 if on else 0), "dgr_set_separable")
+
+
+def dgr_set_staged_walk(on: bool):
+    """Bulk-copy staging of the path walks through shared memory (default off)."""
+    _rc(lib().dgr_set_staged_walk(1 if on else 0), "dgr_set_staged_walk")
 
 
 def dgr_set_tile_depth(tz: int):

@@ -2,7 +2,7 @@
 every input already in HBM -- a fixed, small command for profilers.
 
     python -m paper_2411_04844_b300.profile_cases OP [--workload 2] [--reps 3] [--views N]
-        [--backprojector 0|1|2] [--isotropic] [--no-separable]
+        [--backprojector 0|1|2] [--isotropic] [--no-separable] [--unstaged]
 
 OP: voxelize | voxelize_backward | project | backproject | step.
 Workload numbers are those of synth.workload (2: 50,000 Gaussians, 256^3,
@@ -27,9 +27,11 @@ def main(argv=None):
     ap.add_argument("--backprojector", type=int, default=0, help="0: ray scatter, 1: column gather, 2: brick scatter")
     ap.add_argument("--isotropic", action="store_true", help="one scale per Gaussian (separable FVR)")
     ap.add_argument("--no-separable", action="store_true", help="general voxelizer even when separable")
+    ap.add_argument("--unstaged", action="store_true", help="path walks without shared-memory staging")
     a = ap.parse_args(argv)
     dgr.dgr_set_backprojector(a.backprojector)
     dgr.dgr_set_separable(not a.no_separable)
+    dgr.dgr_set_staged_walk(not a.unstaged)
     wl = synth.workload(a.workload)
     geo_spec = wl.geom
     if a.views:
