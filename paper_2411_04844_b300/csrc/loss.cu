@@ -189,20 +189,21 @@ __global__ void __launch_bounds__(S_THREADS) k_ssim_grad(const __grid_constant__
     }
 }
 
-// TV: tile of 32 (x) x 1 (y) x 32 (z) voxels with a one-voxel halo in x, y, z
-constexpr int TVX = 32, TVZ = 32;
+// TV: tile of 32 (x) x TVY (y) x TVZ (z) voxels; the volume with a one-voxel
+// halo in x, y and z goes through shared memory once (rows y-1 .. y+TVY), so
+// each voxel is read about (TVY + 2) / TVY times
+constexpr int TVX = 32, TVY = 8, TVZ = 16;
 __global__ void __launch_bounds__(256) k_tv(const __grid_constant__ Batch B, float *__restrict__ tpart,
                                             int accumulate) {
-    __shared__ float s[3][TVZ + 2][TVX + 3];
+    __shared__ float s[TVY + 2][TVZ + 2][TVX + 3];
     const Inst &I = B.in[inst_of_tv(B, blockIdx.x)];
     const dgr_grid &g = I.g;
-    const int ntx = (g.nx + TVX - 1) / TVX;
+    const int ntx = (g.nx + TVX - 1) / TVX, nty = (g.ny + TVY - 1) / TVY;
     const int b = blockIdx.x - I.tv0;
-    const int bx = b % ntx, y = (b / ntx) % g.ny, bzt = b / (ntx * g.ny);
-    const int x0 = bx * TVX, z0 = bzt * TVZ;
+    const int x0 = (b % ntx) * TVX, y0 = ((b / ntx) % nty) * TVY, z0 = (b / (ntx * nty)) * TVZ;
     const bool zfast = I.vsz == 1;
-    // load V[x0-1 .. x0+32][y-1 .. y+1][z0-1 .. z0+32] (zero outside)
-    const int nl = 3 * (TVZ + 2) * (TVX + 2);
+    // load V[x0-1 .. x0+32][y0-1 .. y0+TVY][z0-1 .. z0+TVZ] (zero outside)
+    const int nl = (TVY + 2) * (TVZ + 2) * (TVX + 2);
     for (int e = threadIdx.x; e < nl; e += 256) {
         int dy, zz, xx;
         if (zfast) {  // consecutive threads along z
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(256) k_tv(const __grid_constant__ Batch B, flo
         } else {      // consecutive threads along x
             xx = e % (TVX + 2); zz = (e / (TVX + 2)) % (TVZ + 2); dy = e / ((TVZ + 2) * (TVX + 2));
         }
-        const int x = x0 + xx - 1, yy = y + dy - 1, z = z0 + zz - 1;
+        const int x = x0 + xx - 1, yy = y0 + dy - 1, z = z0 + zz - 1;
         float v = 0.f;
         if (x >= 0 && x < g.nx && yy >= 0 && yy < g.ny && z >= 0 && z < g.nz)
             v = I.vol[(size_t)x * I.vsx + (size_t)yy * I.vsy + (size_t)z * I.vsz];
@@ -218,21 +219,22 @@ __global__ void __launch_bounds__(256) k_tv(const __grid_constant__ Batch B, flo
     }
     __syncthreads();
     const float w = I.w_tv / (float)((double)g.nx * g.ny * g.nz);
-    const int xx = threadIdx.x & 31, zr = threadIdx.x >> 5;  // 32 x 8
-    float acc = 0.f;
+    const int xx = threadIdx.x & 31, r8 = threadIdx.x >> 5;  // 32 x 8
     const int x = x0 + xx;
-    for (int zz = zr; zz < TVZ; zz += 8) {
-        const int z = z0 + zz;
-        if (x >= g.nx || z >= g.nz) continue;
-        const float c = s[1][zz + 1][xx + 1];
+    float acc = 0.f;
+    for (int e = r8; e < TVY * TVZ; e += 8) {
+        const int yy = e / TVZ, zz = e % TVZ;
+        const int y = y0 + yy, z = z0 + zz;
+        if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
+        const float c = s[yy + 1][zz + 1][xx + 1];
         float grad = 0.f;
         // forward differences (the term) and the two differences each voxel is in
-        if (x + 1 < g.nx) { const float d = s[1][zz + 1][xx + 2] - c; acc += fabsf(d); grad -= (d > 0.f) - (d < 0.f); }
-        if (x > 0) { const float d = c - s[1][zz + 1][xx]; grad += (d > 0.f) - (d < 0.f); }
-        if (y + 1 < g.ny) { const float d = s[2][zz + 1][xx + 1] - c; acc += fabsf(d); grad -= (d > 0.f) - (d < 0.f); }
-        if (y > 0) { const float d = c - s[0][zz + 1][xx + 1]; grad += (d > 0.f) - (d < 0.f); }
-        if (z + 1 < g.nz) { const float d = s[1][zz + 2][xx + 1] - c; acc += fabsf(d); grad -= (d > 0.f) - (d < 0.f); }
-        if (z > 0) { const float d = c - s[1][zz][xx + 1]; grad += (d > 0.f) - (d < 0.f); }
+        if (x + 1 < g.nx) { const float d = s[yy + 1][zz + 1][xx + 2] - c; acc += fabsf(d); grad -= (d > 0.f) - (d < 0.f); }
+        if (x > 0) { const float d = c - s[yy + 1][zz + 1][xx]; grad += (d > 0.f) - (d < 0.f); }
+        if (y + 1 < g.ny) { const float d = s[yy + 2][zz + 1][xx + 1] - c; acc += fabsf(d); grad -= (d > 0.f) - (d < 0.f); }
+        if (y > 0) { const float d = c - s[yy][zz + 1][xx + 1]; grad += (d > 0.f) - (d < 0.f); }
+        if (z + 1 < g.nz) { const float d = s[yy + 1][zz + 2][xx + 1] - c; acc += fabsf(d); grad -= (d > 0.f) - (d < 0.f); }
+        if (z > 0) { const float d = c - s[yy + 1][zz][xx + 1]; grad += (d > 0.f) - (d < 0.f); }
         float *o = I.gvol + ((size_t)z * g.ny + y) * g.nx + x;
         *o = accumulate ? fmaf(w, grad, *o) : w * grad;
     }
@@ -290,7 +292,9 @@ void loss_tiles(Batch &B) {
         I.nst = I.w_ssim != 0.f ? I.n_views * ((I.nu + STX - 1) / STX) * ((I.nv + STY - 1) / STY) : 0;
         st += I.nst;
         I.tv0 = tv;
-        I.ntv = I.w_tv != 0.f ? ((I.g.nx + TVX - 1) / TVX) * I.g.ny * ((I.g.nz + TVZ - 1) / TVZ) : 0;
+        I.ntv = I.w_tv != 0.f
+                    ? ((I.g.nx + TVX - 1) / TVX) * ((I.g.ny + TVY - 1) / TVY) * ((I.g.nz + TVZ - 1) / TVZ)
+                    : 0;
         tv += I.ntv;
     }
     B.tot_st = st;
@@ -302,8 +306,8 @@ size_t ssim_tiles_cap(long long max_views, int max_nu, int max_nv, int ninst) {
     return (size_t)max_views * ((max_nu + STX - 1) / STX) * ((max_nv + STY - 1) / STY) + ninst;
 }
 size_t tv_tiles_cap(long long max_vox, int ninst) {
-    // a tile holds up to 32 x 32 voxels of one y row; grids thinner than
-    // 8 voxels in x times z need more tiles than this and are refused
+    // a tile holds up to 32 x 8 x 16 voxels; thin grids (fewer than 8 voxels
+    // in x times y times z per tile) need more tiles than this and are refused
     return (size_t)(max_vox / 8) + (size_t)4096 * ninst;
 }
 

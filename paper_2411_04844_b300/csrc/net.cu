@@ -12,16 +12,20 @@
 // pool: 2^3 average; up: 2^3 nearest.  Activations are BF16, channels-last
 // ([z][y][x][c]); every convolution accumulates in FP32.
 //
-// The tensor-core convolutions are implicit GEMMs on mma.sync m16n8k16 (BF16
-// operands, FP32 accumulators) with operands gathered into shared memory:
+// The tensor-core convolutions are implicit GEMMs (BF16 operands, FP32
+// accumulators):
 //   forward      C[p][co] = sum_{tap,ci} X[p + tap][ci] W[tap][ci][co]
 //   data grad    C[p][ci] = sum_{tap,co} G[p - tap][co] W[tap][ci][co]
 //   weight grad  C[tap*Ci + ci][co] = sum_p X[p + tap][ci] G[p][co]
 //                (split over voxel ranges; partials summed in a fixed order)
+// Forward and data gradient run on tcgen05 (k_conv_halo by default,
+// k_conv_umma, or k_conv_gemm on mma.sync m16n8k16 by dgr_set_conv_engine);
+// the weight gradient on mma.sync (k_conv_gemm).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
 
+#include "async_ops.cuh"
 #include "dgr_internal.cuh"
 
 namespace dgr {
@@ -47,6 +51,8 @@ struct ConvArgs {
     const bf16 *g;    // WGRAD: output grads [n^3][co]
     bf16 *y;          // FWD: output [n^3][co]
     float *out;       // DGRAD: [n^3][ci] FP32; WGRAD: partials [splits][27*ci][co]
+    const bf16 *wt;   // tcgen05 FWD / DGRAD: the weights as B, K-major [N][K]
+    int *status;      // device status word (bounded waits)
 };
 
 __device__ __forceinline__ void tap_offset(int tap, int &dx, int &dy, int &dz) {
@@ -190,6 +196,315 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_conv_gemm(const ConvArgs a) {
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same forward and data-gradient GEMMs on the fifth-generation tensor
+// cores (tcgen05).  A CTA of four warps owns UM = 128 rows (voxels) and all
+// BN columns; the FP32 accumulator D[128][BN] lives in tensor memory (row i in
+// lane i).  K runs in stages of UK = 64 through two shared-memory buffers:
+// every thread gathers its own row of A (eight 16-byte chunks; a chunk is 8
+// channels of one tap, since C is a multiple of 8) and a share of B from the
+// packed K-major weights, then one thread issues UK / 16 MMAs of
+// 128 x BN x 16 and commits them to the buffer's mbarrier, which frees the
+// buffer for the stage after next.  Operands use the no-swizzle K-major
+// layout: core matrix (8 rows x 16 bytes) (g, c) of a row group g and K chunk
+// c at byte (g UK / 8 + c) 128, so K-adjacent core matrices are 128 bytes
+// apart and M-adjacent ones UK / 8 x 128.
+// ---------------------------------------------------------------------------
+constexpr int UM = 128, UK = 64;
+
+__host__ __device__ constexpr int umma_cols(int bn) { return bn <= 32 ? 32 : bn; }
+__host__ __device__ constexpr size_t umma_smem(int bn) {
+    return 1024 + 2 * (size_t)UM * UK * 2 + 2 * (size_t)bn * UK * 2 + 64;
+}
+
+// 16 consecutive accumulator columns c0 .. c0 + 15 of output row `row`:
+// forward relu(v + bias (+ skip)) to BF16, data gradient FP32 as is
+template <int MODE>
+__device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int c0, float *v) {
+    if (MODE == MODE_FWD) {
+        if (a.skip) {
+            const uint4 *sp = reinterpret_cast<const uint4 *>(a.skip + row * a.co + c0);
+            const uint4 s0 = sp[0], s1 = sp[1];
+            const uint32_t su[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                __nv_bfloat162 h;
+                memcpy(&h, &su[i], 4);
+                const float2 f = __bfloat1622float2(h);
+                v[2 * i] += f.x;
+                v[2 * i + 1] += f.y;
+            }
+        }
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[2 * i] + a.bias[c0 + 2 * i], 0.f),
+                                                           fmaxf(v[2 * i + 1] + a.bias[c0 + 2 * i + 1], 0.f));
+            memcpy(&pk[i], &h, 4);
+        }
+        uint4 *yp = reinterpret_cast<uint4 *>(a.y + row * a.co + c0);
+        yp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        yp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    } else {
+        float4 *op = reinterpret_cast<float4 *>(a.out + row * a.ci + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) op[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+}
+
+template <int MODE, int BN>
+__global__ void __launch_bounds__(128) k_conv_umma(const ConvArgs a) {
+    static_assert(MODE == MODE_FWD || MODE == MODE_DGRAD, "forward and data gradient only");
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 64, "M = 128 needs N a multiple of 16");
+    constexpr unsigned NCOL = umma_cols(BN);
+    constexpr int ABYTES = UM * UK * 2, BBYTES = BN * UK * 2;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned char *As = sm, *Bs = sm + 2 * ABYTES;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm + 2 * ABYTES + 2 * BBYTES);
+    unsigned *tslot = reinterpret_cast<unsigned *>(bar + 2);
+
+    const int n = a.n, n3 = n * n * n;
+    const int C = MODE == MODE_FWD ? a.ci : a.co;
+    const int K = 27 * C;
+    const int w = threadIdx.x >> 5;
+    if (w == 0) {
+        tmem_alloc(tslot, NCOL);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tslot;
+
+    // this thread's row of A: voxel m
+    const int r = threadIdx.x, m = blockIdx.x * UM + r;
+    const bool mv = m < n3;
+    const int px = m % n, py = (m / n) % n, pz = m / (n * n);
+    const int nk = (K + UK - 1) / UK;
+    constexpr unsigned IDESC = idesc_bf16_f32(UM, BN);
+    int issued = -1;  // last stage whose MMAs were committed
+    bool ok = true;
+    for (int ks = 0; ks < nk; ++ks) {
+        const int s = ks & 1;
+        // the MMAs of stage ks - 2 read this buffer
+        if (ks >= 2 && !mbar_wait(&bar[s], ((ks >> 1) - 1) & 1, a.status)) ok = false;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        unsigned char *A = As + s * ABYTES, *Bm = Bs + s * BBYTES;
+        const int k0 = ks * UK;
+#pragma unroll
+        for (int c = 0; c < UK / 8; ++c) {
+            const int k = k0 + 8 * c;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (mv && k < K) {
+                const int tap = k / C, ch = k - tap * C;
+                int dx, dy, dz;
+                tap_offset(tap, dx, dy, dz);
+                if (MODE == MODE_DGRAD) { dx = -dx; dy = -dy; dz = -dz; }
+                const int qx = px + dx, qy = py + dy, qz = pz + dz;
+                if (qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n)
+                    v = *reinterpret_cast<const uint4 *>(a.x + ((size_t)(qz * n + qy) * n + qx) * C + ch);
+            }
+            *reinterpret_cast<uint4 *>(A + ((r >> 3) * (UK / 8) + c) * 128 + (r & 7) * 16) = v;
+        }
+        for (int e = threadIdx.x; e < BN * (UK / 8); e += 128) {
+            const int nn = e % BN, c = e / BN, k = k0 + 8 * c;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (k < K) v = *reinterpret_cast<const uint4 *>(a.wt + (size_t)nn * K + k);
+            *reinterpret_cast<uint4 *>(Bm + ((nn >> 3) * (UK / 8) + c) * 128 + (nn & 7) * 16) = v;
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const unsigned ab = smem_u32(A), bb = smem_u32(Bm);
+#pragma unroll
+            for (int kk = 0; kk < UK / 16; ++kk)
+                umma_bf16(tmem, smem_desc(ab + kk * 256, 128, (UK / 8) * 128),
+                          smem_desc(bb + kk * 256, 128, (UK / 8) * 128), IDESC, (ks | kk) != 0);
+            umma_commit(&bar[s]);
+        }
+        issued = ks;
+    }
+    // the last commit arrives once every MMA of the tile has completed
+    if (issued >= 0 && !mbar_wait(&bar[issued & 1], (issued >> 1) & 1, a.status)) ok = false;
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    if (ok && issued == nk - 1) {
+        const int row = blockIdx.x * UM + 32 * w + (threadIdx.x & 31);
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((unsigned)(32 * w) << 16) + (unsigned)c0, v);
+            if (row >= n3) continue;
+            store_row16<MODE>(a, (size_t)row, c0, v);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, NCOL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Halo-tile form of the same convolutions on tcgen05: no im2col at all.  A
+// CTA loads the input block of an output tile of 8 (x) x 16 (y) x ZT (z)
+// voxels plus a one-voxel halo (10 x 18 x (ZT + 2) voxels, C channels) into
+// shared memory once, and every tap's A operand is a descriptor into that
+// block: with 16-byte channel chunks stored x-contiguous, eight consecutive x
+// voxels of one (y, z) line are a core matrix (rows 16 bytes apart) starting
+// at any x, the 16 lines of the tile are M-adjacent core matrices (one line,
+// 160 bytes, apart) and the next channel chunk is K-adjacent (one chunk plane
+// apart).  Shifting by a tap (dx, dy, dz) moves the start address only.  The
+// whole packed weight matrix B [N][27 C] sits in shared memory for the CTA's
+// lifetime; per output slice z one FP32 accumulator of 128 x N in tensor
+// memory; per tile 27 ZT C / 16 MMAs from one thread, then one commit.
+// The CTA walks tiles (persistent); the halo block is rewritten only after
+// the tile's commit has arrived.
+// ---------------------------------------------------------------------------
+template <int C, int N, int ZT>
+struct Halo {
+    static constexpr int HX = 10, HY = 18, HZ = ZT + 2;
+    static constexpr int CH = C / 8;  // 16-byte chunks per voxel
+    // chunk-plane pitch in 16-byte slots, padded to (8 / CH) mod 8 so the CH
+    // chunks of the 8 / CH voxels that 8 lanes store together fall in
+    // different 16-byte bank slots
+    static constexpr unsigned BASE16 = (unsigned)HX * HY * HZ;
+    static constexpr unsigned PLANE = 16u * (BASE16 + (8u + (unsigned)(8 / CH) - BASE16 % 8u) % 8u);
+    static constexpr unsigned HBYTES = PLANE * CH;
+    static constexpr unsigned BLEAD = (unsigned)N * 16;  // K-chunk pitch of B
+    static constexpr unsigned BBYTES = (unsigned)27 * CH * BLEAD;
+    static constexpr unsigned NCOL = ZT * N <= 32 ? 32 : (ZT * N <= 64 ? 64 : (ZT * N <= 128 ? 128 : 256));
+    static constexpr size_t SMEM = 1024 + (size_t)BBYTES + HBYTES + 64;
+    static_assert(ZT * N <= 256, "accumulators exceed the tensor-memory allocation");
+    static_assert(PLANE % 16 == 0 && (PLANE >> 4) < 16384, "descriptor field");
+};
+
+template <int MODE, int C, int N, int ZT>
+__global__ void __launch_bounds__(128) k_conv_halo(const ConvArgs a) {
+    static_assert(MODE == MODE_FWD || MODE == MODE_DGRAD, "forward and data gradient only");
+    static_assert(N % 16 == 0 && N >= 16 && N <= 64 && C % 16 == 0, "tile shapes");
+    using H = Halo<C, N, ZT>;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned char *Bs = sm, *Hs = sm + H::BBYTES;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(Hs + H::HBYTES);
+    unsigned *tslot = reinterpret_cast<unsigned *>(bar + 1);
+
+    const int n = a.n;
+    const int w = threadIdx.x >> 5;
+    if (w == 0) {
+        tmem_alloc(tslot, H::NCOL);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    // B: the packed weights [N][27 C] (K-major rows) as core matrices
+    // (n group g, K chunk kc) at kc BLEAD + g 128
+    for (int e = threadIdx.x; e < N * 27 * H::CH; e += 128) {
+        const int nn = e % N, kc = e / N;
+        const uint4 v = *reinterpret_cast<const uint4 *>(a.wt + (size_t)nn * 27 * C + 8 * kc);
+        *reinterpret_cast<uint4 *>(Bs + kc * H::BLEAD + (nn >> 3) * 128 + (nn & 7) * 16) = v;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tslot;
+    const unsigned hs = smem_u32(Hs), bs = smem_u32(Bs);
+    constexpr unsigned IDESC = idesc_bf16_f32(128, N);
+
+    const int ntx = (n + 7) / 8, nty = (n + 15) / 16, ntz = (n + ZT - 1) / ZT;
+    const int ntiles = ntx * nty * ntz;
+    bool ok = true;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int x0 = (tile % ntx) * 8, y0 = ((tile / ntx) % nty) * 16, z0 = (tile / (ntx * nty)) * ZT;
+        // the input block x0-1 .. x0+8, y0-1 .. y0+16, z0-1 .. z0+ZT (zero outside)
+        for (int e = threadIdx.x; e < H::HX * H::HY * H::HZ * H::CH; e += 128) {
+            const int c = e % H::CH, v = e / H::CH;
+            const int xx = v % H::HX, yy = (v / H::HX) % H::HY, zz = v / (H::HX * H::HY);
+            const int qx = x0 + xx - 1, qy = y0 + yy - 1, qz = z0 + zz - 1;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n)
+                val = *reinterpret_cast<const uint4 *>(a.x + ((size_t)(qz * n + qy) * n + qx) * C + 8 * c);
+            *reinterpret_cast<uint4 *>(Hs + c * H::PLANE + ((zz * H::HY + yy) * H::HX + xx) * 16) = val;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            for (int zs = 0; zs < ZT; ++zs) {
+                for (int tap = 0; tap < 27; ++tap) {
+                    int dx, dy, dz;
+                    tap_offset(tap, dx, dy, dz);
+                    if (MODE == MODE_DGRAD) { dx = -dx; dy = -dy; dz = -dz; }
+                    const unsigned a0 = hs + (unsigned)(((zs + 1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx) * 16;
+#pragma unroll
+                    for (int cp = 0; cp < H::CH; cp += 2)
+                        umma_bf16(tmem + (unsigned)(zs * N),
+                                  smem_desc(a0 + cp * H::PLANE, H::PLANE, H::HX * 16),
+                                  smem_desc(bs + (tap * H::CH + cp) * H::BLEAD, H::BLEAD, 128), IDESC,
+                                  (tap | cp) != 0);
+                }
+            }
+            umma_commit(bar);
+        }
+        if (!mbar_wait(bar, it & 1, a.status)) ok = false;
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        tc_fence_after();
+        // epilogue: thread of row m = 32 w + lane holds voxel (x0 + m % 8, y0 + m / 8)
+        const int m = 32 * w + (threadIdx.x & 31);
+        const int x = x0 + (m & 7), y = y0 + (m >> 3);
+        for (int zs = 0; zs < ZT; ++zs) {
+            const int z = z0 + zs;
+            const bool inside = x < n && y < n && z < n;
+            const size_t row = ((size_t)z * n + y) * n + x;
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((unsigned)(32 * w) << 16) + (unsigned)(zs * N + c0), v);
+                if (!inside) continue;
+                store_row16<MODE>(a, row, c0, v);
+            }
+        }
+        // every thread's tensor-memory reads are complete (tmem_ld16 waits)
+        // before the next tile's first MMA overwrites the accumulators
+        tc_fence_before();
+    }
+    // after a wait gave up: let the MMAs in flight finish (bounded) before
+    // the tensor memory is freed
+    if (!ok && threadIdx.x == 0) mbar_wait(bar, it & 1, a.status);
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, H::NCOL);
+    }
+}
+
+// the weights [27][ci][co] as the B operand of the tcgen05 GEMMs, K-major:
+//   forward       wt[co][tap ci + ch] = w[tap][ch][co]
+//   data gradient wt[ci][tap co + ch] = w[tap][ci][ch]
+__global__ void k_wpack(int mode, int ci, int co, const bf16 *__restrict__ w, bf16 *__restrict__ wt) {
+    const int C = mode == MODE_FWD ? ci : co, N = mode == MODE_FWD ? co : ci, K = 27 * C;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * K) return;
+    const int nn = i / K, k = i % K, tap = k / C, ch = k % C;
+    wt[i] = mode == MODE_FWD ? w[((size_t)tap * ci + ch) * co + nn] : w[((size_t)tap * ci + nn) * co + ch];
 }
 
 // ---------------------------------------------------------------------------
@@ -571,8 +886,17 @@ struct WS {
     size_t wbf;                                  // BF16 copy of every parameter
     size_t ga5f, gz5b, gz5f, gu1f, gz4b, gz4f, gu2f, gz3b, gz3f, gp2f, gz2b, gz2f, gp1f, gz1f;
     size_t part, bpart, lpart;
+    size_t wpk;     // tcgen05 B operands: per layer 1..4, forward then data gradient
+    size_t status;  // device status word
     size_t total;
 };
+
+// offset (elements) of layer l's packed weights for mode (0 forward, 1 data gradient)
+inline size_t wpk_off(int l, int mode) {
+    size_t o = 0;
+    for (int i = 1; i < l; ++i) o += 2 * (size_t)27 * L[i].ci * L[i].co;
+    return o + (mode ? (size_t)27 * L[l].ci * L[l].co : 0);
+}
 
 inline WS layout(int n) {
     WS w;
@@ -622,6 +946,8 @@ inline WS layout(int n) {
     w.part = take(4 * pmax);
     w.bpart = take(4 * 64 * 64);
     w.lpart = take(4 * 1024);
+    w.wpk = take(2 * wpk_off(5, 0));
+    w.status = take(4);
     w.total = o;
     return w;
 }
@@ -639,6 +965,79 @@ static void gemm_bn(int bn, const ConvArgs &a, int gx, int gy, cudaStream_t st) 
     if (bn <= 16) gemm<MODE, 16>(a, gx, gy, st);
     else if (bn <= 32) gemm<MODE, 32>(a, gx, gy, st);
     else gemm<MODE, 64>(a, gx, gy, st);
+}
+
+// engine of the forward and data-gradient convolutions: 2 tcgen05 halo
+// tiles, 1 tcgen05 gathered tiles, 0 mma.sync
+std::atomic<int> g_conv_engine{2};
+
+template <int MODE, int BN>
+static bool umma(const ConvArgs &a, long long rows, cudaStream_t st) {
+    static int attr = 0;  // 1 set, -1 refused
+    if (attr == 0) {
+        attr = cudaFuncSetAttribute(k_conv_umma<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)umma_smem(BN)) == cudaSuccess ? 1 : -1;
+        if (attr < 0) (void)cudaGetLastError();
+    }
+    if (attr < 0) return false;
+    k_conv_umma<MODE, BN><<<(unsigned)((rows + UM - 1) / UM), 128, umma_smem(BN), st>>>(a);
+    counted(1);
+    return true;
+}
+
+// persistent halo-tile launch: as many CTAs as fit on the device at once
+template <int MODE, int C, int N, int ZT>
+static bool halo(const ConvArgs &a, cudaStream_t st) {
+    using HH = Halo<C, N, ZT>;
+    static int per_sm = 0;  // resident CTAs per SM; -1 refused
+    static int sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_conv_halo<MODE, C, N, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)HH::SMEM) == cudaSuccess &&
+                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_halo<MODE, C, N, ZT>, 128,
+                                                                HH::SMEM) == cudaSuccess;
+        if (!ok || per_sm < 1) {
+            per_sm = -1;
+            (void)cudaGetLastError();
+        }
+    }
+    if (per_sm < 0) return false;
+    const int n = a.n;
+    const long long tiles = (long long)((n + 7) / 8) * ((n + 15) / 16) * ((n + ZT - 1) / ZT);
+    const long long cap = (long long)sms * per_sm;
+    k_conv_halo<MODE, C, N, ZT><<<(unsigned)(tiles < cap ? tiles : cap), 128, HH::SMEM, st>>>(a);
+    counted(1);
+    return true;
+}
+
+template <int MODE>
+static bool halo_cn(int C, int N, const ConvArgs &a, cudaStream_t st) {
+    if (C == 16 && N == 32) return halo<MODE, 16, 32, 4>(a, st);
+    if (C == 32 && N == 64) return halo<MODE, 32, 64, 4>(a, st);
+    if (C == 64 && N == 32) return halo<MODE, 64, 32, 2>(a, st);
+    if (C == 32 && N == 16) return halo<MODE, 32, 16, 4>(a, st);
+    return false;
+}
+
+// forward / data-gradient convolution: tcgen05 when selected and the shapes
+// fit it (halo tiles: the four layer shapes; gathered tiles: N in {16, 32,
+// 64}, C a multiple of 8; 16-byte aligned operands), else mma.sync
+template <int MODE>
+static void conv_gemm(const ConvArgs &a, long long rows, cudaStream_t st) {
+    const int N = MODE == MODE_FWD ? a.co : a.ci, C = MODE == MODE_FWD ? a.ci : a.co;
+    const bool aligned = ((uintptr_t)a.x | (uintptr_t)a.wt | (uintptr_t)a.skip |
+                          (uintptr_t)(MODE == MODE_FWD ? (void *)a.y : (void *)a.out)) % 16 == 0;
+    const int engine = g_conv_engine.load();
+    if (engine == 2 && a.wt && aligned && halo_cn<MODE>(C, N, a, st)) return;
+    if (engine >= 1 && a.wt && C % 8 == 0 && aligned && (N == 16 || N == 32 || N == 64)) {
+        bool done = N == 16 ? umma<MODE, 16>(a, rows, st)
+                            : N == 32 ? umma<MODE, 32>(a, rows, st) : umma<MODE, 64>(a, rows, st);
+        if (done) return;
+    }
+    gemm_bn<MODE>(N, a, (int)((rows + GM - 1) / GM), 1, st);
 }
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -671,6 +1070,14 @@ int dgr_net_forward(int n, const float *params, const float *input, float *outpu
     bf16 *wbf = B(W.wbf);
     const long long np = (long long)net::n_params();
     k_to_bf16<<<nblk(np, 256), 256, 0, st>>>(np, params, wbf);
+    int *status = reinterpret_cast<int *>(base + W.status);
+    cudaMemsetAsync(status, 0, sizeof(int), st);
+    bf16 *wpk = B(W.wpk);
+    for (int l = 1; l <= 4; ++l)
+        for (int mode = 0; mode < 2; ++mode)
+            k_wpack<<<nblk(27 * net::L[l].ci * net::L[l].co, 256), 256, 0, st>>>(
+                mode, net::L[l].ci, net::L[l].co, wbf + net::w_off(l), wpk + net::wpk_off(l, mode));
+    counted(8);
     k_conv1_fwd<<<nblk(n3, 128), 128, 0, st>>>(n, input, params + net::w_off(0),
                                                 params + net::b_off(0), B(W.a1));
     k_pool<<<nblk(h3 * 16, 256), 256, 0, st>>>(h, 16, B(W.a1), B(W.p1));
@@ -679,8 +1086,8 @@ int dgr_net_forward(int n, const float *params, const float *input, float *outpu
         ConvArgs a{};
         a.n = side; a.ci = net::L[l].ci; a.co = net::L[l].co;
         a.x = x; a.w = wbf + net::w_off(l); a.bias = params + net::b_off(l); a.skip = skip; a.y = y;
-        const long long s3 = (long long)side * side * side;
-        gemm_bn<MODE_FWD>(a.co, a, (int)nblk(s3, GM), 1, st);
+        a.wt = wpk + net::wpk_off(l, 0); a.status = status;
+        conv_gemm<MODE_FWD>(a, (long long)side * side * side, st);
     };
     conv(1, h, B(W.p1), nullptr, B(W.a2));
     k_pool<<<nblk(q3 * 32, 256), 256, 0, st>>>(q, 32, B(W.a2), B(W.p2));
@@ -727,12 +1134,14 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
         k_reduce_parts<<<1, 64, 0, st>>>(64, co, bpart, grad_params + net::b_off(l));
         counted(3);
     };
+    // the packed weights and the status word come from the forward pass on this workspace
+    const bf16 *wpk = B(W.wpk);
+    int *status = reinterpret_cast<int *>(base + W.status);
     auto dgrad = [&](int l, int side, const bf16 *gz_b, float *gx) {
         ConvArgs d{};
         d.n = side; d.ci = net::L[l].ci; d.co = net::L[l].co; d.x = gz_b; d.w = wbf + net::w_off(l);
-        d.out = gx;
-        const long long s3 = (long long)side * side * side;
-        gemm_bn<MODE_DGRAD>(d.ci, d, (int)nblk(s3, GM), 1, st);
+        d.out = gx; d.wt = wpk + net::wpk_off(l, 1); d.status = status;
+        conv_gemm<MODE_DGRAD>(d, (long long)side * side * side, st);
     };
     // layer 5: a5 = relu(conv(u1) + b5 + a1)
     k_relu_grad<<<nblk(n3 * 16, 256), 256, 0, st>>>(n, 16, B(W.a5), F(W.ga5f), nullptr, nullptr,
@@ -781,6 +1190,22 @@ int dgr_net_loss(int n, const float *output, const float *target, float w_densit
     k_reduce_parts<<<1, 32, 0, st>>>(256, 1, lp, loss);
     counted(2);
     return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_set_conv_engine(int engine) {
+    if (engine < 0 || engine > 2) return DGR_ERR_ARG;
+    g_conv_engine.store(engine);
+    return DGR_OK;
+}
+
+int dgr_net_status(int n, const void *ws, size_t ws_bytes, int *status) {
+    if (!net_side_ok(n) || !ws || !status) return DGR_ERR_ARG;
+    const net::WS W = net::layout(n);
+    if (ws_bytes < W.total) return DGR_ERR_WS_TOO_SMALL;
+    return cudaMemcpy(status, static_cast<const char *>(ws) + W.status, sizeof(int), cudaMemcpyDeviceToHost) ==
+                   cudaSuccess
+               ? DGR_OK
+               : DGR_ERR_CUDA;
 }
 
 int dgr_adam_flat(long long n, float *params, const float *grads, float *m, float *v, int t,

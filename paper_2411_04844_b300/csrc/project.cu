@@ -26,6 +26,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "async_ops.cuh"
 #include "dgr_internal.cuh"
 
 namespace dgr {
@@ -228,53 +229,6 @@ __device__ __forceinline__ float group_step(const Inst &I, const unsigned *view_
 // for the backprojector, and the lanes work on shared memory.  Two stages: the
 // next chunk's copies fly while the current one is walked.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void bulk_s2g_add(int *dst, const int *src, unsigned bytes) {
-    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;" ::"l"(dst),
-                 "r"(smem_u32(src)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// a bounded wait: gives up (and flags the status word) instead of spinning forever
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *status) {
-    for (int it = 0; it < (1 << 20); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(status, DGR_STATUS_TIMEOUT);
-    return false;
-}
-
 // where the walk reads (MODE 0) or adds (MODE 1): the global volume / integer
 // sums at cell offset + z (unstaged), or a shared-memory window of each cell's
 // column: [slot][z - zlo] for the segments s0 .. s0 + nslot - 1 (staged)

@@ -351,8 +351,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
         const int x = x0 + (lane & 7);
         const int wy0 = y0 + 4 * w;
         const int y = wy0 + (lane >> 3);
-        // per-voxel sums with Kahan compensation: a voxel inside many boxes
-        // keeps its FP32 sum within a few ulps of the exact sum
+        // running per-voxel sums with Kahan compensation (per chunk, below)
         float acc[TZ], cmp[TZ];
 #pragma unroll
         for (int k = 0; k < TZ; ++k) acc[k] = cmp[k] = 0.f;
@@ -367,6 +366,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 sp[i] = reinterpret_cast<const float4 *>(prep + gi)[i & 3];
             }
             __syncthreads();
+            // the chunk's plain sums; a z outside a box contributes exp2(-inf) = 0
+            float cs[TZ];
+#pragma unroll
+            for (int k = 0; k < TZ; ++k) cs[k] = 0.f;
             for (int j = 0; j < nc; ++j) {
                 const float4 p3 = sp[4 * j + 3];
                 const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z),
@@ -390,19 +393,34 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
 #pragma unroll
                 for (int g8 = 0; g8 < TZ / TZG; ++g8) {
                     if (zhi < g8 * TZG || zlo >= (g8 + 1) * TZG) continue;  // warp-uniform
+                    if (zlo <= g8 * TZG && zhi >= (g8 + 1) * TZG - 1) {       // whole group in the box
 #pragma unroll
-                    for (int kk = 0; kk < TZG; ++kk) {
-                        const int k = g8 * TZG + kk;
-                        if (k >= zlo && k <= zhi) {
+                        for (int kk = 0; kk < TZG; ++kk) {
+                            const int k = g8 * TZG + kk;
+                            const float dz = dz0 + (float)k;
+                            cs[k] = fmaf(r, ex2_approx(fmaf(dz, fmaf(a22, dz, Lz), C)), cs[k]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < TZG; ++kk) {
+                            const int k = g8 * TZG + kk;
                             const float dz = dz0 + (float)k;
                             const float qf = fmaf(dz, fmaf(a22, dz, Lz), C);
-                            const float y = fmaf(r, ex2_approx(qf), -cmp[k]);
-                            const float tsum = acc[k] + y;
-                            cmp[k] = (tsum - acc[k]) - y;
-                            acc[k] = tsum;
+                            const float e2 = ex2_approx((k >= zlo && k <= zhi) ? qf : -INFINITY);
+                            cs[k] = fmaf(r, e2, cs[k]);
                         }
                     }
                 }
+            }
+            // Kahan: each chunk sum joins the running sum with compensation, so
+            // a voxel inside thousands of boxes keeps its FP32 sum within a few
+            // ulps of the exact sum
+#pragma unroll
+            for (int k = 0; k < TZ; ++k) {
+                const float yv = cs[k] - cmp[k];
+                const float tsum = acc[k] + yv;
+                cmp[k] = (tsum - acc[k]) - yv;
+                acc[k] = tsum;
             }
         }
         if (x < g.nx && y < g.ny) {

@@ -38,6 +38,7 @@ EXPORTS = [
     "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
     "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
     "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss", "dgr_densify", "dgr_set_separable", "dgr_set_staged_walk",
+    "dgr_set_conv_engine", "dgr_net_status",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -141,6 +142,8 @@ def lib():
             "dgr_set_separable": [i],
             "dgr_set_staged_walk": [i],
             "dgr_set_backprojector": [i],
+            "dgr_set_conv_engine": [i],
+            "dgr_net_status": [i, P, ctypes.c_size_t, ctypes.POINTER(i)],
             "dgr_footprint": [ctypes.POINTER(Grid), i, P, P, P, f, P, P, P],
             "dgr_voxelize_count": [ctypes.POINTER(Grid), i, P, P, P, f, ctypes.POINTER(ll),
                                    ctypes.POINTER(ll), P, P],
@@ -526,6 +529,20 @@ def dgr_net_ws_bytes(n: int) -> int:
     b = ctypes.c_size_t()
     _rc(lib().dgr_net_ws_bytes(int(n), ctypes.byref(b)), "dgr_net_ws_bytes")
     return int(b.value)
+
+
+def dgr_set_conv_engine(engine: int):
+    """Forward / data-gradient convolutions: 2 tcgen05 halo tiles (default),
+    1 tcgen05 gathered tiles, 0 mma.sync."""
+    _rc(lib().dgr_set_conv_engine(int(engine)), "dgr_set_conv_engine")
+
+
+def dgr_net_status(n, ws) -> int:
+    """The network's device status word (synchronous read)."""
+    v = ctypes.c_int()
+    _rc(lib().dgr_net_status(int(n), _ptr(ws), ws.numel() * ws.element_size(), ctypes.byref(v)),
+        "dgr_net_status")
+    return int(v.value)
 
 
 def dgr_net_forward(n, params, inp, out, ws, stream=None):

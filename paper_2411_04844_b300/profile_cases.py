@@ -4,7 +4,10 @@ every input already in HBM -- a fixed, small command for profilers.
     python -m paper_2411_04844_b300.profile_cases OP [--workload 2] [--reps 3] [--views N]
         [--backprojector 0|1|2] [--isotropic] [--no-separable] [--unstaged]
 
-OP: voxelize | voxelize_backward | project | backproject | step.
+OP: voxelize | voxelize_backward | project | backproject | step | net_forward |
+net_backward (the warm-start network on a --side^3 grid, default 128, with
+--conv-engine 1 tcgen05 / 0 mma.sync; also prints the four tensor-core
+convolutions' GEMM rate).
 Workload numbers are those of synth.workload (2: 50,000 Gaussians, 256^3,
 cone 50 views x 256^2).  --views keeps only the first N views (smaller
 captures).  Prints the mean CUDA-event time per call.
@@ -20,7 +23,8 @@ from . import dgr, synth
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["voxelize", "voxelize_backward", "project", "backproject", "step"])
+    ap.add_argument("op", choices=["voxelize", "voxelize_backward", "project", "backproject", "step",
+                                   "net_forward", "net_backward"])
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--views", type=int, default=0)
@@ -28,7 +32,11 @@ def main(argv=None):
     ap.add_argument("--isotropic", action="store_true", help="one scale per Gaussian (separable FVR)")
     ap.add_argument("--no-separable", action="store_true", help="general voxelizer even when separable")
     ap.add_argument("--unstaged", action="store_true", help="path walks without shared-memory staging")
+    ap.add_argument("--side", type=int, default=128, help="network grid side")
+    ap.add_argument("--conv-engine", type=int, default=1, help="1: tcgen05, 0: mma.sync")
     a = ap.parse_args(argv)
+    if a.op.startswith("net"):
+        return net_case(a)
     dgr.dgr_set_backprojector(a.backprojector)
     dgr.dgr_set_separable(not a.no_separable)
     dgr.dgr_set_staged_walk(not a.unstaged)
@@ -83,6 +91,42 @@ def main(argv=None):
     torch.cuda.synchronize()
     status = dgr.dgr_status(ws)
     print(f"{a.op}: {e0.elapsed_time(e1) / a.reps:.4f} ms per call (status {status})")
+    return 0 if status == 0 else 1
+
+
+def net_case(a):
+    """forward (or forward + backward) of the warm-start network"""
+    dev, n = "cuda", a.side
+    rng = np.random.default_rng(0)
+    npar = dgr.dgr_net_param_count()
+    params = torch.as_tensor(rng.standard_normal(npar).astype(np.float32) * 0.05, device=dev)
+    x = torch.as_tensor(rng.uniform(0, 1, (n, n, n)).astype(np.float32), device=dev)
+    gy = torch.as_tensor(rng.standard_normal((n, n, n, 2)).astype(np.float32), device=dev)
+    out = torch.empty((n, n, n, 2), device=dev)
+    gp = torch.empty(npar, device=dev)
+    ws = torch.empty(dgr.dgr_net_ws_bytes(n), dtype=torch.uint8, device=dev)
+    dgr.dgr_set_conv_engine(a.conv_engine)
+
+    def once():
+        dgr.dgr_net_forward(n, params, x, out, ws)
+        if a.op == "net_backward":
+            dgr.dgr_net_backward(n, params, x, gy, gp, ws)
+
+    once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    status = dgr.dgr_net_status(n, ws)
+    h3, q3, n3 = (n // 2) ** 3, (n // 4) ** 3, n ** 3
+    # GEMM FLOPs of the four tensor-core convolutions (forward)
+    fl = 2 * 27 * (h3 * 16 * 32 + q3 * 32 * 64 + h3 * 64 * 32 + n3 * 32 * 16)
+    print(f"{a.op} n={n} engine={a.conv_engine}: {ms:.4f} ms per call (status {status}); "
+          f"forward conv GEMMs {fl / 1e9:.1f} GFLOP")
     return 0 if status == 0 else 1
 
 

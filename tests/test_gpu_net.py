@@ -32,20 +32,34 @@ def init_params(rng):
     return np.concatenate(parts).astype(np.float32)
 
 
+def run_net(n, P, x, gy, engine):
+    """forward + backward through the C ABI with the given convolution engine
+    (2 tcgen05 halo tiles, 1 tcgen05 gathered tiles, 0 mma.sync); returns
+    output, parameter gradient, status"""
+    ws = torch.empty(dgr.dgr_net_ws_bytes(n), dtype=torch.uint8, device=DEV)
+    out = torch.full((n, n, n, 2), float("nan"), device=DEV)
+    gp = torch.full((N.n_params(),), float("nan"), device=DEV)
+    Pt, xt = T(P), T(x)
+    try:
+        dgr.dgr_set_conv_engine(engine)
+        dgr.dgr_net_forward(n, Pt, xt, out, ws)
+        dgr.dgr_net_backward(n, Pt, xt, T(gy), gp, ws)
+        torch.cuda.synchronize()
+    finally:
+        dgr.dgr_set_conv_engine(2)
+    return out, gp, dgr.dgr_net_status(n, ws)
+
+
+@pytest.mark.parametrize("engine", [2, 1, 0])
 @pytest.mark.parametrize("n", [8, 16])
-def test_net_forward_and_gradients_match_oracle(n):
+def test_net_forward_and_gradients_match_oracle(n, engine):
     assert dgr.dgr_net_param_count() == N.n_params()
     rng = np.random.default_rng(n)
     P = init_params(rng)
     x = rng.uniform(0, 1, (n, n, n)).astype(np.float32)
     gy = rng.standard_normal((n, n, n, 2)).astype(np.float32)
-    ws = torch.empty(dgr.dgr_net_ws_bytes(n), dtype=torch.uint8, device=DEV)
-    out = torch.empty((n, n, n, 2), device=DEV)
-    gp = torch.full((N.n_params(),), float("nan"), device=DEV)
-    Pt, xt = T(P), T(x)
-    dgr.dgr_net_forward(n, Pt, xt, out, ws)
-    dgr.dgr_net_backward(n, Pt, xt, T(gy), gp, ws)
-    torch.cuda.synchronize()
+    out, gp, status = run_net(n, P, x, gy, engine)
+    assert status == 0
     yo, _ = N.forward(P.astype(np.float64), x, bf=True)
     assert rel_l2(out.cpu().numpy(), yo) <= 2e-3, rel_l2(out.cpu().numpy(), yo)
     go = N.backward(P.astype(np.float64), x, gy, bf=True)
@@ -56,6 +70,31 @@ def test_net_forward_and_gradients_match_oracle(n):
         for name, sz in (("w", t * ci * co), ("b", co)):
             e = rel_l2(g[o:o + sz], go[o:o + sz])
             assert e <= 2e-2, (l, name, e)
+            o += sz
+
+
+@pytest.mark.parametrize("engine", [2, 1])
+@pytest.mark.parametrize("n", [32, 36])
+def test_tcgen05_and_mma_sync_engines_agree_on_many_tiles(n, engine):
+    """32^3: 256, 32 and 4 gathered tiles of 128 rows at sides n, n/2 and n/4,
+    and 8 x 16 x 4 halo tiles (8 x 16 x 2 for 64 input channels) with
+    several tiles per persistent CTA; 36^3: sides 36, 18 and 9 end in partial
+    tiles in x, y and z.  Both engines accumulate in FP32, so they differ by
+    summation order and the rare BF16 rounding it flips."""
+    rng = np.random.default_rng(n)
+    P = init_params(rng)
+    x = rng.uniform(0, 1, (n, n, n)).astype(np.float32)
+    gy = rng.standard_normal((n, n, n, 2)).astype(np.float32)
+    o1, g1, s1 = run_net(n, P, x, gy, engine)
+    o0, g0, s0 = run_net(n, P, x, gy, 0)
+    assert s1 == 0 and s0 == 0
+    assert torch.isfinite(o1).all() and torch.isfinite(g1).all()
+    assert rel_l2(o1.cpu().numpy(), o0.cpu().numpy()) <= 1e-3
+    a, b = g1.cpu().numpy(), g0.cpu().numpy()
+    o = 0
+    for l, (ci, co, t) in enumerate(N.LAYERS):
+        for name, sz in (("w", t * ci * co), ("b", co)):
+            assert rel_l2(a[o:o + sz], b[o:o + sz]) <= 1e-2, (l, name)
             o += sz
 
 
