@@ -338,10 +338,9 @@ int dgr_project_noalloc(const dgr_grid *grid, const dgr_geom *geom, const float 
  * pooling and nearest upsampling, additive skips, a 1^3 head to 2 outputs
  * (density, log-scale in voxels).  Activations and weights BF16 (channels-last
  * [z][y][x][c]), every convolution accumulating in FP32; the four inner
- * convolutions are implicit GEMMs on the tensor cores: forward and data
- * gradient on tcgen05 (FP32 accumulators in tensor memory; by default halo
- * tiles whose taps are shared-memory descriptors into one input block),
- * weight gradient on mma.sync m16n8k16.
+ * convolutions are implicit GEMMs on the tcgen05 tensor cores (forward, data
+ * and weight gradient; FP32 accumulators in tensor memory; halo tiles whose
+ * taps are shared-memory descriptors into one input block).
  * params: FP32 [dgr_net_param_count()], per layer [tap][c_in][c_out] weights
  * then [c_out] biases.  input: FP32 [n^3]; output: FP32 [n^3][2].
  * ws: caller-owned device scratch of dgr_net_ws_bytes(n) bytes holding the
@@ -358,11 +357,12 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
  * (device scalar) and grad_output = d loss / d output. */
 int dgr_net_loss(int n, const float *output, const float *target, float w_density, float w_scale,
                  float *grad_output, float *loss, void *ws, size_t ws_bytes, cudaStream_t stream);
-/* Engine of the forward and data-gradient convolutions: 2 = tcgen05 on
- * halo tiles (default: an 8 x 16 x ZT output tile's input block with a
- * one-voxel halo loaded once, every tap a descriptor into it), 1 = tcgen05
- * on gathered 128-row tiles (im2col into shared memory), 0 = mma.sync
- * m16n8k16.  Process-wide; DGR_ERR_ARG otherwise. */
+/* Convolution engine: 2 = tcgen05 on halo tiles for all three GEMMs
+ * (default: an 8 x 16 x ZT output tile's input block with a one-voxel halo
+ * loaded once, every tap a descriptor into it), 1 = tcgen05 on gathered
+ * 128-row tiles (im2col into shared memory) for forward and data gradient,
+ * mma.sync for the weight gradient, 0 = mma.sync m16n8k16 for all.
+ * Process-wide; DGR_ERR_ARG otherwise. */
 int dgr_set_conv_engine(int engine);
 /* The network's device status word on ws (DGR_STATUS_TIMEOUT when a bounded
  * wait of a tcgen05 convolution gave up; the output is then incomplete).

@@ -64,6 +64,17 @@ __device__ __forceinline__ void bulk_s2g_add(int *dst, const int *src, unsigned 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// 16-byte asynchronous copy global -> shared through L2 (cp.async); with
+// src_bytes = 0 nothing is read and the 16 bytes are zero-filled
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 // generic-proxy shared-memory writes become visible to the asynchronous proxy
 // (bulk copies, tensor-core operand reads)
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -91,14 +102,17 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // Shared-memory matrix descriptor, no swizzle: start address, the byte
 // distance between core matrices adjacent in K (leading) and in M or N
 // (stride), the fixed version field 1 (bits 46-47), base offset 0, layout 0.
-// A core matrix is 8 rows x 16 bytes stored as 128 contiguous bytes.
+// A core matrix is 8 rows x 16 bytes stored as 128 contiguous bytes: 8 M/N
+// rows of 8 K elements (K-major) or 8 K rows of 8 M/N elements (MN-major);
+// the leading / stride assignment is the same for both.
 __device__ __forceinline__ uint64_t smem_desc(unsigned saddr, unsigned lead_bytes, unsigned stride_bytes) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lead_bytes >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((stride_bytes >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
-// Instruction descriptor of kind::f16 with BF16 A and B (both K-major), FP32
-// accumulation, dense: D format bits 4-5 = 1 (F32), A format bits 7-9 = 1
-// (BF16), B format bits 10-12 = 1, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulation,
+// dense: D format bits 4-5 = 1 (F32), A format bits 7-9 = 1 (BF16), B format
+// bits 10-12 = 1, N >> 3 at bits 17-22, M >> 4 at bits 24-28; A and B K-major
+// (OR in bit 15 / bit 16 for an MN-major A / B).
 __host__ __device__ constexpr unsigned idesc_bf16_f32(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
 }

@@ -18,9 +18,10 @@
 //   data grad    C[p][ci] = sum_{tap,co} G[p - tap][co] W[tap][ci][co]
 //   weight grad  C[tap*Ci + ci][co] = sum_p X[p + tap][ci] G[p][co]
 //                (split over voxel ranges; partials summed in a fixed order)
-// Forward and data gradient run on tcgen05 (k_conv_halo by default,
-// k_conv_umma, or k_conv_gemm on mma.sync m16n8k16 by dgr_set_conv_engine);
-// the weight gradient on mma.sync (k_conv_gemm).
+// By default all three run on tcgen05 over halo blocks (k_conv_halo,
+// k_wgrad_halo); dgr_set_conv_engine selects gathered 128-row tcgen05 tiles
+// for forward and data gradient (k_conv_umma) or mma.sync m16n8k16
+// (k_conv_gemm, also the weight gradient of the other two engines).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -372,6 +373,29 @@ __global__ void __launch_bounds__(128) k_conv_umma(const ConvArgs a) {
 // The CTA walks tiles (persistent); the halo block is rewritten only after
 // the tile's commit has arrived.
 // ---------------------------------------------------------------------------
+// Threads of the halo-tile kernels: eight warps load; warp w reads tensor
+// memory lanes 32 (w % 4) .. + 31 (its lane quarter) and takes every other
+// 16-column chunk of the epilogue with its partner warp w ^ 4.
+constexpr int HALO_THREADS = 256;
+
+// the input block of a tile: voxels x0-1 .. x0+8, y0-1 .. y0+16, z0-1 ..
+// z0+HZ-2 of x [n^3][C] (zero outside) as 16-byte channel chunks at
+// chunk plane c, offset ((zz 18 + yy) 10 + xx) 16, by asynchronous copies
+// (all of a thread's copies in flight at once; the caller commits and waits)
+template <int C, int HZ>
+__device__ __forceinline__ void load_halo(const bf16 *__restrict__ x, int n, int x0, int y0, int z0,
+                                          unsigned char *Hs, unsigned plane) {
+    constexpr int CH = C / 8, TOT = 10 * 18 * HZ * CH;
+    for (int e = threadIdx.x; e < TOT; e += HALO_THREADS) {
+        const int c = e % CH, v = e / CH;
+        const int xx = v % 10, yy = (v / 10) % 18, zz = v / 180;
+        const int qx = x0 + xx - 1, qy = y0 + yy - 1, qz = z0 + zz - 1;
+        const bool in = qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n;
+        const bf16 *src = in ? x + ((size_t)(qz * n + qy) * n + qx) * C + 8 * c : x;
+        cp_async16(Hs + c * plane + ((zz * 18 + yy) * 10 + xx) * 16, src, in ? 16u : 0u);
+    }
+}
+
 template <int C, int N, int ZT>
 struct Halo {
     static constexpr int HX = 10, HY = 18, HZ = ZT + 2;
@@ -391,7 +415,7 @@ struct Halo {
 };
 
 template <int MODE, int C, int N, int ZT>
-__global__ void __launch_bounds__(128) k_conv_halo(const ConvArgs a) {
+__global__ void __launch_bounds__(HALO_THREADS) k_conv_halo(const ConvArgs a) {
     static_assert(MODE == MODE_FWD || MODE == MODE_DGRAD, "forward and data gradient only");
     static_assert(N % 16 == 0 && N >= 16 && N <= 64 && C % 16 == 0, "tile shapes");
     using H = Halo<C, N, ZT>;
@@ -414,7 +438,7 @@ __global__ void __launch_bounds__(128) k_conv_halo(const ConvArgs a) {
     }
     // B: the packed weights [N][27 C] (K-major rows) as core matrices
     // (n group g, K chunk kc) at kc BLEAD + g 128
-    for (int e = threadIdx.x; e < N * 27 * H::CH; e += 128) {
+    for (int e = threadIdx.x; e < N * 27 * H::CH; e += HALO_THREADS) {
         const int nn = e % N, kc = e / N;
         const uint4 v = *reinterpret_cast<const uint4 *>(a.wt + (size_t)nn * 27 * C + 8 * kc);
         *reinterpret_cast<uint4 *>(Bs + kc * H::BLEAD + (nn >> 3) * 128 + (nn & 7) * 16) = v;
@@ -433,54 +457,46 @@ __global__ void __launch_bounds__(128) k_conv_halo(const ConvArgs a) {
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int x0 = (tile % ntx) * 8, y0 = ((tile / ntx) % nty) * 16, z0 = (tile / (ntx * nty)) * ZT;
-        // the input block x0-1 .. x0+8, y0-1 .. y0+16, z0-1 .. z0+ZT (zero outside)
-        for (int e = threadIdx.x; e < H::HX * H::HY * H::HZ * H::CH; e += 128) {
-            const int c = e % H::CH, v = e / H::CH;
-            const int xx = v % H::HX, yy = (v / H::HX) % H::HY, zz = v / (H::HX * H::HY);
-            const int qx = x0 + xx - 1, qy = y0 + yy - 1, qz = z0 + zz - 1;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n)
-                val = *reinterpret_cast<const uint4 *>(a.x + ((size_t)(qz * n + qy) * n + qx) * C + 8 * c);
-            *reinterpret_cast<uint4 *>(Hs + c * H::PLANE + ((zz * H::HY + yy) * H::HX + xx) * 16) = val;
-        }
+        load_halo<C, H::HZ>(a.x, n, x0, y0, z0, Hs, H::PLANE);
+        cp_async_commit();
+        cp_async_wait<0>();
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         if (threadIdx.x == 0) {
             tc_fence_after();
-            for (int zs = 0; zs < ZT; ++zs) {
-                for (int tap = 0; tap < 27; ++tap) {
-                    int dx, dy, dz;
-                    tap_offset(tap, dx, dy, dz);
-                    if (MODE == MODE_DGRAD) { dx = -dx; dy = -dy; dz = -dz; }
-                    const unsigned a0 = hs + (unsigned)(((zs + 1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx) * 16;
+            // descriptors built once; a tap, slice or chunk moves the start
+            // address field only (offsets in 16-byte units, no carry: shared
+            // addresses stay below 2^18)
+            const uint64_t ad0 = smem_desc(hs, H::PLANE, H::HX * 16), bd0 = smem_desc(bs, H::BLEAD, 128);
+            for (int tap = 0; tap < 27; ++tap) {
+                int dx, dy, dz;
+                tap_offset(tap, dx, dy, dz);
+                if (MODE == MODE_DGRAD) { dx = -dx; dy = -dy; dz = -dz; }
+                const uint64_t at = ad0 + (uint64_t)(((1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx);
+                const uint64_t bt = bd0 + (uint64_t)(tap * H::CH * (H::BLEAD / 16));
+#pragma unroll
+                for (int zs = 0; zs < ZT; ++zs)
 #pragma unroll
                     for (int cp = 0; cp < H::CH; cp += 2)
-                        umma_bf16(tmem + (unsigned)(zs * N),
-                                  smem_desc(a0 + cp * H::PLANE, H::PLANE, H::HX * 16),
-                                  smem_desc(bs + (tap * H::CH + cp) * H::BLEAD, H::BLEAD, 128), IDESC,
-                                  (tap | cp) != 0);
-                }
+                        umma_bf16(tmem + (unsigned)(zs * N), at + (uint64_t)(zs * H::HY * H::HX + cp * (H::PLANE / 16)),
+                                  bt + (uint64_t)(cp * (H::BLEAD / 16)), IDESC, (tap | cp) != 0);
             }
             umma_commit(bar);
         }
         if (!mbar_wait(bar, it & 1, a.status)) ok = false;
         if (!__syncthreads_and(ok)) { ok = false; break; }
         tc_fence_after();
-        // epilogue: thread of row m = 32 w + lane holds voxel (x0 + m % 8, y0 + m / 8)
-        const int m = 32 * w + (threadIdx.x & 31);
+        // epilogue: thread of row m = 32 (w % 4) + lane holds voxel (x0 + m % 8,
+        // y0 + m / 8); warps w and w ^ 4 share the 16-column chunks
+        const int q = w & 3, m = 32 * q + (threadIdx.x & 31);
         const int x = x0 + (m & 7), y = y0 + (m >> 3);
-        for (int zs = 0; zs < ZT; ++zs) {
+        for (int j = w >> 2; j < ZT * (N / 16); j += 2) {
+            const int zs = j / (N / 16), c0 = 16 * (j % (N / 16));
             const int z = z0 + zs;
-            const bool inside = x < n && y < n && z < n;
-            const size_t row = ((size_t)z * n + y) * n + x;
-#pragma unroll
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((unsigned)(32 * w) << 16) + (unsigned)(zs * N + c0), v);
-                if (!inside) continue;
-                store_row16<MODE>(a, row, c0, v);
-            }
+            float v[16];
+            tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(zs * N + c0), v);
+            if (x < n && y < n && z < n) store_row16<MODE>(a, ((size_t)z * n + y) * n + x, c0, v);
         }
         // every thread's tensor-memory reads are complete (tmem_ld16 waits)
         // before the next tile's first MMA overwrites the accumulators
@@ -493,6 +509,161 @@ __global__ void __launch_bounds__(128) k_conv_halo(const ConvArgs a) {
     if (w == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, H::NCOL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05 over the same halo blocks.  Per tap,
+//   dW_tap[ci][co] = sum_p X[p + tap][ci] G[p][co]
+// is a GEMM with K = voxels whose operands are both channel-contiguous
+// (MN-major): A = G of an output tile (M = 128 rows: the CO channels, the
+// rest padding planes of zeros whose rows are discarded), B = the shifted
+// input window (N = CI).  A core matrix is 8 voxels (K) x 16 bytes (8
+// channels); K-adjacent core matrices are the next line of the tile (128
+// bytes in the G block, 160 in the halo block), MN-adjacent ones the next
+// channel plane.  A CTA owns a group of TPG taps (TPG x CI accumulator
+// columns in tensor memory) and a range of tiles, accumulates over all of
+// them and writes its partial [split][tap][ci][co]; the partials are summed
+// in a fixed order.  Without swizzling the descriptor's stride field holds
+// the MN-direction core-matrix pitch and the leading field the K-direction
+// pitch for MN-major operands too (checked against the mma.sync weight
+// gradient; the exchanged assignment gives wrong sums).
+// ---------------------------------------------------------------------------
+template <int CI, int CO, int ZT>
+struct WgHalo {
+    using H = Halo<CI, 16, ZT>;  // the X block of the forward kernels (N unused)
+    static constexpr unsigned GPLANE = 8u * 16 * ZT * 16;  // bytes of one G channel plane
+    static constexpr unsigned GREAL = (CO / 8) * GPLANE;    // the CO / 8 planes that are loaded
+    // one buffer: G planes, then the X block; two buffers (double buffering)
+    static constexpr unsigned BUF = (GREAL + H::HBYTES + 1023u) & ~1023u;
+    // rows CO .. 127 of A read planes CO / 8 .. 15 past a buffer's G planes:
+    // whatever lies there (rows discarded), but inside the allocation
+    static constexpr unsigned REACH = BUF + 16 * GPLANE;
+    static constexpr unsigned DATA = 2 * BUF > REACH ? 2 * BUF : REACH;
+    static constexpr size_t SMEM = 1024 + (size_t)DATA + 64;
+};
+
+template <int CI, int CO, int TPG, int ZT>
+__global__ void __launch_bounds__(HALO_THREADS) k_wgrad_halo(const ConvArgs a, int splits) {
+    static_assert(CI % 16 == 0 && CI <= 64 && CO % 8 == 0 && CO <= 128, "channels");
+    using W = WgHalo<CI, CO, ZT>;
+    using H = typename W::H;
+    constexpr int NCOLS = TPG * CI;
+    constexpr unsigned NCOL = NCOLS <= 32 ? 32 : (NCOLS <= 64 ? 64 : (NCOLS <= 128 ? 128 : (NCOLS <= 256 ? 256 : 512)));
+    static_assert(NCOLS <= 512, "accumulators exceed tensor memory");
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm + W::DATA);  // [2]
+    unsigned *tslot = reinterpret_cast<unsigned *>(bar + 2);
+
+    const int n = a.n;
+    const int w = threadIdx.x >> 5;
+    const int grp = blockIdx.x % ((27 + TPG - 1) / TPG), split = blockIdx.x / ((27 + TPG - 1) / TPG);
+    const int tap0 = grp * TPG, ntap = min(TPG, 27 - tap0);
+    if (w == 0) {
+        tmem_alloc(tslot, NCOL);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tslot;
+    const unsigned base = smem_u32(sm);
+    constexpr unsigned IDESC = idesc_bf16_f32(128, CI) | (1u << 15) | (1u << 16);  // A, B MN-major
+
+    const int ntx = (n + 7) / 8, nty = (n + 15) / 16, ntz = (n + ZT - 1) / ZT;
+    const long long ntiles = (long long)ntx * nty * ntz;
+    const long long tb = ntiles * split / splits, te = ntiles * (split + 1) / splits;
+    const int cnt = (int)(te - tb);
+    // asynchronous copies of tile tb + i into buffer i & 1: the X block with
+    // its halo, and G of the tile (no halo; zero outside the grid, where it
+    // adds nothing)
+    auto load = [&](int i) {
+        const long long tile = tb + i;
+        const int x0 = (int)(tile % ntx) * 8, y0 = (int)((tile / ntx) % nty) * 16,
+                  z0 = (int)(tile / ((long long)ntx * nty)) * ZT;
+        unsigned char *G = sm + (i & 1) * W::BUF;
+        load_halo<CI, H::HZ>(a.x, n, x0, y0, z0, G + W::GREAL, H::PLANE);
+        for (int e = threadIdx.x; e < 8 * 16 * ZT * (CO / 8); e += HALO_THREADS) {
+            const int c = e % (CO / 8), v = e / (CO / 8);
+            const int qx = x0 + v % 8, qy = y0 + (v / 8) % 16, qz = z0 + v / 128;
+            const bool in = qx < n && qy < n && qz < n;
+            const bf16 *src = in ? a.g + ((size_t)(qz * n + qy) * n + qx) * CO + 8 * c : a.g;
+            cp_async16(G + c * W::GPLANE + v * 16, src, in ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+    bool ok = true;
+    int i = 0;
+    if (cnt > 0) load(0);
+    for (; i < cnt; ++i) {
+        const int b = i & 1;
+        if (i + 1 < cnt) {
+            // buffer b ^ 1 was read by the MMAs of tile i - 1
+            if (i >= 1 && !mbar_wait(&bar[b ^ 1], ((i - 1) >> 1) & 1, a.status)) ok = false;
+            if (__syncthreads_or(!ok)) break;
+            load(i + 1);
+            cp_async_wait<1>();  // tile i's copies have landed
+        } else {
+            cp_async_wait<0>();
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const unsigned gs = base + b * W::BUF, hs = gs + W::GREAL;
+            // descriptors built once; taps, slices and line pairs move the
+            // start address field only (16-byte units, no carry)
+            const uint64_t ad0 = smem_desc(gs, 128, W::GPLANE), bd0 = smem_desc(hs, H::HX * 16, H::PLANE);
+            for (int j = 0; j < ntap; ++j) {
+                int dx, dy, dz;
+                tap_offset(tap0 + j, dx, dy, dz);
+                const uint64_t bt = bd0 + (uint64_t)(((1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx);
+#pragma unroll
+                for (int zs = 0; zs < ZT; ++zs)
+#pragma unroll
+                    for (int l = 0; l < 16; l += 2)  // K = 16 voxels: lines l and l + 1
+                        umma_bf16(tmem + (unsigned)(j * CI), ad0 + (uint64_t)((zs * 16 + l) * 8),
+                                  bt + (uint64_t)((zs * H::HY + l) * H::HX), IDESC, (i | zs | l) != 0);
+            }
+            umma_commit(&bar[b]);
+        }
+    }
+    cp_async_wait<0>();
+    // the last commit arrives once every MMA of the CTA has completed
+    const int last = i - 1;
+    if (last >= 0 && !mbar_wait(&bar[last & 1], (last >> 1) & 1, a.status)) ok = false;
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    // partial of this split: rows m < CO of the accumulators (row m = lane m)
+    if (ok) {
+        const int q = w & 3, m = 32 * q + (threadIdx.x & 31);
+        float *out = a.out + (size_t)split * 27 * CI * CO;
+        // warps w and w ^ 4 share the 16-column chunks (tap j, channels c0 ..)
+        for (int k = w >> 2; k < ntap * (CI / 16); k += 2) {
+            const int j = k / (CI / 16), c0 = 16 * (k % (CI / 16));
+            float v[16];
+            tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(j * CI + c0), v);
+            if (m >= CO) continue;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                // a CTA with no tiles holds no accumulator: its partial is zero
+                out[((size_t)(tap0 + j) * CI + c0 + u) * CO + m] = cnt > 0 ? v[u] : 0.f;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, NCOL);
     }
 }
 
@@ -533,37 +704,55 @@ __global__ void k_conv1_fwd(int n, const float *__restrict__ x, const float *__r
     for (int c = 0; c < 16; ++c) y[(size_t)p * 16 + c] = __float2bfloat16(fmaxf(acc[c], 0.f));
 }
 
-// weight gradient of the first layer: partial sums per block (fixed order)
-__global__ void k_conv1_wgrad(int n, const float *__restrict__ x, const float *__restrict__ gz,
-                              float *__restrict__ part) {
-    // part[block][27*16 + 16]
-    __shared__ float s[27 * 16 + 16];
-    for (int i = threadIdx.x; i < 27 * 16 + 16; i += blockDim.x) s[i] = 0.f;
-    __syncthreads();
-    const int n3 = n * n * n;
-    const int p0 = blockIdx.x * 1024;
-    // each thread owns (tap, c) pairs and loops over the block's voxels
-    for (int i = threadIdx.x; i < 27 * 16 + 16; i += blockDim.x) {
-        float acc = 0.f;
-        if (i < 27 * 16) {
-            const int tap = i / 16, c = i % 16;
-            int dx, dy, dz;
-            tap_offset(tap, dx, dy, dz);
-            for (int p = p0; p < min(n3, p0 + 1024); ++p) {
-                const int px = p % n, py = (p / n) % n, pz = p / (n * n);
-                const int qx = px + dx, qy = py + dy, qz = pz + dz;
-                if (qx < 0 || qx >= n || qy < 0 || qy >= n || qz < 0 || qz >= n) continue;
-                acc = fmaf(x[(qz * n + qy) * n + qx], gz[(size_t)p * 16 + c], acc);
+// weight gradient of the first layer: a block walks 8^3 voxel tiles (tile
+// b, b + gridDim.x, ...) with the input block (10^3, zero outside) and the
+// tile's gz [512][16] in shared memory; thread i < 432 owns (tap, c) = (i / 16,
+// i % 16), threads 432 .. 447 the bias sums; one partial per block, summed
+// in a fixed order afterwards
+constexpr int C1_THREADS = 448;
+__global__ void __launch_bounds__(C1_THREADS) k_conv1_wgrad(int n, const float *__restrict__ x,
+                                                            const float *__restrict__ gz,
+                                                            float *__restrict__ part) {
+    __shared__ float xs[10 * 10 * 10];
+    __shared__ __align__(16) float gs[512 * 16];
+    const int nt = (n + 7) / 8, ntiles = nt * nt * nt;
+    const int i = threadIdx.x;
+    int tap = 0, c = 0, dx = 0, dy = 0, dz = 0;
+    if (i < 432) {
+        tap = i / 16;
+        c = i % 16;
+        tap_offset(tap, dx, dy, dz);
+    } else {
+        c = i - 432;
+    }
+    float acc = 0.f;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int x0 = (t % nt) * 8, y0 = ((t / nt) % nt) * 8, z0 = (t / (nt * nt)) * 8;
+        __syncthreads();
+        for (int e = i; e < 1000; e += C1_THREADS) {
+            const int qx = x0 + e % 10 - 1, qy = y0 + (e / 10) % 10 - 1, qz = z0 + e / 100 - 1;
+            xs[e] = (qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n) ? x[((size_t)qz * n + qy) * n + qx]
+                                                                                   : 0.f;
+        }
+        for (int e = i; e < 512 * 4; e += C1_THREADS) {  // float4 of gz (zero outside)
+            const int v = e >> 2, q = e & 3;
+            const int px = x0 + (v & 7), py = y0 + ((v >> 3) & 7), pz = z0 + (v >> 6);
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (px < n && py < n && pz < n)
+                g = reinterpret_cast<const float4 *>(gz + (((size_t)pz * n + py) * n + px) * 16)[q];
+            reinterpret_cast<float4 *>(gs)[e] = g;
+        }
+        __syncthreads();
+        if (i < 432) {
+            for (int v = 0; v < 512; ++v) {
+                const int vx = v & 7, vy = (v >> 3) & 7, vz = v >> 6;
+                acc = fmaf(xs[((vz + 1 + dz) * 10 + vy + 1 + dy) * 10 + vx + 1 + dx], gs[v * 16 + c], acc);
             }
         } else {
-            const int c = i - 27 * 16;
-            for (int p = p0; p < min(n3, p0 + 1024); ++p) acc += gz[(size_t)p * 16 + c];
+            for (int v = 0; v < 512; ++v) acc += gs[v * 16 + c];
         }
-        s[i] = acc;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 27 * 16 + 16; i += blockDim.x)
-        part[(size_t)blockIdx.x * (27 * 16 + 16) + i] = s[i];
+    part[(size_t)blockIdx.x * (27 * 16 + 16) + i] = acc;
 }
 
 // head: 1x1 conv 16 -> 2, FP32 output [n^3][2]
@@ -871,7 +1060,7 @@ struct Layer {
     int ci, co, taps;
 };
 constexpr Layer L[6] = {{1, 16, 27}, {16, 32, 27}, {32, 64, 27}, {64, 32, 27}, {32, 16, 27}, {16, 2, 1}};
-constexpr int C1_VOX = 1024;  // voxels per block of the first layer's weight gradient
+constexpr int C1_BLOCKS = 1024;  // most blocks (partials) of the first layer's weight gradient
 
 inline size_t w_off(int l) {
     size_t o = 0;
@@ -940,7 +1129,7 @@ inline WS layout(int n) {
         const size_t v = splits * 27 * L[l].ci * L[l].co;
         pmax = v > pmax ? v : pmax;
     }
-    const size_t c1 = ((n3 + C1_VOX - 1) / C1_VOX) * (27 * 16 + 16);
+    const size_t c1 = (size_t)C1_BLOCKS * (27 * 16 + 16);
     pmax = c1 > pmax ? c1 : pmax;
     pmax = (size_t)256 * 34 > pmax ? (size_t)256 * 34 : pmax;
     w.part = take(4 * pmax);
@@ -967,8 +1156,8 @@ static void gemm_bn(int bn, const ConvArgs &a, int gx, int gy, cudaStream_t st) 
     else gemm<MODE, 64>(a, gx, gy, st);
 }
 
-// engine of the forward and data-gradient convolutions: 2 tcgen05 halo
-// tiles, 1 tcgen05 gathered tiles, 0 mma.sync
+// convolution engine: 2 tcgen05 halo tiles (all three GEMMs), 1 tcgen05
+// gathered tiles (forward, data gradient), 0 mma.sync
 std::atomic<int> g_conv_engine{2};
 
 template <int MODE, int BN>
@@ -997,7 +1186,7 @@ static bool halo(const ConvArgs &a, cudaStream_t st) {
                   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
                   cudaFuncSetAttribute(k_conv_halo<MODE, C, N, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)HH::SMEM) == cudaSuccess &&
-                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_halo<MODE, C, N, ZT>, 128,
+                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_halo<MODE, C, N, ZT>, HALO_THREADS,
                                                                 HH::SMEM) == cudaSuccess;
         if (!ok || per_sm < 1) {
             per_sm = -1;
@@ -1008,7 +1197,7 @@ static bool halo(const ConvArgs &a, cudaStream_t st) {
     const int n = a.n;
     const long long tiles = (long long)((n + 7) / 8) * ((n + 15) / 16) * ((n + ZT - 1) / ZT);
     const long long cap = (long long)sms * per_sm;
-    k_conv_halo<MODE, C, N, ZT><<<(unsigned)(tiles < cap ? tiles : cap), 128, HH::SMEM, st>>>(a);
+    k_conv_halo<MODE, C, N, ZT><<<(unsigned)(tiles < cap ? tiles : cap), HALO_THREADS, HH::SMEM, st>>>(a);
     counted(1);
     return true;
 }
@@ -1020,6 +1209,43 @@ static bool halo_cn(int C, int N, const ConvArgs &a, cudaStream_t st) {
     if (C == 64 && N == 32) return halo<MODE, 64, 32, 2>(a, st);
     if (C == 32 && N == 16) return halo<MODE, 32, 16, 4>(a, st);
     return false;
+}
+
+// weight gradient on tcgen05: partials [splits][27 ci][co] into a.out;
+// returns the number of splits, 0 if not launched
+template <int CI, int CO, int TPG>
+static int wgrad_halo(const ConvArgs &a, int max_splits, cudaStream_t st) {
+    constexpr int ZT = 2;
+    using WW = WgHalo<CI, CO, ZT>;
+    static int sms = 0, attr = 0;
+    if (attr == 0) {
+        int dev = 0;
+        attr = (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                cudaFuncSetAttribute(k_wgrad_halo<CI, CO, TPG, ZT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WW::SMEM) == cudaSuccess)
+                   ? 1
+                   : -1;
+        if (attr < 0) (void)cudaGetLastError();
+    }
+    if (attr < 0) return 0;
+    const int n = a.n, ng = (27 + TPG - 1) / TPG;
+    const long long tiles = (long long)((n + 7) / 8) * ((n + 15) / 16) * ((n + ZT - 1) / ZT);
+    long long s = (long long)sms / ng;  // one CTA per SM (up to 512 tensor-memory columns each)
+    if (s > max_splits) s = max_splits;
+    if (s > tiles) s = tiles;
+    if (s < 1) s = 1;
+    k_wgrad_halo<CI, CO, TPG, ZT><<<(unsigned)(s * ng), HALO_THREADS, WW::SMEM, st>>>(a, (int)s);
+    counted(1);
+    return (int)s;
+}
+
+static int wgrad_halo_cn(const ConvArgs &a, int max_splits, cudaStream_t st) {
+    if (a.ci == 16 && a.co == 32) return wgrad_halo<16, 32, 27>(a, max_splits, st);
+    if (a.ci == 32 && a.co == 64) return wgrad_halo<32, 64, 14>(a, max_splits, st);
+    if (a.ci == 64 && a.co == 32) return wgrad_halo<64, 32, 7>(a, max_splits, st);
+    if (a.ci == 32 && a.co == 16) return wgrad_halo<32, 16, 14>(a, max_splits, st);
+    return 0;
 }
 
 // forward / data-gradient convolution: tcgen05 when selected and the shapes
@@ -1120,23 +1346,33 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
                                     F(W.ga5f), part);
     k_reduce_parts<<<1, 64, 0, st>>>(256, 34, part, grad_params + net::w_off(5));
     counted(2);
+    // the packed weights and the status word come from the forward pass on this workspace
+    const bf16 *wpk = B(W.wpk);
+    int *status = reinterpret_cast<int *>(base + W.status);
     // weight and bias gradients of tensor-core layer l (input x at side^3)
     auto wgrad = [&](int l, int side, const bf16 *x, const bf16 *gz_b, const float *gz_f) {
         const int ci = net::L[l].ci, co = net::L[l].co;
         const long long s3 = (long long)side * side * side;
         ConvArgs a{};
         a.n = side; a.ci = ci; a.co = co; a.x = x; a.g = gz_b; a.out = part;
-        const int splits = (int)nblk(s3, WG_SPLIT);
-        gemm_bn<MODE_WGRAD>(co, a, (int)nblk(27 * ci, GM), splits, st);
+        const int max_splits = (int)nblk(s3, WG_SPLIT);  // the partial buffer's capacity
+        const int engine = g_conv_engine.load();
+        const bool aligned = ((uintptr_t)a.x | (uintptr_t)a.g) % 16 == 0;
+        int splits = 0;
+        if (engine == 2 && aligned) {
+            a.status = status;
+            splits = wgrad_halo_cn(a, max_splits, st);
+        }
+        if (splits == 0) {
+            splits = max_splits;
+            gemm_bn<MODE_WGRAD>(co, a, (int)nblk(27 * ci, GM), splits, st);
+        }
         k_reduce_parts<<<nblk(27 * ci * co, 256), 256, 0, st>>>(splits, 27 * ci * co, part,
                                                                 grad_params + net::w_off(l));
         k_bias_part<<<dim3(64, co), 256, 0, st>>>(s3, co, gz_f, bpart);
         k_reduce_parts<<<1, 64, 0, st>>>(64, co, bpart, grad_params + net::b_off(l));
         counted(3);
     };
-    // the packed weights and the status word come from the forward pass on this workspace
-    const bf16 *wpk = B(W.wpk);
-    int *status = reinterpret_cast<int *>(base + W.status);
     auto dgrad = [&](int l, int side, const bf16 *gz_b, float *gx) {
         ConvArgs d{};
         d.n = side; d.ci = net::L[l].ci; d.co = net::L[l].co; d.x = gz_b; d.w = wbf + net::w_off(l);
@@ -1170,8 +1406,9 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
     // layer 1: a1 = relu(conv(x) + b1); gradient: skip of layer 5 + pool^T(gp1)
     k_relu_grad<<<nblk(n3 * 16, 256), 256, 0, st>>>(n, 16, B(W.a1), F(W.gz5f), nullptr, F(W.gp1f),
                                                    nullptr, nullptr, F(W.gz1f));
-    const unsigned c1b = nblk(n3, net::C1_VOX);
-    k_conv1_wgrad<<<c1b, 256, 0, st>>>(n, input, F(W.gz1f), part);
+    const unsigned c1t = (unsigned)(((n + 7) / 8) * ((n + 7) / 8) * ((n + 7) / 8));
+    const unsigned c1b = c1t < (unsigned)net::C1_BLOCKS ? c1t : (unsigned)net::C1_BLOCKS;  // blocks = partials
+    k_conv1_wgrad<<<c1b, C1_THREADS, 0, st>>>(n, input, F(W.gz1f), part);
     k_reduce_parts<<<nblk(27 * 16 + 16, 256), 256, 0, st>>>((int)c1b, 27 * 16 + 16, part,
                                                             grad_params + net::w_off(0));
     counted(3);

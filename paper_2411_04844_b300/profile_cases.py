@@ -6,8 +6,8 @@ every input already in HBM -- a fixed, small command for profilers.
 
 OP: voxelize | voxelize_backward | project | backproject | step | net_forward |
 net_backward (the warm-start network on a --side^3 grid, default 128, with
---conv-engine 1 tcgen05 / 0 mma.sync; also prints the four tensor-core
-convolutions' GEMM rate).
+--conv-engine as dgr_set_conv_engine, default 2; also prints the four
+tensor-core convolutions' forward GEMM FLOPs).
 Workload numbers are those of synth.workload (2: 50,000 Gaussians, 256^3,
 cone 50 views x 256^2).  --views keeps only the first N views (smaller
 captures).  Prints the mean CUDA-event time per call.
@@ -33,7 +33,7 @@ def main(argv=None):
     ap.add_argument("--no-separable", action="store_true", help="general voxelizer even when separable")
     ap.add_argument("--unstaged", action="store_true", help="path walks without shared-memory staging")
     ap.add_argument("--side", type=int, default=128, help="network grid side")
-    ap.add_argument("--conv-engine", type=int, default=1, help="1: tcgen05, 0: mma.sync")
+    ap.add_argument("--conv-engine", type=int, default=2, help="2: tcgen05 halo tiles, 1: tcgen05 gathered tiles, 0: mma.sync")
     a = ap.parse_args(argv)
     if a.op.startswith("net"):
         return net_case(a)

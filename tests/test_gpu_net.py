@@ -51,7 +51,7 @@ def run_net(n, P, x, gy, engine):
 
 
 @pytest.mark.parametrize("engine", [2, 1, 0])
-@pytest.mark.parametrize("n", [8, 16])
+@pytest.mark.parametrize("n", [8, 12, 16])
 def test_net_forward_and_gradients_match_oracle(n, engine):
     assert dgr.dgr_net_param_count() == N.n_params()
     rng = np.random.default_rng(n)
