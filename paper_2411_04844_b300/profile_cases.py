@@ -2,7 +2,7 @@
 every input already in HBM -- a fixed, small command for profilers.
 
     python -m paper_2411_04844_b300.profile_cases OP [--workload 2] [--reps 3] [--views N]
-        [--backprojector 0|1|2] [--isotropic] [--no-separable] [--unstaged]
+        [--backprojector 0|1|2] [--isotropic] [--no-separable] [--staged]
 
 OP: voxelize | voxelize_backward | project | backproject | step | net_forward |
 net_backward (the warm-start network on a --side^3 grid, default 128, with
@@ -31,7 +31,7 @@ def main(argv=None):
     ap.add_argument("--backprojector", type=int, default=0, help="0: ray scatter, 1: column gather, 2: brick scatter")
     ap.add_argument("--isotropic", action="store_true", help="one scale per Gaussian (separable FVR)")
     ap.add_argument("--no-separable", action="store_true", help="general voxelizer even when separable")
-    ap.add_argument("--unstaged", action="store_true", help="path walks without shared-memory staging")
+    ap.add_argument("--staged", action="store_true", help="path walks staged through shared memory (off by default, as in the library)")
     ap.add_argument("--side", type=int, default=128, help="network grid side")
     ap.add_argument("--conv-engine", type=int, default=2, help="2: tcgen05 halo tiles, 1: tcgen05 gathered tiles, 0: mma.sync")
     a = ap.parse_args(argv)
@@ -39,7 +39,7 @@ def main(argv=None):
         return net_case(a)
     dgr.dgr_set_backprojector(a.backprojector)
     dgr.dgr_set_separable(not a.no_separable)
-    dgr.dgr_set_staged_walk(not a.unstaged)
+    dgr.dgr_set_staged_walk(a.staged)
     wl = synth.workload(a.workload)
     geo_spec = wl.geom
     if a.views:
