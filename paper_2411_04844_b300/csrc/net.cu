@@ -512,6 +512,153 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo(const ConvArgs a) {
     }
 }
 
+// Double-buffered form: two input blocks and two accumulator sets, so the
+// MMAs of tile i run while the accumulators of tile i - 1 are drained and
+// the block of tile i + 1 is in flight.  Per iteration i: wait for tile i's
+// copies; one thread issues tile i's MMAs into accumulator set i & 1 and
+// commits them to barrier i & 1; all wait for tile i - 1's commit (its block
+// and accumulators are then free), start the copies of tile i + 1 into that
+// block, and write tile i - 1's output.
+template <int C, int N, int ZT>
+struct Halo2 {
+    using H = Halo<C, N, ZT>;
+    static constexpr unsigned HB = (H::HBYTES + 1023u) & ~1023u;  // one input block
+    static constexpr int COLS = 2 * ZT * N;
+    static constexpr unsigned NCOL = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
+    static constexpr size_t SMEM = 1024 + (size_t)H::BBYTES + 2 * (size_t)HB + 64;
+    static_assert(COLS <= 512, "accumulators exceed tensor memory");
+};
+
+template <int MODE, int C, int N, int ZT>
+__global__ void __launch_bounds__(HALO_THREADS) k_conv_halo2(const ConvArgs a) {
+    static_assert(MODE == MODE_FWD || MODE == MODE_DGRAD, "forward and data gradient only");
+    static_assert(N % 16 == 0 && N >= 16 && N <= 64 && C % 16 == 0, "tile shapes");
+    using H = Halo<C, N, ZT>;
+    using H2 = Halo2<C, N, ZT>;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned char *Bs = sm, *Hs = sm + H::BBYTES;  // blocks at Hs and Hs + HB
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(Hs + 2 * H2::HB);  // [2]
+    unsigned *tslot = reinterpret_cast<unsigned *>(bar + 2);
+
+    const int n = a.n;
+    const int w = threadIdx.x >> 5;
+    if (w == 0) {
+        tmem_alloc(tslot, H2::NCOL);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    for (int e = threadIdx.x; e < N * 27 * H::CH; e += HALO_THREADS) {
+        const int nn = e % N, kc = e / N;
+        const uint4 v = *reinterpret_cast<const uint4 *>(a.wt + (size_t)nn * 27 * C + 8 * kc);
+        *reinterpret_cast<uint4 *>(Bs + kc * H::BLEAD + (nn >> 3) * 128 + (nn & 7) * 16) = v;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tslot;
+    const unsigned hs0 = smem_u32(Hs), bs = smem_u32(Bs);
+    constexpr unsigned IDESC = idesc_bf16_f32(128, N);
+
+    const int ntx = (n + 7) / 8, nty = (n + 15) / 16, ntz = (n + ZT - 1) / ZT;
+    const int ntiles = ntx * nty * ntz;
+    const int cnt = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    auto origin = [&](int i, int &x0, int &y0, int &z0) {
+        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+        x0 = (tile % ntx) * 8;
+        y0 = ((tile / ntx) % nty) * 16;
+        z0 = (tile / (ntx * nty)) * ZT;
+    };
+    auto load = [&](int i) {
+        int x0, y0, z0;
+        origin(i, x0, y0, z0);
+        load_halo<C, H::HZ>(a.x, n, x0, y0, z0, Hs + (i & 1) * H2::HB, H::PLANE);
+        cp_async_commit();
+    };
+    // output of tile i from accumulator set i & 1: thread of row m = 32 (w % 4)
+    // + lane holds voxel (x0 + m % 8, y0 + m / 8); warps w, w ^ 4 share chunks
+    auto drain = [&](int i) {
+        int x0, y0, z0;
+        origin(i, x0, y0, z0);
+        const int q = w & 3, m = 32 * q + (threadIdx.x & 31);
+        const int x = x0 + (m & 7), y = y0 + (m >> 3);
+        const unsigned acc = tmem + (unsigned)((i & 1) * ZT * N);
+        for (int j = w >> 2; j < ZT * (N / 16); j += 2) {
+            const int zs = j / (N / 16), c0 = 16 * (j % (N / 16));
+            const int z = z0 + zs;
+            float v[16];
+            tmem_ld16(acc + ((unsigned)(32 * q) << 16) + (unsigned)(zs * N + c0), v);
+            if (x < n && y < n && z < n) store_row16<MODE>(a, ((size_t)z * n + y) * n + x, c0, v);
+        }
+    };
+    bool ok = true;
+    int issued = -1;
+    if (cnt > 0) load(0);
+    for (int i = 0; i < cnt; ++i) {
+        const int b = i & 1;
+        cp_async_wait<0>();  // tile i's block has landed
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint64_t ad0 = smem_desc(hs0 + b * H2::HB, H::PLANE, H::HX * 16),
+                           bd0 = smem_desc(bs, H::BLEAD, 128);
+            const unsigned acc = tmem + (unsigned)(b * ZT * N);
+            for (int tap = 0; tap < 27; ++tap) {
+                int dx, dy, dz;
+                tap_offset(tap, dx, dy, dz);
+                if (MODE == MODE_DGRAD) { dx = -dx; dy = -dy; dz = -dz; }
+                const uint64_t at = ad0 + (uint64_t)(((1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx);
+                const uint64_t bt = bd0 + (uint64_t)(tap * H::CH * (H::BLEAD / 16));
+#pragma unroll
+                for (int zs = 0; zs < ZT; ++zs)
+#pragma unroll
+                    for (int cp = 0; cp < H::CH; cp += 2)
+                        umma_bf16(acc + (unsigned)(zs * N), at + (uint64_t)(zs * H::HY * H::HX + cp * (H::PLANE / 16)),
+                                  bt + (uint64_t)(cp * (H::BLEAD / 16)), IDESC, (tap | cp) != 0);
+            }
+            umma_commit(&bar[b]);
+        }
+        issued = i;
+        // tile i - 1: its block and accumulators are free once its commit arrived
+        if (i >= 1 && !mbar_wait(&bar[b ^ 1], ((i - 1) >> 1) & 1, a.status)) ok = false;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        if (i + 1 < cnt) load(i + 1);
+        if (i >= 1) {
+            tc_fence_after();
+            drain(i - 1);
+        }
+        tc_fence_before();
+    }
+    // the last tile
+    if (ok && issued >= 0) {
+        if (!mbar_wait(&bar[issued & 1], (issued >> 1) & 1, a.status)) ok = false;
+        if (__syncthreads_and(ok)) {
+            tc_fence_after();
+            drain(issued);
+        } else {
+            ok = false;
+        }
+    }
+    cp_async_wait<0>();
+    // after a wait gave up: let the MMAs in flight finish (bounded) before
+    // the tensor memory is freed
+    if (!ok && issued >= 0 && threadIdx.x == 0) mbar_wait(&bar[issued & 1], (issued >> 1) & 1, a.status);
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, H2::NCOL);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Weight gradient on tcgen05 over the same halo blocks.  Per tap,
 //   dW_tap[ci][co] = sum_p X[p + tap][ci] G[p][co]
@@ -1202,12 +1349,43 @@ static bool halo(const ConvArgs &a, cudaStream_t st) {
     return true;
 }
 
+// persistent double-buffered halo-tile launch
+template <int MODE, int C, int N, int ZT>
+static bool halo2(const ConvArgs &a, cudaStream_t st) {
+    using HH = Halo2<C, N, ZT>;
+    static int per_sm = 0;  // resident CTAs per SM; -1 refused
+    static int sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_conv_halo2<MODE, C, N, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)HH::SMEM) == cudaSuccess &&
+                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_halo2<MODE, C, N, ZT>,
+                                                                HALO_THREADS, HH::SMEM) == cudaSuccess;
+        if (!ok || per_sm < 1) {
+            per_sm = -1;
+            (void)cudaGetLastError();
+        }
+    }
+    if (per_sm < 0) return false;
+    // tensor memory: at most 512 columns per SM between the resident CTAs
+    const int fit = (int)(512 / HH::NCOL);
+    const int per = per_sm < fit ? per_sm : fit;
+    const int n = a.n;
+    const long long tiles = (long long)((n + 7) / 8) * ((n + 15) / 16) * ((n + ZT - 1) / ZT);
+    const long long cap = (long long)sms * per;
+    k_conv_halo2<MODE, C, N, ZT><<<(unsigned)(tiles < cap ? tiles : cap), HALO_THREADS, HH::SMEM, st>>>(a);
+    counted(1);
+    return true;
+}
+
 template <int MODE>
 static bool halo_cn(int C, int N, const ConvArgs &a, cudaStream_t st) {
-    if (C == 16 && N == 32) return halo<MODE, 16, 32, 4>(a, st);
-    if (C == 32 && N == 64) return halo<MODE, 32, 64, 4>(a, st);
-    if (C == 64 && N == 32) return halo<MODE, 64, 32, 2>(a, st);
-    if (C == 32 && N == 16) return halo<MODE, 32, 16, 4>(a, st);
+    if (C == 16 && N == 32) return halo2<MODE, 16, 32, 4>(a, st);
+    if (C == 32 && N == 64) return halo2<MODE, 32, 64, 2>(a, st);
+    if (C == 64 && N == 32) return halo<MODE, 64, 32, 2>(a, st);  // two blocks do not fit next to B
+    if (C == 32 && N == 16) return halo2<MODE, 32, 16, 4>(a, st);
     return false;
 }
 
