@@ -548,9 +548,11 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo2(const ConvArgs a) {
         tmem_alloc(tslot, H2::NCOL);
         tmem_relinquish();
     }
+    // one MMA issuer per output slice (lane 0 of warp zs): each commit is one
+    // arrival, the barrier completes when all ZT slices' MMAs have
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&bar[0], ZT);
+        mbar_init(&bar[1], ZT);
         fence_barrier_init();
     }
     for (int e = threadIdx.x; e < N * 27 * H::CH; e += HALO_THREADS) {
@@ -606,11 +608,13 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo2(const ConvArgs a) {
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if ((threadIdx.x & 31) == 0 && w < ZT) {
+            const int zs = w;
             tc_fence_after();
-            const uint64_t ad0 = smem_desc(hs0 + b * H2::HB, H::PLANE, H::HX * 16),
+            const uint64_t ad0 = smem_desc(hs0 + b * H2::HB, H::PLANE, H::HX * 16) +
+                                 (uint64_t)(zs * H::HY * H::HX),
                            bd0 = smem_desc(bs, H::BLEAD, 128);
-            const unsigned acc = tmem + (unsigned)(b * ZT * N);
+            const unsigned acc = tmem + (unsigned)(b * ZT * N + zs * N);
             for (int tap = 0; tap < 27; ++tap) {
                 int dx, dy, dz;
                 tap_offset(tap, dx, dy, dz);
@@ -618,11 +622,9 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo2(const ConvArgs a) {
                 const uint64_t at = ad0 + (uint64_t)(((1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx);
                 const uint64_t bt = bd0 + (uint64_t)(tap * H::CH * (H::BLEAD / 16));
 #pragma unroll
-                for (int zs = 0; zs < ZT; ++zs)
-#pragma unroll
-                    for (int cp = 0; cp < H::CH; cp += 2)
-                        umma_bf16(acc + (unsigned)(zs * N), at + (uint64_t)(zs * H::HY * H::HX + cp * (H::PLANE / 16)),
-                                  bt + (uint64_t)(cp * (H::BLEAD / 16)), IDESC, (tap | cp) != 0);
+                for (int cp = 0; cp < H::CH; cp += 2)
+                    umma_bf16(acc, at + (uint64_t)(cp * (H::PLANE / 16)), bt + (uint64_t)(cp * (H::BLEAD / 16)),
+                              IDESC, (tap | cp) != 0);
             }
             umma_commit(&bar[b]);
         }
@@ -712,9 +714,12 @@ __global__ void __launch_bounds__(HALO_THREADS) k_wgrad_halo(const ConvArgs a, i
         tmem_alloc(tslot, NCOL);
         tmem_relinquish();
     }
+    // MMA issuers: lane 0 of warps 0 .. NI - 1, warp w taking taps w, w + NI, ..;
+    // each commit is one arrival
+    const int NI = min(HALO_THREADS / 32, ntap);
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&bar[0], NI);
+        mbar_init(&bar[1], NI);
         fence_barrier_init();
     }
     tc_fence_before();
@@ -763,13 +768,13 @@ __global__ void __launch_bounds__(HALO_THREADS) k_wgrad_halo(const ConvArgs a, i
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if ((threadIdx.x & 31) == 0 && w < NI) {
             tc_fence_after();
             const unsigned gs = base + b * W::BUF, hs = gs + W::GREAL;
             // descriptors built once; taps, slices and line pairs move the
             // start address field only (16-byte units, no carry)
             const uint64_t ad0 = smem_desc(gs, 128, W::GPLANE), bd0 = smem_desc(hs, H::HX * 16, H::PLANE);
-            for (int j = 0; j < ntap; ++j) {
+            for (int j = w; j < ntap; j += NI) {
                 int dx, dy, dz;
                 tap_offset(tap0 + j, dx, dy, dz);
                 const uint64_t bt = bd0 + (uint64_t)(((1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx);
