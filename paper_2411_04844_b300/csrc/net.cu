@@ -396,8 +396,9 @@ __device__ __forceinline__ void load_halo(const bf16 *__restrict__ x, int n, int
     }
 }
 
-template <int C, int N, int ZT>
-struct Halo {
+// the input block of an 8 x 16 x ZT tile with its one-voxel halo, C channels
+template <int C, int ZT>
+struct HaloBlock {
     static constexpr int HX = 10, HY = 18, HZ = ZT + 2;
     static constexpr int CH = C / 8;  // 16-byte chunks per voxel
     // chunk-plane pitch in 16-byte slots, padded to (8 / CH) mod 8 so the CH
@@ -406,19 +407,31 @@ struct Halo {
     static constexpr unsigned BASE16 = (unsigned)HX * HY * HZ;
     static constexpr unsigned PLANE = 16u * (BASE16 + (8u + (unsigned)(8 / CH) - BASE16 % 8u) % 8u);
     static constexpr unsigned HBYTES = PLANE * CH;
+    static_assert(PLANE % 16 == 0 && (PLANE >> 4) < 16384, "descriptor field");
+};
+
+// forward / data gradient: the block plus the packed weights B [N][27 C]
+template <int C, int N, int ZT>
+struct Halo : HaloBlock<C, ZT> {
+    using HaloBlock<C, ZT>::CH;
+    using HaloBlock<C, ZT>::HBYTES;
     static constexpr unsigned BLEAD = (unsigned)N * 16;  // K-chunk pitch of B
     static constexpr unsigned BBYTES = (unsigned)27 * CH * BLEAD;
+};
+
+// single-buffered kernel: B, one block, one accumulator set
+template <int C, int N, int ZT>
+struct Halo1 : Halo<C, N, ZT> {
     static constexpr unsigned NCOL = ZT * N <= 32 ? 32 : (ZT * N <= 64 ? 64 : (ZT * N <= 128 ? 128 : 256));
-    static constexpr size_t SMEM = 1024 + (size_t)BBYTES + HBYTES + 64;
+    static constexpr size_t SMEM = 1024 + (size_t)Halo<C, N, ZT>::BBYTES + Halo<C, N, ZT>::HBYTES + 64;
     static_assert(ZT * N <= 256, "accumulators exceed the tensor-memory allocation");
-    static_assert(PLANE % 16 == 0 && (PLANE >> 4) < 16384, "descriptor field");
 };
 
 template <int MODE, int C, int N, int ZT>
 __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo(const ConvArgs a) {
     static_assert(MODE == MODE_FWD || MODE == MODE_DGRAD, "forward and data gradient only");
     static_assert(N % 16 == 0 && N >= 16 && N <= 64 && C % 16 == 0, "tile shapes");
-    using H = Halo<C, N, ZT>;
+    using H = Halo1<C, N, ZT>;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
@@ -432,8 +445,9 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo(const ConvArgs a) {
         tmem_alloc(tslot, H::NCOL);
         tmem_relinquish();
     }
+    // one MMA issuer per output slice (lane 0 of warp zs), one arrival each
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        mbar_init(bar, ZT);
         fence_barrier_init();
     }
     // B: the packed weights [N][27 C] (K-major rows) as core matrices
@@ -463,12 +477,14 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo(const ConvArgs a) {
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if ((threadIdx.x & 31) == 0 && w < ZT) {
+            const int zs = w;
             tc_fence_after();
-            // descriptors built once; a tap, slice or chunk moves the start
-            // address field only (offsets in 16-byte units, no carry: shared
+            // descriptors built once; a tap or chunk moves the start address
+            // field only (offsets in 16-byte units, no carry: shared
             // addresses stay below 2^18)
-            const uint64_t ad0 = smem_desc(hs, H::PLANE, H::HX * 16), bd0 = smem_desc(bs, H::BLEAD, 128);
+            const uint64_t ad0 = smem_desc(hs, H::PLANE, H::HX * 16) + (uint64_t)(zs * H::HY * H::HX),
+                           bd0 = smem_desc(bs, H::BLEAD, 128);
             for (int tap = 0; tap < 27; ++tap) {
                 int dx, dy, dz;
                 tap_offset(tap, dx, dy, dz);
@@ -476,11 +492,9 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo(const ConvArgs a) {
                 const uint64_t at = ad0 + (uint64_t)(((1 + dz) * H::HY + 1 + dy) * H::HX + 1 + dx);
                 const uint64_t bt = bd0 + (uint64_t)(tap * H::CH * (H::BLEAD / 16));
 #pragma unroll
-                for (int zs = 0; zs < ZT; ++zs)
-#pragma unroll
-                    for (int cp = 0; cp < H::CH; cp += 2)
-                        umma_bf16(tmem + (unsigned)(zs * N), at + (uint64_t)(zs * H::HY * H::HX + cp * (H::PLANE / 16)),
-                                  bt + (uint64_t)(cp * (H::BLEAD / 16)), IDESC, (tap | cp) != 0);
+                for (int cp = 0; cp < H::CH; cp += 2)
+                    umma_bf16(tmem + (unsigned)(zs * N), at + (uint64_t)(cp * (H::PLANE / 16)),
+                              bt + (uint64_t)(cp * (H::BLEAD / 16)), IDESC, (tap | cp) != 0);
             }
             umma_commit(bar);
         }
@@ -680,7 +694,7 @@ __global__ void __launch_bounds__(HALO_THREADS) k_conv_halo2(const ConvArgs a) {
 // ---------------------------------------------------------------------------
 template <int CI, int CO, int ZT>
 struct WgHalo {
-    using H = Halo<CI, 16, ZT>;  // the X block of the forward kernels (N unused)
+    using H = HaloBlock<CI, ZT>;  // the X block of the forward kernels
     static constexpr unsigned GPLANE = 8u * 16 * ZT * 16;  // bytes of one G channel plane
     static constexpr unsigned GREAL = (CO / 8) * GPLANE;    // the CO / 8 planes that are loaded
     // one buffer: G planes, then the X block; two buffers (double buffering)
@@ -1329,7 +1343,7 @@ static bool umma(const ConvArgs &a, long long rows, cudaStream_t st) {
 // persistent halo-tile launch: as many CTAs as fit on the device at once
 template <int MODE, int C, int N, int ZT>
 static bool halo(const ConvArgs &a, cudaStream_t st) {
-    using HH = Halo<C, N, ZT>;
+    using HH = Halo1<C, N, ZT>;
     static int per_sm = 0;  // resident CTAs per SM; -1 refused
     static int sms = 0;
     if (per_sm == 0) {
