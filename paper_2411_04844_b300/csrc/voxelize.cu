@@ -366,10 +366,12 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 sp[i] = reinterpret_cast<const float4 *>(prep + gi)[i & 3];
             }
             __syncthreads();
-            // the chunk's plain sums; a z outside a box contributes exp2(-inf) = 0
-            float cs[TZ];
+            // the chunk's plain sums, z pairs in packed FP32 (each half rounds
+            // exactly as the scalar FMA); a z outside a box contributes
+            // exp2(-inf) = 0
+            float2 cs[TZ / 2];
 #pragma unroll
-            for (int k = 0; k < TZ; ++k) cs[k] = 0.f;
+            for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(0.f, 0.f);
             for (int j = 0; j < nc; ++j) {
                 const float4 p3 = sp[4 * j + 3];
                 const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z),
@@ -389,25 +391,28 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 C = in ? C : -INFINITY;
                 const float Lz = fmaf(p2.x, dx, p2.y * dy);
                 const float dz0 = (float)(z0 - az) - p0.z;
-                const float a22 = p1.z, r = p0.w;
+                const float2 a22v = make_float2(p1.z, p1.z), Lzv = make_float2(Lz, Lz), Cv = make_float2(C, C),
+                             rv = make_float2(p0.w, p0.w);
 #pragma unroll
                 for (int g8 = 0; g8 < TZ / TZG; ++g8) {
                     if (zhi < g8 * TZG || zlo >= (g8 + 1) * TZG) continue;  // warp-uniform
                     if (zlo <= g8 * TZG && zhi >= (g8 + 1) * TZG - 1) {       // whole group in the box
 #pragma unroll
-                        for (int kk = 0; kk < TZG; ++kk) {
+                        for (int kk = 0; kk < TZG; kk += 2) {
                             const int k = g8 * TZG + kk;
-                            const float dz = dz0 + (float)k;
-                            cs[k] = fmaf(r, ex2_approx(fmaf(dz, fmaf(a22, dz, Lz), C)), cs[k]);
+                            const float2 dz = make_float2(dz0 + (float)k, dz0 + (float)(k + 1));
+                            const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
+                            cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
                         }
                     } else {
 #pragma unroll
-                        for (int kk = 0; kk < TZG; ++kk) {
+                        for (int kk = 0; kk < TZG; kk += 2) {
                             const int k = g8 * TZG + kk;
-                            const float dz = dz0 + (float)k;
-                            const float qf = fmaf(dz, fmaf(a22, dz, Lz), C);
-                            const float e2 = ex2_approx((k >= zlo && k <= zhi) ? qf : -INFINITY);
-                            cs[k] = fmaf(r, e2, cs[k]);
+                            const float2 dz = make_float2(dz0 + (float)k, dz0 + (float)(k + 1));
+                            const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
+                            const float e0 = ex2_approx((k >= zlo && k <= zhi) ? q.x : -INFINITY);
+                            const float e1 = ex2_approx((k + 1 >= zlo && k + 1 <= zhi) ? q.y : -INFINITY);
+                            cs[k / 2] = __ffma2_rn(rv, make_float2(e0, e1), cs[k / 2]);
                         }
                     }
                 }
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
             // ulps of the exact sum
 #pragma unroll
             for (int k = 0; k < TZ; ++k) {
-                const float yv = cs[k] - cmp[k];
+                const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - cmp[k];
                 const float tsum = acc[k] + yv;
                 cmp[k] = (tsum - acc[k]) - yv;
                 acc[k] = tsum;

@@ -76,7 +76,10 @@ __global__ void __launch_bounds__(256) k_bwd_items(
             const float Lz = fmaf(P.a02, dx, P.a12 * dy);
             const float *col = gv + ((size_t)zb * g.ny + yy) * g.nx + xx;
             const size_t zs = (size_t)g.nx * g.ny;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            // the column's sums over z of ge, ge dz, ge dz^2 (ge = G_V e), in two
+            // packed FP32 lanes (even and odd layers of each group of four)
+            const float2 a22v = make_float2(P.a22, P.a22), Lzv = make_float2(Lz, Lz), Cv = make_float2(C, C);
+            float2 s0v = make_float2(0.f, 0.f), s1v = s0v, s2v = s0v;
             int z = zb;
             // four layers at a time: loads first, then the arithmetic
             for (; z + 3 <= ze; z += 4) {
@@ -85,14 +88,15 @@ __global__ void __launch_bounds__(256) k_bwd_items(
                 for (int u = 0; u < 4; ++u) gz[u] = __ldg(col + u * zs);
                 col += 4 * zs;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float dz = dz0 + (float)(z + u - zb);
-                    const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
-                    const float ge = gz[u] * e;
-                    s0 += ge;
-                    const float t = ge * dz;
-                    s1 += t;
-                    s2 = fmaf(t, dz, s2);
+                for (int u = 0; u < 4; u += 2) {
+                    const float2 dz = make_float2(dz0 + (float)(z + u - zb), dz0 + (float)(z + u + 1 - zb));
+                    const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
+                    const float2 ge = __fmul2_rn(make_float2(gz[u], gz[u + 1]),
+                                                 make_float2(ex2_approx(q.x), ex2_approx(q.y)));
+                    s0v = __fadd2_rn(s0v, ge);
+                    const float2 t = __fmul2_rn(ge, dz);
+                    s1v = __fadd2_rn(s1v, t);
+                    s2v = __ffma2_rn(t, dz, s2v);
                 }
             }
             for (; z <= ze; ++z) {
@@ -100,11 +104,12 @@ __global__ void __launch_bounds__(256) k_bwd_items(
                 const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
                 const float ge = __ldg(col) * e;
                 col += zs;
-                s0 += ge;
+                s0v.x += ge;
                 const float t = ge * dz;
-                s1 += t;
-                s2 = fmaf(t, dz, s2);
+                s1v.x += t;
+                s2v.x = fmaf(t, dz, s2v.x);
             }
+            const float s0 = s0v.x + s0v.y, s1 = s1v.x + s1v.y, s2 = s2v.x + s2v.y;
             m[0] += s0;
             m[1] = fmaf(dx, s0, m[1]);
             m[2] = fmaf(dy, s0, m[2]);
