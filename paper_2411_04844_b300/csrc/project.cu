@@ -282,12 +282,12 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
         } else {
 #pragma unroll
             for (int j = 0; j < WALK; ++j) {
-                // without a crossing the second segment is empty and names the same voxel
+                // without a crossing the second segment is empty (q1 = 0): one
+                // reduction; integer sums do not depend on how they are split
                 const float2 lw = __fmul2_rn(make_float2(l0[j], l1[j]), make_float2(wq, wq));
                 const int q0 = __float2int_rn(lw.x), q1 = __float2int_rn(lw.y);
-                const bool same = a1[j] == a0[j];
-                atomicAdd(acci + a0[j], same ? q0 + q1 : q0);
-                if (!same) atomicAdd(acci + a1[j], q1);
+                atomicAdd(acci + a0[j], q0);
+                if (q1 != 0) atomicAdd(acci + a1[j], q1);
             }
         }
     }
