@@ -14,6 +14,8 @@
 // through u = (mu - o)/h - 1/2 and A = h^2 R(q/|q|) diag(s^-2) R^T.
 #include <math.h>
 
+#include <type_traits>
+
 #include "dgr_internal.cuh"
 
 namespace dgr {
@@ -81,14 +83,15 @@ __global__ void __launch_bounds__(256) k_bwd_items(
             const float2 a22v = make_float2(P.a22, P.a22), Lzv = make_float2(Lz, Lz), Cv = make_float2(C, C);
             float2 s0v = make_float2(0.f, 0.f), s1v = s0v, s2v = s0v;
             int z = zb;
-            // four layers at a time: loads first, then the arithmetic
-            for (; z + 3 <= ze; z += 4) {
-                float gz[4];
+            // U layers at a time (8, then 4): loads first, then the arithmetic
+            auto layers = [&](auto U_) {
+                constexpr int U = decltype(U_)::value;
+                float gz[U];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) gz[u] = __ldg(col + u * zs);
-                col += 4 * zs;
+                for (int u = 0; u < U; ++u) gz[u] = __ldg(col + u * zs);
+                col += U * zs;
 #pragma unroll
-                for (int u = 0; u < 4; u += 2) {
+                for (int u = 0; u < U; u += 2) {
                     const float2 dz = make_float2(dz0 + (float)(z + u - zb), dz0 + (float)(z + u + 1 - zb));
                     const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
                     const float2 ge = __fmul2_rn(make_float2(gz[u], gz[u + 1]),
@@ -98,7 +101,10 @@ __global__ void __launch_bounds__(256) k_bwd_items(
                     s1v = __fadd2_rn(s1v, t);
                     s2v = __ffma2_rn(t, dz, s2v);
                 }
-            }
+                z += U;
+            };
+            while (z + 7 <= ze) layers(std::integral_constant<int, 8>());
+            if (z + 3 <= ze) layers(std::integral_constant<int, 4>());
             for (; z <= ze; ++z) {
                 const float dz = dz0 + (float)(z - zb);
                 const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
