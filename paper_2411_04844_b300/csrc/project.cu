@@ -247,7 +247,11 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
                                            float xi0z, float iez) {
     const unsigned zmax = (unsigned)(nz - 1);
     const int zl = STAGED ? G.zlo : 0, zh = STAGED ? G.zhi : nz - 1;
-    int zc = min(max(iz, zl), zh);
+    // the layer the addresses use: clamped into the volume (unstaged: one
+    // unsigned min -- a lane below the volume is clamped to the top layer,
+    // harmless since its masked segments have zero length) or the window
+    auto layer = [&](int i) { return STAGED ? min(max(i, zl), zh) : (int)min((unsigned)i, zmax); };
+    int zc = layer(iz);
     const float fsg = (float)sgz;
     for (int r = r0; r < r1; r += WALK) {
         float l0[WALK], l1[WALK];
@@ -264,7 +268,7 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
                 iz += sgz;
                 fz += fsg;
                 tz = (fz - xi0z) * iez;
-                zc = min(max(iz, zl), zh);
+                zc = layer(iz);
             }
             l1[j] = (!MASKZ || (unsigned)iz <= zmax) ? fminf(tz, t1) - m : 0.f;
             a1[j] = base + zc;
