@@ -239,7 +239,7 @@ struct Stage {
 // Fast walk for geometries where no ray crosses two z planes inside one
 // (x, y) cell (sqrt(2) max|e_z| / min|e_xy| < 1 with margin; checked on the
 // host): the crossing is a predicated update and the second segment's length
-// is min(tz, t1) - min(tz_before, t1), zero when nothing was crossed.
+// is t1 - min(tz_before, t1), zero when nothing was crossed.
 template <int MODE, bool MASKZ, bool STAGED>
 __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *__restrict__ acci, float wq,
                                            const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
@@ -270,7 +270,9 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
                 tz = (fz - xi0z) * iez;
                 zc = layer(iz);
             }
-            l1[j] = (!MASKZ || (unsigned)iz <= zmax) ? fminf(tz, t1) - m : 0.f;
+            // at most one z crossing per cell: the next one lies beyond t1, so
+            // the second segment is t1 - m (zero without a crossing)
+            l1[j] = (!MASKZ || (unsigned)iz <= zmax) ? t1 - m : 0.f;
             a1[j] = base + zc;
             t = t1;
         }
