@@ -179,7 +179,7 @@ __device__ __forceinline__ int entry_cell(float tmin, float e, float xi0, float 
 constexpr int PR_THREADS = 256;
 constexpr int PR_ROWS = PR_THREADS;
 constexpr int SEG_MAX = 2048;  // path segments staged per round
-constexpr int WALK = 4;
+constexpr int WALK = 4;  // segments per unrolled group (at most; the scatter walks 2 at a time)
 
 struct __align__(8) Seg {
     float t1;  // end of the segment (the crossing that leaves its cell)
@@ -245,6 +245,9 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
                                            const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
                                            float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
                                            float xi0z, float iez) {
+    // segments per unrolled group: 4 loads in flight for the projector; the
+    // scatter keeps 2 (fewer registers, more resident warps)
+    constexpr int NW = MODE == 0 ? WALK : 2;
     const unsigned zmax = (unsigned)(nz - 1);
     const int zl = STAGED ? G.zlo : 0, zh = STAGED ? G.zhi : nz - 1;
     // the layer the addresses use: clamped into the volume (unstaged: one
@@ -253,11 +256,11 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
     auto layer = [&](int i) { return STAGED ? min(max(i, zl), zh) : (int)min((unsigned)i, zmax); };
     int zc = layer(iz);
     const float fsg = (float)sgz;
-    for (int r = r0; r < r1; r += WALK) {
-        float l0[WALK], l1[WALK];
-        int a0[WALK], a1[WALK];
+    for (int r = r0; r < r1; r += NW) {
+        float l0[NW], l1[NW];
+        int a0[NW], a1[NW];
 #pragma unroll
-        for (int j = 0; j < WALK; ++j) {
+        for (int j = 0; j < NW; ++j) {
             const Seg S = seg[r + j - c0];  // past the round's end: padding, empty segments
             const int base = STAGED ? min(r + j - G.s0, G.nslot - 1) * G.zspan - G.zlo : S.cb;
             const float t1 = S.t1;
@@ -277,17 +280,17 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
             t = t1;
         }
         if (MODE == 0) {
-            float v0[WALK], v1[WALK];
+            float v0[NW], v1[NW];
 #pragma unroll
-            for (int j = 0; j < WALK; ++j) {
+            for (int j = 0; j < NW; ++j) {
                 v0[j] = STAGED ? vol[a0[j]] : __ldg(vol + a0[j]);
                 v1[j] = STAGED ? vol[a1[j]] : __ldg(vol + a1[j]);
             }
 #pragma unroll
-            for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
+            for (int j = 0; j < NW; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
         } else {
 #pragma unroll
-            for (int j = 0; j < WALK; ++j) {
+            for (int j = 0; j < NW; ++j) {
                 // without a crossing the second segment is empty (q1 = 0): one
                 // reduction; integer sums do not depend on how they are split
                 const float2 lw = __fmul2_rn(make_float2(l0[j], l1[j]), make_float2(wq, wq));
@@ -306,15 +309,18 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
                                           const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
                                           float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
                                           float xi0z, float iez) {
+    // segments per unrolled group: 4 loads in flight for the projector; the
+    // scatter keeps 2 (fewer registers, more resident warps)
+    constexpr int NW = MODE == 0 ? WALK : 2;
     const unsigned zmax = (unsigned)(nz - 1);
     const int zl = STAGED ? G.zlo : 0, zh = STAGED ? G.zhi : nz - 1;
     int zc = min(max(iz, zl), zh);
     const float fsg = (float)sgz;
-    for (int r = r0; r < r1; r += WALK) {
-        float l0[WALK], l1[WALK];
-        int a0[WALK], a1[WALK];
+    for (int r = r0; r < r1; r += NW) {
+        float l0[NW], l1[NW];
+        int a0[NW], a1[NW];
 #pragma unroll
-        for (int j = 0; j < WALK; ++j) {
+        for (int j = 0; j < NW; ++j) {
             const Seg S = seg[r + j - c0];  // past the round's end: padding, empty segments
             const int base = STAGED ? min(r + j - G.s0, G.nslot - 1) * G.zspan - G.zlo : S.cb;
             const float t1 = S.t1;
@@ -351,17 +357,17 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
             t = t1;
         }
         if (MODE == 0) {
-            float v0[WALK], v1[WALK];
+            float v0[NW], v1[NW];
 #pragma unroll
-            for (int j = 0; j < WALK; ++j) {
+            for (int j = 0; j < NW; ++j) {
                 v0[j] = STAGED ? vol[a0[j]] : __ldg(vol + a0[j]);
                 v1[j] = STAGED ? vol[a1[j]] : __ldg(vol + a1[j]);
             }
 #pragma unroll
-            for (int j = 0; j < WALK; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
+            for (int j = 0; j < NW; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
         } else {
 #pragma unroll
-            for (int j = 0; j < WALK; ++j) {
+            for (int j = 0; j < NW; ++j) {
                 if (l0[j] != 0.f) atomicAdd(acci + a0[j], __float2int_rn(l0[j] * wq));
                 if (l1[j] != 0.f) atomicAdd(acci + a1[j], __float2int_rn(l1[j] * wq));
             }
