@@ -203,11 +203,15 @@ __device__ __forceinline__ int count_before(float T, int n, int p0, int sg, floa
 // of two S with VGROUP x col_u x col_v x (longest chord in t units) x
 // max |scaled residual| x S < 2^30, so that a voxel's integer sum over the
 // group cannot overflow (a voxel meets at most col_u x col_v rays per view).
-// Returns 0 if a residual of the group is not finite.
+// Returns 0 if a residual of the group is not finite.  Called by whole warps
+// (converged): the lanes share the maximum over the group's views.
 constexpr int VGROUP = 64;
+constexpr int FOLD_Y = 4;  // y rows of 32 x 32 (x, z) tiles per CTA of k_bp_fold
 __device__ __forceinline__ float group_step(const Inst &I, const unsigned *view_max, int kv0, int nkv) {
     unsigned m = 0u;
-    for (int j = 0; j < nkv; ++j) m = max(m, view_max[I.view0 + kv0 + j]);
+    for (int j = threadIdx.x & 31; j < nkv; j += 32) m = max(m, view_max[I.view0 + kv0 + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     const float amax = __uint_as_float(m);
     if (!(amax <= 3.0e38f)) return 0.f;
     // longest chord of a voxel in t units: sqrt(3) h / |D|, |D| >= dsd (cone) or 1 (parallel)
@@ -637,28 +641,31 @@ __global__ void k_bp_fold(const __grid_constant__ Batch B, const unsigned *__res
     const Inst &I = B.in[ii];
     if (I.nkv <= 0) return;
     const dgr_grid &g = I.g;
-    const int ntx = (g.nx + 31) / 32, ntz = (g.nz + 31) / 32;
+    const int ntx = (g.nx + 31) / 32, nty = (g.ny + FOLD_Y - 1) / FOLD_Y, ntz = (g.nz + 31) / 32;
     const int b = blockIdx.x - I.fb0;
-    const int bx = b % ntx, y = (b / ntx) % g.ny, bzt = b / (ntx * g.ny);
+    const int bx = b % ntx, by = (b / ntx) % nty, bzt = b / (ntx * nty);
     if (bzt >= ntz) return;
     const float S = group_step(I, view_max, I.kv0, I.nkv);
     const float inv_s = S > 0.f ? 1.f / S : 0.f;  // a power of two: exact
     const int x0 = bx * 32, z0 = bzt * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-    for (int j = ty; j < 32; j += 8) {  // read along z
-        const int x = x0 + j, z = z0 + tx;
-        if (x < g.nx && z < g.nz) {
-            int *p = I.acc + ((size_t)x * g.ny + y) * g.nz + z;
-            tile[j][tx] = S > 0.f ? (float)*p * inv_s : NAN;
-            *p = 0;
+    for (int y = by * FOLD_Y; y < min(g.ny, (by + 1) * FOLD_Y); ++y) {  // CTA-uniform
+        __syncthreads();  // the previous row's readers of the tile are done
+        for (int j = ty; j < 32; j += 8) {  // read along z
+            const int x = x0 + j, z = z0 + tx;
+            if (x < g.nx && z < g.nz) {
+                int *p = I.acc + ((size_t)x * g.ny + y) * g.nz + z;
+                tile[j][tx] = S > 0.f ? (float)*p * inv_s : NAN;
+                *p = 0;
+            }
         }
-    }
-    __syncthreads();
-    for (int j = ty; j < 32; j += 8) {  // write along x
-        const int z = z0 + j, x = x0 + tx;
-        if (x < g.nx && z < g.nz) {
-            float *q = I.gvol + ((size_t)z * g.ny + y) * g.nx + x;
-            *q = I.kv0 == 0 ? tile[tx][j] : *q + tile[tx][j];
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {  // write along x
+            const int z = z0 + j, x = x0 + tx;
+            if (x < g.nx && z < g.nz) {
+                float *q = I.gvol + ((size_t)z * g.ny + y) * g.nx + x;
+                *q = I.kv0 == 0 ? tile[tx][j] : *q + tile[tx][j];
+            }
         }
     }
 }
@@ -1391,7 +1398,7 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
             I.pb0 = pb;
             pb += I.nkv * I.nu * I.npv;
             I.fb0 = fb;
-            if (I.nkv > 0) fb += ((I.g.nx + 31) / 32) * I.g.ny * ((I.g.nz + 31) / 32);
+            if (I.nkv > 0) fb += ((I.g.nx + 31) / 32) * ((I.g.ny + FOLD_Y - 1) / FOLD_Y) * ((I.g.nz + 31) / 32);
         }
         if (pb > 0) {
             const int smem = staging(B, status);
