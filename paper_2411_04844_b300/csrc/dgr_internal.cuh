@@ -267,7 +267,7 @@ int backprojector_variant();
 void set_backprojector_variant(int v);
 
 // step.cu
-constexpr int L1_BLOCKS = 148;  // per instance; fixed so the loss reduction order is fixed
+constexpr int L1_BLOCKS = 148 * 8;  // per instance (8 per SM); fixed so the loss reduction order is fixed
 cudaError_t launch_l1(const Batch &B, float *part, const float *gadd, cudaStream_t st);
 cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float *resid,
                              float *loss, float *part, cudaStream_t st);

@@ -24,6 +24,7 @@ __device__ __forceinline__ float l1_block(const float *pred, const float *meas, 
     __shared__ float ws[L1_THREADS / 32];
     const float wm = (float)((double)w / (double)m);
     float s = 0.f;
+#pragma unroll 4
     for (long long i = (long long)blk * L1_THREADS + threadIdx.x; i < m;
          i += (long long)nblk * L1_THREADS) {
         const float d = pred[i] - meas[i];
