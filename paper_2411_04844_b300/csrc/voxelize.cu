@@ -505,9 +505,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
                 ez[j][k] = (z >= box_lo(bz) && z <= box_hi(bz)) ? ex2_approx(p1.z * dz * dz) : 0.f;
             }
             __syncthreads();
-            float cs[SEP_TZ];
+            float2 cs[SEP_TZ / 2];  // z pairs in packed FP32 (each half as the scalar FMA)
 #pragma unroll
-            for (int k = 0; k < SEP_TZ; ++k) cs[k] = 0.f;
+            for (int k = 0; k < SEP_TZ / 2; ++k) cs[k] = make_float2(0.f, 0.f);
             for (int j = 0; j < nc; ++j) {
                 const float4 p3 = sp[4 * j + 3];
                 const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z), bz = __float_as_int(p3.w);
@@ -526,19 +526,16 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
                 for (int g8 = 0; g8 < SEP_TZ / 8; ++g8) {
                     if (zhi < g8 * 8 || zlo >= (g8 + 1) * 8) continue;  // warp-uniform
                     const float4 u = e4[2 * g8], v = e4[2 * g8 + 1];
-                    cs[8 * g8 + 0] = fmaf(a, u.x, cs[8 * g8 + 0]);
-                    cs[8 * g8 + 1] = fmaf(a, u.y, cs[8 * g8 + 1]);
-                    cs[8 * g8 + 2] = fmaf(a, u.z, cs[8 * g8 + 2]);
-                    cs[8 * g8 + 3] = fmaf(a, u.w, cs[8 * g8 + 3]);
-                    cs[8 * g8 + 4] = fmaf(a, v.x, cs[8 * g8 + 4]);
-                    cs[8 * g8 + 5] = fmaf(a, v.y, cs[8 * g8 + 5]);
-                    cs[8 * g8 + 6] = fmaf(a, v.z, cs[8 * g8 + 6]);
-                    cs[8 * g8 + 7] = fmaf(a, v.w, cs[8 * g8 + 7]);
+                    const float2 av = make_float2(a, a);
+                    cs[4 * g8 + 0] = __ffma2_rn(av, make_float2(u.x, u.y), cs[4 * g8 + 0]);
+                    cs[4 * g8 + 1] = __ffma2_rn(av, make_float2(u.z, u.w), cs[4 * g8 + 1]);
+                    cs[4 * g8 + 2] = __ffma2_rn(av, make_float2(v.x, v.y), cs[4 * g8 + 2]);
+                    cs[4 * g8 + 3] = __ffma2_rn(av, make_float2(v.z, v.w), cs[4 * g8 + 3]);
                 }
             }
 #pragma unroll
             for (int k = 0; k < SEP_TZ; ++k) {  // Kahan: chunk sum into the running sum
-                const float yv = cs[k] - cmp[k];
+                const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - cmp[k];
                 const float tsum = acc[k] + yv;
                 cmp[k] = (tsum - acc[k]) - yv;
                 acc[k] = tsum;
