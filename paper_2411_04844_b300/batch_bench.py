@@ -1,6 +1,7 @@
 """Batched reconstructions vs sequential plain runs (one B300).
 
     python -m paper_2411_04844_b300.batch_bench [--inst 16] [--steps 10] [--warmup 3]
+        [--sizes 64 128 192 256] [--n-range 5000 200000]
 
 16 independent reconstructions (synth.batched_workload: grids of 64^3 ..
 256^3, 5K..200K Gaussians, 25..100 cone-beam views, detector N x N): one
@@ -66,9 +67,13 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--sizes", type=int, nargs="+", default=[64, 128, 192, 256],
+                    help="grid sides the instances draw from")
+    ap.add_argument("--n-range", type=int, nargs=2, default=[5000, 200000],
+                    help="Gaussian counts, log-uniform")
     a = ap.parse_args(argv)
     dev = "cuda"
-    insts = synth.batched_workload(a.inst)
+    insts = synth.batched_workload(a.inst, sizes=tuple(a.sizes), n_range=tuple(a.n_range))
     B = build(insts, dev)
     n_inst = len(insts)
     loss = torch.zeros(n_inst, device=dev)
