@@ -235,6 +235,40 @@ def test_project_and_backproject_parity(case):
     assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs))
 
 
+@pytest.mark.parametrize("variant", [0, 2])
+def test_backproject_several_view_groups(variant):
+    """150 views: the fixed-point scatters run three groups of views (64, 64,
+    22), each with its own step from its own largest residual (the residual
+    scale differs by 10^4 between groups), and the fold adds the groups."""
+    gs = synth.GridSpec((32, 28, 24), 1.0, (-16.0, -14.0, -12.0))
+    geo = synth.cone_geom(150, 40, 32, 1.5, 1.5, 300.0, 450.0)
+    y = np.random.default_rng(19).standard_normal(geo.shape).astype(np.float32)
+    y[64:128] *= 1e-4
+    y[128:] *= 30.0
+    grid = dgr.Grid.of(gs)
+    ang = T(geo.angles)
+    gg = dgr.Geom.of(geo, ang)
+    ws = dgr.Workspace(dgr.make_plan(grid, 0, 0, 0, gg))
+    try:
+        dgr.dgr_set_backprojector(variant)
+        a = torch.empty(gs.shape, device=DEV)
+        dgr.dgr_backproject(grid, gg, T(y), a, ws)
+        torch.cuda.synchronize()
+        assert dgr.dgr_status(ws) == 0
+    finally:
+        dgr.dgr_set_backprojector(0)
+    bo = O.backproject(oracle_grid(gs), oracle_geom(geo), y)
+    assert rel_l2(H(a), bo) <= 1e-5, rel_l2(H(a), bo)
+    # the small group alone is still resolved (its own step)
+    b = torch.empty(gs.shape, device=DEV)
+    ymid = np.zeros_like(y)
+    ymid[64:128] = y[64:128]
+    dgr.dgr_backproject(grid, gg, T(ymid), b, ws)
+    torch.cuda.synchronize()
+    bmid = O.backproject(oracle_grid(gs), oracle_geom(geo), ymid)
+    assert rel_l2(H(b), bmid) <= 1e-5, rel_l2(H(b), bmid)
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_backproject_variants_agree_and_are_deterministic(variant):
     """Every backprojector (ray scatter, column gather, brick scatter) gives the oracle's
