@@ -288,7 +288,8 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
 #pragma unroll
             for (int j = 0; j < NW; ++j) {
                 v0[j] = STAGED ? vol[a0[j]] : __ldg(vol + a0[j]);
-                v1[j] = STAGED ? vol[a1[j]] : __ldg(vol + a1[j]);
+                // the second segment's voxel only after a crossing (else l1 = 0)
+                v1[j] = l1[j] != 0.f ? (STAGED ? vol[a1[j]] : __ldg(vol + a1[j])) : 0.f;
             }
 #pragma unroll
             for (int j = 0; j < NW; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
