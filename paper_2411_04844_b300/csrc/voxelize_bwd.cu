@@ -143,8 +143,11 @@ __global__ void __launch_bounds__(256) k_bwd_items(
 __global__ void k_bwd_final(const __grid_constant__ Batch B,
                             const uint32_t *__restrict__ item_off, unsigned long long cap,
                             const float *__restrict__ part) {
-    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= B.tot_g) return;
+    // four lanes per Gaussian: lane c of the quad sums items b + c, b + c + 4,
+    // ... in FP64, two fixed butterfly steps combine the quad, lane 0 of it
+    // finishes the chain rule
+    const int gi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 2), c4 = threadIdx.x & 3;
+    if (gi >= B.tot_g) return;  // quad-uniform (quads never straddle a warp)
     const Inst &I = B.in[inst_of_g(B, gi)];
     const dgr_grid &g = I.g;
     const int i = gi - I.g0;
@@ -161,11 +164,19 @@ __global__ void k_bwd_final(const __grid_constant__ Batch B,
     double Md[NMOM];
 #pragma unroll
     for (int k = 0; k < NMOM; ++k) Md[k] = 0.0;
-    for (unsigned long long it = b; it < e; ++it) {
+    for (unsigned long long it = b + c4; it < e; it += 4) {
         const float *src = part + it * NMOM;
 #pragma unroll
         for (int k = 0; k < NMOM; ++k) Md[k] += (double)src[k];
     }
+    // the quad's lanes are consecutive: xor 1 then xor 2 stays inside it
+    const unsigned qmask = 0xFu << (threadIdx.x & 28);
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) {
+        Md[k] += __shfl_xor_sync(qmask, Md[k], 1);
+        Md[k] += __shfl_xor_sync(qmask, Md[k], 2);
+    }
+    if (c4 != 0) return;
     float M[NMOM];
 #pragma unroll
     for (int k = 0; k < NMOM; ++k) M[k] = (float)Md[k];
@@ -255,7 +266,7 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
                                ws_ptr<unsigned long long>(ws, ws->scan_tmp), st);
     if (err != cudaSuccess) return err;
     k_bwd_items<<<148 * 8, 256, 0, st>>>(B, prep, item_off, cap, part);
-    k_bwd_final<<<(B.tot_g + 127) / 128, 128, 0, st>>>(B, item_off, cap, part);
+    k_bwd_final<<<(unsigned)(((long long)B.tot_g * 4 + 127) / 128), 128, 0, st>>>(B, item_off, cap, part);
     counted(2);
     return cudaGetLastError();
 }
