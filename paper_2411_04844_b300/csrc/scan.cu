@@ -1,7 +1,8 @@
 // Exclusive prefix sum of uint32 counts (work-list offsets of the voxelizer's
 // binning and of the backward work items).  Three launches: per-block sums,
 // one-block scan of the block sums (64-bit, so an overflow is detected), and a
-// per-block scan that adds the block offset.  Deterministic (no atomics).
+// per-block scan that adds the block offset; one launch when the input fits
+// one block.  Deterministic (no atomics).
 #include "dgr_internal.cuh"
 
 namespace dgr {
@@ -93,6 +94,32 @@ __global__ void k_block_scan(const uint32_t *in, int len, const unsigned long lo
         off += v[i];
     }
 }
+// len <= SCAN_BLOCK: the whole scan, the total and the capacity check in
+// one block
+__global__ void k_scan_single(const uint32_t *in, int len, uint32_t *out, unsigned long long cap,
+                              int *status, int flag) {
+    __shared__ unsigned long long wt[32];
+    __shared__ unsigned long long tot;
+    const int base = threadIdx.x * SCAN_PER_THREAD;
+    uint32_t v[SCAN_PER_THREAD];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER_THREAD; ++i) {
+        v[i] = base + i < len ? in[base + i] : 0u;
+        s += v[i];
+    }
+    unsigned long long off = block_exclusive_scan<unsigned long long>(s, wt, &tot);
+#pragma unroll
+    for (int i = 0; i < SCAN_PER_THREAD; ++i) {
+        if (base + i < len) out[base + i] = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
+        off += v[i];
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long t = tot;
+        if (t > cap) atomicOr(status, flag);
+        out[len] = t > 0xffffffffull ? 0xffffffffu : (uint32_t)t;
+    }
+}
 }  // namespace
 
 size_t scan_tmp_elems(int len) { return (size_t)(len + SCAN_BLOCK - 1) / SCAN_BLOCK + 1; }
@@ -104,6 +131,11 @@ cudaError_t scan_u32(const uint32_t *in, uint32_t *out, int len, unsigned long l
     if (nb == 0) {
         // empty input: total 0
         return cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
+    }
+    if (nb == 1) {
+        k_scan_single<<<1, SCAN_THREADS, 0, st>>>(in, len, out, cap, status, flag);
+        counted(1);
+        return cudaGetLastError();
     }
     k_block_sums<<<nb, SCAN_THREADS, 0, st>>>(in, len, tmp);
     k_scan_block_sums<<<1, SCAN_THREADS, 0, st>>>(tmp, nb, out, len, cap, status, flag);
