@@ -100,6 +100,8 @@ constexpr int MAX_INST = 16;
 // status block (256 bytes of the workspace): [0] device status flags,
 // [16] voxelizer tile queue head, [17] set when a Gaussian is not separable
 constexpr int SEP_FLAG = 17;
+constexpr int BIG_COUNT = 18;  // status word: Gaussians of the adjoint with more than BIG_ITEMS items
+constexpr int BIG_ITEMS = 256;
 
 struct Inst {
     dgr_grid g;

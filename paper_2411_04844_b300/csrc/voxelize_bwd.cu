@@ -140,17 +140,10 @@ __global__ void __launch_bounds__(256) k_bwd_items(
     }
 }
 
-__global__ void k_bwd_final(const __grid_constant__ Batch B,
-                            const uint32_t *__restrict__ item_off, unsigned long long cap,
-                            const float *__restrict__ part) {
-    // four lanes per Gaussian: lane c of the quad sums items b + c, b + c + 4,
-    // ... in FP64, two fixed butterfly steps combine the quad, lane 0 of it
-    // finishes the chain rule
-    const int gi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 2), c4 = threadIdx.x & 3;
-    if (gi >= B.tot_g) return;  // quad-uniform (quads never straddle a warp)
-    const Inst &I = B.in[inst_of_g(B, gi)];
+// the chain rule of one Gaussian from its summed moments M (empty: no
+// voxel of its box was reached, every gradient is zero)
+__device__ void bwd_finish(const Inst &I, int i, bool empty, const float *M) {
     const dgr_grid &g = I.g;
-    const int i = gi - I.g0;
     const float *__restrict__ s = I.s;
     const float4 *__restrict__ q = reinterpret_cast<const float4 *>(I.q);
     const float *__restrict__ rho = I.rho;
@@ -158,29 +151,7 @@ __global__ void k_bwd_final(const __grid_constant__ Batch B,
     float *__restrict__ g_s = I.g_s;
     float *__restrict__ g_q = I.g_q;
     float *__restrict__ g_rho = I.g_rho;
-    unsigned long long b = item_off[gi], e = item_off[gi + 1];
-    if (e > cap) e = cap;
-    // item partials summed in FP64 (a large box has tens of thousands of items)
-    double Md[NMOM];
-#pragma unroll
-    for (int k = 0; k < NMOM; ++k) Md[k] = 0.0;
-    for (unsigned long long it = b + c4; it < e; it += 4) {
-        const float *src = part + it * NMOM;
-#pragma unroll
-        for (int k = 0; k < NMOM; ++k) Md[k] += (double)src[k];
-    }
-    // the quad's lanes are consecutive: xor 1 then xor 2 stays inside it
-    const unsigned qmask = 0xFu << (threadIdx.x & 28);
-#pragma unroll
-    for (int k = 0; k < NMOM; ++k) {
-        Md[k] += __shfl_xor_sync(qmask, Md[k], 1);
-        Md[k] += __shfl_xor_sync(qmask, Md[k], 2);
-    }
-    if (c4 != 0) return;
-    float M[NMOM];
-#pragma unroll
-    for (int k = 0; k < NMOM; ++k) M[k] = (float)Md[k];
-    if (b >= e) {
+    if (empty) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) { g_mu[3 * i + a] = 0.f; g_s[3 * i + a] = 0.f; }
 #pragma unroll
@@ -253,6 +224,101 @@ __global__ void k_bwd_final(const __grid_constant__ Batch B,
     g_q[4 * i + 3] = (gz - z * dot) * iq;
 }
 
+__global__ void k_bwd_final(const __grid_constant__ Batch B,
+                            const uint32_t *__restrict__ item_off, unsigned long long cap,
+                            const float *__restrict__ part, uint32_t *__restrict__ big,
+                            int *__restrict__ big_count) {
+    // four lanes per Gaussian: lane c of the quad sums items b + c, b + c + 4,
+    // ... in FP64, two fixed butterfly steps combine the quad, lane 0 of it
+    // finishes the chain rule
+    const int gi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 2), c4 = threadIdx.x & 3;
+    if (gi >= B.tot_g) return;  // quad-uniform (quads never straddle a warp)
+    const Inst &I = B.in[inst_of_g(B, gi)];
+    const int i = gi - I.g0;
+    unsigned long long b = item_off[gi], e = item_off[gi + 1];
+    if (e > cap) e = cap;
+    // a Gaussian with many items goes to k_bwd_big (a CTA each)
+    if (e > b + BIG_ITEMS) {
+        if (c4 == 0) big[atomicAdd(big_count, 1)] = (uint32_t)gi;
+        return;
+    }
+    // item partials summed in FP64 (at most BIG_ITEMS items)
+    double Md[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) Md[k] = 0.0;
+    for (unsigned long long it = b + c4; it < e; it += 4) {
+        const float *src = part + it * NMOM;
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) Md[k] += (double)src[k];
+    }
+    // the quad's lanes are consecutive: xor 1 then xor 2 stays inside it
+    const unsigned qmask = 0xFu << (threadIdx.x & 28);
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) {
+        Md[k] += __shfl_xor_sync(qmask, Md[k], 1);
+        Md[k] += __shfl_xor_sync(qmask, Md[k], 2);
+    }
+    if (c4 != 0) return;
+    float M[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) M[k] = (float)Md[k];
+    bwd_finish(I, i, b >= e, M);
+}
+
+// Gaussians with more than BIG_ITEMS items: a CTA each (CTAs stride over the
+// list k_bwd_final built); every thread sums items b + t, b + t + 256, ... with
+// Kahan-compensated FP32 sums, the CTA combines them in FP64 in a fixed order
+__global__ void __launch_bounds__(256) k_bwd_big(const __grid_constant__ Batch B,
+                                                 const uint32_t *__restrict__ item_off, unsigned long long cap,
+                                                 const float *__restrict__ part,
+                                                 const uint32_t *__restrict__ big,
+                                                 const int *__restrict__ big_count) {
+    __shared__ double sred[256 / 32][NMOM];
+    const int nbig = *big_count;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = blockIdx.x; j < nbig; j += gridDim.x) {  // CTA-uniform
+        const int gi = (int)big[j];
+        const Inst &I = B.in[inst_of_g(B, gi)];
+        unsigned long long b = item_off[gi], e = item_off[gi + 1];
+        if (e > cap) e = cap;
+        float sm[NMOM], cm[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) sm[k] = cm[k] = 0.f;
+        for (unsigned long long it = b + threadIdx.x; it < e; it += 256) {
+            const float *src = part + it * NMOM;
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) {
+                const float y = src[k] - cm[k];
+                const float t = sm[k] + y;
+                cm[k] = (t - sm[k]) - y;
+                sm[k] = t;
+            }
+        }
+        double d[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            d[k] = (double)sm[k] - (double)cm[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) sred[w][k] = d[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float M[NMOM];
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) {
+                double t = 0.0;
+                for (int u = 0; u < 256 / 32; ++u) t += sred[u][k];
+                M[k] = (float)t;
+            }
+            bwd_finish(I, gi - I.g0, false, M);
+        }
+        __syncthreads();  // sred is rewritten by the next Gaussian
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st) {
@@ -265,9 +331,17 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
     cudaError_t err = scan_u32(itemcnt, item_off, B.tot_g, cap, status, DGR_STATUS_ITEM_OVERFLOW,
                                ws_ptr<unsigned long long>(ws, ws->scan_tmp), st);
     if (err != cudaSuccess) return err;
+    // the item counts are consumed by the scan: their array holds the list of
+    // Gaussians with many items, its length in the status word BIG_COUNT
+    uint32_t *big = itemcnt;
+    int *big_count = status + BIG_COUNT;
+    err = cudaMemsetAsync(big_count, 0, sizeof(int), st);
+    if (err != cudaSuccess) return err;
     k_bwd_items<<<148 * 8, 256, 0, st>>>(B, prep, item_off, cap, part);
-    k_bwd_final<<<(unsigned)(((long long)B.tot_g * 4 + 127) / 128), 128, 0, st>>>(B, item_off, cap, part);
-    counted(2);
+    k_bwd_final<<<(unsigned)(((long long)B.tot_g * 4 + 127) / 128), 128, 0, st>>>(B, item_off, cap, part, big,
+                                                                                    big_count);
+    k_bwd_big<<<148 * 2, 256, 0, st>>>(B, item_off, cap, part, big, big_count);
+    counted(3);
     return cudaGetLastError();
 }
 

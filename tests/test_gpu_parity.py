@@ -383,6 +383,29 @@ def test_voxelize_backward_matches_oracle_gradient():
         assert rel_l2(a, b) <= 1e-4, (name, rel_l2(a, b))
 
 
+def test_voxelize_backward_large_boxes():
+    """Gaussians whose boxes hold more than 256 work items (over 512K voxels:
+    scales of 12-20 voxels in a 96 x 96 x 88 grid) are summed by a CTA each;
+    with small ones around them, every gradient matches the oracle."""
+    gs = synth.GridSpec((96, 96, 88), 1.0, (-48.0, -48.0, -44.0))
+    big = synth.gaussian_field(synth.rng_for(1, 71), 6, gs, ("loguniform", 12.0, 20.0), unnormalised_q=True)
+    big.mu = (0.25 * big.mu).astype(np.float32)  # near the centre: boxes mostly inside the grid
+    small = synth.gaussian_field(synth.rng_for(1, 72), 300, gs, ("loguniform", 0.5, 4.0), unnormalised_q=True)
+    f = synth.Field(np.concatenate([big.mu, small.mu]), np.concatenate([big.s, small.s]),
+                            np.concatenate([big.q, small.q]), np.concatenate([big.rho, small.rho]))
+    f = guard_field(f, gs)
+    og = oracle_grid(gs)
+    _, box = O.footprint(og, f.mu, f.s, f.q, 3.0)
+    vox = np.prod(np.maximum(box[:, 3:6] - box[:, 0:3] + 1, 0), axis=1)
+    assert (vox[:6] > 256 * 2048).sum() >= 3  # several Gaussians take the large-box path
+    W = np.random.default_rng(6).standard_normal(gs.shape).astype(np.float32)
+    gg = _gpu_backward(gs, f, W)
+    go = O.voxelize_backward(og, f.mu, f.s, f.q, f.rho, W, 3.0)
+    for name, a, b in zip(("mu", "s", "q", "rho"), gg, go):
+        assert rel_l2(a, b) <= 1e-4, (name, rel_l2(a, b))
+        assert rel_l2(a[:6], b[:6]) <= 1e-4, (name, "large", rel_l2(a[:6], b[:6]))
+
+
 def test_voxelize_backward_vs_fp64_finite_differences():
     """16 Gaussians in 16^3 with the 512^3 workload's heavy-tailed scale law."""
     gs = synth.GridSpec((16, 16, 16), 1.0, (-8.0, -8.0, -8.0))
