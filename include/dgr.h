@@ -140,7 +140,7 @@ int dgr_set_staged_walk(int on);
  * accumulates a voxel brick in shared memory, its warps walking the detector
  * columns that cross it, each lane carrying several detector rows.  The two
  * scatters add the same fixed-point integers (exact, order-independent; the
- * step is chosen per group of 64 views from the largest residual so that no
+ * step is chosen per group of 128 views from the largest residual so that no
  * sum can overflow) and fold them into FP32 sums in a fixed order: they
  * return the same bits.  A process-wide setting. */
 int dgr_set_backprojector(int variant);

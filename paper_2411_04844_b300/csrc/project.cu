@@ -199,13 +199,13 @@ __device__ __forceinline__ int count_before(float T, int n, int p0, int sg, floa
     return lo;
 }
 
-// fixed-point step of one group of views of an instance: the largest power
-// of two S with VGROUP x col_u x col_v x (longest chord in t units) x
+// fixed-point step of one group of nkv <= VGROUP views of an instance: the
+// largest power of two S with nkv x col_u x col_v x (longest chord in t units) x
 // max |scaled residual| x S < 2^30, so that a voxel's integer sum over the
 // group cannot overflow (a voxel meets at most col_u x col_v rays per view).
 // Returns 0 if a residual of the group is not finite.  Called by whole warps
 // (converged): the lanes share the maximum over the group's views.
-constexpr int VGROUP = 64;
+constexpr int VGROUP = 128;
 constexpr int FOLD_Y = 4;  // y rows of 32 x 32 (x, z) tiles per CTA of k_bp_fold
 __device__ __forceinline__ float group_step(const Inst &I, const unsigned *view_max, int kv0, int nkv) {
     unsigned m = 0u;
@@ -216,7 +216,7 @@ __device__ __forceinline__ float group_step(const Inst &I, const unsigned *view_
     if (!(amax <= 3.0e38f)) return 0.f;
     // longest chord of a voxel in t units: sqrt(3) h / |D|, |D| >= dsd (cone) or 1 (parallel)
     const float tchord = 1.7320509f * I.g.h / (I.beam == DGR_CONE ? I.dsd : 1.f) * 1.001f;
-    const float bound = (float)(VGROUP * I.col_u * I.col_v) * tchord * amax;
+    const float bound = (float)(nkv * I.col_u * I.col_v) * tchord * amax;
     if (!(bound > 0.f)) return 1.f;
     int ex;
     frexpf(bound, &ex);  // bound < 2^ex

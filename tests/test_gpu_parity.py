@@ -237,14 +237,15 @@ def test_project_and_backproject_parity(case):
 
 @pytest.mark.parametrize("variant", [0, 2])
 def test_backproject_several_view_groups(variant):
-    """150 views: the fixed-point scatters run three groups of views (64, 64,
-    22), each with its own step from its own largest residual (the residual
-    scale differs by 10^4 between groups), and the fold adds the groups."""
+    """300 views: the fixed-point scatters run three groups of views (128,
+    128, 44), each with its own step from its own largest residual (the
+    residual scale differs by 10^4 between groups), and the fold adds the
+    groups."""
     gs = synth.GridSpec((32, 28, 24), 1.0, (-16.0, -14.0, -12.0))
-    geo = synth.cone_geom(150, 40, 32, 1.5, 1.5, 300.0, 450.0)
+    geo = synth.cone_geom(300, 40, 32, 1.5, 1.5, 300.0, 450.0)
     y = np.random.default_rng(19).standard_normal(geo.shape).astype(np.float32)
-    y[64:128] *= 1e-4
-    y[128:] *= 30.0
+    y[128:256] *= 1e-4
+    y[256:] *= 30.0
     grid = dgr.Grid.of(gs)
     ang = T(geo.angles)
     gg = dgr.Geom.of(geo, ang)
@@ -262,7 +263,7 @@ def test_backproject_several_view_groups(variant):
     # the small group alone is still resolved (its own step)
     b = torch.empty(gs.shape, device=DEV)
     ymid = np.zeros_like(y)
-    ymid[64:128] = y[64:128]
+    ymid[128:256] = y[128:256]
     dgr.dgr_backproject(grid, gg, T(ymid), b, ws)
     torch.cuda.synchronize()
     bmid = O.backproject(oracle_grid(gs), oracle_geom(geo), ymid)
