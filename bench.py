@@ -198,7 +198,8 @@ def run_ours(args, dist, rank, local):
     loss = torch.zeros(1, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     K, W = args.steps, args.warmup
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(dgr.DGR_STEP_EVENTS)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(dgr.DGR_STEP_KERNEL_EVENTS)]
+          for _ in range(K)]
     for row in ev:
         for e in row:
             e.record(stream)
@@ -228,6 +229,9 @@ def run_ours(args, dist, rank, local):
     step_ms = [ev[k][0].elapsed_time(ev[k][6]) for k in range(K)]
     phase_ms = {name: [ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]
                 for i, name in enumerate(dgr.STEP_PHASES)}
+    # the main kernels of the two projector phases, timed on their own stream
+    kernel_ms = {"backproject": [ev[k][7].elapsed_time(ev[k][8]) for k in range(K)],
+                 "project": [ev[k][9].elapsed_time(ev[k][10]) for k in range(K)]}
 
     # end to end through the C ABI: every step's measured projections copied
     # pinned host -> device on a copy stream (into one of two device buffers,
@@ -280,12 +284,23 @@ def run_ours(args, dist, rank, local):
     value = N * K / tot_s
     e2e_value = N * K / tot_e2e
     phases = {k: statistics.mean(v) for k, v in phase_ms.items()}
+    kernels = {k: statistics.mean(v) for k, v in kernel_ms.items()}
     return dict(P=P, value=value, e2e=e2e_value, step_ms=statistics.mean(step_ms), phases=phases,
+                kernels=kernels,
                 launches=launches, clocks=clk, t_wall=t_wall, loss=float(loss_host[-1].item()))
 
 
-def roofline(P, phases, clk, pk):
-    """Roofline of the dominant kernel (longest phase) of one iteration."""
+KERNEL_NAMES = {"project": "k_path<0> (projector walk)",
+                "backproject": "k_path<1> (backprojector walk + fixed-point scatter)",
+                "voxelize": "voxelize phase (binning + k_voxelize)",
+                "voxelize_backward": "FVR adjoint phase (k_bwd_items + k_bwd_final + k_bwd_big)"}
+
+
+def roofline(P, phases, clk, pk, kernels=None):
+    """Roofline of the dominant kernel of one iteration.  The two projector
+    phases are represented by their main kernel, timed by its own pair of
+    events; the other phases by the phase time."""
+    kernels = kernels or {}
     wl = P["wl"]
     nvox = wl.grid.dims[0] * wl.grid.dims[1] * wl.grid.dims[2]
     nrays = wl.geom.n_views * wl.geom.nu * wl.geom.nv
@@ -294,7 +309,8 @@ def roofline(P, phases, clk, pk):
     sfu_peak = SMS * MUFU_PER_CLK_SM * mhz * 1e6 / 1e9  # G ex2 / s
     ffma_peak = SMS * FFMA_PER_CLK_SM * mhz * 1e6 / 1e9  # G FFMA / s
     per = {}
-    for name, ms in phases.items():
+    for name, ph_ms in phases.items():
+        ms = kernels.get(name, ph_ms)
         s = ms / 1000.0
         if name in ("project", "backproject"):
             a = proj_bytes / s / 1e9
@@ -310,10 +326,13 @@ def roofline(P, phases, clk, pk):
                          "frac": a / ffma_peak, "ms": ms}
         else:
             per[name] = {"ms": ms}
-    dom = max(phases, key=lambda k: phases[k])
+        per[name]["phase_ms"] = ph_ms
+    dom = max(per, key=lambda k: per[k]["ms"])
     r = dict(per[dom])
-    r.pop("ms", None)
-    r["kernel"] = dom
+    r["kernel_ms"] = r.pop("ms")
+    r.pop("phase_ms")
+    r["kernel"] = KERNEL_NAMES.get(dom, dom)
+    r["phase"] = dom
     r["peak_src"] = pk["src"] if r.get("unit") == "GB/s" else f"{SMS} SMs x unit rate x {mhz:.0f} MHz"
     r["traffic"] = traffic_for(dom)
     return r, per
@@ -428,7 +447,7 @@ def main():
     if rank != 0:
         return
     pk = peaks()
-    roof, per = roofline(R["P"], R["phases"], R["clocks"], pk)
+    roof, per = roofline(R["P"], R["phases"], R["clocks"], pk, R["kernels"])
     P = R["P"]
     wl = P["wl"]
     fvr_ms = R["phases"]["voxelize"]

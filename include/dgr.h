@@ -296,8 +296,13 @@ int dgr_step_batched(int n_inst, const dgr_problem *probs, const dgr_params *par
 /* dgr_step with CUDA events recorded on `stream` at its phase boundaries:
  * events[0] before voxelize, [1] after voxelize, [2] after project, [3] after
  * the L1 residual, [4] after backproject, [5] after the voxelize adjoint,
- * [6] after Adam.  events: host array of n_events (>= 7) cudaEvent_t. */
+ * [6] after Adam.  With n_events >= DGR_STEP_KERNEL_EVENTS (11), also
+ * [7] / [8] right before / after the backprojector's main kernel (the path
+ * scatter, without the residual scaling and the fold) and [9] / [10] around
+ * the projector's main kernel.  events: host array of n_events (>= 7)
+ * cudaEvent_t. */
 #define DGR_STEP_EVENTS 7
+#define DGR_STEP_KERNEL_EVENTS 11
 int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *measured,
                    float *loss_out, dgr_ws *ws, cudaStream_t stream, cudaEvent_t *events,
                    int n_events);

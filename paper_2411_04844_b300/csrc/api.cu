@@ -512,9 +512,11 @@ int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t s
 
 // voxelize -> project -> L1 -> backproject -> voxelize adjoint -> Adam, for a
 // batch of problems, one launch per phase
+// ev: phase events (DGR_STEP_EVENTS) or nullptr; kev: optional events
+// around the backprojector's and the projector's main kernels (4)
 static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *params,
                       const float *const *measured, float *loss_out, dgr_ws *ws,
-                      cudaStream_t stream, cudaEvent_t *ev) {
+                      cudaStream_t stream, cudaEvent_t *ev, const cudaEvent_t *kev = nullptr) {
     if (n_inst < 1 || n_inst > MAX_INST || !probs || !params || !measured || !loss_out || !ws)
         return DGR_ERR_ARG;
     Batch &B = *new_batch();
@@ -583,14 +585,16 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
     if (e == cudaSuccess) e = launch_voxelize(B, prep, ws, g_deterministic, stream);
     if (e == cudaSuccess) e = mark(1);
     if (e == cudaSuccess) e = launch_ray_tables(B, tab, stream);
-    if (e == cudaSuccess) e = launch_project(B, tab, ws_ptr<int>(ws, ws->status), stream);
+    if (e == cudaSuccess) e = launch_project(B, tab, ws_ptr<int>(ws, ws->status), stream, kev ? kev + 2 : nullptr);
     if (e == cudaSuccess) e = mark(2);
     float *ssim_g = ws_ptr<float>(ws, ws->ssim_g);
     if (e == cudaSuccess && any_ssim)
         e = launch_ssim(B, ws_ptr<float>(ws, ws->ssim_maps), ws_ptr<float>(ws, ws->ssim_part), ssim_g, stream);
     if (e == cudaSuccess) e = launch_l1(B, ws_ptr<float>(ws, ws->loss_part), any_ssim ? ssim_g : nullptr, stream);
     if (e == cudaSuccess) e = mark(3);
-    if (e == cudaSuccess) e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc), ws->plan.max_vox, ws_ptr<int>(ws, ws->status), stream);
+    if (e == cudaSuccess)
+        e = launch_backproject(B, tab, ws_ptr<float>(ws, ws->sino_scaled), ws_ptr<int>(ws, ws->acc),
+                               ws->plan.max_vox, ws_ptr<int>(ws, ws->status), stream, kev);
     if (e == cudaSuccess && any_tv) e = launch_tv(B, ws_ptr<float>(ws, ws->tv_part), 1, stream);
     if (e == cudaSuccess)
         e = launch_loss_final(B, ws_ptr<float>(ws, ws->loss_part), L1_BLOCKS, ws_ptr<float>(ws, ws->ssim_part),
@@ -612,7 +616,8 @@ int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *me
                    float *loss_out, dgr_ws *ws, cudaStream_t stream, cudaEvent_t *events,
                    int n_events) {
     if (!events || n_events < DGR_STEP_EVENTS) return DGR_ERR_ARG;
-    return step_batch(1, prob, p, &measured, loss_out, ws, stream, events);
+    return step_batch(1, prob, p, &measured, loss_out, ws, stream, events,
+                      n_events >= DGR_STEP_KERNEL_EVENTS ? events + DGR_STEP_EVENTS : nullptr);
 }
 
 int dgr_step_batched(int n_inst, const dgr_problem *probs, const dgr_params *params,

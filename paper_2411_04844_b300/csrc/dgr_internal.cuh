@@ -233,7 +233,9 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
 // project.cu
 size_t ray_table_bytes(int n_tab, int n_views, int n_rows);
 cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st);
-cudaError_t launch_project(const Batch &B, const RayXY *tab, int *status, cudaStream_t st);
+// kev (optional): two events recorded right before / after the main kernel
+cudaError_t launch_project(const Batch &B, const RayXY *tab, int *status, cudaStream_t st,
+                           const cudaEvent_t *kev = nullptr);
 void set_staged_walk(int on);
 // x-fastest -> z-fastest copy of a volume (the row-warp projector's layout)
 cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cudaStream_t st);
@@ -253,7 +255,8 @@ cudaError_t launch_loss_final(const Batch &B, const float *l1part, int l1_blocks
                               const float *tpart, cudaStream_t st);
 // acc: the workspace's integer sums (ray scatter), room for acc_vox voxels
 cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, int *acc,
-                               long long acc_vox, int *status, cudaStream_t st);
+                               long long acc_vox, int *status, cudaStream_t st,
+                               const cudaEvent_t *kev = nullptr);
 // the projector of one instance with caller-provided tables (no workspace)
 cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY *tab,
                                   const float *vol, float *sino, cudaStream_t st);

@@ -1333,15 +1333,18 @@ static int staging(Batch &B, int *status) {
     return smem;
 }
 
-cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaStream_t st) {
+cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaStream_t st,
+                           const cudaEvent_t *kev) {
     // row-warp projector when every volume is z fastest, else per-ray
     bool zfast = B0.n > 0;
     for (int i = 0; i < B0.n; ++i) zfast = zfast && B0.in[i].vsz == 1;
     if (!zfast) {
         const long long blocks = (B0.tot_rays + 127) / 128;
         if (blocks == 0) return cudaSuccess;
+        if (kev) cudaEventRecord(kev[0], st);
         k_project_ray<<<(unsigned)blocks, 128, 0, st>>>(B0, const_cast<RayXY *>(tab));
         counted(1);
+        if (kev) cudaEventRecord(kev[1], st);
         return cudaGetLastError();
     }
     // projector blocks: one detector column x PR_ROWS rows of one view
@@ -1358,11 +1361,13 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaS
     }
     if (pb == 0) return cudaSuccess;
     const int smem = staging(B, status);
+    if (kev) cudaEventRecord(kev[0], st);
     if (smem > 0)
         k_path<0, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     else
         k_path<0, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     counted(1);
+    if (kev) cudaEventRecord(kev[1], st);
     return cudaGetLastError();
 }
 
@@ -1374,8 +1379,12 @@ cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cu
 }
 
 // ray-driven backprojector: per group of VGROUP views, the scatter and the fold
+// kev: [0] before the first group's scatter, [1] after the last group's
+// scatter (with several groups the folds in between fall inside)
 static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const float *sino_scaled,
-                                     const unsigned *view_max, int *acc, int *status, cudaStream_t st) {
+                                     const unsigned *view_max, int *acc, int *status, cudaStream_t st,
+                                     const cudaEvent_t *kev) {
+    bool first = true;
     static thread_local Batch B;
     B = B0;
     int ngroups = 0;
@@ -1403,11 +1412,14 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
         }
         if (pb > 0) {
             const int smem = staging(B, status);
+            if (kev && first) cudaEventRecord(kev[0], st);
+            first = false;
             if (smem > 0)
                 k_path<1, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
             else
                 k_path<1, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
             counted(1);
+            if (kev) cudaEventRecord(kev[1], st);
         }
         if (fb > 0) {
             k_bp_fold<<<fb, 256, 0, st>>>(B, view_max);
@@ -1418,7 +1430,7 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
 }
 
 cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_scaled, int *acc,
-                               long long acc_vox, int *status, cudaStream_t st) {
+                               long long acc_vox, int *status, cudaStream_t st, const cudaEvent_t *kev) {
     long long vox = 0;
     for (int i = 0; i < B.n; ++i) vox += (long long)B.in[i].g.nx * B.in[i].g.ny * B.in[i].g.nz;
     // the ray scatter (0) needs the workspace's integer sums; without them, the brick scatter (2)
@@ -1432,16 +1444,18 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
         k_scale_dn<<<dim3((max_per + 255) / 256, B.tot_views), 256, 0, st>>>(B, const_cast<RayXY *>(tab),
                                                                            sino_scaled, view_max);
         counted(1);
-        if (variant == 0) return launch_bp_scatter(B, tab, sino_scaled, view_max, acc, status, st);
+        if (variant == 0) return launch_bp_scatter(B, tab, sino_scaled, view_max, acc, status, st, kev);
         const int smem = 2 * BBV * (int)sizeof(float);
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_bp_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             attr = true;
         }
+        if (kev) cudaEventRecord(kev[0], st);
         k_bp_brick<<<B.tot_bricks, BB_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), sino_scaled,
                                                            view_max);
         counted(1);
+        if (kev) cudaEventRecord(kev[1], st);
         return cudaGetLastError();
     }
     int max_u = 1, max_v = 1;
@@ -1451,7 +1465,9 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
     }
     dim3 tgrid((max_u + TR - 1) / TR, (max_v + TR - 1) / TR, B.tot_views);
     k_scale_dn_t<<<tgrid, 256, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled);
+    if (kev) cudaEventRecord(kev[0], st);
     k_backproject<<<B.tot_blk, 32 * BP_W, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled);
+    if (kev) cudaEventRecord(kev[1], st);
     counted(2);
     return cudaGetLastError();
 }

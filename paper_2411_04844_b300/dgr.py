@@ -43,6 +43,9 @@ EXPORTS = [
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
 DGR_STEP_EVENTS = 7
+# with 11 events, [7]/[8] bracket the backprojector's path scatter kernel and
+# [9]/[10] the projector's main kernel
+DGR_STEP_KERNEL_EVENTS = 11
 STEP_PHASES = ("voxelize", "project", "l1", "backproject", "voxelize_backward", "adam")
 
 
@@ -472,10 +475,11 @@ def dgr_step(prob: Problem, st: State, measured, loss_out, ws: Workspace, stream
 def dgr_step_timed(prob: Problem, st: State, measured, loss_out, ws: Workspace, events,
                    stream=None):
     """dgr_step recording torch.cuda.Events (already created, i.e. recorded
-    once) at the 7 phase boundaries."""
+    once) at the 7 phase boundaries; given 11, also around the backprojector's
+    and the projector's main kernels."""
     _check(measured, "measured"); _check(loss_out, "loss_out")
     if len(events) < DGR_STEP_EVENTS:
-        raise DgrError("dgr_step_timed needs 7 events")
+        raise DgrError(f"dgr_step_timed needs {DGR_STEP_EVENTS} events")
     arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
     p = st.params()
     _rc(lib().dgr_step_timed(ctypes.byref(prob), ctypes.byref(p), _ptr(measured), _ptr(loss_out),

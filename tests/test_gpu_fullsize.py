@@ -107,3 +107,34 @@ def test_fullsize_step_loss(problem):
     lo, _ = O.l1_loss(O.project(og, oo, vo), meas)
     assert abs(float(loss) - lo) <= 1e-5 * lo
     assert bool(torch.isfinite(st.theta).all())
+
+
+def test_fullsize_step_timed_kernel_events(problem):
+    """dgr_step_timed with the kernel events does the same step as dgr_step
+    (same loss, same parameters, bit for bit), and the two kernel intervals
+    lie inside their phases."""
+    P = problem
+    wl = P["wl"]
+    meas = T(np.random.default_rng(43).uniform(0, 50, wl.geom.shape).astype(np.float32))
+    prob = dgr.make_problem(P["grid"], P["geom"], 3.0, 3e-4, 3e-5, wl.n_iters)
+    out = []
+    for timed in (False, True):
+        st = dgr.State(*[t.clone() for t in P["t"]])
+        dgr.dgr_params_init(prob, st)
+        loss = torch.zeros(1, device=DEV)
+        if timed:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(dgr.DGR_STEP_KERNEL_EVENTS)]
+            for e in ev:
+                e.record()
+            dgr.dgr_step_timed(prob, st, meas, loss, P["ws"], ev)
+        else:
+            dgr.dgr_step(prob, st, meas, loss, P["ws"])
+        torch.cuda.synchronize()
+        assert dgr.dgr_status(P["ws"]) == 0
+        out.append((float(loss), st.theta.clone()))
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][1], out[1][1])
+    assert ev[7].elapsed_time(ev[8]) > 0 and ev[9].elapsed_time(ev[10]) > 0
+    assert ev[3].elapsed_time(ev[7]) >= 0 and ev[8].elapsed_time(ev[4]) >= 0  # backproject phase
+    assert ev[1].elapsed_time(ev[9]) >= 0 and ev[10].elapsed_time(ev[2]) >= 0  # project phase
+    assert ev[7].elapsed_time(ev[8]) <= ev[3].elapsed_time(ev[4])
