@@ -384,22 +384,38 @@ def oracle_sample(frac_gauss, n_views_sample, seed_rank=0):
     desc = (f"FP64 oracle on {O.num_threads()} threads: voxelize + adjoint of {ng} of "
             f"{wl.n_gauss} Gaussians, project + backproject of {n_views_sample} of "
             f"{geo.n_views} views, 256^3 grid; scaled to one full iteration")
-    return 1.0 / t_iter, O.num_threads(), desc, t4 - t0
+    parts = ((t1 - t0) + (t4 - t3), (t2 - t1) + (t3 - t2))  # Gaussian part, view part
+    return 1.0 / t_iter, O.num_threads(), desc, t4 - t0, parts
 
 
 def sample_size(target_s, frac0=0.01):
-    """Calibrate on a small sample, then size (fraction of Gaussians, views)
-    so that one sample takes about target_s seconds."""
-    _, _, _, spent = oracle_sample(frac0, 1)
-    k = max(1.0, target_s / max(spent, 1e-3))
-    return min(1.0, frac0 * k), int(max(1, min(50, round(k))))
+    """Calibrate on a small sample (a fraction frac0 of the Gaussians, one
+    view), then size (fraction of Gaussians, views) so that one sample takes
+    about target_s seconds: half for the views (at most all of them), the
+    rest for the Gaussians (at most all of them), and what the Gaussians
+    leave back to the views."""
+    *_, (tg, tv) = oracle_sample(frac0, 1)
+    tg, tv = max(tg, 1e-3), max(tv, 1e-3)
+    nv = int(max(1, min(50, round(0.5 * target_s / tv))))
+    fg = min(1.0, frac0 * max(0.5 * target_s, target_s - nv * tv) / tg)
+    nv = int(max(nv, min(50, round((target_s - fg / frac0 * tg) / tv))))
+    return fg, nv
 
 
 def cpu_baseline(target_s):
+    """The oracle's iterations/s on a bounded sample; when even the whole
+    iteration is shorter than the target, it is repeated (at most 4 times)
+    and the times summed."""
     fg, nv = sample_size(target_s)
-    v, th, desc, spent = oracle_sample(fg, nv)
-    return {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": desc,
-            "seconds": round(spent, 2)}
+    times, spent, th, desc = [], 0.0, None, None
+    while not times or (spent < 0.66 * target_s and len(times) < 4):
+        v, th, desc, t, _ = oracle_sample(fg, nv)
+        times.append(1.0 / v)
+        spent += t
+    if len(times) > 1:
+        desc += f" (x{len(times)})"
+    return {"value": len(times) / sum(times), "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": desc, "seconds": round(spent, 2)}
 
 
 def run_reference(args, rank, ws_n):
@@ -413,7 +429,7 @@ def run_reference(args, rank, ws_n):
     per = []
     desc = th = None
     for k in range(W + K):
-        v, th, desc, spent = oracle_sample(fg, nv, seed_rank=k % 3)
+        v, th, desc, spent, _ = oracle_sample(fg, nv, seed_rank=k % 3)
         if k >= W:
             per.append(1.0 / v)
     value = K / sum(per)
