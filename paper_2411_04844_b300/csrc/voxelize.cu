@@ -334,6 +334,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
     unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off) {
     __shared__ float4 sp[VOX_CHUNK * 4];
+    // the running per-voxel sums and their Kahan compensations: one column per
+    // thread (touched by that thread only), kept out of registers so that more
+    // CTAs fit on an SM
+    __shared__ float s_acc[TZ][VOX_THREADS], s_cmp[TZ][VOX_THREADS];
     __shared__ int s_tile;
     if (sep_off && *sep_off == 0) return;  // every Gaussian separable: k_voxelize_sep runs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -352,9 +356,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
         const int wy0 = y0 + 4 * w;
         const int y = wy0 + (lane >> 3);
         // running per-voxel sums with Kahan compensation (per chunk, below)
-        float acc[TZ], cmp[TZ];
 #pragma unroll
-        for (int k = 0; k < TZ; ++k) acc[k] = cmp[k] = 0.f;
+        for (int k = 0; k < TZ; ++k) s_acc[k][threadIdx.x] = s_cmp[k][threadIdx.x] = 0.f;
 
         unsigned long long b = tile_off[tg], e = tile_off[tg + 1];
         if (e > cap) e = cap;
@@ -422,12 +425,14 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
             // ulps of the exact sum
 #pragma unroll
             for (int k = 0; k < TZ; ++k) {
-                const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - cmp[k];
-                const float tsum = acc[k] + yv;
-                cmp[k] = (tsum - acc[k]) - yv;
-                acc[k] = tsum;
+                const float a = s_acc[k][threadIdx.x];
+                const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - s_cmp[k][threadIdx.x];
+                const float tsum = a + yv;
+                s_cmp[k][threadIdx.x] = (tsum - a) - yv;
+                s_acc[k][threadIdx.x] = tsum;
             }
         }
+        const auto acc = [&](int k) { return s_acc[k][threadIdx.x]; };
         if (x < g.nx && y < g.ny) {
             // element strides: x fastest (the C ABI's layout) or z fastest
             // (the step's internal layout, read by the row-warp projector)
@@ -437,12 +442,12 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
 #pragma unroll
                 for (int k = 0; k < TZ; k += 4)
                     *reinterpret_cast<float4 *>(col + z0 + k) =
-                        make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+                        make_float4(acc(k), acc(k + 1), acc(k + 2), acc(k + 3));
             } else {
                 const size_t zs = (size_t)I.vsz;
 #pragma unroll
                 for (int k = 0; k < TZ; ++k)
-                    if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+                    if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc(k);
             }
         }
     }
