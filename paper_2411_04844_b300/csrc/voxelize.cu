@@ -471,6 +471,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
     unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off) {
     __shared__ float4 sp[VOX_CHUNK * 4];
     __shared__ __align__(16) float ez[VOX_CHUNK][SEP_TZ];
+    // running sums and Kahan compensations, one column per thread (as in k_voxelize)
+    __shared__ float s_acc[SEP_TZ][VOX_THREADS], s_cmp[SEP_TZ][VOX_THREADS];
     __shared__ int s_tile;
     if (*sep_off != 0) return;  // a non-separable Gaussian: the general kernel runs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -488,9 +490,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
         const int x = x0 + (lane & 7);
         const int wy0 = y0 + 4 * w;
         const int y = wy0 + (lane >> 3);
-        float acc[SEP_TZ], cmp[SEP_TZ];
 #pragma unroll
-        for (int k = 0; k < SEP_TZ; ++k) acc[k] = cmp[k] = 0.f;
+        for (int k = 0; k < SEP_TZ; ++k) s_acc[k][threadIdx.x] = s_cmp[k][threadIdx.x] = 0.f;
         unsigned long long b = tile_off[tg], e = tile_off[tg + 1];
         if (e > cap) e = cap;
         for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
@@ -540,24 +541,26 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
             }
 #pragma unroll
             for (int k = 0; k < SEP_TZ; ++k) {  // Kahan: chunk sum into the running sum
-                const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - cmp[k];
-                const float tsum = acc[k] + yv;
-                cmp[k] = (tsum - acc[k]) - yv;
-                acc[k] = tsum;
+                const float a = s_acc[k][threadIdx.x];
+                const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - s_cmp[k][threadIdx.x];
+                const float tsum = a + yv;
+                s_cmp[k][threadIdx.x] = (tsum - a) - yv;
+                s_acc[k][threadIdx.x] = tsum;
             }
         }
+        const auto acc = [&](int k) { return s_acc[k][threadIdx.x]; };
         if (x < g.nx && y < g.ny) {
             float *col = I.vol + (size_t)x * I.vsx + (size_t)y * I.vsy;
             if (I.vsz == 1 && (g.nz & 3) == 0 && z0 + SEP_TZ <= g.nz &&
                 (reinterpret_cast<uintptr_t>(I.vol) & 15) == 0) {
 #pragma unroll
                 for (int k = 0; k < SEP_TZ; k += 4)
-                    *reinterpret_cast<float4 *>(col + z0 + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+                    *reinterpret_cast<float4 *>(col + z0 + k) = make_float4(acc(k), acc(k + 1), acc(k + 2), acc(k + 3));
             } else {
                 const size_t zs = (size_t)I.vsz;
 #pragma unroll
                 for (int k = 0; k < SEP_TZ; ++k)
-                    if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc[k];
+                    if (z0 + k < g.nz) col[(size_t)(z0 + k) * zs] = acc(k);
             }
         }
     }
