@@ -6,7 +6,8 @@
 //       k_tile_fill /   fill of the (tile, Gaussian) work list, sort of each
 //       k_tile_sort     tile's list by Gaussian index (deterministic order)
 //   a3  k_voxelize      one CTA per 8x16x32 tile: prep records staged in shared
-//                       memory, voxels in registers, one ex2 per in-box pair
+//                       memory, chunk sums in registers, running sums in
+//                       shared memory, one ex2 per in-box pair
 //
 // The paper (Sec. 4.2, Algorithm 1) materialises a [n, 17, 17, 17]
 // contribution tensor and scatter_adds it with global atomics; here nothing
@@ -327,7 +328,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 // a3: persistent CTAs take tiles from a global queue (tiles of every instance
 // back to back).  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
-// (lx, ly) = (lane & 7, lane >> 3), and z in [tz0, tz0 + TZ) in registers.
+// (lx, ly) = (lane & 7, lane >> 3), and the column z in [tz0, tz0 + TZ).
 template <int TZ>
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
