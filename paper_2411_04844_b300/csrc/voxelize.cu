@@ -326,6 +326,23 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Masks of a z group of TZG partly inside a box: row [lo][hi] adds 0 to the
+// exponent of the layers lo..hi of the group and -1e30 (ex2 -> 0) to the
+// others, so the range test costs one packed FP32 add per pair on the FMA
+// pipe instead of integer compares and selects per layer.  Adding 0 leaves
+// the exponent's bits as they are (-0 becomes +0; ex2 of either is 1).
+struct ZMask {
+    float v[TZG][TZG][TZG];
+};
+constexpr ZMask make_zmask() {
+    ZMask t{};
+    for (int lo = 0; lo < TZG; ++lo)
+        for (int hi = 0; hi < TZG; ++hi)
+            for (int k = 0; k < TZG; ++k) t.v[lo][hi][k] = (lo <= k && k <= hi) ? 0.f : -1e30f;
+    return t;
+}
+__constant__ ZMask c_zmask = make_zmask();
+
 // a3: persistent CTAs take tiles from a global queue (tiles of every instance
 // back to back).  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
 // (lx, ly) = (lane & 7, lane >> 3), and the column z in [tz0, tz0 + TZ).
@@ -409,14 +426,14 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                             cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
                         }
                     } else {
+                        const float *zm = c_zmask.v[max(zlo - g8 * TZG, 0)][min(zhi - g8 * TZG, TZG - 1)];
 #pragma unroll
                         for (int kk = 0; kk < TZG; kk += 2) {
                             const int k = g8 * TZG + kk;
                             const float2 dz = make_float2(dz0 + (float)k, dz0 + (float)(k + 1));
-                            const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
-                            const float e0 = ex2_approx((k >= zlo && k <= zhi) ? q.x : -INFINITY);
-                            const float e1 = ex2_approx((k + 1 >= zlo && k + 1 <= zhi) ? q.y : -INFINITY);
-                            cs[k / 2] = __ffma2_rn(rv, make_float2(e0, e1), cs[k / 2]);
+                            float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
+                            q = __fadd2_rn(q, make_float2(zm[kk], zm[kk + 1]));
+                            cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
                         }
                     }
                 }
