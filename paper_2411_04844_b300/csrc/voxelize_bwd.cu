@@ -27,7 +27,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-__global__ void __launch_bounds__(256) k_bwd_items(
+__global__ void __launch_bounds__(256, 3) k_bwd_items(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ item_off, unsigned long long cap, float *__restrict__ part) {
     const int n = B.tot_g;
@@ -35,21 +35,32 @@ __global__ void __launch_bounds__(256) k_bwd_items(
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     unsigned long long total = item_off[n];
     if (total > cap) total = cap;
-    for (long long it = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-         it < (long long)total; it += warps) {
-        // Gaussian owning item `it`: the last gi with item_off[gi] <= it, by a
-        // 32-ary search (each round every lane probes one pivot)
-        int lo = 0, hi = n;  // item_off[lo] <= it < item_off[hi]
-        while (hi - lo > 1) {
-            const int step = (hi - lo + 31) >> 5;
-            const int probe = lo + lane * step;
-            const bool le = probe < hi && (unsigned long long)item_off[probe] <= (unsigned long long)it;
-            const unsigned m = __ballot_sync(0xffffffffu, le);  // lane 0 always set
-            const int k = 31 - __clz(m);
-            lo += k * step;
-            hi = min(hi, lo + step);
+    // each warp a contiguous run of items (consecutive items mostly belong to
+    // the same Gaussian): one search for the run's first item, then the owner
+    // only moves forward
+    const long long per = ((long long)total + warps - 1) / warps;
+    const long long it0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per;
+    const long long it1 = min((long long)total, it0 + per);
+    int gi = -1;
+    for (long long it = it0; it < it1; ++it) {
+        if (gi < 0) {
+            // Gaussian owning item `it`: the last gi with item_off[gi] <= it, by a
+            // 32-ary search (each round every lane probes one pivot)
+            int lo = 0, hi = n;  // item_off[lo] <= it < item_off[hi]
+            while (hi - lo > 1) {
+                const int step = (hi - lo + 31) >> 5;
+                const int probe = lo + lane * step;
+                const bool le = probe < hi && (unsigned long long)item_off[probe] <= (unsigned long long)it;
+                const unsigned m = __ballot_sync(0xffffffffu, le);  // lane 0 always set
+                const int k = 31 - __clz(m);
+                lo += k * step;
+                hi = min(hi, lo + step);
+            }
+            gi = lo;
+        } else {
+            // it < total <= item_off[n]: stops at gi <= n - 1 (skips Gaussians without items)
+            while ((unsigned long long)item_off[gi + 1] <= (unsigned long long)it) ++gi;
         }
-        const int gi = lo;
         const int c = (int)(it - item_off[gi]);
         const Inst &I = B.in[inst_of_g(B, gi)];
         const dgr_grid &g = I.g;
