@@ -101,6 +101,7 @@ constexpr int MAX_INST = 16;
 // [16] voxelizer tile queue head, [17] set when a Gaussian is not separable
 constexpr int SEP_FLAG = 17;
 constexpr int BIG_COUNT = 18;  // status word: Gaussians of the adjoint with more than BIG_ITEMS items
+constexpr int ITEM_QUEUE = 19;  // status word: next run of the adjoint's work items (zeroed with BIG_COUNT)
 constexpr int BIG_ITEMS = 256;
 
 struct Inst {

@@ -27,126 +27,135 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// items per run taken from the queue: consecutive items mostly belong to
+// the same Gaussian, so a run costs one owner search
+constexpr int ITEM_RUN = 8;
+
 __global__ void __launch_bounds__(256, 3) k_bwd_items(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
-    const uint32_t *__restrict__ item_off, unsigned long long cap, float *__restrict__ part) {
+    const uint32_t *__restrict__ item_off, unsigned long long cap, float *__restrict__ part,
+    int *__restrict__ queue) {
     const int n = B.tot_g;
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     unsigned long long total = item_off[n];
     if (total > cap) total = cap;
-    // each warp a contiguous run of items (consecutive items mostly belong to
-    // the same Gaussian): one search for the run's first item, then the owner
+    // warps take runs of ITEM_RUN consecutive items from a global queue (load
+    // balance for uneven items); one owner search per run, then the owner
     // only moves forward
-    const long long per = ((long long)total + warps - 1) / warps;
-    const long long it0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per;
-    const long long it1 = min((long long)total, it0 + per);
-    int gi = -1;
-    for (long long it = it0; it < it1; ++it) {
-        if (gi < 0) {
-            // Gaussian owning item `it`: the last gi with item_off[gi] <= it, by a
-            // 32-ary search (each round every lane probes one pivot)
-            int lo = 0, hi = n;  // item_off[lo] <= it < item_off[hi]
-            while (hi - lo > 1) {
-                const int step = (hi - lo + 31) >> 5;
-                const int probe = lo + lane * step;
-                const bool le = probe < hi && (unsigned long long)item_off[probe] <= (unsigned long long)it;
-                const unsigned m = __ballot_sync(0xffffffffu, le);  // lane 0 always set
-                const int k = 31 - __clz(m);
-                lo += k * step;
-                hi = min(hi, lo + step);
-            }
-            gi = lo;
-        } else {
-            // it < total <= item_off[n]: stops at gi <= n - 1 (skips Gaussians without items)
-            while ((unsigned long long)item_off[gi + 1] <= (unsigned long long)it) ++gi;
-        }
-        const int c = (int)(it - item_off[gi]);
-        const Inst &I = B.in[inst_of_g(B, gi)];
-        const dgr_grid &g = I.g;
-        const float *__restrict__ gv = I.gvol;
-        const Prep P = prep[gi];
-        const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
-                  lz = box_lo(P.bz), hz = box_hi(P.bz);
-        const int ex = hx - lx + 1, ey = hy - ly + 1;
-        int yb, ye, zb, ze;
-        item_range(c, ex, ey, ly, hy, lz, hz, yb, ye, zb, ze);
-        float m[NMOM];
-#pragma unroll
-        for (int k = 0; k < NMOM; ++k) m[k] = 0.f;
-        const int exy = ex * (ye - yb + 1);
-        const float dz0 = (float)(zb - P.az) - P.dz;
-        const float inv_ex = 1.0f / (float)ex;
-        for (int j = lane; j < exy; j += 32) {
-            // j = row * ex + col, by a float reciprocal and one correction
-            int row = (int)((float)j * inv_ex);
-            row -= row * ex > j;
-            row += (row + 1) * ex <= j;
-            const int yy = yb + row, xx = lx + (j - row * ex);
-            const float dx = (float)(xx - P.ax) - P.dx;
-            const float dy = (float)(yy - P.ay) - P.dy;
-            const float C = fmaf(P.a00 * dx, dx, fmaf(P.a11 * dy, dy, P.a01 * dx * dy));
-            const float Lz = fmaf(P.a02, dx, P.a12 * dy);
-            const float *col = gv + ((size_t)zb * g.ny + yy) * g.nx + xx;
-            const size_t zs = (size_t)g.nx * g.ny;
-            // the column's sums over z of ge, ge dz, ge dz^2 (ge = G_V e), in two
-            // packed FP32 lanes (even and odd layers of each group of four)
-            const float2 a22v = make_float2(P.a22, P.a22), Lzv = make_float2(Lz, Lz), Cv = make_float2(C, C);
-            float2 s0v = make_float2(0.f, 0.f), s1v = s0v, s2v = s0v;
-            int z = zb;
-            // U layers at a time (8, then 4): loads first, then the arithmetic
-            auto layers = [&](auto U_) {
-                constexpr int U = decltype(U_)::value;
-                float gz[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) gz[u] = __ldg(col + u * zs);
-                col += U * zs;
-#pragma unroll
-                for (int u = 0; u < U; u += 2) {
-                    const float2 dz = make_float2(dz0 + (float)(z + u - zb), dz0 + (float)(z + u + 1 - zb));
-                    const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
-                    const float2 ge = __fmul2_rn(make_float2(gz[u], gz[u + 1]),
-                                                 make_float2(ex2_approx(q.x), ex2_approx(q.y)));
-                    s0v = __fadd2_rn(s0v, ge);
-                    const float2 t = __fmul2_rn(ge, dz);
-                    s1v = __fadd2_rn(s1v, t);
-                    s2v = __ffma2_rn(t, dz, s2v);
+    for (;;) {
+        int run = 0;
+        if (lane == 0) run = atomicAdd(queue, 1);
+        run = __shfl_sync(0xffffffffu, run, 0);
+        const long long it0 = (long long)run * ITEM_RUN;
+        if (it0 >= (long long)total) break;
+        const long long it1 = min((long long)total, it0 + ITEM_RUN);
+        int gi = -1;
+        for (long long it = it0; it < it1; ++it) {
+            if (gi < 0) {
+                // Gaussian owning item `it`: the last gi with item_off[gi] <= it, by a
+                // 32-ary search (each round every lane probes one pivot)
+                int lo = 0, hi = n;  // item_off[lo] <= it < item_off[hi]
+                while (hi - lo > 1) {
+                    const int step = (hi - lo + 31) >> 5;
+                    const int probe = lo + lane * step;
+                    const bool le = probe < hi && (unsigned long long)item_off[probe] <= (unsigned long long)it;
+                    const unsigned m = __ballot_sync(0xffffffffu, le);  // lane 0 always set
+                    const int k = 31 - __clz(m);
+                    lo += k * step;
+                    hi = min(hi, lo + step);
                 }
-                z += U;
-            };
-            while (z + 7 <= ze) layers(std::integral_constant<int, 8>());
-            if (z + 3 <= ze) layers(std::integral_constant<int, 4>());
-            for (; z <= ze; ++z) {
-                const float dz = dz0 + (float)(z - zb);
-                const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
-                const float ge = __ldg(col) * e;
-                col += zs;
-                s0v.x += ge;
-                const float t = ge * dz;
-                s1v.x += t;
-                s2v.x = fmaf(t, dz, s2v.x);
+                gi = lo;
+            } else {
+                // it < total <= item_off[n]: stops at gi <= n - 1 (skips Gaussians without items)
+                while ((unsigned long long)item_off[gi + 1] <= (unsigned long long)it) ++gi;
             }
-            const float s0 = s0v.x + s0v.y, s1 = s1v.x + s1v.y, s2 = s2v.x + s2v.y;
-            m[0] += s0;
-            m[1] = fmaf(dx, s0, m[1]);
-            m[2] = fmaf(dy, s0, m[2]);
-            m[3] += s1;
-            m[4] = fmaf(dx * dx, s0, m[4]);  // xx
-            m[5] = fmaf(dy * dy, s0, m[5]);  // yy
-            m[6] += s2;                      // zz
-            m[7] = fmaf(dx * dy, s0, m[7]);  // xy
-            m[8] = fmaf(dx, s1, m[8]);       // xz
-            m[9] = fmaf(dy, s1, m[9]);       // yz
-        }
+            const int c = (int)(it - item_off[gi]);
+            const Inst &I = B.in[inst_of_g(B, gi)];
+            const dgr_grid &g = I.g;
+            const float *__restrict__ gv = I.gvol;
+            const Prep P = prep[gi];
+            const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
+                      lz = box_lo(P.bz), hz = box_hi(P.bz);
+            const int ex = hx - lx + 1, ey = hy - ly + 1;
+            int yb, ye, zb, ze;
+            item_range(c, ex, ey, ly, hy, lz, hz, yb, ye, zb, ze);
+            float m[NMOM];
 #pragma unroll
-        for (int k = 0; k < NMOM; ++k) {
+            for (int k = 0; k < NMOM; ++k) m[k] = 0.f;
+            const int exy = ex * (ye - yb + 1);
+            const float dz0 = (float)(zb - P.az) - P.dz;
+            const float inv_ex = 1.0f / (float)ex;
+            for (int j = lane; j < exy; j += 32) {
+                // j = row * ex + col, by a float reciprocal and one correction
+                int row = (int)((float)j * inv_ex);
+                row -= row * ex > j;
+                row += (row + 1) * ex <= j;
+                const int yy = yb + row, xx = lx + (j - row * ex);
+                const float dx = (float)(xx - P.ax) - P.dx;
+                const float dy = (float)(yy - P.ay) - P.dy;
+                const float C = fmaf(P.a00 * dx, dx, fmaf(P.a11 * dy, dy, P.a01 * dx * dy));
+                const float Lz = fmaf(P.a02, dx, P.a12 * dy);
+                const float *col = gv + ((size_t)zb * g.ny + yy) * g.nx + xx;
+                const size_t zs = (size_t)g.nx * g.ny;
+                // the column's sums over z of ge, ge dz, ge dz^2 (ge = G_V e), in two
+                // packed FP32 lanes (even and odd layers of each group of four)
+                const float2 a22v = make_float2(P.a22, P.a22), Lzv = make_float2(Lz, Lz), Cv = make_float2(C, C);
+                float2 s0v = make_float2(0.f, 0.f), s1v = s0v, s2v = s0v;
+                int z = zb;
+                // U layers at a time (8, then 4): loads first, then the arithmetic
+                auto layers = [&](auto U_) {
+                    constexpr int U = decltype(U_)::value;
+                    float gz[U];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
-        }
-        if (lane == 0) {
-            float *dst = part + (size_t)it * NMOM;
+                    for (int u = 0; u < U; ++u) gz[u] = __ldg(col + u * zs);
+                    col += U * zs;
 #pragma unroll
-            for (int k = 0; k < NMOM; ++k) dst[k] = m[k];
+                    for (int u = 0; u < U; u += 2) {
+                        const float2 dz = make_float2(dz0 + (float)(z + u - zb), dz0 + (float)(z + u + 1 - zb));
+                        const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
+                        const float2 ge = __fmul2_rn(make_float2(gz[u], gz[u + 1]),
+                                                     make_float2(ex2_approx(q.x), ex2_approx(q.y)));
+                        s0v = __fadd2_rn(s0v, ge);
+                        const float2 t = __fmul2_rn(ge, dz);
+                        s1v = __fadd2_rn(s1v, t);
+                        s2v = __ffma2_rn(t, dz, s2v);
+                    }
+                    z += U;
+                };
+                while (z + 7 <= ze) layers(std::integral_constant<int, 8>());
+                if (z + 3 <= ze) layers(std::integral_constant<int, 4>());
+                for (; z <= ze; ++z) {
+                    const float dz = dz0 + (float)(z - zb);
+                    const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
+                    const float ge = __ldg(col) * e;
+                    col += zs;
+                    s0v.x += ge;
+                    const float t = ge * dz;
+                    s1v.x += t;
+                    s2v.x = fmaf(t, dz, s2v.x);
+                }
+                const float s0 = s0v.x + s0v.y, s1 = s1v.x + s1v.y, s2 = s2v.x + s2v.y;
+                m[0] += s0;
+                m[1] = fmaf(dx, s0, m[1]);
+                m[2] = fmaf(dy, s0, m[2]);
+                m[3] += s1;
+                m[4] = fmaf(dx * dx, s0, m[4]);  // xx
+                m[5] = fmaf(dy * dy, s0, m[5]);  // yy
+                m[6] += s2;                      // zz
+                m[7] = fmaf(dx * dy, s0, m[7]);  // xy
+                m[8] = fmaf(dx, s1, m[8]);       // xz
+                m[9] = fmaf(dy, s1, m[9]);       // yz
+            }
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+            }
+            if (lane == 0) {
+                float *dst = part + (size_t)it * NMOM;
+#pragma unroll
+                for (int k = 0; k < NMOM; ++k) dst[k] = m[k];
+            }
         }
     }
 }
@@ -346,9 +355,15 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
     // Gaussians with many items, its length in the status word BIG_COUNT
     uint32_t *big = itemcnt;
     int *big_count = status + BIG_COUNT;
-    err = cudaMemsetAsync(big_count, 0, sizeof(int), st);
+    static_assert(ITEM_QUEUE == BIG_COUNT + 1, "one memset zeroes both words");
+    err = cudaMemsetAsync(big_count, 0, 2 * sizeof(int), st);
     if (err != cudaSuccess) return err;
-    k_bwd_items<<<148 * 8, 256, 0, st>>>(B, prep, item_off, cap, part);
+    // one wave of resident CTAs; warps take runs of items from the queue
+    int dev = 0, sms = 148, per_sm = 3;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_items, 256, 0);
+    k_bwd_items<<<sms * max(per_sm, 1), 256, 0, st>>>(B, prep, item_off, cap, part, status + ITEM_QUEUE);
     k_bwd_final<<<(unsigned)(((long long)B.tot_g * 4 + 127) / 128), 128, 0, st>>>(B, item_off, cap, part, big,
                                                                                     big_count);
     k_bwd_big<<<148 * 2, 256, 0, st>>>(B, item_off, cap, part, big, big_count);
