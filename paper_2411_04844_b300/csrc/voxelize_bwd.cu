@@ -249,8 +249,8 @@ __global__ void k_bwd_final(const __grid_constant__ Batch B,
                             const float *__restrict__ part, uint32_t *__restrict__ big,
                             int *__restrict__ big_count) {
     // four lanes per Gaussian: lane c of the quad sums items b + c, b + c + 4,
-    // ... in FP64, two fixed butterfly steps combine the quad, lane 0 of it
-    // finishes the chain rule
+    // ... (compensated FP32), two fixed butterfly steps combine the quad, lane
+    // 0 of it finishes the chain rule
     const int gi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 2), c4 = threadIdx.x & 3;
     if (gi >= B.tot_g) return;  // quad-uniform (quads never straddle a warp)
     const Inst &I = B.in[inst_of_g(B, gi)];
@@ -262,26 +262,41 @@ __global__ void k_bwd_final(const __grid_constant__ Batch B,
         if (c4 == 0) big[atomicAdd(big_count, 1)] = (uint32_t)gi;
         return;
     }
-    // item partials summed in FP64 (at most BIG_ITEMS items)
-    double Md[NMOM];
+    // item partials in compensated FP32 (Kahan: the sum s and the running
+    // error c, exact sum ~ s - c; at most BIG_ITEMS items, BIG_ITEMS / 4 per
+    // lane), the quad's lanes combined by an error-free two-sum.  A fixed order
+    // throughout: bit-reproducible.
+    float Ms[NMOM], Mc[NMOM];
 #pragma unroll
-    for (int k = 0; k < NMOM; ++k) Md[k] = 0.0;
+    for (int k = 0; k < NMOM; ++k) Ms[k] = Mc[k] = 0.f;
     for (unsigned long long it = b + c4; it < e; it += 4) {
         const float *src = part + it * NMOM;
 #pragma unroll
-        for (int k = 0; k < NMOM; ++k) Md[k] += (double)src[k];
+        for (int k = 0; k < NMOM; ++k) {
+            const float y = src[k] - Mc[k];
+            const float t = Ms[k] + y;
+            Mc[k] = (t - Ms[k]) - y;
+            Ms[k] = t;
+        }
     }
     // the quad's lanes are consecutive: xor 1 then xor 2 stays inside it
     const unsigned qmask = 0xFu << (threadIdx.x & 28);
 #pragma unroll
-    for (int k = 0; k < NMOM; ++k) {
-        Md[k] += __shfl_xor_sync(qmask, Md[k], 1);
-        Md[k] += __shfl_xor_sync(qmask, Md[k], 2);
+    for (int o = 1; o <= 2; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            const float a = Ms[k], bb = __shfl_xor_sync(qmask, Ms[k], o);
+            const float cb = __shfl_xor_sync(qmask, Mc[k], o);
+            const float t = a + bb, bp = t - a;
+            const float err = (a - (t - bp)) + (bb - bp);  // a + bb = t + err exactly
+            Ms[k] = t;
+            Mc[k] = (Mc[k] + cb) - err;
+        }
     }
     if (c4 != 0) return;
     float M[NMOM];
 #pragma unroll
-    for (int k = 0; k < NMOM; ++k) M[k] = (float)Md[k];
+    for (int k = 0; k < NMOM; ++k) M[k] = Ms[k] - Mc[k];
     bwd_finish(I, i, b >= e, M);
 }
 
