@@ -31,7 +31,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // the same Gaussian, so a run costs one owner search
 constexpr int ITEM_RUN = 8;
 
-__global__ void __launch_bounds__(256, 3) k_bwd_items(
+__global__ void __launch_bounds__(256, 4) k_bwd_items(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ item_off, unsigned long long cap, float *__restrict__ part,
     int *__restrict__ queue) {
