@@ -1,4 +1,4 @@
-"""Separable voxelizer (SURVEY NEXT f3; the paper's isotropic representation,
+"""Separable voxelizer (the paper's isotropic representation,
 Sec. 4.1): when every Gaussian has a diagonal A (isotropic scales under any
 rotation, or the identity rotation) FVR becomes a sum of outer products of two
 small exponential tables per tile.  Same tolerances as the general voxelizer
