@@ -324,8 +324,13 @@ int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *me
  *  - Geometries whose ray tables exceed the array (e.g. more than ~130,000
  *    views x detector columns) return DGR_ERR_WS_TOO_SMALL; nothing runs.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current) and caches it; make that
- *    first call before any stream capture on the device.
+ *    (cudaGetSymbolAddress, with that device current) and caches it per
+ *    device ordinal; make that first call before any stream capture on the
+ *    device.  The cached address is invalid after cudaDeviceReset and under a
+ *    context other than the device's primary context: do not call this entry
+ *    point after either.
+ *  - Geometries are validated exactly as by dgr_project; the table size is
+ *    checked in 64-bit arithmetic (views x columns) before anything runs.
  *  - It calls no cudaMalloc, cudaFree or other allocating routine.
  *  - All calls on a device share the one array (it keeps the last call's
  *    tables, every call rewrites them in full): calls that overlap on the GPU

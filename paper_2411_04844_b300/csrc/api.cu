@@ -12,27 +12,15 @@ using namespace dgr;
 
 std::atomic<long long> dgr::g_launches{0};
 
-namespace {
-
-int g_deterministic = 1;
-
-constexpr int MAX_DIM = 32767;
-constexpr int MAX_VIEWS_BP = 1 << 20;
-
-bool grid_ok(const dgr_grid *g) {
+// Host-side validators shared by every entry point (also the no-allocation
+// projector).
+bool dgr::grid_ok(const dgr_grid *g) {
     return g && g->nx > 0 && g->ny > 0 && g->nz > 0 && g->nx <= MAX_DIM && g->ny <= MAX_DIM &&
            g->nz <= MAX_DIM && isfinite(g->h) && g->h > 0.f && isfinite(g->ox) &&
            isfinite(g->oy) && isfinite(g->oz);
 }
 
-bool k_ok(float k) {
-    if (!isfinite(k) || k == 0.f) return false;
-    if (k > 0.f) return true;
-    const float K = -k;
-    return K == floorf(K) && ((int)K % 2 == 1) && K < 65536.f;
-}
-
-bool geom_ok(const dgr_geom *geo) {
+bool dgr::geom_ok(const dgr_geom *geo) {
     if (!geo || !geo->angles) return false;
     if (geo->beam != DGR_PARALLEL && geo->beam != DGR_CONE) return false;
     if (geo->n_views <= 0 || geo->nu <= 0 || geo->nv <= 0 || geo->n_views > MAX_VIEWS_BP) return false;
@@ -43,9 +31,7 @@ bool geom_ok(const dgr_geom *geo) {
     return true;
 }
 
-bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
-
-bool geom_fits_grid(const dgr_grid *g, const dgr_geom *geo) {
+bool dgr::geom_fits_grid(const dgr_grid *g, const dgr_geom *geo) {
     // cone: the whole grid must lie in front of the source (every corner
     // strictly inside the source circle), so central projection is convex
     if (geo->beam != DGR_CONE) return true;
@@ -57,6 +43,19 @@ bool geom_fits_grid(const dgr_grid *g, const dgr_geom *geo) {
     }
     return sqrt(r2) < 0.999 * geo->dso;
 }
+
+namespace {
+
+int g_deterministic = 1;
+
+bool k_ok(float k) {
+    if (!isfinite(k) || k == 0.f) return false;
+    if (k > 0.f) return true;
+    const float K = -k;
+    return K == floorf(K) && ((int)K % 2 == 1) && K < 65536.f;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA; }
 
@@ -97,7 +96,8 @@ Layout layout_of(const dgr_ws_plan &p) {
     L.list_tmp = take(4 * (size_t)p.max_pairs);  // merge scratch of long tile lists
     L.partials = take(4 * (size_t)NMOM * (size_t)p.max_items);
     const int ninst = p.max_inst > 0 ? p.max_inst : 1;
-    L.rayxy = take(ray_table_bytes(p.max_views * p.max_nu, p.max_views, ninst * p.max_nv));
+    L.rayxy = take(ray_table_bytes((long long)p.max_views * p.max_nu, p.max_views,
+                                   (long long)ninst * p.max_nv));
     // residual x |D| for the backprojector (standalone calls; the step reuses its sinogram)
     // scaled residual of the backprojector, then (64-float aligned) one maximum per view
     L.sino_scaled = take(4 * ((size_t)p.max_views * p.max_nu * p.max_nv + 64 + (size_t)p.max_views));

@@ -9,6 +9,13 @@
 
 namespace dgr {
 
+// Host-side argument validators (api.cu), shared by every entry point.
+constexpr int MAX_DIM = 32767;          // grid side
+constexpr int MAX_VIEWS_BP = 1 << 20;   // views of one geometry
+bool grid_ok(const dgr_grid *g);
+bool geom_ok(const dgr_geom *geo);
+bool geom_fits_grid(const dgr_grid *g, const dgr_geom *geo);  // cone: grid inside the source circle
+
 // Voxel tile of the forward voxelizer: 8 (x) x 16 (y) x 32 (z).  A CTA of four
 // warps owns one tile; a warp owns an 8 x 4 patch in (x, y) and every lane
 // keeps the 32 z-voxels of its (x, y) column in registers, so the per-Gaussian
@@ -232,7 +239,7 @@ cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const fl
 cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st);
 
 // project.cu
-size_t ray_table_bytes(int n_tab, int n_views, int n_rows);
+size_t ray_table_bytes(long long n_tab, long long n_views, long long n_rows);
 cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st);
 // kev (optional): two events recorded right before / after the main kernel
 cudaError_t launch_project(const Batch &B, const RayXY *tab, int *status, cudaStream_t st,
@@ -261,7 +268,7 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
 // the projector of one instance with caller-provided tables (no workspace)
 cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY *tab,
                                   const float *vol, float *sino, cudaStream_t st);
-size_t ray_table_bytes_single(const dgr_geom &geo);
+size_t ray_table_bytes_single(const dgr_geom &geo);  // 64-bit sizes: no wrap-around
 // backprojector CTAs covering a grid (x blocks of 8 columns x ny x z passes)
 int bp_blocks(const dgr_grid &g, int &nbx, int &nbz);
 // brick backprojector: bricks per axis and the ray colour classes of a geometry

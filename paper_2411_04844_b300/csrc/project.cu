@@ -1226,7 +1226,7 @@ __global__ void __launch_bounds__(BB_THREADS) k_bp_brick(const __grid_constant__
 
 }  // namespace
 
-size_t ray_table_bytes(int n_tab, int n_views, int n_rows) {
+size_t ray_table_bytes(long long n_tab, long long n_views, long long n_rows) {
     return sizeof(RayXY) * (size_t)n_tab + ((sizeof(float2) * (size_t)n_views + 15) / 16) * 16 +
            sizeof(RowZ) * (size_t)n_rows;
 }
@@ -1473,7 +1473,7 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
 }
 
 size_t ray_table_bytes_single(const dgr_geom &geo) {
-    return ray_table_bytes(geo.n_views * geo.nu, geo.n_views, geo.nv);
+    return ray_table_bytes((long long)geo.n_views * geo.nu, geo.n_views, geo.nv);
 }
 
 cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY *tab,

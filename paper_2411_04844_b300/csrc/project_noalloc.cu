@@ -20,7 +20,9 @@ void *g_scratch_ptr[MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device.  The array's
 // name is a host-side stand-in in host code, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached.  The cache is keyed by
+// device ordinal: after cudaDeviceReset (which unloads the module) or under a
+// context other than the device's primary one the cached address is stale.
 cudaError_t scratch_of_current_device(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -37,38 +39,21 @@ cudaError_t scratch_of_current_device(void **out) {
     return cudaSuccess;
 }
 
-bool args_ok(const dgr_grid *g, const dgr_geom *geo, const float *vol, const float *sino) {
-    if (!g || !geo || !vol || !sino || !geo->angles) return false;
-    if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || g->nx > 32767 || g->ny > 32767 || g->nz > 32767)
-        return false;
-    if (!isfinite(g->h) || !(g->h > 0.f) || !isfinite(g->ox) || !isfinite(g->oy) || !isfinite(g->oz))
-        return false;
-    if (geo->beam != DGR_PARALLEL && geo->beam != DGR_CONE) return false;
-    if (geo->n_views <= 0 || geo->nu <= 0 || geo->nv <= 0) return false;
-    if (!(isfinite(geo->pu) && geo->pu > 0.f && isfinite(geo->pv) && geo->pv > 0.f)) return false;
-    if (geo->beam == DGR_CONE) {
-        if (!(isfinite(geo->dso) && isfinite(geo->dsd) && geo->dso > 0.f && geo->dsd > geo->dso))
-            return false;
-        // the grid must lie strictly inside the source circle
-        const double o[2] = {g->ox, g->oy}, e[2] = {g->nx * (double)g->h, g->ny * (double)g->h};
-        double r2 = 0;
-        for (int a = 0; a < 2; ++a) {
-            const double m = fmax(fabs(o[a]), fabs(o[a] + e[a]));
-            r2 += m * m;
-        }
-        if (!(sqrt(r2) < 0.999 * geo->dso)) return false;
-    }
-    return true;
-}
+// Ray-table entries (one per view x detector column) the array can hold.
+constexpr long long MAX_TABLE_ENTRIES = DGR_NOALLOC_SCRATCH_BYTES / (long long)sizeof(dgr::RayXY);
 
 }  // namespace
 
 extern "C" int dgr_project_noalloc(const dgr_grid *grid, const dgr_geom *geom, const float *vol,
                                    float *sino, cudaStream_t stream) {
-    if (!args_ok(grid, geom, vol, sino)) return DGR_ERR_ARG;
-    if (dgr::ray_table_bytes_single(*geom) > (size_t)DGR_NOALLOC_SCRATCH_BYTES)
-        return DGR_ERR_WS_TOO_SMALL;
+    // the same validation as dgr_project (shared validators)
+    if (!dgr::grid_ok(grid) || !dgr::geom_ok(geom) || !vol || !sino) return DGR_ERR_ARG;
+    if (!dgr::geom_fits_grid(grid, geom)) return DGR_ERR_ARG;
     if ((long long)grid->nx * grid->ny * grid->nz >= (1ll << 31)) return DGR_ERR_ARG;
+    // scratch capacity, in 64-bit counts before any int arithmetic on the tables
+    if ((long long)geom->n_views * geom->nu > MAX_TABLE_ENTRIES ||
+        dgr::ray_table_bytes_single(*geom) > (size_t)DGR_NOALLOC_SCRATCH_BYTES)
+        return DGR_ERR_WS_TOO_SMALL;
     void *scratch = nullptr;
     if (scratch_of_current_device(&scratch) != cudaSuccess) return DGR_ERR_CUDA;
     dgr::RayXY *tab = static_cast<dgr::RayXY *>(scratch);

@@ -58,3 +58,27 @@ def test_host_side_validation_without_gpu():
 def test_library_is_sm103a_only():
     from paper_2411_04844_b300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_noalloc_projector_refuses_on_the_host():
+    """dgr_project_noalloc validates like dgr_project and sizes its ray tables
+    in 64-bit arithmetic: a views x columns product just above 2^32 (which
+    would wrap to a small 32-bit count) is refused before anything runs, as
+    are more views than any geometry may have.  The pointers are never
+    dereferenced on these paths."""
+    from paper_2411_04844_b300 import dgr
+    L = dgr.lib()
+    g = dgr.Grid(16, 16, 16, 1.0, -8.0, -8.0, -8.0)
+    fake = ctypes.c_void_p(256)
+    # 65536 views x 65538 columns = 2^32 + 2^17 entries (a 17 GB sinogram at one row)
+    geo = dgr.Geom(dgr.DGR_PARALLEL, 65536, 65538, 1, 1.0, 1.0, 0.0, 0.0, 256)
+    assert (65536 * 65538) % (1 << 32) * 32 <= dgr.NOALLOC_SCRATCH_BYTES
+    assert L.dgr_project_noalloc(ctypes.byref(g), ctypes.byref(geo), fake, fake,
+                                 None) == dgr.DGR_ERR_WS_TOO_SMALL
+    geo = dgr.Geom(dgr.DGR_PARALLEL, (1 << 20) + 1, 1, 1, 1.0, 1.0, 0.0, 0.0, 256)
+    assert L.dgr_project_noalloc(ctypes.byref(g), ctypes.byref(geo), fake, fake,
+                                 None) == dgr.DGR_ERR_ARG
+    # a cone whose source circle does not contain the grid, as dgr_project refuses
+    geo = dgr.Geom(dgr.DGR_CONE, 4, 8, 8, 1.0, 1.0, 10.0, 20.0, 256)
+    assert L.dgr_project_noalloc(ctypes.byref(g), ctypes.byref(geo), fake, fake,
+                                 None) == dgr.DGR_ERR_ARG

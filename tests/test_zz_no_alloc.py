@@ -2,8 +2,8 @@
 memory (its scratch is a fixed device array, not a workspace).  Through the C
 ABI it must give what dgr_project gives -- same tolerance as the projector
 parity tests (relative L2 <= 1e-5) -- on two calls in a row with different
-geometries, and refuse a geometry whose ray tables exceed the fixed array.
-Collected last so that a failure here stops a -x run after everything else."""
+geometries, refuse a geometry whose ray tables exceed the fixed array, and
+leave the device's free memory unchanged over repeated calls.  Collected last so that a failure here stops a -x run after everything else."""
 import numpy as np
 import pytest
 
@@ -61,3 +61,23 @@ def test_noalloc_projector_refuses_oversized_geometry():
     out = torch.zeros(geo.shape, device=DEV)
     with pytest.raises(dgr.DgrError, match="workspace plan too small"):
         dgr.dgr_project_noalloc(grid, gg, vol, out)
+
+
+def test_noalloc_projector_leaves_free_memory_unchanged():
+    """After a first call (which loads the kernels and looks up the scratch
+    address), further calls take no device memory: the driver's free-memory
+    count is the same before and after them."""
+    gs = synth.GridSpec((32, 32, 32), 1.0, (-16.0, -16.0, -16.0))
+    geo = synth.cone_geom(16, 48, 40, 1.5, 1.5, 100.0, 150.0)
+    grid, gg, ang, vol = _case(gs, geo, 4)
+    out = torch.empty(geo.shape, device=DEV)
+    dgr.dgr_project_noalloc(grid, gg, vol, out)
+    torch.cuda.synchronize()
+    first = out.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        dgr.dgr_project_noalloc(grid, gg, vol, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(out, first)
