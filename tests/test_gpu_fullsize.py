@@ -1,7 +1,15 @@
 """Parity at the full size of the benchmark workload (50,000 Gaussians, 256^3,
-cone beam 50 views x 256^2), in the launch configuration bench.py times:
-sampled voxels, sampled views, sampled Gaussians, the adjoint identity at full
-size, and the loss of one full optimisation step."""
+cone beam 50 views x 256^2), in the launch configuration bench.py times,
+element by element against the FP64 oracle: the whole volume (Eq. 4 with
+3-sigma confinement, Sec. 4.1), all 50 views of the projection and the whole
+backprojection (Sec. 4.3), the gradients of all 50,000 Gaussians, the
+adjoint identity at full size, and the loss of one full optimisation step.
+
+Tolerances as in the small parity tests: volume relative L2 <= 1e-5 and
+max |diff| <= 1e-5 max(rho); sinogram relative L2 <= 1e-5; backprojection of
+non-negative data relative L2 <= 1e-5, of signed data |diff| <= 1e-5 |BP(|y|)|
+(the FP32 chord lengths' error does not cancel with the data's signs);
+gradients relative L2 <= 1e-4 per parameter kind."""
 import numpy as np
 import pytest
 
@@ -36,22 +44,22 @@ def problem():
     return dict(wl=wl, f=f, grid=grid, ang=ang, geom=geom, ws=ws, t=(mu, s, q, rho))
 
 
-def test_fullsize_voxelize_sampled(problem):
+def test_fullsize_voxelize_whole_volume(problem):
     P = problem
     wl, f = P["wl"], P["f"]
     vol = torch.empty(wl.grid.shape, device=DEV)
     dgr.dgr_voxelize(P["grid"], *P["t"], 3.0, vol, P["ws"])
     torch.cuda.synchronize()
     assert dgr.dgr_status(P["ws"]) == 0
-    rng = np.random.default_rng(41)
-    pts = np.stack([rng.integers(0, 256, 400) for _ in range(3)], 1)
-    vo = O.voxelize_points(oracle_grid(wl.grid), f.mu, f.s, f.q, f.rho, pts, 3.0)
-    vg = vol[pts[:, 2], pts[:, 1], pts[:, 0]].cpu().numpy()
+    vo = O.voxelize(oracle_grid(wl.grid), f.mu, f.s, f.q, f.rho, 3.0)
+    vg = vol.cpu().numpy().astype(np.float64)
+    err = np.max(np.abs(vg - vo))
+    print(f"256^3 volume: rel-L2 {rel_l2(vg, vo):.3e}, max-abs {err:.3e}, max V {vo.max():.3f}")
     assert rel_l2(vg, vo) <= 1e-5
-    assert np.max(np.abs(vg - vo)) <= 1e-5 * float(f.rho.max()) * max(1.0, float(np.abs(vo).max()))
+    assert err <= 1e-5 * float(f.rho.max()), err
 
 
-def test_fullsize_project_sampled_views_and_adjoint(problem):
+def test_fullsize_project_all_views_backproject_and_adjoint(problem):
     P = problem
     wl = P["wl"]
     rng = np.random.default_rng(42)
@@ -62,17 +70,31 @@ def test_fullsize_project_sampled_views_and_adjoint(problem):
     dgr.dgr_project(P["grid"], P["geom"], T(vol), sg, P["ws"])
     dgr.dgr_backproject(P["grid"], P["geom"], T(y), bg, P["ws"])
     torch.cuda.synchronize()
-    views = np.array([0, 13, 29, 41])
-    g = wl.geom
-    sub = O.Geom(g.beam, g.angles[views], g.nu, g.nv, g.pu, g.pv, g.dso, g.dsd)
-    so = O.project(oracle_grid(wl.grid), sub, vol)
-    assert rel_l2(sg[torch.as_tensor(views, device=DEV)].cpu().numpy(), so) <= 1e-5
+    og, oo = oracle_grid(wl.grid), oracle_geom(wl.geom)
+    so = O.project(og, oo, vol)
+    assert rel_l2(sg.cpu().numpy(), so) <= 1e-5, rel_l2(sg.cpu().numpy(), so)
+    # backprojection: of non-negative data, relative L2 <= 1e-5; of signed data
+    # (random signs cancel in every voxel's sum) the error is bounded relative
+    # to the backprojection of |y| -- each FP32 chord length is a difference
+    # of plane-crossing parameters along a ray ~360 voxels long (relative
+    # error ~1e-5 per chord), so a cancelling sum keeps that error per term
+    ya = np.abs(y)
+    ba = torch.empty(wl.grid.shape, device=DEV)
+    dgr.dgr_backproject(P["grid"], P["geom"], T(ya), ba, P["ws"])
+    torch.cuda.synchronize()
+    boa = O.backproject(og, oo, ya)
+    assert rel_l2(ba.cpu().numpy(), boa) <= 1e-5, rel_l2(ba.cpu().numpy(), boa)
+    bo = O.backproject(og, oo, y)
+    err = np.linalg.norm(bg.cpu().numpy().astype(np.float64) - bo)
+    print(f"backprojection of signed data: rel-L2 {rel_l2(bg.cpu().numpy(), bo):.3e}, "
+          f"relative to |BP(|y|)| {err / np.linalg.norm(boa):.3e}")
+    assert err <= 1e-5 * np.linalg.norm(boa)
     lhs = float((sg.double() * T(y).double()).sum())
     rhs = float((T(vol).double() * bg.double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs))
 
 
-def test_fullsize_voxelize_backward_sampled(problem):
+def test_fullsize_voxelize_backward_all_gaussians(problem):
     P = problem
     wl, f = P["wl"], P["f"]
     rng = np.random.default_rng(43)
@@ -82,10 +104,9 @@ def test_fullsize_voxelize_backward_sampled(problem):
     dgr.dgr_voxelize_backward(P["grid"], *P["t"], 3.0, T(GV), *out, P["ws"])
     torch.cuda.synchronize()
     assert dgr.dgr_status(P["ws"]) == 0
-    idx = np.concatenate([rng.choice(n, 80, replace=False), np.argsort(-f.s.max(1))[:4]])
-    ref = O.voxelize_backward(oracle_grid(wl.grid), f.mu[idx], f.s[idx], f.q[idx], f.rho[idx], GV, 3.0)
+    ref = O.voxelize_backward(oracle_grid(wl.grid), f.mu, f.s, f.q, f.rho, GV, 3.0)
     for o, r, name in zip(out, ref, ("mu", "s", "q", "rho")):
-        assert rel_l2(o[torch.as_tensor(idx, device=DEV)].cpu().numpy(), r) <= 1e-4, name
+        assert rel_l2(o.cpu().numpy(), r) <= 1e-4, (name, rel_l2(o.cpu().numpy(), r))
 
 
 def test_fullsize_step_loss(problem):
@@ -111,7 +132,7 @@ def test_fullsize_step_loss(problem):
 
 def test_fullsize_step_timed_kernel_events(problem):
     """dgr_step_timed with the kernel events does the same step as dgr_step
-    (same loss, same parameters, bit for bit), and the two kernel intervals
+    (same loss, same parameters, bit for bit), and the four kernel intervals
     lie inside their phases."""
     P = problem
     wl = P["wl"]
@@ -138,3 +159,6 @@ def test_fullsize_step_timed_kernel_events(problem):
     assert ev[3].elapsed_time(ev[7]) >= 0 and ev[8].elapsed_time(ev[4]) >= 0  # backproject phase
     assert ev[1].elapsed_time(ev[9]) >= 0 and ev[10].elapsed_time(ev[2]) >= 0  # project phase
     assert ev[7].elapsed_time(ev[8]) <= ev[3].elapsed_time(ev[4])
+    assert ev[0].elapsed_time(ev[11]) >= 0 and ev[12].elapsed_time(ev[1]) >= 0  # voxelize phase
+    assert ev[4].elapsed_time(ev[13]) >= 0 and ev[14].elapsed_time(ev[5]) >= 0  # adjoint phase
+    assert ev[11].elapsed_time(ev[12]) > 0 and ev[13].elapsed_time(ev[14]) > 0

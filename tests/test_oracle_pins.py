@@ -501,6 +501,63 @@ def test_lr_schedule_endpoints_and_transforms():
         assert np.max(np.abs(a - b)) < 1e-12
 
 
+def _step_fd_problem():
+    g = grid_of(16)
+    gs = synth.GridSpec((16, 16, 16), 1.0, g.org)
+    f = synth.gaussian_field(synth.rng_for(3, 520), 12, gs, ("loguniform", 0.6, 3.0),
+                             unnormalised_q=True)
+    f.rho = np.clip(f.rho, 0.05, 1.0).astype(np.float32)
+    geo = synth.parallel_geom(5, 22, 18, 1.0, 1.0)
+    og = O.Geom(geo.beam, geo.angles, geo.nu, geo.nv, geo.pu, geo.pv)
+    phantom = synth.ellipsoid_phantom(synth.rng_for(3, 521), gs, 4)
+    meas = O.project(g, og, phantom)
+    return g, og, f, meas
+
+
+@pytest.mark.parametrize("weights", [(1.0, 0.0, 0.0), (0.6, 0.2, 1.0)])
+def test_step_gradients_in_optimiser_variables_match_central_differences(weights):
+    """The gradients oracle.step hands to Adam are d(loss)/d(theta) for the
+    optimiser variables theta = ((mu - c)/half, log s, raw q, softplus^-1 rho):
+    the chain factors half, s and sigmoid(theta_rho) are checked against FP64
+    central differences of the whole objective (Eq. 13 with the given weights,
+    box integers fixed) in theta, for every entry."""
+    g, og, f, meas = _step_fd_problem()
+    d = lambda a: np.asarray(a, np.float64)
+    th0 = O.to_opt(g, d(f.mu), d(f.s), d(f.q), d(f.rho))
+
+    def loss_grads(th):
+        m = {k: np.zeros_like(a) for k, a in th.items()}
+        v = {k: np.zeros_like(a) for k, a in th.items()}
+        lo, _, gr = O.step(g, og, f.mu, f.s, f.q, f.rho, th, m, v, 1, meas, 3.0, 3e-4, 3e-5, 10,
+                           weights=weights)
+        return lo, gr
+
+    # no L1 residual that a Gaussian reaches may sit near its kink (rays no
+    # box meets stay at exactly 0 under every perturbation; where the
+    # measurement is 0 a positive prediction stays positive)
+    mu0, s0, q0, r0 = O.from_opt(g, th0)
+    _, box = O.footprint(g, f.mu, f.s, f.q, 3.0)
+    pred = O.project(g, og, O.voxelize_core(g, mu0, s0, q0, r0, box))
+    assert np.min(np.abs(pred - meas)[(pred > 0) & (meas > 0)]) > 1e-4
+    _, grads = loss_grads(th0)
+    for k in ("mu", "s", "q", "rho"):
+        ga = grads[k].reshape(-1)
+        scale = np.max(np.abs(ga))
+        assert scale > 0
+        worst = 0.0
+        for j in range(ga.size):
+            th = {kk: a.copy() for kk, a in th0.items()}
+            # step near the cube root of FP64 epsilon (central differences)
+            eps = 1e-5 * max(1.0, abs(th[k].reshape(-1)[j]))
+            th[k].reshape(-1)[j] += eps
+            lp, _ = loss_grads(th)
+            th[k].reshape(-1)[j] -= 2 * eps
+            lm, _ = loss_grads(th)
+            fd = (lp - lm) / (2 * eps)
+            worst = max(worst, abs(fd - ga[j]) / max(abs(fd), 1e-3 * scale))
+        assert worst < 1e-6, (k, worst)
+
+
 # ---------------------------------------------------------------------------
 # full objective: SSIM (projection domain) and TV (volume), Sec. 4.3 / App. D.1
 # ---------------------------------------------------------------------------
