@@ -513,7 +513,8 @@ int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t s
 // voxelize -> project -> L1 -> backproject -> voxelize adjoint -> Adam, for a
 // batch of problems, one launch per phase
 // ev: phase events (DGR_STEP_EVENTS) or nullptr; kev: optional events
-// around the backprojector's and the projector's main kernels (4)
+// around the main kernels of the backprojector, the projector, the voxelizer
+// and the voxelize adjoint (2 each)
 static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *params,
                       const float *const *measured, float *loss_out, dgr_ws *ws,
                       cudaStream_t stream, cudaEvent_t *ev, const cudaEvent_t *kev = nullptr) {
@@ -582,7 +583,7 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], stream) : cudaSuccess; };
     cudaError_t e = mark(0);
     if (e == cudaSuccess) e = launch_prep(B, prep, ws_ptr<uint32_t>(ws, ws->itemcnt), status, stream);
-    if (e == cudaSuccess) e = launch_voxelize(B, prep, ws, g_deterministic, stream);
+    if (e == cudaSuccess) e = launch_voxelize(B, prep, ws, g_deterministic, stream, kev ? kev + 4 : nullptr);
     if (e == cudaSuccess) e = mark(1);
     if (e == cudaSuccess) e = launch_ray_tables(B, tab, stream);
     if (e == cudaSuccess) e = launch_project(B, tab, ws_ptr<int>(ws, ws->status), stream, kev ? kev + 2 : nullptr);
@@ -600,7 +601,7 @@ static int step_batch(int n_inst, const dgr_problem *probs, const dgr_params *pa
         e = launch_loss_final(B, ws_ptr<float>(ws, ws->loss_part), L1_BLOCKS, ws_ptr<float>(ws, ws->ssim_part),
                               ws_ptr<float>(ws, ws->tv_part), stream);
     if (e == cudaSuccess) e = mark(4);
-    if (e == cudaSuccess) e = launch_voxelize_backward(B, prep, ws, stream);
+    if (e == cudaSuccess) e = launch_voxelize_backward(B, prep, ws, stream, kev ? kev + 6 : nullptr);
     if (e == cudaSuccess) e = mark(5);
     if (e == cudaSuccess) e = launch_adam(B, stream);
     if (e == cudaSuccess) e = mark(6);

@@ -66,10 +66,17 @@ __host__ __device__ inline void item_range(int c, int ex, int ey, int ly, int hy
 constexpr float LOG2E = 1.4426950408889634f;
 
 // Per-Gaussian record written by the prep kernel (64 bytes, 4 x float4).
+// The exponent -1/2 log2(e) d^T A d is kept in column form: along the z column
+// through (dx, dy) it peaks at dz* = zx dx + zy dy with the value
+// m00 dx^2 + m11 dy^2 + m01 dx dy (the xy block of Sigma inverted, scaled), and
+//     q(dz) = (m00 dx^2 + m11 dy^2 + m01 dx dy) + a22 (dz - dz*)^2,
+// a sum of two terms <= 0: no cancellation however far the peak lies from the
+// centre plane (an expansion about dz = 0 cancels terms of the size of the
+// box corner's exponent for a tilted, elongated Gaussian).
 struct __align__(16) Prep {
     float dx, dy, dz, rho;      // delta = u - a (voxel units), intensity
-    float a00, a11, a22, a01;   // -1/2 log2(e) * A, off-diagonals doubled
-    float a02, a12;
+    float m00, m11, a22, m01;   // x 1/2 log2(e): (Sigma_xy)^-1 (off-diagonal doubled), A_zz
+    float zx, zy;               // the column's peak: dz* = zx dx + zy dy
     int ax, ay;                 // anchor a = floor(u)
     int az;
     int bx, by, bz;             // box per axis: lo | hi << 16 (lo > hi: empty)
@@ -231,12 +238,14 @@ cudaError_t launch_prep(const Batch &B, Prep *prep, uint32_t *itemcnt, int *stat
 cudaError_t launch_count_pairs(const Batch &B, const Prep *prep, dgr_ws *ws, unsigned long long cap,
                                cudaStream_t st);
 cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int deterministic,
-                            cudaStream_t st);
+                            cudaStream_t st, const cudaEvent_t *kev = nullptr);
 cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const float *s,
                              const float *q, float k, int *anchor, int *box, cudaStream_t st);
 
 // voxelize_bwd.cu (grad_vol = Inst::vol; outputs Inst::g_*)
-cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st);
+// kev (optional): two events recorded right before / after the main kernel
+cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st,
+                                     const cudaEvent_t *kev = nullptr);
 
 // project.cu
 size_t ray_table_bytes(long long n_tab, long long n_views, long long n_rows);

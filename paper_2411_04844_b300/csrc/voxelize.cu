@@ -150,29 +150,59 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
         const double u = ((double)m[a] - org[a]) / h - 0.5;
         del[a] = (float)(u - (double)F.an[a]);
     }
-    // A = h^2 R diag(1/s^2) R^T (voxel units), scaled by -1/2 log2(e)
-    const float *R = F.R;
-    const float h2 = g.h * g.h;
-    const float is0 = h2 / (sc[0] * sc[0]), is1 = h2 / (sc[1] * sc[1]), is2 = h2 / (sc[2] * sc[2]);
-    float A[6];
+    // column form of the exponent (FP64 per Gaussian): Sigma = R diag(s^2) R^T
+    // in voxel units from the normalised quaternion; the z column through
+    // (dx, dy) peaks at dz* = Sigma_z,xy (Sigma_xy)^-1 (dx, dy) with the value
+    // -1/2 (dx, dy) (Sigma_xy)^-1 (dx, dy)^T, and A_zz = 1 / Var(z | x, y)
+    // = sum_k R_zk^2 / s_k^2 (a sum of positive terms).  The xy block is
+    // inverted directly: the Schur complement of A would cancel for thin,
+    // tilted Gaussians.  Scaled by -1/2 log2(e) for ex2.
+    const double c = -0.5 * (double)LOG2E;
+    double m00, m11, m01, zx, zy, azz;
+    bool diag;
     if (sc[0] == sc[1] && sc[1] == sc[2]) {
-        // isotropic (the paper's representation): A = h^2 / s^2 I for any rotation
-        A[0] = A[1] = A[2] = is0;
-        A[3] = A[4] = A[5] = 0.f;
+        // isotropic (the paper's representation): diagonal for any rotation
+        const double v = ((double)sc[0] / h) * ((double)sc[0] / h);
+        m00 = m11 = azz = 1.0 / v;
+        m01 = zx = zy = 0.0;
+        diag = true;
     } else {
-        A[0] = R[0] * R[0] * is0 + R[1] * R[1] * is1 + R[2] * R[2] * is2;  // 00
-        A[1] = R[3] * R[3] * is0 + R[4] * R[4] * is1 + R[5] * R[5] * is2;  // 11
-        A[2] = R[6] * R[6] * is0 + R[7] * R[7] * is1 + R[8] * R[8] * is2;  // 22
-        A[3] = R[0] * R[3] * is0 + R[1] * R[4] * is1 + R[2] * R[5] * is2;  // 01
-        A[4] = R[0] * R[6] * is0 + R[1] * R[7] * is1 + R[2] * R[8] * is2;  // 02
-        A[5] = R[3] * R[6] * is0 + R[4] * R[7] * is1 + R[5] * R[8] * is2;  // 12
+        const double q0 = qq.x, q1 = qq.y, q2 = qq.z, q3 = qq.w;
+        const double iq = 1.0 / sqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+        const double w = q0 * iq, x = q1 * iq, y = q2 * iq, z = q3 * iq;
+        const double Rd[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                              2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                              2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+        double v[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = ((double)sc[k] / h) * ((double)sc[k] / h);
+        double S[6] = {0, 0, 0, 0, 0, 0};  // 00 11 22 01 02 12
+        azz = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            S[0] += Rd[k] * Rd[k] * v[k];
+            S[1] += Rd[3 + k] * Rd[3 + k] * v[k];
+            S[3] += Rd[k] * Rd[3 + k] * v[k];
+            S[4] += Rd[k] * Rd[6 + k] * v[k];
+            S[5] += Rd[3 + k] * Rd[6 + k] * v[k];
+            azz += Rd[6 + k] * Rd[6 + k] / v[k];
+        }
+        const double det = S[0] * S[1] - S[3] * S[3];
+        m00 = S[1] / det;
+        m11 = S[0] / det;
+        m01 = -S[3] / det;
+        zx = m00 * S[4] + m01 * S[5];
+        zy = m01 * S[4] + m11 * S[5];
+        diag = S[3] == 0.0 && S[4] == 0.0 && S[5] == 0.0;
     }
     // a Gaussian with off-diagonal terms rules out the separable voxelizer
-    if (A[3] != 0.f || A[4] != 0.f || A[5] != 0.f) status[SEP_FLAG] = 1;
-    const float c = -0.5f * LOG2E;
+    if (!diag) status[SEP_FLAG] = 1;
     P.dx = del[0]; P.dy = del[1]; P.dz = del[2]; P.rho = r;
-    P.a00 = c * A[0]; P.a11 = c * A[1]; P.a22 = c * A[2];
-    P.a01 = 2.f * c * A[3]; P.a02 = 2.f * c * A[4]; P.a12 = 2.f * c * A[5];
+    P.m00 = (float)(c * m00); P.m11 = (float)(c * m11); P.m01 = (float)(2.0 * c * m01);
+    P.a22 = (float)(c * azz);
+    P.zx = diag ? 0.f : (float)zx;
+    P.zy = diag ? 0.f : (float)zy;
+    if (diag) P.m01 = 0.f;
     P.ax = F.an[0]; P.ay = F.an[1]; P.az = F.an[2];
     // an axis that misses the grid empties the whole box (packed as lo 1, hi 0)
     const bool empty = F.lo[0] > F.hi[0] || F.lo[1] > F.hi[1] || F.lo[2] > F.hi[2];
@@ -326,32 +356,66 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Masks of a z group of TZG partly inside a box: row [lo][hi] adds 0 to the
-// exponent of the layers lo..hi of the group and -1e30 (ex2 -> 0) to the
-// others, so the range test costs one packed FP32 add per pair on the FMA
+
+// Layer masks of a z group of TZG partly inside a box: row lo * TZG + hi adds
+// 0 to the exponent of the layers lo..hi of the group and -1e30 (ex2 -> 0) to
+// the others, so the range test costs one packed FP32 add per pair on the FMA
 // pipe instead of integer compares and selects per layer.  Adding 0 leaves
 // the exponent's bits as they are (-0 becomes +0; ex2 of either is 1).
 struct ZMask {
-    float v[TZG][TZG][TZG];
+    float4 v[TZG * TZG][TZG / 4];
 };
 constexpr ZMask make_zmask() {
     ZMask t{};
     for (int lo = 0; lo < TZG; ++lo)
         for (int hi = 0; hi < TZG; ++hi)
-            for (int k = 0; k < TZG; ++k) t.v[lo][hi][k] = (lo <= k && k <= hi) ? 0.f : -1e30f;
+            for (int k4 = 0; k4 < TZG / 4; ++k4) {
+                float e[4] = {};
+                for (int c = 0; c < 4; ++c) {
+                    const int k = 4 * k4 + c;
+                    e[c] = (lo <= k && k <= hi) ? 0.f : -1e30f;
+                }
+                t.v[lo * TZG + hi][k4] = float4{e[0], e[1], e[2], e[3]};
+            }
     return t;
 }
 __constant__ ZMask c_zmask = make_zmask();
 
+// Per (tile, Gaussian) record of a staged chunk, built once per CTA by one
+// thread, so that a warp's visit of the Gaussian costs only the per-lane set-up
+// of its column's quadratic:
+//   r0 = (a_x - x0, a_y - y0) as exact floats and delta_x, delta_y
+//   r1 = (m00, m11, m01, rho), r2 = (zx, zy, a22, dz0 = (z0 - a_z) - delta_z)
+//   lane masks: per warp, bit l set when lane l's (x, y) column lies in the box
+//   zinfo: bits 0-3 the z groups of TZG layers the box reaches, bits 4-7 those
+//          it covers whole; rows: per group, the row (lo * TZG + hi) of the
+//          layer-mask table for a partly covered group
+// Every value a lane computes from a record is computed with the same
+// operations, in the same order, as from the prep record itself.
+struct VisitChunk {
+    float4 r0[VOX_CHUNK], r1[VOX_CHUNK], r2[VOX_CHUNK];
+    unsigned lanes[VOX_THREADS / 32][VOX_CHUNK];
+    int zinfo[VOX_CHUNK], rows[VOX_CHUNK];
+};
+
 // a3: persistent CTAs take tiles from a global queue (tiles of every instance
 // back to back).  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
 // (lx, ly) = (lane & 7, lane >> 3), and the column z in [tz0, tz0 + TZ).
+// Per chunk of VOX_CHUNK Gaussians of the tile's list: the staging threads
+// build the visit records; each warp visits (ballot over the chunk) only the
+// Gaussians whose box covers one of its columns, in list order; per visit a
+// lane sets up its column's peak (value qmin, offset t0 of the tile's first
+// layer from the peak) and evaluates q = qmin + a22 t^2, t = t0 + k, on the z
+// groups of TZG layers the box reaches (a partly covered group adds 0 or -1e30 from the
+// layer-mask table to the exponent: ex2 of the latter is 0).
 template <int TZ>
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
     unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off) {
-    __shared__ float4 sp[VOX_CHUNK * 4];
+    static_assert(TZ / TZG <= 4, "z groups are tracked in 4-bit masks");
+    constexpr int NG = TZ / TZG;
+    __shared__ VisitChunk vc;
     // the running per-voxel sums and their Kahan compensations: one column per
     // thread (touched by that thread only), kept out of registers so that more
     // CTAs fit on an SM
@@ -359,8 +423,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     __shared__ int s_tile;
     if (sep_off && *sep_off == 0) return;  // every Gaussian separable: k_voxelize_sep runs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float lxf = (float)(lane & 7), lyf = (float)(4 * w + (lane >> 3));
     for (;;) {
-        __syncthreads();  // everyone is done with s_tile and sp
+        __syncthreads();  // everyone is done with s_tile and the records
         if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
         __syncthreads();
         const int tg = s_tile;
@@ -371,9 +436,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
         const int tx = t % I.ntx, ty = (t / I.ntx) % I.nty, tz = t / (I.ntx * I.nty);
         const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
         const int x = x0 + (lane & 7);
-        const int wy0 = y0 + 4 * w;
-        const int y = wy0 + (lane >> 3);
-        // running per-voxel sums with Kahan compensation (per chunk, below)
+        const int y = y0 + 4 * w + (lane >> 3);
 #pragma unroll
         for (int k = 0; k < TZ; ++k) s_acc[k][threadIdx.x] = s_cmp[k][threadIdx.x] = 0.f;
 
@@ -382,57 +445,88 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
         for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
             const int nc = (int)min((unsigned long long)VOX_CHUNK, e - c0);
             if (c0 != b) __syncthreads();
-            for (int i = threadIdx.x; i < nc * 4; i += VOX_THREADS) {
-                const uint32_t gi = list[c0 + (i >> 2)];
-                sp[i] = reinterpret_cast<const float4 *>(prep + gi)[i & 3];
+            if (threadIdx.x < nc) {
+                const int j = threadIdx.x;
+                const float4 *pp = reinterpret_cast<const float4 *>(prep + list[c0 + j]);
+                const float4 p0 = pp[0], p1 = pp[1], p2 = pp[2], p3 = pp[3];
+                const int ax = __float_as_int(p2.z), ay = __float_as_int(p2.w), az = __float_as_int(p3.x);
+                const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z), bz = __float_as_int(p3.w);
+                const int xl = max(box_lo(bx) - x0, 0), xh = min(box_hi(bx) - x0, TX - 1);
+                const int yl = box_lo(by) - y0, yh = box_hi(by) - y0;
+                const int zl = max(box_lo(bz) - z0, 0), zh = min(box_hi(bz) - z0, TZ - 1);
+                const unsigned xm = xl <= xh ? (0xffu >> (TX - 1 - xh)) & (0xffu << xl) : 0u;
+#pragma unroll
+                for (int ww = 0; ww < VOX_THREADS / 32; ++ww) {
+                    unsigned m = 0u;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (4 * ww + r >= yl && 4 * ww + r <= yh) m |= xm << (8 * r);
+                    vc.lanes[ww][j] = m;
+                }
+                int act = 0, full = 0, rows = 0;
+#pragma unroll
+                for (int g8 = 0; g8 < NG; ++g8) {
+                    const int lo = zl - g8 * TZG, hi = zh - g8 * TZG;
+                    if (hi >= 0 && lo < TZG && zl <= zh) {
+                        act |= 1 << g8;
+                        if (lo <= 0 && hi >= TZG - 1) full |= 1 << g8;
+                        rows |= (max(lo, 0) * TZG + min(hi, TZG - 1)) << (8 * g8);
+                    }
+                }
+                vc.zinfo[j] = act | (full << 4);
+                vc.rows[j] = rows;
+                vc.r0[j] = make_float4((float)(ax - x0), (float)(ay - y0), p0.x, p0.y);
+                vc.r1[j] = make_float4(p1.x, p1.y, p1.w, p0.w);
+                vc.r2[j] = make_float4(p2.x, p2.y, p1.z, (float)(z0 - az) - p0.z);
             }
             __syncthreads();
+            // this warp's visits, in list order
+            unsigned long long vis =
+                (unsigned long long)__ballot_sync(0xffffffffu, lane < nc && vc.lanes[w][lane] != 0u) |
+                ((unsigned long long)__ballot_sync(0xffffffffu, lane + 32 < nc && vc.lanes[w][lane + 32] != 0u)
+                 << 32);
             // the chunk's plain sums, z pairs in packed FP32 (each half rounds
             // exactly as the scalar FMA); a z outside a box contributes
             // exp2(-inf) = 0
             float2 cs[TZ / 2];
 #pragma unroll
             for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(0.f, 0.f);
-            for (int j = 0; j < nc; ++j) {
-                const float4 p3 = sp[4 * j + 3];
-                const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z),
-                          bz = __float_as_int(p3.w);
-                const int lx = box_lo(bx), hx = box_hi(bx), ly = box_lo(by), hy = box_hi(by);
-                const int zlo = max(box_lo(bz) - z0, 0), zhi = min(box_hi(bz) - z0, TZ - 1);
-                // warp-uniform skip: the warp's 8 x 4 patch or the z range misses the box
-                if (hx < x0 || lx > x0 + 7 || hy < wy0 || ly > wy0 + 3 || zlo > zhi) continue;
-                const float4 p0 = sp[4 * j], p1 = sp[4 * j + 1], p2 = sp[4 * j + 2];
-                const int ax = __float_as_int(p2.z), ay = __float_as_int(p2.w),
-                          az = __float_as_int(p3.x);
-                const float dx = (float)(x - ax) - p0.x;
-                const float dy = (float)(y - ay) - p0.y;
-                const bool in = x >= lx && x <= hx && y >= ly && y <= hy;
-                // quadratic form in dz: a22 dz^2 + Lz dz + C  (already scaled)
-                float C = fmaf(p1.x * dx, dx, fmaf(p1.y * dy, dy, p1.w * dx * dy));
-                C = in ? C : -INFINITY;
-                const float Lz = fmaf(p2.x, dx, p2.y * dy);
-                const float dz0 = (float)(z0 - az) - p0.z;
-                const float2 a22v = make_float2(p1.z, p1.z), Lzv = make_float2(Lz, Lz), Cv = make_float2(C, C),
-                             rv = make_float2(p0.w, p0.w);
+            while (vis) {
+                const int j = __ffsll((long long)vis) - 1;
+                vis &= vis - 1;
+                const bool in = (vc.lanes[w][j] >> lane) & 1u;
+                const float4 r0 = vc.r0[j], r1 = vc.r1[j], r2 = vc.r2[j];
+                const int zi = vc.zinfo[j], rows = vc.rows[j];
+                const float dx = (lxf - r0.x) - r0.z;
+                const float dy = (lyf - r0.y) - r0.w;
+                // the column's peak value (<= 0, already scaled) and the offset
+                // of the tile's first layer from the peak
+                float qm = fmaf(r1.x * dx, dx, fmaf(r1.y * dy, dy, r1.z * dx * dy));
+                qm = in ? qm : -INFINITY;
+                const float t0 = r2.w - fmaf(r2.x, dx, r2.y * dy);
+                const float2 a22v = make_float2(r2.z, r2.z), t0v = make_float2(t0, t0),
+                             qmv = make_float2(qm, qm), rv = make_float2(r1.w, r1.w);
 #pragma unroll
-                for (int g8 = 0; g8 < TZ / TZG; ++g8) {
-                    if (zhi < g8 * TZG || zlo >= (g8 + 1) * TZG) continue;  // warp-uniform
-                    if (zlo <= g8 * TZG && zhi >= (g8 + 1) * TZG - 1) {       // whole group in the box
+                for (int g8 = 0; g8 < NG; ++g8) {
+                    if (!(zi & (1 << g8))) continue;  // warp-uniform
+                    if (zi & (16 << g8)) {            // whole group in the box
 #pragma unroll
                         for (int kk = 0; kk < TZG; kk += 2) {
                             const int k = g8 * TZG + kk;
-                            const float2 dz = make_float2(dz0 + (float)k, dz0 + (float)(k + 1));
-                            const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
+                            const float2 t = __fadd2_rn(t0v, make_float2((float)k, (float)(k + 1)));
+                            const float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
                             cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
                         }
                     } else {
-                        const float *zm = c_zmask.v[max(zlo - g8 * TZG, 0)][min(zhi - g8 * TZG, TZG - 1)];
+                        const int row = (rows >> (8 * g8)) & 0xff;
+                        const float4 zm0 = c_zmask.v[row][0], zm1 = c_zmask.v[row][1];
+                        const float zmv[TZG] = {zm0.x, zm0.y, zm0.z, zm0.w, zm1.x, zm1.y, zm1.z, zm1.w};
 #pragma unroll
                         for (int kk = 0; kk < TZG; kk += 2) {
                             const int k = g8 * TZG + kk;
-                            const float2 dz = make_float2(dz0 + (float)k, dz0 + (float)(k + 1));
-                            float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
-                            q = __fadd2_rn(q, make_float2(zm[kk], zm[kk + 1]));
+                            const float2 t = __fadd2_rn(t0v, make_float2((float)k, (float)(k + 1)));
+                            float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
+                            q = __fadd2_rn(q, make_float2(zmv[kk], zmv[kk + 1]));
                             cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
                         }
                     }
@@ -472,7 +566,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
 }
 
 // FVR for separable Gaussians (the paper's isotropic representation, or
-// axis-aligned ones): with A diagonal, rho exp2(a00 dx^2 + a11 dy^2 + a22 dz^2)
+// axis-aligned ones): with A diagonal (m00 = a00, m11 = a11, no column shift),
+// rho exp2(a00 dx^2 + a11 dy^2 + a22 dz^2)
 // = EXY(x, y) EZ(z).  Same tiles, work lists, warps and skips as k_voxelize
 // (a warp owns an 8 x 4 (x, y) patch, each lane a z column of the tile), but
 // per chunk of Gaussians the z factors EZ (zero outside each box) are built
@@ -661,7 +756,7 @@ static cudaError_t launch_vox_tz(const Batch &B, const Prep *prep, const uint32_
 }
 
 cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int deterministic,
-                            cudaStream_t st) {
+                            cudaStream_t st, const cudaEvent_t *kev) {
     uint32_t *tile_off = ws_ptr<uint32_t>(ws, ws->tile_off);
     uint32_t *tile_fill = ws_ptr<uint32_t>(ws, ws->tile_fill);
     uint32_t *list = ws_ptr<uint32_t>(ws, ws->list);
@@ -683,11 +778,14 @@ cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int de
     }
     // persistent: enough CTAs to fill every SM, each pulling tiles from the queue
     const int *sep_flag = ws_ptr<int>(ws, ws->status) + SEP_FLAG;
+    if (kev && (err = cudaEventRecord(kev[0], st)) != cudaSuccess) return err;
     switch (B.tz) {
-        case 8: return launch_vox_tz<8>(B, prep, tile_off, list, cap, queue, sep_flag, st);
-        case 16: return launch_vox_tz<16>(B, prep, tile_off, list, cap, queue, sep_flag, st);
-        default: return launch_vox_tz<32>(B, prep, tile_off, list, cap, queue, sep_flag, st);
+        case 8: err = launch_vox_tz<8>(B, prep, tile_off, list, cap, queue, sep_flag, st); break;
+        case 16: err = launch_vox_tz<16>(B, prep, tile_off, list, cap, queue, sep_flag, st); break;
+        default: err = launch_vox_tz<32>(B, prep, tile_off, list, cap, queue, sep_flag, st);
     }
+    if (err == cudaSuccess && kev) err = cudaEventRecord(kev[1], st);
+    return err;
 }
 
 }  // namespace dgr

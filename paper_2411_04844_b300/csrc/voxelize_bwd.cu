@@ -93,13 +93,16 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
                 const int yy = yb + row, xx = lx + (j - row * ex);
                 const float dx = (float)(xx - P.ax) - P.dx;
                 const float dy = (float)(yy - P.ay) - P.dy;
-                const float C = fmaf(P.a00 * dx, dx, fmaf(P.a11 * dy, dy, P.a01 * dx * dy));
-                const float Lz = fmaf(P.a02, dx, P.a12 * dy);
+                // column form: q = qm + a22 t^2, t = dz - dz* (the column's peak)
+                const float qm = fmaf(P.m00 * dx, dx, fmaf(P.m11 * dy, dy, P.m01 * dx * dy));
+                const float dzs = fmaf(P.zx, dx, P.zy * dy);
+                const float t0 = dz0 - dzs;
                 const float *col = gv + ((size_t)zb * g.ny + yy) * g.nx + xx;
                 const size_t zs = (size_t)g.nx * g.ny;
-                // the column's sums over z of ge, ge dz, ge dz^2 (ge = G_V e), in two
+                // the column's sums over z of ge, ge t, ge t^2 (ge = G_V e), in two
                 // packed FP32 lanes (even and odd layers of each group of four)
-                const float2 a22v = make_float2(P.a22, P.a22), Lzv = make_float2(Lz, Lz), Cv = make_float2(C, C);
+                const float2 a22v = make_float2(P.a22, P.a22), qmv = make_float2(qm, qm),
+                             t0v = make_float2(t0, t0);
                 float2 s0v = make_float2(0.f, 0.f), s1v = s0v, s2v = s0v;
                 int z = zb;
                 // U layers at a time (8, then 4): loads first, then the arithmetic
@@ -111,30 +114,33 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
                     col += U * zs;
 #pragma unroll
                     for (int u = 0; u < U; u += 2) {
-                        const float2 dz = make_float2(dz0 + (float)(z + u - zb), dz0 + (float)(z + u + 1 - zb));
-                        const float2 q = __ffma2_rn(dz, __ffma2_rn(a22v, dz, Lzv), Cv);
+                        const float2 t = __fadd2_rn(t0v, make_float2((float)(z + u - zb), (float)(z + u + 1 - zb)));
+                        const float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
                         const float2 ge = __fmul2_rn(make_float2(gz[u], gz[u + 1]),
                                                      make_float2(ex2_approx(q.x), ex2_approx(q.y)));
                         s0v = __fadd2_rn(s0v, ge);
-                        const float2 t = __fmul2_rn(ge, dz);
-                        s1v = __fadd2_rn(s1v, t);
-                        s2v = __ffma2_rn(t, dz, s2v);
+                        const float2 gt = __fmul2_rn(ge, t);
+                        s1v = __fadd2_rn(s1v, gt);
+                        s2v = __ffma2_rn(gt, t, s2v);
                     }
                     z += U;
                 };
                 while (z + 7 <= ze) layers(std::integral_constant<int, 8>());
                 if (z + 3 <= ze) layers(std::integral_constant<int, 4>());
                 for (; z <= ze; ++z) {
-                    const float dz = dz0 + (float)(z - zb);
-                    const float e = ex2_approx(fmaf(dz, fmaf(P.a22, dz, Lz), C));
+                    const float t = t0 + (float)(z - zb);
+                    const float e = ex2_approx(fmaf(P.a22 * t, t, qm));
                     const float ge = __ldg(col) * e;
                     col += zs;
                     s0v.x += ge;
-                    const float t = ge * dz;
-                    s1v.x += t;
-                    s2v.x = fmaf(t, dz, s2v.x);
+                    const float gt = ge * t;
+                    s1v.x += gt;
+                    s2v.x = fmaf(gt, t, s2v.x);
                 }
-                const float s0 = s0v.x + s0v.y, s1 = s1v.x + s1v.y, s2 = s2v.x + s2v.y;
+                // back to moments in dz = t + dz*
+                const float s0 = s0v.x + s0v.y, s1t = s1v.x + s1v.y, s2t = s2v.x + s2v.y;
+                const float s1 = fmaf(dzs, s0, s1t);
+                const float s2 = fmaf(dzs, fmaf(dzs, s0, 2.f * s1t), s2t);
                 m[0] += s0;
                 m[1] = fmaf(dx, s0, m[1]);
                 m[2] = fmaf(dy, s0, m[2]);
@@ -356,7 +362,8 @@ __global__ void __launch_bounds__(256) k_bwd_big(const __grid_constant__ Batch B
 
 }  // namespace
 
-cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st) {
+cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *ws, cudaStream_t st,
+                                     const cudaEvent_t *kev) {
     if (B.tot_g == 0) return cudaSuccess;
     uint32_t *itemcnt = ws_ptr<uint32_t>(ws, ws->itemcnt);
     uint32_t *item_off = ws_ptr<uint32_t>(ws, ws->item_off);
@@ -378,7 +385,9 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_items, 256, 0);
+    if (kev && (err = cudaEventRecord(kev[0], st)) != cudaSuccess) return err;
     k_bwd_items<<<sms * max(per_sm, 1), 256, 0, st>>>(B, prep, item_off, cap, part, status + ITEM_QUEUE);
+    if (kev && (err = cudaEventRecord(kev[1], st)) != cudaSuccess) return err;
     k_bwd_final<<<(unsigned)(((long long)B.tot_g * 4 + 127) / 128), 128, 0, st>>>(B, item_off, cap, part, big,
                                                                                     big_count);
     k_bwd_big<<<148 * 2, 256, 0, st>>>(B, item_off, cap, part, big, big_count);
