@@ -37,8 +37,6 @@ UNIT = "iter/s"
 WORKLOAD = 2  # 50,000 Gaussians, 256^3, cone 50 x 256^2
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SMS = 148
-MUFU_PER_CLK_SM = 16
-FFMA_PER_CLK_SM = 128
 
 
 def parse():
@@ -194,6 +192,10 @@ def run_ours(args, dist, rank, local):
     dev = f"cuda:{local}"
     P = setup_problem(rank, dev, args.objective)
     wl, ws, prob, st, meas = P["wl"], P["ws"], P["prob"], P["st"], P["meas"]
+    # the exp2 and FMA pipes' rates per SM clock on this GPU (the voxelizer's
+    # and its adjoint's roofline peaks), measured before the timed region
+    from paper_2411_04844_b300 import peaks as pipe_peaks
+    rates = pipe_peaks.pipe_rates()
     stream = torch.cuda.current_stream()
     loss = torch.zeros(1, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
@@ -231,7 +233,9 @@ def run_ours(args, dist, rank, local):
                 for i, name in enumerate(dgr.STEP_PHASES)}
     # the main kernels of the two projector phases, timed on their own stream
     kernel_ms = {"backproject": [ev[k][7].elapsed_time(ev[k][8]) for k in range(K)],
-                 "project": [ev[k][9].elapsed_time(ev[k][10]) for k in range(K)]}
+                 "project": [ev[k][9].elapsed_time(ev[k][10]) for k in range(K)],
+                 "voxelize": [ev[k][11].elapsed_time(ev[k][12]) for k in range(K)],
+                 "voxelize_backward": [ev[k][13].elapsed_time(ev[k][14]) for k in range(K)]}
 
     # end to end through the C ABI: every step's measured projections copied
     # pinned host -> device on a copy stream (into one of two device buffers,
@@ -286,28 +290,34 @@ def run_ours(args, dist, rank, local):
     phases = {k: statistics.mean(v) for k, v in phase_ms.items()}
     kernels = {k: statistics.mean(v) for k, v in kernel_ms.items()}
     return dict(P=P, value=value, e2e=e2e_value, step_ms=statistics.mean(step_ms), phases=phases,
-                kernels=kernels,
+                kernels=kernels, rates=rates,
                 launches=launches, clocks=clk, t_wall=t_wall, loss=float(loss_host[-1].item()))
 
 
 KERNEL_NAMES = {"project": "k_path<0> (projector walk)",
                 "backproject": "k_path<1> (backprojector walk + fixed-point scatter)",
-                "voxelize": "voxelize phase (binning + k_voxelize)",
-                "voxelize_backward": "FVR adjoint phase (k_bwd_items + k_bwd_final + k_bwd_big)"}
+                "voxelize": "k_voxelize (tile evaluation)",
+                "voxelize_backward": "k_bwd_items (per-item moments of the FVR adjoint)"}
 
 
-def roofline(P, phases, clk, pk, kernels=None):
-    """Roofline of the dominant kernel of one iteration.  The two projector
-    phases are represented by their main kernel, timed by its own pair of
-    events; the other phases by the phase time."""
+def roofline(P, phases, clk, pk, kernels=None, rates=None):
+    """Roofline of the dominant kernel of one iteration.  Each of the four
+    heavy phases is represented by its main kernel, timed by its own pair of
+    events (the phase time is kept beside it); the others by the phase time.
+    The exp2 and FMA peaks are the rates measured on this GPU (per SM clock)
+    x SMs x the SM clock sampled during the timed region."""
     kernels = kernels or {}
+    rates = rates or {}
     wl = P["wl"]
     nvox = wl.grid.dims[0] * wl.grid.dims[1] * wl.grid.dims[2]
     nrays = wl.geom.n_views * wl.geom.nu * wl.geom.nv
     proj_bytes = 4.0 * nvox * wl.geom.n_views + 4.0 * nrays
     mhz = clk.get("sm_mhz") or pk["sm_max_mhz"]
-    sfu_peak = SMS * MUFU_PER_CLK_SM * mhz * 1e6 / 1e9  # G ex2 / s
-    ffma_peak = SMS * FFMA_PER_CLK_SM * mhz * 1e6 / 1e9  # G FFMA / s
+    sms = rates.get("sms", SMS)
+    ex2_clk = rates.get("ex2")
+    fma_clk = max(rates.get("ffma", 0.0), rates.get("ffma2", 0.0)) or None
+    sfu_peak = sms * ex2_clk * mhz * 1e6 / 1e9 if ex2_clk else None  # G ex2 / s
+    ffma_peak = sms * fma_clk * mhz * 1e6 / 1e9 if fma_clk else None  # G FFMA / s
     per = {}
     for name, ph_ms in phases.items():
         ms = kernels.get(name, ph_ms)
@@ -316,14 +326,16 @@ def roofline(P, phases, clk, pk, kernels=None):
             a = proj_bytes / s / 1e9
             per[name] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": a / pk["hbm_gbs"], "ms": ms}
-        elif name == "voxelize":
+        elif name == "voxelize" and sfu_peak:
             a = P["inbox"] / s / 1e9
             per[name] = {"bound": "alu", "achieved": a, "peak": sfu_peak, "unit": "Gex2/s",
-                         "frac": a / sfu_peak, "ms": ms}
-        elif name == "voxelize_backward":
+                         "frac": a / sfu_peak, "ms": ms,
+                         "frac_phase": P["inbox"] / (ph_ms / 1000.0) / 1e9 / sfu_peak}
+        elif name == "voxelize_backward" and ffma_peak:
             a = 12.0 * P["inbox"] / s / 1e9
             per[name] = {"bound": "alu", "achieved": a, "peak": ffma_peak, "unit": "GFFMA/s",
-                         "frac": a / ffma_peak, "ms": ms}
+                         "frac": a / ffma_peak, "ms": ms,
+                         "frac_phase": 12.0 * P["inbox"] / (ph_ms / 1000.0) / 1e9 / ffma_peak}
         else:
             per[name] = {"ms": ms}
         per[name]["phase_ms"] = ph_ms
@@ -333,7 +345,8 @@ def roofline(P, phases, clk, pk, kernels=None):
     r.pop("phase_ms")
     r["kernel"] = KERNEL_NAMES.get(dom, dom)
     r["phase"] = dom
-    r["peak_src"] = pk["src"] if r.get("unit") == "GB/s" else f"{SMS} SMs x unit rate x {mhz:.0f} MHz"
+    r["peak_src"] = (pk["src"] if r.get("unit") == "GB/s" else
+                     f"measured pipe rate per clock x {sms} SMs x {mhz:.0f} MHz")
     r["traffic"] = traffic_for(dom)
     return r, per
 
@@ -463,7 +476,7 @@ def main():
     if rank != 0:
         return
     pk = peaks()
-    roof, per = roofline(R["P"], R["phases"], R["clocks"], pk, R["kernels"])
+    roof, per = roofline(R["P"], R["phases"], R["clocks"], pk, R["kernels"], R["rates"])
     P = R["P"]
     wl = P["wl"]
     fvr_ms = R["phases"]["voxelize"]
@@ -473,6 +486,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config_block(),
         "fvr_gvoxel_evals_per_s": P["inbox"] / (fvr_ms / 1000.0) / 1e9,
+        "fvr_kernel_gvoxel_evals_per_s": P["inbox"] / (R["kernels"]["voxelize"] / 1000.0) / 1e9,
+        "pipe_rates_per_clk_sm": {k: (round(v, 3) if isinstance(v, float) else v)
+                                  for k, v in R["rates"].items()},
         "phases_ms": {k: round(v, 4) for k, v in R["phases"].items()},
         "phase_roofline": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                                for kk, vv in v.items()} for k, v in per.items()},

@@ -296,13 +296,15 @@ int dgr_step_batched(int n_inst, const dgr_problem *probs, const dgr_params *par
 /* dgr_step with CUDA events recorded on `stream` at its phase boundaries:
  * events[0] before voxelize, [1] after voxelize, [2] after project, [3] after
  * the L1 residual, [4] after backproject, [5] after the voxelize adjoint,
- * [6] after Adam.  With n_events >= DGR_STEP_KERNEL_EVENTS (11), also
+ * [6] after Adam.  With n_events >= DGR_STEP_KERNEL_EVENTS (15), also
  * [7] / [8] right before / after the backprojector's main kernel (the path
- * scatter, without the residual scaling and the fold) and [9] / [10] around
- * the projector's main kernel.  events: host array of n_events (>= 7)
- * cudaEvent_t. */
+ * scatter, without the residual scaling and the fold), [9] / [10] around
+ * the projector's main kernel, [11] / [12] around the voxelizer's main kernel
+ * (the tile evaluation, without prep and binning) and [13] / [14] around the
+ * voxelize adjoint's main kernel (the per-item moments).  events: host array
+ * of n_events (>= 7) cudaEvent_t. */
 #define DGR_STEP_EVENTS 7
-#define DGR_STEP_KERNEL_EVENTS 11
+#define DGR_STEP_KERNEL_EVENTS 15
 int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *measured,
                    float *loss_out, dgr_ws *ws, cudaStream_t stream, cudaEvent_t *events,
                    int n_events);
@@ -382,9 +384,26 @@ int dgr_net_status(int n, const void *ws, size_t ws_bytes, int *status);
 int dgr_adam_flat(long long n, float *params, const float *grads, float *m, float *v, int t,
                   float lr, float beta1, float beta2, float eps, cudaStream_t stream);
 /* FDK-style filtering of projections for the network input: each detector
- * row is cosine-weighted (cone: dsd / sqrt(dsd^2 + u^2 + v^2)) and convolved
- * with the Ram-Lak ramp kernel; out has the sinogram layout. */
-int dgr_fdk_filter(const dgr_geom *geom, const float *sino, float *out, cudaStream_t stream);
+ * row is cosine-weighted (cone: dsd / sqrt(dsd^2 + u^2 + v^2)), convolved
+ * with the Ram-Lak ramp kernel and multiplied by scale (the FBP constant,
+ * pi / n_views x pu pv / (M h^3) with M = dsd / dso, so that dgr_backproject
+ * of the result is the FDK volume); out has the sinogram layout. */
+int dgr_fdk_filter(const dgr_geom *geom, float scale, const float *sino, float *out,
+                   cudaStream_t stream);
+/* Seeding proposals from a source volume of n_vox voxels with `channels`
+ * values each: density = max(src[channels * i], 0); log_scale = src[2 i + 1]
+ * (channels 2: the network's output) or log_scale_default (channels 1: an FDK
+ * volume, the plain fallback). */
+int dgr_proposals(long long n_vox, const float *src, int channels, float log_scale_default,
+                  float *density, float *log_scale, cudaStream_t stream);
+/* Training targets from a fit of the plain method: w[i] = rho[i] x mean over
+ * axes of log(s / h) (voxelize it for the weighted log-scale sum), then
+ * out[i] = (density[i], clamp(wsum[i] / density[i], log_lo, log_hi)) where
+ * density > min_density, (density[i], log_default) elsewhere; out [n_vox][2]. */
+int dgr_logscale_weight(int n, const float *s, const float *rho, float h, float *w,
+                        cudaStream_t stream);
+int dgr_fit_targets(long long n_vox, const float *density, const float *wsum, float min_density,
+                    float log_lo, float log_hi, float log_default, float *out, cudaStream_t stream);
 /* Seeding from proposals on a cubic grid: ns voxels drawn with probability
  * proportional to max(density, 0) (u: uniform [0,1) per seed, given), mu = the
  * voxel centre + jitter * h (jitter in [-1/2, 1/2)^3, given), isotropic s =
@@ -402,6 +421,32 @@ int dgr_seed_rescale(int ns, const int *voxel, const float *density, const float
 /* Total number of kernels this library has launched in this process (a host
  * counter; lets callers count launches inside a timed region). */
 long long dgr_launch_count(void);
+
+/* Measurement utility (the paper has no counterpart): the rate of one
+ * arithmetic pipe per SM clock on the running GPU, the peak the voxelizer
+ * (exp2 per in-box pair, Eq. 4) and its adjoint (FP32 FMA) are judged by.
+ * kind: DGR_PIPE_EX2 (ex2.approx.ftz.f32), DGR_PIPE_FFMA (FP32 fma) or
+ * DGR_PIPE_FFMA2 (packed f32x2 fma; counted as two FMAs).  Launches n_blocks
+ * CTAs of 256 threads, each thread iters x 32 operations in 8 independent
+ * chains.  rec: device [4 n_blocks] uint64, per CTA: SM id, clock64 at start,
+ * clock64 at end, operations; sink: device [256 n_blocks] floats (keeps the
+ * results live).  Per SM, rate = its CTAs' operations / (latest end -
+ * earliest start).  DGR_ERR_ARG for a bad kind or size (1 <= iters <= 2^20,
+ * 1 <= n_blocks <= 2^16) or a null pointer; asynchronous on stream. */
+#define DGR_PIPE_EX2 0
+#define DGR_PIPE_FFMA 1
+#define DGR_PIPE_FFMA2 2
+int dgr_pipe_rate(int kind, int iters, int n_blocks, unsigned long long *rec, float *sink,
+                  cudaStream_t stream);
+/* Measurement utility (no paper counterpart): L2 bandwidth over a device
+ * buffer of `bytes` (a multiple of 16, of 512 for kind 1; 16-byte aligned) small enough to stay
+ * in L2, `passes` passes by n_blocks CTAs of 256 threads.  kind 0: streaming
+ * 16-byte reads (sink: device [256 n_blocks] floats keeps them live); kind 1:
+ * 32-bit integer reductions (+1 to every word, the backprojector's scatter
+ * operation; buf is modified).  The caller times it (bytes x passes / time).
+ * DGR_ERR_ARG for a bad kind, size or pointer; asynchronous on stream. */
+int dgr_l2_rate(int kind, long long bytes, int passes, int n_blocks, void *buf, float *sink,
+                cudaStream_t stream);
 
 #ifdef __cplusplus
 }

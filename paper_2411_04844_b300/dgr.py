@@ -38,14 +38,16 @@ EXPORTS = [
     "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
     "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
     "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss", "dgr_densify", "dgr_set_separable", "dgr_set_staged_walk",
-    "dgr_set_conv_engine", "dgr_net_status",
+    "dgr_set_conv_engine", "dgr_net_status", "dgr_pipe_rate", "dgr_l2_rate", "dgr_proposals",
+    "dgr_logscale_weight", "dgr_fit_targets",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
 NOALLOC_SCRATCH_BYTES = 4 << 20
 DGR_STEP_EVENTS = 7
-# with 11 events, [7]/[8] bracket the backprojector's path scatter kernel and
-# [9]/[10] the projector's main kernel
-DGR_STEP_KERNEL_EVENTS = 11
+# with 15 events, [7]/[8] bracket the backprojector's path scatter kernel,
+# [9]/[10] the projector's main kernel, [11]/[12] the voxelizer's tile kernel
+# and [13]/[14] the voxelize adjoint's item kernel
+DGR_STEP_KERNEL_EVENTS = 15
 STEP_PHASES = ("voxelize", "project", "l1", "backproject", "voxelize_backward", "adam")
 
 
@@ -164,6 +166,8 @@ def lib():
             "dgr_step_timed": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P,
                                ctypes.POINTER(P), i],
             "dgr_project_noalloc": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P],
+            "dgr_pipe_rate": [i, i, i, P, P, P],
+            "dgr_l2_rate": [i, ll, i, i, P, P, P],
             "dgr_step_batched": [i, ctypes.POINTER(Problem), ctypes.POINTER(Params),
                                  ctypes.POINTER(P), P, P, P],
             "dgr_net_ws_bytes": [i, ctypes.POINTER(ctypes.c_size_t)],
@@ -171,7 +175,10 @@ def lib():
             "dgr_net_backward": [i, P, P, P, P, P, ctypes.c_size_t, P],
             "dgr_net_loss": [i, P, P, f, f, P, P, P, ctypes.c_size_t, P],
             "dgr_adam_flat": [ll, P, P, P, P, i, f, f, f, f, P],
-            "dgr_fdk_filter": [ctypes.POINTER(Geom), P, P, P],
+            "dgr_fdk_filter": [ctypes.POINTER(Geom), f, P, P, P],
+            "dgr_proposals": [ll, P, i, f, P, P, P],
+            "dgr_logscale_weight": [i, P, P, f, P, P],
+            "dgr_fit_targets": [ll, P, P, f, f, f, f, P, P],
             "dgr_seed_bytes": [i, ctypes.POINTER(ctypes.c_size_t)],
             "dgr_seed": [ctypes.POINTER(Grid), P, P, i, P, P, P, P, P, P, P, P,
                          ctypes.c_size_t, P],
@@ -490,6 +497,30 @@ def dgr_launch_count() -> int:
     return int(lib().dgr_launch_count())
 
 
+DGR_PIPE_EX2, DGR_PIPE_FFMA, DGR_PIPE_FFMA2 = 0, 1, 2
+
+
+def dgr_l2_rate(kind: int, buf, passes: int, n_blocks: int, sink, stream=None):
+    """Launch the L2 bandwidth kernel over the whole of buf (see include/dgr.h)."""
+    _check(sink, "sink")
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise DgrError("dgr_l2_rate: buf must be a contiguous device tensor")
+    _rc(lib().dgr_l2_rate(int(kind), buf.numel() * buf.element_size(), int(passes), int(n_blocks),
+                          ctypes.c_void_p(buf.data_ptr()), _ptr(sink), _stream(stream)),
+        "dgr_l2_rate")
+
+
+def dgr_pipe_rate(kind: int, iters: int, n_blocks: int, rec, sink, stream=None):
+    """Launch the pipe-rate kernel (see include/dgr.h); rec: int64 device
+    tensor [4 n_blocks], sink: float32 device tensor [256 n_blocks]."""
+    _check(rec, "rec", torch.int64)
+    _check(sink, "sink")
+    if rec.numel() < 4 * n_blocks or sink.numel() < 256 * n_blocks:
+        raise DgrError("dgr_pipe_rate: rec needs 4 n_blocks entries, sink 256 n_blocks")
+    _rc(lib().dgr_pipe_rate(kind, iters, n_blocks, ctypes.c_void_p(rec.data_ptr()), _ptr(sink),
+                            _stream(stream)), "dgr_pipe_rate")
+
+
 def dgr_step_batched(probs, states, measured, loss_out, ws: Workspace, stream=None):
     """One optimisation step of every instance: probs [Problem], states
     [State], measured [device tensors], loss_out device tensor [n_inst]."""
@@ -581,10 +612,34 @@ def dgr_adam_flat(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, 
         "dgr_adam_flat")
 
 
-def dgr_fdk_filter(geom: Geom, sino, out, stream=None):
+def dgr_fdk_filter(geom: Geom, sino, out, scale=1.0, stream=None):
     _check(sino, "sino"); _check(out, "out")
-    _rc(lib().dgr_fdk_filter(ctypes.byref(geom), _ptr(sino), _ptr(out), _stream(stream)),
-        "dgr_fdk_filter")
+    _rc(lib().dgr_fdk_filter(ctypes.byref(geom), float(scale), _ptr(sino), _ptr(out),
+                             _stream(stream)), "dgr_fdk_filter")
+
+
+def dgr_proposals(src, channels: int, log_scale_default: float, density, log_scale, stream=None):
+    """density = max(src[..., 0], 0); log_scale = src[..., 1] (channels 2) or
+    the default (channels 1)."""
+    for t, nm in ((src, "src"), (density, "density"), (log_scale, "log_scale")):
+        _check(t, nm)
+    _rc(lib().dgr_proposals(density.numel(), _ptr(src), int(channels), float(log_scale_default),
+                            _ptr(density), _ptr(log_scale), _stream(stream)), "dgr_proposals")
+
+
+def dgr_logscale_weight(s, rho, h: float, w, stream=None):
+    for t, nm in ((s, "s"), (rho, "rho"), (w, "w")):
+        _check(t, nm)
+    _rc(lib().dgr_logscale_weight(rho.numel(), _ptr(s), _ptr(rho), float(h), _ptr(w),
+                                  _stream(stream)), "dgr_logscale_weight")
+
+
+def dgr_fit_targets(density, wsum, min_density, log_lo, log_hi, log_default, out, stream=None):
+    for t, nm in ((density, "density"), (wsum, "wsum"), (out, "out")):
+        _check(t, nm)
+    _rc(lib().dgr_fit_targets(density.numel(), _ptr(density), _ptr(wsum), float(min_density),
+                              float(log_lo), float(log_hi), float(log_default), _ptr(out),
+                              _stream(stream)), "dgr_fit_targets")
 
 
 def dgr_seed(grid: Grid, density, log_scale, u, jitter, mu, s, q, rho, voxel, scratch, stream=None):
