@@ -1112,7 +1112,7 @@ __global__ void k_adam_flat(long long n, float *__restrict__ p, const float *__r
 // cosine weight and ramp filter along detector rows (Ram-Lak kernel in the
 // spatial domain: h(0) = 1/(4 p^2), h(odd k) = -1/(pi k p)^2, h(even) = 0,
 // times the pitch): one thread per output pixel, direct convolution.
-__global__ void k_fdk_filter(dgr_geom geo, const float *__restrict__ in, float *__restrict__ out) {
+__global__ void k_fdk_filter(dgr_geom geo, float scale, const float *__restrict__ in, float *__restrict__ out) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long tot = (long long)geo.n_views * geo.nv * geo.nu;
     if (r >= tot) return;
@@ -1137,7 +1137,42 @@ __global__ void k_fdk_filter(dgr_geom geo, const float *__restrict__ in, float *
         }
         acc = fmaf(hk * pu, wgt * src[j], acc);
     }
-    out[r] = acc;
+    out[r] = scale * acc;
+}
+
+// proposals for seeding: density = max(src[c * i], 0); log-scale = the second
+// channel (c = 2, the network's output) or a constant (c = 1, an FDK volume)
+__global__ void k_proposals(long long n, const float *__restrict__ src, int c, float log_default,
+                            float *__restrict__ density, float *__restrict__ log_scale) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    density[i] = fmaxf(src[c * i], 0.f);
+    log_scale[i] = c == 2 ? src[2 * i + 1] : log_default;
+}
+
+// per-Gaussian weight rho * mean_a log(s_a / h) (the intensity-weighted
+// log-scale, voxelized to build training targets)
+__global__ void k_logscale_weight(int n, const float *__restrict__ s, const float *__restrict__ rho,
+                                  float inv_h, float *__restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float l = (logf(s[3 * i] * inv_h) + logf(s[3 * i + 1] * inv_h) + logf(s[3 * i + 2] * inv_h)) *
+                    (1.f / 3.f);
+    w[i] = rho[i] * l;
+}
+
+// training targets [n][2]: the fitted density and, where it exceeds
+// min_density, the density-weighted mean log-scale clamped to [lo, hi]
+// (log_default elsewhere)
+__global__ void k_fit_targets(long long n, const float *__restrict__ dens, const float *__restrict__ wsum,
+                              float min_density, float lo, float hi, float log_default,
+                              float *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float d = dens[i];
+    const float l = d > min_density ? wsum[i] / fmaxf(d, min_density) : log_default;
+    out[2 * i] = d;
+    out[2 * i + 1] = fminf(fmaxf(l, lo), hi);
 }
 
 // per-block sums of a non-negative field (FP64) for the sampling CDF
@@ -1652,11 +1687,43 @@ int dgr_adam_flat(long long n, float *params, const float *grads, float *m, floa
     return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
 }
 
-int dgr_fdk_filter(const dgr_geom *geom, const float *sino, float *out, cudaStream_t st) {
-    if (!geom || !sino || !out || geom->n_views <= 0 || geom->nu <= 0 || geom->nv <= 0) return DGR_ERR_ARG;
+int dgr_fdk_filter(const dgr_geom *geom, float scale, const float *sino, float *out, cudaStream_t st) {
+    if (!geom || !sino || !out || geom->n_views <= 0 || geom->nu <= 0 || geom->nv <= 0 || !isfinite(scale))
+        return DGR_ERR_ARG;
     if (geom->beam != DGR_PARALLEL && geom->beam != DGR_CONE) return DGR_ERR_ARG;
     const long long tot = (long long)geom->n_views * geom->nv * geom->nu;
-    k_fdk_filter<<<nblk(tot, 128), 128, 0, st>>>(*geom, sino, out);
+    k_fdk_filter<<<nblk(tot, 128), 128, 0, st>>>(*geom, scale, sino, out);
+    counted(1);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_proposals(long long n_vox, const float *src, int channels, float log_scale_default,
+                  float *density, float *log_scale, cudaStream_t st) {
+    if (n_vox < 0 || (channels != 1 && channels != 2) || !isfinite(log_scale_default) ||
+        (n_vox > 0 && (!src || !density || !log_scale)))
+        return DGR_ERR_ARG;
+    if (n_vox == 0) return DGR_OK;
+    k_proposals<<<nblk(n_vox, 256), 256, 0, st>>>(n_vox, src, channels, log_scale_default, density, log_scale);
+    counted(1);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_logscale_weight(int n, const float *s, const float *rho, float h, float *w, cudaStream_t st) {
+    if (n < 0 || !(h > 0.f) || (n > 0 && (!s || !rho || !w))) return DGR_ERR_ARG;
+    if (n == 0) return DGR_OK;
+    k_logscale_weight<<<nblk(n, 256), 256, 0, st>>>(n, s, rho, 1.f / h, w);
+    counted(1);
+    return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
+}
+
+int dgr_fit_targets(long long n_vox, const float *density, const float *wsum, float min_density,
+                    float log_lo, float log_hi, float log_default, float *out, cudaStream_t st) {
+    if (n_vox < 0 || !(min_density > 0.f) || !(log_lo <= log_hi) || !isfinite(log_default) ||
+        (n_vox > 0 && (!density || !wsum || !out)))
+        return DGR_ERR_ARG;
+    if (n_vox == 0) return DGR_OK;
+    k_fit_targets<<<nblk(n_vox, 256), 256, 0, st>>>(n_vox, density, wsum, min_density, log_lo, log_hi,
+                                                    log_default, out);
     counted(1);
     return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
 }

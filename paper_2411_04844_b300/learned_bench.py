@@ -1,23 +1,34 @@
-"""Learned warm start vs the plain FBP-seeded initialisation (one B300).
+"""Learned warm start (and batching) vs the plain FBP-seeded initialisation
+(one B300).
 
     python -m paper_2411_04844_b300.learned_bench [--side 128] [--views 50]
-        [--train 256] [--test 16] [--ns 100000] [--fit-iters 300] [--epochs 4]
+        [--train 256] [--test 16] [--ns 100000] [--train-iters 300]
+        [--fit-iters 2000] [--epochs 4] [--record 10]
 
 1. training phantoms (seeded, 40 ellipsoids), their projections (+ noise) and
    FDK-style inputs;
 2. the plain method fits every training problem from the FBP-seeded
    initialisation (batched, CUDA graph) -> targets (fitted density, mean
-   log-scale per voxel);
+   log-scale per voxel).  These fits only make targets: they run the short
+   schedule --train-lr0 -> --train-lr1 over --train-iters iterations;
 3. the network is trained on (FDK input -> targets) with the project's own
    kernels (forward, backward, loss, Adam);
-4. held-out problems are fitted twice -- plain initialisation and learned
-   initialisation -- and compared on the iterations and the wall time each
-   needs to reach the plain fit's final PSNR (within 0.1 dB).
+4. held-out problems, fitted with the method's schedule (Adam, lr --lr0 ->
+   --lr1 = 3e-4 -> 3e-5 over --fit-iters, Sec. 5.1):
+   * plain: each problem alone, FBP-seeded initialisation, its PSNR recorded
+     every --record iterations; its target is its final PSNR - 0.1 dB;
+   * learned: the same problems, initialised by the network, the same way;
+   * learned + batched: all held-out problems in one dgr_step_batched graph
+     from the learned initialisation, run until every instance has reached
+     its target.
+   Wall times are CUDA-event times of the initialisation and of the steps up
+   to (and including) the block of --record iterations in which the target
+   is reached; PSNR evaluations between blocks are outside the timed
+   intervals.
 Prints one JSON line.
 """
 import argparse
 import json
-import math
 import sys
 import time
 
@@ -37,42 +48,85 @@ def problems(gs, geo, ids, dev):
     return out
 
 
-def batched_fits(probs, inits, iters, lr0, lr1, batch, record=None):
-    """Fits in batches; returns the states (and PSNR curves every `record` iterations)."""
-    states, curves = [], []
+def batched_fits(probs, inits, iters, lr0, lr1, batch):
+    """Fits in batches of `batch` instances; returns the final states."""
+    states = []
     for b0 in range(0, len(probs), batch):
         F = W.Fit(probs[b0:b0 + batch], inits[b0:b0 + batch], lr0, lr1, iters)
-        curve = [F.psnrs()] if record else None
-        done = 0
-        while done < iters:
-            k = min(record or iters, iters - done)
-            F.step(k)
-            done += k
-            if record:
-                curve.append(F.psnrs())
+        F.step(iters)
         if F.status():
             raise RuntimeError(f"device status {F.status():#x} in a fit")
         states += F.states
-        if record:
-            curves += list(map(list, zip(*curve)))
-    return states, curves
+    return states
 
 
-def main(argv=None):
+class Timer:
+    def __init__(self):
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def __enter__(self):
+        self.e0.record()
+        return self
+
+    def __exit__(self, *exc):
+        self.e1.record()
+        torch.cuda.synchronize()
+        self.ms = self.e0.elapsed_time(self.e1)
+
+
+def timed_fit(probs, init_fn, iters, lr0, lr1, record, targets=None):
+    """Initialise (timed) and fit the problems together (one instance: a
+    single fit), recording PSNR every `record` iterations.  Returns the init
+    time, per-block step times and the PSNR curves (index 0 = initial)."""
+    with Timer() as ti:
+        inits = [init_fn(p) for p in probs]
+    F = W.Fit(probs, inits, lr0, lr1, iters)
+    curves = [[v] for v in F.psnrs()]
+    blocks = []
+    done = 0
+    while done < iters:
+        k = min(record, iters - done)
+        with Timer() as tb:
+            F.step(k)
+        blocks.append(tb.ms)
+        done += k
+        for c, v in zip(curves, F.psnrs()):
+            c.append(v)
+        if targets is not None and all(max(c) >= t for c, t in zip(curves, targets)):
+            break
+    if F.status():
+        raise RuntimeError(f"device status {F.status():#x} in a fit")
+    return ti.ms, blocks, curves
+
+
+def reach(curve, target):
+    """Index of the first record at or above target (None if never)."""
+    return next((i for i, v in enumerate(curve) if v >= target), None)
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--side", type=int, default=128)
     ap.add_argument("--views", type=int, default=50)
     ap.add_argument("--train", type=int, default=256)
     ap.add_argument("--test", type=int, default=16)
     ap.add_argument("--ns", type=int, default=100000)
-    ap.add_argument("--fit-iters", type=int, default=300)
+    ap.add_argument("--train-iters", type=int, default=300)
+    ap.add_argument("--train-lr0", type=float, default=3e-3)
+    ap.add_argument("--train-lr1", type=float, default=3e-4)
+    ap.add_argument("--fit-iters", type=int, default=2000)
+    ap.add_argument("--lr0", type=float, default=3e-4)
+    ap.add_argument("--lr1", type=float, default=3e-5)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--lr0", type=float, default=3e-3)
-    ap.add_argument("--lr1", type=float, default=3e-4)
     ap.add_argument("--net-lr", type=float, default=1e-3)
     ap.add_argument("--record", type=int, default=10)
-    a = ap.parse_args(argv)
+    return ap.parse_args(argv)
+
+
+def study(a) -> dict:
+    """Steps 1-4 of the module doc with the options a; returns the record."""
     dev = "cuda"
     gs, geo = synth.learned_workload(a.side, a.views)
     t0 = time.time()
@@ -81,7 +135,7 @@ def main(argv=None):
     train = problems(gs, geo, range(a.train), dev)
     rng = np.random.default_rng(1)
     inits = [W.plain_init(p, a.ns, rng) for p in train]
-    states, _ = batched_fits(train, inits, a.fit_iters, a.lr0, a.lr1, a.batch)
+    states = batched_fits(train, inits, a.train_iters, a.train_lr0, a.train_lr1, a.batch)
     targets = [W.targets_from_fit(p, st) for p, st in zip(train, states)]
     del states, inits
     torch.cuda.synchronize()
@@ -98,59 +152,62 @@ def main(argv=None):
     log["train_net_s"] = round(time.time() - t1, 1)
     log["train_steps"] = len(losses)
     log["net_loss_first_last"] = [float(losses[0]), float(torch.stack(losses[-len(train):]).mean())]
-    del targets
+    del targets, train
     # 4: held-out comparison
     test = problems(gs, geo, range(100_000, 100_000 + a.test), dev)
-    rng_p, rng_l = np.random.default_rng(3), np.random.default_rng(3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record()
-    plain0 = [W.plain_init(p, a.ns, rng_p) for p in test]
-    ev[1].record()
-    learned0 = [W.learned_init(p, net, a.ns, rng_l) for p in test]
-    ev[2].record()
-    torch.cuda.synchronize()
-    init_ms_plain = ev[0].elapsed_time(ev[1]) / a.test
-    init_ms_learned = ev[1].elapsed_time(ev[2]) / a.test
     t2 = time.time()
-    _, cp = batched_fits(test, plain0, a.fit_iters, a.lr0, a.lr1, a.batch, record=a.record)
-    _, cl = batched_fits(test, learned0, a.fit_iters, a.lr0, a.lr1, a.batch, record=a.record)
-    torch.cuda.synchronize()
+    rng_p = np.random.default_rng(3)
+    plain = [timed_fit([p], lambda q: W.plain_init(q, a.ns, rng_p), a.fit_iters, a.lr0, a.lr1,
+                       a.record) for p in test]
+    tgt = [c[0][-1] - 0.1 for _, _, c in plain]
+    rng_l = np.random.default_rng(3)
+    learned = [timed_fit([p], lambda q: W.learned_init(q, net, a.ns, rng_l), a.fit_iters, a.lr0,
+                         a.lr1, a.record, [t]) for p, t in zip(test, tgt)]
+    rng_b = np.random.default_rng(3)
+    b_init, b_blocks, b_curves = timed_fit(test, lambda q: W.learned_init(q, net, a.ns, rng_b),
+                                           a.fit_iters, a.lr0, a.lr1, a.record, tgt)
     log["fit_test_s"] = round(time.time() - t2, 1)
-    # per-iteration time of a fit of one problem (batched graph over the test set / test count)
-    F = W.Fit(test[:1], [W.plain_init(test[0], a.ns, np.random.default_rng(9))], a.lr0, a.lr1, a.fit_iters)
-    F.step(3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(); F.step(20); e1.record(); torch.cuda.synchronize()
-    ms_iter = e0.elapsed_time(e1) / 20
-    reach, gains = [], []
-    for p_curve, l_curve in zip(cp, cl):
-        target = p_curve[-1] - 0.1
-        it_plain = a.record * next(i for i, v in enumerate(p_curve) if v >= target)
-        hit = [i for i, v in enumerate(l_curve) if v >= target]
-        it_learned = a.record * hit[0] if hit else None
-        reach.append((it_plain, it_learned))
-        gains.append(l_curve[0] - p_curve[0])
-    ok = [r for r in reach if r[1] is not None]
-    iters_plain = float(np.mean([r[0] for r in reach]))
-    iters_learned = float(np.mean([r[1] for r in ok])) if ok else None
-    wall_plain = init_ms_plain + iters_plain * ms_iter
-    wall_learned = (init_ms_learned + iters_learned * ms_iter) if ok else None
+
+    def cost(init_ms, blocks, curve, target):
+        i = reach(curve, target)
+        if i is None:
+            return None, None
+        return i * a.record, init_ms + sum(blocks[:i])
+
+    rp = [cost(im, bl, c[0], t) for (im, bl, c), t in zip(plain, tgt)]
+    rl = [cost(im, bl, c[0], t) for (im, bl, c), t in zip(learned, tgt)]
+    hit_b = [reach(c, t) for c, t in zip(b_curves, tgt)]
+    ok = [r for r in rl if r[0] is not None]
+    batched_ms = (b_init + sum(b_blocks[:max(hit_b)])) if all(h is not None for h in hit_b) else None
     out = {
         "workload": f"{a.side}^3 grid, cone {a.views} views x {a.side}^2, {a.ns} Gaussians, "
                     f"{a.train} training / {a.test} held-out phantoms (40 ellipsoids, N(0,0.01^2))",
-        "fit": {"iters": a.fit_iters, "lr": [a.lr0, a.lr1], "ms_per_iter_single": ms_iter},
-        "plain_final_psnr_mean": float(np.mean([c[-1] for c in cp])),
-        "learned_final_psnr_mean": float(np.mean([c[-1] for c in cl])),
-        "initial_psnr_gain_db_mean": float(np.mean(gains)),
-        "iters_to_plain_final_plain": iters_plain,
-        "iters_to_plain_final_learned": iters_learned,
-        "reached": f"{len(ok)}/{len(reach)}",
-        "wall_ms_to_plain_final_plain": wall_plain,
-        "wall_ms_to_plain_final_learned": wall_learned,
-        "init_ms": {"plain": init_ms_plain, "learned": init_ms_learned},
+        "schedule": {"held_out": {"iters": a.fit_iters, "lr": [a.lr0, a.lr1]},
+                     "training_fits": {"iters": a.train_iters, "lr": [a.train_lr0, a.train_lr1]}},
+        "plain_final_psnr_mean": float(np.mean([c[0][-1] for _, _, c in plain])),
+        "initial_psnr_mean": {"plain": float(np.mean([c[0][0] for _, _, c in plain])),
+                              "learned": float(np.mean([c[0][0] for _, _, c in learned]))},
+        "reached_learned": f"{len(ok)}/{len(rl)}",
+        "reached_learned_batched": f"{sum(h is not None for h in hit_b)}/{len(hit_b)}",
+        "iters_to_target_mean": {"plain": float(np.mean([r[0] for r in rp])),
+                                 "learned": float(np.mean([r[0] for r in ok])) if ok else None},
+        "wall_ms_to_target_per_problem_mean": {
+            "plain": float(np.mean([r[1] for r in rp])),
+            "learned": float(np.mean([r[1] for r in ok])) if ok else None},
+        "wall_ms_all_problems": {
+            "plain_sequential": float(sum(r[1] for r in rp)),
+            "learned_sequential": float(sum(r[1] for r in rl)) if len(ok) == len(rl) else None,
+            "learned_batched": batched_ms},
+        "init_ms_mean": {"plain": float(np.mean([im for im, _, _ in plain])),
+                         "learned": float(np.mean([im for im, _, _ in learned])),
+                         "learned_batched_all": b_init},
         "log": log,
     }
-    print(json.dumps(out))
+    return out
+
+
+def main(argv=None):
+    print(json.dumps(study(parse(argv))))
     return 0
 
 

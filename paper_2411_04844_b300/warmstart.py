@@ -109,18 +109,18 @@ def make_problem(gs, geo, phantom_np, noise_sigma, noise_seed, device="cuda") ->
 
 
 def fdk_volume(P: Problem, ws=None):
-    """Cosine-weighted ramp-filtered backprojection, scaled by pi / n_views."""
+    """Cosine-weighted ramp-filtered backprojection with the FBP constant
+    pi / N x pu pv / (M h^3) (M = dsd / dso; a ramp at detector pitch) folded
+    into the filter."""
     own = ws is None
     if own:
         ws = dgr.Workspace(dgr.make_plan(P.grid, 0, 0, 0, P.geom))
     filt = torch.empty_like(P.meas)
-    dgr.dgr_fdk_filter(P.geom, P.meas, filt)
+    mag = P.geo.dsd / P.geo.dso if P.geo.beam == dgr.DGR_CONE else 1.0
+    scale = math.pi / P.geo.n_views * (P.geo.pu * P.geo.pv) / (mag * P.gs.h ** 3)
+    dgr.dgr_fdk_filter(P.geom, P.meas, filt, scale)
     vol = torch.empty(P.gs.shape, device=P.meas.device)
     dgr.dgr_backproject(P.grid, P.geom, filt, vol, ws)
-    # FBP on a ray grid: f ~ (pi / N) * (pu pv / (M h^3)) * A^T q for a ramp
-    # filter applied at detector pitch (M = dsd / dso the magnification)
-    mag = P.geo.dsd / P.geo.dso if P.geo.beam == dgr.DGR_CONE else 1.0
-    vol *= math.pi / P.geo.n_views * (P.geo.pu * P.geo.pv) / (mag * P.gs.h ** 3)
     if own:
         ws.close()
     return vol
@@ -152,15 +152,15 @@ def seed(P: Problem, density, log_scale, ns, rng, rescale_iters=3):
 
 def plain_init(P: Problem, ns, rng):
     """The fallback: FBP-seeded Gaussians of a fixed scale (1.5 voxels)."""
-    dens = P.fdk.clamp(min=0.0)
-    logs = torch.full_like(dens, PLAIN_LOG_SCALE)
+    dens, logs = torch.empty_like(P.fdk), torch.empty_like(P.fdk)
+    dgr.dgr_proposals(P.fdk, 1, PLAIN_LOG_SCALE, dens, logs)
     return seed(P, dens, logs, ns, rng)
 
 
 def learned_init(P: Problem, net: Net, ns, rng):
     out = net.forward(P.fdk)
-    dens = out[..., 0].clamp(min=0.0).contiguous()
-    logs = out[..., 1].contiguous()
+    dens, logs = torch.empty_like(P.fdk), torch.empty_like(P.fdk)
+    dgr.dgr_proposals(out, 2, PLAIN_LOG_SCALE, dens, logs)
     return seed(P, dens, logs, ns, rng)
 
 
@@ -225,10 +225,14 @@ def targets_from_fit(P: Problem, st: dgr.State):
     pp, it = dgr.dgr_voxelize_count(P.grid, st.mu, st.s, st.q, 3.0, ws0)
     ws0.close()
     ws = dgr.Workspace(dgr.make_plan(P.grid, st.n, pp + 64, it + 64))
+    mu, s, q, rho = st.view()
     dens = torch.empty(P.gs.shape, device=dev)
-    dgr.dgr_voxelize(P.grid, st.mu, st.s, st.q, st.rho, 3.0, dens, ws)
-    logs_g = (torch.log(st.s / P.gs.h).mean(1)).contiguous()
+    dgr.dgr_voxelize(P.grid, mu, s, q, rho, 3.0, dens, ws)
+    w = torch.empty_like(rho)
+    dgr.dgr_logscale_weight(s, rho, P.gs.h, w)
     wsum = torch.empty_like(dens)
-    dgr.dgr_voxelize(P.grid, st.mu, st.s, st.q, (st.rho * logs_g).contiguous(), 3.0, wsum, ws)
-    logs = torch.where(dens > 1e-3, wsum / dens.clamp(min=1e-3), torch.full_like(dens, PLAIN_LOG_SCALE))
-    return torch.stack([dens, logs.clamp(math.log(0.3), math.log(8.0))], -1).contiguous()
+    dgr.dgr_voxelize(P.grid, mu, s, q, w, 3.0, wsum, ws)
+    out = torch.empty(P.gs.shape + (2,), device=dev)
+    dgr.dgr_fit_targets(dens, wsum, 1e-3, math.log(0.3), math.log(8.0), PLAIN_LOG_SCALE, out)
+    ws.close()
+    return out

@@ -129,10 +129,45 @@ def test_fdk_filter_matches_oracle():
     ang = T(geo.angles)
     gg = dgr.Geom.of(geo, ang)
     out = torch.empty(geo.shape, device=DEV)
-    dgr.dgr_fdk_filter(gg, T(sino), out)
+    dgr.dgr_fdk_filter(gg, T(sino), out, 0.37)
     torch.cuda.synchronize()
-    ref = N.ramlak_filter(sino, geo.pu, 1, dsd=geo.dsd, pv=geo.pv)
+    ref = 0.37 * N.ramlak_filter(sino, geo.pu, 1, dsd=geo.dsd, pv=geo.pv)
     assert rel_l2(out.cpu().numpy(), ref) <= 1e-5
+
+
+def test_proposals_and_fit_targets():
+    """The seeding proposals (density clamped at 0; log-scale from the second
+    channel or a constant) and the training targets (density-weighted mean
+    log-scale, clamped, a default where the density is negligible) against
+    the same definitions written in numpy."""
+    rng = np.random.default_rng(12)
+    src = rng.normal(0, 1, (6, 7, 8, 2)).astype(np.float32)
+    d, l = torch.empty((6, 7, 8), device=DEV), torch.empty((6, 7, 8), device=DEV)
+    dgr.dgr_proposals(T(src), 2, 0.4, d, l)
+    torch.cuda.synchronize()
+    assert np.array_equal(d.cpu().numpy(), np.maximum(src[..., 0], 0))
+    assert np.array_equal(l.cpu().numpy(), src[..., 1])
+    one = np.ascontiguousarray(src[..., 0])
+    dgr.dgr_proposals(T(one), 1, 0.4, d, l)
+    torch.cuda.synchronize()
+    assert np.array_equal(d.cpu().numpy(), np.maximum(one, 0))
+    assert np.all(l.cpu().numpy() == np.float32(0.4))
+    s = rng.uniform(0.4, 5, (50, 3)).astype(np.float32)
+    rho = rng.uniform(0, 1, 50).astype(np.float32)
+    w = torch.empty(50, device=DEV)
+    dgr.dgr_logscale_weight(T(s), T(rho), 0.8, w)
+    torch.cuda.synchronize()
+    assert np.allclose(w.cpu().numpy(), rho * np.log(s / 0.8).mean(1), rtol=1e-5, atol=1e-6)
+    dens = rng.uniform(-0.001, 0.5, 300).astype(np.float32)
+    dens[:20] = 0.0
+    wsum = (dens * rng.uniform(-3, 3, 300)).astype(np.float32)
+    out = torch.empty((300, 2), device=DEV)
+    dgr.dgr_fit_targets(T(dens), T(wsum), 1e-3, np.log(0.3), np.log(8.0), 0.4, out)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    ref = np.where(dens > 1e-3, wsum / np.maximum(dens, 1e-3), 0.4)
+    assert np.array_equal(o[:, 0], dens)
+    assert np.allclose(o[:, 1], np.clip(ref, np.log(0.3), np.log(8.0)), rtol=1e-6, atol=1e-7)
 
 
 def test_seeding_draws_from_the_density():
