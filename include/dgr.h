@@ -46,11 +46,23 @@ extern "C" {
 #define DGR_STATUS_ITEM_OVERFLOW 0x40 /* backward work items exceeded the plan; gradients incomplete */
 #define DGR_STATUS_TIMEOUT 0x80      /* a bounded wait inside a kernel gave up; its output is invalid */
 
-/* Voxel grid: nx, ny, nz <= 32767 voxels of size h, min corner (ox, oy, oz). */
+/* Voxel grid: nx, ny, nz <= 32767 voxels of size h, min corner (ox, oy, oz).
+ * z0 (>= 0, usually 0): this grid is the z-slab of layers [z0, z0 + nz) of a
+ * larger grid with the same origin (ox, oy, oz) and voxel size; voxel (i, j, k)
+ * of the slab has centre (ox, oy, oz) + (i + 1/2, j + 1/2, z0 + k + 1/2) h.
+ * Footprint integers are taken in the larger grid's frame, so a slab's
+ * voxelized values are those of the same layers of the whole grid (bit for
+ * bit when z0 is a multiple of the voxelizer's tile depth, 32).  The line
+ * integral is additive over z-slabs (Sec. 4.3) and the voxel sum over
+ * Gaussians (Eq. 4): the z-slab split of one reconstruction over several GPUs
+ * runs voxelize, project, backproject and the voxelize adjoint on slab grids.
+ * dgr_step, dgr_params_init, dgr_adam, dgr_densify and dgr_seed take whole
+ * grids (z0 = 0). */
 typedef struct {
     int nx, ny, nz;
     float h;
     float ox, oy, oz;
+    int z0;
 } dgr_grid;
 
 #define DGR_PARALLEL 0
@@ -194,9 +206,12 @@ int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sin
                     dgr_ws *ws, cudaStream_t stream);
 
 /* L1 data term of the paper's objective (Sec. 4.3, Eq. 13, first term):
- * loss = mean |pred - meas| (device scalar, fixed-order reduction) and
- * resid = sign(pred - meas) / m (sign(0) = 0).  resid may alias pred. */
-int dgr_l1_residual(const float *pred, const float *meas, long long m, float *resid,
+ * loss = weight x mean |pred - meas| (device scalar, fixed-order reduction)
+ * and resid = weight x sign(pred - meas) / m (sign(0) = 0).  resid may alias
+ * pred.  weight 1 is the term itself; a part of a sinogram (views split over
+ * GPUs) takes weight = m / (all rays), so the parts' losses and residuals add
+ * up to those of the whole. */
+int dgr_l1_residual(const float *pred, const float *meas, long long m, float weight, float *resid,
                     float *loss, dgr_ws *ws, cudaStream_t stream);
 
 /* SSIM term of the objective (paper Sec. 4.3, App. D.1) on its own:
@@ -245,6 +260,16 @@ typedef struct {
 
 /* theta from (mu, s, q, rho); m = v = 0; step = 0. */
 int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t stream);
+
+/* The last phase of dgr_step on its own (Sec. 5.1): with the gradients of
+ * the loss with respect to (mu, s, q, rho) given (device [n][3], [n][3],
+ * [n][4], [n]), one Adam step on theta (chain factors half-extent, s and
+ * sigmoid(theta_rho); learning rate of step *p->step + 1 on the problem's
+ * schedule), mu/s/q/rho rewritten from theta, step incremented.  For a loss
+ * whose gradients were assembled elsewhere (e.g. summed over the z-slabs of
+ * several GPUs): on identical inputs every replica takes the identical step. */
+int dgr_adam(const dgr_problem *prob, const dgr_params *p, const float *g_mu, const float *g_s,
+             const float *g_q, const float *g_rho, cudaStream_t stream);
 
 /* voxelize -> project -> loss and residual -> backproject (+ TV gradient) -> voxelize adjoint ->
  * chain rule to theta -> Adam.  measured: device [n_views][nv][nu];
@@ -417,6 +442,17 @@ int dgr_seed(const dgr_grid *grid, const float *density, const float *log_scale,
  * step matching the seeds' voxelized field vol to the proposed density). */
 int dgr_seed_rescale(int ns, const int *voxel, const float *density, const float *vol, float *rho,
                      cudaStream_t stream);
+
+/* Failure-detection check (the paper has no counterpart).  Every kernel of
+ * this library that waits for asynchronous copies or tensor-core MMAs waits
+ * on an mbarrier for a bounded number of polls; if the wait runs out it ORs
+ * DGR_STATUS_TIMEOUT into the status word and returns, so the host detects the
+ * failure and the context stays usable.  This launches one CTA whose bounded
+ * wait (at most `polls` polls, 1 <= polls <= 2^20, the kernels' own limit)
+ * runs out on purpose: it waits on an mbarrier that nothing arrives at, with
+ * nothing in flight.  status: device int, OR-ed with DGR_STATUS_TIMEOUT;
+ * gave_up: device int, set to 1 (0 if the wait had completed). */
+int dgr_test_bounded_wait(int polls, int *status, int *gave_up, cudaStream_t stream);
 
 /* Total number of kernels this library has launched in this process (a host
  * counter; lets callers count launches inside a timed region). */

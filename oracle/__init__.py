@@ -394,8 +394,19 @@ def step(grid: Grid, geom: Geom, mu, s, q, rho, th, m, v, t, meas, k_trunc, lr0,
         loss += w3 * lt
         gv = gv + w3 * gt
     g_mu, g_s, g_q, g_rho = voxelize_backward_core(grid, mu64, s64, q64, rho64, box, gv)
+    th_new, grads = optimiser_step(grid, th, m, v, t, (g_mu, g_s, g_q, g_rho), lr0, lr1, n_iters)
+    return loss, th_new, grads
+
+
+def optimiser_step(grid: Grid, th, m, v, t, param_grads, lr0, lr1, n_iters):
+    """The last link of an iteration (Sec. 5.1): the gradients with respect
+    to (mu, s, q, rho) chained to the optimiser variables -- d/d((mu-c)/half)
+    = half d/dmu, d/dlog s = s d/ds, q raw, d/d(softplus^-1 rho) =
+    sigmoid(theta_rho) d/drho -- then one Adam step at lr(t).  Returns the new
+    variables and the chained gradients (m, v updated in place)."""
+    g_mu, g_s, g_q, g_rho = param_grads
     _, half = grid_centre_half(grid)
+    s64 = np.exp(th["s"])
     sig = 1.0 / (1.0 + np.exp(-th["rho"]))
     grads = {"mu": g_mu * half, "s": g_s * s64, "q": g_q, "rho": g_rho * sig}
-    th_new = adam_update(th, grads, m, v, t, lr_at(t, lr0, lr1, n_iters))
-    return loss, th_new, grads
+    return adam_update(th, grads, m, v, t, lr_at(t, lr0, lr1, n_iters)), grads

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "dgr_internal.cuh"
@@ -12,12 +13,38 @@ using namespace dgr;
 
 std::atomic<long long> dgr::g_launches{0};
 
+int dgr::wave_ctas(const void *kernel, int threads, size_t smem) {
+    struct Entry {
+        const void *k;
+        int dev, threads, ctas;
+        size_t smem;
+    };
+    static std::mutex mu;
+    static Entry cache[64];
+    static int used = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+        if (cache[i].k == kernel && cache[i].dev == dev && cache[i].threads == threads && cache[i].smem == smem)
+            return cache[i].ctas;
+    int sms = 148, per_sm = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int ctas = sms * per_sm;
+    if (used < 64) cache[used++] = Entry{kernel, dev, threads, ctas, smem};
+    return ctas;
+}
+
 // Host-side validators shared by every entry point (also the no-allocation
 // projector).
 bool dgr::grid_ok(const dgr_grid *g) {
     return g && g->nx > 0 && g->ny > 0 && g->nz > 0 && g->nx <= MAX_DIM && g->ny <= MAX_DIM &&
            g->nz <= MAX_DIM && isfinite(g->h) && g->h > 0.f && isfinite(g->ox) &&
-           isfinite(g->oy) && isfinite(g->oz);
+           isfinite(g->oy) && isfinite(g->oz) && g->z0 >= 0 && g->z0 <= (1 << 24) &&
+           isfinite(slab_origin(*g));
 }
 
 bool dgr::geom_ok(const dgr_geom *geo) {
@@ -253,8 +280,14 @@ namespace {
 
 void set_grid(Inst &I, const dgr_grid &g, float k) {
     I.g = g;
+    // a z-slab is an ordinary grid at its own origin for every kernel but the
+    // prep (footprint integers in the whole grid's frame)
+    I.g.oz = slab_origin(g);
+    I.g.z0 = 0;
+    I.z0 = g.z0;
+    I.oz_full = g.oz;
     I.k = k;
-    I.zoff = -g.oz / g.h;
+    I.zoff = -I.g.oz / g.h;
     tile_dims(g, I.ntx, I.nty, I.ntz);
     I.vsx = 1;  // the C ABI's volume layout: [nz][ny][nx]
     I.vsy = g.nx;
@@ -468,10 +501,11 @@ int dgr_backproject(const dgr_grid *grid, const dgr_geom *geom, const float *sin
     return cuda_rc(e);
 }
 
-int dgr_l1_residual(const float *pred, const float *meas, long long m, float *resid, float *loss,
-                    dgr_ws *ws, cudaStream_t stream) {
-    if (!pred || !meas || !resid || !loss || !ws || m <= 0) return DGR_ERR_ARG;
-    return cuda_rc(launch_l1_single(pred, meas, m, resid, loss, ws_ptr<float>(ws, ws->loss_part), stream));
+int dgr_l1_residual(const float *pred, const float *meas, long long m, float weight, float *resid,
+                    float *loss, dgr_ws *ws, cudaStream_t stream) {
+    if (!pred || !meas || !resid || !loss || !ws || m <= 0 || !isfinite(weight)) return DGR_ERR_ARG;
+    return cuda_rc(launch_l1_single(pred, meas, m, weight, resid, loss, ws_ptr<float>(ws, ws->loss_part),
+                                    stream));
 }
 
 static bool weights_ok(const dgr_problem *P) {
@@ -491,7 +525,7 @@ static void set_objective(Inst &I, const dgr_problem &P) {
 }
 
 static int problem_ok(const dgr_problem *P) {
-    return P && grid_ok(&P->grid) && geom_ok(&P->geom) && k_ok(P->k_trunc) && weights_ok(P) &&
+    return P && grid_ok(&P->grid) && P->grid.z0 == 0 && geom_ok(&P->geom) && k_ok(P->k_trunc) && weights_ok(P) &&
            geom_fits_grid(&P->grid, &P->geom) && isfinite(P->lr0) && isfinite(P->lr1) &&
            P->lr0 > 0.f && P->lr1 > 0.f && P->n_iters >= 1 && P->beta1 >= 0.f && P->beta1 < 1.f &&
            P->beta2 >= 0.f && P->beta2 < 1.f && P->eps > 0.f &&
@@ -508,6 +542,27 @@ static int params_ok(const dgr_params *p) {
 int dgr_params_init(const dgr_problem *prob, const dgr_params *p, cudaStream_t stream) {
     if (!problem_ok(prob) || !params_ok(p)) return DGR_ERR_ARG;
     return cuda_rc(launch_params_init(*prob, *p, stream));
+}
+
+int dgr_adam(const dgr_problem *prob, const dgr_params *p, const float *g_mu, const float *g_s,
+             const float *g_q, const float *g_rho, cudaStream_t stream) {
+    if (!problem_ok(prob) || !params_ok(p) || (p->n > 0 && (!g_mu || !g_s || !g_q || !g_rho)))
+        return DGR_ERR_ARG;
+    Batch &B = *new_batch();
+    B.n = 1;
+    Inst &I = B.in[0];
+    set_grid(I, prob->grid, prob->k_trunc);
+    I.n = p->n;
+    I.g0 = 0;
+    I.mu = p->mu; I.s = p->s; I.q = p->q; I.rho = p->rho;
+    I.mu_w = p->mu; I.s_w = p->s; I.q_w = p->q; I.rho_w = p->rho;
+    I.theta = p->theta; I.m = p->m; I.v = p->v; I.step = p->step; I.gacc = p->grad_accum;
+    I.lr0 = prob->lr0; I.lr1 = prob->lr1; I.b1 = prob->beta1; I.b2 = prob->beta2; I.eps = prob->eps;
+    I.n_iters = prob->n_iters;
+    I.g_mu = const_cast<float *>(g_mu); I.g_s = const_cast<float *>(g_s);
+    I.g_q = const_cast<float *>(g_q); I.g_rho = const_cast<float *>(g_rho);
+    B.tot_g = p->n;
+    return cuda_rc(launch_adam(B, stream));
 }
 
 // voxelize -> project -> L1 -> backproject -> voxelize adjoint -> Adam, for a
@@ -678,7 +733,8 @@ int dgr_tv_loss(const dgr_grid *grid, const float *vol, float *grad, float *loss
 
 int dgr_densify(const dgr_grid *grid, const dgr_densify_cfg *cfg, int iters, const dgr_params *in,
                 const float *normals, dgr_params *out, int *n_out, dgr_ws *ws, cudaStream_t stream) {
-    if (!grid_ok(grid) || !cfg || !in || !out || !n_out || !ws || iters < 1) return DGR_ERR_ARG;
+    if (!grid_ok(grid) || grid->z0 != 0 || !cfg || !in || !out || !n_out || !ws || iters < 1)
+        return DGR_ERR_ARG;
     if (!(cfg->tau >= 0.f) || !(cfg->theta_frac >= 0.f) || !(cfg->size > 0.f) || cfg->n_max < 1 ||
         cfg->n_max >= (1 << 24))
         return DGR_ERR_ARG;

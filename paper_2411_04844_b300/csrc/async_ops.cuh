@@ -38,9 +38,12 @@ __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 // a bounded wait for the phase of the given parity to complete: gives up (and
-// flags the status word) instead of spinning forever
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *status) {
-    for (int it = 0; it < (1 << 20); ++it)
+// flags the status word) after `polls` unsuccessful polls instead of spinning
+// forever (every kernel of the library waits with the default limit)
+constexpr int MBAR_POLLS = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *status,
+                                          int polls = MBAR_POLLS) {
+    for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(status, DGR_STATUS_TIMEOUT);
     return false;

@@ -9,7 +9,14 @@
 
 namespace dgr {
 
+// CTAs of one full wave of `kernel` on the current device (SMs x CTAs resident
+// per SM at `threads` threads and `smem` dynamic shared bytes), looked up once
+// per (device, kernel) and cached: launches do not query the device each time.
+int wave_ctas(const void *kernel, int threads, size_t smem);
+
 // Host-side argument validators (api.cu), shared by every entry point.
+// slab_origin: the z origin of a slab's first layer, oz + z0 h (FP64, rounded once)
+inline float slab_origin(const dgr_grid &g) { return (float)((double)g.oz + (double)g.z0 * (double)g.h); }
 constexpr int MAX_DIM = 32767;          // grid side
 constexpr int MAX_VIEWS_BP = 1 << 20;   // views of one geometry
 bool grid_ok(const dgr_grid *g);
@@ -119,7 +126,10 @@ constexpr int ITEM_QUEUE = 19;  // status word: next run of the adjoint's work i
 constexpr int BIG_ITEMS = 256;
 
 struct Inst {
-    dgr_grid g;
+    dgr_grid g;                       // the grid as the kernels see it: a z-slab's origin
+                                      // moved to its first layer, z0 = 0
+    int z0;                           // the slab's first layer in the whole grid
+    float oz_full;                    // the whole grid's z origin (footprint frame)
     int beam, n_views, nu, nv;
     float pu, pv, dso, dsd;
     const float *angles;
@@ -291,7 +301,7 @@ void set_backprojector_variant(int v);
 // step.cu
 constexpr int L1_BLOCKS = 148 * 8;  // per instance (8 per SM); fixed so the loss reduction order is fixed
 cudaError_t launch_l1(const Batch &B, float *part, const float *gadd, cudaStream_t st);
-cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float *resid,
+cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float w, float *resid,
                              float *loss, float *part, cudaStream_t st);
 cudaError_t launch_params_init(const dgr_problem &P, const dgr_params &p, cudaStream_t st);
 cudaError_t launch_adam(const Batch &B, cudaStream_t st);

@@ -1739,7 +1739,8 @@ int dgr_seed_bytes(int n_side, size_t *bytes) {
 int dgr_seed(const dgr_grid *grid, const float *density, const float *log_scale, int ns,
              const float *u, const float *jitter, float *mu, float *s, float *q, float *rho,
              int *voxel, void *scratch, size_t scratch_bytes, cudaStream_t st) {
-    if (!grid || grid->nx <= 0 || grid->nx != grid->ny || grid->nx != grid->nz || ns < 0) return DGR_ERR_ARG;
+    if (!grid || grid->nx <= 0 || grid->nx != grid->ny || grid->nx != grid->nz || grid->z0 != 0 || ns < 0)
+        return DGR_ERR_ARG;
     if (ns > 0 && (!density || !log_scale || !u || !jitter || !mu || !s || !q || !rho || !voxel || !scratch))
         return DGR_ERR_ARG;
     const long long n3 = (long long)grid->nx * grid->nx * grid->nx;

@@ -1483,7 +1483,9 @@ cudaError_t launch_project_single(const dgr_grid &g, const dgr_geom &geo, RayXY 
     B.n = 1;
     Inst &I = B.in[0];
     I.g = g;
-    I.zoff = -g.oz / g.h;
+    I.g.oz = slab_origin(g);  // a z-slab: an ordinary grid at its first layer
+    I.g.z0 = 0;
+    I.zoff = -I.g.oz / g.h;
     I.beam = geo.beam; I.n_views = geo.n_views; I.nu = geo.nu; I.nv = geo.nv;
     I.pu = geo.pu; I.pv = geo.pv; I.dso = geo.dso; I.dsd = geo.dsd; I.angles = geo.angles;
     I.vol = const_cast<float *>(vol);

@@ -54,22 +54,23 @@ __global__ void __launch_bounds__(L1_THREADS) k_l1(const __grid_constant__ Batch
 }
 
 __global__ void k_l1_single(const float *__restrict__ pred, const float *__restrict__ meas,
-                            long long m, float *resid, float *__restrict__ part) {
-    const float t = l1_block(pred, meas, m, resid, blockIdx.x, gridDim.x, 1.f, nullptr);
+                            long long m, float w, float *resid, float *__restrict__ part) {
+    const float t = l1_block(pred, meas, m, resid, blockIdx.x, gridDim.x, w, nullptr);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// one warp per instance, fixed order: lane-strided FP64 sums, then a shuffle tree
-__device__ __forceinline__ void l1_final(const float *part, int nb, long long m, float *loss) {
+// one warp per instance, fixed order: lane-strided FP64 sums, then a shuffle
+// tree; loss = w x (sum / m)
+__device__ __forceinline__ void l1_final(const float *part, int nb, long long m, float w, float *loss) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) s += (double)part[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) *loss = (float)(s / (double)m);
+    if (threadIdx.x == 0) *loss = (float)((double)w * (s / (double)m));
 }
 
-__global__ void k_l1_final_single(const float *__restrict__ part, long long m, float *loss) {
-    l1_final(part, L1_BLOCKS, m, loss);
+__global__ void k_l1_final_single(const float *__restrict__ part, long long m, float w, float *loss) {
+    l1_final(part, L1_BLOCKS, m, w, loss);
 }
 
 struct Affine {
@@ -173,10 +174,10 @@ cudaError_t launch_l1(const Batch &B, float *part, const float *gadd, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float *resid,
+cudaError_t launch_l1_single(const float *pred, const float *meas, long long m, float w, float *resid,
                              float *loss, float *part, cudaStream_t st) {
-    k_l1_single<<<L1_BLOCKS, L1_THREADS, 0, st>>>(pred, meas, m, resid, part);
-    k_l1_final_single<<<1, 32, 0, st>>>(part, m, loss);
+    k_l1_single<<<L1_BLOCKS, L1_THREADS, 0, st>>>(pred, meas, m, w, resid, part);
+    k_l1_final_single<<<1, 32, 0, st>>>(part, m, w, loss);
     counted(2);
     return cudaGetLastError();
 }

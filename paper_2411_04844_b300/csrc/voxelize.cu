@@ -49,6 +49,9 @@ __device__ __forceinline__ void rot_f32_exact(float w, float x, float y, float z
     R[8] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
 }
 
+// g.oz is the whole grid's z origin and g.z0 the first layer of the slab g
+// describes: the integers are taken in the whole grid's frame, then the z axis
+// is shifted to the slab's layers and clipped to them
 __device__ __forceinline__ void footprint_f32(const dgr_grid &g, const float *mu, const float *s,
                                               const float4 q, float k, Foot &F) {
     rot_f32_exact(q.x, q.y, q.z, q.w, F.R);
@@ -82,9 +85,10 @@ __device__ __forceinline__ void footprint_f32(const dgr_grid &g, const float *mu
             lo = an - half;
             hi = an + half;
         }
-        lo = max(lo, 0);
-        hi = min(hi, dims[a] - 1);
-        F.an[a] = an;
+        const int sh = a == 2 ? g.z0 : 0;
+        lo = max(lo - sh, 0);
+        hi = min(hi - sh, dims[a] - 1);
+        F.an[a] = an - sh;
         F.lo[a] = lo;
         F.hi[a] = hi;
     }
@@ -121,7 +125,10 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= B.tot_g) return;
     const Inst &I = B.in[inst_of_g(B, gi)];
-    const dgr_grid &g = I.g;
+    // the footprint frame: the whole grid's origin and the slab's first layer
+    dgr_grid g = I.g;
+    g.oz = I.oz_full;
+    g.z0 = I.z0;
     const int i = gi - I.g0;
     float m[3] = {I.mu[3 * i], I.mu[3 * i + 1], I.mu[3 * i + 2]};
     float sc[3] = {I.s[3 * i], I.s[3 * i + 1], I.s[3 * i + 2]};
@@ -148,7 +155,7 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double u = ((double)m[a] - org[a]) / h - 0.5;
-        del[a] = (float)(u - (double)F.an[a]);
+        del[a] = (float)(u - (double)(F.an[a] + (a == 2 ? g.z0 : 0)));
     }
     // column form of the exponent (FP64 per Gaussian): Sigma = R diag(s^2) R^T
     // in voxel units from the normalised quaternion; the z column through
@@ -504,16 +511,22 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 float qm = fmaf(r1.x * dx, dx, fmaf(r1.y * dy, dy, r1.z * dx * dy));
                 qm = in ? qm : -INFINITY;
                 const float t0 = r2.w - fmaf(r2.x, dx, r2.y * dy);
-                const float2 a22v = make_float2(r2.z, r2.z), t0v = make_float2(t0, t0),
-                             qmv = make_float2(qm, qm), rv = make_float2(r1.w, r1.w);
+                const float2 a22v = make_float2(r2.z, r2.z), qmv = make_float2(qm, qm),
+                             rv = make_float2(r1.w, r1.w);
+                float2 tv = __fadd2_rn(make_float2(t0, t0), make_float2(0.f, 1.f));
+                const float2 two = make_float2(2.f, 2.f), step8 = make_float2((float)TZG, (float)TZG);
 #pragma unroll
                 for (int g8 = 0; g8 < NG; ++g8) {
-                    if (!(zi & (1 << g8))) continue;  // warp-uniform
+                    if (!(zi & (1 << g8))) {  // warp-uniform
+                        tv = __fadd2_rn(tv, step8);
+                        continue;
+                    }
                     if (zi & (16 << g8)) {            // whole group in the box
 #pragma unroll
                         for (int kk = 0; kk < TZG; kk += 2) {
                             const int k = g8 * TZG + kk;
-                            const float2 t = __fadd2_rn(t0v, make_float2((float)k, (float)(k + 1)));
+                            const float2 t = tv;
+                            tv = __fadd2_rn(tv, two);
                             const float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
                             cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
                         }
@@ -524,7 +537,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
 #pragma unroll
                         for (int kk = 0; kk < TZG; kk += 2) {
                             const int k = g8 * TZG + kk;
-                            const float2 t = __fadd2_rn(t0v, make_float2((float)k, (float)(k + 1)));
+                            const float2 t = tv;
+                            tv = __fadd2_rn(tv, two);
                             float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
                             q = __fadd2_rn(q, make_float2(zmv[kk], zmv[kk + 1]));
                             cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
@@ -736,19 +750,13 @@ template <int TZ>
 static cudaError_t launch_vox_tz(const Batch &B, const Prep *prep, const uint32_t *tile_off,
                                  const uint32_t *list, unsigned long long cap, int *queue,
                                  const int *sep_flag, cudaStream_t st) {
-    int dev = 0, sms = 148, per_sm = 8;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxelize<TZ>, VOX_THREADS, 0);
-    const int grid = max(1, min(B.tot_tiles, sms * max(per_sm, 1)));
+    const int grid = max(1, min(B.tot_tiles, wave_ctas((const void *)k_voxelize<TZ>, VOX_THREADS, 0)));
     // depth 32: the separable kernel as well; exactly one of the two does the work
     const bool sep = TZ == SEP_TZ && g_separable;
     k_voxelize<TZ><<<grid, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep ? sep_flag : nullptr);
     counted(1);
     if (sep) {
-        int per_sm2 = 4;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_voxelize_sep, VOX_THREADS, 0);
-        const int grid2 = max(1, min(B.tot_tiles, sms * max(per_sm2, 1)));
+        const int grid2 = max(1, min(B.tot_tiles, wave_ctas((const void *)k_voxelize_sep, VOX_THREADS, 0)));
         k_voxelize_sep<<<grid2, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep_flag);
         counted(1);
     }

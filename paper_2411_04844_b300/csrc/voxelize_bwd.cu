@@ -381,12 +381,9 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
     err = cudaMemsetAsync(big_count, 0, 2 * sizeof(int), st);
     if (err != cudaSuccess) return err;
     // one wave of resident CTAs; warps take runs of items from the queue
-    int dev = 0, sms = 148, per_sm = 3;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_items, 256, 0);
     if (kev && (err = cudaEventRecord(kev[0], st)) != cudaSuccess) return err;
-    k_bwd_items<<<sms * max(per_sm, 1), 256, 0, st>>>(B, prep, item_off, cap, part, status + ITEM_QUEUE);
+    k_bwd_items<<<wave_ctas((const void *)k_bwd_items, 256, 0), 256, 0, st>>>(B, prep, item_off, cap, part,
+                                                                              status + ITEM_QUEUE);
     if (kev && (err = cudaEventRecord(kev[1], st)) != cudaSuccess) return err;
     k_bwd_final<<<(unsigned)(((long long)B.tot_g * 4 + 127) / 128), 128, 0, st>>>(B, item_off, cap, part, big,
                                                                                     big_count);

@@ -33,12 +33,12 @@ EXPORTS = [
     "dgr_ws_bytes", "dgr_ws_create", "dgr_ws_destroy", "dgr_tile_count", "dgr_status",
     "dgr_strerror", "dgr_set_deterministic", "dgr_footprint", "dgr_voxelize_count",
     "dgr_voxelize", "dgr_voxelize_backward", "dgr_project", "dgr_backproject",
-    "dgr_l1_residual", "dgr_params_init", "dgr_step", "dgr_step_timed", "dgr_launch_count",
+    "dgr_l1_residual", "dgr_params_init", "dgr_adam", "dgr_step", "dgr_step_timed", "dgr_launch_count",
     "dgr_project_noalloc", "dgr_step_batched", "dgr_set_tile_depth", "dgr_set_backprojector",
     "dgr_net_param_count", "dgr_net_ws_bytes", "dgr_net_forward", "dgr_net_backward",
     "dgr_net_loss", "dgr_adam_flat", "dgr_fdk_filter", "dgr_seed_bytes", "dgr_seed",
     "dgr_seed_rescale", "dgr_ssim_loss", "dgr_tv_loss", "dgr_densify", "dgr_set_separable", "dgr_set_staged_walk",
-    "dgr_set_conv_engine", "dgr_net_status", "dgr_pipe_rate", "dgr_l2_rate", "dgr_proposals",
+    "dgr_set_conv_engine", "dgr_net_status", "dgr_pipe_rate", "dgr_l2_rate", "dgr_test_bounded_wait", "dgr_proposals",
     "dgr_logscale_weight", "dgr_fit_targets",
 ]
 # size of the fixed device scratch of dgr_project_noalloc (DGR_NOALLOC_SCRATCH_BYTES)
@@ -56,15 +56,23 @@ class DgrError(RuntimeError):
 
 
 class Grid(ctypes.Structure):
+    """dgr_grid; z0 > 0: the z-slab of layers [z0, z0 + nz) of a larger grid
+    with the same origin (see include/dgr.h)."""
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_float), ("ox", ctypes.c_float), ("oy", ctypes.c_float),
-                ("oz", ctypes.c_float)]
+                ("oz", ctypes.c_float), ("z0", ctypes.c_int)]
 
     @staticmethod
     def of(spec) -> "Grid":
         """From any object with dims (nx, ny, nz), h and org."""
         nx, ny, nz = spec.dims
-        return Grid(nx, ny, nz, spec.h, *spec.org)
+        return Grid(nx, ny, nz, spec.h, *spec.org, 0)
+
+    def slab(self, z0: int, nz: int) -> "Grid":
+        """Layers [z0, z0 + nz) of this (whole) grid."""
+        if self.z0 != 0 or z0 < 0 or nz < 1 or z0 + nz > self.nz:
+            raise DgrError(f"slab [{z0}, {z0 + nz}) of a grid of {self.nz} layers")
+        return Grid(self.nx, self.ny, nz, self.h, self.ox, self.oy, self.oz, z0)
 
     @property
     def shape(self):
@@ -156,7 +164,8 @@ def lib():
             "dgr_voxelize_backward": [ctypes.POINTER(Grid), i, P, P, P, P, f, P, P, P, P, P, P, P],
             "dgr_project": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P, P],
             "dgr_backproject": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P, P],
-            "dgr_l1_residual": [P, P, ll, P, P, P, P],
+            "dgr_l1_residual": [P, P, ll, f, P, P, P, P],
+            "dgr_adam": [ctypes.POINTER(Problem), ctypes.POINTER(Params), P, P, P, P, P],
             "dgr_ssim_loss": [ctypes.POINTER(Geom), P, P, f, P, P, P, P],
             "dgr_tv_loss": [ctypes.POINTER(Grid), P, P, P, P, P],
             "dgr_densify": [ctypes.POINTER(Grid), ctypes.POINTER(DensifyCfg), i, ctypes.POINTER(Params),
@@ -167,6 +176,7 @@ def lib():
                                ctypes.POINTER(P), i],
             "dgr_project_noalloc": [ctypes.POINTER(Grid), ctypes.POINTER(Geom), P, P, P],
             "dgr_pipe_rate": [i, i, i, P, P, P],
+            "dgr_test_bounded_wait": [i, P, P, P],
             "dgr_l2_rate": [i, ll, i, i, P, P, P],
             "dgr_step_batched": [i, ctypes.POINTER(Problem), ctypes.POINTER(Params),
                                  ctypes.POINTER(P), P, P, P],
@@ -377,11 +387,12 @@ def dgr_project_noalloc(grid: Grid, geom: Geom, vol, sino, stream=None):
                                   _stream(stream)), "dgr_project_noalloc")
 
 
-def dgr_l1_residual(pred, meas, resid, loss, ws: Workspace, stream=None):
+def dgr_l1_residual(pred, meas, resid, loss, ws: Workspace, weight=1.0, stream=None):
+    """loss = weight mean|pred - meas|, resid = weight sign(pred - meas) / m."""
     for t, nm in ((pred, "pred"), (meas, "meas"), (resid, "resid"), (loss, "loss")):
         _check(t, nm)
-    _rc(lib().dgr_l1_residual(_ptr(pred), _ptr(meas), pred.numel(), _ptr(resid), _ptr(loss),
-                              ws.ptr, _stream(stream)), "dgr_l1_residual")
+    _rc(lib().dgr_l1_residual(_ptr(pred), _ptr(meas), pred.numel(), float(weight), _ptr(resid),
+                              _ptr(loss), ws.ptr, _stream(stream)), "dgr_l1_residual")
 
 
 def dgr_ssim_loss(geom: Geom, pred, meas, grad, loss, ws: Workspace, data_range=1.0, stream=None):
@@ -441,9 +452,14 @@ class State:
         self.grad_accum = torch.zeros(cap, device=dev) if accumulate else None
 
     def params(self) -> Params:
-        return Params(self.n, _ptr(self.mu), _ptr(self.s), _ptr(self.q), _ptr(self.rho),
-                      _ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.step),
-                      _ptr(self.grad_accum) if self.grad_accum is not None else None)
+        """The dgr_params descriptor (the tensors never move; rebuilt when n changes)."""
+        c = getattr(self, "_params", None)
+        if c is None or c.n != self.n:
+            c = Params(self.n, _ptr(self.mu), _ptr(self.s), _ptr(self.q), _ptr(self.rho),
+                       _ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.step),
+                       _ptr(self.grad_accum) if self.grad_accum is not None else None)
+            self._params = c
+        return c
 
     def view(self):
         """(mu, s, q, rho) of the n Gaussians in use."""
@@ -472,6 +488,15 @@ def dgr_params_init(prob: Problem, st: State, stream=None):
         "dgr_params_init")
 
 
+def dgr_adam(prob: Problem, st: State, g_mu, g_s, g_q, g_rho, stream=None):
+    """One Adam step of the optimiser state from given parameter gradients."""
+    for t, nm in ((g_mu, "g_mu"), (g_s, "g_s"), (g_q, "g_q"), (g_rho, "g_rho")):
+        _check(t, nm)
+    p = st.params()
+    _rc(lib().dgr_adam(ctypes.byref(prob), ctypes.byref(p), _ptr(g_mu), _ptr(g_s), _ptr(g_q),
+                       _ptr(g_rho), _stream(stream)), "dgr_adam")
+
+
 def dgr_step(prob: Problem, st: State, measured, loss_out, ws: Workspace, stream=None):
     _check(measured, "measured"); _check(loss_out, "loss_out")
     p = st.params()
@@ -482,8 +507,8 @@ def dgr_step(prob: Problem, st: State, measured, loss_out, ws: Workspace, stream
 def dgr_step_timed(prob: Problem, st: State, measured, loss_out, ws: Workspace, events,
                    stream=None):
     """dgr_step recording torch.cuda.Events (already created, i.e. recorded
-    once) at the 7 phase boundaries; given 11, also around the backprojector's
-    and the projector's main kernels."""
+    once) at the 7 phase boundaries; given 15, also around the main kernels of
+    the backprojector, the projector, the voxelizer and its adjoint."""
     _check(measured, "measured"); _check(loss_out, "loss_out")
     if len(events) < DGR_STEP_EVENTS:
         raise DgrError(f"dgr_step_timed needs {DGR_STEP_EVENTS} events")
@@ -498,6 +523,14 @@ def dgr_launch_count() -> int:
 
 
 DGR_PIPE_EX2, DGR_PIPE_FFMA, DGR_PIPE_FFMA2 = 0, 1, 2
+DGR_STATUS_TIMEOUT = 0x80
+
+
+def dgr_test_bounded_wait(polls: int, status, gave_up, stream=None):
+    """One CTA whose bounded mbarrier wait runs out (see include/dgr.h)."""
+    _check(status, "status", torch.int32); _check(gave_up, "gave_up", torch.int32)
+    _rc(lib().dgr_test_bounded_wait(int(polls), _ptr(status), _ptr(gave_up), _stream(stream)),
+        "dgr_test_bounded_wait")
 
 
 def dgr_l2_rate(kind: int, buf, passes: int, n_blocks: int, sink, stream=None):

@@ -54,14 +54,17 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def margin_measurement(og, oo, th, rng, k=3.0, lo=0.02, hi=0.06):
+def margin_measurement(og, oo, th, rng, k=3.0, lo=0.02, hi=0.06, signs="random"):
     """Measured projections for an oracle-vs-GPU step comparison: the FP64
     oracle's own prediction at optimiser variables th plus +-U[lo, hi] per
     ray, so no L1 residual sits near its kink (both sides take every sign
-    decision alike).  Also returns the FP32 parameters that decide the box
-    integers (mu, s, q, rho)."""
+    decision alike).  signs="random": a random sign per ray; "positive": the
+    prediction always above the measurement (a residual of one sign, whose
+    backprojection does not cancel).  Also returns the FP32 parameters that
+    decide the box integers (mu, s, q, rho)."""
     p32 = tuple(a.astype(np.float32) for a in O.from_opt(og, th))
     _, box = O.footprint(og, p32[0], p32[1], p32[2], k)
     pred = O.project(og, oo, O.voxelize_core(og, *O.from_opt(og, th), box))
-    meas = pred + rng.choice([-1.0, 1.0], pred.shape) * rng.uniform(lo, hi, pred.shape)
+    sg = rng.choice([-1.0, 1.0], pred.shape) if signs == "random" else -np.ones(pred.shape)
+    meas = pred + sg * rng.uniform(lo, hi, pred.shape)
     return meas.astype(np.float32), p32
