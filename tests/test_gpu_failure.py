@@ -4,6 +4,8 @@ its poll limit, flags DGR_STATUS_TIMEOUT in the status word the host reads,
 and leaves the context usable.  The wait is made to run out on purpose on an
 mbarrier nothing arrives at, with nothing in flight (dgr_test_bounded_wait);
 no trap, fault or endless loop is involved."""
+import time
+
 import numpy as np
 import pytest
 
@@ -21,8 +23,13 @@ DEV = "cuda"
 def test_bounded_wait_gives_up_flags_timeout_and_the_context_survives(polls):
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     gave_up = torch.full((1,), -1, dtype=torch.int32, device=DEV)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     dgr.dgr_test_bounded_wait(polls, status, gave_up)
     torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(f"{polls} unsuccessful polls: {dt * 1e3:.3f} ms")
+    assert dt < 5.0  # the wait ends by its own limit
     assert int(gave_up) == 1
     assert int(status) & dgr.DGR_STATUS_TIMEOUT
     # the context still runs work correctly afterwards

@@ -12,8 +12,9 @@ the parity tests (relative L2 <= 1e-5, max-abs <= 1e-5 max rho); projections and
 relative L2 <= 1e-5; gradients relative L2 <= 1e-5 per kind against the whole
 grid's (the same FP32 moments, split differently); a split step vs dgr_step
 and the oracle: loss within 1e-5 of the mean measured projection (the loss is
-a mean of margins, its error that of the prediction), m and v relative
-L2 <= 2e-4."""
+a mean of margins, its error that of the prediction) for three steps; after
+the first, m and v relative L2 <= 2e-4 and the moves of entries with a
+non-negligible gradient within 1e-2 lr."""
 import datetime
 import socket
 
@@ -154,6 +155,13 @@ def _split(flat, n):
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_emulated_split_steps_match_dgr_step_and_the_oracle(world):
+    """Step 1: the split's Adam moments (they carry the gradients in optimiser
+    variables) and its moves on entries with a non-negligible gradient against
+    dgr_step and the oracle.  Steps 2 and 3: the loss, and every replica
+    identical.  (Beyond step 1 two correct FP32 paths drift apart on entries
+    whose gradient is near Adam's eps: lr g / (|g| + eps) turns their rounding
+    differences into different moves -- the multi-step optimiser parity lives
+    in test_gpu_step_multi, on a field without such entries.)"""
     gs, geo, f, grid, ang, geom, og, oo, th, meas, prob = _split_problem()
     n = f.n
     ranks, states = [], []
@@ -168,10 +176,15 @@ def test_emulated_split_steps_match_dgr_step_and_the_oracle(world):
     st1 = dgr.State(T(f.mu), T(f.s), T(f.q), T(f.rho))
     dgr.dgr_params_init(prob, st1)
     ws1 = _ws(grid, f, geom)
-    ws1 = dgr.Workspace(dgr.make_plan(grid, n, ws1.plan.max_pairs, ws1.plan.max_items, geom, step=True))
+    ws1 = dgr.Workspace(dgr.make_plan(grid, n, 2 * ws1.plan.max_pairs, 2 * ws1.plan.max_items, geom,
+                                      step=True))
     loss1 = torch.zeros(1, device=DEV)
+    th0 = {k: a.copy() for k, a in th.items()}
     m = {k: np.zeros_like(a) for k, a in th.items()}
     v = {k: np.zeros_like(a) for k, a in th.items()}
+    # the loss is a mean of |pred - meas| ~ the margin; its error is that of
+    # the prediction (sinogram tolerance 1e-5 of the projection's scale)
+    tol = 1e-5 * float(np.abs(meas).mean())
     for t in range(1, 4):
         p32 = [a.astype(np.float32) for a in O.from_opt(og, th)]
         lo, th, _ = O.step(og, oo, *p32, th, m, v, t, meas, 3.0, 1e-4, 1e-5, 10)
@@ -179,21 +192,23 @@ def test_emulated_split_steps_match_dgr_step_and_the_oracle(world):
         dgr.dgr_step(prob, st1, T(meas), loss1, ws1)
         torch.cuda.synchronize()
         assert all(R.be.status() == 0 for R in ranks) and dgr.dgr_status(ws1) == 0
-        # the loss is a mean of |pred - meas| ~ the margin; its error is that of
-        # the prediction (sinogram tolerance 1e-5 of the projection's scale)
-        tol = 1e-5 * float(np.abs(meas).mean())
         assert abs(ls - lo) <= tol and abs(ls - float(loss1)) <= tol, (t, ls, lo, float(loss1))
-    # replicas stay identical
-    for st in states[1:]:
-        assert torch.equal(st.theta, states[0].theta) and torch.equal(st.v, states[0].v)
-    for which, ref in (("dgr_step", (st1.m.cpu().numpy(), st1.v.cpu().numpy())),
-                       ("oracle", (np.concatenate([m[k].reshape(-1) for k, _ in KINDS]),
-                                   np.concatenate([v[k].reshape(-1) for k, _ in KINDS])))):
+        for st in states[1:]:  # replicas stay identical
+            assert torch.equal(st.theta, states[0].theta) and torch.equal(st.v, states[0].v)
+        if t > 1:
+            continue
         mg, vg = _split(states[0].m.cpu().numpy(), n), _split(states[0].v.cpu().numpy(), n)
-        mr, vr = _split(ref[0], n), _split(ref[1], n)
-        for k, _ in KINDS:
-            assert rel_l2(mg[k], mr[k]) <= 2e-4, (which, k, "m")
-            assert rel_l2(vg[k], vr[k]) <= 2e-4, (which, k, "v")
+        tg = _split(states[0].theta.cpu().numpy().astype(np.float64), n)
+        refs = (("dgr_step", _split(st1.m.cpu().numpy(), n), _split(st1.v.cpu().numpy(), n),
+                 _split(st1.theta.cpu().numpy().astype(np.float64), n)),
+                ("oracle", m, v, th))
+        for which, mr, vr, thr in refs:
+            for k, _ in KINDS:
+                assert rel_l2(mg[k], mr[k]) <= 2e-4, (which, k, "m", rel_l2(mg[k], mr[k]))
+                assert rel_l2(vg[k], vr[k]) <= 2e-4, (which, k, "v", rel_l2(vg[k], vr[k]))
+                live = np.sqrt(vr[k]) >= 1e-3 * np.max(np.sqrt(vr[k]))
+                d = np.abs((tg[k] - th0[k]) - (thr[k] - th0[k]))
+                assert np.all(d[live] <= 1e-2 * 1e-4), (which, k, float(d[live].max()))
 
 
 def test_split_step_through_a_single_rank_nccl_group():
