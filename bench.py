@@ -50,6 +50,10 @@ def parse():
                     help="l1: the L1 data term (the hot path); paper: 0.6 L1 + 0.2 SSIM + 1 TV")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--split", choices=["replicas", "slab"], default="replicas",
+                    help="replicas: one independent reconstruction per GPU (weak scaling); slab: "
+                         "one reconstruction split into z-slabs over the GPUs (strong scaling, "
+                         "NCCL reduce-scatter / all-gather / all-reduce)")
     return ap.parse_args()
 
 
@@ -494,11 +498,69 @@ def config_block():
             "parallelism": "replicas (one independent reconstruction per GPU)"}
 
 
+def run_slab(args, rank, world, local):
+    """One reconstruction of the workload split into z-slabs over the ranks
+    (paper_2411_04844_b300.slab): per-step CUDA events around each rank's
+    iteration, max over ranks; iterations of the one reconstruction per
+    second."""
+    import torch
+    import torch.distributed as dist
+    from paper_2411_04844_b300 import dgr, slab
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    if "MASTER_ADDR" not in os.environ:  # one GPU without torchrun: a group of one rank
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(sk.getsockname()[1]),
+                              RANK="0", WORLD_SIZE="1")
+    dist.init_process_group("nccl", device_id=torch.device(dev))
+    P = setup_problem(0, dev, "l1")  # every rank builds the same reconstruction
+    wl, prob, st, meas = P["wl"], P["prob"], P["st"], P["meas"]
+    spec = slab.slab_spec(wl.grid.dims[2], wl.geom.n_views, wl.geom.nu * wl.geom.nv, rank, world)
+    R = slab.SlabRank(spec, slab.CudaBackend(prob, st, spec, dev))
+    comm = slab.TorchComm()
+    meas_mine = meas[spec.v0:spec.v0 + spec.nv].contiguous()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        slab.run_step(R, comm, meas_mine)
+    torch.cuda.synchronize()
+    if R.be.status():
+        raise RuntimeError(f"device status {R.be.status():#x} after warm-up")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    loss = None
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record()
+        loss = slab.run_step(R, comm, meas_mine)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    tot = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    t = torch.tensor([tot], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot = float(t.item())
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": K / tot, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": 1000.0 * tot / K, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**config_block(), "parallelism": f"z-slab split of one reconstruction over {world} GPUs"},
+            "loss": float(loss.item()), "split": "slab"}))
+    dist.destroy_process_group()
+
+
 def main():
     args = parse()
     world, rank, local = dist_info()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.split == "slab":
+        run_slab(args, rank, world, local)
         return
     dist = dist_init(world)
     R = run_ours(args, dist, rank, local)

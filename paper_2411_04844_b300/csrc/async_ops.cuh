@@ -39,8 +39,11 @@ __device__ __forceinline__ void fence_barrier_init() {
 }
 // a bounded wait for the phase of the given parity to complete: gives up (and
 // flags the status word) after `polls` unsuccessful polls instead of spinning
-// forever (every kernel of the library waits with the default limit)
-constexpr int MBAR_POLLS = 1 << 20;
+// forever (every kernel of the library waits with the default limit).  An
+// unsuccessful try_wait suspends the thread for about 3 us on the B300, so the
+// default gives up after about 0.8 s; the copies and MMAs waited for complete
+// in microseconds.
+constexpr int MBAR_POLLS = 1 << 18;
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *status,
                                           int polls = MBAR_POLLS) {
     for (int it = 0; it < polls; ++it)

@@ -49,6 +49,6 @@ def test_bounded_wait_gives_up_flags_timeout_and_the_context_survives(polls):
 def test_bounded_wait_rejects_limits_beyond_the_kernels_own():
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     gave_up = torch.zeros(1, dtype=torch.int32, device=DEV)
-    for bad in (0, (1 << 20) + 1):
+    for bad in (0, (1 << 18) + 1):
         with pytest.raises(dgr.DgrError):
             dgr.dgr_test_bounded_wait(bad, status, gave_up)
