@@ -72,23 +72,29 @@ __host__ __device__ inline void item_range(int c, int ex, int ey, int ly, int hy
 // log2(e): the exponent exp(-x/2) is evaluated as ex2(-x/2 * log2(e)).
 constexpr float LOG2E = 1.4426950408889634f;
 
-// Per-Gaussian record written by the prep kernel (64 bytes, 4 x float4).
+// Per-Gaussian record written by the prep kernel (96 bytes, 6 x 16).
 // The exponent -1/2 log2(e) d^T A d is kept in column form: along the z column
 // through (dx, dy) it peaks at dz* = zx dx + zy dy with the value
-// m00 dx^2 + m11 dy^2 + m01 dx dy (the xy block of Sigma inverted, scaled), and
-//     q(dz) = (m00 dx^2 + m11 dy^2 + m01 dx dy) + a22 (dz - dz*)^2,
-// a sum of two terms <= 0: no cancellation however far the peak lies from the
-// centre plane (an expansion about dz = 0 cancels terms of the size of the
-// box corner's exponent for a tilted, elongated Gaussian).
+//     qmin = l1 (n1 . (dx, dy))^2 + l2 (n2 . (dx, dy))^2,
+// n1 = (n1x, n1y), n2 = (-n1y, n1x) and l1, l2 the principal axes and values of
+// (Sigma_xy)^-1 (scaled), and
+//     q(dz) = qmin + a22 (dz - dz*)^2,
+// a sum of terms <= 0: no cancellation however far the peak lies from the
+// centre plane.  The FP64 copies of n1 and (zx, zy) let a caller evaluate the
+// principal coordinates and the peak at a point far from the centre (a tile's
+// centre) in FP64 once, so that lanes add only small FP32 offsets.  For a
+// diagonal A: n1 = (1, 0), l1 = the x and l2 the y coefficient, zx = zy = 0.
 struct __align__(16) Prep {
     float dx, dy, dz, rho;      // delta = u - a (voxel units), intensity
-    float m00, m11, a22, m01;   // x 1/2 log2(e): (Sigma_xy)^-1 (off-diagonal doubled), A_zz
+    float l1, l2, a22, n1x;     // x -1/2 log2(e): principal values of (Sigma_xy)^-1, A_zz
     float zx, zy;               // the column's peak: dz* = zx dx + zy dy
     int ax, ay;                 // anchor a = floor(u)
     int az;
     int bx, by, bz;             // box per axis: lo | hi << 16 (lo > hi: empty)
+    double n1x_d, n1y_d;        // n1 in FP64
+    double zx_d, zy_d;          // (zx, zy) in FP64
 };
-static_assert(sizeof(Prep) == 64, "Prep must be 64 bytes");
+static_assert(sizeof(Prep) == 96, "Prep must be 96 bytes");
 
 __host__ __device__ inline int box_lo(int p) { return (int)(short)(p & 0xffff); }
 __host__ __device__ inline int box_hi(int p) { return (int)(short)((unsigned)p >> 16); }

@@ -26,6 +26,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "async_ops.cuh"
 #include "dgr_internal.cuh"
 
@@ -1241,7 +1243,46 @@ int bp_bricks(const dgr_grid &g, int &nbx, int &nby, int &nbz) {
 // Colour classes for the brick backprojector: a voxel's projected footprint,
 // bounded over a 5 x 5 x 5 lattice of grid positions and every view (FP64,
 // 10% margin), must be narrower than col_u x col_v pixels.
+// The bound depends on the grid and the geometry's scalars only (every angle
+// of the full circle is sampled): cached for the last few (grid, geometry)
+// pairs, so an iteration does not redo the 72 x 125 x 8 corner projections.
+static void bp_colours_compute(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv);
 void bp_colours(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv) {
+    struct Entry {
+        dgr_grid g;
+        int beam, nu, nv;
+        float pu, pv, dso, dsd;
+        int cu, cv;
+    };
+    static std::mutex mu;
+    static Entry cache[32];
+    static int next = 0, used = 0;
+    auto same = [&](const Entry &e) {
+        return memcmp(&e.g, &g, sizeof(dgr_grid)) == 0 && e.beam == geo.beam && e.nu == geo.nu &&
+               e.nv == geo.nv && e.pu == geo.pu && e.pv == geo.pv && e.dso == geo.dso && e.dsd == geo.dsd;
+    };
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (int i = 0; i < used; ++i)
+            if (same(cache[i])) {
+                cu = cache[i].cu;
+                cv = cache[i].cv;
+                return;
+            }
+    }
+    bp_colours_compute(g, geo, cu, cv);
+    std::lock_guard<std::mutex> lock(mu);
+    Entry e{};
+    e.g = g;
+    e.beam = geo.beam; e.nu = geo.nu; e.nv = geo.nv;
+    e.pu = geo.pu; e.pv = geo.pv; e.dso = geo.dso; e.dsd = geo.dsd;
+    e.cu = cu; e.cv = cv;
+    cache[next] = e;
+    next = (next + 1) % 32;
+    if (used < 32) ++used;
+}
+
+static void bp_colours_compute(const dgr_grid &g, const dgr_geom &geo, int &cu, int &cv) {
     double wu = 0.0, wv = 0.0;
     const double h = g.h;
     // the angles live on the device: bound over the full circle instead,

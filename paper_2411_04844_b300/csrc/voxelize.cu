@@ -162,8 +162,9 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
     // (dx, dy) peaks at dz* = Sigma_z,xy (Sigma_xy)^-1 (dx, dy) with the value
     // -1/2 (dx, dy) (Sigma_xy)^-1 (dx, dy)^T, and A_zz = 1 / Var(z | x, y)
     // = sum_k R_zk^2 / s_k^2 (a sum of positive terms).  The xy block is
-    // inverted directly: the Schur complement of A would cancel for thin,
-    // tilted Gaussians.  Scaled by -1/2 log2(e) for ex2.
+    // inverted directly (the Schur complement of A would cancel for thin,
+    // tilted Gaussians) and split into principal axes.  Scaled by
+    // -1/2 log2(e) for ex2.
     const double c = -0.5 * (double)LOG2E;
     double m00, m11, m01, zx, zy, azz;
     bool diag;
@@ -202,14 +203,33 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
         zy = m01 * S[4] + m11 * S[5];
         diag = S[3] == 0.0 && S[4] == 0.0 && S[5] == 0.0;
     }
+    // principal axes of (Sigma_xy)^-1: l1 >= l2 with unit vector n1 (diagonal:
+    // the x and y axes, in that order)
+    double l1, l2, n1x, n1y;
+    if (diag || m01 == 0.0) {
+        l1 = m00; l2 = m11; n1x = 1.0; n1y = 0.0;
+    } else {
+        const double hm = 0.5 * (m00 + m11), dm = 0.5 * (m00 - m11);
+        const double r = sqrt(dm * dm + m01 * m01);
+        l1 = hm + r;
+        l2 = (m00 * m11 - m01 * m01) / l1;  // the product of the eigenvalues over l1: no cancellation
+        // eigenvector of l1: (m01, l1 - m00) or (l1 - m11, m01), whichever is longer
+        const double ax1 = m01, ay1 = l1 - m00, ax2 = l1 - m11, ay2 = m01;
+        const bool first = ax1 * ax1 + ay1 * ay1 >= ax2 * ax2 + ay2 * ay2;
+        const double ex = first ? ax1 : ax2, ey = first ? ay1 : ay2;
+        const double inv = 1.0 / sqrt(ex * ex + ey * ey);
+        n1x = ex * inv;
+        n1y = ey * inv;
+    }
     // a Gaussian with off-diagonal terms rules out the separable voxelizer
     if (!diag) status[SEP_FLAG] = 1;
     P.dx = del[0]; P.dy = del[1]; P.dz = del[2]; P.rho = r;
-    P.m00 = (float)(c * m00); P.m11 = (float)(c * m11); P.m01 = (float)(2.0 * c * m01);
+    P.l1 = (float)(c * l1); P.l2 = (float)(c * l2); P.n1x = (float)n1x;
     P.a22 = (float)(c * azz);
     P.zx = diag ? 0.f : (float)zx;
     P.zy = diag ? 0.f : (float)zy;
-    if (diag) P.m01 = 0.f;
+    P.n1x_d = n1x; P.n1y_d = n1y;
+    P.zx_d = diag ? 0.0 : zx; P.zy_d = diag ? 0.0 : zy;
     P.ax = F.an[0]; P.ay = F.an[1]; P.az = F.an[2];
     // an axis that misses the grid empties the whole box (packed as lo 1, hi 0)
     const bool empty = F.lo[0] > F.hi[0] || F.lo[1] > F.hi[1] || F.lo[2] > F.hi[2];
@@ -391,8 +411,12 @@ __constant__ ZMask c_zmask = make_zmask();
 // Per (tile, Gaussian) record of a staged chunk, built once per CTA by one
 // thread, so that a warp's visit of the Gaussian costs only the per-lane set-up
 // of its column's quadratic:
-//   r0 = (a_x - x0, a_y - y0) as exact floats and delta_x, delta_y
-//   r1 = (m00, m11, m01, rho), r2 = (zx, zy, a22, dz0 = (z0 - a_z) - delta_z)
+//   r0 = (c1, c2, tau, rho): the principal coordinates n1 . d, n2 . d of the
+//        tile's centre column and the offset tau of the tile's middle layer
+//        from that column's peak, in FP64 (then rounded): lanes add only
+//        offsets of at most 3.5 (x) and 7.5 (y) voxels, so the exponent keeps
+//        its precision however far the tile lies from the Gaussian's centre
+//   r1 = (l1, l2, a22, zx), r2 = (n1x, n1y, zy, 0)
 //   lane masks: per warp, bit l set when lane l's (x, y) column lies in the box
 //   zinfo: bits 0-3 the z groups of TZG layers the box reaches, bits 4-7 those
 //          it covers whole; rows: per group, the row (lo * TZG + hi) of the
@@ -411,9 +435,10 @@ struct VisitChunk {
 // Per chunk of VOX_CHUNK Gaussians of the tile's list: the staging threads
 // build the visit records; each warp visits (ballot over the chunk) only the
 // Gaussians whose box covers one of its columns, in list order; per visit a
-// lane sets up its column's peak (value qmin, offset t0 of the tile's first
-// layer from the peak) and evaluates q = qmin + a22 t^2, t = t0 + k, on the z
-// groups of TZG layers the box reaches (a partly covered group adds 0 or -1e30 from the
+// lane sets up its column's peak (value qmin from its principal coordinates,
+// offset t0 of the tile's middle layer from the peak) and evaluates
+// q = qmin + a22 t^2, t = t0 + k - (TZ - 1)/2, on the z groups of TZG layers
+// the box reaches (a partly covered group adds 0 or -1e30 from the
 // layer-mask table to the exponent: ex2 of the latter is 0).
 template <int TZ>
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
@@ -430,7 +455,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     __shared__ int s_tile;
     if (sep_off && *sep_off == 0) return;  // every Gaussian separable: k_voxelize_sep runs
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float lxf = (float)(lane & 7), lyf = (float)(4 * w + (lane >> 3));
+    // the lane's column relative to the tile's centre column
+    const float lxc = (float)(lane & 7) - 0.5f * (TX - 1), lyc = (float)(4 * w + (lane >> 3)) - 0.5f * (TY - 1);
     for (;;) {
         __syncthreads();  // everyone is done with s_tile and the records
         if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
@@ -456,6 +482,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 const int j = threadIdx.x;
                 const float4 *pp = reinterpret_cast<const float4 *>(prep + list[c0 + j]);
                 const float4 p0 = pp[0], p1 = pp[1], p2 = pp[2], p3 = pp[3];
+                const double2 n1 = reinterpret_cast<const double2 *>(pp + 4)[0],
+                              zz = reinterpret_cast<const double2 *>(pp + 4)[1];
                 const int ax = __float_as_int(p2.z), ay = __float_as_int(p2.w), az = __float_as_int(p3.x);
                 const int bx = __float_as_int(p3.y), by = __float_as_int(p3.z), bz = __float_as_int(p3.w);
                 const int xl = max(box_lo(bx) - x0, 0), xh = min(box_hi(bx) - x0, TX - 1);
@@ -482,9 +510,16 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 }
                 vc.zinfo[j] = act | (full << 4);
                 vc.rows[j] = rows;
-                vc.r0[j] = make_float4((float)(ax - x0), (float)(ay - y0), p0.x, p0.y);
-                vc.r1[j] = make_float4(p1.x, p1.y, p1.w, p0.w);
-                vc.r2[j] = make_float4(p2.x, p2.y, p1.z, (float)(z0 - az) - p0.z);
+                // the tile's centre column and middle layer relative to the
+                // Gaussian's centre, in FP64
+                const double Xc = (double)(x0 - ax) + 0.5 * (TX - 1) - (double)p0.x;
+                const double Yc = (double)(y0 - ay) + 0.5 * (TY - 1) - (double)p0.y;
+                const double Zc = (double)(z0 - az) + 0.5 * (TZ - 1) - (double)p0.z;
+                const double c1 = n1.x * Xc + n1.y * Yc, c2 = n1.x * Yc - n1.y * Xc;
+                const double tau = Zc - (zz.x * Xc + zz.y * Yc);
+                vc.r0[j] = make_float4((float)c1, (float)c2, (float)tau, p0.w);
+                vc.r1[j] = make_float4(p1.x, p1.y, p1.z, p2.x);
+                vc.r2[j] = make_float4(p1.w, (float)n1.y, p2.y, 0.f);
             }
             __syncthreads();
             // this warp's visits, in list order
@@ -504,16 +539,18 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 const bool in = (vc.lanes[w][j] >> lane) & 1u;
                 const float4 r0 = vc.r0[j], r1 = vc.r1[j], r2 = vc.r2[j];
                 const int zi = vc.zinfo[j], rows = vc.rows[j];
-                const float dx = (lxf - r0.x) - r0.z;
-                const float dy = (lyf - r0.y) - r0.w;
-                // the column's peak value (<= 0, already scaled) and the offset
-                // of the tile's first layer from the peak
-                float qm = fmaf(r1.x * dx, dx, fmaf(r1.y * dy, dy, r1.z * dx * dy));
+                // the column's principal coordinates, its peak value (<= 0,
+                // already scaled) and the offset of the tile's middle layer
+                // from the peak
+                const float c1 = fmaf(r2.x, lxc, fmaf(r2.y, lyc, r0.x));
+                const float c2 = fmaf(-r2.y, lxc, fmaf(r2.x, lyc, r0.y));
+                float qm = fmaf(r1.x * c1, c1, r1.y * c2 * c2);
                 qm = in ? qm : -INFINITY;
-                const float t0 = r2.w - fmaf(r2.x, dx, r2.y * dy);
-                const float2 a22v = make_float2(r2.z, r2.z), qmv = make_float2(qm, qm),
-                             rv = make_float2(r1.w, r1.w);
-                float2 tv = __fadd2_rn(make_float2(t0, t0), make_float2(0.f, 1.f));
+                const float t0 = r0.z - fmaf(r1.w, lxc, r2.z * lyc);
+                const float2 a22v = make_float2(r1.z, r1.z), qmv = make_float2(qm, qm),
+                             rv = make_float2(r0.w, r0.w);
+                float2 tv = __fadd2_rn(make_float2(t0, t0),
+                                       make_float2(-0.5f * (TZ - 1), 1.f - 0.5f * (TZ - 1)));
                 const float2 two = make_float2(2.f, 2.f), step8 = make_float2((float)TZG, (float)TZG);
 #pragma unroll
                 for (int g8 = 0; g8 < NG; ++g8) {

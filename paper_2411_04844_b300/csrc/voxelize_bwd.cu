@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
             const dgr_grid &g = I.g;
             const float *__restrict__ gv = I.gvol;
             const Prep P = prep[gi];
+            const float n1y = (float)P.n1y_d;
             const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
                       lz = box_lo(P.bz), hz = box_hi(P.bz);
             const int ex = hx - lx + 1, ey = hy - ly + 1;
@@ -93,8 +94,10 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
                 const int yy = yb + row, xx = lx + (j - row * ex);
                 const float dx = (float)(xx - P.ax) - P.dx;
                 const float dy = (float)(yy - P.ay) - P.dy;
-                // column form: q = qm + a22 t^2, t = dz - dz* (the column's peak)
-                const float qm = fmaf(P.m00 * dx, dx, fmaf(P.m11 * dy, dy, P.m01 * dx * dy));
+                // column form: q = qm + a22 t^2, t = dz - dz* (the column's peak),
+                // qm from the column's principal coordinates
+                const float c1 = fmaf(P.n1x, dx, n1y * dy), c2 = fmaf(-n1y, dx, P.n1x * dy);
+                const float qm = fmaf(P.l1 * c1, c1, P.l2 * c2 * c2);
                 const float dzs = fmaf(P.zx, dx, P.zy * dy);
                 const float t0 = dz0 - dzs;
                 const float *col = gv + ((size_t)zb * g.ny + yy) * g.nx + xx;

@@ -82,3 +82,27 @@ def test_noalloc_projector_refuses_on_the_host():
     geo = dgr.Geom(dgr.DGR_CONE, 4, 8, 8, 1.0, 1.0, 10.0, 20.0, 256)
     assert L.dgr_project_noalloc(ctypes.byref(g), ctypes.byref(geo), fake, fake,
                                  None) == dgr.DGR_ERR_ARG
+
+
+def test_slab_grids_are_validated_on_the_host():
+    """dgr_grid.z0 must be >= 0; the calls that take whole grids (the fused
+    step, the optimiser, densification, seeding) refuse a slab.  The pointers
+    are never dereferenced on these paths."""
+    from paper_2411_04844_b300 import dgr
+    L = dgr.lib()
+    t = ctypes.c_int()
+    whole = dgr.Grid(64, 64, 64, 1.0, -32.0, -32.0, -32.0)
+    assert L.dgr_tile_count(ctypes.byref(whole.slab(32, 32)), ctypes.byref(t)) == dgr.DGR_OK
+    bad = dgr.Grid(64, 64, 32, 1.0, -32.0, -32.0, -32.0, -1)
+    assert L.dgr_tile_count(ctypes.byref(bad), ctypes.byref(t)) == dgr.DGR_ERR_ARG
+    with pytest.raises(dgr.DgrError):
+        whole.slab(40, 32)  # past the whole grid's last layer
+    fake = ctypes.c_void_p(256)
+    geo = dgr.Geom(dgr.DGR_PARALLEL, 4, 8, 8, 1.0, 1.0, 0.0, 0.0, 256)
+    prob = dgr.make_problem(whole.slab(0, 32), geo)
+    prob.grid.z0 = 8
+    p = dgr.Params(4, fake, fake, fake, fake, fake, fake, fake, fake, None)
+    assert L.dgr_adam(ctypes.byref(prob), ctypes.byref(p), fake, fake, fake, fake, None) == dgr.DGR_ERR_ARG
+    assert L.dgr_params_init(ctypes.byref(prob), ctypes.byref(p), None) == dgr.DGR_ERR_ARG
+    prob.grid.z0 = 0
+    assert L.dgr_adam(ctypes.byref(prob), ctypes.byref(p), None, fake, fake, fake, None) == dgr.DGR_ERR_ARG
