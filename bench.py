@@ -252,7 +252,8 @@ def run_ours(args, dist, rank, local):
     meas_dev = [meas.clone() for _ in range(2)]
     # the step as a CUDA graph (graph.step_graph, the library's replayable
     # iteration), one per input buffer: one launch per step, so the host's
-    # enqueue time (about 1.2 ms per eager dgr_step) cannot limit the loop
+    # enqueue time (about 0.1 ms per eager dgr_step, more on a slower host)
+    # cannot limit the loop
     from paper_2411_04844_b300 import graph as dgr_graph
     g_e2e = [dgr_graph.step_graph(prob, st, meas_dev[b], loss, ws, warmup=1) for b in range(2)]
     copy_stream = torch.cuda.Stream()
