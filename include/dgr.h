@@ -394,11 +394,15 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
  * (device scalar) and grad_output = d loss / d output. */
 int dgr_net_loss(int n, const float *output, const float *target, float w_density, float w_scale,
                  float *grad_output, float *loss, void *ws, size_t ws_bytes, cudaStream_t stream);
-/* Convolution engine: 2 = tcgen05 on halo tiles for all three GEMMs
- * (default: an 8 x 16 x ZT output tile's input block with a one-voxel halo
- * loaded once, every tap a descriptor into it), 1 = tcgen05 on gathered
+/* Convolution engine: 2 = tcgen05 (default): forward and data gradient with
+ * the three z taps of one (dy, dx) in one MMA (N = 3 x output channels) over
+ * TMA-loaded halo blocks (an 8 x 16 x ZT output tile's input block with a
+ * one-voxel halo, every tap a descriptor into it), weight gradient with the
+ * input channels x z offsets on M and the y offsets x output channels on N;
+ * 3 = tcgen05 on halo tiles with one MMA per tap (N = output channels) and
+ * the weight gradient with the output channels on M; 1 = tcgen05 on gathered
  * 128-row tiles (im2col into shared memory) for forward and data gradient,
- * mma.sync for the weight gradient, 0 = mma.sync m16n8k16 for all.
+ * mma.sync for the weight gradient; 0 = mma.sync m16n8k16 for all.
  * Process-wide; DGR_ERR_ARG otherwise. */
 int dgr_set_conv_engine(int engine);
 /* The network's device status word on ws (DGR_STATUS_TIMEOUT when a bounded

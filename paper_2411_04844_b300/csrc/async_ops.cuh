@@ -67,6 +67,22 @@ __device__ __forceinline__ void bulk_s2g_add(int *dst, const int *src, unsigned 
                  "r"(smem_u32(src)), "r"(bytes)
                  : "memory");
 }
+// 4D tiled tensor copy global -> shared through a tensor map (the tensor map
+// a __grid_constant__ kernel parameter; coordinates innermost first, elements
+// outside the tensor read as zero), completing on an mbarrier with its bytes.
+// The innermost coordinate times the element size must be a multiple of 16
+// bytes and the destination 128-byte aligned.
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
@@ -76,7 +92,17 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned 
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
                  : "memory");
 }
+// 4-byte form (through L1); src_bytes = 0 zero-fills
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// the mbarrier receives one arrival (counted in its expected count) once every
+// cp.async this thread issued so far has completed
+__device__ __forceinline__ void cp_async_mbar_arrive(unsigned long long *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
@@ -159,6 +185,18 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
                  : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns of one tensor-memory lane per thread written
+// with zeros (lanes as for tmem_ld16); waits until the stores are done
+__device__ __forceinline__ void tmem_zero16(unsigned taddr) {
+    const unsigned z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+            taddr),
+        "r"(z)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 }  // namespace dgr

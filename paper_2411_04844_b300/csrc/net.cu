@@ -18,13 +18,20 @@
 //   data grad    C[p][ci] = sum_{tap,co} G[p - tap][co] W[tap][ci][co]
 //   weight grad  C[tap*Ci + ci][co] = sum_p X[p + tap][ci] G[p][co]
 //                (split over voxel ranges; partials summed in a fixed order)
-// By default all three run on tcgen05 over halo blocks (k_conv_halo,
-// k_wgrad_halo); dgr_set_conv_engine selects gathered 128-row tcgen05 tiles
-// for forward and data gradient (k_conv_umma) or mma.sync m16n8k16
-// (k_conv_gemm, also the weight gradient of the other two engines).
+// By default all three run on tcgen05 over TMA-loaded halo blocks with
+// several taps per MMA (k_conv_dz: the three z taps of one (dy, dx);
+// k_wgrad_dz: z offsets on M, y offsets on N; k_wgrad_halo for the 16 -> 32
+// layer); dgr_set_conv_engine selects the earlier designs for comparison:
+// halo blocks with one MMA per tap (k_conv_halo, k_wgrad_halo), gathered
+// 128-row tcgen05 tiles for forward and data gradient (k_conv_umma) or
+// mma.sync m16n8k16 (k_conv_gemm, also the weight gradient of engines 0, 1).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "async_ops.cuh"
 #include "dgr_internal.cuh"
@@ -53,7 +60,9 @@ struct ConvArgs {
     bf16 *y;          // FWD: output [n^3][co]
     float *out;       // DGRAD: [n^3][ci] FP32; WGRAD: partials [splits][27*ci][co]
     const bf16 *wt;   // tcgen05 FWD / DGRAD: the weights as B, K-major [N][K]
+    const bf16 *wdz;  // k_conv_dz FWD / DGRAD: the weights as its B (k_wpack_dz)
     int *status;      // device status word (bounded waits)
+    int up_adj;       // k_conv_dz DGRAD: write the 2^3 child sums at half resolution (see k_conv_dz)
 };
 
 __device__ __forceinline__ void tap_offset(int tap, int &dx, int &dy, int &dz) {
@@ -253,6 +262,25 @@ __device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int c
 #pragma unroll
         for (int i = 0; i < 4; ++i) op[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
+}
+
+// forward output of 16 channels: relu(v + bias + residual) as BF16 (the
+// residual, 16 BF16, passed in two uint4; zero without one)
+__device__ __forceinline__ void store_fwd16(bf16 *y, float *v, const float *bias, uint4 s0, uint4 s1) {
+    const uint32_t su[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    uint32_t pk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        __nv_bfloat162 h;
+        memcpy(&h, &su[i], 4);
+        const float2 f = __bfloat1622float2(h);
+        const __nv_bfloat162 o = __floats2bfloat162_rn(fmaxf(v[2 * i] + f.x + bias[2 * i], 0.f),
+                                                       fmaxf(v[2 * i + 1] + f.y + bias[2 * i + 1], 0.f));
+        memcpy(&pk[i], &o, 4);
+    }
+    uint4 *yp = reinterpret_cast<uint4 *>(y);
+    yp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    yp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 }
 
 template <int MODE, int BN>
@@ -833,6 +861,484 @@ __global__ void __launch_bounds__(HALO_THREADS) k_wgrad_halo(const ConvArgs a, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Forward and data gradient on tcgen05 with the three z taps of one (dy, dx)
+// in one MMA.  Output slice zo of a tile takes input slice zo + 1 + dz (halo
+// coordinates) through the weights of input offset dz, so one input slice zi
+// feeds the output slices zi - 2, zi - 1 and zi through the offsets dz = +1, 0
+// and -1: with B holding those three weight matrices side by side (N = 3 NO)
+// and the accumulators of consecutive output slices in consecutive
+// tensor-memory columns, one MMA of N = 3 NO per (input slice, dy, dx, K
+// chunk pair) covers all three.  Per tile that is (ZT + 2) x 9 x C / 16 MMAs
+// instead of 27 ZT C / 16 with N = NO: the A tile (128 voxels x 16 channels,
+// read from shared memory by the tensor core for every MMA) is read about
+// 3 ZT / (ZT + 2) times less often.  Input slices at the ends feed only the
+// output slices inside the tile (narrower N, no wasted products).
+//
+// The MMAs of one thread do not overlap one another on the tensor core (for
+// these narrow MMAs each costs about its operand reads + math + accumulate),
+// so ISS threads issue them: thread k the input slices zi = k (mod ISS), into
+// its own accumulator set (no two threads write the same columns); the
+// epilogue adds the sets.  Every MMA accumulates: the epilogue zeroes a set
+// after draining it (and once at the start).
+//
+// The input block of a tile (10 x 18 x (ZT + 2) voxels with the one-voxel
+// halo, zero outside the grid) arrives by TMA, one 4D box per 8-channel chunk
+// plane: elements [z][y][x][8 channels] in a plane, so eight consecutive x
+// voxels of a line are a K-major core matrix (rows 16 bytes apart), lines are
+// M-adjacent (160 bytes) and chunk planes K-adjacent.  Units of CH / KS chunk
+// planes of one tile cycle through S stages.  Warp roles: warp 0 lane 0
+// issues the copies, lane 0 of warps 1 .. ISS the MMAs (two accumulator
+// buffers, so tile i's MMAs run while tile i - 1 is drained), warps 4-7 drain
+// the accumulators (warp w reads tensor-memory lanes 32 (w % 4) ..) into the
+// output.  Every wait is bounded; a role that gives up stops, and the copies
+// and MMAs it issued are waited for (bounded) before the tensor memory is
+// freed.
+// ---------------------------------------------------------------------------
+template <int C, int NO, int ZT, int KS, int S, int ISS>
+struct DzCfg {
+    static constexpr int HX = 10, HY = 18, HZ = ZT + 2, CH = C / 8, CHS = CH / KS;
+    static constexpr unsigned PLANE = 16u * HX * HY * HZ;  // one chunk plane of the input block
+    static constexpr unsigned STAGE = PLANE * CHS;         // one unit: CHS chunk planes of a tile
+    static constexpr int N3 = 3 * NO;
+    static constexpr unsigned BLEAD = (unsigned)N3 * 16;  // K-chunk pitch of B
+    static constexpr unsigned BBYTES = 9u * CH * BLEAD;    // = 27 C NO bf16
+    static constexpr unsigned SOFF = (BBYTES + 1023u) & ~1023u;
+    static constexpr unsigned BAROFF = SOFF + (unsigned)S * STAGE;
+    static constexpr int SET = ZT * NO;               // columns of one accumulator set
+    static constexpr int COLS = 2 * ISS * SET;        // two buffers of ISS sets
+    static constexpr unsigned NCOL = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
+    static constexpr size_t SMEM = 1024 + (size_t)BAROFF + 512;  // + barriers, tensor-memory slot, biases
+    static_assert(PLANE % 128 == 0, "TMA destinations are 128-byte aligned");
+    static_assert(CH % KS == 0 && CHS % 2 == 0, "units of whole K chunk pairs");
+    static_assert(NO % 16 == 0 && N3 <= 256 && COLS <= 512, "MMA and tensor-memory shapes");
+    static_assert(ISS >= 1 && ISS <= 3 && SMEM <= 232448, "issuers, shared memory");
+};
+
+constexpr int DZ_THREADS = 256;
+
+template <int MODE, int C, int NO, int ZT, int KS, int S, int ISS>
+__global__ void __launch_bounds__(DZ_THREADS, 1) k_conv_dz(const __grid_constant__ CUtensorMap tmap,
+                                                           const ConvArgs a) {
+    static_assert(MODE == MODE_FWD || MODE == MODE_DGRAD, "forward and data gradient only");
+    using D = DzCfg<C, NO, ZT, KS, S, ISS>;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned char *Bs = sm, *St = sm + D::SOFF;
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(sm + D::BAROFF);
+    unsigned long long *empty = full + S, *accf = full + 2 * S, *acce = full + 2 * S + 2;
+    unsigned *tslot = reinterpret_cast<unsigned *>(full + 2 * S + 4);
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w == 0) {
+        tmem_alloc(tslot, D::NCOL);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);     // the producer's expect_tx arrival (+ the copies' bytes)
+            mbar_init(&empty[s], ISS);  // one commit per issuer
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], ISS);  // each issuer's commit after a tile's last MMA
+            mbar_init(&acce[b], 4);    // one arrival per draining warp (zeroed, free)
+        }
+        fence_barrier_init();
+    }
+    // B: the weights of the three z offsets of each (dy, dx) side by side,
+    // core matrix (n group g, K chunk t9 CH + kc) at (t9 CH + kc) BLEAD + g 128
+    for (int e = threadIdx.x; e < 9 * D::CH * D::N3; e += DZ_THREADS) {
+        const int tk = e / D::N3, r = e % D::N3;
+        const uint4 v = reinterpret_cast<const uint4 *>(a.wdz)[e];
+        *reinterpret_cast<uint4 *>(Bs + tk * D::BLEAD + (r >> 3) * 128 + (r & 7) * 16) = v;
+    }
+    float *sbias = reinterpret_cast<float *>(tslot + 1);  // NO biases (forward)
+    if (MODE == MODE_FWD)
+        for (int c = threadIdx.x; c < NO; c += DZ_THREADS) sbias[c] = a.bias[c];
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tslot;
+
+    const int n = a.n;
+    const int ntx = (n + 7) / 8, nty = (n + 15) / 16, ntz = (n + ZT - 1) / ZT;
+    const int ntiles = ntx * nty * ntz;
+    const int cnt = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const int units = cnt * KS;
+    auto origin = [&](int i, int &x0, int &y0, int &z0) {
+        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+        x0 = (tile % ntx) * 8;
+        y0 = ((tile / ntx) % nty) * 16;
+        z0 = (tile / (ntx * nty)) * ZT;
+    };
+
+    if (w == 0 && lane == 0) {
+        // producer: unit u = (tile i, channel group ks) into stage u % S
+        int u = 0;
+        for (; u < units; ++u) {
+            const int s = u % S;
+            if (u >= S && !mbar_wait(&empty[s], ((u / S) - 1) & 1, a.status)) break;
+            const int i = u / KS, ks = u % KS;
+            int x0, y0, z0;
+            origin(i, x0, y0, z0);
+            mbar_expect_tx(&full[s], D::STAGE);
+#pragma unroll
+            for (int c = 0; c < D::CHS; ++c)
+                tma_load_4d(St + s * D::STAGE + c * D::PLANE, &tmap, 8 * (ks * D::CHS + c), x0 - 1, y0 - 1,
+                            z0 - 1, &full[s]);
+        }
+        // the copies of the last units land before the CTA can exit (already
+        // waited for by the MMA issuers unless they gave up)
+        for (int v = u - S > 0 ? u - S : 0; v < u; ++v) mbar_wait(&full[v % S], (v / S) & 1, a.status);
+    } else if (w >= 1 && w <= ISS && lane == 0) {
+        // MMA issuer k = w - 1: input slices zi = k (mod ISS) into set k
+        const int k = w - 1;
+        const uint64_t bd0 = smem_desc(smem_u32(Bs), D::BLEAD, 128);
+        int u = 0;
+        for (; u < units; ++u) {
+            const int s = u % S, i = u / KS, ks = u % KS, b = i & 1;
+            if (!mbar_wait(&full[s], (u / S) & 1, a.status)) break;
+            // accumulator buffer b is drained and zeroed (tile i - 2, or the start)
+            if (ks == 0 && !mbar_wait(&acce[b], (i >> 1) & 1, a.status)) break;
+            tc_fence_after();
+            const uint64_t ad0 = smem_desc(smem_u32(St + s * D::STAGE), D::PLANE, D::HX * 16);
+            const unsigned acc = tmem + (unsigned)((b * ISS + k) * D::SET);
+            for (int zi = k; zi < D::HZ; zi += ISS) {
+                // blocks blo .. bhi of B (dz = +1, 0, -1) feed output slices zi - 2 + blk inside the tile
+                const int blo = zi < 2 ? 2 - zi : 0, bhi = zi > ZT - 1 ? ZT + 1 - zi : 2, nb = bhi - blo + 1;
+                const unsigned idesc = idesc_bf16_f32(128, nb * NO);
+                const unsigned col = acc + (unsigned)((zi - 2 + blo) * NO);
+                for (int t9 = 0; t9 < 9; ++t9) {
+                    const uint64_t at = ad0 + (uint64_t)((zi * D::HY + t9 / 3) * D::HX + t9 % 3);
+                    const uint64_t bt = bd0 + (uint64_t)((t9 * D::CH + ks * D::CHS) * (D::BLEAD / 16) + blo * NO);
+#pragma unroll
+                    for (int cp = 0; cp < D::CHS; cp += 2)
+                        umma_bf16(col, at + (uint64_t)(cp * (D::PLANE / 16)),
+                                  bt + (uint64_t)(cp * (D::BLEAD / 16)), idesc, 1);
+                }
+            }
+            umma_commit(&empty[s]);
+            if (ks == KS - 1) umma_commit(&accf[b]);
+        }
+        // every MMA issued has completed before the tensor memory is freed
+        if (u > 0) mbar_wait(&empty[(u - 1) % S], ((u - 1) / S) & 1, a.status);
+    } else if (w >= 4) {
+        // epilogue: thread of row m = 32 (w % 4) + lane holds voxel (x0 + m % 8, y0 + m / 8)
+        const int q = w & 3, m = 32 * q + lane;
+        const unsigned lrow = (unsigned)(32 * q) << 16;
+        // zero both buffers, then hand them to the issuers
+        for (int c0 = 0; c0 < 2 * ISS * D::SET; c0 += 16) tmem_zero16(tmem + lrow + (unsigned)c0);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&acce[0]);
+            mbar_arrive(&acce[1]);
+        }
+        for (int i = 0; i < cnt; ++i) {
+            const int b = i & 1;
+            int x0, y0, z0;
+            origin(i, x0, y0, z0);
+            const int x = x0 + (m & 7), y = y0 + (m >> 3);
+            // the residual rows of this thread's voxel, all slices at once
+            // (independent loads in flight while the MMAs finish)
+            uint4 sk[MODE == MODE_FWD ? ZT * NO / 8 : 1];
+            if (MODE == MODE_FWD) {
+#pragma unroll
+                for (int zo = 0; zo < ZT; ++zo)
+#pragma unroll
+                    for (int c8 = 0; c8 < NO / 8; ++c8) {
+                        const bool in = a.skip && x < n && y < n && z0 + zo < n;
+                        sk[zo * (NO / 8) + c8] =
+                            in ? reinterpret_cast<const uint4 *>(a.skip + (((size_t)(z0 + zo) * n + y) * n + x) * NO)[c8]
+                               : make_uint4(0u, 0u, 0u, 0u);
+                    }
+            }
+            const bool got = mbar_wait(&accf[b], (i >> 1) & 1, a.status);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc_fence_after();
+            const unsigned acc = tmem + lrow + (unsigned)(b * ISS * D::SET);
+            if (MODE == MODE_DGRAD && a.up_adj) {
+                // the adjoint of the next layer's 2^3 nearest upsampling: the sum
+                // over the 8 children (x pairs: lanes ^ 1; y pairs: lanes ^ 8;
+                // z pairs: slices 2 zp, 2 zp + 1) written at half resolution by
+                // the lane of the even child (n is even: every in-grid parent
+                // has its 8 children in the grid)
+                const int hn = n / 2, px = x >> 1, py = y >> 1;
+#pragma unroll 1
+                for (int zp = 0; zp < ZT / 2; ++zp) {
+                    const int pz = (z0 >> 1) + zp;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < NO; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(acc + (unsigned)(2 * zp * NO + c0), v);
+#pragma unroll
+                        for (int k = 0; k < 2 * ISS; ++k) {
+                            if (k == 0) continue;
+                            float v2[16];
+                            tmem_ld16(acc + (unsigned)((k % ISS) * D::SET + (2 * zp + k / ISS) * NO + c0), v2);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) v[j] += v2[j];
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            v[j] += __shfl_xor_sync(0xffffffffu, v[j], 1);
+                            v[j] += __shfl_xor_sync(0xffffffffu, v[j], 8);
+                        }
+                        if ((lane & 9) == 0 && px < hn && py < hn && pz < hn) {
+                            float4 *op = reinterpret_cast<float4 *>(a.out + (((size_t)pz * hn + py) * hn + px) * NO + c0);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                op[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                        }
+                    }
+                }
+            } else
+#pragma unroll
+            for (int zo = 0; zo < ZT; ++zo) {
+                const int z = z0 + zo;
+#pragma unroll
+                for (int c0 = 0; c0 < NO; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(acc + (unsigned)(zo * NO + c0), v);
+#pragma unroll
+                    for (int k = 1; k < ISS; ++k) {
+                        float v2[16];
+                        tmem_ld16(acc + (unsigned)(k * D::SET + zo * NO + c0), v2);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] += v2[j];
+                    }
+                    if (x < n && y < n && z < n) {
+                        const size_t row = ((size_t)z * n + y) * n + x;
+                        if (MODE == MODE_FWD)
+                            store_fwd16(a.y + row * NO + c0, v, sbias + c0, sk[zo * (NO / 8) + c0 / 8],
+                                        sk[zo * (NO / 8) + c0 / 8 + 1]);
+                        else
+                            store_row16<MODE>(a, row, c0, v);
+                    }
+                }
+            }
+            for (int c0 = 0; c0 < ISS * D::SET; c0 += 16) tmem_zero16(acc + (unsigned)c0);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, D::NCOL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05 with the input channels and z offsets on M and
+// the y offsets and output channels on N.  For one x offset dx,
+//   D[(dz, ci)][(j, co)] = sum_p X[p + (dx, 0, dz)][ci] G[p + (0, j - 1, 0)][co]
+//                        = dW[tap (dz, 1 - j, dx)][ci][co]
+// (substituting q = p + (0, j - 1, 0); the terms the substitution moves out
+// of the tiles multiply a zero: X or G outside the grid).  A = the input
+// block, MN-major: a core matrix is 8 consecutive x voxels (K, 16 bytes
+// apart) x 8 channels; with the block stored as [chunk][z][y][x] planes of
+// 16 lines, the 16 M-adjacent core matrices of 4 chunks x 4 z offsets are one
+// plane (2,560 bytes) apart, so rows (chunk, dz + 1) cover four z offsets of
+// 32 channels (the fourth discarded: a quarter of the rows wasted instead of
+// seven eighths with the output channels on M); K-adjacent core matrices are
+// the next line.  B = the output gradient with a one-line y halo stored as
+// [z][y][chunk][x]: N-adjacent core matrices (8 channels) one chunk apart run
+// on into the next line, so N = 3 COG covers the three y offsets of a group
+// of COG output channels.  Per (tile of 8 x 16 x 2 voxels, dx, M half, z
+// slice, line pair) one MMA of 128 x 3 COG x 16.  A CTA owns a group of
+// COG output channels and a range of tiles (a split); its accumulators stay
+// in tensor memory over all of them and it writes its partial
+// [split][tap][ci][co] at the end (summed over splits in a fixed order).
+// Copies: the input block by TMA (one 4D box per 8-channel chunk: 10 x 16 x 4
+// voxels) from warp 0 lane 0, the output-gradient block by cp.async from
+// warps 4-5 (zero outside the grid).  The MMAs of one thread do not overlap
+// one another, so three threads issue them (lane 0 of warps 1-3), one per dx,
+// each into its own accumulators.  S stages.
+// ---------------------------------------------------------------------------
+template <int CI, int CO, int COG, int S>
+struct WzCfg {
+    static constexpr int ZT = 2, HX = 10, LINES = 16, CH = CI / 8, MH = CI / 32;
+    static constexpr unsigned XP = 16u * HX * LINES;          // one (chunk, z) plane of the input block
+    static constexpr unsigned XBYTES = (unsigned)CH * 4 * XP;  // chunks x 4 z slices
+    static constexpr unsigned LS = (unsigned)(COG / 8) * 128;  // output-gradient line pitch
+    static constexpr unsigned GBYTES = (unsigned)ZT * 18 * LS;
+    static constexpr unsigned STAGE = XBYTES + GBYTES;
+    static constexpr int NG = CO / COG, NB = 3 * COG, COLS = 3 * MH * NB;
+    static constexpr unsigned NCOL = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
+    static constexpr unsigned BAROFF = (unsigned)S * STAGE;
+    static constexpr size_t SMEM = 1024 + (size_t)BAROFF + 256;
+    static_assert(CI % 32 == 0 && CO % COG == 0 && COG % 16 == 0 && NB <= 256 && COLS <= 512, "shapes");
+    // the discarded rows of the last chunk read one plane past the input block
+    static_assert(STAGE % 128 == 0 && GBYTES >= XP, "layout");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+constexpr int WZ_THREADS = 256;
+
+template <int CI, int CO, int COG, int S>
+__global__ void __launch_bounds__(WZ_THREADS, 1) k_wgrad_dz(const __grid_constant__ CUtensorMap tmap,
+                                                            const ConvArgs a, int splits) {
+    using W = WzCfg<CI, CO, COG, S>;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(sm + W::BAROFF);
+    unsigned long long *empty = full + S, *done = full + 2 * S;
+    unsigned *tslot = reinterpret_cast<unsigned *>(full + 2 * S + 1);
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = (int)blockIdx.x % W::NG, split = (int)blockIdx.x / W::NG, co0 = grp * COG;
+    if (w == 0) {
+        tmem_alloc(tslot, W::NCOL);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1 + 64);  // the TMA's expect_tx arrival + one per cp.async thread
+            mbar_init(&empty[s], 3);      // one commit per issuer
+        }
+        mbar_init(done, 3);
+        fence_barrier_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tslot;
+
+    const int n = a.n;
+    const int ntx = (n + 7) / 8, nty = (n + 15) / 16, ntz = (n + W::ZT - 1) / W::ZT;
+    const long long ntiles = (long long)ntx * nty * ntz;
+    const long long tb = ntiles * split / splits, te = ntiles * (split + 1) / splits;
+    const int cnt = (int)(te - tb);
+    auto origin = [&](int i, int &x0, int &y0, int &z0) {
+        const long long tile = tb + i;
+        x0 = (int)(tile % ntx) * 8;
+        y0 = (int)((tile / ntx) % nty) * 16;
+        z0 = (int)(tile / ((long long)ntx * nty)) * W::ZT;
+    };
+
+    if (w == 0 && lane == 0) {
+        // input block of unit u by TMA: chunk c at (4 c) planes
+        int u = 0;
+        for (; u < cnt; ++u) {
+            const int s = u % S;
+            if (u >= S && !mbar_wait(&empty[s], ((u / S) - 1) & 1, a.status)) break;
+            int x0, y0, z0;
+            origin(u, x0, y0, z0);
+            unsigned char *X = sm + s * W::STAGE;
+            mbar_expect_tx(&full[s], W::XBYTES);
+#pragma unroll
+            for (int c = 0; c < W::CH; ++c) tma_load_4d(X + c * 4 * W::XP, &tmap, 8 * c, x0 - 1, y0, z0 - 1, &full[s]);
+        }
+        for (int v = u - S > 0 ? u - S : 0; v < u; ++v) mbar_wait(&full[v % S], (v / S) & 1, a.status);
+    } else if (w == 4 || w == 5) {
+        // output-gradient block of unit u (lines y0 - 1 .. y0 + 16, the group's channels)
+        const int t = threadIdx.x - 128;
+        constexpr int CC = COG / 8, TOT = W::ZT * 18 * CC * 8;
+        for (int u = 0; u < cnt; ++u) {
+            const int s = u % S;
+            if (u >= S && !mbar_wait(&empty[s], ((u / S) - 1) & 1, a.status)) break;
+            int x0, y0, z0;
+            origin(u, x0, y0, z0);
+            unsigned char *G = sm + s * W::STAGE + W::XBYTES;
+            for (int e = t; e < TOT; e += 64) {
+                const int xv = e % 8, cc = (e / 8) % CC, ly = (e / (8 * CC)) % 18, zs = e / (8 * CC * 18);
+                const int qx = x0 + xv, qy = y0 + ly - 1, qz = z0 + zs;
+                const bool in = qx < n && qy >= 0 && qy < n && qz < n;
+                const bf16 *src = in ? a.g + ((size_t)(qz * n + qy) * n + qx) * CO + co0 + 8 * cc : a.g;
+                cp_async16(G + ((zs * 18 + ly) * CC + cc) * 128 + xv * 16, src, in ? 16u : 0u);
+            }
+            cp_async_mbar_arrive(&full[s]);
+        }
+        cp_async_wait<0>();
+    } else if (w >= 1 && w <= 3 && lane == 0) {
+        // MMA issuer of x offset dxi = w - 1 (its accumulators: MH halves)
+        const int dxi = w - 1;
+        constexpr unsigned IDESC = idesc_bf16_f32(128, W::NB) | (1u << 15) | (1u << 16);  // A, B MN-major
+        for (int u = 0; u < cnt; ++u) {
+            const int s = u % S;
+            if (!mbar_wait(&full[s], (u / S) & 1, a.status)) break;
+            fence_async_smem();  // the cp.async writes, for the tensor core's reads
+            tc_fence_after();
+            const unsigned xs = smem_u32(sm + s * W::STAGE), gs = xs + W::XBYTES;
+#pragma unroll 1
+            for (int zs = 0; zs < W::ZT; ++zs)
+#pragma unroll 2
+                for (int lp = 0; lp < 8; ++lp) {
+                    const uint64_t bd = smem_desc(gs + (unsigned)(zs * 18 + 2 * lp) * W::LS, W::LS, 128);
+#pragma unroll
+                    for (int h = 0; h < W::MH; ++h) {
+                        const uint64_t ad = smem_desc(
+                            xs + (unsigned)(h * 16 + zs) * W::XP + (unsigned)(2 * lp * 160 + dxi * 16), 160, W::XP);
+                        umma_bf16(tmem + (unsigned)((dxi * W::MH + h) * W::NB), ad, bd, IDESC, (u | zs | lp) != 0);
+                    }
+                }
+            umma_commit(&empty[s]);
+        }
+        // arrives once every MMA this thread issued has completed
+        umma_commit(done);
+    }
+    if (w >= 4) {
+        const bool got = mbar_wait(done, 0, a.status);
+        __syncwarp();
+        tc_fence_after();
+        // row m = (chunk c, dz + 1) of an M half, channel ci = 8 c + m % 8
+        const int q = w & 3, m = 32 * q + lane, mg = m >> 3, dzp = mg & 3;
+        float *out = a.out + (size_t)split * 27 * CI * CO;
+        for (int dxi = 0; dxi < 3; ++dxi)
+            for (int h = 0; h < W::MH; ++h) {
+                const int ci = 8 * (h * 4 + (mg >> 2)) + (m & 7);
+                for (int j = 0; j < 3; ++j)
+#pragma unroll 1
+                    for (int c16 = 0; c16 < COG; c16 += 16) {
+                        float v[16];
+                        tmem_ld16(tmem + ((unsigned)(32 * q) << 16) +
+                                      (unsigned)((dxi * W::MH + h) * W::NB + j * COG + c16),
+                                  v);
+                        if (dzp == 3 || !got) continue;
+                        const int tap = dzp * 9 + (2 - j) * 3 + dxi;
+                        float *o = out + ((size_t)tap * CI + ci) * CO + co0 + c16;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) o[k] = cnt > 0 ? v[k] : 0.f;  // no tiles: no accumulator
+                    }
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, W::NCOL);
+    }
+}
+
+// the weights [27][ci][co] as k_conv_dz's B: wt[((t9 CH + kc) 3 NO + r) 8 + k]
+// for (dy, dx) = t9, chunk kc of the C input channels, row r = blk NO + o
+// (input offset dz = 1 - blk) and the k-th channel of the chunk:
+//   forward        W[tap (dz, dy, dx)][ci 8 kc + k][co o]
+//   data gradient  W[tap (-dz, -dy, -dx)][ci o][co 8 kc + k]  (input offset = -tap)
+// grid.y: 0 forward, 1 data gradient
+__global__ void k_wpack_dz(int ci, int co, const bf16 *__restrict__ w, bf16 *__restrict__ wf,
+                           bf16 *__restrict__ wd) {
+    const int mode = blockIdx.y;
+    const int C = mode == 0 ? ci : co, NO = mode == 0 ? co : ci, CH = C / 8;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 27 * C * NO) return;
+    const int k = i % 8, r = (i / 8) % (3 * NO), tk = i / (24 * NO);
+    const int kc = tk % CH, t9 = tk / CH;
+    const int dz = 1 - r / NO, o = r % NO, dy = t9 / 3 - 1, dx = t9 % 3 - 1, c = 8 * kc + k;
+    if (mode == 0) {
+        const int tap = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+        wf[i] = w[((size_t)tap * ci + c) * co + o];
+    } else {
+        const int tap = (1 - dz) * 9 + (1 - dy) * 3 + (1 - dx);
+        wd[i] = w[((size_t)tap * ci + o) * co + c];
+    }
+}
+
 // the weights [27][ci][co] as the B operand of the tcgen05 GEMMs, K-major:
 //   forward       wt[co][tap ci + ch] = w[tap][ch][co]
 //   data gradient wt[ci][tap co + ch] = w[tap][ci][ch]
@@ -847,78 +1353,185 @@ __global__ void k_wpack(int mode, int ci, int co, const bf16 *__restrict__ w, bf
 // ---------------------------------------------------------------------------
 // CUDA-core layers and elementwise kernels
 // ---------------------------------------------------------------------------
-// first layer: 1 -> 16 channels, input FP32
-__global__ void k_conv1_fwd(int n, const float *__restrict__ x, const float *__restrict__ w,
-                            const float *__restrict__ b, bf16 *__restrict__ y) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n3 = n * n * n;
-    if (p >= n3) return;
-    const int px = p % n, py = (p / n) % n, pz = p / (n * n);
-    float acc[16];
+// 8 / 16 consecutive BF16 values (16-byte aligned) to and from FP32
+__device__ __forceinline__ void load8_bf16(const bf16 *p, float *v) {
+    const uint4 u = *reinterpret_cast<const uint4 *>(p);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = b[c];
-    for (int tap = 0; tap < 27; ++tap) {
-        int dx, dy, dz;
-        tap_offset(tap, dx, dy, dz);
-        const int qx = px + dx, qy = py + dy, qz = pz + dz;
-        if (qx < 0 || qx >= n || qy < 0 || qy >= n || qz < 0 || qz >= n) continue;
-        const float v = x[(qz * n + qy) * n + qx];
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h;
+        memcpy(&h, &w[i], 4);
+        const float2 f = __bfloat1622float2(h);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void store8_bf16(bf16 *p, const float *v) {
+    uint32_t w[4];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = fmaf(v, w[tap * 16 + c], acc[c]);
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        memcpy(&w[i], &h, 4);
+    }
+    *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ void load16_bf16(const bf16 *p, float *v) {
+    load8_bf16(p, v);
+    load8_bf16(p + 8, v + 8);
+}
+__device__ __forceinline__ void store16_bf16(bf16 *p, const float *v) {
+    store8_bf16(p, v);
+    store8_bf16(p + 8, v + 8);
+}
+
+// first layer: 1 -> 16 channels, input FP32.  A thread computes 4
+// consecutive x voxels; the block's weights and biases sit in shared memory
+// (read as float4 broadcasts).  Per (dz, dy) the six inputs x0 - 1 .. x0 + 4
+// of the row are loaded once and feed the three dx taps: 6 loads + 12
+// float4 weight reads per 192 FMAs.
+constexpr int C1_VX = 4;
+__global__ void __launch_bounds__(128) k_conv1_fwd(int n, const float *__restrict__ x, const float *__restrict__ w,
+                                                   const float *__restrict__ b, bf16 *__restrict__ y) {
+    __shared__ __align__(16) float wsm[27 * 16 + 16];
+    for (int e = threadIdx.x; e < 27 * 16 + 16; e += blockDim.x) wsm[e] = e < 27 * 16 ? w[e] : b[e - 27 * 16];
+    __syncthreads();
+    const int nxg = (n + C1_VX - 1) / C1_VX;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nxg * n * n) return;
+    const int px0 = (int)(t % nxg) * C1_VX, py = (int)((t / nxg) % n), pz = (int)(t / ((long long)nxg * n));
+    float acc[C1_VX][16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        const float bc = wsm[27 * 16 + c];
+#pragma unroll
+        for (int i = 0; i < C1_VX; ++i) acc[i][c] = bc;
     }
 #pragma unroll
-    for (int c = 0; c < 16; ++c) y[(size_t)p * 16 + c] = __float2bfloat16(fmaxf(acc[c], 0.f));
+    for (int r = 0; r < 9; ++r) {  // (dz, dy) = (r / 3 - 1, r % 3 - 1)
+        const int qy = py + r % 3 - 1, qz = pz + r / 3 - 1;
+        const bool rowok = qy >= 0 && qy < n && qz >= 0 && qz < n;
+        const float *row = x + ((size_t)(rowok ? qz : 0) * n + (rowok ? qy : 0)) * n;
+        float xv[C1_VX + 2];
+#pragma unroll
+        for (int i = 0; i < C1_VX + 2; ++i) {
+            const int qx = px0 + i - 1;
+            xv[i] = (rowok && qx >= 0 && qx < n) ? row[qx] : 0.f;
+        }
+#pragma unroll
+        for (int dxi = 0; dxi < 3; ++dxi) {
+            const float4 *wt = reinterpret_cast<const float4 *>(wsm + (r * 3 + dxi) * 16);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 wk = wt[k];
+#pragma unroll
+                for (int i = 0; i < C1_VX; ++i) {
+                    const float v = xv[i + dxi];
+                    acc[i][4 * k] = fmaf(v, wk.x, acc[i][4 * k]);
+                    acc[i][4 * k + 1] = fmaf(v, wk.y, acc[i][4 * k + 1]);
+                    acc[i][4 * k + 2] = fmaf(v, wk.z, acc[i][4 * k + 2]);
+                    acc[i][4 * k + 3] = fmaf(v, wk.w, acc[i][4 * k + 3]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < C1_VX; ++i) {
+        if (px0 + i >= n) break;
+        float o[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) o[c] = fmaxf(acc[i][c], 0.f);
+        store16_bf16(y + (((size_t)pz * n + py) * n + px0 + i) * 16, o);
+    }
 }
 
 // weight gradient of the first layer: a block walks 8^3 voxel tiles (tile
 // b, b + gridDim.x, ...) with the input block (10^3, zero outside) and the
-// tile's gz [512][16] in shared memory; thread i < 432 owns (tap, c) = (i / 16,
-// i % 16), threads 432 .. 447 the bias sums; one partial per block, summed
-// in a fixed order afterwards
+// tile's gz [512][16] in shared memory, double-buffered (the next tile's
+// copies run during this tile's sums).  Thread i < 432 owns tap i % 27 and
+// the voxels v = i / 27 (mod 16) of each tile, for all 16 channels: the
+// lanes of a warp share (at most two) voxels, so their gz reads are
+// broadcasts, and one input plus four float4 reads feed 16 FMAs.  Threads
+// 432 .. 447 sum gz per channel (the bias gradient).  At the end the 16
+// voxel groups are summed in a fixed order: one partial [27 x 16 + 16] per
+// block (tap-major, then channel), summed over blocks afterwards.
 constexpr int C1_THREADS = 448;
+constexpr size_t C1_SMEM = sizeof(float) * 2 * (1000 + 512 * 16);  // dynamic: two (input, gz) buffers
 __global__ void __launch_bounds__(C1_THREADS) k_conv1_wgrad(int n, const float *__restrict__ x,
                                                             const float *__restrict__ gz,
                                                             float *__restrict__ part) {
-    __shared__ float xs[10 * 10 * 10];
-    __shared__ __align__(16) float gs[512 * 16];
+    extern __shared__ __align__(16) float c1sm[];
+    float(*xs)[1000] = reinterpret_cast<float(*)[1000]>(c1sm);               // [2][1000]
+    float(*gs)[512 * 16] = reinterpret_cast<float(*)[512 * 16]>(c1sm + 2000);  // [2][8192], 16-byte aligned
     const int nt = (n + 7) / 8, ntiles = nt * nt * nt;
     const int i = threadIdx.x;
-    int tap = 0, c = 0, dx = 0, dy = 0, dz = 0;
-    if (i < 432) {
-        tap = i / 16;
-        c = i % 16;
-        tap_offset(tap, dx, dy, dz);
-    } else {
-        c = i - 432;
-    }
-    float acc = 0.f;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int tap = i % 27, g = i / 27;  // for i < 432; i >= 432: bias channel i - 432
+    int dx = 0, dy = 0, dz = 0;
+    if (i < 432) tap_offset(tap, dx, dy, dz);
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+    auto load = [&](int t, int buf) {
         const int x0 = (t % nt) * 8, y0 = ((t / nt) % nt) * 8, z0 = (t / (nt * nt)) * 8;
-        __syncthreads();
         for (int e = i; e < 1000; e += C1_THREADS) {
             const int qx = x0 + e % 10 - 1, qy = y0 + (e / 10) % 10 - 1, qz = z0 + e / 100 - 1;
-            xs[e] = (qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n) ? x[((size_t)qz * n + qy) * n + qx]
-                                                                                   : 0.f;
+            const bool in = qx >= 0 && qx < n && qy >= 0 && qy < n && qz >= 0 && qz < n;
+            cp_async4(&xs[buf][e], in ? x + ((size_t)qz * n + qy) * n + qx : x, in ? 4u : 0u);
         }
-        for (int e = i; e < 512 * 4; e += C1_THREADS) {  // float4 of gz (zero outside)
+        for (int e = i; e < 512 * 4; e += C1_THREADS) {  // 16-byte pieces of gz (zero outside)
             const int v = e >> 2, q = e & 3;
             const int px = x0 + (v & 7), py = y0 + ((v >> 3) & 7), pz = z0 + (v >> 6);
-            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (px < n && py < n && pz < n)
-                g = reinterpret_cast<const float4 *>(gz + (((size_t)pz * n + py) * n + px) * 16)[q];
-            reinterpret_cast<float4 *>(gs)[e] = g;
+            const bool in = px < n && py < n && pz < n;
+            cp_async16(&gs[buf][4 * e], in ? gz + (((size_t)pz * n + py) * n + px) * 16 + 4 * q : gz, in ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+    int buf = 0;
+    if ((int)blockIdx.x < ntiles) load(blockIdx.x, 0);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+        if (t + (int)gridDim.x < ntiles) {
+            load(t + gridDim.x, buf ^ 1);
+            cp_async_wait<1>();  // this tile's copies have landed
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
         if (i < 432) {
-            for (int v = 0; v < 512; ++v) {
+            const float *xb = xs[buf];
+#pragma unroll 4
+            for (int v = g; v < 512; v += 16) {
                 const int vx = v & 7, vy = (v >> 3) & 7, vz = v >> 6;
-                acc = fmaf(xs[((vz + 1 + dz) * 10 + vy + 1 + dy) * 10 + vx + 1 + dx], gs[v * 16 + c], acc);
+                const float xv = xb[((vz + 1 + dz) * 10 + vy + 1 + dy) * 10 + vx + 1 + dx];
+                const float4 *gp = reinterpret_cast<const float4 *>(gs[buf] + v * 16);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float4 gk = gp[k];
+                    acc[4 * k] = fmaf(xv, gk.x, acc[4 * k]);
+                    acc[4 * k + 1] = fmaf(xv, gk.y, acc[4 * k + 1]);
+                    acc[4 * k + 2] = fmaf(xv, gk.z, acc[4 * k + 2]);
+                    acc[4 * k + 3] = fmaf(xv, gk.w, acc[4 * k + 3]);
+                }
             }
         } else {
-            for (int v = 0; v < 512; ++v) acc += gs[v * 16 + c];
+            const int c = i - 432;
+#pragma unroll 8
+            for (int v = 0; v < 512; ++v) acc[0] += gs[buf][v * 16 + c];
         }
+        __syncthreads();  // buffer buf is refilled two tiles on
     }
-    part[(size_t)blockIdx.x * (27 * 16 + 16) + i] = acc;
+    // per (tap, group) sums through shared memory, then the 16 groups in order
+    float *red = gs[0];  // 432 x 16 floats fit in the 8,192 of a gz buffer
+    if (i < 432) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) red[(tap * 16 + g) * 16 + c] = acc[c];
+    }
+    __syncthreads();
+    float s = acc[0];  // the bias threads' sums
+    if (i < 432) {
+        const int tp = i / 16, c = i % 16;
+        s = 0.f;
+        for (int k = 0; k < 16; ++k) s += red[(tp * 16 + k) * 16 + c];
+    }
+    part[(size_t)blockIdx.x * (27 * 16 + 16) + i] = s;
 }
 
 // head: 1x1 conv 16 -> 2, FP32 output [n^3][2]
@@ -926,20 +1539,21 @@ __global__ void k_head_fwd(int n3, const bf16 *__restrict__ a, const float *__re
                            const float *__restrict__ b, float *__restrict__ y) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n3) return;
+    float v[16];
+    load16_bf16(a + (size_t)p * 16, v);
     float o0 = b[0], o1 = b[1];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-        const float v = __bfloat162float(a[(size_t)p * 16 + c]);
-        o0 = fmaf(v, w[c * 2 + 0], o0);
-        o1 = fmaf(v, w[c * 2 + 1], o1);
+        o0 = fmaf(v[c], w[c * 2 + 0], o0);
+        o1 = fmaf(v[c], w[c * 2 + 1], o1);
     }
-    y[(size_t)p * 2] = o0;
-    y[(size_t)p * 2 + 1] = o1;
+    reinterpret_cast<float2 *>(y)[p] = make_float2(o0, o1);
 }
 
-// head backward: da = gy W^T (FP32 [n^3][16]); partial dW, db per block
+// head backward with the ReLU of the layer below: gz = (a > 0) gy W^T (BF16
+// and FP32 [n^3][16]); partial dW, db per block
 __global__ void k_head_bwd(int n3, const bf16 *__restrict__ a, const float *__restrict__ w,
-                           const float *__restrict__ gy, float *__restrict__ da,
+                           const float *__restrict__ gy, bf16 *__restrict__ gz_bf, float *__restrict__ gz_f,
                            float *__restrict__ part) {
     __shared__ float s[34 * 8];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;  // 8 warps
@@ -947,16 +1561,21 @@ __global__ void k_head_bwd(int n3, const bf16 *__restrict__ a, const float *__re
 #pragma unroll
     for (int i = 0; i < 34; ++i) loc[i] = 0.f;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += gridDim.x * blockDim.x) {
-        const float g0 = gy[(size_t)p * 2], g1 = gy[(size_t)p * 2 + 1];
+        const float2 g = reinterpret_cast<const float2 *>(gy)[p];
+        float v[16], gz[16];
+        load16_bf16(a + (size_t)p * 16, v);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            const float v = __bfloat162float(a[(size_t)p * 16 + c]);
-            da[(size_t)p * 16 + c] = g0 * w[c * 2] + g1 * w[c * 2 + 1];
-            loc[c * 2] = fmaf(v, g0, loc[c * 2]);
-            loc[c * 2 + 1] = fmaf(v, g1, loc[c * 2 + 1]);
+            gz[c] = v[c] > 0.f ? g.x * w[c * 2] + g.y * w[c * 2 + 1] : 0.f;
+            loc[c * 2] = fmaf(v[c], g.x, loc[c * 2]);
+            loc[c * 2 + 1] = fmaf(v[c], g.y, loc[c * 2 + 1]);
         }
-        loc[32] += g0;
-        loc[33] += g1;
+        loc[32] += g.x;
+        loc[33] += g.y;
+        store16_bf16(gz_bf + (size_t)p * 16, gz);
+        float4 *fp = reinterpret_cast<float4 *>(gz_f + (size_t)p * 16);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) fp[i] = make_float4(gz[4 * i], gz[4 * i + 1], gz[4 * i + 2], gz[4 * i + 3]);
     }
 #pragma unroll
     for (int i = 0; i < 34; ++i) {
@@ -973,34 +1592,41 @@ __global__ void k_head_bwd(int n3, const bf16 *__restrict__ a, const float *__re
     }
 }
 
-// 2^3 average pool, channels-last: [(2m)^3][c] -> [m^3][c]
+// 2^3 average pool, channels-last: [(2m)^3][c] -> [m^3][c]; a thread per 8 channels
 __global__ void k_pool(int m, int c, const bf16 *__restrict__ in, bf16 *__restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)m * m * m * c;
+    const int c8 = c / 8;
+    const long long tot = (long long)m * m * m * c8;
     if (i >= tot) return;
-    const int ch = (int)(i % c);
-    const long long p = i / c;
+    const int ch = (int)(i % c8) * 8;
+    const long long p = i / c8;
     const int x = (int)(p % m), y = (int)((p / m) % m), z = (int)(p / ((long long)m * m));
     const int n = 2 * m;
-    float s = 0.f;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const int qx = 2 * x + (d & 1), qy = 2 * y + ((d >> 1) & 1), qz = 2 * z + (d >> 2);
-        s += __bfloat162float(in[((size_t)(qz * n + qy) * n + qx) * c + ch]);
+        float v[8];
+        load8_bf16(in + ((size_t)(qz * n + qy) * n + qx) * c + ch, v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += v[k];
     }
-    out[i] = __float2bfloat16(0.125f * s);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] *= 0.125f;
+    store8_bf16(out + (size_t)p * c + ch, s);
 }
 
-// 2^3 nearest upsample: [m^3][c] -> [(2m)^3][c]
+// 2^3 nearest upsample: [m^3][c] -> [(2m)^3][c]; a thread per 8 channels
 __global__ void k_up(int m, int c, const bf16 *__restrict__ in, bf16 *__restrict__ out) {
-    const int n = 2 * m;
+    const int n = 2 * m, c8 = c / 8;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)n * n * n * c;
+    const long long tot = (long long)n * n * n * c8;
     if (i >= tot) return;
-    const int ch = (int)(i % c);
-    const long long p = i / c;
+    const int ch8 = (int)(i % c8);
+    const long long p = i / c8;
     const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((long long)n * n));
-    out[i] = in[((size_t)((z / 2) * m + y / 2) * m + x / 2) * c + ch];
+    reinterpret_cast<uint4 *>(out)[i] =
+        reinterpret_cast<const uint4 *>(in)[((size_t)((z / 2) * m + y / 2) * m + x / 2) * c8 + ch8];
 }
 
 // gradient through relu(z) = a (a > 0) of the pre-activation, in BF16 for the
@@ -1008,61 +1634,106 @@ __global__ void k_up(int m, int c, const bf16 *__restrict__ in, bf16 *__restrict
 //   gz = (a > 0) * (g1 + up^T(g2) + pool^T(g3) + g4)  (terms optional)
 // g2: FP32 at twice the resolution (nearest-upsample adjoint: sum of the 8
 // children); g3: FP32 at half the resolution (average-pool adjoint: 1/8).
+// A thread per 4 channels.
 __global__ void k_relu_grad(int n, int c, const bf16 *__restrict__ a, const float *__restrict__ g1,
                             const float *__restrict__ g2, const float *__restrict__ g3,
                             const float *__restrict__ g4, bf16 *__restrict__ gz_bf,
                             float *__restrict__ gz_f) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)n * n * n * c;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // a float4 of channels
+    const int c4 = c / 4;
+    const long long tot = (long long)n * n * n * c4;
     if (i >= tot) return;
-    const int ch = (int)(i % c);
-    const long long p = i / c;
+    const int ch = (int)(i % c4) * 4;
+    const long long p = i / c4;
     const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((long long)n * n));
-    float s = 0.f;
-    if (g1) s += g1[i];
-    if (g4) s += g4[i];
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto add = [&](float4 v, float k) {
+        s.x = fmaf(k, v.x, s.x);
+        s.y = fmaf(k, v.y, s.y);
+        s.z = fmaf(k, v.z, s.z);
+        s.w = fmaf(k, v.w, s.w);
+    };
+    if (g1) add(reinterpret_cast<const float4 *>(g1)[i], 1.f);
+    if (g4) add(reinterpret_cast<const float4 *>(g4)[i], 1.f);
     if (g2) {
         const int N2 = 2 * n;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             const int qx = 2 * x + (d & 1), qy = 2 * y + ((d >> 1) & 1), qz = 2 * z + (d >> 2);
-            s += g2[((size_t)(qz * N2 + qy) * N2 + qx) * c + ch];
+            add(*reinterpret_cast<const float4 *>(g2 + ((size_t)(qz * N2 + qy) * N2 + qx) * c + ch), 1.f);
         }
     }
     if (g3) {
         const int h = n / 2;
-        s += 0.125f * g3[((size_t)((z / 2) * h + y / 2) * h + x / 2) * c + ch];
+        add(*reinterpret_cast<const float4 *>(g3 + ((size_t)((z / 2) * h + y / 2) * h + x / 2) * c + ch), 0.125f);
     }
-    const float gz = __bfloat162float(a[i]) > 0.f ? s : 0.f;
-    if (gz_bf) gz_bf[i] = __float2bfloat16(gz);
-    if (gz_f) gz_f[i] = gz;
+    const uint2 av = reinterpret_cast<const uint2 *>(a)[i];
+    __nv_bfloat162 a01, a23;
+    memcpy(&a01, &av.x, 4);
+    memcpy(&a23, &av.y, 4);
+    const float2 f01 = __bfloat1622float2(a01), f23 = __bfloat1622float2(a23);
+    const float4 gz = make_float4(f01.x > 0.f ? s.x : 0.f, f01.y > 0.f ? s.y : 0.f, f23.x > 0.f ? s.z : 0.f,
+                                  f23.y > 0.f ? s.w : 0.f);
+    if (gz_bf) {
+        const __nv_bfloat162 b01 = __floats2bfloat162_rn(gz.x, gz.y), b23 = __floats2bfloat162_rn(gz.z, gz.w);
+        uint2 o;
+        memcpy(&o.x, &b01, 4);
+        memcpy(&o.y, &b23, 4);
+        reinterpret_cast<uint2 *>(gz_bf)[i] = o;
+    }
+    if (gz_f) reinterpret_cast<float4 *>(gz_f)[i] = gz;
 }
 
-// sum over splits (fixed order) and, for biases, over the output positions
-__global__ void k_reduce_parts(int splits, int len, const float *__restrict__ part,
-                               float *__restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= len) return;
+// out[i] = sum over k of part[k][i] (splits, blocks), in a fixed order: a
+// block of 32 x 8 threads owns 32 consecutive i; warp j sums k = j, j + 8,
+// ..., then the eight warp sums are added in order
+__global__ void __launch_bounds__(256) k_reduce_parts(int splits, int len, const float *__restrict__ part,
+                                                      float *__restrict__ out) {
+    __shared__ float sm[8][32];
+    const int i = blockIdx.x * 32 + threadIdx.x, j = threadIdx.y;
     float s = 0.f;
-    for (int k = 0; k < splits; ++k) s += part[(size_t)k * len + i];
-    out[i] = s;
+    if (i < len)
+        for (int k = j; k < splits; k += 8) s += part[(size_t)k * len + i];
+    sm[j][threadIdx.x] = s;
+    __syncthreads();
+    if (j == 0 && i < len) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += sm[k][threadIdx.x];
+        out[i] = t;
+    }
 }
 
 // bias gradient: sum of gz [P][c] over P (block partials, fixed order)
-__global__ void k_bias_part(long long P, int c, const float *__restrict__ gz, float *__restrict__ part) {
-    __shared__ float s[256];
-    const int ch = blockIdx.y;
-    float acc = 0.f;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
-         p += (long long)gridDim.x * blockDim.x)
-        acc += gz[p * c + ch];
+// per-block partial sums over the voxels of gz [P][c] (c a multiple of 4, at
+// most 64; 256 threads): a thread reads float4s of one channel group (the
+// grid stride is a multiple of c / 4), then the block sums its threads per
+// channel in a fixed order; part[block][c]
+__global__ void __launch_bounds__(256) k_bias_part(long long P, int c, const float *__restrict__ gz,
+                                                   float *__restrict__ part) {
+    __shared__ float4 s[256];
+    const int c4 = c / 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long tot = P * c4;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < tot; e += (long long)gridDim.x * 256) {
+        const float4 v = reinterpret_cast<const float4 *>(gz)[e];
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+    }
     s[threadIdx.x] = acc;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-        __syncthreads();
+    if (threadIdx.x < c4) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = threadIdx.x; k < 256; k += c4) {
+            t.x += s[k].x;
+            t.y += s[k].y;
+            t.z += s[k].z;
+            t.w += s[k].w;
+        }
+        reinterpret_cast<float4 *>(part + (size_t)blockIdx.x * c)[threadIdx.x] = t;
     }
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * gridDim.y + ch] = s[0];
 }
 
 __global__ void k_to_bf16(long long n, const float *__restrict__ in, bf16 *__restrict__ out) {
@@ -1262,6 +1933,8 @@ struct Layer {
 };
 constexpr Layer L[6] = {{1, 16, 27}, {16, 32, 27}, {32, 64, 27}, {64, 32, 27}, {32, 16, 27}, {16, 2, 1}};
 constexpr int C1_BLOCKS = 1024;  // most blocks (partials) of the first layer's weight gradient
+constexpr int BIAS_BLOCKS = 592;  // blocks (partials) of a bias gradient: 4 per SM of a 148-SM device
+constexpr int HEAD_BLOCKS = 592;  // blocks (partials) of the head's backward
 
 inline size_t w_off(int l) {
     size_t o = 0;
@@ -1274,9 +1947,11 @@ inline size_t n_params() { return w_off(6); }
 struct WS {
     size_t a1, p1, a2, p2, a3, u2, a4, u1, a5;  // BF16 activations
     size_t wbf;                                  // BF16 copy of every parameter
-    size_t ga5f, gz5b, gz5f, gu1f, gz4b, gz4f, gu2f, gz3b, gz3f, gp2f, gz2b, gz2f, gp1f, gz1f;
+    size_t gz5b, gz5f, gu1f, gz4b, gz4f, gu2f, gz3b, gz3f, gp2f, gz2b, gz2f, gp1f, gz1f;
     size_t part, bpart, lpart;
+    size_t part_n;  // floats of the weight-gradient partial buffer
     size_t wpk;     // tcgen05 B operands: per layer 1..4, forward then data gradient
+    size_t wdz;     // the same for k_conv_dz (three z offsets side by side), same offsets
     size_t status;  // device status word
     size_t total;
 };
@@ -1307,7 +1982,6 @@ inline WS layout(int n) {
     w.u1 = take(2 * n3 * 32);
     w.a5 = take(2 * n3 * 16);
     w.wbf = take(2 * n_params());
-    w.ga5f = take(4 * n3 * 16);
     w.gz5b = take(2 * n3 * 16);
     w.gz5f = take(4 * n3 * 16);
     w.gu1f = take(4 * n3 * 32);
@@ -1332,11 +2006,13 @@ inline WS layout(int n) {
     }
     const size_t c1 = (size_t)C1_BLOCKS * (27 * 16 + 16);
     pmax = c1 > pmax ? c1 : pmax;
-    pmax = (size_t)256 * 34 > pmax ? (size_t)256 * 34 : pmax;
+    pmax = (size_t)HEAD_BLOCKS * 34 > pmax ? (size_t)HEAD_BLOCKS * 34 : pmax;
     w.part = take(4 * pmax);
-    w.bpart = take(4 * 64 * 64);
+    w.part_n = pmax;
+    w.bpart = take(4 * (size_t)BIAS_BLOCKS * 64);
     w.lpart = take(4 * 1024);
     w.wpk = take(2 * wpk_off(5, 0));
+    w.wdz = take(2 * wpk_off(5, 0));
     w.status = take(4);
     w.total = o;
     return w;
@@ -1434,6 +2110,71 @@ static bool halo2(const ConvArgs &a, cudaStream_t st) {
     return true;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if the driver does not provide it
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// tensor map of BF16 activations [n][n][n][c] (channels fastest) read in
+// boxes of 8 channels x bx x by x bz voxels, zero outside the grid
+static bool act_tmap(CUtensorMap *tm, const bf16 *x, int n, int c, int bx, int by, int bz) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || (uintptr_t)x % 16 != 0 || c % 8 != 0) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)c * 2, (cuuint64_t)n * c * 2, (cuuint64_t)n * n * c * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(x), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// persistent k_conv_dz launch, one CTA per SM
+template <int MODE, int C, int NO, int ZT, int KS, int S, int ISS>
+static bool dz(const ConvArgs &a, cudaStream_t st) {
+    using D = DzCfg<C, NO, ZT, KS, S, ISS>;
+    static int sms = 0, attr = 0;  // attr: 1 set, -1 refused
+    if (attr == 0) {
+        int dev = 0;
+        attr = (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                cudaFuncSetAttribute(k_conv_dz<MODE, C, NO, ZT, KS, S, ISS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)D::SMEM) == cudaSuccess)
+                   ? 1
+                   : -1;
+        if (attr < 0) (void)cudaGetLastError();
+    }
+    if (attr < 0) return false;
+    CUtensorMap tm;
+    if (!act_tmap(&tm, a.x, a.n, C, D::HX, D::HY, D::HZ)) return false;
+    const int n = a.n;
+    const long long tiles = (long long)((n + 7) / 8) * ((n + 15) / 16) * ((n + ZT - 1) / ZT);
+    k_conv_dz<MODE, C, NO, ZT, KS, S, ISS><<<(unsigned)(tiles < sms ? tiles : sms), DZ_THREADS, D::SMEM, st>>>(tm, a);
+    counted(1);
+    return true;
+}
+
+template <int MODE>
+static bool dz_cn(int C, int N, const ConvArgs &a, cudaStream_t st) {
+    if (C == 16 && N == 32) return dz<MODE, 16, 32, 4, 1, 4, 2>(a, st);
+    if (C == 32 && N == 64) return dz<MODE, 32, 64, 2, 2, 4, 2>(a, st);
+    if (C == 64 && N == 32) return dz<MODE, 64, 32, 4, 4, 3, 2>(a, st);
+    if (C == 32 && N == 16) return dz<MODE, 32, 16, 8, 2, 3, 2>(a, st);
+    return false;
+}
+
 template <int MODE>
 static bool halo_cn(int C, int N, const ConvArgs &a, cudaStream_t st) {
     if (C == 16 && N == 32) return halo2<MODE, 16, 32, 4>(a, st);
@@ -1472,6 +2213,43 @@ static int wgrad_halo(const ConvArgs &a, int max_splits, cudaStream_t st) {
     return (int)s;
 }
 
+// weight gradient by k_wgrad_dz: partials [splits][27 ci][co] into a.out;
+// returns the number of splits, 0 if not launched
+template <int CI, int CO, int COG, int S>
+static int wgrad_dz(const ConvArgs &a, int max_splits, cudaStream_t st) {
+    using W = WzCfg<CI, CO, COG, S>;
+    static int sms = 0, attr = 0;
+    if (attr == 0) {
+        int dev = 0;
+        attr = (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                cudaFuncSetAttribute(k_wgrad_dz<CI, CO, COG, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)W::SMEM) == cudaSuccess)
+                   ? 1
+                   : -1;
+        if (attr < 0) (void)cudaGetLastError();
+    }
+    if (attr < 0) return 0;
+    CUtensorMap tm;
+    if (!act_tmap(&tm, a.x, a.n, CI, W::HX, W::LINES, W::ZT + 2)) return 0;
+    const int n = a.n;
+    const long long tiles = (long long)((n + 7) / 8) * ((n + 15) / 16) * ((n + W::ZT - 1) / W::ZT);
+    long long s = (long long)sms / W::NG;  // one CTA per SM
+    if (s > max_splits) s = max_splits;
+    if (s > tiles) s = tiles;
+    if (s < 1) s = 1;
+    k_wgrad_dz<CI, CO, COG, S><<<(unsigned)(s * W::NG), WZ_THREADS, W::SMEM, st>>>(tm, a, (int)s);
+    counted(1);
+    return (int)s;
+}
+
+static int wgrad_dz_cn(const ConvArgs &a, int max_splits, cudaStream_t st) {
+    if (a.ci == 32 && a.co == 16) return wgrad_dz<32, 16, 16, 4>(a, max_splits, st);
+    if (a.ci == 64 && a.co == 32) return wgrad_dz<64, 32, 16, 2>(a, max_splits, st);
+    if (a.ci == 32 && a.co == 64) return wgrad_dz<32, 64, 32, 3>(a, max_splits, st);
+    return 0;
+}
+
 static int wgrad_halo_cn(const ConvArgs &a, int max_splits, cudaStream_t st) {
     if (a.ci == 16 && a.co == 32) return wgrad_halo<16, 32, 27>(a, max_splits, st);
     if (a.ci == 32 && a.co == 64) return wgrad_halo<32, 64, 14>(a, max_splits, st);
@@ -1484,21 +2262,33 @@ static int wgrad_halo_cn(const ConvArgs &a, int max_splits, cudaStream_t st) {
 // fit it (halo tiles: the four layer shapes; gathered tiles: N in {16, 32,
 // 64}, C a multiple of 8; 16-byte aligned operands), else mma.sync
 template <int MODE>
-static void conv_gemm(const ConvArgs &a, long long rows, cudaStream_t st) {
+// Returns whether the output went out in the form a.up_adj asks for (only
+// k_conv_dz sums a data gradient over the children of an upsampling; the
+// other engines write every voxel).
+static bool conv_gemm(ConvArgs a, long long rows, cudaStream_t st) {
     const int N = MODE == MODE_FWD ? a.co : a.ci, C = MODE == MODE_FWD ? a.ci : a.co;
-    const bool aligned = ((uintptr_t)a.x | (uintptr_t)a.wt | (uintptr_t)a.skip |
+    const bool aligned = ((uintptr_t)a.x | (uintptr_t)a.wt | (uintptr_t)a.wdz | (uintptr_t)a.skip |
                           (uintptr_t)(MODE == MODE_FWD ? (void *)a.y : (void *)a.out)) % 16 == 0;
     const int engine = g_conv_engine.load();
-    if (engine == 2 && a.wt && aligned && halo_cn<MODE>(C, N, a, st)) return;
+    if (MODE == MODE_FWD || a.n % 2 != 0) a.up_adj = 0;
+    if (engine == 2 && a.wdz && aligned && dz_cn<MODE>(C, N, a, st)) return true;
+    const bool want = a.up_adj != 0;
+    a.up_adj = 0;
+    if (engine == 3 && a.wt && aligned && halo_cn<MODE>(C, N, a, st)) return !want;
     if (engine >= 1 && a.wt && C % 8 == 0 && aligned && (N == 16 || N == 32 || N == 64)) {
         bool done = N == 16 ? umma<MODE, 16>(a, rows, st)
                             : N == 32 ? umma<MODE, 32>(a, rows, st) : umma<MODE, 64>(a, rows, st);
-        if (done) return;
+        if (done) return !want;
     }
     gemm_bn<MODE>(N, a, (int)((rows + GM - 1) / GM), 1, st);
+    return !want;
 }
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static void reduce_parts(int splits, int len, const float *part, float *out, cudaStream_t st) {
+    k_reduce_parts<<<nblk(len, 32), dim3(32, 8), 0, st>>>(splits, len, part, out);
+}
 
 }  // namespace dgr
 
@@ -1530,29 +2320,32 @@ int dgr_net_forward(int n, const float *params, const float *input, float *outpu
     k_to_bf16<<<nblk(np, 256), 256, 0, st>>>(np, params, wbf);
     int *status = reinterpret_cast<int *>(base + W.status);
     cudaMemsetAsync(status, 0, sizeof(int), st);
-    bf16 *wpk = B(W.wpk);
-    for (int l = 1; l <= 4; ++l)
+    bf16 *wpk = B(W.wpk), *wdz = B(W.wdz);
+    for (int l = 1; l <= 4; ++l) {
         for (int mode = 0; mode < 2; ++mode)
             k_wpack<<<nblk(27 * net::L[l].ci * net::L[l].co, 256), 256, 0, st>>>(
                 mode, net::L[l].ci, net::L[l].co, wbf + net::w_off(l), wpk + net::wpk_off(l, mode));
-    counted(8);
-    k_conv1_fwd<<<nblk(n3, 128), 128, 0, st>>>(n, input, params + net::w_off(0),
+        k_wpack_dz<<<dim3(nblk(27 * net::L[l].ci * net::L[l].co, 256), 2), 256, 0, st>>>(
+            net::L[l].ci, net::L[l].co, wbf + net::w_off(l), wdz + net::wpk_off(l, 0), wdz + net::wpk_off(l, 1));
+    }
+    counted(12);
+    k_conv1_fwd<<<nblk((long long)((n + C1_VX - 1) / C1_VX) * n * n, 128), 128, 0, st>>>(n, input, params + net::w_off(0),
                                                 params + net::b_off(0), B(W.a1));
-    k_pool<<<nblk(h3 * 16, 256), 256, 0, st>>>(h, 16, B(W.a1), B(W.p1));
+    k_pool<<<nblk(h3 * 2, 256), 256, 0, st>>>(h, 16, B(W.a1), B(W.p1));
     counted(3);
     auto conv = [&](int l, int side, const bf16 *x, const bf16 *skip, bf16 *y) {
         ConvArgs a{};
         a.n = side; a.ci = net::L[l].ci; a.co = net::L[l].co;
         a.x = x; a.w = wbf + net::w_off(l); a.bias = params + net::b_off(l); a.skip = skip; a.y = y;
-        a.wt = wpk + net::wpk_off(l, 0); a.status = status;
+        a.wt = wpk + net::wpk_off(l, 0); a.wdz = wdz + net::wpk_off(l, 0); a.status = status;
         conv_gemm<MODE_FWD>(a, (long long)side * side * side, st);
     };
     conv(1, h, B(W.p1), nullptr, B(W.a2));
-    k_pool<<<nblk(q3 * 32, 256), 256, 0, st>>>(q, 32, B(W.a2), B(W.p2));
+    k_pool<<<nblk(q3 * 4, 256), 256, 0, st>>>(q, 32, B(W.a2), B(W.p2));
     conv(2, q, B(W.p2), nullptr, B(W.a3));
-    k_up<<<nblk(h3 * 64, 256), 256, 0, st>>>(q, 64, B(W.a3), B(W.u2));
+    k_up<<<nblk(h3 * 8, 256), 256, 0, st>>>(q, 64, B(W.a3), B(W.u2));
     conv(3, h, B(W.u2), B(W.a2), B(W.a4));
-    k_up<<<nblk(n3 * 32, 256), 256, 0, st>>>(h, 32, B(W.a4), B(W.u1));
+    k_up<<<nblk(n3 * 4, 256), 256, 0, st>>>(h, 32, B(W.a4), B(W.u1));
     conv(4, n, B(W.u1), B(W.a1), B(W.a5));
     k_head_fwd<<<nblk(n3, 256), 256, 0, st>>>((int)n3, B(W.a5), params + net::w_off(5),
                                                params + net::b_off(5), output);
@@ -1573,13 +2366,13 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
     const long long n3 = (long long)n * n * n, h3 = n3 / 8, q3 = n3 / 64;
     const bf16 *wbf = B(W.wbf);
     float *part = F(W.part), *bpart = F(W.bpart);
-    // head: dL/da5, dW6, db6
-    k_head_bwd<<<256, 256, 0, st>>>((int)n3, B(W.a5), params + net::w_off(5), grad_output,
-                                    F(W.ga5f), part);
-    k_reduce_parts<<<1, 64, 0, st>>>(256, 34, part, grad_params + net::w_off(5));
+    // head: dW6, db6 and the pre-activation gradient of layer 5, (a5 > 0) dL/da5
+    k_head_bwd<<<net::HEAD_BLOCKS, 256, 0, st>>>((int)n3, B(W.a5), params + net::w_off(5), grad_output,
+                                                B(W.gz5b), F(W.gz5f), part);
+    reduce_parts(net::HEAD_BLOCKS, 34, part, grad_params + net::w_off(5), st);
     counted(2);
     // the packed weights and the status word come from the forward pass on this workspace
-    const bf16 *wpk = B(W.wpk);
+    const bf16 *wpk = B(W.wpk), *wdz = B(W.wdz);
     int *status = reinterpret_cast<int *>(base + W.status);
     // weight and bias gradients of tensor-core layer l (input x at side^3)
     auto wgrad = [&](int l, int side, const bf16 *x, const bf16 *gz_b, const float *gz_f) {
@@ -1587,62 +2380,82 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
         const long long s3 = (long long)side * side * side;
         ConvArgs a{};
         a.n = side; a.ci = ci; a.co = co; a.x = x; a.g = gz_b; a.out = part;
-        const int max_splits = (int)nblk(s3, WG_SPLIT);  // the partial buffer's capacity
+        const int max_splits = (int)nblk(s3, WG_SPLIT);  // mma.sync: splits of WG_SPLIT voxels
+        // tcgen05: as many splits as the partial buffer holds (the launch
+        // takes at most one per SM and tile)
+        const long long cap = (long long)(W.part_n / ((size_t)27 * ci * co));
+        const int tc_splits = (int)(cap < 4096 ? cap : 4096);
         const int engine = g_conv_engine.load();
         const bool aligned = ((uintptr_t)a.x | (uintptr_t)a.g) % 16 == 0;
         int splits = 0;
-        if (engine == 2 && aligned) {
+        if (engine >= 2 && aligned) {
             a.status = status;
-            splits = wgrad_halo_cn(a, max_splits, st);
+            if (engine == 2) splits = wgrad_dz_cn(a, tc_splits, st);
+            if (splits == 0) splits = wgrad_halo_cn(a, engine == 2 ? tc_splits : max_splits, st);
         }
         if (splits == 0) {
             splits = max_splits;
             gemm_bn<MODE_WGRAD>(co, a, (int)nblk(27 * ci, GM), splits, st);
         }
-        k_reduce_parts<<<nblk(27 * ci * co, 256), 256, 0, st>>>(splits, 27 * ci * co, part,
-                                                                grad_params + net::w_off(l));
-        k_bias_part<<<dim3(64, co), 256, 0, st>>>(s3, co, gz_f, bpart);
-        k_reduce_parts<<<1, 64, 0, st>>>(64, co, bpart, grad_params + net::b_off(l));
+        reduce_parts(splits, 27 * ci * co, part, grad_params + net::w_off(l), st);
+        k_bias_part<<<net::BIAS_BLOCKS, 256, 0, st>>>(s3, co, gz_f, bpart);
+        reduce_parts(net::BIAS_BLOCKS, co, bpart, grad_params + net::b_off(l), st);
         counted(3);
     };
-    auto dgrad = [&](int l, int side, const bf16 *gz_b, float *gx) {
+    // data gradient of layer l into gx; with up_adj, asks for it summed over
+    // the 2^3 children of the upsampling that fed layer l (half resolution);
+    // returns whether it came in that form (else every voxel, full resolution)
+    auto dgrad = [&](int l, int side, const bf16 *gz_b, float *gx, bool up_adj) {
         ConvArgs d{};
         d.n = side; d.ci = net::L[l].ci; d.co = net::L[l].co; d.x = gz_b; d.w = wbf + net::w_off(l);
-        d.out = gx; d.wt = wpk + net::wpk_off(l, 1); d.status = status;
-        conv_gemm<MODE_DGRAD>(d, (long long)side * side * side, st);
+        d.out = gx; d.wt = wpk + net::wpk_off(l, 1); d.wdz = wdz + net::wpk_off(l, 1); d.status = status;
+        d.up_adj = up_adj ? 1 : 0;
+        return conv_gemm<MODE_DGRAD>(d, (long long)side * side * side, st) && up_adj;
     };
-    // layer 5: a5 = relu(conv(u1) + b5 + a1)
-    k_relu_grad<<<nblk(n3 * 16, 256), 256, 0, st>>>(n, 16, B(W.a5), F(W.ga5f), nullptr, nullptr,
-                                                   nullptr, B(W.gz5b), F(W.gz5f));
-    counted(1);
+    // layer 5: a5 = relu(conv(u1) + b5 + a1); its pre-activation gradient came with the head's
     wgrad(4, n, B(W.u1), B(W.gz5b), F(W.gz5f));
-    dgrad(4, n, B(W.gz5b), F(W.gu1f));
+    const bool up4 = dgrad(4, n, B(W.gz5b), F(W.gu1f), true);
     // layer 4: a4 = relu(conv(up(a3)) + b4 + a2); its gradient is up^T(gu1)
-    k_relu_grad<<<nblk(h3 * 32, 256), 256, 0, st>>>(h, 32, B(W.a4), nullptr, F(W.gu1f), nullptr,
-                                                   nullptr, B(W.gz4b), F(W.gz4f));
+    k_relu_grad<<<nblk(h3 * 8, 256), 256, 0, st>>>(h, 32, B(W.a4), up4 ? F(W.gu1f) : nullptr,
+                                                   up4 ? nullptr : F(W.gu1f), nullptr, nullptr, B(W.gz4b),
+                                                   F(W.gz4f));
     counted(1);
     wgrad(3, h, B(W.u2), B(W.gz4b), F(W.gz4f));
-    dgrad(3, h, B(W.gz4b), F(W.gu2f));
+    const bool up3 = dgrad(3, h, B(W.gz4b), F(W.gu2f), true);
     // layer 3: a3 = relu(conv(pool(a2)) + b3); gradient up^T(gu2)
-    k_relu_grad<<<nblk(q3 * 64, 256), 256, 0, st>>>(q, 64, B(W.a3), nullptr, F(W.gu2f), nullptr,
-                                                   nullptr, B(W.gz3b), F(W.gz3f));
+    k_relu_grad<<<nblk(q3 * 16, 256), 256, 0, st>>>(q, 64, B(W.a3), up3 ? F(W.gu2f) : nullptr,
+                                                   up3 ? nullptr : F(W.gu2f), nullptr, nullptr, B(W.gz3b),
+                                                   F(W.gz3f));
     counted(1);
     wgrad(2, q, B(W.p2), B(W.gz3b), F(W.gz3f));
-    dgrad(2, q, B(W.gz3b), F(W.gp2f));
+    dgrad(2, q, B(W.gz3b), F(W.gp2f), false);
     // layer 2: a2 = relu(conv(pool(a1)) + b2); gradient: skip of layer 4 + pool^T(gp2)
-    k_relu_grad<<<nblk(h3 * 32, 256), 256, 0, st>>>(h, 32, B(W.a2), F(W.gz4f), nullptr, F(W.gp2f),
+    k_relu_grad<<<nblk(h3 * 8, 256), 256, 0, st>>>(h, 32, B(W.a2), F(W.gz4f), nullptr, F(W.gp2f),
                                                    nullptr, B(W.gz2b), F(W.gz2f));
     counted(1);
     wgrad(1, h, B(W.p1), B(W.gz2b), F(W.gz2f));
-    dgrad(1, h, B(W.gz2b), F(W.gp1f));
+    dgrad(1, h, B(W.gz2b), F(W.gp1f), false);
     // layer 1: a1 = relu(conv(x) + b1); gradient: skip of layer 5 + pool^T(gp1)
-    k_relu_grad<<<nblk(n3 * 16, 256), 256, 0, st>>>(n, 16, B(W.a1), F(W.gz5f), nullptr, F(W.gp1f),
+    k_relu_grad<<<nblk(n3 * 4, 256), 256, 0, st>>>(n, 16, B(W.a1), F(W.gz5f), nullptr, F(W.gp1f),
                                                    nullptr, nullptr, F(W.gz1f));
+    // two resident blocks per SM, each walking many tiles (its copies
+    // double-buffered); blocks = partials
+    static int c1_sms = 0;
+    if (c1_sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c1_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            c1_sms = 148;
+    }
     const unsigned c1t = (unsigned)(((n + 7) / 8) * ((n + 7) / 8) * ((n + 7) / 8));
-    const unsigned c1b = c1t < (unsigned)net::C1_BLOCKS ? c1t : (unsigned)net::C1_BLOCKS;  // blocks = partials
-    k_conv1_wgrad<<<c1b, C1_THREADS, 0, st>>>(n, input, F(W.gz1f), part);
-    k_reduce_parts<<<nblk(27 * 16 + 16, 256), 256, 0, st>>>((int)c1b, 27 * 16 + 16, part,
-                                                            grad_params + net::w_off(0));
+    unsigned c1b = (unsigned)(2 * c1_sms);
+    if (c1b > (unsigned)net::C1_BLOCKS) c1b = (unsigned)net::C1_BLOCKS;
+    if (c1b > c1t) c1b = c1t;
+    static const bool c1_attr =
+        cudaFuncSetAttribute(k_conv1_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C1_SMEM) == cudaSuccess;
+    if (!c1_attr) return DGR_ERR_CUDA;
+    k_conv1_wgrad<<<c1b, C1_THREADS, C1_SMEM, st>>>(n, input, F(W.gz1f), part);
+    reduce_parts((int)c1b, 27 * 16 + 16, part, grad_params + net::w_off(0), st);
     counted(3);
     return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
 }
@@ -1656,13 +2469,13 @@ int dgr_net_loss(int n, const float *output, const float *target, float w_densit
     float *lp = reinterpret_cast<float *>(static_cast<char *>(ws) + W.lpart);
     const long long n3 = (long long)n * n * n;
     k_mse<<<256, 256, 0, st>>>(n3, output, target, w_density, w_scale, grad_output, lp);
-    k_reduce_parts<<<1, 32, 0, st>>>(256, 1, lp, loss);
+    reduce_parts(256, 1, lp, loss, st);
     counted(2);
     return cudaGetLastError() == cudaSuccess ? DGR_OK : DGR_ERR_CUDA;
 }
 
 int dgr_set_conv_engine(int engine) {
-    if (engine < 0 || engine > 2) return DGR_ERR_ARG;
+    if (engine < 0 || engine > 3) return DGR_ERR_ARG;
     g_conv_engine.store(engine);
     return DGR_OK;
 }

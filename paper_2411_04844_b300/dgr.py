@@ -600,8 +600,9 @@ def dgr_net_ws_bytes(n: int) -> int:
 
 
 def dgr_set_conv_engine(engine: int):
-    """Convolutions: 2 tcgen05 halo tiles for all three GEMMs (default),
-    1 tcgen05 gathered tiles for forward / data gradient, 0 mma.sync."""
+    """Convolutions: 2 tcgen05 on TMA-loaded halo blocks with several taps
+    per MMA (default), 3 tcgen05 halo blocks with one MMA per tap, 1 tcgen05
+    gathered tiles for forward / data gradient, 0 mma.sync."""
     _rc(lib().dgr_set_conv_engine(int(engine)), "dgr_set_conv_engine")
 
 

@@ -33,7 +33,7 @@ def main(argv=None):
     ap.add_argument("--no-separable", action="store_true", help="general voxelizer even when separable")
     ap.add_argument("--staged", action="store_true", help="path walks staged through shared memory (off by default, as in the library)")
     ap.add_argument("--side", type=int, default=128, help="network grid side")
-    ap.add_argument("--conv-engine", type=int, default=2, help="2: tcgen05 halo tiles, 1: tcgen05 gathered tiles, 0: mma.sync")
+    ap.add_argument("--conv-engine", type=int, default=2, help="2: tcgen05, several taps per MMA; 3: tcgen05 halo tiles, one tap per MMA; 1: tcgen05 gathered tiles; 0: mma.sync")
     a = ap.parse_args(argv)
     if a.op.startswith("net"):
         return net_case(a)

@@ -34,8 +34,8 @@ def init_params(rng):
 
 def run_net(n, P, x, gy, engine):
     """forward + backward through the C ABI with the given convolution engine
-    (2 tcgen05 halo tiles, 1 tcgen05 gathered tiles, 0 mma.sync); returns
-    output, parameter gradient, status"""
+    (2 tcgen05 several taps per MMA, 3 tcgen05 one tap per MMA, 1 tcgen05
+    gathered tiles, 0 mma.sync); returns output, parameter gradient, status"""
     ws = torch.empty(dgr.dgr_net_ws_bytes(n), dtype=torch.uint8, device=DEV)
     out = torch.full((n, n, n, 2), float("nan"), device=DEV)
     gp = torch.full((N.n_params(),), float("nan"), device=DEV)
@@ -50,9 +50,13 @@ def run_net(n, P, x, gy, engine):
     return out, gp, dgr.dgr_net_status(n, ws)
 
 
-@pytest.mark.parametrize("engine", [2, 1, 0])
-@pytest.mark.parametrize("n", [8, 12, 16])
+@pytest.mark.parametrize("engine,n", [(e, n) for n in (8, 12, 16, 32, 36) for e in (2, 3, 1, 0)] + [(2, 64)])
 def test_net_forward_and_gradients_match_oracle(n, engine):
+    """8^3 .. 16^3: one to a few tiles per layer; 32^3: tens of tiles per
+    layer and several weight-gradient splits; 36^3: partial tiles in x, y
+    and z at sides 36 / 18 / 9; 64^3 (default engine): two tiles for some
+    persistent CTAs of the last layer (a copy stage and an accumulator
+    buffer reused) and 2,048 weight-gradient tiles over the splits."""
     assert dgr.dgr_net_param_count() == N.n_params()
     rng = np.random.default_rng(n)
     P = init_params(rng)
@@ -73,14 +77,15 @@ def test_net_forward_and_gradients_match_oracle(n, engine):
             o += sz
 
 
-@pytest.mark.parametrize("engine", [2, 1])
-@pytest.mark.parametrize("n", [32, 36])
+@pytest.mark.parametrize("engine,n", [(2, 32), (3, 32), (1, 32), (2, 36), (3, 36), (1, 36), (2, 128), (3, 128)])
 def test_tcgen05_and_mma_sync_engines_agree_on_many_tiles(n, engine):
     """32^3: 256, 32 and 4 gathered tiles of 128 rows at sides n, n/2 and n/4,
-    and 8 x 16 x 4 halo tiles (8 x 16 x 2 for 64 input channels) with
-    several tiles per persistent CTA; 36^3: sides 36, 18 and 9 end in partial
-    tiles in x, y and z.  Both engines accumulate in FP32, so they differ by
-    summation order and the rare BF16 rounding it flips."""
+    and halo tiles with several tiles per persistent CTA; 36^3: sides 36, 18
+    and 9 end in partial tiles in x, y and z; 128^3: the full-size network,
+    whose persistent CTAs cycle through every copy stage and both
+    accumulator buffers many times (about 14 tiles per CTA in the last
+    layer).  Both engines accumulate in FP32, so they differ by summation
+    order and the rare BF16 rounding it flips."""
     rng = np.random.default_rng(n)
     P = init_params(rng)
     x = rng.uniform(0, 1, (n, n, n)).astype(np.float32)
