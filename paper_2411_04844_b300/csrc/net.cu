@@ -1315,6 +1315,163 @@ __global__ void __launch_bounds__(WZ_THREADS, 1) k_wgrad_dz(const __grid_constan
     }
 }
 
+// Weight gradient for few input channels (16): the roles of k_wgrad_dz's
+// operands swapped.  A = the output-gradient block (MN-major, [z][y][chunk][x]
+// with a one-line y halo): M-adjacent core matrices one chunk apart run on
+// into the next line, so the 128 rows are (j, co) for four y offsets j (the
+// fourth discarded) of 32 output channels; B = the input block (MN-major,
+// [chunk][z][y][x] planes): N = (chunk, dz + 1) x 8 channels = 4 CI columns
+// (the fourth z offset discarded).  D[(j, co)][(dz, ci)] = dW[tap (dz, 1 - j,
+// dx)][ci][co] for one dx, with the same substitution as k_wgrad_dz.  Rows
+// wasted: a quarter, against three quarters with the output channels alone
+// on M.  Copies, issuers (one per dx) and stages as in k_wgrad_dz.
+template <int CI, int CO, int S>
+struct WtCfg {
+    static constexpr int ZT = 2, HX = 10, LINES = 16, CH = CI / 8;
+    static constexpr unsigned XP = 16u * HX * LINES;          // one (chunk, z) plane of the input block
+    static constexpr unsigned XBYTES = (unsigned)CH * 4 * XP;  // chunks x 4 z slices
+    static constexpr unsigned LS = (unsigned)(CO / 8) * 128;   // output-gradient line pitch
+    // 18 lines per slice; the discarded fourth y offset reads up to two lines
+    // past the last slice: padding
+    static constexpr unsigned GBYTES = (unsigned)(ZT * 18 + 2) * LS;
+    static constexpr unsigned STAGE = XBYTES + GBYTES;
+    static constexpr int NB = 4 * CI, COLS = 3 * NB;
+    static constexpr unsigned NCOL = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
+    static constexpr unsigned BAROFF = (unsigned)S * STAGE;
+    static constexpr size_t SMEM = 1024 + (size_t)BAROFF + 256;
+    static_assert(CO * 4 == 128 && NB % 16 == 0 && NB <= 256 && COLS <= 512, "shapes");
+    // the discarded z offset of the last chunk reads one plane past the input block
+    static_assert(STAGE % 128 == 0 && GBYTES >= XP, "layout");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+template <int CI, int CO, int S>
+__global__ void __launch_bounds__(WZ_THREADS, 1) k_wgrad_dzt(const __grid_constant__ CUtensorMap tmap,
+                                                             const ConvArgs a, int splits) {
+    using W = WtCfg<CI, CO, S>;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(sm + W::BAROFF);
+    unsigned long long *empty = full + S, *done = full + 2 * S;
+    unsigned *tslot = reinterpret_cast<unsigned *>(full + 2 * S + 1);
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = (int)blockIdx.x;
+    if (w == 0) {
+        tmem_alloc(tslot, W::NCOL);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1 + 64);  // the TMA's expect_tx arrival + one per cp.async thread
+            mbar_init(&empty[s], 3);      // one commit per issuer
+        }
+        mbar_init(done, 3);
+        fence_barrier_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tslot;
+
+    const int n = a.n;
+    const int ntx = (n + 7) / 8, nty = (n + 15) / 16, ntz = (n + W::ZT - 1) / W::ZT;
+    const long long ntiles = (long long)ntx * nty * ntz;
+    const long long tb = ntiles * split / splits, te = ntiles * (split + 1) / splits;
+    const int cnt = (int)(te - tb);
+    auto origin = [&](int i, int &x0, int &y0, int &z0) {
+        const long long tile = tb + i;
+        x0 = (int)(tile % ntx) * 8;
+        y0 = (int)((tile / ntx) % nty) * 16;
+        z0 = (int)(tile / ((long long)ntx * nty)) * W::ZT;
+    };
+
+    if (w == 0 && lane == 0) {
+        int u = 0;
+        for (; u < cnt; ++u) {
+            const int s = u % S;
+            if (u >= S && !mbar_wait(&empty[s], ((u / S) - 1) & 1, a.status)) break;
+            int x0, y0, z0;
+            origin(u, x0, y0, z0);
+            unsigned char *X = sm + s * W::STAGE;
+            mbar_expect_tx(&full[s], W::XBYTES);
+#pragma unroll
+            for (int c = 0; c < W::CH; ++c) tma_load_4d(X + c * 4 * W::XP, &tmap, 8 * c, x0 - 1, y0, z0 - 1, &full[s]);
+        }
+        for (int v = u - S > 0 ? u - S : 0; v < u; ++v) mbar_wait(&full[v % S], (v / S) & 1, a.status);
+    } else if (w == 4 || w == 5) {
+        const int t = threadIdx.x - 128;
+        constexpr int CC = CO / 8, TOT = W::ZT * 18 * CC * 8;
+        for (int u = 0; u < cnt; ++u) {
+            const int s = u % S;
+            if (u >= S && !mbar_wait(&empty[s], ((u / S) - 1) & 1, a.status)) break;
+            int x0, y0, z0;
+            origin(u, x0, y0, z0);
+            unsigned char *G = sm + s * W::STAGE + W::XBYTES;
+            for (int e = t; e < TOT; e += 64) {
+                const int xv = e % 8, cc = (e / 8) % CC, ly = (e / (8 * CC)) % 18, zs = e / (8 * CC * 18);
+                const int qx = x0 + xv, qy = y0 + ly - 1, qz = z0 + zs;
+                const bool in = qx < n && qy >= 0 && qy < n && qz < n;
+                const bf16 *src = in ? a.g + ((size_t)(qz * n + qy) * n + qx) * CO + 8 * cc : a.g;
+                cp_async16(G + ((zs * 18 + ly) * CC + cc) * 128 + xv * 16, src, in ? 16u : 0u);
+            }
+            cp_async_mbar_arrive(&full[s]);
+        }
+        cp_async_wait<0>();
+    } else if (w >= 1 && w <= 3 && lane == 0) {
+        const int dxi = w - 1;
+        constexpr unsigned IDESC = idesc_bf16_f32(128, W::NB) | (1u << 15) | (1u << 16);  // A, B MN-major
+        for (int u = 0; u < cnt; ++u) {
+            const int s = u % S;
+            if (!mbar_wait(&full[s], (u / S) & 1, a.status)) break;
+            fence_async_smem();  // the cp.async writes, for the tensor core's reads
+            tc_fence_after();
+            const unsigned xs = smem_u32(sm + s * W::STAGE), gs = xs + W::XBYTES;
+#pragma unroll 1
+            for (int zs = 0; zs < W::ZT; ++zs)
+#pragma unroll 2
+                for (int lp = 0; lp < 8; ++lp) {
+                    const uint64_t ad = smem_desc(gs + (unsigned)(zs * 18 + 2 * lp) * W::LS, W::LS, 128);
+                    const uint64_t bd =
+                        smem_desc(xs + (unsigned)zs * W::XP + (unsigned)(2 * lp * 160 + dxi * 16), 160, W::XP);
+                    umma_bf16(tmem + (unsigned)(dxi * W::NB), ad, bd, IDESC, (u | zs | lp) != 0);
+                }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(done);
+    }
+    if (w >= 4) {
+        const bool got = mbar_wait(done, 0, a.status);
+        __syncwarp();
+        tc_fence_after();
+        // row m = (j, co): j = m / CO (the warp's lane quarter), co = m % CO
+        const int q = w & 3, m = 32 * q + lane, j = m / CO, co = m % CO;
+        float *out = a.out + (size_t)split * 27 * CI * CO;
+        for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll 1
+            for (int n0 = 0; n0 < W::NB; n0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(dxi * W::NB + n0), v);
+                if (j == 3 || !got) continue;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    // column n0 + k = ((chunk c) 4 + dz + 1) 8 + channel
+                    const int g = (n0 + k) >> 3, c = g >> 2, dzp = g & 3, ci = 8 * c + ((n0 + k) & 7);
+                    if (dzp == 3) continue;
+                    const int tap = dzp * 9 + (2 - j) * 3 + dxi;
+                    out[((size_t)tap * CI + ci) * CO + co] = cnt > 0 ? v[k] : 0.f;
+                }
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, W::NCOL);
+    }
+}
+
 // the weights [27][ci][co] as k_conv_dz's B: wt[((t9 CH + kc) 3 NO + r) 8 + k]
 // for (dy, dx) = t9, chunk kc of the C input channels, row r = blk NO + o
 // (input offset dz = 1 - blk) and the k-th channel of the chunk:
@@ -1447,14 +1604,15 @@ __global__ void __launch_bounds__(128) k_conv1_fwd(int n, const float *__restric
 // weight gradient of the first layer: a block walks 8^3 voxel tiles (tile
 // b, b + gridDim.x, ...) with the input block (10^3, zero outside) and the
 // tile's gz [512][16] in shared memory, double-buffered (the next tile's
-// copies run during this tile's sums).  Thread i < 432 owns tap i % 27 and
-// the voxels v = i / 27 (mod 16) of each tile, for all 16 channels: the
-// lanes of a warp share (at most two) voxels, so their gz reads are
-// broadcasts, and one input plus four float4 reads feed 16 FMAs.  Threads
-// 432 .. 447 sum gz per channel (the bias gradient).  At the end the 16
-// voxel groups are summed in a fixed order: one partial [27 x 16 + 16] per
-// block (tap-major, then channel), summed over blocks afterwards.
-constexpr int C1_THREADS = 448;
+// copies run during this tile's sums).  Thread i < 144 owns the three taps
+// (dz, dy, dx = -1, 0, 1) of row r = i % 9 and the voxels v = i / 9 (mod 16)
+// of each tile, for all 16 channels: per voxel three inputs and four float4
+// gz reads (broadcasts: the lanes of a warp share at most three voxels) feed
+// 48 FMAs.  Threads 144 .. 159 sum gz per channel (the bias gradient).  At
+// the end the 16 voxel groups are summed in a fixed order: one partial
+// [27 x 16 + 16] per block (tap-major, then channel), summed over blocks
+// afterwards.
+constexpr int C1_THREADS = 160;
 constexpr size_t C1_SMEM = sizeof(float) * 2 * (1000 + 512 * 16);  // dynamic: two (input, gz) buffers
 __global__ void __launch_bounds__(C1_THREADS) k_conv1_wgrad(int n, const float *__restrict__ x,
                                                             const float *__restrict__ gz,
@@ -1464,12 +1622,13 @@ __global__ void __launch_bounds__(C1_THREADS) k_conv1_wgrad(int n, const float *
     float(*gs)[512 * 16] = reinterpret_cast<float(*)[512 * 16]>(c1sm + 2000);  // [2][8192], 16-byte aligned
     const int nt = (n + 7) / 8, ntiles = nt * nt * nt;
     const int i = threadIdx.x;
-    const int tap = i % 27, g = i / 27;  // for i < 432; i >= 432: bias channel i - 432
-    int dx = 0, dy = 0, dz = 0;
-    if (i < 432) tap_offset(tap, dx, dy, dz);
-    float acc[16];
+    const int r = i % 9, g = i / 9;  // for i < 144; i >= 144: bias channel i - 144
+    const int dz = r / 3 - 1, dy = r % 3 - 1;
+    float acc[3][16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[d][c] = 0.f;
     auto load = [&](int t, int buf) {
         const int x0 = (t % nt) * 8, y0 = ((t / nt) % nt) * 8, z0 = (t / (nt * nt)) * 8;
         for (int e = i; e < 1000; e += C1_THREADS) {
@@ -1495,43 +1654,50 @@ __global__ void __launch_bounds__(C1_THREADS) k_conv1_wgrad(int n, const float *
             cp_async_wait<0>();
         }
         __syncthreads();
-        if (i < 432) {
+        if (i < 144) {
             const float *xb = xs[buf];
-#pragma unroll 4
+#pragma unroll 2
             for (int v = g; v < 512; v += 16) {
                 const int vx = v & 7, vy = (v >> 3) & 7, vz = v >> 6;
-                const float xv = xb[((vz + 1 + dz) * 10 + vy + 1 + dy) * 10 + vx + 1 + dx];
+                const float *xr = xb + ((vz + 1 + dz) * 10 + vy + 1 + dy) * 10 + vx;  // dx = -1 at xr[0]
+                const float x0v = xr[0], x1v = xr[1], x2v = xr[2];
                 const float4 *gp = reinterpret_cast<const float4 *>(gs[buf] + v * 16);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float4 gk = gp[k];
-                    acc[4 * k] = fmaf(xv, gk.x, acc[4 * k]);
-                    acc[4 * k + 1] = fmaf(xv, gk.y, acc[4 * k + 1]);
-                    acc[4 * k + 2] = fmaf(xv, gk.z, acc[4 * k + 2]);
-                    acc[4 * k + 3] = fmaf(xv, gk.w, acc[4 * k + 3]);
+                    const float gv[4] = {gk.x, gk.y, gk.z, gk.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        acc[0][4 * k + e] = fmaf(x0v, gv[e], acc[0][4 * k + e]);
+                        acc[1][4 * k + e] = fmaf(x1v, gv[e], acc[1][4 * k + e]);
+                        acc[2][4 * k + e] = fmaf(x2v, gv[e], acc[2][4 * k + e]);
+                    }
                 }
             }
         } else {
-            const int c = i - 432;
+            const int c = i - 144;
 #pragma unroll 8
-            for (int v = 0; v < 512; ++v) acc[0] += gs[buf][v * 16 + c];
+            for (int v = 0; v < 512; ++v) acc[0][0] += gs[buf][v * 16 + c];
         }
         __syncthreads();  // buffer buf is refilled two tiles on
     }
     // per (tap, group) sums through shared memory, then the 16 groups in order
     float *red = gs[0];  // 432 x 16 floats fit in the 8,192 of a gz buffer
-    if (i < 432) {
+    if (i < 144) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) red[(tap * 16 + g) * 16 + c] = acc[c];
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) red[((r * 3 + d) * 16 + g) * 16 + c] = acc[d][c];
     }
     __syncthreads();
-    float s = acc[0];  // the bias threads' sums
-    if (i < 432) {
-        const int tp = i / 16, c = i % 16;
-        s = 0.f;
+    float *out = part + (size_t)blockIdx.x * (27 * 16 + 16);
+    for (int o = i; o < 432; o += C1_THREADS) {
+        const int tp = o / 16, c = o % 16;
+        float s = 0.f;
         for (int k = 0; k < 16; ++k) s += red[(tp * 16 + k) * 16 + c];
+        out[o] = s;
     }
-    part[(size_t)blockIdx.x * (27 * 16 + 16) + i] = s;
+    if (i >= 144) out[432 + i - 144] = acc[0][0];  // the bias threads' sums
 }
 
 // head: 1x1 conv 16 -> 2, FP32 output [n^3][2]
@@ -2243,10 +2409,39 @@ static int wgrad_dz(const ConvArgs &a, int max_splits, cudaStream_t st) {
     return (int)s;
 }
 
+template <int CI, int CO, int S>
+static int wgrad_dzt(const ConvArgs &a, int max_splits, cudaStream_t st) {
+    using W = WtCfg<CI, CO, S>;
+    static int sms = 0, attr = 0;
+    if (attr == 0) {
+        int dev = 0;
+        attr = (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                cudaFuncSetAttribute(k_wgrad_dzt<CI, CO, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)W::SMEM) == cudaSuccess)
+                   ? 1
+                   : -1;
+        if (attr < 0) (void)cudaGetLastError();
+    }
+    if (attr < 0) return 0;
+    CUtensorMap tm;
+    if (!act_tmap(&tm, a.x, a.n, CI, W::HX, W::LINES, W::ZT + 2)) return 0;
+    const int n = a.n;
+    const long long tiles = (long long)((n + 7) / 8) * ((n + 15) / 16) * ((n + W::ZT - 1) / W::ZT);
+    long long s = sms;  // one CTA per SM
+    if (s > max_splits) s = max_splits;
+    if (s > tiles) s = tiles;
+    if (s < 1) s = 1;
+    k_wgrad_dzt<CI, CO, S><<<(unsigned)s, WZ_THREADS, W::SMEM, st>>>(tm, a, (int)s);
+    counted(1);
+    return (int)s;
+}
+
 static int wgrad_dz_cn(const ConvArgs &a, int max_splits, cudaStream_t st) {
     if (a.ci == 32 && a.co == 16) return wgrad_dz<32, 16, 16, 4>(a, max_splits, st);
     if (a.ci == 64 && a.co == 32) return wgrad_dz<64, 32, 16, 2>(a, max_splits, st);
     if (a.ci == 32 && a.co == 64) return wgrad_dz<32, 64, 32, 3>(a, max_splits, st);
+    if (a.ci == 16 && a.co == 32) return wgrad_dzt<16, 32, 4>(a, max_splits, st);
     return 0;
 }
 
@@ -2438,7 +2633,7 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
     // layer 1: a1 = relu(conv(x) + b1); gradient: skip of layer 5 + pool^T(gp1)
     k_relu_grad<<<nblk(n3 * 4, 256), 256, 0, st>>>(n, 16, B(W.a1), F(W.gz5f), nullptr, F(W.gp1f),
                                                    nullptr, nullptr, F(W.gz1f));
-    // two resident blocks per SM, each walking many tiles (its copies
+    // three resident blocks per SM, each walking many tiles (its copies
     // double-buffered); blocks = partials
     static int c1_sms = 0;
     if (c1_sms == 0) {
@@ -2448,7 +2643,7 @@ int dgr_net_backward(int n, const float *params, const float *input, const float
             c1_sms = 148;
     }
     const unsigned c1t = (unsigned)(((n + 7) / 8) * ((n + 7) / 8) * ((n + 7) / 8));
-    unsigned c1b = (unsigned)(2 * c1_sms);
+    unsigned c1b = (unsigned)(3 * c1_sms);
     if (c1b > (unsigned)net::C1_BLOCKS) c1b = (unsigned)net::C1_BLOCKS;
     if (c1b > c1t) c1b = c1t;
     static const bool c1_attr =
