@@ -149,12 +149,13 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
     Foot F;
     footprint_f32(g, m, sc, qq, I.k, F);
     // delta = u - a, with u in FP64 so the fractional offset is exact to FP32
-    const double h = (double)g.h;
+    // (FP64 divisions and square roots are slow here: one reciprocal of h)
+    const double h = (double)g.h, ih = 1.0 / h;
     const double org[3] = {(double)g.ox, (double)g.oy, (double)g.oz};
     float del[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double u = ((double)m[a] - org[a]) / h - 0.5;
+        const double u = ((double)m[a] - org[a]) * ih - 0.5;
         del[a] = (float)(u - (double)(F.an[a] + (a == 2 ? g.z0 : 0)));
     }
     // column form of the exponent (FP64 per Gaussian): Sigma = R diag(s^2) R^T
@@ -170,20 +171,26 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
     bool diag;
     if (sc[0] == sc[1] && sc[1] == sc[2]) {
         // isotropic (the paper's representation): diagonal for any rotation
-        const double v = ((double)sc[0] / h) * ((double)sc[0] / h);
-        m00 = m11 = azz = 1.0 / v;
+        const double sv = (double)sc[0] * ih;
+        m00 = m11 = azz = 1.0 / (sv * sv);
         m01 = zx = zy = 0.0;
         diag = true;
     } else {
         const double q0 = qq.x, q1 = qq.y, q2 = qq.z, q3 = qq.w;
-        const double iq = 1.0 / sqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+        const double iq = rsqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
         const double w = q0 * iq, x = q1 * iq, y = q2 * iq, z = q3 * iq;
         const double Rd[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
                               2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
                               2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
         double v[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) v[k] = ((double)sc[k] / h) * ((double)sc[k] / h);
+        for (int k = 0; k < 3; ++k) {
+            const double sv = (double)sc[k] * ih;
+            v[k] = sv * sv;
+        }
+        // 1 / v_k from one reciprocal of their product
+        const double ip = 1.0 / (v[0] * v[1] * v[2]);
+        const double iv[3] = {v[1] * v[2] * ip, v[0] * v[2] * ip, v[0] * v[1] * ip};
         double S[6] = {0, 0, 0, 0, 0, 0};  // 00 11 22 01 02 12
         azz = 0.0;
 #pragma unroll
@@ -193,12 +200,12 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
             S[3] += Rd[k] * Rd[3 + k] * v[k];
             S[4] += Rd[k] * Rd[6 + k] * v[k];
             S[5] += Rd[3 + k] * Rd[6 + k] * v[k];
-            azz += Rd[6 + k] * Rd[6 + k] / v[k];
+            azz += Rd[6 + k] * Rd[6 + k] * iv[k];
         }
-        const double det = S[0] * S[1] - S[3] * S[3];
-        m00 = S[1] / det;
-        m11 = S[0] / det;
-        m01 = -S[3] / det;
+        const double det = S[0] * S[1] - S[3] * S[3], idet = 1.0 / det;
+        m00 = S[1] * idet;
+        m11 = S[0] * idet;
+        m01 = -S[3] * idet;
         zx = m00 * S[4] + m01 * S[5];
         zy = m01 * S[4] + m11 * S[5];
         diag = S[3] == 0.0 && S[4] == 0.0 && S[5] == 0.0;
@@ -212,12 +219,13 @@ __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
         const double hm = 0.5 * (m00 + m11), dm = 0.5 * (m00 - m11);
         const double r = sqrt(dm * dm + m01 * m01);
         l1 = hm + r;
-        l2 = (m00 * m11 - m01 * m01) / l1;  // the product of the eigenvalues over l1: no cancellation
+        // the product of the eigenvalues (det (Sigma_xy)^-1 = 1 / det Sigma_xy) over l1: no cancellation
+        l2 = (m00 * m11 - m01 * m01) / l1;
         // eigenvector of l1: (m01, l1 - m00) or (l1 - m11, m01), whichever is longer
         const double ax1 = m01, ay1 = l1 - m00, ax2 = l1 - m11, ay2 = m01;
         const bool first = ax1 * ax1 + ay1 * ay1 >= ax2 * ax2 + ay2 * ay2;
         const double ex = first ? ax1 : ax2, ey = first ? ay1 : ay2;
-        const double inv = 1.0 / sqrt(ex * ex + ey * ey);
+        const double inv = rsqrt(ex * ex + ey * ey);
         n1x = ex * inv;
         n1y = ey * inv;
     }
