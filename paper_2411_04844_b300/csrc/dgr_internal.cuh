@@ -45,27 +45,44 @@ constexpr int NMOM = 10;  // moments per item: S0, S1[3], S2[6]
 // the z range is kept long (the per-column set-up is paid once per column):
 //   zc = min(ez, max(1, ITEM_VOX / ex)) layers, yc = min(ey, max(1, ITEM_VOX /
 //   (ex zc))) rows; items are the ceil(ey / yc) x ceil(ez / zc) blocks.
+// a / b for 0 <= a, 1 <= b (exact); on the device for operands below 2^20 by a
+// float reciprocal and one correction (the estimate is within 0.25 of a / b),
+// else by the integer division
+__host__ __device__ inline int div_small(int a, int b) {
+#ifdef __CUDA_ARCH__
+    if (a < (1 << 20) && b < (1 << 20)) {
+        int q = (int)((float)a * __frcp_rn((float)b));
+        const int r = a - q * b;
+        if (r < 0) --q;
+        else if (r >= b) ++q;
+        return q;
+    }
+#endif
+    return a / b;
+}
 __host__ __device__ inline void item_shape(int ex, int ey, int ez, int &yc, int &zc) {
-    zc = ez < ITEM_VOX / ex ? ez : (ITEM_VOX / ex > 1 ? ITEM_VOX / ex : 1);
-    const long long xz = (long long)ex * zc;
-    yc = xz < ITEM_VOX ? (int)(ITEM_VOX / xz) : 1;
+    const int zmax = div_small(ITEM_VOX, ex);
+    zc = ez < zmax ? ez : (zmax > 1 ? zmax : 1);
+    const int xz = ex * zc;  // <= max(ITEM_VOX, ex)
+    yc = xz < ITEM_VOX ? div_small(ITEM_VOX, xz) : 1;
     if (yc > ey) yc = ey;
 }
 __host__ __device__ inline uint32_t item_count(int ex, int ey, int ez) {
     if (ex <= 0 || ey <= 0 || ez <= 0) return 0u;
     int yc, zc;
     item_shape(ex, ey, ez, yc, zc);
-    return (uint32_t)((ey + yc - 1) / yc) * (uint32_t)((ez + zc - 1) / zc);
+    return (uint32_t)div_small(ey + yc - 1, yc) * (uint32_t)div_small(ez + zc - 1, zc);
 }
 // item c of a box with lower corner (ly, lz) and upper (hy, hz): y and z ranges
 __host__ __device__ inline void item_range(int c, int ex, int ey, int ly, int hy, int lz, int hz,
                                            int &yb, int &ye, int &zb, int &ze) {
     int yc, zc;
     item_shape(ex, ey, hz - lz + 1, yc, zc);
-    const int nyc = (ey + yc - 1) / yc;
-    yb = ly + (c % nyc) * yc;
+    const int nyc = div_small(ey + yc - 1, yc);
+    const int zi = div_small(c, nyc);
+    yb = ly + (c - zi * nyc) * yc;
     ye = min(yb + yc - 1, hy);
-    zb = lz + (c / nyc) * zc;
+    zb = lz + zi * zc;
     ze = min(zb + zc - 1, hz);
 }
 

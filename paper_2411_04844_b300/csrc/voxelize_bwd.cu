@@ -27,6 +27,49 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Transposing butterfly over the 32 lanes for NMOM = 10 partial sums per
+// lane.  Level xor 16: lists of 10 split 5 / 5; xor 8: 5 split 3 / 2; xor 4:
+// 3 (the 2-lists padded with a zero) split 2 / 1; xor 2: 2 split 1 / 1; xor
+// 1: both lanes add their single values.  Per shuffle, the lane whose mask
+// bit is clear keeps the low part and sends the high one, its partner the
+// reverse.  m[0] then holds, for lane pair p = lane / 2, the full sum of
+// moment kMomOfPair[p] (-1: a padding zero).
+static_assert(NMOM == 10, "the butterfly's splits are laid out for 10 moments");
+__constant__ int kMomOfPair[16] = {0, 1, 2, -1, 3, 4, -1, -1, 5, 6, 7, -1, 8, 9, -1, -1};
+__device__ __forceinline__ void mom_reduce(float *v, int lane) {
+    const unsigned FULL = 0xffffffffu;
+    {   // 10 -> 5
+        const bool hi = lane & 16;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float send = hi ? v[i] : v[5 + i], keep = hi ? v[5 + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, 16);
+        }
+    }
+    {   // 5 -> 3 (low: 0..2) or 2 (high: 3..4, padded to 3)
+        const bool hi = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float h = i < 2 ? v[3 + i] : 0.f;
+            const float send = hi ? v[i] : h, keep = hi ? h : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, 8);
+        }
+    }
+    {   // 3 -> 2 (low: 0..1) or 1 (high: 2)
+        const bool hi = lane & 4;
+        const float s0 = hi ? v[0] : v[2], k0 = hi ? v[2] : v[0];
+        const float s1 = hi ? v[1] : 0.f, k1 = hi ? 0.f : v[1];
+        v[0] = k0 + __shfl_xor_sync(FULL, s0, 4);
+        v[1] = k1 + __shfl_xor_sync(FULL, s1, 4);
+    }
+    {   // 2 -> 1
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(FULL, send, 2);
+    }
+    v[0] += __shfl_xor_sync(FULL, v[0], 1);
+}
+
 // items per run taken from the queue: consecutive items mostly belong to
 // the same Gaussian, so a run costs one owner search
 constexpr int ITEM_RUN = 8;
@@ -155,16 +198,14 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
                 m[8] = fmaf(dx, s1, m[8]);       // xz
                 m[9] = fmaf(dy, s1, m[9]);       // yz
             }
-#pragma unroll
-            for (int k = 0; k < NMOM; ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
-            }
-            if (lane == 0) {
-                float *dst = part + (size_t)it * NMOM;
-#pragma unroll
-                for (int k = 0; k < NMOM; ++k) dst[k] = m[k];
-            }
+            // the 10 sums over the warp by a transposing butterfly: at each
+            // level the pair of lanes splits its list of partial sums, each
+            // keeping one half and adding the partner's copy of it (12
+            // shuffles instead of 10 x 5); the even lanes of 10 lane pairs end
+            // with one moment each (mom_of_pair)
+            mom_reduce(m, lane);
+            const int k = kMomOfPair[lane >> 1];
+            if ((lane & 1) == 0 && k >= 0) part[(size_t)it * NMOM + k] = m[0];
         }
     }
 }
