@@ -632,6 +632,205 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
     if (MODE == 0 && iv < I.nv) I.sino[ray] = acc * ray_norm(R, row, I.beam);
 }
 
+// a4 with two rays per thread: the projector's CTA covers the same column of
+// PR_ROWS rows with half the threads, lane l of warp w taking the rows
+// w 64 + l and w 64 + 32 + l (each load instruction still reads 32
+// consecutive rows' voxels).  The walk keeps one (x, y) path position for
+// both rays and pairs their arithmetic where it is the same operation (the
+// segment lengths as packed FP32 subtractions, the sums as packed FMAs; each
+// half rounds as the scalar operation), so the sinogram is bit-identical to
+// k_path<0>'s.  Single-crossing geometries only (no instance with multiz),
+// no staging: the launcher keeps k_path<0> otherwise.
+constexpr int PR2_THREADS = PR_ROWS / 2;
+
+template <bool MASKZ>
+__device__ __forceinline__ void walk_segs1_x2(const float *__restrict__ vol, const Seg *seg, int c0, int r0, int r1,
+                                              int nz, float &t, float2 &acc, int (&iz)[2], float (&fz)[2],
+                                              float (&tz)[2], const int (&sgz)[2], const float (&xi0z)[2],
+                                              const float (&iez)[2]) {
+    constexpr int NW = WALK;
+    const unsigned zmax = (unsigned)(nz - 1);
+    int zc[2] = {(int)min((unsigned)iz[0], zmax), (int)min((unsigned)iz[1], zmax)};
+    const float fsg[2] = {(float)sgz[0], (float)sgz[1]};
+    for (int r = r0; r < r1; r += NW) {
+        float2 l0[NW], l1[NW];
+        int a0[NW][2], a1[NW][2];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            const Seg S = seg[r + j - c0];  // past the round's end: padding, empty segments
+            const float t1 = S.t1;
+            const float m0 = fminf(tz[0], t1), m1 = fminf(tz[1], t1);
+            float2 d = __fadd2_rn(make_float2(m0, m1), make_float2(-t, -t));
+            if (MASKZ) {
+                d.x = (unsigned)iz[0] <= zmax ? d.x : 0.f;
+                d.y = (unsigned)iz[1] <= zmax ? d.y : 0.f;
+            }
+            l0[j] = d;
+            a0[j][0] = S.cb + zc[0];
+            a0[j][1] = S.cb + zc[1];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (tz[q] < t1) {
+                    iz[q] += sgz[q];
+                    fz[q] += fsg[q];
+                    tz[q] = (fz[q] - xi0z[q]) * iez[q];
+                    zc[q] = (int)min((unsigned)iz[q], zmax);
+                }
+            }
+            // at most one z crossing per cell: the second segment is t1 - m
+            d = __fadd2_rn(make_float2(t1, t1), make_float2(-m0, -m1));
+            if (MASKZ) {
+                d.x = (unsigned)iz[0] <= zmax ? d.x : 0.f;
+                d.y = (unsigned)iz[1] <= zmax ? d.y : 0.f;
+            }
+            l1[j] = d;
+            a1[j][0] = S.cb + zc[0];
+            a1[j][1] = S.cb + zc[1];
+            t = t1;
+        }
+        float2 v0[NW], v1[NW];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            v0[j] = make_float2(__ldg(vol + a0[j][0]), __ldg(vol + a0[j][1]));
+            // the second segment's voxel only after a crossing (else its length is 0)
+            v1[j] = make_float2(l1[j].x != 0.f ? __ldg(vol + a1[j][0]) : 0.f,
+                                l1[j].y != 0.f ? __ldg(vol + a1[j][1]) : 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < NW; ++j) acc = __ffma2_rn(l1[j], v1[j], __ffma2_rn(l0[j], v0[j], acc));
+    }
+}
+
+__global__ void __launch_bounds__(PR2_THREADS) k_path2(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base) {
+    __shared__ Seg seg[SEG_MAX + WALK];
+    const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
+    int ii = 0;
+    while (ii + 1 < B.n && B.in[ii + 1].pb0 <= (int)blockIdx.x) ++ii;
+    const Inst &I = B.in[ii];
+    const dgr_grid &g = I.g;
+    const int b = blockIdx.x - I.pb0;
+    const int iu = b % I.nu, rg = (b / I.nu) % I.npv, k = I.kv0 + b / (I.nu * I.npv);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int iv[2];
+    iv[0] = rg * PR_ROWS + w * 64 + lane;
+    iv[1] = iv[0] + 32;
+    const RayXY R = T.tab[I.tab0 + k * I.nu + iu];
+    RowZ row[2];
+    size_t ray[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        row[q] = T.rows[I.row0 + min(iv[q], I.nv - 1)];
+        ray[q] = ((size_t)k * I.nv + min(iv[q], I.nv - 1)) * I.nu + iu;
+    }
+    // (x, y) interval of the grid and entry cell: the same for the whole CTA
+    float tmin = -INFINITY, tmax = INFINITY;
+    bool miss = false;
+    float fx = 0.f, fy = 0.f;
+    if (R.ex != 0.f) {
+        const float t0 = plane_t(0, R.xi0x, R.inv_ex), t1 = plane_t(g.nx, R.xi0x, R.inv_ex);
+        tmin = fmaxf(tmin, fminf(t0, t1));
+        tmax = fminf(tmax, fmaxf(t0, t1));
+    } else {
+        fx = floorf(R.xi0x);
+        miss = miss || !(fx >= 0.f && fx < (float)g.nx);
+    }
+    if (R.ey != 0.f) {
+        const float t0 = plane_t(0, R.xi0y, R.inv_ey), t1 = plane_t(g.ny, R.xi0y, R.inv_ey);
+        tmin = fmaxf(tmin, fminf(t0, t1));
+        tmax = fminf(tmax, fmaxf(t0, t1));
+    } else {
+        fy = floorf(R.xi0y);
+        miss = miss || !(fy >= 0.f && fy < (float)g.ny);
+    }
+    if (miss || !(tmax > tmin)) {  // CTA-uniform
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (iv[q] < I.nv) I.sino[ray[q]] = 0.f;
+        return;
+    }
+    const int sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
+    const int sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
+    const int ix0 = sgx ? entry_cell(tmin, R.ex, R.xi0x, R.inv_ex, sgx, 0, g.nx - 1) : (int)fx;
+    const int iy0 = sgy ? entry_cell(tmin, R.ey, R.xi0y, R.inv_ey, sgy, 0, g.ny - 1) : (int)fy;
+    const int nxe = sgx > 0 ? g.nx - ix0 : (sgx < 0 ? ix0 + 1 : 0);
+    const int nye = sgy > 0 ? g.ny - iy0 : (sgy < 0 ? iy0 + 1 : 0);
+    const int px0 = sgx > 0 ? ix0 + 1 : ix0, py0 = sgy > 0 ? iy0 + 1 : iy0;
+    int rend = INT_MAX;
+    if (nxe > 0) {
+        const float te = plane_t(px0 + sgx * (nxe - 1), R.xi0x, R.inv_ex);
+        rend = min(rend, nxe - 1 + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false));
+    }
+    if (nye > 0) {
+        const float te = plane_t(py0 + sgy * (nye - 1), R.xi0y, R.inv_ey);
+        rend = min(rend, nye - 1 + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true));
+    }
+    const int nseg = rend + 1;
+    const int cb0 = ix0 * I.vsx + iy0 * I.vsy;
+    // each ray's z: entry layer (unbounded), next crossing, whether it stays in the z range
+    int iz[2], sgz[2];
+    float tz[2], fz[2], xi0z[2], iez[2];
+    bool zin[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const RayZ Z = ray_z(R, row[q], I.zoff);
+        xi0z[q] = Z.xi0z;
+        iez[q] = Z.inv_ez;
+        sgz[q] = 0;
+        tz[q] = INFINITY;
+        fz[q] = 0.f;
+        if (Z.ez != 0.f) {
+            sgz[q] = Z.ez > 0.f ? 1 : -1;
+            const float t0 = plane_t(0, Z.xi0z, Z.inv_ez), t1 = plane_t(g.nz, Z.xi0z, Z.inv_ez);
+            zin[q] = fminf(t0, t1) <= tmin && fmaxf(t0, t1) >= tmax;
+            iz[q] = entry_cell(tmin, Z.ez, Z.xi0z, Z.inv_ez, sgz[q], INT_MIN / 2, INT_MAX / 2);
+            fz[q] = (float)(sgz[q] > 0 ? iz[q] + 1 : iz[q]);
+            tz[q] = (fz[q] - Z.xi0z) * Z.inv_ez;
+        } else {
+            const float f = floorf(Z.xi0z);
+            zin[q] = f >= 0.f && f < (float)g.nz;
+            iz[q] = zin[q] ? (int)f : -1;
+        }
+    }
+    const bool masked = __any_sync(0xffffffffu, !zin[0] || !zin[1]);
+    float t = tmin;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c0 = 0; c0 < nseg; c0 += SEG_MAX) {
+        const int c1 = min(nseg, c0 + SEG_MAX);
+        __syncthreads();  // the previous round's readers are done
+        if (c0 == 0 && threadIdx.x == 0) seg[0].cb = cb0;
+        for (int e = threadIdx.x; e < nxe + nye; e += PR2_THREADS) {
+            float te;
+            int r, cx, cy;  // rank; cell after the crossing
+            if (e < nxe) {
+                te = plane_t(px0 + sgx * e, R.xi0x, R.inv_ex);
+                r = e + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false);
+                cx = ix0 + sgx * (e + 1);
+                cy = iy0 + sgy * (r - e);
+            } else {
+                const int i = e - nxe;
+                te = plane_t(py0 + sgy * i, R.xi0y, R.inv_ey);
+                r = i + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true);
+                cx = ix0 + sgx * (r - i);
+                cy = iy0 + sgy * (i + 1);
+            }
+            if (r >= c0 && r < c1) seg[r - c0].t1 = te;
+            if (r + 1 >= c0 && r + 1 < c1) seg[r + 1 - c0].cb = cx * I.vsx + cy * I.vsy;
+        }
+        __syncthreads();
+        if (threadIdx.x < WALK) {  // pad to whole groups: empty segments at the last crossing
+            const Seg last = seg[c1 - 1 - c0];
+            seg[c1 - c0 + threadIdx.x] = last;
+        }
+        __syncthreads();
+        if (masked)
+            walk_segs1_x2<true>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+        else
+            walk_segs1_x2<false>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+    }
+    if (iv[0] < I.nv) I.sino[ray[0]] = acc.x * ray_norm(R, row[0], I.beam);
+    if (iv[1] < I.nv) I.sino[ray[1]] = acc.y * ray_norm(R, row[1], I.beam);
+}
+
 // a6, last step of the ray-driven backprojector: after a group of views, the
 // integer sums (z fastest) are scaled by the group's fixed-point step and
 // added to the FP32 gradient ([nz][ny][nx]; the first group writes it), then
@@ -1402,9 +1601,13 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaS
     }
     if (pb == 0) return cudaSuccess;
     const int smem = staging(B, status);
+    bool single = true;
+    for (int i = 0; i < B.n; ++i) single = single && !B.in[i].multiz;
     if (kev) cudaEventRecord(kev[0], st);
     if (smem > 0)
         k_path<0, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
+    else if (single)
+        k_path2<<<pb, PR2_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab));
     else
         k_path<0, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     counted(1);
