@@ -632,44 +632,54 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
     if (MODE == 0 && iv < I.nv) I.sino[ray] = acc * ray_norm(R, row, I.beam);
 }
 
-// a4 with two rays per thread: the projector's CTA covers the same column of
-// PR_ROWS rows with half the threads, lane l of warp w taking the rows
-// w 64 + l and w 64 + 32 + l (each load instruction still reads 32
-// consecutive rows' voxels).  The walk keeps one (x, y) path position for
-// both rays and pairs their arithmetic where it is the same operation (the
-// segment lengths as packed FP32 subtractions, the sums as packed FMAs; each
-// half rounds as the scalar operation), so the sinogram is bit-identical to
-// k_path<0>'s.  Single-crossing geometries only (no instance with multiz),
-// no staging: the launcher keeps k_path<0> otherwise.
-constexpr int PR2_THREADS = PR_ROWS / 2;
+// a4 with NR rays per thread (2 by default): the projector's CTA covers the
+// same column of PR_ROWS rows with 1 / NR of the threads, lane l of warp w
+// taking the rows w 32 NR + 32 q + l, q < NR (each load instruction still
+// reads 32 consecutive rows' voxels).  The walk keeps one (x, y) path
+// position for all NR rays and pairs their arithmetic where it is the same
+// operation (the segment lengths as packed FP32 subtractions, the sums as
+// packed FMAs; each half rounds as the scalar operation), so the sinogram is
+// bit-identical to k_path<0>'s.  Single-crossing geometries only (no
+// instance with multiz), no staging: the launcher keeps k_path<0> otherwise.
+constexpr int PR_NR = 2;  // rays per thread
 
-template <bool MASKZ>
-__device__ __forceinline__ void walk_segs1_x2(const float *__restrict__ vol, const Seg *seg, int c0, int r0, int r1,
-                                              int nz, float &t, float2 &acc, int (&iz)[2], float (&fz)[2],
-                                              float (&tz)[2], const int (&sgz)[2], const float (&xi0z)[2],
-                                              const float (&iez)[2]) {
-    constexpr int NW = WALK;
+template <bool MASKZ, int NR>
+__device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, const Seg *seg, int c0, int r0, int r1,
+                                              int nz, float &t, float2 (&acc)[NR / 2], int (&iz)[NR],
+                                              float (&fz)[NR], float (&tz)[NR], const int (&sgz)[NR],
+                                              const float (&xi0z)[NR], const float (&iez)[NR]) {
+    constexpr int NW = WALK, NP = NR / 2;
     const unsigned zmax = (unsigned)(nz - 1);
-    int zc[2] = {(int)min((unsigned)iz[0], zmax), (int)min((unsigned)iz[1], zmax)};
-    const float fsg[2] = {(float)sgz[0], (float)sgz[1]};
+    int zc[NR];
+    float fsg[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        zc[q] = (int)min((unsigned)iz[q], zmax);
+        fsg[q] = (float)sgz[q];
+    }
     for (int r = r0; r < r1; r += NW) {
-        float2 l0[NW], l1[NW];
-        int a0[NW][2], a1[NW][2];
+        float2 l0[NW][NP], l1[NW][NP];
+        int a0[NW][NR], a1[NW][NR];
 #pragma unroll
         for (int j = 0; j < NW; ++j) {
             const Seg S = seg[r + j - c0];  // past the round's end: padding, empty segments
             const float t1 = S.t1;
-            const float m0 = fminf(tz[0], t1), m1 = fminf(tz[1], t1);
-            float2 d = __fadd2_rn(make_float2(m0, m1), make_float2(-t, -t));
-            if (MASKZ) {
-                d.x = (unsigned)iz[0] <= zmax ? d.x : 0.f;
-                d.y = (unsigned)iz[1] <= zmax ? d.y : 0.f;
-            }
-            l0[j] = d;
-            a0[j][0] = S.cb + zc[0];
-            a0[j][1] = S.cb + zc[1];
+            float m[NR];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NR; ++q) m[q] = fminf(tz[q], t1);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float2 d = __fadd2_rn(make_float2(m[2 * p], m[2 * p + 1]), make_float2(-t, -t));
+                if (MASKZ) {
+                    d.x = (unsigned)iz[2 * p] <= zmax ? d.x : 0.f;
+                    d.y = (unsigned)iz[2 * p + 1] <= zmax ? d.y : 0.f;
+                }
+                l0[j][p] = d;
+            }
+#pragma unroll
+            for (int q = 0; q < NR; ++q) a0[j][q] = S.cb + zc[q];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
                 if (tz[q] < t1) {
                     iz[q] += sgz[q];
                     fz[q] += fsg[q];
@@ -678,30 +688,40 @@ __device__ __forceinline__ void walk_segs1_x2(const float *__restrict__ vol, con
                 }
             }
             // at most one z crossing per cell: the second segment is t1 - m
-            d = __fadd2_rn(make_float2(t1, t1), make_float2(-m0, -m1));
-            if (MASKZ) {
-                d.x = (unsigned)iz[0] <= zmax ? d.x : 0.f;
-                d.y = (unsigned)iz[1] <= zmax ? d.y : 0.f;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float2 d = __fadd2_rn(make_float2(t1, t1), make_float2(-m[2 * p], -m[2 * p + 1]));
+                if (MASKZ) {
+                    d.x = (unsigned)iz[2 * p] <= zmax ? d.x : 0.f;
+                    d.y = (unsigned)iz[2 * p + 1] <= zmax ? d.y : 0.f;
+                }
+                l1[j][p] = d;
             }
-            l1[j] = d;
-            a1[j][0] = S.cb + zc[0];
-            a1[j][1] = S.cb + zc[1];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) a1[j][q] = S.cb + zc[q];
             t = t1;
         }
-        float2 v0[NW], v1[NW];
+        float2 v0[NW][NP], v1[NW][NP];
 #pragma unroll
-        for (int j = 0; j < NW; ++j) {
-            v0[j] = make_float2(__ldg(vol + a0[j][0]), __ldg(vol + a0[j][1]));
-            // the second segment's voxel only after a crossing (else its length is 0)
-            v1[j] = make_float2(l1[j].x != 0.f ? __ldg(vol + a1[j][0]) : 0.f,
-                                l1[j].y != 0.f ? __ldg(vol + a1[j][1]) : 0.f);
-        }
+        for (int j = 0; j < NW; ++j)
 #pragma unroll
-        for (int j = 0; j < NW; ++j) acc = __ffma2_rn(l1[j], v1[j], __ffma2_rn(l0[j], v0[j], acc));
+            for (int p = 0; p < NP; ++p) {
+                v0[j][p] = make_float2(__ldg(vol + a0[j][2 * p]), __ldg(vol + a0[j][2 * p + 1]));
+                // the second segment's voxel only after a crossing (else its length is 0)
+                v1[j][p] = make_float2(l1[j][p].x != 0.f ? __ldg(vol + a1[j][2 * p]) : 0.f,
+                                       l1[j][p].y != 0.f ? __ldg(vol + a1[j][2 * p + 1]) : 0.f);
+            }
+#pragma unroll
+        for (int j = 0; j < NW; ++j)
+#pragma unroll
+            for (int p = 0; p < NP; ++p) acc[p] = __ffma2_rn(l1[j][p], v1[j][p], __ffma2_rn(l0[j][p], v0[j][p], acc[p]));
     }
 }
 
-__global__ void __launch_bounds__(PR2_THREADS) k_path2(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base) {
+template <int NR>
+__global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base) {
+    static_assert(NR % 2 == 0 && PR_ROWS % (32 * NR) == 0, "pairs of rays, whole warps");
+    constexpr int NT = PR_ROWS / NR, NP = NR / 2;
     __shared__ Seg seg[SEG_MAX + WALK];
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
     int ii = 0;
@@ -711,14 +731,13 @@ __global__ void __launch_bounds__(PR2_THREADS) k_path2(const __grid_constant__ B
     const int b = blockIdx.x - I.pb0;
     const int iu = b % I.nu, rg = (b / I.nu) % I.npv, k = I.kv0 + b / (I.nu * I.npv);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int iv[2];
-    iv[0] = rg * PR_ROWS + w * 64 + lane;
-    iv[1] = iv[0] + 32;
     const RayXY R = T.tab[I.tab0 + k * I.nu + iu];
-    RowZ row[2];
-    size_t ray[2];
+    int iv[NR];
+    RowZ row[NR];
+    size_t ray[NR];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NR; ++q) {
+        iv[q] = rg * PR_ROWS + w * 32 * NR + 32 * q + lane;
         row[q] = T.rows[I.row0 + min(iv[q], I.nv - 1)];
         ray[q] = ((size_t)k * I.nv + min(iv[q], I.nv - 1)) * I.nu + iu;
     }
@@ -744,7 +763,7 @@ __global__ void __launch_bounds__(PR2_THREADS) k_path2(const __grid_constant__ B
     }
     if (miss || !(tmax > tmin)) {  // CTA-uniform
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < NR; ++q)
             if (iv[q] < I.nv) I.sino[ray[q]] = 0.f;
         return;
     }
@@ -767,38 +786,42 @@ __global__ void __launch_bounds__(PR2_THREADS) k_path2(const __grid_constant__ B
     const int nseg = rend + 1;
     const int cb0 = ix0 * I.vsx + iy0 * I.vsy;
     // each ray's z: entry layer (unbounded), next crossing, whether it stays in the z range
-    int iz[2], sgz[2];
-    float tz[2], fz[2], xi0z[2], iez[2];
-    bool zin[2];
+    int iz[NR], sgz[NR];
+    float tz[NR], fz[NR], xi0z[NR], iez[NR];
+    bool out = false;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NR; ++q) {
         const RayZ Z = ray_z(R, row[q], I.zoff);
         xi0z[q] = Z.xi0z;
         iez[q] = Z.inv_ez;
         sgz[q] = 0;
         tz[q] = INFINITY;
         fz[q] = 0.f;
+        bool zin;
         if (Z.ez != 0.f) {
             sgz[q] = Z.ez > 0.f ? 1 : -1;
             const float t0 = plane_t(0, Z.xi0z, Z.inv_ez), t1 = plane_t(g.nz, Z.xi0z, Z.inv_ez);
-            zin[q] = fminf(t0, t1) <= tmin && fmaxf(t0, t1) >= tmax;
+            zin = fminf(t0, t1) <= tmin && fmaxf(t0, t1) >= tmax;
             iz[q] = entry_cell(tmin, Z.ez, Z.xi0z, Z.inv_ez, sgz[q], INT_MIN / 2, INT_MAX / 2);
             fz[q] = (float)(sgz[q] > 0 ? iz[q] + 1 : iz[q]);
             tz[q] = (fz[q] - Z.xi0z) * Z.inv_ez;
         } else {
             const float f = floorf(Z.xi0z);
-            zin[q] = f >= 0.f && f < (float)g.nz;
-            iz[q] = zin[q] ? (int)f : -1;
+            zin = f >= 0.f && f < (float)g.nz;
+            iz[q] = zin ? (int)f : -1;
         }
+        out = out || !zin;
     }
-    const bool masked = __any_sync(0xffffffffu, !zin[0] || !zin[1]);
+    const bool masked = __any_sync(0xffffffffu, out);
     float t = tmin;
-    float2 acc = make_float2(0.f, 0.f);
+    float2 acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
     for (int c0 = 0; c0 < nseg; c0 += SEG_MAX) {
         const int c1 = min(nseg, c0 + SEG_MAX);
         __syncthreads();  // the previous round's readers are done
         if (c0 == 0 && threadIdx.x == 0) seg[0].cb = cb0;
-        for (int e = threadIdx.x; e < nxe + nye; e += PR2_THREADS) {
+        for (int e = threadIdx.x; e < nxe + nye; e += NT) {
             float te;
             int r, cx, cy;  // rank; cell after the crossing
             if (e < nxe) {
@@ -823,12 +846,15 @@ __global__ void __launch_bounds__(PR2_THREADS) k_path2(const __grid_constant__ B
         }
         __syncthreads();
         if (masked)
-            walk_segs1_x2<true>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1_xn<true, NR>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
         else
-            walk_segs1_x2<false>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1_xn<false, NR>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
     }
-    if (iv[0] < I.nv) I.sino[ray[0]] = acc.x * ray_norm(R, row[0], I.beam);
-    if (iv[1] < I.nv) I.sino[ray[1]] = acc.y * ray_norm(R, row[1], I.beam);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (iv[2 * p] < I.nv) I.sino[ray[2 * p]] = acc[p].x * ray_norm(R, row[2 * p], I.beam);
+        if (iv[2 * p + 1] < I.nv) I.sino[ray[2 * p + 1]] = acc[p].y * ray_norm(R, row[2 * p + 1], I.beam);
+    }
 }
 
 // a6, last step of the ray-driven backprojector: after a group of views, the
@@ -1607,7 +1633,7 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaS
     if (smem > 0)
         k_path<0, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     else if (single)
-        k_path2<<<pb, PR2_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab));
+        k_path_n<PR_NR><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab));
     else
         k_path<0, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     counted(1);
