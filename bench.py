@@ -305,8 +305,8 @@ def run_ours(args, dist, rank, local):
                 launches=launches, clocks=clk, t_wall=t_wall, loss=float(loss_host[-1].item()))
 
 
-KERNEL_NAMES = {"project": "k_path<0> (projector walk)",
-                "backproject": "k_path<1> (backprojector walk + fixed-point scatter)",
+KERNEL_NAMES = {"project": "k_path_n<0, 2> (projector walk, two rays per thread)",
+                "backproject": "k_path_n<1, 2> (backprojector walk + fixed-point scatter, two rays per thread)",
                 "voxelize": "k_voxelize (tile evaluation)",
                 "voxelize_backward": "k_bwd_items (per-item moments of the FVR adjoint)"}
 

@@ -643,12 +643,17 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
 // instance with multiz), no staging: the launcher keeps k_path<0> otherwise.
 constexpr int PR_NR = 2;  // rays per thread
 
-template <bool MASKZ, int NR>
-__device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, const Seg *seg, int c0, int r0, int r1,
+// MODE 0: acc += length x volume value; MODE 1: the integer sums at the same
+// voxels += round(length x wq), as walk_segs1.
+template <int MODE, bool MASKZ, int NR>
+__device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, int *__restrict__ acci,
+                                              const float2 (&wqv)[NR / 2], const Seg *seg, int c0, int r0, int r1,
                                               int nz, float &t, float2 (&acc)[NR / 2], int (&iz)[NR],
                                               float (&fz)[NR], float (&tz)[NR], const int (&sgz)[NR],
                                               const float (&xi0z)[NR], const float (&iez)[NR]) {
-    constexpr int NW = WALK, NP = NR / 2;
+    // segments per unrolled group: 4 loads in flight for the projector; the
+    // scatter keeps 2 (fewer registers)
+    constexpr int NW = MODE == 0 ? WALK : 2, NP = NR / 2;
     const unsigned zmax = (unsigned)(nz - 1);
     int zc[NR];
     float fsg[NR];
@@ -701,25 +706,45 @@ __device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, con
             for (int q = 0; q < NR; ++q) a1[j][q] = S.cb + zc[q];
             t = t1;
         }
-        float2 v0[NW][NP], v1[NW][NP];
+        if (MODE == 0) {
+            float2 v0[NW][NP], v1[NW][NP];
 #pragma unroll
-        for (int j = 0; j < NW; ++j)
+            for (int j = 0; j < NW; ++j)
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                v0[j][p] = make_float2(__ldg(vol + a0[j][2 * p]), __ldg(vol + a0[j][2 * p + 1]));
-                // the second segment's voxel only after a crossing (else its length is 0)
-                v1[j][p] = make_float2(l1[j][p].x != 0.f ? __ldg(vol + a1[j][2 * p]) : 0.f,
-                                       l1[j][p].y != 0.f ? __ldg(vol + a1[j][2 * p + 1]) : 0.f);
-            }
+                for (int p = 0; p < NP; ++p) {
+                    v0[j][p] = make_float2(__ldg(vol + a0[j][2 * p]), __ldg(vol + a0[j][2 * p + 1]));
+                    // the second segment's voxel only after a crossing (else its length is 0)
+                    v1[j][p] = make_float2(l1[j][p].x != 0.f ? __ldg(vol + a1[j][2 * p]) : 0.f,
+                                           l1[j][p].y != 0.f ? __ldg(vol + a1[j][2 * p + 1]) : 0.f);
+                }
 #pragma unroll
-        for (int j = 0; j < NW; ++j)
+            for (int j = 0; j < NW; ++j)
 #pragma unroll
-            for (int p = 0; p < NP; ++p) acc[p] = __ffma2_rn(l1[j][p], v1[j][p], __ffma2_rn(l0[j][p], v0[j][p], acc[p]));
+                for (int p = 0; p < NP; ++p)
+                    acc[p] = __ffma2_rn(l1[j][p], v1[j][p], __ffma2_rn(l0[j][p], v0[j][p], acc[p]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < NW; ++j)
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    // without a crossing the second segment is empty (q1 = 0): one
+                    // reduction; integer sums do not depend on how they are split
+                    const float2 w0 = __fmul2_rn(l0[j][p], wqv[p]), w1 = __fmul2_rn(l1[j][p], wqv[p]);
+                    const int q0a = __float2int_rn(w0.x), q0b = __float2int_rn(w0.y);
+                    const int q1a = __float2int_rn(w1.x), q1b = __float2int_rn(w1.y);
+                    atomicAdd(acci + a0[j][2 * p], q0a);
+                    atomicAdd(acci + a0[j][2 * p + 1], q0b);
+                    if (q1a != 0) atomicAdd(acci + a1[j][2 * p], q1a);
+                    if (q1b != 0) atomicAdd(acci + a1[j][2 * p + 1], q1b);
+                }
+        }
     }
 }
 
-template <int NR>
-__global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base) {
+template <int MODE, int NR>
+__global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
+                                                         const float *__restrict__ sino_s,
+                                                         const unsigned *__restrict__ view_max) {
     static_assert(NR % 2 == 0 && PR_ROWS % (32 * NR) == 0, "pairs of rays, whole warps");
     constexpr int NT = PR_ROWS / NR, NP = NR / 2;
     __shared__ Seg seg[SEG_MAX + WALK];
@@ -762,10 +787,26 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
         miss = miss || !(fy >= 0.f && fy < (float)g.ny);
     }
     if (miss || !(tmax > tmin)) {  // CTA-uniform
+        if (MODE == 0) {
 #pragma unroll
-        for (int q = 0; q < NR; ++q)
-            if (iv[q] < I.nv) I.sino[ray[q]] = 0.f;
+            for (int q = 0; q < NR; ++q)
+                if (iv[q] < I.nv) I.sino[ray[q]] = 0.f;
+        }
         return;
+    }
+    float2 wqv[NR / 2];  // MODE 1: the rows' scaled residuals in fixed point
+#pragma unroll
+    for (int p = 0; p < NR / 2; ++p) wqv[p] = make_float2(0.f, 0.f);
+    if (MODE == 1) {
+        const float S = group_step(I, view_max, I.kv0, I.nkv);
+        bool zero = true;
+#pragma unroll
+        for (int p = 0; p < NR / 2; ++p) {
+            wqv[p].x = iv[2 * p] < I.nv ? sino_s[I.ray0 + ray[2 * p]] * S : 0.f;
+            wqv[p].y = iv[2 * p + 1] < I.nv ? sino_s[I.ray0 + ray[2 * p + 1]] * S : 0.f;
+            zero = zero && wqv[p].x == 0.f && wqv[p].y == 0.f;
+        }
+        if (__syncthreads_and(zero)) return;  // nothing to add (or a bad group)
     }
     const int sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
     const int sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
@@ -846,14 +887,16 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
         }
         __syncthreads();
         if (masked)
-            walk_segs1_xn<true, NR>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1_xn<MODE, true, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
         else
-            walk_segs1_xn<false, NR>(I.vol, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1_xn<MODE, false, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
     }
+    if (MODE == 0) {
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        if (iv[2 * p] < I.nv) I.sino[ray[2 * p]] = acc[p].x * ray_norm(R, row[2 * p], I.beam);
-        if (iv[2 * p + 1] < I.nv) I.sino[ray[2 * p + 1]] = acc[p].y * ray_norm(R, row[2 * p + 1], I.beam);
+        for (int p = 0; p < NP; ++p) {
+            if (iv[2 * p] < I.nv) I.sino[ray[2 * p]] = acc[p].x * ray_norm(R, row[2 * p], I.beam);
+            if (iv[2 * p + 1] < I.nv) I.sino[ray[2 * p + 1]] = acc[p].y * ray_norm(R, row[2 * p + 1], I.beam);
+        }
     }
 }
 
@@ -1633,7 +1676,7 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaS
     if (smem > 0)
         k_path<0, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     else if (single)
-        k_path_n<PR_NR><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab));
+        k_path_n<0, PR_NR><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     else
         k_path<0, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     counted(1);
@@ -1684,8 +1727,13 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
             const int smem = staging(B, status);
             if (kev && first) cudaEventRecord(kev[0], st);
             first = false;
+            bool single = true;
+            for (int i = 0; i < B.n; ++i) single = single && !B.in[i].multiz;
             if (smem > 0)
                 k_path<1, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
+            else if (single)
+                k_path_n<1, PR_NR><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled,
+                                                                  view_max);
             else
                 k_path<1, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
             counted(1);
