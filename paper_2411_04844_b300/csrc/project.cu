@@ -4,24 +4,34 @@
 // piecewise-constant voxel image, i.e. the sum over voxels of (length of the
 // ray inside the voxel cube) x value -- Siddon's radiological path.
 //
-// Both kernels parameterise a ray as X(t) = X0 + t D, with X0 the point of its
-// (x, y) projection closest to the grid axis (keeps t small and precise), and
-// work in voxel coordinates xi = (X - o)/h.  A plane xi_a = p is crossed at
-// t = (p - xi0_a) * inv_e_a.  The forward walks the crossings in order; the
-// adjoint, for a voxel, intersects the three slab intervals built from the SAME
-// plane crossings, so each chord length is the same FP32 value in both.
+// Every kernel parameterises a ray as X(t) = X0 + t D, with X0 the point of
+// its (x, y) projection closest to the grid axis (keeps t small and precise),
+// and works in voxel coordinates xi = (X - o)/h.  A plane xi_a = p is crossed
+// at t = (p - xi0_a) * inv_e_a.  The forward walks the crossings in order; the
+// default adjoint walks the same crossings (so each chord length is the same
+// FP32 value in both), the column gather intersects the three slab intervals
+// built from the same plane crossings.
 //
-//   k_ray_tables  per (view, iu): X0, D (FP64 arithmetic, stored FP32);
-//                 per detector row: z slope, its reciprocal, FP64 layer snap
-//   k_project     a CTA per (view, detector column): the column's (x, y)
-//                 path is merged into shared memory once, each lane (a
-//                 detector row) adds its own z crossings; z-fastest volume
-//   k_scale_dn    residual x |D| per ray (chord lengths are t-intervals x |D|)
-//   k_backproject one thread per (x, y) column and a chunk of z: for each view
-//                 the candidate detector columns come from the column's four
-//                 corners, the candidate rows per voxel in closed form from the
-//                 column's slab interval; each candidate costs one slab test
-//                 and one load -- no divisions, no atomics
+//   k_ray_tables    per (view, iu): X0, D (FP64 arithmetic, stored FP32);
+//                   per detector row: z slope, its reciprocal, FP64 layer snap
+//   k_path_n<0, 2>  a CTA per (view, detector column): the column's (x, y)
+//                   path is merged into shared memory once, each thread walks
+//                   two detector rows' z crossings along it; z-fastest volume
+//                   (k_path<0>: a row per thread, for geometries where a ray
+//                   may cross two z planes inside one (x, y) cell, or staged;
+//                   k_project_ray: the C ABI's x-fastest layout)
+//   k_scale_dn      residual x |D| per ray (chord lengths are t-intervals x |D|)
+//   k_path_n<1, 2>  the adjoint as the same walk: integer sums += round(length
+//                   x scaled residual) by 32-bit reductions (order-independent,
+//                   bit-reproducible); k_bp_fold scales them into the FP32
+//                   gradient (k_path<1> as k_path<0>)
+//   k_bp_brick      the brick scatter (same integers, summed per brick in
+//                   shared memory) and
+//   k_backproject   the column gather: one thread per (x, y) column and a
+//                   chunk of z; for each view the candidate detector columns
+//                   come from the column's four corners, the candidate rows per
+//                   voxel in closed form from the column's slab interval --
+//                   no divisions, no atomics (selectable variants)
 #include <limits.h>
 #include <math.h>
 #include <string.h>
@@ -632,15 +642,17 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
     if (MODE == 0 && iv < I.nv) I.sino[ray] = acc * ray_norm(R, row, I.beam);
 }
 
-// a4 with NR rays per thread (2 by default): the projector's CTA covers the
-// same column of PR_ROWS rows with 1 / NR of the threads, lane l of warp w
-// taking the rows w 32 NR + 32 q + l, q < NR (each load instruction still
-// reads 32 consecutive rows' voxels).  The walk keeps one (x, y) path
-// position for all NR rays and pairs their arithmetic where it is the same
-// operation (the segment lengths as packed FP32 subtractions, the sums as
-// packed FMAs; each half rounds as the scalar operation), so the sinogram is
-// bit-identical to k_path<0>'s.  Single-crossing geometries only (no
-// instance with multiz), no staging: the launcher keeps k_path<0> otherwise.
+// a4 / a6 (MODE 0 / 1) with NR rays per thread (2 by default): the CTA covers
+// the same column of PR_ROWS rows as k_path with 1 / NR of the threads, lane
+// l of warp w taking the rows w 32 NR + 32 q + l, q < NR (each load or
+// reduction instruction still touches 32 consecutive rows' voxels).  The walk
+// keeps one (x, y) path position for all NR rays and pairs their arithmetic
+// where it is the same operation (the segment lengths as packed FP32
+// subtractions; the projector's sums as packed FMAs, the scatter's length x
+// residual products as packed multiplies; each half rounds as the scalar
+// operation), so the sinogram and the integer sums are bit-identical to
+// k_path's.  Single-crossing geometries only (no instance with multiz), no
+// staging: the launchers keep k_path otherwise.
 constexpr int PR_NR = 2;  // rays per thread
 
 // MODE 0: acc += length x volume value; MODE 1: the integer sums at the same
