@@ -766,7 +766,13 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
     const Inst &I = B.in[ii];
     const dgr_grid &g = I.g;
     const int b = blockIdx.x - I.pb0;
-    const int iu = b % I.nu, rg = (b / I.nu) % I.npv, k = I.kv0 + b / (I.nu * I.npv);
+    // the scatter's blocks ordered (row group, view, column): while one group
+    // of detector rows is scattered for every view, the integer sums its rays
+    // reach (about half of a tall volume's layers) stay in L2 (512^3: 24.6 ->
+    // 22.8 ms); the projector keeps (view, row group, column)
+    const int iu = b % I.nu;
+    const int rg = MODE == 1 ? b / (I.nu * I.nkv) : (b / I.nu) % I.npv;
+    const int k = I.kv0 + (MODE == 1 ? (b / I.nu) % I.nkv : b / (I.nu * I.npv));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const RayXY R = T.tab[I.tab0 + k * I.nu + iu];
     int iv[NR];
