@@ -302,8 +302,9 @@ __global__ void k_tile_fill(const __grid_constant__ Batch B, const Prep *__restr
     }
 }
 
-// a2: sort each tile's list ascending.  Up to SORT_SMEM entries: bitonic
-// sort in shared memory (padded there with +inf).  Longer lists: sort chunks
+// a2: sort each tile's list ascending.  Up to WSORT_MAX entries: a warp in
+// registers (below); up to SORT_SMEM entries: bitonic sort in shared memory
+// (padded there with +inf).  Longer lists: sort chunks
 // of SORT_SMEM in shared memory the same way, then merge runs pairwise
 // (width doubling) through a scratch list of the same layout, each output
 // position finding its source by a co-rank (merge-path) binary search.
@@ -347,6 +348,78 @@ __device__ __forceinline__ int corank(int k, const uint32_t *A, int alen, const 
     return lo;
 }
 
+// Lists of at most WSORT_MAX entries are sorted by one warp in registers
+// (k_tile_sort_warp); k_tile_sort takes the longer ones.
+constexpr int WSORT_MAX = 256;
+
+// bitonic sort of the 32 E values of a warp, ascending in i = lane E + r:
+// partners in other lanes through shuffles, in the same lane by register
+__device__ __forceinline__ uint32_t umin_(uint32_t a, uint32_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t umax_(uint32_t a, uint32_t b) { return a < b ? b : a; }
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint32_t (&v)[E], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                const int lj = j / E;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const bool up = ((lane * E + r) & k) == 0;
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, v[r], lj);
+                    v[r] = lower == up ? umin_(v[r], o) : umax_(v[r], o);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int q = r ^ j;
+                    if (q > r) {
+                        const bool up = ((lane * E + r) & k) == 0;
+                        const uint32_t a = v[r], b = v[q];
+                        v[r] = up ? umin_(a, b) : umax_(a, b);
+                        v[q] = up ? umax_(a, b) : umin_(a, b);
+                    }
+                }
+            }
+        }
+    }
+}
+template <int E>
+__device__ __forceinline__ void warp_sort_list(uint32_t *seg, int m, int lane) {
+    uint32_t v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = lane * E + r;
+        v[r] = i < m ? seg[i] : 0xffffffffu;
+    }
+    warp_bitonic<E>(v, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = lane * E + r;
+        if (i < m) seg[i] = v[r];
+    }
+}
+
+// a2: a warp per tile sorts lists of 2 .. WSORT_MAX entries
+__global__ void __launch_bounds__(256) k_tile_sort_warp(int ntiles, const uint32_t *__restrict__ tile_off,
+                                                        uint32_t *__restrict__ list, unsigned long long cap) {
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    unsigned long long b = tile_off[t], e = tile_off[t + 1];
+    if (e > cap) e = cap;
+    if (b >= e) return;
+    const int m = (int)(e - b);
+    if (m < 2 || m > WSORT_MAX) return;
+    uint32_t *seg = list + b;
+    if (m <= 32) warp_sort_list<1>(seg, m, lane);
+    else if (m <= 64) warp_sort_list<2>(seg, m, lane);
+    else if (m <= 128) warp_sort_list<4>(seg, m, lane);
+    else warp_sort_list<8>(seg, m, lane);
+}
+
 __global__ void k_tile_sort(int ntiles, const uint32_t *__restrict__ tile_off,
                             uint32_t *__restrict__ list, uint32_t *__restrict__ scratch,
                             unsigned long long cap) {
@@ -356,7 +429,7 @@ __global__ void k_tile_sort(int ntiles, const uint32_t *__restrict__ tile_off,
     if (e > cap) e = cap;
     if (b >= e) return;
     const int m = (int)(e - b);
-    if (m < 2) return;
+    if (m <= WSORT_MAX) return;  // k_tile_sort_warp
     uint32_t *seg = list + b;
     if (m <= SORT_SMEM) {
         sort_chunk(seg, m, sm);
@@ -825,9 +898,10 @@ cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int de
         counted(1);
     }
     if (deterministic) {
+        k_tile_sort_warp<<<(B.tot_tiles + 7) / 8, 256, 0, st>>>(B.tot_tiles, tile_off, list, cap);
         k_tile_sort<<<B.tot_tiles, SORT_THREADS, 0, st>>>(B.tot_tiles, tile_off, list,
                                                           ws_ptr<uint32_t>(ws, ws->list_tmp), cap);
-        counted(1);
+        counted(2);
     }
     // persistent: enough CTAs to fill every SM, each pulling tiles from the queue
     const int *sep_flag = ws_ptr<int>(ws, ws->status) + SEP_FLAG;
