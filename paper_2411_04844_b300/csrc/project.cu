@@ -211,6 +211,77 @@ __device__ __forceinline__ int count_before(float T, int n, int p0, int sg, floa
     return lo;
 }
 
+// the (x, y) path of a column through the whole grid, shared by every ray of a
+// CTA: entry cell (ix0, iy0), the crossings ahead -- x planes px0 + sgx j for
+// j < nxe, the last one leaving the grid, likewise y -- and the number of
+// segments, which ends at the first leaving crossing
+struct PathXY {
+    int sgx, sgy, ix0, iy0, nxe, nye, px0, py0, nseg, cb0;
+};
+
+__device__ __forceinline__ PathXY xy_path(const RayXY &R, const Inst &I, float tmin, float fx, float fy) {
+    const dgr_grid &g = I.g;
+    PathXY P;
+    P.sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
+    P.sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
+    P.ix0 = P.sgx ? entry_cell(tmin, R.ex, R.xi0x, R.inv_ex, P.sgx, 0, g.nx - 1) : (int)fx;
+    P.iy0 = P.sgy ? entry_cell(tmin, R.ey, R.xi0y, R.inv_ey, P.sgy, 0, g.ny - 1) : (int)fy;
+    P.nxe = P.sgx > 0 ? g.nx - P.ix0 : (P.sgx < 0 ? P.ix0 + 1 : 0);
+    P.nye = P.sgy > 0 ? g.ny - P.iy0 : (P.sgy < 0 ? P.iy0 + 1 : 0);
+    P.px0 = P.sgx > 0 ? P.ix0 + 1 : P.ix0;
+    P.py0 = P.sgy > 0 ? P.iy0 + 1 : P.iy0;
+    int rend = INT_MAX;
+    if (P.nxe > 0) {
+        const float te = plane_t(P.px0 + P.sgx * (P.nxe - 1), R.xi0x, R.inv_ex);
+        rend = min(rend, P.nxe - 1 + count_before(te, P.nye, P.py0, P.sgy, R.xi0y, R.inv_ey, false));
+    }
+    if (P.nye > 0) {
+        const float te = plane_t(P.py0 + P.sgy * (P.nye - 1), R.xi0y, R.inv_ey);
+        rend = min(rend, P.nye - 1 + count_before(te, P.nxe, P.px0, P.sgx, R.xi0x, R.inv_ex, true));
+    }
+    P.nseg = rend + 1;  // segments 0 .. rend
+    P.cb0 = P.ix0 * I.vsx + P.iy0 * I.vsy;
+    return P;
+}
+
+// segments c0 .. c1 - 1 of the path into seg[0 .. c1 - c0), each with its cell
+// and leaving parameter, then WALK copies of the last one (empty segments at
+// the last crossing, so groups are whole).  Every crossing finds its rank r in
+// the merged x/y order by a binary search of the other axis; NT threads of the
+// CTA take the crossings in turn.  Synchronises before (the previous round's
+// readers are done) and after.
+template <int NT>
+__device__ __forceinline__ void stage_segs(Seg *seg, const PathXY &P, const RayXY &R, const Inst &I, int c0,
+                                           int c1) {
+    __syncthreads();
+    if (c0 == 0 && threadIdx.x == 0) seg[0].cb = P.cb0;
+    for (int e = threadIdx.x; e < P.nxe + P.nye; e += NT) {
+        float te;
+        int r, cx, cy;  // rank; cell after the crossing
+        if (e < P.nxe) {
+            te = plane_t(P.px0 + P.sgx * e, R.xi0x, R.inv_ex);
+            r = e + count_before(te, P.nye, P.py0, P.sgy, R.xi0y, R.inv_ey, false);
+            cx = P.ix0 + P.sgx * (e + 1);
+            cy = P.iy0 + P.sgy * (r - e);
+        } else {
+            const int i = e - P.nxe;
+            te = plane_t(P.py0 + P.sgy * i, R.xi0y, R.inv_ey);
+            r = i + count_before(te, P.nxe, P.px0, P.sgx, R.xi0x, R.inv_ex, true);
+            cx = P.ix0 + P.sgx * (r - i);
+            cy = P.iy0 + P.sgy * (i + 1);
+        }
+        if (r >= c0 && r < c1) seg[r - c0].t1 = te;
+        // r + 1 < c1 <= nseg: the crossing is not the leaving one, the cell is inside
+        if (r + 1 >= c0 && r + 1 < c1) seg[r + 1 - c0].cb = cx * I.vsx + cy * I.vsy;
+    }
+    __syncthreads();
+    if (threadIdx.x < WALK) {
+        const Seg last = seg[c1 - 1 - c0];
+        seg[c1 - c0 + threadIdx.x] = last;
+    }
+    __syncthreads();
+}
+
 // fixed-point step of one group of nkv <= VGROUP views of an instance: the
 // largest power of two S with nkv x col_u x col_v x (longest chord in t units) x
 // max |scaled residual| x S < 2^30, so that a voxel's integer sum over the
@@ -471,26 +542,8 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
         wq = iv < I.nv ? sino_s[I.ray0 + ray] * S : 0.f;
         if (__syncthreads_and(wq == 0.f)) return;  // nothing to add (or a bad group)
     }
-    const int sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
-    const int sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
-    const int ix0 = sgx ? entry_cell(tmin, R.ex, R.xi0x, R.inv_ex, sgx, 0, g.nx - 1) : (int)fx;
-    const int iy0 = sgy ? entry_cell(tmin, R.ey, R.xi0y, R.inv_ey, sgy, 0, g.ny - 1) : (int)fy;
-    // crossings ahead: x planes px0 + sgx j, j < nxe (the last one leaves the
-    // grid), likewise y; the walk ends at the first leaving crossing
-    const int nxe = sgx > 0 ? g.nx - ix0 : (sgx < 0 ? ix0 + 1 : 0);
-    const int nye = sgy > 0 ? g.ny - iy0 : (sgy < 0 ? iy0 + 1 : 0);
-    const int px0 = sgx > 0 ? ix0 + 1 : ix0, py0 = sgy > 0 ? iy0 + 1 : iy0;
-    int rend = INT_MAX;
-    if (nxe > 0) {
-        const float te = plane_t(px0 + sgx * (nxe - 1), R.xi0x, R.inv_ex);
-        rend = min(rend, nxe - 1 + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false));
-    }
-    if (nye > 0) {
-        const float te = plane_t(py0 + sgy * (nye - 1), R.xi0y, R.inv_ey);
-        rend = min(rend, nye - 1 + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true));
-    }
-    const int nseg = rend + 1;  // segments 0 .. rend
-    const int cb0 = ix0 * I.vsx + iy0 * I.vsy;
+    const PathXY P = xy_path(R, I, tmin, fx, fy);
+    const int nseg = P.nseg;
     // this lane's z: entry layer (unbounded), next crossing, and whether the
     // ray stays inside the z range over the whole (x, y) chord
     const RayZ Z = ray_z(R, row, I.zoff);
@@ -554,33 +607,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
     int use = 0;  // sub-chunks processed (stage = use & 1, phase = (use >> 1) & 1)
     for (int c0 = 0; c0 < nseg; c0 += SEG_MAX) {
         const int c1 = min(nseg, c0 + SEG_MAX);
-        __syncthreads();  // the previous round's readers are done
-        if (c0 == 0 && threadIdx.x == 0) seg[0].cb = cb0;
-        for (int e = threadIdx.x; e < nxe + nye; e += PR_THREADS) {
-            float te;
-            int r, cx, cy;  // rank; cell after the crossing
-            if (e < nxe) {
-                te = plane_t(px0 + sgx * e, R.xi0x, R.inv_ex);
-                r = e + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false);
-                cx = ix0 + sgx * (e + 1);
-                cy = iy0 + sgy * (r - e);
-            } else {
-                const int i = e - nxe;
-                te = plane_t(py0 + sgy * i, R.xi0y, R.inv_ey);
-                r = i + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true);
-                cx = ix0 + sgx * (r - i);
-                cy = iy0 + sgy * (i + 1);
-            }
-            if (r >= c0 && r < c1) seg[r - c0].t1 = te;
-            // r + 1 < c1 <= nseg: the crossing is not the leaving one, the cell is inside
-            if (r + 1 >= c0 && r + 1 < c1) seg[r + 1 - c0].cb = cx * I.vsx + cy * I.vsy;
-        }
-        __syncthreads();
-        if (threadIdx.x < WALK) {  // pad to whole groups: empty segments at the last crossing
-            const Seg last = seg[c1 - 1 - c0];
-            seg[c1 - c0 + threadIdx.x] = last;
-        }
-        __syncthreads();
+        stage_segs<PR_THREADS>(seg, P, R, I, c0, c1);
         if (!TMA || !staged) {
             walk_any<MODE, false>(I.multiz, masked, I.vol, I.acc, wq, seg, c0, c0, c1, g.nz, G, t, acc, iz,
                                   fz, tz, sgz, Z.xi0z, Z.inv_ez);
@@ -826,24 +853,8 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
         }
         if (__syncthreads_and(zero)) return;  // nothing to add (or a bad group)
     }
-    const int sgx = R.ex > 0.f ? 1 : (R.ex < 0.f ? -1 : 0);
-    const int sgy = R.ey > 0.f ? 1 : (R.ey < 0.f ? -1 : 0);
-    const int ix0 = sgx ? entry_cell(tmin, R.ex, R.xi0x, R.inv_ex, sgx, 0, g.nx - 1) : (int)fx;
-    const int iy0 = sgy ? entry_cell(tmin, R.ey, R.xi0y, R.inv_ey, sgy, 0, g.ny - 1) : (int)fy;
-    const int nxe = sgx > 0 ? g.nx - ix0 : (sgx < 0 ? ix0 + 1 : 0);
-    const int nye = sgy > 0 ? g.ny - iy0 : (sgy < 0 ? iy0 + 1 : 0);
-    const int px0 = sgx > 0 ? ix0 + 1 : ix0, py0 = sgy > 0 ? iy0 + 1 : iy0;
-    int rend = INT_MAX;
-    if (nxe > 0) {
-        const float te = plane_t(px0 + sgx * (nxe - 1), R.xi0x, R.inv_ex);
-        rend = min(rend, nxe - 1 + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false));
-    }
-    if (nye > 0) {
-        const float te = plane_t(py0 + sgy * (nye - 1), R.xi0y, R.inv_ey);
-        rend = min(rend, nye - 1 + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true));
-    }
-    const int nseg = rend + 1;
-    const int cb0 = ix0 * I.vsx + iy0 * I.vsy;
+    const PathXY P = xy_path(R, I, tmin, fx, fy);
+    const int nseg = P.nseg;
     // each ray's z: entry layer (unbounded), next crossing, whether it stays in the z range
     int iz[NR], sgz[NR];
     float tz[NR], fz[NR], xi0z[NR], iez[NR];
@@ -878,32 +889,7 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
     for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
     for (int c0 = 0; c0 < nseg; c0 += SEG_MAX) {
         const int c1 = min(nseg, c0 + SEG_MAX);
-        __syncthreads();  // the previous round's readers are done
-        if (c0 == 0 && threadIdx.x == 0) seg[0].cb = cb0;
-        for (int e = threadIdx.x; e < nxe + nye; e += NT) {
-            float te;
-            int r, cx, cy;  // rank; cell after the crossing
-            if (e < nxe) {
-                te = plane_t(px0 + sgx * e, R.xi0x, R.inv_ex);
-                r = e + count_before(te, nye, py0, sgy, R.xi0y, R.inv_ey, false);
-                cx = ix0 + sgx * (e + 1);
-                cy = iy0 + sgy * (r - e);
-            } else {
-                const int i = e - nxe;
-                te = plane_t(py0 + sgy * i, R.xi0y, R.inv_ey);
-                r = i + count_before(te, nxe, px0, sgx, R.xi0x, R.inv_ex, true);
-                cx = ix0 + sgx * (r - i);
-                cy = iy0 + sgy * (i + 1);
-            }
-            if (r >= c0 && r < c1) seg[r - c0].t1 = te;
-            if (r + 1 >= c0 && r + 1 < c1) seg[r + 1 - c0].cb = cx * I.vsx + cy * I.vsy;
-        }
-        __syncthreads();
-        if (threadIdx.x < WALK) {  // pad to whole groups: empty segments at the last crossing
-            const Seg last = seg[c1 - 1 - c0];
-            seg[c1 - c0 + threadIdx.x] = last;
-        }
-        __syncthreads();
+        stage_segs<NT>(seg, P, R, I, c0, c1);
         if (masked)
             walk_segs1_xn<MODE, true, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
         else
