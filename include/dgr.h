@@ -352,10 +352,9 @@ int dgr_step_timed(const dgr_problem *prob, const dgr_params *p, const float *me
  *    views x detector columns) return DGR_ERR_WS_TOO_SMALL; nothing runs.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current) and caches it per
- *    device ordinal; make that first call before any stream capture on the
- *    device.  The cached address is invalid after cudaDeviceReset and under a
- *    context other than the device's primary context: do not call this entry
- *    point after either.
+ *    device ordinal.  The cached address is invalid after cudaDeviceReset and
+ *    under a context other than the device's primary context: do not call
+ *    this entry point after either.
  *  - Geometries are validated exactly as by dgr_project; the table size is
  *    checked in 64-bit arithmetic (views x columns) before anything runs.
  *  - It calls no cudaMalloc, cudaFree or other allocating routine.
