@@ -497,17 +497,17 @@ __constant__ ZMask c_zmask = make_zmask();
 //        from that column's peak, in FP64 (then rounded): lanes add only
 //        offsets of at most 3.5 (x) and 7.5 (y) voxels, so the exponent keeps
 //        its precision however far the tile lies from the Gaussian's centre
-//   r1 = (l1, l2, a22, zx), r2 = (n1x, n1y, zy, 0)
+//   r1 = (l1, l2, a22, -zx), r2 = (n1x, n1y, -zy, 0)
 //   lane masks: per warp, bit l set when lane l's (x, y) column lies in the box
 //   zinfo: bits 0-3 the z groups of TZG layers the box reaches, bits 4-7 those
-//          it covers whole; rows: per group, the row (lo * TZG + hi) of the
-//          layer-mask table for a partly covered group
+//          it covers whole; bits 8 + 6 g .. 13 + 6 g: for a partly covered
+//          group g, the row (lo * TZG + hi) of the layer-mask table
 // Every value a lane computes from a record is computed with the same
 // operations, in the same order, as from the prep record itself.
 struct VisitChunk {
     float4 r0[VOX_CHUNK], r1[VOX_CHUNK], r2[VOX_CHUNK];
     unsigned lanes[VOX_THREADS / 32][VOX_CHUNK];
-    int zinfo[VOX_CHUNK], rows[VOX_CHUNK];
+    int zinfo[VOX_CHUNK];
 };
 
 // a3: persistent CTAs take tiles from a global queue (tiles of every instance
@@ -586,11 +586,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                     if (hi >= 0 && lo < TZG && zl <= zh) {
                         act |= 1 << g8;
                         if (lo <= 0 && hi >= TZG - 1) full |= 1 << g8;
-                        rows |= (max(lo, 0) * TZG + min(hi, TZG - 1)) << (8 * g8);
+                        rows |= (max(lo, 0) * TZG + min(hi, TZG - 1)) << (6 * g8);
                     }
                 }
-                vc.zinfo[j] = act | (full << 4);
-                vc.rows[j] = rows;
+                vc.zinfo[j] = act | (full << 4) | (rows << 8);
                 // the tile's centre column and middle layer relative to the
                 // Gaussian's centre, in FP64
                 const double Xc = (double)(x0 - ax) + 0.5 * (TX - 1) - (double)p0.x;
@@ -599,67 +598,63 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 const double c1 = n1.x * Xc + n1.y * Yc, c2 = n1.x * Yc - n1.y * Xc;
                 const double tau = Zc - (zz.x * Xc + zz.y * Yc);
                 vc.r0[j] = make_float4((float)c1, (float)c2, (float)tau, p0.w);
-                vc.r1[j] = make_float4(p1.x, p1.y, p1.z, p2.x);
-                vc.r2[j] = make_float4(p1.w, (float)n1.y, p2.y, 0.f);
+                vc.r1[j] = make_float4(p1.x, p1.y, p1.z, -p2.x);
+                vc.r2[j] = make_float4(p1.w, (float)n1.y, -p2.y, 0.f);
             }
             __syncthreads();
-            // this warp's visits, in list order
-            unsigned long long vis =
-                (unsigned long long)__ballot_sync(0xffffffffu, lane < nc && vc.lanes[w][lane] != 0u) |
-                ((unsigned long long)__ballot_sync(0xffffffffu, lane + 32 < nc && vc.lanes[w][lane + 32] != 0u)
-                 << 32);
             // the chunk's plain sums, z pairs in packed FP32 (each half rounds
             // exactly as the scalar FMA); a z outside a box contributes
             // exp2(-inf) = 0
             float2 cs[TZ / 2];
 #pragma unroll
             for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(0.f, 0.f);
-            while (vis) {
-                const int j = __ffsll((long long)vis) - 1;
-                vis &= vis - 1;
-                const bool in = (vc.lanes[w][j] >> lane) & 1u;
-                const float4 r0 = vc.r0[j], r1 = vc.r1[j], r2 = vc.r2[j];
-                const int zi = vc.zinfo[j], rows = vc.rows[j];
-                // the column's principal coordinates, its peak value (<= 0,
-                // already scaled) and the offset of the tile's middle layer
-                // from the peak
-                const float c1 = fmaf(r2.x, lxc, fmaf(r2.y, lyc, r0.x));
-                const float c2 = fmaf(-r2.y, lxc, fmaf(r2.x, lyc, r0.y));
-                float qm = fmaf(r1.x * c1, c1, r1.y * c2 * c2);
-                qm = in ? qm : -INFINITY;
-                const float t0 = r0.z - fmaf(r1.w, lxc, r2.z * lyc);
-                const float2 a22v = make_float2(r1.z, r1.z), qmv = make_float2(qm, qm),
-                             rv = make_float2(r0.w, r0.w);
-                float2 tv = __fadd2_rn(make_float2(t0, t0),
-                                       make_float2(-0.5f * (TZ - 1), 1.f - 0.5f * (TZ - 1)));
-                const float2 two = make_float2(2.f, 2.f), step8 = make_float2((float)TZG, (float)TZG);
+            // this warp's visits, in list order: the chunk's two halves of 32
+#pragma unroll 1
+            for (int h = 0; h < VOX_CHUNK; h += 32) {
+                unsigned vis = __ballot_sync(0xffffffffu, lane + h < nc && vc.lanes[w][lane + h] != 0u);
+                while (vis) {
+                    const int j = h + __ffs(vis) - 1;
+                    vis &= vis - 1;
+                    const bool in = (vc.lanes[w][j] >> lane) & 1u;
+                    const float4 r0 = vc.r0[j], r1 = vc.r1[j], r2 = vc.r2[j];
+                    const int zi = vc.zinfo[j];
+                    // the column's principal coordinates, its peak value (<= 0,
+                    // already scaled) and the offset of the tile's middle layer
+                    // from the peak
+                    const float c1 = fmaf(r2.x, lxc, fmaf(r2.y, lyc, r0.x));
+                    const float c2 = fmaf(-r2.y, lxc, fmaf(r2.x, lyc, r0.y));
+                    float qm = fmaf(r1.x * c1, c1, r1.y * c2 * c2);
+                    qm = in ? qm : -INFINITY;
+                    const float t0 = fmaf(r1.w, lxc, fmaf(r2.z, lyc, r0.z));
+                    const float2 a22v = make_float2(r1.z, r1.z), qmv = make_float2(qm, qm),
+                                 rv = make_float2(r0.w, r0.w);
+                    // (t, t + 1) at layers (0, 1); each pair's offsets are added to
+                    // it directly, so the pairs do not wait on one another
+                    const float2 tb = __fadd2_rn(make_float2(t0, t0),
+                                                 make_float2(-0.5f * (TZ - 1), 1.f - 0.5f * (TZ - 1)));
 #pragma unroll
-                for (int g8 = 0; g8 < NG; ++g8) {
-                    if (!(zi & (1 << g8))) {  // warp-uniform
-                        tv = __fadd2_rn(tv, step8);
-                        continue;
-                    }
-                    if (zi & (16 << g8)) {            // whole group in the box
+                    for (int g8 = 0; g8 < NG; ++g8) {
+                        if (!(zi & (1 << g8))) continue;  // warp-uniform
+                        if (zi & (16 << g8)) {  // whole group in the box (warp-uniform)
 #pragma unroll
-                        for (int kk = 0; kk < TZG; kk += 2) {
-                            const int k = g8 * TZG + kk;
-                            const float2 t = tv;
-                            tv = __fadd2_rn(tv, two);
-                            const float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
-                            cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
-                        }
-                    } else {
-                        const int row = (rows >> (8 * g8)) & 0xff;
-                        const float4 zm0 = c_zmask.v[row][0], zm1 = c_zmask.v[row][1];
-                        const float zmv[TZG] = {zm0.x, zm0.y, zm0.z, zm0.w, zm1.x, zm1.y, zm1.z, zm1.w};
+                            for (int kk = 0; kk < TZG; kk += 2) {
+                                const int k = g8 * TZG + kk;
+                                const float2 t = k == 0 ? tb : __fadd2_rn(tb, make_float2((float)k, (float)k));
+                                const float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
+                                cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
+                            }
+                        } else {
+                            const int row = (zi >> (8 + 6 * g8)) & 63;
+                            const float4 zm0 = c_zmask.v[row][0], zm1 = c_zmask.v[row][1];
+                            const float zmv[TZG] = {zm0.x, zm0.y, zm0.z, zm0.w, zm1.x, zm1.y, zm1.z, zm1.w};
 #pragma unroll
-                        for (int kk = 0; kk < TZG; kk += 2) {
-                            const int k = g8 * TZG + kk;
-                            const float2 t = tv;
-                            tv = __fadd2_rn(tv, two);
-                            float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
-                            q = __fadd2_rn(q, make_float2(zmv[kk], zmv[kk + 1]));
-                            cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
+                            for (int kk = 0; kk < TZG; kk += 2) {
+                                const int k = g8 * TZG + kk;
+                                const float2 t = k == 0 ? tb : __fadd2_rn(tb, make_float2((float)k, (float)k));
+                                float2 q = __ffma2_rn(__fmul2_rn(a22v, t), t, qmv);
+                                q = __fadd2_rn(q, make_float2(zmv[kk], zmv[kk + 1]));
+                                cs[k / 2] = __ffma2_rn(rv, make_float2(ex2_approx(q.x), ex2_approx(q.y)), cs[k / 2]);
+                            }
                         }
                     }
                 }
