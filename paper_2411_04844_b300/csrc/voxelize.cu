@@ -492,18 +492,18 @@ __constant__ ZMask c_zmask = make_zmask();
 // Per (tile, Gaussian) record of a staged chunk, built once per CTA by one
 // thread, so that a warp's visit of the Gaussian costs only the per-lane set-up
 // of its column's quadratic:
-//   r0 = (c1, c2, tau, rho): the principal coordinates n1 . d, n2 . d of the
-//        tile's centre column and the offset tau of the tile's middle layer
-//        from that column's peak, in FP64 (then rounded): lanes add only
-//        offsets of at most 3.5 (x) and 7.5 (y) voxels, so the exponent keeps
-//        its precision however far the tile lies from the Gaussian's centre
-//   r1 = (l1, l2, a22, -zx), r2 = (n1x, n1y, -zy, 0)
+//   r0 = (c1', c2', tau, rho): the principal coordinates n1 . d, n2 . d of the
+//        tile's centre column, scaled by s1 = sqrt(-l1) and s2 = sqrt(-l2) (the
+//        column's peak value is then -(c1'^2 + c2'^2)), and the offset tau of
+//        the tile's middle layer from that column's peak, in FP64 (then
+//        rounded): lanes add only offsets of at most 3.5 (x) and 7.5 (y)
+//        voxels, so the exponent keeps its precision however far the tile lies
+//        from the Gaussian's centre
+//   r1 = (s1 n1x, s1 n1y, a22, -zx), r2 = (-s2 n1y, s2 n1x, -zy, 0)
 //   lane masks: per warp, bit l set when lane l's (x, y) column lies in the box
 //   zinfo: bits 0-3 the z groups of TZG layers the box reaches, bits 4-7 those
 //          it covers whole; bits 8 + 6 g .. 13 + 6 g: for a partly covered
 //          group g, the row (lo * TZG + hi) of the layer-mask table
-// Every value a lane computes from a record is computed with the same
-// operations, in the same order, as from the prep record itself.
 struct VisitChunk {
     float4 r0[VOX_CHUNK], r1[VOX_CHUNK], r2[VOX_CHUNK];
     unsigned lanes[VOX_THREADS / 32][VOX_CHUNK];
@@ -551,11 +551,14 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
         const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
         const int x = x0 + (lane & 7);
         const int y = y0 + 4 * w + (lane >> 3);
-#pragma unroll
-        for (int k = 0; k < TZ; ++k) s_acc[k][threadIdx.x] = s_cmp[k][threadIdx.x] = 0.f;
-
         unsigned long long b = tile_off[tg], e = tile_off[tg + 1];
         if (e > cap) e = cap;
+        // the chunk's plain sums, z pairs in packed FP32 (each half rounds
+        // exactly as the scalar FMA); a z outside a box contributes
+        // exp2(-inf) = 0
+        float2 cs[TZ / 2];
+#pragma unroll
+        for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(0.f, 0.f);
         for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
             const int nc = (int)min((unsigned long long)VOX_CHUNK, e - c0);
             if (c0 != b) __syncthreads();
@@ -597,17 +600,14 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                 const double Zc = (double)(z0 - az) + 0.5 * (TZ - 1) - (double)p0.z;
                 const double c1 = n1.x * Xc + n1.y * Yc, c2 = n1.x * Yc - n1.y * Xc;
                 const double tau = Zc - (zz.x * Xc + zz.y * Yc);
-                vc.r0[j] = make_float4((float)c1, (float)c2, (float)tau, p0.w);
-                vc.r1[j] = make_float4(p1.x, p1.y, p1.z, -p2.x);
-                vc.r2[j] = make_float4(p1.w, (float)n1.y, -p2.y, 0.f);
+                // principal coordinates scaled by sqrt(-l1), sqrt(-l2): the peak
+                // value is then -(c1'^2 + c2'^2)
+                const double s1 = sqrtf(fmaxf(-p1.x, 0.f)), s2 = sqrtf(fmaxf(-p1.y, 0.f));
+                vc.r0[j] = make_float4((float)(s1 * c1), (float)(s2 * c2), (float)tau, p0.w);
+                vc.r1[j] = make_float4((float)(s1 * n1.x), (float)(s1 * n1.y), p1.z, -p2.x);
+                vc.r2[j] = make_float4((float)(-s2 * n1.y), (float)(s2 * n1.x), -p2.y, 0.f);
             }
             __syncthreads();
-            // the chunk's plain sums, z pairs in packed FP32 (each half rounds
-            // exactly as the scalar FMA); a z outside a box contributes
-            // exp2(-inf) = 0
-            float2 cs[TZ / 2];
-#pragma unroll
-            for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(0.f, 0.f);
             // this warp's visits, in list order: the chunk's two halves of 32
 #pragma unroll 1
             for (int h = 0; h < VOX_CHUNK; h += 32) {
@@ -621,9 +621,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
                     // the column's principal coordinates, its peak value (<= 0,
                     // already scaled) and the offset of the tile's middle layer
                     // from the peak
-                    const float c1 = fmaf(r2.x, lxc, fmaf(r2.y, lyc, r0.x));
-                    const float c2 = fmaf(-r2.y, lxc, fmaf(r2.x, lyc, r0.y));
-                    float qm = fmaf(r1.x * c1, c1, r1.y * c2 * c2);
+                    const float c1 = fmaf(r1.x, lxc, fmaf(r1.y, lyc, r0.x));
+                    const float c2 = fmaf(r2.x, lxc, fmaf(r2.y, lyc, r0.y));
+                    float qm = -fmaf(c1, c1, c2 * c2);
                     qm = in ? qm : -INFINITY;
                     const float t0 = fmaf(r1.w, lxc, fmaf(r2.z, lyc, r0.z));
                     const float2 a22v = make_float2(r1.z, r1.z), qmv = make_float2(qm, qm),
@@ -661,17 +661,38 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
             }
             // Kahan: each chunk sum joins the running sum with compensation, so
             // a voxel inside thousands of boxes keeps its FP32 sum within a few
-            // ulps of the exact sum
+            // ulps of the exact sum.  The first chunk's sum is the running sum
+            // as it stands (Kahan from zero gives the same bits); a tile of one
+            // chunk keeps it in registers.
+            const bool more = c0 + VOX_CHUNK < e;
+            if (c0 == b) {
+                if (more) {
 #pragma unroll
-            for (int k = 0; k < TZ; ++k) {
-                const float a = s_acc[k][threadIdx.x];
-                const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - s_cmp[k][threadIdx.x];
-                const float tsum = a + yv;
-                s_cmp[k][threadIdx.x] = (tsum - a) - yv;
-                s_acc[k][threadIdx.x] = tsum;
+                    for (int k = 0; k < TZ; ++k) {
+                        s_acc[k][threadIdx.x] = (k & 1) ? cs[k / 2].y : cs[k / 2].x;
+                        s_cmp[k][threadIdx.x] = 0.f;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < TZ; ++k) {
+                    const float a = s_acc[k][threadIdx.x];
+                    const float yv = ((k & 1) ? cs[k / 2].y : cs[k / 2].x) - s_cmp[k][threadIdx.x];
+                    const float tsum = a + yv;
+                    s_cmp[k][threadIdx.x] = (tsum - a) - yv;
+                    s_acc[k][threadIdx.x] = tsum;
+                }
+            }
+            if (more) {
+#pragma unroll
+                for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(0.f, 0.f);
             }
         }
-        const auto acc = [&](int k) { return s_acc[k][threadIdx.x]; };
+        if (e - b > (unsigned long long)VOX_CHUNK) {
+#pragma unroll
+            for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(s_acc[2 * k][threadIdx.x], s_acc[2 * k + 1][threadIdx.x]);
+        }
+        const auto acc = [&](int k) { return (k & 1) ? cs[k / 2].y : cs[k / 2].x; };
         if (x < g.nx && y < g.ny) {
             // element strides: x fastest (the C ABI's layout) or z fastest
             // (the step's internal layout, read by the row-warp projector)
