@@ -19,8 +19,9 @@
      every --record iterations; its target is its final PSNR - 0.1 dB;
    * learned: the same problems, initialised by the network, the same way;
    * learned + batched: all held-out problems in one dgr_step_batched graph
-     from the learned initialisation, run until every instance has reached
-     its target.
+     from the learned initialisation; after every block of --record
+     iterations the instances at their target leave the batch (re-planned,
+     graph captured again, both timed), until none is left.
    Wall times are CUDA-event times of the initialisation and of the steps up
    to (and including) the block of --record iterations in which the target
    is reached; PSNR evaluations between blocks are outside the timed
@@ -100,6 +101,46 @@ def timed_fit(probs, init_fn, iters, lr0, lr1, record, targets=None):
     return ti.ms, blocks, curves
 
 
+def retiring_fit(probs, init_fn, iters, lr0, lr1, record, targets):
+    """All problems in one batched fit (one graph replay per iteration); after
+    every block of `record` iterations the instances that reached their
+    target leave the batch (its workspace is planned again and the next block
+    captures a new graph).  Returns the total wall time (initialisation, step
+    blocks and the re-planning, each CUDA-event timed) until the last
+    instance reaches its target (None if one never does), and the iteration
+    at which each instance reached it."""
+    with Timer() as ti:
+        inits = [init_fn(p) for p in probs]
+    F = W.Fit(probs, inits, lr0, lr1, iters)
+    active = list(range(len(probs)))
+    hit = [None] * len(probs)
+    total = ti.ms
+    done = 0
+    for i, v in zip(active, F.psnrs()):
+        if v >= targets[i]:
+            hit[i] = 0
+    while done < iters:
+        keep = [j for j, i in enumerate(active) if hit[i] is None]
+        if not keep:
+            break
+        if len(keep) < len(active):
+            with Timer() as tr:
+                F.keep(keep)
+            total += tr.ms
+            active = [active[j] for j in keep]
+        k = min(record, iters - done)
+        with Timer() as tb:
+            F.step(k)
+        total += tb.ms
+        done += k
+        if F.status():
+            raise RuntimeError(f"device status {F.status():#x} in a fit")
+        for i, v in zip(active, F.psnrs()):
+            if hit[i] is None and v >= targets[i]:
+                hit[i] = done
+    return (total if all(h is not None for h in hit) else None), hit, ti.ms
+
+
 def reach(curve, target):
     """Index of the first record at or above target (None if never)."""
     return next((i for i, v in enumerate(curve) if v >= target), None)
@@ -164,8 +205,8 @@ def study(a) -> dict:
     learned = [timed_fit([p], lambda q: W.learned_init(q, net, a.ns, rng_l), a.fit_iters, a.lr0,
                          a.lr1, a.record, [t]) for p, t in zip(test, tgt)]
     rng_b = np.random.default_rng(3)
-    b_init, b_blocks, b_curves = timed_fit(test, lambda q: W.learned_init(q, net, a.ns, rng_b),
-                                           a.fit_iters, a.lr0, a.lr1, a.record, tgt)
+    batched_ms, hit_b, b_init = retiring_fit(test, lambda q: W.learned_init(q, net, a.ns, rng_b),
+                                             a.fit_iters, a.lr0, a.lr1, a.record, tgt)
     log["fit_test_s"] = round(time.time() - t2, 1)
 
     def cost(init_ms, blocks, curve, target):
@@ -176,9 +217,7 @@ def study(a) -> dict:
 
     rp = [cost(im, bl, c[0], t) for (im, bl, c), t in zip(plain, tgt)]
     rl = [cost(im, bl, c[0], t) for (im, bl, c), t in zip(learned, tgt)]
-    hit_b = [reach(c, t) for c, t in zip(b_curves, tgt)]
     ok = [r for r in rl if r[0] is not None]
-    batched_ms = (b_init + sum(b_blocks[:max(hit_b)])) if all(h is not None for h in hit_b) else None
     out = {
         "workload": f"{a.side}^3 grid, cone {a.views} views x {a.side}^2, {a.ns} Gaussians, "
                     f"{a.train} training / {a.test} held-out phantoms (40 ellipsoids, N(0,0.01^2))",
@@ -190,7 +229,9 @@ def study(a) -> dict:
         "reached_learned": f"{len(ok)}/{len(rl)}",
         "reached_learned_batched": f"{sum(h is not None for h in hit_b)}/{len(hit_b)}",
         "iters_to_target_mean": {"plain": float(np.mean([r[0] for r in rp])),
-                                 "learned": float(np.mean([r[0] for r in ok])) if ok else None},
+                                 "learned": float(np.mean([r[0] for r in ok])) if ok else None,
+                                 "learned_batched": float(np.mean([h for h in hit_b if h is not None]))
+                                 if any(h is not None for h in hit_b) else None},
         "wall_ms_to_target_per_problem_mean": {
             "plain": float(np.mean([r[1] for r in rp])),
             "learned": float(np.mean([r[1] for r in ok])) if ok else None},

@@ -189,6 +189,18 @@ class Fit:
         self.ws = dgr.Workspace(dgr.make_batch_plan([p.grid for p in self.P], [p.geom for p in self.P],
                                                     [st.n for st in self.states], pairs, items))
 
+    def keep(self, idx):
+        """Restrict the batch to the instances at positions idx: their states
+        (parameters, Adam moments, step counters) carry on; the workspace is
+        planned again for them and the next step captures a new graph."""
+        self.g = None
+        self.ws.close()
+        self.P = [self.P[i] for i in idx]
+        self.states = [self.states[i] for i in idx]
+        self.problems = [self.problems[i] for i in idx]
+        self.loss = torch.zeros(len(idx), device=self.loss.device)
+        self._plan(slack=1.6)
+
     def step(self, k=1):
         if self.g is None:
             self.g = graph.batched_step_graph(self.problems, self.states, [p.meas for p in self.P],
