@@ -114,6 +114,12 @@ def main(argv=None):
 
     ms_seq = timed(sequential)
     ms_bat = timed(g.replay)
+    # each instance's step alone (L2 flushed before it): where the sequential
+    # time goes, and how much of it batching can reach (the small instances'
+    # idle SMs and launch gaps; a large instance fills the GPU on its own)
+    ms_inst = [timed(lambda i=i: dgr.dgr_step(B["probs"][i], B["states"][i], B["meas"][i],
+                                              loss[i:i + 1], ws_s[i]))
+               for i in range(n_inst)]
     status = dgr.dgr_status(ws_b)
     out = {"workload": f"{n_inst} instances: grids {sorted(set(x.nx for x in B['grids']))}^3, "
                        f"Gaussians {min(B['ns'])}..{max(B['ns'])}, views "
@@ -121,6 +127,9 @@ def main(argv=None):
            "tile_depth": depth, "ms_per_iteration_sequential": ms_seq,
            "ms_per_iteration_batched_graph": ms_bat, "speedup": ms_seq / ms_bat,
            "iterations_per_s_all_instances_batched": 1000.0 / ms_bat, "status": status,
+           "ms_per_instance_alone": [round(x, 4) for x in ms_inst],
+           "instances": [{"side": x.nx, "gaussians": n, "views": ge.n_views}
+                         for x, n, ge in zip(B["grids"], B["ns"], B["geoms"])],
            "total_gaussians": int(sum(B["ns"])), "l2": "flushed before every iteration (256 MiB write)"}
     print(json.dumps(out))
     return 0 if status == 0 else 1

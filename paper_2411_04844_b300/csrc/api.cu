@@ -89,7 +89,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DGR_OK : DGR_ERR_CUDA; }
 struct Layout {
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
         partials, grads, vol, sino, loss_part, rayxy, sino_scaled, list_tmp, gvol, ssim_maps, ssim_g,
-        ssim_part, tv_part, dens, acc, total;
+        ssim_part, tv_part, dens, vsplit, vpart, acc, total;
     size_t scan_elems;
 };
 
@@ -144,6 +144,9 @@ Layout layout_of(const dgr_ws_plan &p) {
     L.tv_part = take(4 * tv_tiles_cap(p.max_vox, ninst));
     // densification: keys, flags, three offset scans of max_n + 1, counts
     L.dens = take(4 * (5 * ((size_t)p.max_n + 1) + 8));
+    // the voxelizer's split plan and partial slots (rewritten by every call)
+    L.vsplit = take(p.max_tiles > 0 ? 4 * split_plan_ints(p.max_tiles, ninst) : 0);
+    L.vpart = take(p.max_tiles > 0 ? 4 * (size_t)ninst * SPLIT_BUDGET * VOX_SLOT : 0);
     // integer sums of the ray-driven backprojector (z fastest), kept zero between calls
     L.acc = take(p.max_vox > 0 ? 4 * ((size_t)p.max_vox + vpad) : 0);
     L.total = o;
@@ -182,6 +185,7 @@ int dgr_ws_create(dgr_ws **ws, const dgr_ws_plan *plan) {
     w->acc = L.acc;
     w->gvol = L.gvol; w->ssim_maps = L.ssim_maps; w->ssim_g = L.ssim_g; w->ssim_part = L.ssim_part;
     w->tv_part = L.tv_part; w->dens = L.dens;
+    w->vsplit = L.vsplit; w->vpart = L.vpart;
     w->scan_tmp_elems = L.scan_elems;
     if (cudaMemset(w->base + L.status, 0, 256) != cudaSuccess ||
         cudaMemset(w->base + L.acc, 0, L.total - L.acc) != cudaSuccess) {

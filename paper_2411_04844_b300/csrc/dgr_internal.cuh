@@ -35,6 +35,44 @@ void set_tile_depth(int tz);
 constexpr int VOX_THREADS = 128;
 constexpr int VOX_CHUNK = 64;  // prep records staged in shared memory at a time
 
+// Long tile lists are cut into segments taken by different CTAs (a grid of
+// few tiles, each in the boxes of thousands of Gaussians, would otherwise
+// leave most SMs idle): each segment's sums go to a partial slot of
+// TZ_MAX x VOX_THREADS floats, the CTA finishing a tile's last segment adds
+// the slots in segment order.  Per instance at most SPLIT_BUDGET slots; a
+// tile splits into at most SPLIT_SMAX segments of at least SPLIT_LMIN list
+// entries (see plan_tile).
+constexpr int SPLIT_BUDGET = 1024;
+constexpr int SPLIT_SMAX = 16;
+constexpr int SPLIT_LMIN = 256;
+constexpr int VOX_SLOT = TZ_MAX * VOX_THREADS;
+// status-word slots: the voxelizer's unit queue head, the count of extra
+// units (segments after the first of split tiles), per-instance slot counters
+constexpr int VOX_QUEUE = 18, VOX_NEXTRA = 19, VOX_SLOTCTR = 20;  // .. VOX_SLOTCTR + MAX_INST - 1
+// workspace ints of the split plan for `tiles` tiles and `ninst` instances:
+// nseg [tiles] | slot [tiles] | done [tiles] | extra [ninst SPLIT_BUDGET]
+inline size_t split_plan_ints(long long tiles, int ninst) {
+    return (size_t)(3 * tiles + (long long)ninst * SPLIT_BUDGET);
+}
+struct VoxSplit {
+    int *nseg;   // segments of each tile (1: not split)
+    int *slot;   // first partial slot of a split tile (-1: not split)
+    int *done;   // segments of a split tile finished
+    int *extra;  // extra units: tile | segment << 24 (segments 1 .. nseg - 1 of split tiles)
+    int *ctr;    // [0] extra units; [1 + i] partial slots taken by instance i
+    float *part; // partial slots
+};
+inline VoxSplit vox_split_of(int *ints, float *part, int *status, long long tiles) {
+    VoxSplit S;
+    S.nseg = ints;
+    S.slot = ints + tiles;
+    S.done = S.slot + tiles;
+    S.extra = S.done + tiles;
+    S.ctr = status + VOX_NEXTRA;
+    S.part = part;
+    return S;
+}
+
 // Backward work item: a piece of one Gaussian's box holding at most about
 // ITEM_VOX voxels (see item_count), processed by one warp.
 constexpr int ITEM_VOX = 2048;
@@ -249,7 +287,7 @@ struct dgr_ws {
     // byte offsets into base
     size_t status, prep, itemcnt, item_off, tile_cnt, tile_off, tile_fill, scan_tmp, list,
         partials, grads, vol, sino, loss_part, rayxy, sino_scaled, losses, list_tmp, acc, gvol, ssim_maps,
-        ssim_g, ssim_part, tv_part, dens;
+        ssim_g, ssim_part, tv_part, dens, vsplit, vpart;
     size_t scan_tmp_elems;
 };
 

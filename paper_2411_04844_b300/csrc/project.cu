@@ -609,8 +609,11 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
         const int c1 = min(nseg, c0 + SEG_MAX);
         stage_segs<PR_THREADS>(seg, P, R, I, c0, c1);
         if (!TMA || !staged) {
-            walk_any<MODE, false>(I.multiz, masked, I.vol, I.acc, wq, seg, c0, c0, c1, g.nz, G, t, acc, iz,
-                                  fz, tz, sgz, Z.xi0z, Z.inv_ez);
+            // a warp whose rows all lie past the detector (nv not a multiple of
+            // the CTA's rows) only takes part in the staging
+            if (rg * PR_ROWS + w * 32 < I.nv)
+                walk_any<MODE, false>(I.multiz, masked, I.vol, I.acc, wq, seg, c0, c0, c1, g.nz, G, t, acc, iz,
+                                      fz, tz, sgz, Z.xi0z, Z.inv_ez);
             continue;
         }
         // staged: sub-chunks of tma_ch cells, their z windows in shared memory
@@ -887,9 +890,16 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
     float2 acc[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) acc[p] = make_float2(0.f, 0.f);
+    // a warp whose rows all lie past the detector (nv not a multiple of the
+    // CTA's rows) only takes part in the staging
     for (int c0 = 0; c0 < nseg; c0 += SEG_MAX) {
         const int c1 = min(nseg, c0 + SEG_MAX);
         stage_segs<NT>(seg, P, R, I, c0, c1);
+        if (MODE == 1 && c1 == nseg) {  // no barrier follows the last staging
+            const int b1 = blockIdx.x - I.pb0;
+            const int rg1 = MODE == 1 ? b1 / (I.nu * I.nkv) : (b1 / I.nu) % I.npv;
+            if (rg1 * PR_ROWS + (int)(threadIdx.x >> 5) * 32 * NR >= I.nv) return;
+        }
         if (masked)
             walk_segs1_xn<MODE, true, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
         else

@@ -348,6 +348,54 @@ __device__ __forceinline__ int corank(int k, const uint32_t *A, int alen, const 
     return lo;
 }
 
+// ---------------------------------------------------------------------------
+// Work units of the voxelizer: units 0 .. tiles - 1 are the tiles (their whole
+// list, or its first segment), then one unit per further segment of a split
+// tile
+// ---------------------------------------------------------------------------
+// a2 (once the tile lists are complete), for tile t: per instance with P list
+// entries in all, the segment length is L = max(SPLIT_LMIN, 3P / (2
+// SPLIT_BUDGET)) rounded up to whole chunks; a tile with more than 2L entries
+// takes r = min(SPLIT_SMAX, ceil(len / L)) segments and r partial slots.  As
+// len / L > 2, r < 1.5 len / L, so an instance's slots stay below 1.5 P / L
+// <= SPLIT_BUDGET: every request fits, and whether and how a tile splits
+// depends only on its own instance's lists (a batch splits exactly as its
+// instances alone).  Slots and extra units are handed out by atomic counters
+// (zeroed before): where a segment's partial sits does not change a bit of
+// the result.
+__device__ __forceinline__ void plan_tile(const Batch &B, int t, const uint32_t *__restrict__ tile_off,
+                                          unsigned long long cap, const VoxSplit &S) {
+    const int i = inst_of_tile(B, t);
+    const Inst &I = B.in[i];
+    const auto off = [&](int j) {
+        const unsigned long long o = tile_off[j];
+        return o > cap ? cap : o;
+    };
+    const unsigned long long tot = off(I.tile0 + I.ntx * I.nty * I.ntz) - off(I.tile0);
+    unsigned long long L = (3ull * tot + 2ull * SPLIT_BUDGET - 1) / (2ull * SPLIT_BUDGET);
+    if (L < (unsigned long long)SPLIT_LMIN) L = SPLIT_LMIN;
+    L = (L + VOX_CHUNK - 1) / VOX_CHUNK * VOX_CHUNK;
+    const unsigned long long b = off(t), e = off(t + 1), len = e > b ? e - b : 0;
+    const int r = len > 2ull * L ? (int)min((unsigned long long)SPLIT_SMAX, (len + L - 1) / L) : 1;
+    S.nseg[t] = r;
+    S.done[t] = 0;
+    if (r > 1) {
+        S.slot[t] = i * SPLIT_BUDGET + atomicAdd(S.ctr + 1 + i, r);
+        const int x = atomicAdd(S.ctr, r - 1);
+        for (int sg = 1; sg < r; ++sg) S.extra[x + sg - 1] = t | (sg << 24);
+    } else {
+        S.slot[t] = -1;
+    }
+}
+
+// plan_tile for every tile (when the lists are not sorted; k_tile_sort_warp
+// does it otherwise)
+__global__ void k_split_plan(const __grid_constant__ Batch B, const uint32_t *__restrict__ tile_off,
+                             unsigned long long cap, const VoxSplit S) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < B.tot_tiles) plan_tile(B, t, tile_off, cap, S);
+}
+
 // Lists of at most WSORT_MAX entries are sorted by one warp in registers
 // (k_tile_sort_warp); k_tile_sort takes the longer ones.
 constexpr int WSORT_MAX = 256;
@@ -403,11 +451,15 @@ __device__ __forceinline__ void warp_sort_list(uint32_t *seg, int m, int lane) {
 }
 
 // a2: a warp per tile sorts lists of 2 .. WSORT_MAX entries
-__global__ void __launch_bounds__(256) k_tile_sort_warp(int ntiles, const uint32_t *__restrict__ tile_off,
-                                                        uint32_t *__restrict__ list, unsigned long long cap) {
+__global__ void __launch_bounds__(256) k_tile_sort_warp(const __grid_constant__ Batch B,
+                                                        const uint32_t *__restrict__ tile_off,
+                                                        uint32_t *__restrict__ list, unsigned long long cap,
+                                                        const VoxSplit S) {
     const int lane = threadIdx.x & 31;
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int ntiles = B.tot_tiles;
     if (t >= ntiles) return;
+    if (lane == 0) plan_tile(B, t, tile_off, cap, S);  // the voxelizer's work units
     unsigned long long b = tile_off[t], e = tile_off[t + 1];
     if (e > cap) e = cap;
     if (b >= e) return;
@@ -510,6 +562,51 @@ struct VisitChunk {
     int zinfo[VOX_CHUNK];
 };
 
+// list range [b, e) of segment seg of nseg: whole chunks, the last one short
+// (possibly empty)
+__device__ __forceinline__ void segment_range(unsigned long long &b, unsigned long long &e, int nseg, int seg) {
+    const unsigned long long len = e - b;
+    unsigned long long L = (len + nseg - 1) / nseg;
+    L = (L + VOX_CHUNK - 1) / VOX_CHUNK * VOX_CHUNK;
+    const unsigned long long sb = min(e, b + (unsigned long long)seg * L);
+    e = min(e, sb + L);
+    b = sb;
+}
+
+// End of a segment of a split tile: its sums val(k), k < TZ, go to its
+// partial slot; the CTA that finishes the tile's last segment (whichever it
+// is) reads every slot of the tile and leaves in out[k][thread] the sum over
+// the segments in segment order, Kahan-compensated -- the same bits whatever
+// the order in which the segments ran.  Returns true for that CTA (it writes
+// the tile), false for the others.  CTA-uniform; flag: a shared int.
+template <int TZ, class Get>
+__device__ __forceinline__ bool fold_segments(const VoxSplit &S, int tg, int seg, int nseg, Get val,
+                                              float (*out)[VOX_THREADS], int *flag) {
+    const int slot = S.slot[tg];
+    float *mine = S.part + (size_t)(slot + seg) * VOX_SLOT + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < TZ; ++k) mine[k * VOX_THREADS] = val(k);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = atomicAdd(S.done + tg, 1) == nseg - 1;
+    __syncthreads();
+    if (!*flag) return false;
+    __threadfence();
+    const float *first = S.part + (size_t)slot * VOX_SLOT + threadIdx.x;
+#pragma unroll 1
+    for (int k = 0; k < TZ; ++k) {
+        float sum = 0.f, c = 0.f;
+        for (int s = 0; s < nseg; ++s) {
+            const float y = __ldcg(first + (size_t)s * VOX_SLOT + k * VOX_THREADS) - c;
+            const float t = sum + y;
+            c = (t - sum) - y;
+            sum = t;
+        }
+        out[k][threadIdx.x] = sum;
+    }
+    return true;
+}
+
 // a3: persistent CTAs take tiles from a global queue (tiles of every instance
 // back to back).  Warp w covers y in [ty0 + 4w, ty0 + 4w + 4), lane
 // (lx, ly) = (lane & 7, lane >> 3), and the column z in [tz0, tz0 + TZ).
@@ -525,7 +622,7 @@ template <int TZ>
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
-    unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off) {
+    unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off, const VoxSplit S) {
     static_assert(TZ / TZG <= 4, "z groups are tracked in 4-bit masks");
     constexpr int NG = TZ / TZG;
     __shared__ VisitChunk vc;
@@ -533,8 +630,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     // thread (touched by that thread only), kept out of registers so that more
     // CTAs fit on an SM
     __shared__ float s_acc[TZ][VOX_THREADS], s_cmp[TZ][VOX_THREADS];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_last;
     if (sep_off && *sep_off == 0) return;  // every Gaussian separable: k_voxelize_sep runs
+    const int n_units = B.tot_tiles + S.ctr[0];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // the lane's column relative to the tile's centre column
     const float lxc = (float)(lane & 7) - 0.5f * (TX - 1), lyc = (float)(4 * w + (lane >> 3)) - 0.5f * (TY - 1);
@@ -542,8 +640,14 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
         __syncthreads();  // everyone is done with s_tile and the records
         if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
         __syncthreads();
-        const int tg = s_tile;
-        if (tg >= B.tot_tiles) return;
+        const int u = s_tile;  // work unit: a tile or a segment of its list
+        if (u >= n_units) return;
+        int tg = u, seg = 0;
+        if (u >= B.tot_tiles) {
+            const int xu = S.extra[u - B.tot_tiles];
+            tg = xu & 0xffffff;
+            seg = xu >> 24;
+        }
         const Inst &I = B.in[inst_of_tile(B, tg)];
         const dgr_grid &g = I.g;
         const int t = tg - I.tile0;
@@ -553,6 +657,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
         const int y = y0 + 4 * w + (lane >> 3);
         unsigned long long b = tile_off[tg], e = tile_off[tg + 1];
         if (e > cap) e = cap;
+        if (b > e) b = e;
+        const int nseg = S.nseg[tg];
+        if (nseg > 1) segment_range(b, e, nseg, seg);
         // the chunk's plain sums, z pairs in packed FP32 (each half rounds
         // exactly as the scalar FMA); a z outside a box contributes
         // exp2(-inf) = 0
@@ -693,6 +800,14 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
             for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(s_acc[2 * k][threadIdx.x], s_acc[2 * k + 1][threadIdx.x]);
         }
         const auto acc = [&](int k) { return (k & 1) ? cs[k / 2].y : cs[k / 2].x; };
+        // a segment of a split tile: its partial sums; the tile's last one adds
+        // them up (through the thread's own column of s_acc, free once the
+        // sums are in registers)
+        if (nseg > 1) {
+            if (!fold_segments<TZ>(S, tg, seg, nseg, acc, s_acc, &s_last)) continue;
+#pragma unroll
+            for (int k = 0; k < TZ / 2; ++k) cs[k] = make_float2(s_acc[2 * k][threadIdx.x], s_acc[2 * k + 1][threadIdx.x]);
+        }
         if (x < g.nx && y < g.ny) {
             // element strides: x fastest (the C ABI's layout) or z fastest
             // (the step's internal layout, read by the row-warp projector)
@@ -729,20 +844,27 @@ constexpr int SEP_TZ = 32;
 __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
-    unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off) {
+    unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off, const VoxSplit S) {
     __shared__ float4 sp[VOX_CHUNK * 4];
     __shared__ __align__(16) float ez[VOX_CHUNK][SEP_TZ];
     // running sums and Kahan compensations, one column per thread (as in k_voxelize)
     __shared__ float s_acc[SEP_TZ][VOX_THREADS], s_cmp[SEP_TZ][VOX_THREADS];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_last;
     if (*sep_off != 0) return;  // a non-separable Gaussian: the general kernel runs
+    const int n_units = B.tot_tiles + S.ctr[0];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
         __syncthreads();
-        const int tg = s_tile;
-        if (tg >= B.tot_tiles) return;
+        const int u = s_tile;  // work unit: a tile or a segment of its list
+        if (u >= n_units) return;
+        int tg = u, seg = 0;
+        if (u >= B.tot_tiles) {
+            const int xu = S.extra[u - B.tot_tiles];
+            tg = xu & 0xffffff;
+            seg = xu >> 24;
+        }
         const Inst &I = B.in[inst_of_tile(B, tg)];
         const dgr_grid &g = I.g;
         const int tl = tg - I.tile0;
@@ -755,6 +877,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
         for (int k = 0; k < SEP_TZ; ++k) s_acc[k][threadIdx.x] = s_cmp[k][threadIdx.x] = 0.f;
         unsigned long long b = tile_off[tg], e = tile_off[tg + 1];
         if (e > cap) e = cap;
+        if (b > e) b = e;
+        const int nseg = S.nseg[tg];
+        if (nseg > 1) segment_range(b, e, nseg, seg);
         for (unsigned long long c0 = b; c0 < e; c0 += VOX_CHUNK) {
             const int nc = (int)min((unsigned long long)VOX_CHUNK, e - c0);
             __syncthreads();
@@ -810,6 +935,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
             }
         }
         const auto acc = [&](int k) { return s_acc[k][threadIdx.x]; };
+        if (nseg > 1 && !fold_segments<SEP_TZ>(S, tg, seg, nseg, acc, s_acc, &s_last)) continue;
         if (x < g.nx && y < g.ny) {
             float *col = I.vol + (size_t)x * I.vsx + (size_t)y * I.vsy;
             if (I.vsz == 1 && (g.nz & 3) == 0 && z0 + SEP_TZ <= g.nz &&
@@ -883,15 +1009,17 @@ cudaError_t launch_count_pairs(const Batch &B, const Prep *prep, dgr_ws *ws, uns
 template <int TZ>
 static cudaError_t launch_vox_tz(const Batch &B, const Prep *prep, const uint32_t *tile_off,
                                  const uint32_t *list, unsigned long long cap, int *queue,
-                                 const int *sep_flag, cudaStream_t st) {
-    const int grid = max(1, min(B.tot_tiles, wave_ctas((const void *)k_voxelize<TZ>, VOX_THREADS, 0)));
+                                 const int *sep_flag, const VoxSplit &S, cudaStream_t st) {
+    // work units: the tiles plus at most SPLIT_BUDGET extra segments per instance
+    const int units = B.tot_tiles + B.n * SPLIT_BUDGET;
+    const int grid = max(1, min(units, wave_ctas((const void *)k_voxelize<TZ>, VOX_THREADS, 0)));
     // depth 32: the separable kernel as well; exactly one of the two does the work
     const bool sep = TZ == SEP_TZ && g_separable;
-    k_voxelize<TZ><<<grid, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep ? sep_flag : nullptr);
+    k_voxelize<TZ><<<grid, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep ? sep_flag : nullptr, S);
     counted(1);
     if (sep) {
-        const int grid2 = max(1, min(B.tot_tiles, wave_ctas((const void *)k_voxelize_sep, VOX_THREADS, 0)));
-        k_voxelize_sep<<<grid2, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep_flag);
+        const int grid2 = max(1, min(units, wave_ctas((const void *)k_voxelize_sep, VOX_THREADS, 0)));
+        k_voxelize_sep<<<grid2, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep_flag, S);
         counted(1);
     }
     return cudaGetLastError();
@@ -902,30 +1030,36 @@ cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int de
     uint32_t *tile_off = ws_ptr<uint32_t>(ws, ws->tile_off);
     uint32_t *tile_fill = ws_ptr<uint32_t>(ws, ws->tile_fill);
     uint32_t *list = ws_ptr<uint32_t>(ws, ws->list);
-    int *queue = ws_ptr<int>(ws, ws->status) + 16;  // tile queue head
+    int *queue = ws_ptr<int>(ws, ws->status) + VOX_QUEUE;  // unit queue head
     const unsigned long long cap = (unsigned long long)ws->plan.max_pairs;
     cudaError_t err = launch_count_pairs(B, prep, ws, cap, st);
     if (err != cudaSuccess) return err;
     err = cudaMemsetAsync(tile_fill, 0, sizeof(uint32_t) * B.tot_tiles, st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    // the queue head and the split counters
+    if (err == cudaSuccess) err = cudaMemsetAsync(queue, 0, sizeof(int) * (VOX_SLOTCTR + MAX_INST - VOX_QUEUE), st);
     if (err != cudaSuccess) return err;
     if (B.tot_g > 0) {
         k_tile_fill<<<warp_grid(B.tot_g), 256, 0, st>>>(B, prep, tile_off, tile_fill, list, cap);
         counted(1);
     }
+    const VoxSplit S = vox_split_of(ws_ptr<int>(ws, ws->vsplit), ws_ptr<float>(ws, ws->vpart),
+                                    ws_ptr<int>(ws, ws->status), B.tot_tiles);
     if (deterministic) {
-        k_tile_sort_warp<<<(B.tot_tiles + 7) / 8, 256, 0, st>>>(B.tot_tiles, tile_off, list, cap);
+        k_tile_sort_warp<<<(B.tot_tiles + 7) / 8, 256, 0, st>>>(B, tile_off, list, cap, S);
         k_tile_sort<<<B.tot_tiles, SORT_THREADS, 0, st>>>(B.tot_tiles, tile_off, list,
                                                           ws_ptr<uint32_t>(ws, ws->list_tmp), cap);
         counted(2);
+    } else {
+        k_split_plan<<<(B.tot_tiles + 255) / 256, 256, 0, st>>>(B, tile_off, cap, S);
+        counted(1);
     }
-    // persistent: enough CTAs to fill every SM, each pulling tiles from the queue
+    // persistent: enough CTAs to fill every SM, each pulling units from the queue
     const int *sep_flag = ws_ptr<int>(ws, ws->status) + SEP_FLAG;
     if (kev && (err = cudaEventRecord(kev[0], st)) != cudaSuccess) return err;
     switch (B.tz) {
-        case 8: err = launch_vox_tz<8>(B, prep, tile_off, list, cap, queue, sep_flag, st); break;
-        case 16: err = launch_vox_tz<16>(B, prep, tile_off, list, cap, queue, sep_flag, st); break;
-        default: err = launch_vox_tz<32>(B, prep, tile_off, list, cap, queue, sep_flag, st);
+        case 8: err = launch_vox_tz<8>(B, prep, tile_off, list, cap, queue, sep_flag, S, st); break;
+        case 16: err = launch_vox_tz<16>(B, prep, tile_off, list, cap, queue, sep_flag, S, st); break;
+        default: err = launch_vox_tz<32>(B, prep, tile_off, list, cap, queue, sep_flag, S, st);
     }
     if (err == cudaSuccess && kev) err = cudaEventRecord(kev[1], st);
     return err;

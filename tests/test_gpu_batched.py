@@ -1,6 +1,7 @@
 """Batching (row a10): dgr_step_batched over heterogeneous instances equals the
 same instances stepped one by one with dgr_step, bit for bit (deterministic
-mode); a CUDA-graph replay equals eager steps; every voxelizer tile depth the
+mode; one instance dense enough that the voxelizer splits its tile lists);
+a CUDA-graph replay equals eager steps; every voxelizer tile depth the
 autotuner may pick gives the oracle's volume."""
 import numpy as np
 import pytest
@@ -26,10 +27,14 @@ def _instances():
          synth.cone_geom(13, 41, 31, 1.1, 1.3, 60.0, 95.0, arc=1.3), 300),
         (synth.GridSpec((40, 40, 40), 1.0, (-20.0, -20.0, -20.0)),
          synth.cone_geom(20, 50, 44, 1.5, 1.5, 120.0, 180.0), 500),
+        # few tiles holding thousands of Gaussians each: the voxelizer splits
+        # their lists over several CTAs (the same way alone and in the batch)
+        (synth.GridSpec((16, 16, 32), 1.0, (-8.0, -8.0, -16.0)), synth.parallel_geom(8, 24, 34), 4000),
     ]
     out = []
     for i, (gs, geo, n) in enumerate(specs):
-        f = synth.gaussian_field(synth.rng_for(4, 50 + i), n, gs, ("loguniform", 0.5, 3.0))
+        scale = ("loguniform", 0.5, 1.5) if n > 1000 else ("loguniform", 0.5, 3.0)
+        f = synth.gaussian_field(synth.rng_for(4, 50 + i), n, gs, scale)
         f.rho = np.clip(f.rho, 0.05, 1.0).astype(np.float32)
         meas = np.abs(np.random.default_rng(i).normal(3.0, 1.0, geo.shape)).astype(np.float32)
         out.append((gs, geo, f, meas))
