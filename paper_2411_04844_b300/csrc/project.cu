@@ -673,7 +673,8 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
 }
 
 // a4 / a6 (MODE 0 / 1) with NR rays per thread (2 by default): the CTA covers
-// the same column of PR_ROWS rows as k_path with 1 / NR of the threads, lane
+// a column of ROWS rows (PR_ROWS as k_path, or 128 / 64 for short detectors)
+// with ROWS / NR threads, lane
 // l of warp w taking the rows w 32 NR + 32 q + l, q < NR (each load or
 // reduction instruction still touches 32 consecutive rows' voxels).  The walk
 // keeps one (x, y) path position for all NR rays and pairs their arithmetic
@@ -783,12 +784,13 @@ __device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, int
     }
 }
 
-template <int MODE, int NR>
-__global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
+// (CTAs of fewer rows: as many threads per SM as the PR_ROWS CTAs at 64 registers)
+template <int MODE, int NR, int ROWS>
+__global__ void __launch_bounds__(ROWS / NR, ROWS == PR_ROWS ? 0 : 8 * PR_ROWS / ROWS) k_path_n(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
                                                          const float *__restrict__ sino_s,
                                                          const unsigned *__restrict__ view_max) {
-    static_assert(NR % 2 == 0 && PR_ROWS % (32 * NR) == 0, "pairs of rays, whole warps");
-    constexpr int NT = PR_ROWS / NR, NP = NR / 2;
+    static_assert(NR % 2 == 0 && ROWS % (32 * NR) == 0 && ROWS <= PR_ROWS, "pairs of rays, whole warps");
+    constexpr int NT = ROWS / NR, NP = NR / 2;
     __shared__ Seg seg[SEG_MAX + WALK];
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
     int ii = 0;
@@ -810,7 +812,7 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
     size_t ray[NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
-        iv[q] = rg * PR_ROWS + w * 32 * NR + 32 * q + lane;
+        iv[q] = rg * ROWS + w * 32 * NR + 32 * q + lane;
         row[q] = T.rows[I.row0 + min(iv[q], I.nv - 1)];
         ray[q] = ((size_t)k * I.nv + min(iv[q], I.nv - 1)) * I.nu + iu;
     }
@@ -898,7 +900,7 @@ __global__ void __launch_bounds__(PR_ROWS / NR) k_path_n(const __grid_constant__
         if (MODE == 1 && c1 == nseg) {  // no barrier follows the last staging
             const int b1 = blockIdx.x - I.pb0;
             const int rg1 = MODE == 1 ? b1 / (I.nu * I.nkv) : (b1 / I.nu) % I.npv;
-            if (rg1 * PR_ROWS + (int)(threadIdx.x >> 5) * 32 * NR >= I.nv) return;
+            if (rg1 * ROWS + (int)(threadIdx.x >> 5) * 32 * NR >= I.nv) return;
         }
         if (masked)
             walk_segs1_xn<MODE, true, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
@@ -1656,6 +1658,23 @@ static int staging(Batch &B, int *status) {
     return smem;
 }
 
+static bool multi_crossing(const Batch &B) {
+    for (int i = 0; i < B.n; ++i)
+        if (B.in[i].multiz) return true;
+    return false;
+}
+
+// detector rows per CTA of the path walks: the two-ray walk (single-crossing
+// geometries, unstaged) takes CTAs of 64 or 128 rows when no instance's
+// detector is taller, so short detectors do not leave half or three quarters
+// of a 256-row CTA idle; otherwise 256
+static int walk_rows(const Batch &B, int smem) {
+    if (smem > 0 || multi_crossing(B)) return PR_ROWS;
+    int nv = 0;
+    for (int i = 0; i < B.n; ++i) nv = max(nv, B.in[i].nv);
+    return nv <= 64 ? 64 : (nv <= 128 ? 128 : PR_ROWS);
+}
+
 cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaStream_t st,
                            const cudaEvent_t *kev) {
     // row-warp projector when every volume is z fastest, else per-ray
@@ -1670,29 +1689,32 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaS
         if (kev) cudaEventRecord(kev[1], st);
         return cudaGetLastError();
     }
-    // projector blocks: one detector column x PR_ROWS rows of one view
+    // projector blocks: one detector column x `rows` rows of one view
     static thread_local Batch B;
     B = B0;
+    const int smem = staging(B, status);
+    const int rows = walk_rows(B, smem);
     int pb = 0;
     for (int i = 0; i < B.n; ++i) {
         Inst &I = B.in[i];
-        I.npv = (I.nv + PR_ROWS - 1) / PR_ROWS;
+        I.npv = (I.nv + rows - 1) / rows;
         I.pb0 = pb;
         I.kv0 = 0;
         I.nkv = I.n_views;
         pb += I.n_views * I.nu * I.npv;
     }
     if (pb == 0) return cudaSuccess;
-    const int smem = staging(B, status);
-    bool single = true;
-    for (int i = 0; i < B.n; ++i) single = single && !B.in[i].multiz;
     if (kev) cudaEventRecord(kev[0], st);
     if (smem > 0)
         k_path<0, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
-    else if (single)
-        k_path_n<0, PR_NR><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
-    else
+    else if (rows == PR_ROWS && multi_crossing(B))
         k_path<0, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
+    else if (rows == PR_ROWS)
+        k_path_n<0, PR_NR, PR_ROWS><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
+    else if (rows == 128)
+        k_path_n<0, PR_NR, 128><<<pb, 128 / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
+    else
+        k_path_n<0, PR_NR, 64><<<pb, 64 / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
     counted(1);
     if (kev) cudaEventRecord(kev[1], st);
     return cudaGetLastError();
@@ -1714,12 +1736,13 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
     bool first = true;
     static thread_local Batch B;
     B = B0;
+    const int rows = walk_rows(B, staging(B, status));
     int ngroups = 0;
     long long ao = 0;
     for (int i = 0; i < B.n; ++i) {
         Inst &I = B.in[i];
         ngroups = max(ngroups, (I.n_views + VGROUP - 1) / VGROUP);
-        I.npv = (I.nv + PR_ROWS - 1) / PR_ROWS;
+        I.npv = (I.nv + rows - 1) / rows;
         I.acc = acc + ao;  // z fastest, instances on 64-int boundaries
         ao += ((long long)I.g.nx * I.g.ny * I.g.nz + 63) / 64 * 64;
         I.vsz = 1;
@@ -1741,15 +1764,17 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
             const int smem = staging(B, status);
             if (kev && first) cudaEventRecord(kev[0], st);
             first = false;
-            bool single = true;
-            for (int i = 0; i < B.n; ++i) single = single && !B.in[i].multiz;
+            RayXY *tb = const_cast<RayXY *>(tab);
             if (smem > 0)
-                k_path<1, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
-            else if (single)
-                k_path_n<1, PR_NR><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled,
-                                                                  view_max);
+                k_path<1, true><<<pb, PR_THREADS, smem, st>>>(B, tb, sino_scaled, view_max);
+            else if (rows == PR_ROWS && multi_crossing(B))
+                k_path<1, false><<<pb, PR_THREADS, 0, st>>>(B, tb, sino_scaled, view_max);
+            else if (rows == PR_ROWS)
+                k_path_n<1, PR_NR, PR_ROWS><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, tb, sino_scaled, view_max);
+            else if (rows == 128)
+                k_path_n<1, PR_NR, 128><<<pb, 128 / PR_NR, 0, st>>>(B, tb, sino_scaled, view_max);
             else
-                k_path<1, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), sino_scaled, view_max);
+                k_path_n<1, PR_NR, 64><<<pb, 64 / PR_NR, 0, st>>>(B, tb, sino_scaled, view_max);
             counted(1);
             if (kev) cudaEventRecord(kev[1], st);
         }
