@@ -309,7 +309,9 @@ int dgr_densify(const dgr_grid *grid, const dgr_densify_cfg *cfg, int iters, con
  * grid, geometry, Gaussian count and optimiser state, advance by one dgr_step
  * each, every phase being ONE launch over the work of all instances (the
  * voxelizer's CTAs are persistent and pull tiles of every instance from one
- * queue).  probs, params, measured: host arrays [n_inst] (measured[i] a device
+ * queue; the projector and backprojector walks take one launch per detector
+ * height class present -- at most 64 rows, at most 128, taller -- whose CTAs
+ * cover that many rows).  probs, params, measured: host arrays [n_inst] (measured[i] a device
  * pointer); loss_out: device [n_inst].  The workspace plan must hold the sums
  * over instances: max_n, max_tiles, max_pairs, max_items, max_vox, max_rays,
  * max_views (sum of views), max_nu / max_nv (maxima) and max_inst >= n_inst.

@@ -1664,15 +1664,32 @@ static bool multi_crossing(const Batch &B) {
     return false;
 }
 
-// detector rows per CTA of the path walks: the two-ray walk (single-crossing
-// geometries, unstaged) takes CTAs of 64 or 128 rows when no instance's
-// detector is taller, so short detectors do not leave half or three quarters
-// of a 256-row CTA idle; otherwise 256
-static int walk_rows(const Batch &B, int smem) {
-    if (smem > 0 || multi_crossing(B)) return PR_ROWS;
-    int nv = 0;
-    for (int i = 0; i < B.n; ++i) nv = max(nv, B.in[i].nv);
-    return nv <= 64 ? 64 : (nv <= 128 ? 128 : PR_ROWS);
+// detector rows per CTA of an instance's path walks: the two-ray walk
+// (single-crossing geometries, unstaged) takes CTAs of 64 or 128 rows for
+// detectors no taller, so short detectors do not leave half or three quarters
+// of a 256-row CTA idle; 256 otherwise, and for every instance when full
+// (staged walks, or a multi-crossing geometry in the batch: the one-ray walk)
+static int inst_rows(const Inst &I, bool full) {
+    if (full) return PR_ROWS;
+    return I.nv <= 64 ? 64 : (I.nv <= 128 ? 128 : PR_ROWS);
+}
+constexpr int ROW_CLASSES[3] = {64, 128, PR_ROWS};
+
+// one launch of the walk over the blocks of the instances of one row class
+template <int MODE>
+static void launch_walk(const Batch &B, int rows, int pb, int smem, bool full, RayXY *tab, const float *sino_s,
+                        const unsigned *view_max, cudaStream_t st) {
+    if (smem > 0)
+        k_path<MODE, true><<<pb, PR_THREADS, smem, st>>>(B, tab, sino_s, view_max);
+    else if (full)
+        k_path<MODE, false><<<pb, PR_THREADS, 0, st>>>(B, tab, sino_s, view_max);
+    else if (rows == PR_ROWS)
+        k_path_n<MODE, PR_NR, PR_ROWS><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, tab, sino_s, view_max);
+    else if (rows == 128)
+        k_path_n<MODE, PR_NR, 128><<<pb, 128 / PR_NR, 0, st>>>(B, tab, sino_s, view_max);
+    else
+        k_path_n<MODE, PR_NR, 64><<<pb, 64 / PR_NR, 0, st>>>(B, tab, sino_s, view_max);
+    counted(1);
 }
 
 cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaStream_t st,
@@ -1689,33 +1706,25 @@ cudaError_t launch_project(const Batch &B0, const RayXY *tab, int *status, cudaS
         if (kev) cudaEventRecord(kev[1], st);
         return cudaGetLastError();
     }
-    // projector blocks: one detector column x `rows` rows of one view
+    // projector blocks: one detector column x `rows` rows of one view; one
+    // launch per row class present (a batch of short and tall detectors)
     static thread_local Batch B;
     B = B0;
     const int smem = staging(B, status);
-    const int rows = walk_rows(B, smem);
-    int pb = 0;
-    for (int i = 0; i < B.n; ++i) {
-        Inst &I = B.in[i];
-        I.npv = (I.nv + rows - 1) / rows;
-        I.pb0 = pb;
-        I.kv0 = 0;
-        I.nkv = I.n_views;
-        pb += I.n_views * I.nu * I.npv;
-    }
-    if (pb == 0) return cudaSuccess;
+    const bool full = smem > 0 || multi_crossing(B);
     if (kev) cudaEventRecord(kev[0], st);
-    if (smem > 0)
-        k_path<0, true><<<pb, PR_THREADS, smem, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
-    else if (rows == PR_ROWS && multi_crossing(B))
-        k_path<0, false><<<pb, PR_THREADS, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
-    else if (rows == PR_ROWS)
-        k_path_n<0, PR_NR, PR_ROWS><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
-    else if (rows == 128)
-        k_path_n<0, PR_NR, 128><<<pb, 128 / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
-    else
-        k_path_n<0, PR_NR, 64><<<pb, 64 / PR_NR, 0, st>>>(B, const_cast<RayXY *>(tab), nullptr, nullptr);
-    counted(1);
+    for (const int rows : ROW_CLASSES) {
+        int pb = 0;
+        for (int i = 0; i < B.n; ++i) {
+            Inst &I = B.in[i];
+            I.npv = inst_rows(I, full) == rows ? (I.nv + rows - 1) / rows : 0;
+            I.pb0 = pb;
+            I.kv0 = 0;
+            I.nkv = I.n_views;
+            pb += I.n_views * I.nu * I.npv;
+        }
+        if (pb > 0) launch_walk<0>(B, rows, pb, smem, full, const_cast<RayXY *>(tab), nullptr, nullptr, st);
+    }
     if (kev) cudaEventRecord(kev[1], st);
     return cudaGetLastError();
 }
@@ -1733,49 +1742,44 @@ cudaError_t launch_vol_zfast(const dgr_grid &g, const float *src, float *dst, cu
 static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const float *sino_scaled,
                                      const unsigned *view_max, int *acc, int *status, cudaStream_t st,
                                      const cudaEvent_t *kev) {
-    bool first = true;
     static thread_local Batch B;
     B = B0;
-    const int rows = walk_rows(B, staging(B, status));
+    const int smem = staging(B, status);
+    const bool full = smem > 0 || multi_crossing(B);
     int ngroups = 0;
     long long ao = 0;
     for (int i = 0; i < B.n; ++i) {
         Inst &I = B.in[i];
         ngroups = max(ngroups, (I.n_views + VGROUP - 1) / VGROUP);
-        I.npv = (I.nv + rows - 1) / rows;
         I.acc = acc + ao;  // z fastest, instances on 64-int boundaries
         ao += ((long long)I.g.nx * I.g.ny * I.g.nz + 63) / 64 * 64;
         I.vsz = 1;
         I.vsy = I.g.nz;
         I.vsx = I.g.ny * I.g.nz;
     }
+    bool first = true;
     for (int gi = 0; gi < ngroups; ++gi) {
-        int pb = 0, fb = 0;
+        int fb = 0;
         for (int i = 0; i < B.n; ++i) {
             Inst &I = B.in[i];
             I.kv0 = gi * VGROUP;
             I.nkv = max(0, min(VGROUP, I.n_views - I.kv0));
-            I.pb0 = pb;
-            pb += I.nkv * I.nu * I.npv;
             I.fb0 = fb;
             if (I.nkv > 0) fb += ((I.g.nx + 31) / 32) * ((I.g.ny + FOLD_Y - 1) / FOLD_Y) * ((I.g.nz + 31) / 32);
         }
-        if (pb > 0) {
-            const int smem = staging(B, status);
+        // the group's scatter: one launch per row class present
+        for (const int rows : ROW_CLASSES) {
+            int pb = 0;
+            for (int i = 0; i < B.n; ++i) {
+                Inst &I = B.in[i];
+                I.npv = inst_rows(I, full) == rows ? (I.nv + rows - 1) / rows : 0;
+                I.pb0 = pb;
+                pb += I.nkv * I.nu * I.npv;
+            }
+            if (pb == 0) continue;
             if (kev && first) cudaEventRecord(kev[0], st);
             first = false;
-            RayXY *tb = const_cast<RayXY *>(tab);
-            if (smem > 0)
-                k_path<1, true><<<pb, PR_THREADS, smem, st>>>(B, tb, sino_scaled, view_max);
-            else if (rows == PR_ROWS && multi_crossing(B))
-                k_path<1, false><<<pb, PR_THREADS, 0, st>>>(B, tb, sino_scaled, view_max);
-            else if (rows == PR_ROWS)
-                k_path_n<1, PR_NR, PR_ROWS><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, tb, sino_scaled, view_max);
-            else if (rows == 128)
-                k_path_n<1, PR_NR, 128><<<pb, 128 / PR_NR, 0, st>>>(B, tb, sino_scaled, view_max);
-            else
-                k_path_n<1, PR_NR, 64><<<pb, 64 / PR_NR, 0, st>>>(B, tb, sino_scaled, view_max);
-            counted(1);
+            launch_walk<1>(B, rows, pb, smem, full, const_cast<RayXY *>(tab), sino_scaled, view_max, st);
             if (kev) cudaEventRecord(kev[1], st);
         }
         if (fb > 0) {
