@@ -248,7 +248,7 @@ def run_ours(args, dist, rank, local):
     # that copy, the loss copied back every step; one interval from the first
     # copy to the last loss read, L2 flushes included
     meas_host = meas.cpu().pin_memory()
-    loss_host = torch.zeros(K).pin_memory()
+    loss_host = torch.zeros(max(K, W, 2)).pin_memory()
     meas_dev = [meas.clone() for _ in range(2)]
     # the step as a CUDA graph (graph.step_graph, the library's replayable
     # iteration), one per input buffer: one launch per step, so the host's
@@ -269,19 +269,30 @@ def run_ours(args, dist, rank, local):
             meas_dev[b].copy_(meas_host, non_blocking=True)
             copied[b].record(copy_stream)
 
+    def e2e_steps(n, first):
+        # n steps of the loop: the first step's copy is not overlapped (it
+        # waits for `first`), every later one overlaps the step before it
+        copy_stream.wait_event(first)
+        upload(0)
+        for k in range(n):
+            if k + 1 < n:
+                upload(k + 1)
+            flush.zero_()
+            stream.wait_event(copied[k & 1])
+            g_e2e[k & 1].replay()
+            used[k & 1].record(stream)
+            loss_host[k:k + 1].copy_(loss, non_blocking=True)
+
+    # untimed warm-up of the loop itself (each graph's first launch uploads
+    # it to the device; the copies and the pinned buffers are touched once)
+    e_warm = torch.cuda.Event()
+    e_warm.record(stream)
+    e2e_steps(max(W, 2), e_warm)
+    torch.cuda.synchronize()
     barrier(dist)
     torch.cuda.synchronize()
     e_start.record(stream)
-    copy_stream.wait_event(e_start)
-    upload(0)
-    for k in range(K):
-        if k + 1 < K:
-            upload(k + 1)
-        flush.zero_()
-        stream.wait_event(copied[k & 1])
-        g_e2e[k & 1].replay()
-        used[k & 1].record(stream)
-        loss_host[k:k + 1].copy_(loss, non_blocking=True)
+    e2e_steps(K, e_start)
     e_end.record(stream)
     torch.cuda.synchronize()
     barrier(dist)
@@ -302,7 +313,7 @@ def run_ours(args, dist, rank, local):
     kernels = {k: statistics.mean(v) for k, v in kernel_ms.items()}
     return dict(P=P, value=value, e2e=e2e_value, step_ms=statistics.mean(step_ms), phases=phases,
                 kernels=kernels, rates=rates,
-                launches=launches, clocks=clk, t_wall=t_wall, loss=float(loss_host[-1].item()))
+                launches=launches, clocks=clk, t_wall=t_wall, loss=float(loss_host[K - 1].item()))
 
 
 KERNEL_NAMES = {"project": "k_path_n<0, 2> (projector walk, two rays per thread)",
