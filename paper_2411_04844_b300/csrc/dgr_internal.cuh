@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <utility>
 
 #include "dgr.h"
 
@@ -276,6 +277,37 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 // host-side count of kernel launches issued by the library
 extern std::atomic<long long> g_launches;
 inline void counted(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Programmatic dependent launch.  A kernel launched by launch_dep may be
+// scheduled onto the SMs while the work before it in the stream is still
+// draining; DEP_ENTER, the first statement of every such kernel, waits until
+// that work has completed and its memory is visible (griddepcontrol.wait),
+// then lets the next kernel in the stream be scheduled in turn
+// (griddepcontrol.launch_dependents).  Nothing before DEP_ENTER touches
+// global memory, so the order of every read and write is that of plain
+// stream order; only the launch latency and the tail of each kernel are
+// overlapped.  Launched without the attribute, both instructions do nothing.
+#define DEP_ENTER()                                                   \
+    do {                                                              \
+        asm volatile("griddepcontrol.wait;" ::: "memory");             \
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+    } while (0)
+
+template <typename... P, typename... A>
+inline cudaError_t launch_dep(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              A &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 }  // namespace dgr
 

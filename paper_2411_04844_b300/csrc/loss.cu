@@ -97,6 +97,7 @@ __device__ __forceinline__ void blur_tile(const float (*in)[SHY][SHX], float (*h
 __global__ void __launch_bounds__(S_THREADS) k_ssim_stats(const __grid_constant__ Batch B,
                                                           float *__restrict__ maps,
                                                           float *__restrict__ spart) {
+    DEP_ENTER();
     __shared__ float in[5][SHY][SHX];
     __shared__ float hs[5][SHY][STX];
     const SsimTile T = ssim_tile(B, blockIdx.x);
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(S_THREADS) k_ssim_stats(const __grid_constant_
 __global__ void __launch_bounds__(S_THREADS) k_ssim_grad(const __grid_constant__ Batch B,
                                                          const float *__restrict__ maps,
                                                          float *__restrict__ gout) {
+    DEP_ENTER();
     __shared__ float in[3][SHY][SHX];
     __shared__ float hs[3][SHY][STX];
     const SsimTile T = ssim_tile(B, blockIdx.x);
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(S_THREADS) k_ssim_grad(const __grid_constant__
 constexpr int TVX = 32, TVY = 8, TVZ = 16;
 __global__ void __launch_bounds__(256) k_tv(const __grid_constant__ Batch B, float *__restrict__ tpart,
                                             int accumulate) {
+    DEP_ENTER();
     __shared__ float s[TVY + 2][TVZ + 2][TVX + 3];
     const Inst &I = B.in[inst_of_tv(B, blockIdx.x)];
     const dgr_grid &g = I.g;
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(256) k_tv(const __grid_constant__ Batch B, flo
 __global__ void k_loss_final(const __grid_constant__ Batch B, const float *__restrict__ l1part,
                              int l1_blocks, const float *__restrict__ spart,
                              const float *__restrict__ tpart) {
+    DEP_ENTER();
     const Inst &I = B.in[blockIdx.x];
     const double m = (double)I.n_views * I.nu * I.nv;
     double l1 = 0.0, ss = 0.0, tv = 0.0;
@@ -313,22 +317,22 @@ size_t tv_tiles_cap(long long max_vox, int ninst) {
 
 cudaError_t launch_ssim(const Batch &B, float *maps, float *spart, float *gout, cudaStream_t st) {
     if (B.tot_st == 0) return cudaSuccess;
-    k_ssim_stats<<<B.tot_st, S_THREADS, 0, st>>>(B, maps, spart);
-    k_ssim_grad<<<B.tot_st, S_THREADS, 0, st>>>(B, maps, gout);
+    launch_dep(k_ssim_stats, dim3(B.tot_st), dim3(S_THREADS), 0, st, B, maps, spart);
+    launch_dep(k_ssim_grad, dim3(B.tot_st), dim3(S_THREADS), 0, st, B, maps, gout);
     counted(2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tv(const Batch &B, float *tpart, int accumulate, cudaStream_t st) {
     if (B.tot_tv == 0) return cudaSuccess;
-    k_tv<<<B.tot_tv, 256, 0, st>>>(B, tpart, accumulate);
+    launch_dep(k_tv, dim3(B.tot_tv), dim3(256), 0, st, B, tpart, accumulate);
     counted(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_loss_final(const Batch &B, const float *l1part, int l1_blocks, const float *spart,
                               const float *tpart, cudaStream_t st) {
-    k_loss_final<<<B.n, 32, 0, st>>>(B, l1part, l1_blocks, spart, tpart);
+    launch_dep(k_loss_final, dim3(B.n), dim3(32), 0, st, B, l1part, l1_blocks, spart, tpart);
     counted(1);
     return cudaGetLastError();
 }

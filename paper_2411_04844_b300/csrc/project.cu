@@ -69,6 +69,7 @@ __device__ __forceinline__ float snap_layer(double xi) { return (float)(floor(xi
 
 // one thread per global RayXY entry, then per global RowZ entry
 __global__ void k_ray_tables(const __grid_constant__ Batch B, RayXY *__restrict__ tab) {
+    DEP_ENTER();
     const Tables T = tables_of(tab, B.tot_tab, B.tot_views);
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= B.tot_tab) {
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
                                                      RayXY *__restrict__ tab_base,
                                                      const float *__restrict__ sino_s,
                                                      const unsigned *__restrict__ view_max) {
+    DEP_ENTER();
     __shared__ Seg seg[SEG_MAX + WALK];
     // TMA: two stages of B.tma_ch cell columns of up to B.tma_zcap words each
     extern __shared__ __align__(128) float cols[];
@@ -789,6 +791,7 @@ template <int MODE, int NR, int ROWS>
 __global__ void __launch_bounds__(ROWS / NR, ROWS == PR_ROWS ? 0 : 8 * PR_ROWS / ROWS) k_path_n(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
                                                          const float *__restrict__ sino_s,
                                                          const unsigned *__restrict__ view_max) {
+    DEP_ENTER();
     static_assert(NR % 2 == 0 && ROWS % (32 * NR) == 0 && ROWS <= PR_ROWS, "pairs of rays, whole warps");
     constexpr int NT = ROWS / NR, NP = NR / 2;
     __shared__ Seg seg[SEG_MAX + WALK];
@@ -922,6 +925,7 @@ __global__ void __launch_bounds__(ROWS / NR, ROWS == PR_ROWS ? 0 : 8 * PR_ROWS /
 // cleared.  A 32 x 32 (x, z) tile at one y goes through shared memory so both
 // sides are coalesced.  blockIdx.x: global tile of the instances in the group.
 __global__ void k_bp_fold(const __grid_constant__ Batch B, const unsigned *__restrict__ view_max) {
+    DEP_ENTER();
     __shared__ float tile[32][33];
     int ii = 0;
     while (ii + 1 < B.n && B.in[ii + 1].fb0 <= (int)blockIdx.x) ++ii;
@@ -1265,6 +1269,7 @@ __global__ void __launch_bounds__(32 * BP_W, 3) k_backproject(const __grid_const
 // fixed-point step).  blockIdx.y: global view; blockIdx.x: 256 rays of it.
 __global__ void k_scale_dn(const __grid_constant__ Batch B, RayXY *__restrict__ tab_base,
                            float *__restrict__ out_base, unsigned *__restrict__ view_max) {
+    DEP_ENTER();
     __shared__ unsigned s_m;
     const Tables T = tables_of(tab_base, B.tot_tab, B.tot_views);
     const int vg = blockIdx.y;
@@ -1619,7 +1624,7 @@ int bp_blocks(const dgr_grid &g, int &nbx, int &nbz) {
 cudaError_t launch_ray_tables(const Batch &B, RayXY *tab, cudaStream_t st) {
     const int m = B.tot_tab + B.tot_rows;
     if (m == 0) return cudaSuccess;
-    k_ray_tables<<<(m + 127) / 128, 128, 0, st>>>(B, tab);
+    launch_dep(k_ray_tables, dim3((m + 127) / 128), dim3(128), 0, st, B, tab);
     counted(1);
     return cudaGetLastError();
 }
@@ -1680,15 +1685,15 @@ template <int MODE>
 static void launch_walk(const Batch &B, int rows, int pb, int smem, bool full, RayXY *tab, const float *sino_s,
                         const unsigned *view_max, cudaStream_t st) {
     if (smem > 0)
-        k_path<MODE, true><<<pb, PR_THREADS, smem, st>>>(B, tab, sino_s, view_max);
+        launch_dep(k_path<MODE, true>, dim3(pb), dim3(PR_THREADS), smem, st, B, tab, sino_s, view_max);
     else if (full)
-        k_path<MODE, false><<<pb, PR_THREADS, 0, st>>>(B, tab, sino_s, view_max);
+        launch_dep(k_path<MODE, false>, dim3(pb), dim3(PR_THREADS), 0, st, B, tab, sino_s, view_max);
     else if (rows == PR_ROWS)
-        k_path_n<MODE, PR_NR, PR_ROWS><<<pb, PR_ROWS / PR_NR, 0, st>>>(B, tab, sino_s, view_max);
+        launch_dep(k_path_n<MODE, PR_NR, PR_ROWS>, dim3(pb), dim3(PR_ROWS / PR_NR), 0, st, B, tab, sino_s, view_max);
     else if (rows == 128)
-        k_path_n<MODE, PR_NR, 128><<<pb, 128 / PR_NR, 0, st>>>(B, tab, sino_s, view_max);
+        launch_dep(k_path_n<MODE, PR_NR, 128>, dim3(pb), dim3(128 / PR_NR), 0, st, B, tab, sino_s, view_max);
     else
-        k_path_n<MODE, PR_NR, 64><<<pb, 64 / PR_NR, 0, st>>>(B, tab, sino_s, view_max);
+        launch_dep(k_path_n<MODE, PR_NR, 64>, dim3(pb), dim3(64 / PR_NR), 0, st, B, tab, sino_s, view_max);
     counted(1);
 }
 
@@ -1783,7 +1788,7 @@ static cudaError_t launch_bp_scatter(const Batch &B0, const RayXY *tab, const fl
             if (kev) cudaEventRecord(kev[1], st);
         }
         if (fb > 0) {
-            k_bp_fold<<<fb, 256, 0, st>>>(B, view_max);
+            launch_dep(k_bp_fold, dim3(fb), dim3(256), 0, st, B, view_max);
             counted(1);
         }
     }
@@ -1802,7 +1807,7 @@ cudaError_t launch_backproject(const Batch &B, const RayXY *tab, float *sino_sca
         if (e != cudaSuccess) return e;
         int max_per = 1;
         for (int i = 0; i < B.n; ++i) max_per = max(max_per, B.in[i].nu * B.in[i].nv);
-        k_scale_dn<<<dim3((max_per + 255) / 256, B.tot_views), 256, 0, st>>>(B, const_cast<RayXY *>(tab),
+        launch_dep(k_scale_dn, dim3((max_per + 255) / 256, B.tot_views), dim3(256), 0, st, B, const_cast<RayXY *>(tab),
                                                                            sino_scaled, view_max);
         counted(1);
         if (variant == 0) return launch_bp_scatter(B, tab, sino_scaled, view_max, acc, status, st, kev);

@@ -39,6 +39,7 @@ __device__ T block_exclusive_scan(T v, T *warp_tot, T *total) {
 }
 
 __global__ void k_block_sums(const uint32_t *in, int len, unsigned long long *bsum) {
+    DEP_ENTER();
     __shared__ unsigned long long wt[32];
     __shared__ unsigned long long tot;
     const long long base = (long long)blockIdx.x * SCAN_BLOCK + threadIdx.x * SCAN_PER_THREAD;
@@ -52,6 +53,7 @@ __global__ void k_block_sums(const uint32_t *in, int len, unsigned long long *bs
 
 __global__ void k_scan_block_sums(unsigned long long *bsum, int nb, uint32_t *out, int len,
                                   unsigned long long cap, int *status, int flag) {
+    DEP_ENTER();
     __shared__ unsigned long long wt[32];
     __shared__ unsigned long long tot;
     // nb <= SCAN_BLOCK: each thread owns SCAN_PER_THREAD consecutive sums
@@ -77,6 +79,7 @@ __global__ void k_scan_block_sums(unsigned long long *bsum, int nb, uint32_t *ou
 
 __global__ void k_block_scan(const uint32_t *in, int len, const unsigned long long *boff,
                              uint32_t *out) {
+    DEP_ENTER();
     __shared__ unsigned long long wt[32];
     __shared__ unsigned long long tot;
     const long long base = (long long)blockIdx.x * SCAN_BLOCK + threadIdx.x * SCAN_PER_THREAD;
@@ -98,6 +101,7 @@ __global__ void k_block_scan(const uint32_t *in, int len, const unsigned long lo
 // one block
 __global__ void k_scan_single(const uint32_t *in, int len, uint32_t *out, unsigned long long cap,
                               int *status, int flag) {
+    DEP_ENTER();
     __shared__ unsigned long long wt[32];
     __shared__ unsigned long long tot;
     const int base = threadIdx.x * SCAN_PER_THREAD;
@@ -133,13 +137,13 @@ cudaError_t scan_u32(const uint32_t *in, uint32_t *out, int len, unsigned long l
         return cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
     }
     if (nb == 1) {
-        k_scan_single<<<1, SCAN_THREADS, 0, st>>>(in, len, out, cap, status, flag);
+        launch_dep(k_scan_single, dim3(1), dim3(SCAN_THREADS), 0, st, in, len, out, cap, status, flag);
         counted(1);
         return cudaGetLastError();
     }
-    k_block_sums<<<nb, SCAN_THREADS, 0, st>>>(in, len, tmp);
-    k_scan_block_sums<<<1, SCAN_THREADS, 0, st>>>(tmp, nb, out, len, cap, status, flag);
-    k_block_scan<<<nb, SCAN_THREADS, 0, st>>>(in, len, tmp, out);
+    launch_dep(k_block_sums, dim3(nb), dim3(SCAN_THREADS), 0, st, in, len, tmp);
+    launch_dep(k_scan_block_sums, dim3(1), dim3(SCAN_THREADS), 0, st, tmp, nb, out, len, cap, status, flag);
+    launch_dep(k_block_scan, dim3(nb), dim3(SCAN_THREADS), 0, st, in, len, tmp, out);
     counted(3);
     return cudaGetLastError();
 }

@@ -46,6 +46,7 @@ __device__ __forceinline__ float l1_block(const float *pred, const float *meas, 
 __global__ void __launch_bounds__(L1_THREADS) k_l1(const __grid_constant__ Batch B,
                                                    float *__restrict__ part,
                                                    const float *__restrict__ gadd) {
+    DEP_ENTER();
     const Inst &I = B.in[blockIdx.y];
     const long long m = (long long)I.n_views * I.nu * I.nv;
     const float t = l1_block(I.sino, I.meas, m, I.sino, blockIdx.x, gridDim.x, I.w_l1,
@@ -120,6 +121,7 @@ __global__ void k_params_init(dgr_grid g, dgr_params p) {
 // Adam on the optimiser variables of every instance (thread per global
 // Gaussian); gradients w.r.t. (mu, s, q, rho) are read from Inst::g_*.
 __global__ void k_adam(const __grid_constant__ Batch B) {
+    DEP_ENTER();
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= B.tot_g) return;
     const Inst &I = B.in[inst_of_g(B, gi)];
@@ -163,13 +165,14 @@ __global__ void k_adam(const __grid_constant__ Batch B) {
 }
 
 __global__ void k_step_inc(const __grid_constant__ Batch B) {
+    DEP_ENTER();
     if (threadIdx.x < B.n) *B.in[threadIdx.x].step += 1;
 }
 
 }  // namespace
 
 cudaError_t launch_l1(const Batch &B, float *part, const float *gadd, cudaStream_t st) {
-    k_l1<<<dim3(L1_BLOCKS, B.n), L1_THREADS, 0, st>>>(B, part, gadd);
+    launch_dep(k_l1, dim3(L1_BLOCKS, B.n), dim3(L1_THREADS), 0, st, B, part, gadd);
     counted(1);
     return cudaGetLastError();
 }
@@ -191,10 +194,10 @@ cudaError_t launch_params_init(const dgr_problem &P, const dgr_params &p, cudaSt
 
 cudaError_t launch_adam(const Batch &B, cudaStream_t st) {
     if (B.tot_g > 0) {
-        k_adam<<<(B.tot_g + 127) / 128, 128, 0, st>>>(B);
+        launch_dep(k_adam, dim3((B.tot_g + 127) / 128), dim3(128), 0, st, B);
         counted(1);
     }
-    k_step_inc<<<1, 32, 0, st>>>(B);
+    launch_dep(k_step_inc, dim3(1), dim3(32), 0, st, B);
     counted(1);
     return cudaGetLastError();
 }

@@ -122,6 +122,7 @@ __global__ void k_footprint(dgr_grid g, int n, const float *__restrict__ mu,
 // a1: per-Gaussian prep (thread per global Gaussian index).
 __global__ void k_prep(const __grid_constant__ Batch B, Prep *__restrict__ prep,
                        uint32_t *__restrict__ itemcnt, int *status) {
+    DEP_ENTER();
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= B.tot_g) return;
     const Inst &I = B.in[inst_of_g(B, gi)];
@@ -264,6 +265,7 @@ __device__ __forceinline__ bool tile_range(const Prep &P, int tz, int &t0x, int 
 // a2: count Gaussians per tile (one warp per Gaussian, lanes over its tiles).
 __global__ void k_tile_count(const __grid_constant__ Batch B, const Prep *__restrict__ prep,
                              uint32_t *__restrict__ tile_cnt) {
+    DEP_ENTER();
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int gi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < B.tot_g; gi += warps) {
@@ -284,6 +286,7 @@ __global__ void k_tile_count(const __grid_constant__ Batch B, const Prep *__rest
 __global__ void k_tile_fill(const __grid_constant__ Batch B, const Prep *__restrict__ prep,
                             const uint32_t *__restrict__ tile_off, uint32_t *__restrict__ tile_fill,
                             uint32_t *__restrict__ list, unsigned long long cap) {
+    DEP_ENTER();
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int gi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < B.tot_g; gi += warps) {
@@ -392,6 +395,7 @@ __device__ __forceinline__ void plan_tile(const Batch &B, int t, const uint32_t 
 // does it otherwise)
 __global__ void k_split_plan(const __grid_constant__ Batch B, const uint32_t *__restrict__ tile_off,
                              unsigned long long cap, const VoxSplit S) {
+    DEP_ENTER();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < B.tot_tiles) plan_tile(B, t, tile_off, cap, S);
 }
@@ -455,6 +459,7 @@ __global__ void __launch_bounds__(256) k_tile_sort_warp(const __grid_constant__ 
                                                         const uint32_t *__restrict__ tile_off,
                                                         uint32_t *__restrict__ list, unsigned long long cap,
                                                         const VoxSplit S) {
+    DEP_ENTER();
     const int lane = threadIdx.x & 31;
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int ntiles = B.tot_tiles;
@@ -475,6 +480,7 @@ __global__ void __launch_bounds__(256) k_tile_sort_warp(const __grid_constant__ 
 __global__ void k_tile_sort(int ntiles, const uint32_t *__restrict__ tile_off,
                             uint32_t *__restrict__ list, uint32_t *__restrict__ scratch,
                             unsigned long long cap) {
+    DEP_ENTER();
     __shared__ uint32_t sm[SORT_SMEM];
     const int t = blockIdx.x;
     unsigned long long b = tile_off[t], e = tile_off[t + 1];
@@ -623,6 +629,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
     unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off, const VoxSplit S) {
+    DEP_ENTER();
     static_assert(TZ / TZG <= 4, "z groups are tracked in 4-bit masks");
     constexpr int NG = TZ / TZG;
     __shared__ VisitChunk vc;
@@ -845,6 +852,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize_sep(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ list,
     unsigned long long cap, int *__restrict__ queue, const int *__restrict__ sep_off, const VoxSplit S) {
+    DEP_ENTER();
     __shared__ float4 sp[VOX_CHUNK * 4];
     __shared__ __align__(16) float ez[VOX_CHUNK][SEP_TZ];
     // running sums and Kahan compensations, one column per thread (as in k_voxelize)
@@ -981,7 +989,7 @@ cudaError_t launch_footprint(const dgr_grid &g, int n, const float *mu, const fl
 cudaError_t launch_prep(const Batch &B, Prep *prep, uint32_t *itemcnt, int *status, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(status + SEP_FLAG, 0, sizeof(int), st);
     if (e != cudaSuccess || B.tot_g == 0) return e;
-    k_prep<<<(B.tot_g + 127) / 128, 128, 0, st>>>(B, prep, itemcnt, status);
+    launch_dep(k_prep, dim3((B.tot_g + 127) / 128), dim3(128), 0, st, B, prep, itemcnt, status);
     counted(1);
     return cudaGetLastError();
 }
@@ -999,7 +1007,7 @@ cudaError_t launch_count_pairs(const Batch &B, const Prep *prep, dgr_ws *ws, uns
     cudaError_t err = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * B.tot_tiles, st);
     if (err != cudaSuccess) return err;
     if (B.tot_g > 0) {
-        k_tile_count<<<warp_grid(B.tot_g), 256, 0, st>>>(B, prep, tile_cnt);
+        launch_dep(k_tile_count, dim3(warp_grid(B.tot_g)), dim3(256), 0, st, B, prep, tile_cnt);
         counted(1);
     }
     return scan_u32(tile_cnt, tile_off, B.tot_tiles, cap, status, DGR_STATUS_PAIR_OVERFLOW,
@@ -1015,11 +1023,11 @@ static cudaError_t launch_vox_tz(const Batch &B, const Prep *prep, const uint32_
     const int grid = max(1, min(units, wave_ctas((const void *)k_voxelize<TZ>, VOX_THREADS, 0)));
     // depth 32: the separable kernel as well; exactly one of the two does the work
     const bool sep = TZ == SEP_TZ && g_separable;
-    k_voxelize<TZ><<<grid, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep ? sep_flag : nullptr, S);
+    launch_dep(k_voxelize<TZ>, dim3(grid), dim3(VOX_THREADS), 0, st, B, prep, tile_off, list, cap, queue, sep ? sep_flag : nullptr, S);
     counted(1);
     if (sep) {
         const int grid2 = max(1, min(units, wave_ctas((const void *)k_voxelize_sep, VOX_THREADS, 0)));
-        k_voxelize_sep<<<grid2, VOX_THREADS, 0, st>>>(B, prep, tile_off, list, cap, queue, sep_flag, S);
+        launch_dep(k_voxelize_sep, dim3(grid2), dim3(VOX_THREADS), 0, st, B, prep, tile_off, list, cap, queue, sep_flag, S);
         counted(1);
     }
     return cudaGetLastError();
@@ -1039,18 +1047,18 @@ cudaError_t launch_voxelize(const Batch &B, const Prep *prep, dgr_ws *ws, int de
     if (err == cudaSuccess) err = cudaMemsetAsync(queue, 0, sizeof(int) * (VOX_SLOTCTR + MAX_INST - VOX_QUEUE), st);
     if (err != cudaSuccess) return err;
     if (B.tot_g > 0) {
-        k_tile_fill<<<warp_grid(B.tot_g), 256, 0, st>>>(B, prep, tile_off, tile_fill, list, cap);
+        launch_dep(k_tile_fill, dim3(warp_grid(B.tot_g)), dim3(256), 0, st, B, prep, tile_off, tile_fill, list, cap);
         counted(1);
     }
     const VoxSplit S = vox_split_of(ws_ptr<int>(ws, ws->vsplit), ws_ptr<float>(ws, ws->vpart),
                                     ws_ptr<int>(ws, ws->status), B.tot_tiles);
     if (deterministic) {
-        k_tile_sort_warp<<<(B.tot_tiles + 7) / 8, 256, 0, st>>>(B, tile_off, list, cap, S);
-        k_tile_sort<<<B.tot_tiles, SORT_THREADS, 0, st>>>(B.tot_tiles, tile_off, list,
+        launch_dep(k_tile_sort_warp, dim3((B.tot_tiles + 7) / 8), dim3(256), 0, st, B, tile_off, list, cap, S);
+        launch_dep(k_tile_sort, dim3(B.tot_tiles), dim3(SORT_THREADS), 0, st, B.tot_tiles, tile_off, list,
                                                           ws_ptr<uint32_t>(ws, ws->list_tmp), cap);
         counted(2);
     } else {
-        k_split_plan<<<(B.tot_tiles + 255) / 256, 256, 0, st>>>(B, tile_off, cap, S);
+        launch_dep(k_split_plan, dim3((B.tot_tiles + 255) / 256), dim3(256), 0, st, B, tile_off, cap, S);
         counted(1);
     }
     // persistent: enough CTAs to fill every SM, each pulling units from the queue

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
     const __grid_constant__ Batch B, const Prep *__restrict__ prep,
     const uint32_t *__restrict__ item_off, unsigned long long cap, float *__restrict__ part,
     int *__restrict__ queue) {
+    DEP_ENTER();
     const int n = B.tot_g;
     const int lane = threadIdx.x & 31;
     unsigned long long total = item_off[n];
@@ -298,6 +299,7 @@ __global__ void k_bwd_final(const __grid_constant__ Batch B,
                             const uint32_t *__restrict__ item_off, unsigned long long cap,
                             const float *__restrict__ part, uint32_t *__restrict__ big,
                             int *__restrict__ big_count) {
+    DEP_ENTER();
     // four lanes per Gaussian: lane c of the quad sums items b + c, b + c + 4,
     // ... (compensated FP32), two fixed butterfly steps combine the quad, lane
     // 0 of it finishes the chain rule
@@ -358,6 +360,7 @@ __global__ void __launch_bounds__(256) k_bwd_big(const __grid_constant__ Batch B
                                                  const float *__restrict__ part,
                                                  const uint32_t *__restrict__ big,
                                                  const int *__restrict__ big_count) {
+    DEP_ENTER();
     __shared__ double sred[256 / 32][NMOM];
     const int nbig = *big_count;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -426,12 +429,12 @@ cudaError_t launch_voxelize_backward(const Batch &B, const Prep *prep, dgr_ws *w
     if (err != cudaSuccess) return err;
     // one wave of resident CTAs; warps take runs of items from the queue
     if (kev && (err = cudaEventRecord(kev[0], st)) != cudaSuccess) return err;
-    k_bwd_items<<<wave_ctas((const void *)k_bwd_items, 256, 0), 256, 0, st>>>(B, prep, item_off, cap, part,
+    launch_dep(k_bwd_items, dim3(wave_ctas((const void *)k_bwd_items, 256, 0)), dim3(256), 0, st, B, prep, item_off, cap, part,
                                                                               status + ITEM_QUEUE);
     if (kev && (err = cudaEventRecord(kev[1], st)) != cudaSuccess) return err;
-    k_bwd_final<<<(unsigned)(((long long)B.tot_g * 4 + 127) / 128), 128, 0, st>>>(B, item_off, cap, part, big,
+    launch_dep(k_bwd_final, dim3((unsigned)(((long long)B.tot_g * 4 + 127) / 128)), dim3(128), 0, st, B, item_off, cap, part, big,
                                                                                     big_count);
-    k_bwd_big<<<148 * 2, 256, 0, st>>>(B, item_off, cap, part, big, big_count);
+    launch_dep(k_bwd_big, dim3(148 * 2), dim3(256), 0, st, B, item_off, cap, part, big, big_count);
     counted(3);
     return cudaGetLastError();
 }

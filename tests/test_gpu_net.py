@@ -2,10 +2,20 @@
 forward and every parameter gradient, the loss, Adam on flat arrays, the
 FDK-style filter and the seeding kernels.
 
-Tolerances: the oracle rounds to BF16 where the kernels store BF16, so the
-remaining differences are FP32-vs-FP64 accumulation order and the rare ReLU
-decision it flips: output relative L2 <= 2e-3, gradient relative L2 per layer
-<= 2e-2."""
+Tolerances.  The oracle rounds to BF16 exactly where the kernels store BF16
+(activations and data gradients), so what remains is FP32 versus FP64
+accumulation (about 1e-6 relative per GEMM output) and the BF16 roundings and
+ReLU decisions that this difference flips: a flipped rounding moves one stored
+value by one BF16 unit (2^-8 relative), and the later layers carry it on.
+Weight gradients are sums over every voxel of products of random sign, so a
+few flipped values weigh more in them than in the output.  The share of
+flipped values depends on the size and the data, not on the engine: all four
+convolution engines (and the CUDA-core first layer) show the same errors.
+Measured relative L2 errors on the B300 (output / worst gradient block of the
+12): 8^3 7e-6 / 1.3e-5; 12^3 and 16^3 1.7e-4 / 6e-4; 32^3 and 36^3 6.8e-4 /
+1.3e-2; 64^3 4.7e-4 / 3.5e-3.  The bounds below sit above those by 1.5x to
+15x: output 2e-3 (1e-4 at 8^3); gradients 1e-4 at 8^3, 2e-3 at 12^3 and
+16^3, 1e-2 at 64^3, 2e-2 at 32^3 and 36^3."""
 import numpy as np
 import pytest
 
@@ -65,7 +75,9 @@ def test_net_forward_and_gradients_match_oracle(n, engine):
     out, gp, status = run_net(n, P, x, gy, engine)
     assert status == 0
     yo, _ = N.forward(P.astype(np.float64), x, bf=True)
-    assert rel_l2(out.cpu().numpy(), yo) <= 2e-3, rel_l2(out.cpu().numpy(), yo)
+    tol_out = 1e-4 if n <= 8 else 2e-3
+    tol_g = 1e-4 if n <= 8 else 2e-3 if n <= 16 else 1e-2 if n >= 64 else 2e-2
+    assert rel_l2(out.cpu().numpy(), yo) <= tol_out, rel_l2(out.cpu().numpy(), yo)
     go = N.backward(P.astype(np.float64), x, gy, bf=True)
     g = gp.cpu().numpy()
     assert np.isfinite(g).all()
@@ -73,7 +85,7 @@ def test_net_forward_and_gradients_match_oracle(n, engine):
     for l, (ci, co, t) in enumerate(N.LAYERS):
         for name, sz in (("w", t * ci * co), ("b", co)):
             e = rel_l2(g[o:o + sz], go[o:o + sz])
-            assert e <= 2e-2, (l, name, e)
+            assert e <= tol_g, (l, name, e)
             o += sz
 
 
