@@ -45,6 +45,7 @@ extern "C" {
 #define DGR_STATUS_PAIR_OVERFLOW 0x20 /* (tile, Gaussian) work list exceeded the plan; volume incomplete */
 #define DGR_STATUS_ITEM_OVERFLOW 0x40 /* backward work items exceeded the plan; gradients incomplete */
 #define DGR_STATUS_TIMEOUT 0x80      /* a bounded wait inside a kernel gave up; its output is invalid */
+#define DGR_STATUS_BOUNDS 0x100      /* bounds-checked build only: an index fell outside its buffer; that access was skipped */
 
 /* Voxel grid: nx, ny, nz <= 32767 voxels of size h, min corner (ox, oy, oz).
  * z0 (>= 0, usually 0): this grid is the z-slab of layers [z0, z0 + nz) of a

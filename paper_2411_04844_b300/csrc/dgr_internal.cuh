@@ -293,6 +293,23 @@ inline void counted(int k) { g_launches.fetch_add(k, std::memory_order_relaxed);
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
     } while (0)
 
+// Bounds-checked build (-DDGR_CHECK_BOUNDS, libdgr_checked.so): the volume,
+// integer-sum and gradient accesses of the walks, the FVR adjoint and the
+// voxelizer's record loads test their index against the buffer's size; an
+// index outside it sets DGR_STATUS_BOUNDS in the status word and the access
+// is skipped (a load reads 0), so a bad index is reported instead of faulting.
+// In the default build DGR_INB is the constant true and the code is unchanged.
+#ifdef DGR_CHECK_BOUNDS
+__device__ __forceinline__ bool dgr_inb(long long i, long long n, int *status) {
+    if ((unsigned long long)i < (unsigned long long)n) return true;
+    if (status) atomicOr(status, DGR_STATUS_BOUNDS);
+    return false;
+}
+#define DGR_INB(i, n, status) dgr_inb((long long)(i), (long long)(n), (status))
+#else
+#define DGR_INB(i, n, status) true
+#endif
+
 template <typename... P, typename... A>
 inline cudaError_t launch_dep(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               A &&...args) {

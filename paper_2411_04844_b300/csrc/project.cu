@@ -332,7 +332,9 @@ template <int MODE, bool MASKZ, bool STAGED>
 __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *__restrict__ acci, float wq,
                                            const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
                                            float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
-                                           float xi0z, float iez) {
+                                           float xi0z, float iez, long long nvox, int *status) {
+    (void)nvox;
+    (void)status;
     // segments per unrolled group: 4 loads in flight for the projector; the
     // scatter keeps 2 (fewer registers, more resident warps)
     constexpr int NW = MODE == 0 ? WALK : 2;
@@ -371,9 +373,9 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
             float v0[NW], v1[NW];
 #pragma unroll
             for (int j = 0; j < NW; ++j) {
-                v0[j] = STAGED ? vol[a0[j]] : __ldg(vol + a0[j]);
+                v0[j] = STAGED ? vol[a0[j]] : ((STAGED || DGR_INB(a0[j], nvox, status)) ? __ldg(vol + a0[j]) : 0.f);
                 // the second segment's voxel only after a crossing (else l1 = 0)
-                v1[j] = l1[j] != 0.f ? (STAGED ? vol[a1[j]] : __ldg(vol + a1[j])) : 0.f;
+                v1[j] = l1[j] != 0.f ? (STAGED ? vol[a1[j]] : ((STAGED || DGR_INB(a1[j], nvox, status)) ? __ldg(vol + a1[j]) : 0.f)) : 0.f;
             }
 #pragma unroll
             for (int j = 0; j < NW; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
@@ -384,8 +386,8 @@ __device__ __forceinline__ void walk_segs1(const float *__restrict__ vol, int *_
                 // reduction; integer sums do not depend on how they are split
                 const float2 lw = __fmul2_rn(make_float2(l0[j], l1[j]), make_float2(wq, wq));
                 const int q0 = __float2int_rn(lw.x), q1 = __float2int_rn(lw.y);
-                atomicAdd(acci + a0[j], q0);
-                if (q1 != 0) atomicAdd(acci + a1[j], q1);
+                if (STAGED || DGR_INB(a0[j], nvox, status)) atomicAdd(acci + a0[j], q0);
+                if (q1 != 0 && (STAGED || DGR_INB(a1[j], nvox, status))) atomicAdd(acci + a1[j], q1);
             }
         }
     }
@@ -397,7 +399,9 @@ template <int MODE, bool MASKZ, bool STAGED>
 __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__restrict__ acci, float wq,
                                           const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
                                           float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
-                                          float xi0z, float iez) {
+                                          float xi0z, float iez, long long nvox, int *status) {
+    (void)nvox;
+    (void)status;
     // segments per unrolled group: 4 loads in flight for the projector; the
     // scatter keeps 2 (fewer registers, more resident warps)
     constexpr int NW = MODE == 0 ? WALK : 2;
@@ -438,8 +442,8 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
                     zc = min(max(iz, zl), zh);
                     if (!MASKZ || (unsigned)iz <= zmax) {
                         const float len = fminf(tz, t1) - ts;
-                        if (MODE == 0) acc = fmaf(len, STAGED ? vol[base + zc] : __ldg(vol + base + zc), acc);
-                        else if (len != 0.f) atomicAdd(acci + base + zc, __float2int_rn(len * wq));
+                        if (MODE == 0) acc = fmaf(len, STAGED ? vol[base + zc] : ((STAGED || DGR_INB(base + zc, nvox, status)) ? __ldg(vol + base + zc) : 0.f), acc);
+                        else if (len != 0.f && (STAGED || DGR_INB(base + zc, nvox, status))) atomicAdd(acci + base + zc, __float2int_rn(len * wq));
                     }
                 }
             }
@@ -449,16 +453,16 @@ __device__ __forceinline__ void walk_segs(const float *__restrict__ vol, int *__
             float v0[NW], v1[NW];
 #pragma unroll
             for (int j = 0; j < NW; ++j) {
-                v0[j] = STAGED ? vol[a0[j]] : __ldg(vol + a0[j]);
-                v1[j] = STAGED ? vol[a1[j]] : __ldg(vol + a1[j]);
+                v0[j] = STAGED ? vol[a0[j]] : ((STAGED || DGR_INB(a0[j], nvox, status)) ? __ldg(vol + a0[j]) : 0.f);
+                v1[j] = STAGED ? vol[a1[j]] : ((STAGED || DGR_INB(a1[j], nvox, status)) ? __ldg(vol + a1[j]) : 0.f);
             }
 #pragma unroll
             for (int j = 0; j < NW; ++j) acc = fmaf(l1[j], v1[j], fmaf(l0[j], v0[j], acc));
         } else {
 #pragma unroll
             for (int j = 0; j < NW; ++j) {
-                if (l0[j] != 0.f) atomicAdd(acci + a0[j], __float2int_rn(l0[j] * wq));
-                if (l1[j] != 0.f) atomicAdd(acci + a1[j], __float2int_rn(l1[j] * wq));
+                if (l0[j] != 0.f && (STAGED || DGR_INB(a0[j], nvox, status))) atomicAdd(acci + a0[j], __float2int_rn(l0[j] * wq));
+                if (l1[j] != 0.f && (STAGED || DGR_INB(a1[j], nvox, status))) atomicAdd(acci + a1[j], __float2int_rn(l1[j] * wq));
             }
         }
     }
@@ -469,17 +473,17 @@ template <int MODE, bool STAGED>
 __device__ __forceinline__ void walk_any(bool multiz, bool masked, const float *vol, int *acci, float wq,
                                          const Seg *seg, int c0, int r0, int r1, int nz, const Stage &G,
                                          float &t, float &acc, int &iz, float &fz, float &tz, int sgz,
-                                         float xi0z, float iez) {
+                                         float xi0z, float iez, long long nvox = 0, int *status = nullptr) {
     if (multiz) {
         if (masked)
-            walk_segs<MODE, true, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs<MODE, true, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez, nvox, status);
         else
-            walk_segs<MODE, false, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs<MODE, false, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez, nvox, status);
     } else {
         if (masked)
-            walk_segs1<MODE, true, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1<MODE, true, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez, nvox, status);
         else
-            walk_segs1<MODE, false, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1<MODE, false, STAGED>(vol, acci, wq, seg, c0, r0, r1, nz, G, t, acc, iz, fz, tz, sgz, xi0z, iez, nvox, status);
     }
 }
 
@@ -615,7 +619,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_path(const __grid_constant__ Bat
             // the CTA's rows) only takes part in the staging
             if (rg * PR_ROWS + w * 32 < I.nv)
                 walk_any<MODE, false>(I.multiz, masked, I.vol, I.acc, wq, seg, c0, c0, c1, g.nz, G, t, acc, iz,
-                                      fz, tz, sgz, Z.xi0z, Z.inv_ez);
+                                      fz, tz, sgz, Z.xi0z, Z.inv_ez, (long long)g.nx * g.ny * g.nz, B.status);
             continue;
         }
         // staged: sub-chunks of tma_ch cells, their z windows in shared memory
@@ -695,10 +699,13 @@ __device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, int
                                               const float2 (&wqv)[NR / 2], const Seg *seg, int c0, int r0, int r1,
                                               int nz, float &t, float2 (&acc)[NR / 2], int (&iz)[NR],
                                               float (&fz)[NR], float (&tz)[NR], const int (&sgz)[NR],
-                                              const float (&xi0z)[NR], const float (&iez)[NR]) {
+                                              const float (&xi0z)[NR], const float (&iez)[NR],
+                                              long long nvox, int *status) {
     // segments per unrolled group: 4 loads in flight for the projector; the
     // scatter keeps 2 (fewer registers)
     constexpr int NW = MODE == 0 ? WALK : 2, NP = NR / 2;
+    (void)nvox;
+    (void)status;
     const unsigned zmax = (unsigned)(nz - 1);
     int zc[NR];
     float fsg[NR];
@@ -757,10 +764,12 @@ __device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, int
             for (int j = 0; j < NW; ++j)
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    v0[j][p] = make_float2(__ldg(vol + a0[j][2 * p]), __ldg(vol + a0[j][2 * p + 1]));
+                    v0[j][p] = make_float2(DGR_INB(a0[j][2 * p], nvox, status) ? __ldg(vol + a0[j][2 * p]) : 0.f,
+                                           DGR_INB(a0[j][2 * p + 1], nvox, status) ? __ldg(vol + a0[j][2 * p + 1]) : 0.f);
                     // the second segment's voxel only after a crossing (else its length is 0)
-                    v1[j][p] = make_float2(l1[j][p].x != 0.f ? __ldg(vol + a1[j][2 * p]) : 0.f,
-                                           l1[j][p].y != 0.f ? __ldg(vol + a1[j][2 * p + 1]) : 0.f);
+                    v1[j][p] = make_float2(
+                        l1[j][p].x != 0.f && DGR_INB(a1[j][2 * p], nvox, status) ? __ldg(vol + a1[j][2 * p]) : 0.f,
+                        l1[j][p].y != 0.f && DGR_INB(a1[j][2 * p + 1], nvox, status) ? __ldg(vol + a1[j][2 * p + 1]) : 0.f);
                 }
 #pragma unroll
             for (int j = 0; j < NW; ++j)
@@ -777,10 +786,10 @@ __device__ __forceinline__ void walk_segs1_xn(const float *__restrict__ vol, int
                     const float2 w0 = __fmul2_rn(l0[j][p], wqv[p]), w1 = __fmul2_rn(l1[j][p], wqv[p]);
                     const int q0a = __float2int_rn(w0.x), q0b = __float2int_rn(w0.y);
                     const int q1a = __float2int_rn(w1.x), q1b = __float2int_rn(w1.y);
-                    atomicAdd(acci + a0[j][2 * p], q0a);
-                    atomicAdd(acci + a0[j][2 * p + 1], q0b);
-                    if (q1a != 0) atomicAdd(acci + a1[j][2 * p], q1a);
-                    if (q1b != 0) atomicAdd(acci + a1[j][2 * p + 1], q1b);
+                    if (DGR_INB(a0[j][2 * p], nvox, status)) atomicAdd(acci + a0[j][2 * p], q0a);
+                    if (DGR_INB(a0[j][2 * p + 1], nvox, status)) atomicAdd(acci + a0[j][2 * p + 1], q0b);
+                    if (q1a != 0 && DGR_INB(a1[j][2 * p], nvox, status)) atomicAdd(acci + a1[j][2 * p], q1a);
+                    if (q1b != 0 && DGR_INB(a1[j][2 * p + 1], nvox, status)) atomicAdd(acci + a1[j][2 * p + 1], q1b);
                 }
         }
     }
@@ -906,9 +915,11 @@ __global__ void __launch_bounds__(ROWS / NR, ROWS == PR_ROWS ? 0 : 8 * PR_ROWS /
             if (rg1 * ROWS + (int)(threadIdx.x >> 5) * 32 * NR >= I.nv) return;
         }
         if (masked)
-            walk_segs1_xn<MODE, true, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1_xn<MODE, true, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez,
+                                          (long long)g.nx * g.ny * g.nz, B.status);
         else
-            walk_segs1_xn<MODE, false, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez);
+            walk_segs1_xn<MODE, false, NR>(I.vol, I.acc, wqv, seg, c0, c0, c1, g.nz, t, acc, iz, fz, tz, sgz, xi0z, iez,
+                                           (long long)g.nx * g.ny * g.nz, B.status);
     }
     if (MODE == 0) {
 #pragma unroll

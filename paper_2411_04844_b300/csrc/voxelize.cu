@@ -678,7 +678,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_voxelize(
             if (c0 != b) __syncthreads();
             if (threadIdx.x < nc) {
                 const int j = threadIdx.x;
-                const float4 *pp = reinterpret_cast<const float4 *>(prep + list[c0 + j]);
+                uint32_t gj = list[c0 + j];
+                if (!DGR_INB(gj, B.tot_g, B.status)) gj = 0;  // (bounds-checked build) a bad list entry
+                const float4 *pp = reinterpret_cast<const float4 *>(prep + gj);
                 const float4 p0 = pp[0], p1 = pp[1], p2 = pp[2], p3 = pp[3];
                 const double2 n1 = reinterpret_cast<const double2 *>(pp + 4)[0],
                               zz = reinterpret_cast<const double2 *>(pp + 4)[1];

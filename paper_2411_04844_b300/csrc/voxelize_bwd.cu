@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
             const Inst &I = B.in[inst_of_g(B, gi)];
             const dgr_grid &g = I.g;
             const float *__restrict__ gv = I.gvol;
+            const long long nvox = (long long)g.nx * g.ny * g.nz;
+            (void)nvox;
             const Prep P = prep[gi];
             const float n1y = (float)P.n1y_d;
             const int lx = box_lo(P.bx), hx = box_hi(P.bx), ly = box_lo(P.by), hy = box_hi(P.by),
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
                     constexpr int U = decltype(U_)::value;
                     float gz[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) gz[u] = __ldg(col + u * zs);
+                    for (int u = 0; u < U; ++u)
+                        gz[u] = DGR_INB(col + u * zs - gv, nvox, B.status) ? __ldg(col + u * zs) : 0.f;
                     col += U * zs;
 #pragma unroll
                     for (int u = 0; u < U; u += 2) {
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd_items(
                 for (; z <= ze; ++z) {
                     const float t = t0 + (float)(z - zb);
                     const float e = ex2_approx(fmaf(P.a22 * t, t, qm));
-                    const float ge = __ldg(col) * e;
+                    const float ge = (DGR_INB(col - gv, nvox, B.status) ? __ldg(col) : 0.f) * e;
                     col += zs;
                     s0v.x += ge;
                     const float gt = ge * t;

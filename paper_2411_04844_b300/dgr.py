@@ -23,6 +23,7 @@ DGR_ERR_CUDA = 3
 DGR_STATUS_NONFINITE = 0x10
 DGR_STATUS_PAIR_OVERFLOW = 0x20
 DGR_STATUS_ITEM_OVERFLOW = 0x40
+DGR_STATUS_BOUNDS = 0x100  # bounds-checked build only (DGR_CHECK_BOUNDS=1)
 DGR_PARALLEL = 0
 DGR_CONE = 1
 
@@ -130,8 +131,15 @@ class DensifyCfg(ctypes.Structure):
         return cls(2e-4, 0.005, 17.0, int(n_max))
 
 
+def checked_build() -> bool:
+    """DGR_CHECK_BOUNDS=1 in the environment: load the bounds-checked library
+    (libdgr_checked.so; indices outside their buffers are reported as
+    DGR_STATUS_BOUNDS instead of faulting)."""
+    return os.environ.get("DGR_CHECK_BOUNDS", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked_build() else _build.LIB
 
 
 def lib():
@@ -139,7 +147,7 @@ def lib():
     library cannot be built or loaded -- there is no CPU fallback."""
     global _LIB
     if _LIB is None:
-        path = _build.build()
+        path = _build.build(checked=checked_build())
         if not os.path.exists(path):
             raise DgrError(f"libdgr not found at {path}")
         L = ctypes.CDLL(path)
